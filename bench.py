@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: correlation poses/sec of the FP32 NUFFT ball-union correlation.
+
+One step = one full correlation of a 20,000-ball ellipsoid with a 20,000-ball
+torus (L = 4 radius levels), 128^3 modes on a 256^3 oversampled grid, KB width
+8: both shapes' spreading, 3D transforms, deconvolution x ball transform x
+level sum, the conjugate product and the inverse transform onto the 128^3
+translation grid.  A pose is one (rotation, translation) pair evaluated, so a
+step evaluates 128^3 poses.
+
+Timing: device-side CUDA events on the stream the library launches on, one
+pair of events around each step; between steps a 256 MiB buffer is written so
+that every step starts with a cold L2.  W warm-up steps are untimed.  Under
+torchrun each rank runs its own correlation (replicas, weak scaling); the time
+is the maximum over ranks.
+
+Also reported: e2e (the same metric through the C ABI with pinned host
+buffers, host<->device copies inside the timed region), the live roofline of
+the dominant stage (CUDA events between stage launches inside the library),
+GPU clocks sampled during the timed region, and the FP64 oracle timed on the
+host cores (cpu_baseline).  `--impl reference` times the oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "correlation poses/sec at rel-L2≤1e-5 vs FP64 oracle; batched+learned vs plain"
+UNIT = "poses/s"
+L2_FLUSH_BYTES = 256 << 20
+
+# DRAM traffic per launch measured by ncu for the kernels below (one capture
+# each; see profiles/).  An entry counts only while the kernel source it was
+# measured on is unchanged (sha256 of csrc/bc_kernels.cu, first 16 hex digits).
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_1711_05075_gb300", "csrc", "bc_kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ workload
+def workload():
+    from paper_1711_05075_gb300 import synth
+    return synth.scale_pair(0)
+
+
+def f32_shape(S):
+    from paper_1711_05075_gb300 import synth
+    return synth.Shape(S.xyz.astype(np.float32).astype(np.float64), S.level, S.radii, S.name)
+
+
+# ------------------------------------------------------------------ oracle timing
+def oracle_sample(wl, fraction):
+    """The FP64 oracle on a bounded sample of the workload: the spectra of the
+    first `fraction` of each shape's knots plus the full-grid inverse.  The
+    spectra cost is linear in the knot count, so the full-workload time is
+    extrapolated as t_spectra / fraction + t_inverse."""
+    import oracle as O
+    from paper_1711_05075_gb300 import synth
+    nA = max(1, int(round(wl.A.n * fraction)))
+    nB = max(1, int(round(wl.B.n * fraction)))
+    A = f32_shape(wl.A)
+    B = f32_shape(wl.B)
+    A = synth.Shape(A.xyz[:nA], A.level[:nA], A.radii)
+    B = synth.Shape(B.xyz[:nB], B.level[:nB], B.radii)
+    q = wl.quats[0].astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    fa = O.shape_spectrum(A.xyz, A.level, A.radii, wl.N, None, wl.period)
+    fb = O.shape_spectrum(B.xyz, B.level, B.radii, wl.N, q, wl.period)
+    t1 = time.perf_counter()
+    O.inverse_grid(O.corr_spectrum(fa, fb), wl.period)
+    t2 = time.perf_counter()
+    full = (t1 - t0) * (wl.A.n + wl.B.n) / (nA + nB) + (t2 - t1)
+    return full, f"{nA}+{nB} of {wl.A.n}+{wl.B.n} knots (spectra time scaled by the knot ratio) + full {wl.N}^3 inverse"
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    wl = workload()
+    import oracle
+    oracle.build()
+    frac = args.ref_fraction
+    for _ in range(args.warmup):
+        oracle_sample(wl, frac)
+    times = []
+    desc = ""
+    for _ in range(args.steps):
+        t, desc = oracle_sample(wl, frac)
+        times.append(t)
+    ms = 1e3 * float(np.mean(times))
+    value = wl.N ** 3 / (ms * 1e-3)
+    cores = int(os.environ.get("OMP_NUM_THREADS", cpu_cores()))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(wl):
+    return {"workload": wl.name, "N": wl.N, "oversampled_grid": 2 * wl.N, "W": wl.W, "sigma": wl.sigma,
+            "period": wl.period, "knots": [wl.A.n, wl.B.n], "levels": list(wl.radii), "rotations_per_step": 1,
+            "poses_per_step": wl.N ** 3, "l2": "flushed between steps (256 MiB write)"}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import paper_1711_05075_gb300 as bc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    wl = workload()
+    ctx = bc.Context(wl.N, wl.W, wl.radii, wl.period, stream=stream)
+    A = ctx.shape(wl.A.xyz, wl.A.level)
+    B = ctx.shape(wl.B.xyz, wl.B.level)
+    q = wl.quats.astype(np.float32)
+    out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        ctx.correlate(A, B, q, out)
+    torch.cuda.synchronize(dev)
+
+    # ---- device-timed region
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local_rank)
+    if rank == 0:
+        clocks.start()
+    bc.bc_profile_begin(ctx.handle, args.steps)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        ctx.correlate(A, B, q, out)
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    t_wall1 = time.perf_counter()
+    prof = bc.bc_profile_end(ctx.handle)
+    clk = clocks.stop() if rank == 0 else None
+    ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_total = float(sum(ms_steps))
+    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_total = float(t.item())
+    ms_per_step = ms_total / args.steps
+    poses = world * args.steps * wl.N ** 3
+    value = poses / (ms_total * 1e-3)
+
+    # ---- e2e through the C ABI with pinned host buffers
+    xa = torch.from_numpy(wl.A.xyz.astype(np.float32)).pin_memory()
+    la = torch.from_numpy(wl.A.level.astype(np.int32)).pin_memory()
+    xb = torch.from_numpy(wl.B.xyz.astype(np.float32)).pin_memory()
+    lb = torch.from_numpy(wl.B.level.astype(np.int32)).pin_memory()
+    host_out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32).pin_memory()
+    h2d = (xa.numel() * 4 + la.numel() * 4 + xb.numel() * 4 + lb.numel() * 4 + q.nbytes)
+    d2h = host_out.numel() * 4
+
+    def e2e_step():
+        ha = bc.bc_shape_create(ctx.handle, xa, la, wl.A.n, 0)
+        hb = bc.bc_shape_create(ctx.handle, xb, lb, wl.B.n, 0)
+        bc.bc_correlate(ctx.handle, ha, hb, q, 1, host_out, 0)
+        bc.bc_shape_destroy(ha)
+        bc.bc_shape_destroy(hb)
+
+    for _ in range(max(args.warmup, 1)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    e_sum = 0.0
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize(dev)
+        s0 = time.perf_counter()
+        e2e_step()
+        e_sum += time.perf_counter() - s0
+    barrier()
+    te = torch.tensor([e_sum], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * args.steps * wl.N ** 3 / float(te.item())
+
+    # ---- roofline of the dominant stage
+    peak, peak_src = load_peaks()
+    stages = prof["stages"]
+    dom = max(stages, key=lambda s: s["ms"])
+    calls = max(prof["calls"], 1)
+    dom_ms = dom["ms"] / calls
+    achieved = dom["bytes"] / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0
+    kname = {"prepare": "k_prepare", "spread": "k_spread", "fft_z": "k_fft_z", "fft_y": "k_fft_y",
+             "fft_x": "k_fft_x", "ifft_y": "k_ifft_y", "ifft_z": "k_ifft_z"}[dom["name"]]
+    tr = NCU_TRAFFIC.get(kname)
+    traffic = tr["bytes"] if tr and tr.get("kernel_hash") == kernel_source_hash() else None
+    stage_share = {s["name"]: round(s["ms"] / max(sum(x["ms"] for x in stages), 1e-12), 4) for s in stages}
+
+    # ---- CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t_full, desc = oracle_sample(wl, args.ref_fraction)
+        cpu = {"value": wl.N ** 3 / t_full, "unit": UNIT,
+               "cores": int(os.environ.get("OMP_NUM_THREADS", cpu_cores())), "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(wl),
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(prof["launches"]),
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "note": f"peak {peak_src}; achieved = algorithmic bytes per launch / mean launch time "
+                                 f"({dom['bytes'] / 1e6:.1f} MB / {dom_ms * 1e3:.1f} us)"},
+            "stage_ms": {s["name"]: round(s["ms"] / calls, 5) for s in stages},
+            "stage_share": stage_share,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "wall_s_timed_region": t_wall1 - t_wall0,
+        }
+        print(json.dumps(line), flush=True)
+    A.close()
+    B.close()
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-fraction", type=float, default=0.25,
+                    help="knot fraction of the oracle's bounded sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

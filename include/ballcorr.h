@@ -1,0 +1,155 @@
+/*
+ * ballcorr: Fourier-domain translational correlation of two unions of balls on
+ * an NVIDIA GB300 (sm_103a).  C ABI; no C++ or framework types cross it.
+ *
+ * What it computes (Behandish & Ilies, "Analytic methods for geometric modeling
+ * via spherical decomposition"):
+ *
+ *   A shape X is a set of knots c_j (centres) with radii drawn from L levels
+ *   rho_1..rho_L; its defining function is the sum of the ball indicators
+ *   (Eq. (un), Sec. 2.1; the alpha -> infinity limit of Eq. (psi), Sec. 2.2).
+ *   Per level the knots form the impulse density of Eq. (rhoP), whose
+ *   transform is the nonequispaced sum of Eq. (rhoPhat) (Sec. 2.5):
+ *       S_{X,l}(m) = sum_{j in level l} exp(-2 pi i m . x_j / P).
+ *   The shape spectrum is the level sum of Eq. (fballhat):
+ *       f^_X(m) = sum_l h^(rho_l, k) S_{X,l}(m),  h^(r,k) = 4 pi (sin kr - kr cos kr)/k^3,
+ *       k = 2 pi |m| / P,
+ *   and the correlation of A with B rotated by R (Eq. (relg), Sec. 3.1) is, in
+ *   the Fourier domain, Eq. (ccghat) (Sec. 3.2):
+ *       g^(m) = f^_A(m) conj(f^_{RB}(m)),
+ *       g(t)  = P^-3 sum_m g^(m) exp(+2 pi i m . t / P)   (App. C).
+ *   Modes m lie in [-N/2, N/2)^3; modes with a component equal to -N/2 are
+ *   zero, so g is real.  g is sampled on t_k = -P/2 + k P/N, k = 0..N-1 per
+ *   axis, and is periodic with period P (knots outside [-P/2, P/2) wrap).
+ *
+ * How: each level's S_{X,l} is a type-1 nonuniform FFT (Kaiser-Bessel
+ * spreading onto a sigma*N oversampled grid, a 3D FFT, division by the window
+ * transform); the window division, the ball transform, the level sum, the
+ * conjugate product and the inverse transform run in fused CUDA kernels.
+ * Floating point work is FP32; the window and ball-transform tables are built
+ * in FP64 on the device and rounded once.
+ *
+ * Conventions for every call:
+ *   - Every function returns a bc_status; nothing throws across the ABI.
+ *     bc_last_error() gives a message for the calling thread's last failure.
+ *   - Work is enqueued on the context's CUDA stream and is asynchronous unless
+ *     a host buffer is involved (then the call synchronises that stream).
+ *   - "device" pointers are CUDA device (or managed) memory of the current
+ *     device; "host" pointers are ordinary or pinned host memory.
+ *   - Caller-owned buffers stay caller-owned; the library copies what it keeps
+ *     and owns all of its internal workspaces.
+ */
+#ifndef BALLCORR_H
+#define BALLCORR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bc_ctx_s *bc_ctx_t;
+typedef struct bc_shape_s *bc_shape_t;
+
+typedef enum {
+    BC_OK = 0,
+    BC_ERR_ARG = 1,         /* invalid argument (sizes, pointers, level id, zero quaternion) */
+    BC_ERR_OOM = 2,         /* device allocation failed */
+    BC_ERR_CUDA = 3,        /* a CUDA call failed; see bc_last_error() */
+    BC_ERR_TIMEOUT = 4,     /* a bounded device-side wait expired */
+    BC_ERR_UNSUPPORTED = 5, /* parameters outside what this build supports */
+    BC_ERR_INTERNAL = 6     /* a device-side consistency check failed */
+} bc_status;
+
+#define BC_MAX_LEVELS 8
+
+/* Correlation parameters.  Supported: N in {32, 64, 96, 128, 256}, sigma = 2
+ * (so the oversampled grid has n = 2N points per axis), 2 <= W <= 10.
+ * beta is rounded to FP32 once; the window and its FP64 transform table both
+ * use that rounded value. */
+typedef struct {
+    int N;                     /* modes per axis = translation samples per axis */
+    int sigma;                 /* oversampling factor of the spreading grid (2) */
+    int W;                     /* Kaiser-Bessel window width in fine-grid cells */
+    double beta;               /* window shape; <= 0 selects pi*sqrt((W/sigma)^2 (sigma-1/2)^2 - 0.8) */
+    double period;             /* P > 0: the translation grid covers [-P/2, P/2)^3 */
+    int level_count;           /* L, 1..BC_MAX_LEVELS */
+    const double *level_radii; /* host array of L radii (> 0); copied */
+    int precision;             /* 0 = FP32 (the only value accepted) */
+} bc_params;
+
+/* Creates a context on the current CUDA device bound to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Builds the window,
+ * ball-transform and twiddle tables.  Errors: BC_ERR_ARG (null pointer,
+ * parameters out of range), BC_ERR_UNSUPPORTED, BC_ERR_OOM, BC_ERR_CUDA. */
+bc_status bc_create(const bc_params *params, void *cuda_stream, bc_ctx_t *out);
+
+/* Synchronises the context stream and frees everything it owns, including the
+ * device memory of shapes still alive on it (their handles stay valid only for
+ * bc_shape_destroy).  NULL is accepted. */
+bc_status bc_destroy(bc_ctx_t ctx);
+
+/* Uploads a shape: n knots, xyz = n x 3 FP32 centres (row major), level = n
+ * level ids in [0, L).  `on_device` says whether both arrays are device (1) or
+ * host (0) memory.  The library copies them; the caller keeps its arrays.
+ * Synchronises the context stream (it validates levels and sizes workspaces).
+ * n = 0 gives an empty shape, whose correlation with anything is 0.
+ * Errors: BC_ERR_ARG (null pointer with n > 0, n < 0, level out of range,
+ * non-finite coordinate), BC_ERR_OOM, BC_ERR_CUDA. */
+bc_status bc_shape_create(bc_ctx_t ctx, const float *xyz, const int *level, int n, int on_device,
+                          bc_shape_t *out);
+
+/* Frees a shape (stream-ordered after pending work on the context).  NULL is accepted.
+ * A shape whose context was destroyed first has already lost its device memory;
+ * this call then only releases the handle. */
+bc_status bc_shape_destroy(bc_shape_t shape);
+
+/* g(R_q, t) for k rotations of B:  out[r][kx][ky][kz] = g(R(q_r), t_k), an
+ * FP32 array of k * N^3 values, kz fastest.  quats: k x 4 FP32 (w, x, y, z),
+ * normalised internally, host memory.  A is not rotated.  `out_on_device`
+ * selects device (1, asynchronous) or host (0, synchronous) output memory.
+ * Errors: BC_ERR_ARG (k < 1, null pointer, zero quaternion, shapes from
+ * another context), BC_ERR_OOM, BC_ERR_CUDA, BC_ERR_INTERNAL. */
+bc_status bc_correlate(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quats, int k,
+                       float *out, int out_on_device);
+
+/* Waits for the context stream and reports any device-side error raised by
+ * earlier asynchronous calls (BC_ERR_INTERNAL, BC_ERR_TIMEOUT) or CUDA error. */
+bc_status bc_sync(bc_ctx_t ctx);
+
+/* ---------------------------------------------------------------- profiling
+ * Per-stage device times of bc_correlate, taken with CUDA events recorded on
+ * the context stream between the stage launches, and the algorithmic bytes of
+ * each stage (every input read once, every output written once), computed
+ * from the support boxes of the last profiled call.  Stages, in launch order:
+ * 0 prepare (rotation + support boxes), 1 spread, 2 fft_z, 3 fft_y,
+ * 4 fft_x (with deconvolution, ball transform, level sum, conjugate product
+ * and inverse x), 5 ifft_y, 6 ifft_z. */
+#define BC_NUM_STAGES 7
+typedef struct {
+    int calls;                   /* profiled bc_correlate calls */
+    long long launches;          /* kernels this library launched during them */
+    double ms[BC_NUM_STAGES];    /* summed device time per stage */
+    double bytes[BC_NUM_STAGES]; /* algorithmic bytes per stage and call */
+} bc_profile;
+
+/* Starts recording the next `max_calls` calls (events are created here, not in
+ * the calls).  Errors: BC_ERR_ARG, BC_ERR_CUDA. */
+bc_status bc_profile_begin(bc_ctx_t ctx, int max_calls);
+
+/* Waits for the stream, fills `out` and stops recording.  Errors: BC_ERR_ARG
+ * (null pointer or no bc_profile_begin), BC_ERR_CUDA. */
+bc_status bc_profile_end(bc_ctx_t ctx, bc_profile *out);
+
+/* Name of stage i (0 <= i < BC_NUM_STAGES), or "" out of range. */
+const char *bc_stage_name(int i);
+
+/* Message for the calling thread's most recent failure ("" if none). */
+const char *bc_last_error(void);
+
+/* Library version string. */
+const char *bc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BALLCORR_H */

@@ -1,0 +1,230 @@
+"""GB300 (sm_103a) ball-union correlation: Python binding of libballcorr.so.
+
+The binding only marshals arguments: every step of the correlation runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  There is
+no CPU fallback: if the library is missing or cannot load, `lib()` raises.
+
+Functions named bc_* mirror the C ABI in include/ballcorr.h one to one; the
+`Context` / `Shape` classes wrap them for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import weakref
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+BC_STATUS = {0: "BC_OK", 1: "BC_ERR_ARG", 2: "BC_ERR_OOM", 3: "BC_ERR_CUDA", 4: "BC_ERR_TIMEOUT",
+             5: "BC_ERR_UNSUPPORTED", 6: "BC_ERR_INTERNAL"}
+BC_MAX_LEVELS = 8
+
+
+BC_NUM_STAGES = 7
+
+
+class bc_profile(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double * BC_NUM_STAGES),
+                ("bytes", ctypes.c_double * BC_NUM_STAGES)]
+
+
+class BallCorrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{BC_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class bc_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("sigma", ctypes.c_int), ("W", ctypes.c_int), ("beta", ctypes.c_double),
+                ("period", ctypes.c_double), ("level_count", ctypes.c_int),
+                ("level_radii", ctypes.POINTER(ctypes.c_double)), ("precision", ctypes.c_int)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libballcorr.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libballcorr.so not found at {path}")
+        L = ctypes.CDLL(path)
+        vp, i, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_int
+        L.bc_create.argtypes = [ctypes.POINTER(bc_params), vp, ctypes.POINTER(vp)]
+        L.bc_destroy.argtypes = [vp]
+        L.bc_shape_create.argtypes = [vp, vp, vp, i, i, ctypes.POINTER(vp)]
+        L.bc_shape_destroy.argtypes = [vp]
+        L.bc_correlate.argtypes = [vp, vp, vp, vp, i, vp, i]
+        L.bc_sync.argtypes = [vp]
+        for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sync"):
+            getattr(L, f).restype = st
+        L.bc_last_error.restype = ctypes.c_char_p
+        L.bc_last_error.argtypes = []
+        L.bc_version.restype = ctypes.c_char_p
+        L.bc_version.argtypes = []
+        L.bc_profile_begin.argtypes = [vp, i]
+        L.bc_profile_begin.restype = st
+        L.bc_profile_end.argtypes = [vp, ctypes.POINTER(bc_profile)]
+        L.bc_profile_end.restype = st
+        L.bc_stage_name.argtypes = [i]
+        L.bc_stage_name.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise BallCorrError(status, lib().bc_last_error().decode())
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (no copies are made here)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------- C ABI mirror
+def bc_create(N, W, radii, period=2.0, beta=0.0, sigma=2, precision=0, stream=None):
+    radii = np.ascontiguousarray(radii, dtype=np.float64)
+    p = bc_params(int(N), int(sigma), int(W), float(beta), float(period), int(radii.size),
+                  radii.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(precision))
+    h = ctypes.c_void_p()
+    s = None if stream is None else ctypes.c_void_p(stream)
+    _check(lib().bc_create(ctypes.byref(p), s, ctypes.byref(h)))
+    return h
+
+
+def bc_destroy(ctx):
+    _check(lib().bc_destroy(ctx))
+
+
+def bc_shape_create(ctx, xyz, level, n, on_device):
+    h = ctypes.c_void_p()
+    _check(lib().bc_shape_create(ctx, _ptr(xyz), _ptr(level), int(n), int(on_device), ctypes.byref(h)))
+    return h
+
+
+def bc_shape_destroy(shape):
+    _check(lib().bc_shape_destroy(shape))
+
+
+def bc_correlate(ctx, A, B, quats, k, out, out_on_device):
+    _check(lib().bc_correlate(ctx, A, B, _ptr(quats), int(k), _ptr(out), int(out_on_device)))
+
+
+def bc_sync(ctx):
+    _check(lib().bc_sync(ctx))
+
+
+def bc_version() -> str:
+    return lib().bc_version().decode()
+
+
+def bc_profile_begin(ctx, max_calls):
+    _check(lib().bc_profile_begin(ctx, int(max_calls)))
+
+
+def bc_profile_end(ctx):
+    """Returns {calls, launches, stages: [{name, ms, bytes}]} for the profiled calls."""
+    p = bc_profile()
+    _check(lib().bc_profile_end(ctx, ctypes.byref(p)))
+    return {"calls": p.calls, "launches": p.launches,
+            "stages": [{"name": lib().bc_stage_name(s).decode(), "ms": p.ms[s], "bytes": p.bytes[s]}
+                       for s in range(BC_NUM_STAGES)]}
+
+
+# ---------------------------------------------------------------- convenience
+def default_beta(W, sigma=2):
+    return math.pi * math.sqrt((W / sigma) ** 2 * (sigma - 0.5) ** 2 - 0.8)
+
+
+class Context:
+    """Correlation context on the current CUDA device and a torch stream."""
+
+    def __init__(self, N, W, radii, period=2.0, beta=0.0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.N, self.W, self.period = int(N), int(W), float(period)
+        self.radii = tuple(float(r) for r in radii)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = bc_create(N, W, radii, period, beta, stream=self.stream.cuda_stream)
+        self._shapes = weakref.WeakSet()
+
+    def shape(self, xyz, level):
+        s = Shape(self, xyz, level)
+        self._shapes.add(s)
+        return s
+
+    def correlate(self, A, B, quats, out=None):
+        """g for each rotation: a (k, N, N, N) float32 CUDA tensor (or `out`)."""
+        import torch
+        q = np.ascontiguousarray(np.asarray(quats, dtype=np.float32).reshape(-1, 4))
+        k = q.shape[0]
+        if out is None:
+            out = torch.empty((k, self.N, self.N, self.N), dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.is_contiguous() and out.dtype == torch.float32 and out.numel() == k * self.N ** 3
+        bc_correlate(self.handle, A.handle, B.handle, q, k, out, 1)
+        return out
+
+    def correlate_host(self, A, B, quats, out):
+        """Same, writing into host memory `out` (numpy array or pinned tensor); synchronous."""
+        q = np.ascontiguousarray(np.asarray(quats, dtype=np.float32).reshape(-1, 4))
+        bc_correlate(self.handle, A.handle, B.handle, q, q.shape[0], out, 0)
+        return out
+
+    def sync(self):
+        bc_sync(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            for s in list(self._shapes):
+                s.close()
+            bc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Shape:
+    """A union of balls uploaded to the device: xyz (n x 3) and level ids (n)."""
+
+    def __init__(self, ctx: Context, xyz, level):
+        import torch
+        self.ctx = ctx
+        if hasattr(xyz, "is_cuda") and xyz.is_cuda:
+            x = xyz.to(torch.float32).contiguous()
+            l = level.to(torch.int32).contiguous()
+            self.n = x.shape[0]
+            self.handle = bc_shape_create(ctx.handle, x, l, self.n, 1)
+        else:
+            x = np.ascontiguousarray(np.asarray(xyz, dtype=np.float32).reshape(-1, 3))
+            l = np.ascontiguousarray(np.asarray(level, dtype=np.int32).reshape(-1))
+            self.n = x.shape[0]
+            self.handle = bc_shape_create(ctx.handle, x, l, self.n, 0)
+
+    def close(self):
+        if self.handle is not None:
+            bc_shape_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,554 @@
+// C-ABI of the ball-union correlation library (declared in include/ballcorr.h).
+//
+// The context owns the FP64-built tables and every workspace; a correlation
+// call fills instance/pair descriptors on the host, copies them to the device
+// and enqueues the kernel sequence on the context stream.  Nothing here does
+// arithmetic of the method: the host code sizes buffers, validates arguments
+// and launches kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "../../include/ballcorr.h"
+#include "bc_internal.h"
+
+using namespace bc;
+
+static thread_local std::string g_last_error;
+
+static bc_status fail(bc_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+static bc_status cuda_fail(cudaError_t e, const char *where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return (e == cudaErrorMemoryAllocation) ? BC_ERR_OOM : BC_ERR_CUDA;
+}
+
+#define CK(call)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);                                              \
+    } while (0)
+
+namespace {
+
+// A device buffer that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t need, bool zero, cudaStream_t s)
+    {
+        if (need <= bytes) return cudaSuccess;
+        if (p) {
+            cudaStreamSynchronize(s);
+            cudaFree(p);
+            p = nullptr;
+            bytes = 0;
+        }
+        size_t cap = need + need / 4 + 256;
+        cudaError_t e = cudaMalloc(&p, cap);
+        if (e != cudaSuccess) return e;
+        bytes = cap;
+        if (zero) return cudaMemsetAsync(p, 0, cap, s);
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+} // namespace
+
+struct bc_ctx_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int nsm = 1;
+    Geometry g{};
+    double beta = 0, period = 2.0;
+    std::vector<double> radii;
+    // tables
+    double *radii_dev = nullptr;
+    float *deconv = nullptr, *ballft = nullptr;
+    float2 *tw_n = nullptr, *tw_N = nullptr;
+    float *consts = nullptr; // [0] = exp(beta) / I0(beta)
+    int qmax = 0;
+    // device status word
+    int *err_dev = nullptr;
+    // workspaces
+    DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, outbuf, stats;
+    std::vector<char> last_desc;            // descriptors the device copies hold
+    void *last_inst_p = nullptr, *last_pairs_p = nullptr;
+    bool grid_dirty = false;
+    std::set<bc_shape_s *> shapes; // live shapes; orphaned (device memory freed) by bc_destroy
+    // profiling
+    bool prof_on = false;
+    int prof_max = 0, prof_calls = 0;
+    long long prof_launches = 0;
+    std::vector<cudaEvent_t> prof_ev; // prof_max x (BC_NUM_STAGES + 1)
+    int last_ninst = 0, last_npairs = 0;
+    std::vector<InstDesc> last_inst;
+};
+
+struct bc_shape_s {
+    bc_ctx_t ctx = nullptr;
+    int n = 0;
+    float4 *knots = nullptr;
+    float rmax = 0.f;
+};
+
+static const char *kStageNames[BC_NUM_STAGES] = {"prepare", "spread", "fft_z", "fft_y", "fft_x", "ifft_y", "ifft_z"};
+
+static void prof_free(bc_ctx_t c)
+{
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->prof_on = false;
+    c->prof_max = c->prof_calls = 0;
+    c->prof_launches = 0;
+}
+
+// Records the event that ends stage `stage` (-1 = start) of the current profiled call.
+static void prof_mark(bc_ctx_t c, int stage)
+{
+    if (!c->prof_on || c->prof_calls >= c->prof_max) return;
+    cudaEventRecord(c->prof_ev[(size_t)c->prof_calls * (BC_NUM_STAGES + 1) + (stage + 1)], c->stream);
+}
+
+static Tables tables_of(bc_ctx_t c)
+{
+    Tables t;
+    t.deconv = c->deconv;
+    t.ballft = c->ballft;
+    t.tw_n = c->tw_n;
+    t.tw_N = c->tw_N;
+    t.qmax = c->qmax;
+    t.consts = c->consts;
+    return t;
+}
+
+// Per-axis capacity of an instance's support box: the stencil cells of knots
+// with |u| <= U = rmax n / P span at most 2U + W + 1 cells; beyond n/2 the
+// coordinates may wrap and the box is the whole period.
+static int cap_extent(const bc_ctx_t c, float rmax)
+{
+    const double U = (double)rmax * c->g.n / c->period;
+    if (U >= 0.5 * c->g.n - 1.0) return c->g.n;
+    int e = (int)std::ceil(2.0 * U) + c->g.W + 3;
+    return e > c->g.n ? c->g.n : e;
+}
+
+extern "C" {
+
+const char *bc_last_error(void) { return g_last_error.c_str(); }
+
+const char *bc_version(void) { return "ballcorr 0.1 (sm_103a, FP32 type-1 NUFFT correlation)"; }
+
+bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
+{
+    try {
+        if (!p || !out) return fail(BC_ERR_ARG, "bc_create: null pointer");
+        *out = nullptr;
+        if (p->precision != 0) return fail(BC_ERR_UNSUPPORTED, "bc_create: only precision 0 (FP32) is supported");
+        if (p->sigma != 2) return fail(BC_ERR_UNSUPPORTED, "bc_create: sigma must be 2");
+        if (!supported_N(p->N)) return fail(BC_ERR_UNSUPPORTED, "bc_create: N must be one of 32, 64, 96, 128, 256");
+        if (p->W < 2 || p->W > 10 || p->W > p->N) return fail(BC_ERR_ARG, "bc_create: W must be in [2, 10] and <= N");
+        if (!(p->period > 0) || !std::isfinite(p->period)) return fail(BC_ERR_ARG, "bc_create: period must be > 0");
+        if (p->level_count < 1 || p->level_count > BC_MAX_LEVELS)
+            return fail(BC_ERR_ARG, "bc_create: level_count must be in [1, 8]");
+        if (!p->level_radii) return fail(BC_ERR_ARG, "bc_create: level_radii is null");
+        for (int l = 0; l < p->level_count; l++)
+            if (!(p->level_radii[l] > 0) || !std::isfinite(p->level_radii[l]))
+                return fail(BC_ERR_ARG, "bc_create: radii must be finite and > 0");
+        double beta = p->beta;
+        if (!(beta > 0)) {
+            const double a = (double)p->W / p->sigma * (p->sigma - 0.5);
+            beta = M_PI * std::sqrt(a * a - 0.8);
+        }
+        if (!std::isfinite(beta) || beta <= 0 || beta > 80) return fail(BC_ERR_ARG, "bc_create: beta out of range");
+        // The spreading kernel evaluates the window with an FP32 beta; the FP64
+        // deconvolution table must describe that same window.
+        beta = (double)(float)beta;
+
+        bc_ctx_t c = new (std::nothrow) bc_ctx_s();
+        if (!c) return fail(BC_ERR_OOM, "bc_create: host allocation failed");
+        c->stream = (cudaStream_t)cuda_stream;
+        cudaError_t e0 = cudaGetDevice(&c->device);
+        if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+        if (e0 != cudaSuccess) {
+            delete c;
+            return cuda_fail(e0, "bc_create: device query");
+        }
+        c->beta = beta;
+        c->period = p->period;
+        c->radii.assign(p->level_radii, p->level_radii + p->level_count);
+        Geometry &g = c->g;
+        g.N = p->N;
+        g.n = p->sigma * p->N;
+        g.W = p->W;
+        g.L = p->level_count;
+        g.H = p->N / 2;
+        g.beta = (float)beta;
+        g.n_over_P = (float)(g.n / p->period);
+        g.inv_P3 = (float)(1.0 / (p->period * p->period * p->period));
+        c->qmax = 3 * (g.N / 2) * (g.N / 2);
+        auto bail = [&](cudaError_t e, const char *w) {
+            bc_status s = cuda_fail(e, w);
+            bc_destroy(c);
+            return s;
+        };
+        cudaError_t e;
+        if ((e = cudaMalloc(&c->radii_dev, sizeof(double) * g.L)) != cudaSuccess) return bail(e, "cudaMalloc radii");
+        if ((e = cudaMalloc(&c->deconv, sizeof(float) * g.N)) != cudaSuccess) return bail(e, "cudaMalloc deconv");
+        if ((e = cudaMalloc(&c->ballft, sizeof(float) * g.L * (c->qmax + 1))) != cudaSuccess) return bail(e, "cudaMalloc ballft");
+        if ((e = cudaMalloc(&c->tw_n, sizeof(float2) * g.n)) != cudaSuccess) return bail(e, "cudaMalloc tw_n");
+        if ((e = cudaMalloc(&c->tw_N, sizeof(float2) * g.N)) != cudaSuccess) return bail(e, "cudaMalloc tw_N");
+        if ((e = cudaMalloc(&c->consts, sizeof(float) * 4)) != cudaSuccess) return bail(e, "cudaMalloc consts");
+        if ((e = cudaMalloc(&c->err_dev, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc err");
+        if ((e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream)) != cudaSuccess) return bail(e, "memset err");
+        if ((e = cudaMemcpyAsync(c->radii_dev, c->radii.data(), sizeof(double) * g.L, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+            return bail(e, "copy radii");
+        if ((e = launch_build_tables(g, beta, p->period, c->radii_dev, c->deconv, c->ballft, c->tw_n, c->tw_N, c->consts, c->stream)) != cudaSuccess)
+            return bail(e, "build tables");
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(e, "bc_create sync");
+        *out = c;
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_create: unexpected exception");
+    }
+}
+
+bc_status bc_destroy(bc_ctx_t c)
+{
+    if (!c) return BC_OK;
+    try {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->radii_dev);
+        cudaFree(c->deconv);
+        cudaFree(c->ballft);
+        cudaFree(c->tw_n);
+        cudaFree(c->tw_N);
+        cudaFree(c->err_dev);
+        cudaFree(c->consts);
+        prof_free(c);
+        for (bc_shape_s *s : c->shapes) {
+            if (s->knots) cudaFree(s->knots);
+            s->knots = nullptr;
+            s->ctx = nullptr;
+        }
+        c->shapes.clear();
+        DevBuf *bufs[] = {&c->ku, &c->plan, &c->inst, &c->pairs, &c->grid, &c->z1, &c->y1, &c->h, &c->fa, &c->outbuf, &c->stats};
+        for (DevBuf *b : bufs) b->release();
+        delete c;
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_destroy: unexpected exception");
+    }
+}
+
+bc_status bc_shape_create(bc_ctx_t c, const float *xyz, const int *level, int n, int on_device, bc_shape_t *out)
+{
+    try {
+        if (!c || !out) return fail(BC_ERR_ARG, "bc_shape_create: null context or output");
+        *out = nullptr;
+        if (n < 0) return fail(BC_ERR_ARG, "bc_shape_create: n < 0");
+        if (n > 0 && (!xyz || !level)) return fail(BC_ERR_ARG, "bc_shape_create: null knot arrays");
+        if (n >= (1 << 26)) return fail(BC_ERR_ARG, "bc_shape_create: too many knots");
+        bc_shape_t s = new (std::nothrow) bc_shape_s();
+        if (!s) return fail(BC_ERR_OOM, "bc_shape_create: host allocation failed");
+        s->ctx = c;
+        s->n = n;
+        if (n == 0) {
+            c->shapes.insert(s);
+            *out = s;
+            return BC_OK;
+        }
+        cudaStream_t st = c->stream;
+        auto bail = [&](cudaError_t e, const char *w) {
+            bc_status r = cuda_fail(e, w);
+            if (s->knots) cudaFreeAsync(s->knots, st);
+            delete s;
+            return r;
+        };
+        cudaError_t e;
+        if ((e = cudaMallocAsync((void **)&s->knots, sizeof(float4) * n, st)) != cudaSuccess) return bail(e, "cudaMallocAsync knots");
+        const float *dx = xyz;
+        const int *dl = level;
+        void *staging = nullptr;
+        if (!on_device) {
+            if ((e = cudaMallocAsync(&staging, sizeof(float) * 3 * n + sizeof(int) * n, st)) != cudaSuccess)
+                return bail(e, "cudaMallocAsync staging");
+            float *sx = (float *)staging;
+            int *sl = (int *)(sx + 3 * (size_t)n);
+            if ((e = cudaMemcpyAsync(sx, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return bail(e, "copy xyz");
+            if ((e = cudaMemcpyAsync(sl, level, sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return bail(e, "copy level");
+            dx = sx;
+            dl = sl;
+        }
+        if ((e = c->stats.ensure(2 * sizeof(unsigned int), false, st)) != cudaSuccess) return bail(e, "stats");
+        unsigned int *stats = (unsigned int *)c->stats.p;
+        if ((e = cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return bail(e, "memset stats");
+        if ((e = launch_pack_knots(dx, dl, n, c->g.L, s->knots, stats, st)) != cudaSuccess) return bail(e, "pack knots");
+        unsigned int hs[2] = {0, 0};
+        if ((e = cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return bail(e, "copy stats");
+        if (staging && (e = cudaFreeAsync(staging, st)) != cudaSuccess) return bail(e, "free staging");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "bc_shape_create sync");
+        if (hs[1] & 1u) {
+            cudaFreeAsync(s->knots, st);
+            delete s;
+            return fail(BC_ERR_ARG, "bc_shape_create: level id out of range [0, L)");
+        }
+        if (hs[1] & 2u) {
+            cudaFreeAsync(s->knots, st);
+            delete s;
+            return fail(BC_ERR_ARG, "bc_shape_create: non-finite knot coordinate");
+        }
+        float r2;
+        std::memcpy(&r2, &hs[0], sizeof(float));
+        s->rmax = std::sqrt(r2) * (1.0f + 1e-6f);
+        c->shapes.insert(s);
+        *out = s;
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_shape_create: unexpected exception");
+    }
+}
+
+bc_status bc_shape_destroy(bc_shape_t s)
+{
+    if (!s) return BC_OK;
+    try {
+        if (s->ctx) { // not orphaned by bc_destroy
+            if (s->knots) cudaFreeAsync(s->knots, s->ctx->stream);
+            s->ctx->shapes.erase(s);
+        }
+        delete s;
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_shape_destroy: unexpected exception");
+    }
+}
+
+bc_status bc_sync(bc_ctx_t c)
+{
+    if (!c) return fail(BC_ERR_ARG, "bc_sync: null context");
+    CK(cudaStreamSynchronize(c->stream));
+    int herr = 0;
+    CK(cudaMemcpy(&herr, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) {
+        CK(cudaMemset(c->err_dev, 0, sizeof(int)));
+        return fail(BC_ERR_INTERNAL, "device-side check failed (support box exceeded its capacity)");
+    }
+    return BC_OK;
+}
+
+const char *bc_stage_name(int i) { return (i >= 0 && i < BC_NUM_STAGES) ? kStageNames[i] : ""; }
+
+bc_status bc_profile_begin(bc_ctx_t c, int max_calls)
+{
+    if (!c || max_calls < 1 || max_calls > (1 << 16)) return fail(BC_ERR_ARG, "bc_profile_begin: bad arguments");
+    CK(cudaStreamSynchronize(c->stream));
+    prof_free(c);
+    c->prof_ev.resize((size_t)max_calls * (BC_NUM_STAGES + 1));
+    for (auto &ev : c->prof_ev) CK(cudaEventCreate(&ev));
+    c->prof_max = max_calls;
+    c->prof_on = true;
+    return BC_OK;
+}
+
+bc_status bc_profile_end(bc_ctx_t c, bc_profile *out)
+{
+    if (!c || !out) return fail(BC_ERR_ARG, "bc_profile_end: null argument");
+    if (!c->prof_on) return fail(BC_ERR_ARG, "bc_profile_end: bc_profile_begin was not called");
+    std::memset(out, 0, sizeof(*out));
+    CK(cudaStreamSynchronize(c->stream));
+    out->calls = c->prof_calls;
+    out->launches = c->prof_launches;
+    for (int k = 0; k < c->prof_calls; k++) {
+        for (int s = 0; s < BC_NUM_STAGES; s++) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->prof_ev[(size_t)k * (BC_NUM_STAGES + 1) + s],
+                                    c->prof_ev[(size_t)k * (BC_NUM_STAGES + 1) + s + 1]));
+            out->ms[s] += ms;
+        }
+    }
+    // algorithmic bytes of the last call, from its device plan
+    if (c->prof_calls > 0 && c->last_ninst > 0) {
+        std::vector<InstPlan> pl(c->last_ninst);
+        CK(cudaMemcpy(pl.data(), c->plan.p, sizeof(InstPlan) * c->last_ninst, cudaMemcpyDeviceToHost));
+        const double L = c->g.L, N = c->g.N, H = c->g.H;
+        double knots = 0, cells = 0, zc = 0, yc = 0;
+        for (int i = 0; i < c->last_ninst; i++) {
+            const double b0 = pl[i].b[0], b1 = pl[i].b[1], b2 = pl[i].b[2];
+            knots += c->last_inst[i].nknots;
+            cells += L * b0 * b1 * b2;   // spreading boxes
+            zc += L * b0 * b1 * H;       // z-transformed rows
+            yc += L * b0 * N * H;        // y-transformed planes
+        }
+        const double P = c->last_npairs, half = N * N * H;
+        out->bytes[0] = knots * 16.0 * 2.0;                 // knots in, prepared knots out
+        out->bytes[1] = knots * 16.0 + cells * 4.0;         // prepared knots in, boxes out
+        out->bytes[2] = cells * 4.0 + zc * 8.0;
+        out->bytes[3] = zc * 8.0 + yc * 8.0;
+        out->bytes[4] = yc * 8.0 + P * half * 8.0;
+        out->bytes[5] = 2.0 * P * half * 8.0;
+        out->bytes[6] = P * half * 8.0 + P * N * N * N * 4.0;
+    }
+    prof_free(c);
+    return BC_OK;
+}
+
+bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, int k, float *out,
+                       int out_on_device)
+{
+    try {
+        if (!c || !A || !B || !quats || !out) return fail(BC_ERR_ARG, "bc_correlate: null argument");
+        if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_correlate: shapes belong to another context");
+        if (k < 1 || k > (1 << 20)) return fail(BC_ERR_ARG, "bc_correlate: k must be in [1, 2^20]");
+        for (int r = 0; r < k; r++) {
+            const float *q = quats + 4 * r;
+            double n2 = (double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] + (double)q[3] * q[3];
+            if (!(n2 > 1e-30) || !std::isfinite(n2)) return fail(BC_ERR_ARG, "bc_correlate: zero or non-finite quaternion");
+        }
+        cudaStream_t st = c->stream;
+        const Geometry &g = c->g;
+        const int N = g.N, H = g.H, L = g.L;
+        const int ninst = 1 + k;
+        const long long N3 = (long long)N * N * N;
+
+        // host-side descriptors
+        std::vector<InstDesc> inst(ninst);
+        long long goff = 0, zoff = 0, yoff = 0;
+        int koff = 0;
+        for (int i = 0; i < ninst; i++) {
+            bc_shape_t s = i == 0 ? A : B;
+            InstDesc &d = inst[i];
+            d.knot_off = koff;
+            d.nknots = s->n;
+            d.src_off = 0;
+            d.knots = s->knots;
+            const int e = cap_extent(c, s->rmax);
+            d.cap_e = e;
+            d.grid_off = goff;
+            d.z1_off = zoff;
+            d.y1_off = yoff;
+            if (i == 0) {
+                d.q[0] = 1.f;
+                d.q[1] = d.q[2] = d.q[3] = 0.f;
+            } else {
+                for (int a = 0; a < 4; a++) d.q[a] = quats[4 * (i - 1) + a];
+            }
+            koff += s->n;
+            goff += (long long)L * e * e * ((e + 3) & ~3);
+            zoff += (long long)L * e * e * H;
+            yoff += (long long)L * e * N * H;
+        }
+        const bool fused = (k == 1);
+        const int npairs_main = k;
+        std::vector<PairDesc> pairs;
+        if (!fused) pairs.push_back(PairDesc{0, -1, 0, 0}); // spectrum of A into the cache
+        for (int r = 0; r < k; r++)
+            pairs.push_back(PairDesc{fused ? 0 : -1, 1 + r, (long long)r * N * N * H, (long long)r * N3});
+        const int npairs = (int)pairs.size();
+
+        cudaError_t e;
+        if ((e = c->ku.ensure(sizeof(float4) * (size_t)(koff > 0 ? koff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "ku");
+        if ((e = c->plan.ensure(sizeof(InstPlan) * ninst, false, st)) != cudaSuccess) return cuda_fail(e, "plan");
+        if ((e = c->inst.ensure(sizeof(InstDesc) * ninst, false, st)) != cudaSuccess) return cuda_fail(e, "inst");
+        if ((e = c->pairs.ensure(sizeof(PairDesc) * npairs, false, st)) != cudaSuccess) return cuda_fail(e, "pairs");
+        const size_t grid_before = c->grid.bytes;
+        if ((e = c->grid.ensure(sizeof(float) * (size_t)(goff > 0 ? goff : 1), true, st)) != cudaSuccess) return cuda_fail(e, "grid");
+        if (c->grid_dirty && c->grid.bytes == grid_before) {
+            if ((e = cudaMemsetAsync(c->grid.p, 0, c->grid.bytes, st)) != cudaSuccess) return cuda_fail(e, "grid clear");
+        }
+        c->grid_dirty = false;
+        if ((e = c->z1.ensure(sizeof(float2) * (size_t)(zoff > 0 ? zoff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "z1");
+        if ((e = c->y1.ensure(sizeof(float2) * (size_t)(yoff > 0 ? yoff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "y1");
+        if ((e = c->h.ensure(sizeof(float2) * (size_t)k * N * N * H, false, st)) != cudaSuccess) return cuda_fail(e, "h");
+        if (!fused && (e = c->fa.ensure(sizeof(float2) * (size_t)N * N * H, false, st)) != cudaSuccess) return cuda_fail(e, "fa");
+        float *dout = out;
+        if (!out_on_device) {
+            if ((e = c->outbuf.ensure(sizeof(float) * (size_t)k * N3, false, st)) != cudaSuccess) return cuda_fail(e, "outbuf");
+            dout = (float *)c->outbuf.p;
+        }
+
+        // descriptors -> device, only when they differ from what the device already holds
+        const size_t inst_bytes = sizeof(InstDesc) * ninst, pair_bytes = sizeof(PairDesc) * npairs;
+        std::vector<char> desc(inst_bytes + pair_bytes);
+        std::memcpy(desc.data(), inst.data(), inst_bytes);
+        std::memcpy(desc.data() + inst_bytes, pairs.data(), pair_bytes);
+        if (desc != c->last_desc || c->inst.p != c->last_inst_p || c->pairs.p != c->last_pairs_p) {
+            if ((e = cudaMemcpyAsync(c->inst.p, desc.data(), inst_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(e, "copy inst");
+            if ((e = cudaMemcpyAsync(c->pairs.p, desc.data() + inst_bytes, pair_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(e, "copy pairs");
+            c->last_desc.swap(desc);
+            c->last_inst_p = c->inst.p;
+            c->last_pairs_p = c->pairs.p;
+        }
+
+        const InstDesc *dinst = (const InstDesc *)c->inst.p;
+        const Tables t = tables_of(c);
+        InstPlan *dplan = (InstPlan *)c->plan.p;
+        const PairDesc *dpairs = (const PairDesc *)c->pairs.p;
+        c->grid_dirty = true; // until the z pass has consumed the spreading boxes
+        const bool prof = c->prof_on && c->prof_calls < c->prof_max;
+        prof_mark(c, -1);
+        if ((e = launch_prepare(g, dinst, ninst, (float4 *)c->ku.p, dplan, c->err_dev, st)) != cudaSuccess) return cuda_fail(e, "prepare");
+        prof_mark(c, 0);
+        if ((e = launch_spread(g, t, dinst, koff, (const float4 *)c->ku.p, dplan, (float *)c->grid.p, st)) != cudaSuccess)
+            return cuda_fail(e, "spread");
+        prof_mark(c, 1);
+        if ((e = launch_fft_z(g, t, dinst, ninst, dplan, (float *)c->grid.p, (float2 *)c->z1.p, c->nsm, st)) != cudaSuccess)
+            return cuda_fail(e, "fft z");
+        c->grid_dirty = false;
+        prof_mark(c, 2);
+        if ((e = launch_fft_y(g, t, dinst, ninst, dplan, (const float2 *)c->z1.p, (float2 *)c->y1.p, c->nsm, st)) != cudaSuccess)
+            return cuda_fail(e, "fft y");
+        prof_mark(c, 3);
+        if (!fused) {
+            if ((e = launch_fft_x(g, t, dinst, dplan, dpairs, 1, (const float2 *)c->y1.p, nullptr, (float2 *)c->fa.p,
+                                  (float2 *)c->h.p, c->nsm, st)) != cudaSuccess)
+                return cuda_fail(e, "fft x (A)");
+        }
+        const PairDesc *pmain = dpairs + (fused ? 0 : 1);
+        if ((e = launch_fft_x(g, t, dinst, dplan, pmain, npairs_main, (const float2 *)c->y1.p, (const float2 *)c->fa.p,
+                              nullptr, (float2 *)c->h.p, c->nsm, st)) != cudaSuccess)
+            return cuda_fail(e, "fft x");
+        prof_mark(c, 4);
+        if ((e = launch_ifft_y(g, t, pmain, npairs_main, (float2 *)c->h.p, c->nsm, st)) != cudaSuccess) return cuda_fail(e, "ifft y");
+        prof_mark(c, 5);
+        if ((e = launch_ifft_z(g, t, pmain, npairs_main, (const float2 *)c->h.p, dout, c->nsm, st)) != cudaSuccess)
+            return cuda_fail(e, "ifft z");
+        prof_mark(c, 6);
+        if (prof) {
+            c->prof_calls++;
+            c->prof_launches += fused ? 7 : 8;
+            c->last_ninst = ninst;
+            c->last_npairs = npairs_main;
+            c->last_inst = inst;
+        }
+        if (!out_on_device) {
+            if ((e = cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)k * N3, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return cuda_fail(e, "copy out");
+            return bc_sync(c);
+        }
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_correlate: unexpected exception");
+    }
+}
+
+} // extern "C"

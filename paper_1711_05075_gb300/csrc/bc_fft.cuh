@@ -1,0 +1,154 @@
+// Batched one-dimensional FFTs in shared memory (FP32), used by every
+// transform pass of the correlation.
+//
+// Algorithm: the self-sorting Stockham formulation of the Cooley-Tukey FFT
+// (T. G. Stockham, 1966; as arranged for GPUs by Govindaraju et al.,
+// "High performance discrete Fourier transforms on graphics processors",
+// SC 2008).  A length-NF transform runs as a sequence of radix-R stages; with
+// Ns the product of the radices already applied, butterfly j of a stage reads
+// x[j + r NF/R] (r < R), multiplies input r by w^(r (j mod Ns) NF/(Ns R)),
+// applies an R-point DFT and writes y[(j div Ns) Ns R + (j mod Ns) + r Ns].
+// Output is in natural order after the last stage; stages ping-pong between
+// two shared-memory buffers.  Radix schedules: 32 = 4.8, 64 = 8.8,
+// 96 = 3.4.8, 128 = 2.8.8, 192 = 3.8.8, 256 = 4.8.8, 512 = 8.8.8.
+//
+// Direction: forward uses exp(-2 pi i jk/NF), inverse exp(+2 pi i jk/NF); no
+// scaling.  The twiddle table holds exp(-2 pi i k/NF), k < NF, rounded once
+// from FP64; the inverse conjugates it.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace bc {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a)
+{
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_small(float2 *v)
+{
+    if constexpr (R == 2) {
+        float2 t = v[0];
+        v[0] = cadd(t, v[1]);
+        v[1] = csub(t, v[1]);
+    } else if constexpr (R == 3) {
+        // exp(-+2 pi i/3) = -1/2 -+ i sqrt(3)/2
+        const float s = INV ? 0.86602540378443864676f : -0.86602540378443864676f;
+        float2 t1 = cadd(v[1], v[2]);
+        float2 t2 = csub(v[1], v[2]);
+        float2 m = make_float2(fmaf(-0.5f, t1.x, v[0].x), fmaf(-0.5f, t1.y, v[0].y));
+        float2 r = make_float2(-s * t2.y, s * t2.x); // i s t2
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(m, r);
+        v[2] = csub(m, r);
+    } else if constexpr (R == 4) {
+        float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        float2 b0 = cadd(v[1], v[3]), b1 = mul_mi<INV>(csub(v[1], v[3]));
+        v[0] = cadd(a0, b0);
+        v[2] = csub(a0, b0);
+        v[1] = cadd(a1, b1);
+        v[3] = csub(a1, b1);
+    } else if constexpr (R == 8) {
+        const float h = 0.70710678118654752440f;
+        float2 a[4], b[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            a[k] = cadd(v[k], v[k + 4]);
+            b[k] = csub(v[k], v[k + 4]);
+        }
+        // b[k] *= exp(-+2 pi i k / 8)
+        b[1] = INV ? make_float2(h * (b[1].x - b[1].y), h * (b[1].x + b[1].y))
+                   : make_float2(h * (b[1].x + b[1].y), h * (b[1].y - b[1].x));
+        b[2] = mul_mi<INV>(b[2]);
+        b[3] = INV ? make_float2(-h * (b[3].x + b[3].y), h * (b[3].x - b[3].y))
+                   : make_float2(h * (b[3].y - b[3].x), -h * (b[3].x + b[3].y));
+        dft_small<4, INV>(a);
+        dft_small<4, INV>(b);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            v[2 * k] = a[k];
+            v[2 * k + 1] = b[k];
+        }
+    }
+}
+
+// One Stockham stage over `nlines` lines of length NF (line stride `ls`).
+template <int NF, int R, int NS, bool INV>
+__device__ __forceinline__ void fft_stage(const float2 *__restrict__ in, float2 *__restrict__ out, int nlines,
+                                          int ls, const float2 *__restrict__ tw)
+{
+    constexpr int NB = NF / R;
+    const int total = nlines * NB;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int line = idx / NB;
+        const int j = idx - line * NB;
+        const float2 *src = in + line * ls;
+        float2 *dst = out + line * ls;
+        const int k = j % NS;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            float2 x = src[j + r * NB];
+            if (NS > 1 && r > 0) {
+                float2 w = tw[r * k * (NF / (NS * R))];
+                if (INV) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[r] = x;
+        }
+        dft_small<R, INV>(v);
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; r++) dst[base + r * NS] = v[r];
+    }
+}
+
+template <int NF>
+struct Radix;
+template <> struct Radix<32>  { static constexpr int r0 = 4, r1 = 8, r2 = 1; };
+template <> struct Radix<64>  { static constexpr int r0 = 8, r1 = 8, r2 = 1; };
+template <> struct Radix<96>  { static constexpr int r0 = 3, r1 = 4, r2 = 8; };
+template <> struct Radix<128> { static constexpr int r0 = 2, r1 = 8, r2 = 8; };
+template <> struct Radix<192> { static constexpr int r0 = 3, r1 = 8, r2 = 8; };
+template <> struct Radix<256> { static constexpr int r0 = 4, r1 = 8, r2 = 8; };
+template <> struct Radix<512> { static constexpr int r0 = 8, r1 = 8, r2 = 8; };
+
+// Transforms `nlines` lines held in `a` (line stride ls); `b` is scratch of the
+// same size.  Every thread of the block must call it.  Returns the buffer that
+// holds the result.  Ends with a block barrier.
+template <int NF, bool INV>
+__device__ __forceinline__ float2 *fft_lines(float2 *a, float2 *b, int nlines, int ls, const float2 *tw)
+{
+    using RR = Radix<NF>;
+    static_assert(RR::r0 * RR::r1 * (RR::r2 > 1 ? RR::r2 : 1) == NF, "radix schedule");
+    fft_stage<NF, RR::r0, 1, INV>(a, b, nlines, ls, tw);
+    __syncthreads();
+    fft_stage<NF, RR::r1, RR::r0, INV>(b, a, nlines, ls, tw);
+    __syncthreads();
+    if constexpr (RR::r2 > 1) {
+        fft_stage<NF, RR::r2, RR::r0 * RR::r1, INV>(a, b, nlines, ls, tw);
+        __syncthreads();
+        return b;
+    } else {
+        return a;
+    }
+}
+
+} // namespace bc

@@ -1,0 +1,77 @@
+// Internal declarations shared by the C-ABI layer (bc_api.cu) and the kernels
+// (bc_kernels.cu).  Not part of the public interface.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bc {
+
+// Per-instance description: one shape (A, or B under one rotation) whose
+// spectrum is computed in this launch.  Built on the host, read on the device.
+struct InstDesc {
+    int knot_off;       // first knot of this instance in the prepared-knot array
+    int nknots;         // knot count
+    int src_off;        // first knot of its shape in the shape's knot array (always 0)
+    int cap_e;          // per-axis capacity of the compact spreading box
+    long long grid_off; // float offset of its spreading boxes (L boxes)
+    long long z1_off;   // float2 offset of its z-transformed planes
+    long long y1_off;   // float2 offset of its y-transformed planes
+    float q[4];         // rotation (w, x, y, z), unit; identity for A
+    const float4 *knots; // the shape's knots (x, y, z, level bits)
+};
+
+// Device-computed support box of one instance in fine-grid cells.
+struct InstPlan {
+    int lo[3]; // first cell (may be negative: cells are centred on the origin)
+    int b[3];  // extent per axis (0 = empty instance)
+    int pos0[3]; // lo mod n: where compact index 0 lands in a length-n line
+    int bzp;   // z extent padded to a multiple of 4
+};
+
+// A correlation output: the spectra of instances a and b are combined into
+// out[...] (a < 0: use the cached spectrum of A).
+struct PairDesc {
+    int a, b;
+    long long h_off;    // float2 offset of this pair's inverse-transform planes
+    long long out_off;  // float offset of this pair's output grid
+};
+
+struct Tables {
+    const float *deconv;  // N: 1 / phi^(m/n), m in FFT order
+    const float *ballft;  // L x (3 (N/2)^2 + 1): h^(rho_l, 2 pi sqrt(q) / P), q = |m|^2
+    const float2 *tw_n;   // n twiddles exp(-2 pi i k / n)
+    const float2 *tw_N;   // N twiddles exp(-2 pi i k / N)
+    int qmax;             // 3 (N/2)^2
+    const float *consts;  // [0] = exp(beta) / I0(beta), the window normalisation
+};
+
+struct Geometry {
+    int N, n, W, L, H;  // H = N/2 kept z modes
+    float beta, n_over_P, inv_P3;
+};
+
+// Kernel launchers (bc_kernels.cu).  All return cudaGetLastError() after launch.
+cudaError_t launch_build_tables(const Geometry &g, double beta, double period, const double *radii_dev,
+                                float *deconv, float *ballft, float2 *tw_n, float2 *tw_N, float *consts,
+                                cudaStream_t s);
+cudaError_t launch_pack_knots(const float *xyz, const int *level, int n, int L, float4 *knots,
+                              unsigned int *stats, cudaStream_t s);
+cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, float4 *ku, InstPlan *plan,
+                           int *err, cudaStream_t s);
+cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *inst, int total_knots,
+                          const float4 *ku, const InstPlan *plan, float *grid, cudaStream_t s);
+cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
+                         const InstPlan *plan, float *grid, float2 *z1, int nsm, cudaStream_t s);
+cudaError_t launch_fft_y(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
+                         const InstPlan *plan, const float2 *z1, float2 *y1, int nsm, cudaStream_t s);
+cudaError_t launch_fft_x(const Geometry &g, const Tables &t, const InstDesc *inst, const InstPlan *plan,
+                         const PairDesc *pairs, int npairs, const float2 *y1, const float2 *fa_cache,
+                         float2 *fa_out, float2 *h, int nsm, cudaStream_t s);
+cudaError_t launch_ifft_y(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, float2 *h,
+                          int nsm, cudaStream_t s);
+cudaError_t launch_ifft_z(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs,
+                          const float2 *h, float *out, int nsm, cudaStream_t s);
+
+bool supported_N(int N);
+
+} // namespace bc

@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads and exports every entry point include/ballcorr.h
+declares; argument validation that happens before any device work is checked on CPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1711_05075_gb300 as bc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ballcorr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(bc_[a-z_]+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sync",
+              "bc_last_error", "bc_version", "bc_profile_begin", "bc_profile_end", "bc_stage_name"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = bc.lib()
+    for f in declared_functions():
+        assert hasattr(L, f), f
+    assert "sm_103a" in bc.bc_version()
+
+
+def _status(fn):
+    try:
+        fn()
+    except bc.BallCorrError as e:
+        return e.status, str(e)
+    return 0, ""
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(N=33, W=6, radii=[0.1]), 5),
+    (dict(N=32, W=1, radii=[0.1]), 1),
+    (dict(N=32, W=12, radii=[0.1]), 1),
+    (dict(N=32, W=6, radii=[]), 1),
+    (dict(N=32, W=6, radii=[0.1] * 9), 1),
+    (dict(N=32, W=6, radii=[-0.1]), 1),
+    (dict(N=32, W=6, radii=[0.1], period=0.0), 1),
+    (dict(N=32, W=6, radii=[0.1], sigma=3), 5),
+    (dict(N=32, W=6, radii=[0.1], precision=1), 5),
+])
+def test_create_rejects_bad_parameters_before_device_work(kw, status):
+    st, msg = _status(lambda: bc.bc_create(**kw))
+    assert st == status, msg
+    assert bc.lib().bc_last_error().decode()
+
+
+def test_null_arguments_are_rejected():
+    L = bc.lib()
+    assert L.bc_create(None, None, None) == 1
+    assert L.bc_destroy(None) == 0
+    assert L.bc_shape_destroy(None) == 0
+    assert L.bc_shape_create(None, None, None, 0, 0, None) == 1
+    assert L.bc_correlate(None, None, None, None, 1, None, 1) == 1
+    assert L.bc_sync(None) == 1
+    assert L.bc_profile_begin(None, 4) == 1
+    assert L.bc_profile_end(None, None) == 1
+    assert [bc.lib().bc_stage_name(i).decode() for i in range(7)] == [
+        "prepare", "spread", "fft_z", "fft_y", "fft_x", "ifft_y", "ifft_z"]
+    assert bc.lib().bc_stage_name(7).decode() == ""

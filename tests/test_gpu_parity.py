@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, layer (b).
+
+Both sides get identical inputs: the seeded knots and quaternions rounded once
+to FP32 (the library's input type) and widened back to FP64 for the oracle.
+Bar: rel-L2 <= 1e-5 over the compared points (FP32 path), as the method's
+accuracy target states; max-abs is reported beside it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1711_05075_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+    torch.cuda.set_device(0)
+    yield
+
+
+def bcmod():
+    import paper_1711_05075_gb300 as bc
+    return bc
+
+
+def f32(shape):
+    return synth.Shape(shape.xyz.astype(np.float32).astype(np.float64), shape.level, shape.radii, shape.name)
+
+
+def run_gpu(A, B, quats, N, W, radii=None, period=2.0):
+    bc = bcmod()
+    radii = A.radii if radii is None else radii
+    ctx = bc.Context(N, W, radii, period)
+    try:
+        sa = ctx.shape(A.xyz.astype(np.float32), A.level)
+        sb = ctx.shape(B.xyz.astype(np.float32), B.level)
+        g = ctx.correlate(sa, sb, np.asarray(quats, dtype=np.float32))
+        ctx.sync()
+        out = g.double().cpu().numpy()
+        sa.close()
+        sb.close()
+    finally:
+        ctx.close()
+    return out
+
+
+def oracle_grid(A, B, q, N, period=2.0):
+    return O.band_limited_corr(f32(A), f32(B), np.asarray(q, np.float32).astype(np.float64), N, period)
+
+
+def rel_l2(got, ref):
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def check(got, ref, tol=REL_TOL, what=""):
+    rel = rel_l2(got, ref)
+    mx = float(np.abs(got - ref).max())
+    print(f"{what}: rel-L2 {rel:.3e}  max-abs {mx:.3e}  (|ref|max {np.abs(ref).max():.3e})")
+    assert rel <= tol, (what, rel, mx)
+    return rel
+
+
+# ------------------------------------------------------------------ workloads
+def test_small_pair_full_grid():
+    wl = synth.small_pair(0)
+    got = run_gpu(wl.A, wl.B, wl.quats, wl.N, wl.W)[0]
+    ref = oracle_grid(wl.A, wl.B, wl.quats[0], wl.N)
+    check(got, ref, what=wl.name)
+
+
+def test_scale_pair_full_grid_and_sampled():
+    wl = synth.scale_pair(0)
+    got = run_gpu(wl.A, wl.B, wl.quats, wl.N, wl.W)[0]
+    g = O.band_limited_spectrum(f32(wl.A), f32(wl.B), wl.quats[0].astype(np.float32).astype(np.float64), wl.N)
+    ref = O.inverse_grid(g)
+    check(got, ref, what=wl.name + " full grid")
+    idx = synth.translation_sample(wl.N, 4096, seed=0)
+    pts = O.inverse_at(g, O.grid_points(wl.N, idx=idx))
+    check(got.reshape(-1)[idx], pts, what=wl.name + " 4096 sampled t")
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_rotations(k):
+    wl = synth.small_pair(1)
+    q = synth.shoemake_quaternions(synth.SplitMix64(99), k)
+    got = run_gpu(wl.A, wl.B, q, wl.N, wl.W)
+    for r in range(k):
+        check(got[r], oracle_grid(wl.A, wl.B, q[r], wl.N), what=f"rotation {r} of {k}")
+
+
+@pytest.mark.parametrize("N,W,n", [(32, 8, 300), (64, 8, 400), (96, 8, 500), (128, 6, 300)])
+def test_grid_sizes(N, W, n):
+    A = synth.ellipsoid_shape(n, 5, synth.RADII_4, synth.PROBS_4)
+    B = synth.torus_shape(n, 6, synth.RADII_4, synth.PROBS_4)
+    q = synth.shoemake_quaternions(synth.SplitMix64(3), 2)
+    got = run_gpu(A, B, q, N, W)
+    for r in range(2):
+        check(got[r], oracle_grid(A, B, q[r], N), what=f"N={N} W={W} rot {r}")
+
+
+def test_grid_size_256_sampled():
+    N, W = 256, 8
+    A = synth.ellipsoid_shape(300, 7, synth.RADII_4, synth.PROBS_4)
+    B = synth.torus_shape(300, 8, synth.RADII_4, synth.PROBS_4)
+    q = synth.IDENTITY_QUAT
+    got = run_gpu(A, B, q, N, W)[0]
+    g = O.band_limited_spectrum(f32(A), f32(B), q[0], N)
+    idx = synth.translation_sample(N, 4096, seed=1)
+    check(got.reshape(-1)[idx], O.inverse_at(g, O.grid_points(N, idx=idx)), what="N=256 sampled")
+
+
+# ------------------------------------------------------------------ edge cases
+def test_repeated_calls_are_identical():
+    # The spreading boxes are cleared by the pass that consumes them; a second
+    # call on the same context must not see the first call's grids.
+    bc = bcmod()
+    wl = synth.small_pair(2)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    sa = ctx.shape(wl.A.xyz, wl.A.level)
+    sb = ctx.shape(wl.B.xyz, wl.B.level)
+    g1 = ctx.correlate(sa, sb, wl.quats).clone()
+    g2 = ctx.correlate(sa, sb, wl.quats).clone()
+    q = synth.shoemake_quaternions(synth.SplitMix64(1), 4)
+    ctx.correlate(sa, sb, q)
+    g3 = ctx.correlate(sa, sb, wl.quats).clone()
+    ctx.sync()
+    assert rel_l2(g2.double().cpu().numpy(), g1.double().cpu().numpy()) < 1e-6
+    assert rel_l2(g3.double().cpu().numpy(), g1.double().cpu().numpy()) < 1e-6
+    sa.close(); sb.close(); ctx.close()
+
+
+def test_host_output_matches_device_output():
+    bc = bcmod()
+    wl = synth.small_pair(3)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    sa = ctx.shape(wl.A.xyz, wl.A.level)
+    sb = ctx.shape(wl.B.xyz, wl.B.level)
+    dev = ctx.correlate(sa, sb, wl.quats).cpu().numpy()
+    host = np.empty_like(dev)
+    ctx.correlate_host(sa, sb, wl.quats, host)
+    # float atomics in the spreading pass add in a run-dependent order: results
+    # agree to rounding, not bit for bit
+    assert rel_l2(host.astype(np.float64), dev.astype(np.float64)) < 1e-6
+    # device-resident knots give the same result as host knots
+    sa2 = ctx.shape(torch.tensor(wl.A.xyz, dtype=torch.float32, device="cuda"),
+                    torch.tensor(wl.A.level, dtype=torch.int32, device="cuda"))
+    dev2 = ctx.correlate(sa2, sb, wl.quats).cpu().numpy()
+    assert rel_l2(dev2.astype(np.float64), dev.astype(np.float64)) < 1e-6
+    for s in (sa, sb, sa2):
+        s.close()
+    ctx.close()
+
+
+def test_empty_shape_gives_zero():
+    bc = bcmod()
+    wl = synth.small_pair(0)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    sa = ctx.shape(wl.A.xyz, wl.A.level)
+    se = ctx.shape(np.zeros((0, 3), np.float32), np.zeros(0, np.int32))
+    g = ctx.correlate(sa, se, wl.quats)
+    g2 = ctx.correlate(se, sa, wl.quats)
+    ctx.sync()
+    assert float(g.abs().max()) == 0.0 and float(g2.abs().max()) == 0.0
+    sa.close(); se.close(); ctx.close()
+
+
+def test_single_balls_and_two_ball_closed_form():
+    # One ball each: g^(m) = h^_{r1} h^_{r2} exp(-2 pi i m.(c1 - R c2)/P); the oracle's
+    # layer (b) gives it, and the GPU must match.
+    A = synth.Shape(np.array([[0.1, -0.2, 0.05]]), np.array([1], np.int32), (0.04, 0.08))
+    B = synth.Shape(np.array([[-0.3, 0.1, 0.2]]), np.array([0], np.int32), (0.04, 0.08))
+    q = synth.shoemake_quaternions(synth.SplitMix64(5), 1)
+    got = run_gpu(A, B, q, 32, 6)[0]
+    check(got, oracle_grid(A, B, q[0], 32), what="one ball each")
+
+
+def test_empty_level_and_single_level():
+    A = synth.ellipsoid_shape(200, 11)
+    A0 = synth.Shape(A.xyz, np.zeros_like(A.level), A.radii)  # level 1 empty
+    B = synth.torus_shape(150, 12)
+    got = run_gpu(A0, B, synth.IDENTITY_QUAT, 32, 6)[0]
+    check(got, oracle_grid(A0, B, synth.IDENTITY_QUAT[0], 32), what="empty level")
+
+
+def test_knots_outside_the_box_wrap():
+    A = synth.ellipsoid_shape(150, 13)
+    B = synth.torus_shape(150, 14)
+    shift = np.array([2.0, -2.0, 4.0])  # whole periods: same periodic shape
+    A2 = synth.Shape(A.xyz + shift, A.level, A.radii)
+    g1 = run_gpu(A, B, synth.IDENTITY_QUAT, 32, 6)[0]
+    g2 = run_gpu(A2, B, synth.IDENTITY_QUAT, 32, 6)[0]
+    check(g2, oracle_grid(A, B, synth.IDENTITY_QUAT[0], 32), what="shifted by periods")
+    assert rel_l2(g2, g1) < 2e-6
+
+
+def test_shape_straddling_the_periodic_boundary():
+    A = synth.ellipsoid_shape(200, 15)
+    A2 = synth.Shape(A.xyz + np.array([0.85, 0.0, -0.9]), A.level, A.radii)  # wraps in x and z
+    B = synth.torus_shape(200, 16)
+    q = synth.shoemake_quaternions(synth.SplitMix64(8), 2)
+    got = run_gpu(A2, B, q, 32, 6)
+    for r in range(2):
+        check(got[r], oracle_grid(A2, B, q[r], 32), what=f"straddling, rot {r}")
+
+
+def test_invalid_arguments_raise():
+    bc = bcmod()
+    ctx = bc.Context(32, 6, (0.04, 0.08))
+    with pytest.raises(bc.BallCorrError) as e:
+        ctx.shape(np.zeros((4, 3), np.float32), np.array([0, 1, 2, 0], np.int32))
+    assert e.value.status == 1
+    with pytest.raises(bc.BallCorrError) as e:
+        ctx.shape(np.full((2, 3), np.nan, np.float32), np.array([0, 1], np.int32))
+    assert e.value.status == 1
+    sa = ctx.shape(np.zeros((1, 3), np.float32), np.array([0], np.int32))
+    with pytest.raises(bc.BallCorrError) as e:
+        ctx.correlate(sa, sa, np.zeros((1, 4), np.float32))
+    assert e.value.status == 1
+    sa.close()
+    ctx.close()
