@@ -142,6 +142,44 @@ bc_status bc_profile_end(bc_ctx_t ctx, bc_profile *out);
 /* Name of stage i (0 <= i < BC_NUM_STAGES), or "" out of range. */
 const char *bc_stage_name(int i);
 
+/* ---------------------------------------------------------------- no allocation
+ * bc_correlate_noalloc: one correlation of a small pair of shapes that
+ * allocates no device memory.  The paper has no counterpart; this is a
+ * service for callers that cannot call cudaMalloc -- code that must not add
+ * allocations while a stream is being captured, plug-ins living inside an
+ * application that owns the device heap, real-time loops that must never wait
+ * on the allocator.  The caller passes device buffers for the inputs and the
+ * output; all other memory the computation needs is one static device array
+ * of BC_NOALLOC_SCRATCH_BYTES inside this library, which every GPU that loads
+ * the library keeps until the process exits.
+ *
+ *   params   as for bc_create, but N must be BC_NOALLOC_MAX_N (32) and
+ *            level_count at most BC_NOALLOC_MAX_LEVELS (2); host memory.
+ *   xyzA, levelA, nA / xyzB, levelB, nB
+ *            the two shapes as in bc_shape_create, in DEVICE memory, each
+ *            with at most BC_NOALLOC_MAX_KNOTS knots (0 allowed).
+ *   quat     one rotation (w, x, y, z) of B, host memory.
+ *   out      device buffer of N^3 floats, [kx][ky][kz]; same result as
+ *            bc_correlate for one rotation (up to the rounding order of the
+ *            spreading sums).
+ *   cuda_stream  stream to run on (NULL = legacy default stream).
+ *
+ * Larger sizes are rejected with BC_ERR_ARG and a message naming the limit.
+ * The call synchronises `cuda_stream` once (to check the level ids) and
+ * returns with the rest of the work enqueued.  The first call on a device
+ * looks up the array's device address; make that first call before any
+ * stream capture.  All calls share the one array and each call clears the
+ * parts that must start at zero, so calls whose GPU work overlaps (two
+ * streams, two host threads) race and corrupt each other's results.
+ * Errors are reported through bc_last_error(). */
+#define BC_NOALLOC_MAX_N 32
+#define BC_NOALLOC_MAX_LEVELS 2
+#define BC_NOALLOC_MAX_KNOTS 8192
+#define BC_NOALLOC_SCRATCH_BYTES (8u << 20)
+bc_status bc_correlate_noalloc(const bc_params *params, const float *xyzA, const int *levelA, int nA,
+                               const float *xyzB, const int *levelB, int nB, const float *quat, float *out,
+                               void *cuda_stream);
+
 /* Message for the calling thread's most recent failure ("" if none). */
 const char *bc_last_error(void);
 

@@ -76,6 +76,8 @@ def lib():
         L.bc_profile_end.restype = st
         L.bc_stage_name.argtypes = [i]
         L.bc_stage_name.restype = ctypes.c_char_p
+        L.bc_correlate_noalloc.argtypes = [ctypes.POINTER(bc_params), vp, vp, i, vp, vp, i, vp, vp, vp]
+        L.bc_correlate_noalloc.restype = st
         _lib = L
     return _lib
 
@@ -129,6 +131,24 @@ def bc_sync(ctx):
 
 def bc_version() -> str:
     return lib().bc_version().decode()
+
+
+BC_NOALLOC_MAX_N = 32
+BC_NOALLOC_MAX_LEVELS = 2
+BC_NOALLOC_MAX_KNOTS = 8192
+
+
+def bc_correlate_noalloc(N, W, radii, xyzA, levelA, nA, xyzB, levelB, nB, quat, out, period=2.0, beta=0.0,
+                         stream=None):
+    """The allocation-free correlation (see include/ballcorr.h): device inputs and output,
+    scratch in the library's static device array."""
+    radii = np.ascontiguousarray(radii, dtype=np.float64)
+    p = bc_params(int(N), 2, int(W), float(beta), float(period), int(radii.size),
+                  radii.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+    q = np.ascontiguousarray(np.asarray(quat, dtype=np.float32).reshape(4))
+    s = None if stream is None else ctypes.c_void_p(stream)
+    _check(lib().bc_correlate_noalloc(ctypes.byref(p), _ptr(xyzA), _ptr(levelA), int(nA), _ptr(xyzB), _ptr(levelB),
+                                      int(nB), _ptr(q), _ptr(out), s))
 
 
 def bc_profile_begin(ctx, max_calls):

@@ -20,6 +20,8 @@ using namespace bc;
 
 static thread_local std::string g_last_error;
 
+void bc::set_last_error(const std::string &msg) { g_last_error = msg; }
+
 static bc_status fail(bc_status s, const std::string &msg)
 {
     g_last_error = msg;

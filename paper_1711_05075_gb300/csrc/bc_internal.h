@@ -2,6 +2,7 @@
 // (bc_kernels.cu).  Not part of the public interface.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace bc {
@@ -73,5 +74,8 @@ cudaError_t launch_ifft_z(const Geometry &g, const Tables &t, const PairDesc *pa
                           const float2 *h, float *out, int nsm, cudaStream_t s);
 
 bool supported_N(int N);
+
+// Sets the calling thread's message returned by bc_last_error() (bc_api.cu).
+void set_last_error(const std::string &msg);
 
 } // namespace bc
