@@ -88,7 +88,8 @@ struct bc_ctx_s {
     // device status word
     int *err_dev = nullptr;
     // workspaces
-    DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, outbuf, stats;
+    DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, outbuf, stats, boxes;
+    bool boxes_dirty = true; // support-box accumulators need their reset state
     std::vector<char> last_desc;            // descriptors the device copies hold
     void *last_inst_p = nullptr, *last_pairs_p = nullptr;
     bool grid_dirty = false;
@@ -249,7 +250,7 @@ bc_status bc_destroy(bc_ctx_t c)
             s->ctx = nullptr;
         }
         c->shapes.clear();
-        DevBuf *bufs[] = {&c->ku, &c->plan, &c->inst, &c->pairs, &c->grid, &c->z1, &c->y1, &c->h, &c->fa, &c->outbuf, &c->stats};
+        DevBuf *bufs[] = {&c->ku, &c->plan, &c->inst, &c->pairs, &c->grid, &c->z1, &c->y1, &c->h, &c->fa, &c->outbuf, &c->stats, &c->boxes};
         for (DevBuf *b : bufs) b->release();
         delete c;
         return BC_OK;
@@ -418,7 +419,7 @@ bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quat
     try {
         if (!c || !A || !B || !quats || !out) return fail(BC_ERR_ARG, "bc_correlate: null argument");
         if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_correlate: shapes belong to another context");
-        if (k < 1 || k > (1 << 20)) return fail(BC_ERR_ARG, "bc_correlate: k must be in [1, 2^20]");
+        if (k < 1 || k > 65534) return fail(BC_ERR_ARG, "bc_correlate: k must be in [1, 65534]");
         for (int r = 0; r < k; r++) {
             const float *q = quats + 4 * r;
             double n2 = (double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] + (double)q[3] * q[3];
@@ -468,6 +469,15 @@ bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quat
         cudaError_t e;
         if ((e = c->ku.ensure(sizeof(float4) * (size_t)(koff > 0 ? koff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "ku");
         if ((e = c->plan.ensure(sizeof(InstPlan) * ninst, false, st)) != cudaSuccess) return cuda_fail(e, "plan");
+        {
+            const size_t before = c->boxes.bytes;
+            if ((e = c->boxes.ensure(sizeof(int) * 8 * (size_t)ninst, false, st)) != cudaSuccess) return cuda_fail(e, "boxes");
+            if (c->boxes.bytes != before || c->boxes_dirty) {
+                if ((e = launch_reset_boxes((int *)c->boxes.p, (int)(c->boxes.bytes / (8 * sizeof(int))), st)) != cudaSuccess)
+                    return cuda_fail(e, "reset boxes");
+                c->boxes_dirty = false;
+            }
+        }
         if ((e = c->inst.ensure(sizeof(InstDesc) * ninst, false, st)) != cudaSuccess) return cuda_fail(e, "inst");
         if ((e = c->pairs.ensure(sizeof(PairDesc) * npairs, false, st)) != cudaSuccess) return cuda_fail(e, "pairs");
         const size_t grid_before = c->grid.bytes;
@@ -508,7 +518,11 @@ bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quat
         c->grid_dirty = true; // until the z pass has consumed the spreading boxes
         const bool prof = c->prof_on && c->prof_calls < c->prof_max;
         prof_mark(c, -1);
-        if ((e = launch_prepare(g, dinst, ninst, (float4 *)c->ku.p, dplan, c->err_dev, st)) != cudaSuccess) return cuda_fail(e, "prepare");
+        const int max_knots = A->n > B->n ? A->n : B->n;
+        c->boxes_dirty = true; // until k_plan has consumed and reset the accumulators
+        if ((e = launch_prepare(g, dinst, ninst, max_knots, (float4 *)c->ku.p, (int *)c->boxes.p, dplan, c->err_dev, st)) != cudaSuccess)
+            return cuda_fail(e, "prepare");
+        c->boxes_dirty = false;
         prof_mark(c, 0);
         if ((e = launch_spread(g, t, dinst, koff, (const float4 *)c->ku.p, dplan, (float *)c->grid.p, st)) != cudaSuccess)
             return cuda_fail(e, "spread");
@@ -537,7 +551,7 @@ bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quat
         prof_mark(c, 6);
         if (prof) {
             c->prof_calls++;
-            c->prof_launches += fused ? 7 : 8;
+            c->prof_launches += fused ? 8 : 9;
             c->last_ninst = ninst;
             c->last_npairs = npairs_main;
             c->last_inst = inst;

@@ -9,7 +9,7 @@
 // x[j + r NF/R] (r < R), multiplies input r by w^(r (j mod Ns) NF/(Ns R)),
 // applies an R-point DFT and writes y[(j div Ns) Ns R + (j mod Ns) + r Ns].
 // Output is in natural order after the last stage; stages ping-pong between
-// two shared-memory buffers.  Radix schedules: 32 = 4.8, 64 = 8.8,
+// two shared-memory tiles.  Radix schedules: 32 = 4.8, 64 = 8.8,
 // 96 = 3.4.8, 128 = 2.8.8, 192 = 3.8.8, 256 = 4.8.8, 512 = 8.8.8.
 //
 // Direction: forward uses exp(-2 pi i jk/NF), inverse exp(+2 pi i jk/NF); no
@@ -89,37 +89,6 @@ __device__ __forceinline__ void dft_small(float2 *v)
     }
 }
 
-// One Stockham stage over `nlines` lines of length NF (line stride `ls`).
-template <int NF, int R, int NS, bool INV>
-__device__ __forceinline__ void fft_stage(const float2 *__restrict__ in, float2 *__restrict__ out, int nlines,
-                                          int ls, const float2 *__restrict__ tw)
-{
-    constexpr int NB = NF / R;
-    const int total = nlines * NB;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int line = idx / NB;
-        const int j = idx - line * NB;
-        const float2 *src = in + line * ls;
-        float2 *dst = out + line * ls;
-        const int k = j % NS;
-        float2 v[R];
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            float2 x = src[j + r * NB];
-            if (NS > 1 && r > 0) {
-                float2 w = tw[r * k * (NF / (NS * R))];
-                if (INV) w.y = -w.y;
-                x = cmul(x, w);
-            }
-            v[r] = x;
-        }
-        dft_small<R, INV>(v);
-        const int base = (j / NS) * NS * R + k;
-#pragma unroll
-        for (int r = 0; r < R; r++) dst[base + r * NS] = v[r];
-    }
-}
-
 template <int NF>
 struct Radix;
 template <> struct Radix<32>  { static constexpr int r0 = 4, r1 = 8, r2 = 1; };
@@ -130,20 +99,55 @@ template <> struct Radix<192> { static constexpr int r0 = 3, r1 = 8, r2 = 8; };
 template <> struct Radix<256> { static constexpr int r0 = 4, r1 = 8, r2 = 8; };
 template <> struct Radix<512> { static constexpr int r0 = 8, r1 = 8, r2 = 8; };
 
-// Transforms `nlines` lines held in `a` (line stride ls); `b` is scratch of the
-// same size.  Every thread of the block must call it.  Returns the buffer that
-// holds the result.  Ends with a block barrier.
-template <int NF, bool INV>
-__device__ __forceinline__ float2 *fft_lines(float2 *a, float2 *b, int nlines, int ls, const float2 *tw)
+// ---------------------------------------------------------------------------
+// Interleaved tiles: C lines stored as x[pos * C + c].  Consecutive threads take
+// consecutive lines c of the same butterfly, so every shared-memory access of
+// a stage is a run of C consecutive complex values (no bank conflicts), and a
+// tile row of C values is one 8C-byte run in global memory as well.
+template <int NF, int R, int NS, bool INV, int C, int NT>
+__device__ __forceinline__ void il_stage(const float2 *__restrict__ in, float2 *__restrict__ out,
+                                         const float2 *__restrict__ tw)
+{
+    constexpr int NB = NF / R;
+    constexpr int TOT = NB * C;
+    constexpr int IT = (TOT + NT - 1) / NT;
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int idx = (int)threadIdx.x + it * NT;
+        if ((TOT % NT) != 0 && idx >= TOT) break;
+        const int c = idx % C, j = idx / C;
+        const int k = j % NS;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            float2 x = in[(j + r * NB) * C + c];
+            if (NS > 1 && r > 0) {
+                float2 w = tw[r * k * (NF / (NS * R))];
+                if (INV) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[r] = x;
+        }
+        dft_small<R, INV>(v);
+        const int base = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; r++) out[(base + r * NS) * C + c] = v[r];
+    }
+}
+
+// Transforms the C interleaved lines of tile `a` (b: scratch tile); all NT
+// threads of the block must call it.  Returns the tile holding the result;
+// ends with a block barrier.
+template <int NF, bool INV, int C, int NT>
+__device__ __forceinline__ float2 *il_fft(float2 *a, float2 *b, const float2 *tw)
 {
     using RR = Radix<NF>;
-    static_assert(RR::r0 * RR::r1 * (RR::r2 > 1 ? RR::r2 : 1) == NF, "radix schedule");
-    fft_stage<NF, RR::r0, 1, INV>(a, b, nlines, ls, tw);
+    il_stage<NF, RR::r0, 1, INV, C, NT>(a, b, tw);
     __syncthreads();
-    fft_stage<NF, RR::r1, RR::r0, INV>(b, a, nlines, ls, tw);
+    il_stage<NF, RR::r1, RR::r0, INV, C, NT>(b, a, tw);
     __syncthreads();
     if constexpr (RR::r2 > 1) {
-        fft_stage<NF, RR::r2, RR::r0 * RR::r1, INV>(a, b, nlines, ls, tw);
+        il_stage<NF, RR::r2, RR::r0 * RR::r1, INV, C, NT>(a, b, tw);
         __syncthreads();
         return b;
     } else {

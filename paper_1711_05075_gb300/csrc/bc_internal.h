@@ -57,8 +57,11 @@ cudaError_t launch_build_tables(const Geometry &g, double beta, double period, c
                                 cudaStream_t s);
 cudaError_t launch_pack_knots(const float *xyz, const int *level, int n, int L, float4 *knots,
                               unsigned int *stats, cudaStream_t s);
-cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, float4 *ku, InstPlan *plan,
-                           int *err, cudaStream_t s);
+// bb: 8 ints per instance (support-box accumulators); they must hold the reset
+// state (launch_reset_boxes) before the first launch and are left reset.
+cudaError_t launch_reset_boxes(int *bb, int ninst, cudaStream_t s);
+cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, int max_knots, float4 *ku, int *bb,
+                           InstPlan *plan, int *err, cudaStream_t s);
 cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *inst, int total_knots,
                           const float4 *ku, const InstPlan *plan, float *grid, cudaStream_t s);
 cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,

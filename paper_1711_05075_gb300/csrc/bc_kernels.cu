@@ -5,7 +5,8 @@
 //
 //   k_prepare   rotate the knots (Eq. (Mink0), Sec. 2.4: a rigid motion only
 //               moves the centres), map them to fine-grid coordinates and find
-//               each instance's support box (the cells its spreading touches).
+//               each instance's support box (the cells its spreading touches);
+//   k_plan      turns the boxes into per-instance plans.
 //   k_spread    type-1 NUFFT step 1 for the impulse densities of Eq. (rhoP):
 //               Kaiser-Bessel spreading of every knot onto its level's grid,
 //               restricted to the support box (cells outside it stay zero).
@@ -21,6 +22,9 @@
 //   k_ifft_y    inverse transform along y.
 //   k_ifft_z    complex-to-real inverse along z (two rows per complex transform)
 //               giving g on the N^3 translation grid.
+//
+// The transform passes work on shared-memory tiles of 16 interleaved lines
+// (bc_fft.cuh) loaded and stored with 16-byte accesses.
 //
 // The support-box pruning computes exactly the transforms of the full
 // oversampled grids: the cells it skips hold zeros.
@@ -146,26 +150,33 @@ cudaError_t launch_pack_knots(const float *xyz, const int *level, int n, int L, 
     return cudaGetLastError();
 }
 
+
 // ------------------------------------------------------------------ prepare
-// One block per instance.  Knot j of instance i becomes
-// ku = (u_x, u_y, u_z, level | i << 4) with u = (R c) n / P wrapped into
-// [-n/2, n/2) (fine-grid cells; the period P spans n cells).  The spreading
-// stencil of a knot covers cells g0 .. g0 + W - 1 per axis, g0 = ceil(u - W/2).
-__global__ void k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 *ku, InstPlan *plan, int *err)
+// Knot j of instance i becomes ku = (u_x, u_y, u_z, level | i << 4) with
+// u = (R c) n / P wrapped into [-n/2, n/2) (fine-grid cells; the period P spans
+// n cells).  The spreading stencil of a knot covers cells g0 .. g0 + W - 1 per
+// axis, g0 = ceil(u - W/2); the support box of the instance is the union of
+// the stencils, accumulated with atomics into bb (lo[3], hi[3] per instance).
+// Grid: (blocks over knots, instance).
+constexpr int PREP_THREADS = 256;
+
+__global__ void __launch_bounds__(PREP_THREADS)
+k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 *ku, int *bb)
 {
-    const int i = blockIdx.x;
+    const int i = blockIdx.y;
     const InstDesc d = inst[i];
-    // rotation matrix of the normalised quaternion (w, x, y, z)
+    const int j = blockIdx.x * PREP_THREADS + threadIdx.x;
+    if (blockIdx.x * PREP_THREADS >= d.nknots) return; // whole block beyond this instance
     float qw = d.q[0], qx = d.q[1], qy = d.q[2], qz = d.q[3];
-    float s = 1.0f / sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    const float s = 1.0f / sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
     qw *= s; qx *= s; qy *= s; qz *= s;
     const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
     const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
     const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
     const float nf = (float)g.n, halfW = 0.5f * (float)g.W;
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
-    for (int j = threadIdx.x; j < d.nknots; j += blockDim.x) {
-        float4 c = d.knots[d.src_off + j];
+    if (j < d.nknots) {
+        const float4 c = d.knots[d.src_off + j];
         float p[3];
         p[0] = fmaf(R00, c.x, fmaf(R01, c.y, R02 * c.z));
         p[1] = fmaf(R10, c.x, fmaf(R11, c.y, R12 * c.z));
@@ -176,14 +187,13 @@ __global__ void k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 
             float v = p[a] * g.n_over_P;
             v -= nf * floorf(v / nf + 0.5f);
             u[a] = v;
-            int g0 = (int)ceilf(v - halfW);
-            lo[a] = min(lo[a], g0);
-            hi[a] = max(hi[a], g0 + g.W - 1);
+            const int g0 = (int)ceilf(v - halfW);
+            lo[a] = g0;
+            hi[a] = g0 + g.W - 1;
         }
-        int tag = __float_as_int(c.w) | (i << 4);
+        const int tag = __float_as_int(c.w) | (i << 4);
         ku[d.knot_off + j] = make_float4(u[0], u[1], u[2], __int_as_float(tag));
     }
-    __shared__ int red[6][32];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -191,55 +201,86 @@ __global__ void k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 
             hi[a] = max(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
         }
     }
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) {
+    __shared__ int red[6][PREP_THREADS / 32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
         for (int a = 0; a < 3; a++) {
             red[a][w] = lo[a];
             red[3 + a][w] = hi[a];
         }
-    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int L0[3], H0[3];
-        for (int a = 0; a < 3; a++) {
-            L0[a] = INT_MAX;
-            H0[a] = INT_MIN;
-            for (int k = 0; k < nw; k++) {
-                L0[a] = min(L0[a], red[a][k]);
-                H0[a] = max(H0[a], red[3 + a][k]);
-            }
-        }
-        InstPlan pl;
-        bool empty = d.nknots <= 0;
-        for (int a = 0; a < 3; a++) {
-            int b = empty ? 0 : min(H0[a] - L0[a] + 1, g.n);
-            if (b > d.cap_e) {
-                atomicOr(err, 1);
-                empty = true;
-            }
-            pl.lo[a] = empty ? 0 : L0[a];
-            pl.b[a] = b;
-            pl.pos0[a] = empty ? 0 : ((L0[a] % g.n) + g.n) % g.n;
-        }
-        if (empty) pl.b[0] = pl.b[1] = pl.b[2] = 0;
-        pl.bzp = (pl.b[2] + 3) & ~3;
-        plan[i] = pl;
+    if (threadIdx.x < 6) {
+        const int a = threadIdx.x;
+        int v = a < 3 ? INT_MAX : INT_MIN;
+        for (int k = 0; k < PREP_THREADS / 32; k++) v = a < 3 ? min(v, red[a][k]) : max(v, red[a][k]);
+        if (a < 3) atomicMin(&bb[8 * i + a], v);
+        else atomicMax(&bb[8 * i + a], v);
     }
 }
 
-cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, float4 *ku, InstPlan *plan,
-                           int *err, cudaStream_t s)
+// Support boxes -> plans (one thread per instance); the accumulators are reset
+// for the next launch.  A box larger than the instance's capacity raises the
+// error word and the instance is treated as empty.
+__global__ void k_plan(Geometry g, const InstDesc *__restrict__ inst, int ninst, int *bb, InstPlan *plan, int *err)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    int L0[3], H0[3];
+    for (int a = 0; a < 3; a++) {
+        L0[a] = bb[8 * i + a];
+        H0[a] = bb[8 * i + 3 + a];
+        bb[8 * i + a] = INT_MAX;
+        bb[8 * i + 3 + a] = INT_MIN;
+    }
+    InstPlan pl;
+    bool empty = inst[i].nknots <= 0 || L0[0] == INT_MAX;
+    for (int a = 0; a < 3; a++) {
+        const int b = empty ? 0 : min(H0[a] - L0[a] + 1, g.n);
+        if (b > inst[i].cap_e) {
+            atomicOr(err, 1);
+            empty = true;
+        }
+        pl.lo[a] = empty ? 0 : L0[a];
+        pl.b[a] = b;
+        pl.pos0[a] = empty ? 0 : ((L0[a] % g.n) + g.n) % g.n;
+    }
+    if (empty) pl.b[0] = pl.b[1] = pl.b[2] = 0;
+    pl.bzp = (pl.b[2] + 3) & ~3;
+    plan[i] = pl;
+}
+
+__global__ void k_reset_boxes(int *bb, int ninst)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 8 * ninst) bb[t] = ((t & 7) < 3) ? INT_MAX : INT_MIN;
+}
+
+cudaError_t launch_reset_boxes(int *bb, int ninst, cudaStream_t s)
 {
     if (ninst <= 0) return cudaSuccess;
-    k_prepare<<<ninst, 1024, 0, s>>>(g, inst, ku, plan, err);
+    k_reset_boxes<<<(8 * ninst + 255) / 256, 256, 0, s>>>(bb, ninst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, int max_knots, float4 *ku, int *bb,
+                           InstPlan *plan, int *err, cudaStream_t s)
+{
+    if (ninst <= 0) return cudaSuccess;
+    const int bx = max_knots > 0 ? (max_knots + PREP_THREADS - 1) / PREP_THREADS : 1;
+    k_prepare<<<dim3(bx, ninst), PREP_THREADS, 0, s>>>(g, inst, ku, bb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_plan<<<(ninst + 127) / 128, 128, 0, s>>>(g, inst, ninst, bb, plan, err);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ spread
 // One warp per knot.  Lanes 0..3W-1 evaluate the separable window weights
-// phi(u_a - g) for the W cells of each axis; the W^3 products are then added
-// into the knot's level grid (compact support-box layout
-// [level][ix][iy][iz], iz padded to bzp), z fastest across lanes.
+// phi(u_a - g) for the W cells of each axis; each lane then takes rows
+// (dx, dy) of the stencil and adds the W z-cells of a row with 16-byte vector
+// atomics aligned to the padded z extent (zero weights fill the unused lanes
+// of the first and last vector).  A row that wraps around the period (only
+// possible when the box spans all n cells) falls back to scalar atomics.
 constexpr int SPREAD_WARPS = 8;
 
 __global__ void __launch_bounds__(SPREAD_WARPS * 32)
@@ -249,7 +290,7 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
     const float inv_scaled_i0beta = consts[0];
     __shared__ float wts[SPREAD_WARPS][3][16];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int W = g.W, W2 = W * W, W3 = W2 * W;
+    const int W = g.W, W2 = W * W;
     const float halfW = 0.5f * (float)W, twoOverW = 2.0f / (float)W;
     for (int k = blockIdx.x * SPREAD_WARPS + wib; k < total; k += gridDim.x * SPREAD_WARPS) {
         const float4 v = ku[k];
@@ -279,16 +320,34 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
         __syncwarp();
         const long long boxsz = (long long)p.b[0] * p.b[1] * p.bzp;
         float *G = grid + inst[i].grid_off + (long long)level * boxsz;
-        for (int e = lane; e < W3; e += 32) {
-            const int dx = e / W2, dy = (e / W) % W, dz = e % W;
+        const int iz0 = g0[2] - p.lo[2];
+        const bool zwrap = iz0 + W - 1 >= g.n;
+        const int a0 = iz0 & ~3, a1 = (iz0 + W - 1) | 3; // aligned vector span [a0, a1]
+        for (int r = lane; r < W2; r += 32) {
+            const int dx = r / W, dy = r - dx * W;
             int ix = g0[0] + dx - p.lo[0];
             int iy = g0[1] + dy - p.lo[1];
-            int iz = g0[2] + dz - p.lo[2];
             if (ix >= g.n) ix -= g.n;
             if (iy >= g.n) iy -= g.n;
-            if (iz >= g.n) iz -= g.n;
-            const float val = wts[wib][0][dx] * wts[wib][1][dy] * wts[wib][2][dz];
-            atomicAdd(&G[((long long)ix * p.b[1] + iy) * p.bzp + iz], val);
+            const float rw = wts[wib][0][dx] * wts[wib][1][dy];
+            float *row = G + ((long long)ix * p.b[1] + iy) * p.bzp;
+            if (!zwrap) {
+                for (int t = a0; t <= a1; t += 4) {
+                    float4 val;
+                    const int e0 = t - iz0;
+                    val.x = (e0 >= 0 && e0 < W) ? rw * wts[wib][2][e0] : 0.f;
+                    val.y = (e0 + 1 >= 0 && e0 + 1 < W) ? rw * wts[wib][2][e0 + 1] : 0.f;
+                    val.z = (e0 + 2 >= 0 && e0 + 2 < W) ? rw * wts[wib][2][e0 + 2] : 0.f;
+                    val.w = (e0 + 3 >= 0 && e0 + 3 < W) ? rw * wts[wib][2][e0 + 3] : 0.f;
+                    atomicAdd(reinterpret_cast<float4 *>(row + t), val);
+                }
+            } else {
+                for (int dz = 0; dz < W; dz++) {
+                    int iz = iz0 + dz;
+                    if (iz >= g.n) iz -= g.n;
+                    atomicAdd(row + iz, rw * wts[wib][2][dz]);
+                }
+            }
         }
         __syncwarp();
     }
@@ -305,13 +364,13 @@ cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *in
 }
 
 // ------------------------------------------------------------------ helpers
-// Block loop over the work blocks of a sequence of instances, giving each
-// block of the grid an even share across instances.
+// Block loop over the work items of a sequence of instances (or pairs),
+// giving each block of the grid an even share across them.
 struct RotStart {
     int rot = 0;
     __device__ __forceinline__ int first() const
     {
-        int st = rot % (int)gridDim.x;
+        const int st = rot % (int)gridDim.x;
         return ((int)blockIdx.x - st + (int)gridDim.x) % (int)gridDim.x;
     }
 };
@@ -322,92 +381,124 @@ __device__ __forceinline__ void load_twiddles(float2 *dst, const float2 *__restr
     for (int k = threadIdx.x; k < NF; k += blockDim.x) dst[k] = src[k];
 }
 
-// ------------------------------------------------------------------ fft z
-// Real rows of the level grids -> m_z in [0, N/2), two rows per complex
-// transform: with Z = FFT(a + i b), A_k = (Z_k + conj Z_{n-k}) / 2 and
-// B_k = (Z_k - conj Z_{n-k}) / (2i).  Compact index iz lands at position
-// (pos0_z + iz) mod n of the length-n row, the rest of the row is zero.
-// Every grid cell read is reset to zero, so the spreading buffer is clean for
-// the next launch without a separate memset pass.
+// Zero an NF x 16 complex tile with 16-byte stores.
 template <int NF>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void zero_tile(float2 *t)
+{
+    float4 *t4 = reinterpret_cast<float4 *>(t);
+    for (int e = threadIdx.x; e < NF * 8; e += blockDim.x) t4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+constexpr int TB = 256;  // threads per transform block
+constexpr int CL = 16;   // interleaved lines per tile
+
+// ------------------------------------------------------------------ fft z
+// 32 real rows (iy0 .. iy0+31) of one (level, ix) plane per item, packed as 16
+// complex lines (row 2q in the real part, row 2q+1 in the imaginary part of
+// line q).  Lane l of a warp owns row iy0 + l: it reads 16 bytes of its row
+// and writes them to tile floats [pos][l], so the shared-memory writes of a
+// warp are 32 consecutive floats.  Compact index iz lands at position
+// (pos0_z + iz) mod n; the rest of the line is zero.  Every cell read is reset
+// to zero, so the spreading boxes are clean for the next launch.
+// Output rows: with Z = FFT(a + i b), A_k = (Z_k + conj Z_{n-k}) / 2,
+// B_k = (Z_k - conj Z_{n-k}) / (2i), for m_z = k in [0, N/2).
+template <int NF>
+__global__ void __launch_bounds__(TB)
 k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
         float *grid, float2 *z1)
 {
-    constexpr int LINES = (4096 / NF) < 4 ? 4 : (4096 / NF);
-    constexpr int LS = NF + 1;
-    extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + NF, *B = A + LINES * LS;
+    extern __shared__ float4 sm4[];
+    float2 *tw = reinterpret_cast<float2 *>(sm4);
+    float2 *A = tw + NF, *B = A + NF * CL;
     load_twiddles<NF>(tw, tb.tw_n);
     const int H = g.H, L = g.L;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *Af = reinterpret_cast<float *>(A);
     RotStart rs;
     for (int i = 0; i < ninst; i++) {
         const InstPlan p = plan[i];
         if (p.b[0] == 0) continue;
-        const int b0 = p.b[0], b1 = p.b[1], bz = p.b[2], bzp = p.bzp, by2 = (b1 + 1) >> 1;
-        const int items = L * b0 * by2;
-        const int nblk = (items + LINES - 1) / LINES;
+        const int b0 = p.b[0], b1 = p.b[1], bz = p.b[2], bzp = p.bzp;
+        const int nyb = (b1 + 31) >> 5;
+        const int items = L * b0 * nyb;
         const InstDesc d = inst[i];
-        for (int blk = rs.first(); blk < nblk; blk += gridDim.x) {
-            for (int e = threadIdx.x; e < LINES * NF; e += blockDim.x) A[(e / NF) * LS + (e % NF)] = make_float2(0.f, 0.f);
+        for (int it = rs.first(); it < items; it += gridDim.x) {
+            const int l = it / (b0 * nyb), rem = it - l * (b0 * nyb);
+            const int ix = rem / nyb, iy0 = (rem - ix * nyb) << 5;
+            zero_tile<NF>(A);
             __syncthreads();
-            for (int e = threadIdx.x; e < LINES * bz; e += blockDim.x) {
-                const int q = e / bz, iz = e - q * bz;
-                const int item = blk * LINES + q;
-                if (item >= items) continue;
-                const int l = item / (b0 * by2), rem = item - l * (b0 * by2);
-                const int ix = rem / by2, iy0 = 2 * (rem - ix * by2);
-                float *G = grid + d.grid_off + (long long)l * b0 * b1 * bzp + ((long long)ix * b1 + iy0) * bzp;
-                float a = G[iz];
-                G[iz] = 0.f;
-                float b = 0.f;
-                if (iy0 + 1 < b1) {
-                    b = G[bzp + iz];
-                    G[bzp + iz] = 0.f;
+            const int iy = iy0 + lane;
+            float *row = grid + d.grid_off + (long long)l * b0 * b1 * bzp + ((long long)ix * b1 + iy) * bzp;
+            if (iy < b1) {
+                // 4 floats per warp per step, warps interleaved along z
+                for (int z4 = w * 4; z4 < bzp; z4 += 4 * (TB / 32) * 4) {
+                    float4 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int zz = z4 + u * 4 * (TB / 32);
+                        v[u] = zz < bzp ? *reinterpret_cast<const float4 *>(row + zz) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int zz = z4 + u * 4 * (TB / 32);
+                        if (zz < bzp) {
+                            *reinterpret_cast<float4 *>(row + zz) = make_float4(0.f, 0.f, 0.f, 0.f);
+                            const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                            for (int s = 0; s < 4; s++) {
+                                const int iz = zz + s;
+                                if (iz < bz) {
+                                    int pos = p.pos0[2] + iz;
+                                    if (pos >= NF) pos -= NF;
+                                    Af[pos * 32 + lane] = vv[s];
+                                }
+                            }
+                        }
+                    }
                 }
-                int pos = p.pos0[2] + iz;
-                if (pos >= NF) pos -= NF;
-                A[q * LS + pos] = make_float2(a, b);
             }
             __syncthreads();
-            float2 *res = fft_lines<NF, false>(A, B, LINES, LS, tw);
-            for (int e = threadIdx.x; e < LINES * H; e += blockDim.x) {
-                const int q = e / H, k = e - q * H;
-                const int item = blk * LINES + q;
-                if (item >= items) continue;
-                const int l = item / (b0 * by2), rem = item - l * (b0 * by2);
-                const int ix = rem / by2, iy0 = 2 * (rem - ix * by2);
-                const float2 zk = res[q * LS + k];
-                const float2 zn = res[q * LS + (k == 0 ? 0 : NF - k)];
-                const float2 ak = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-                const float2 bk = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
-                float2 *Z = z1 + d.z1_off + (((long long)l * b0 + ix) * b1 + iy0) * H;
-                Z[k] = ak;
-                if (iy0 + 1 < b1) Z[H + k] = bk;
+            const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
+            // unpack: lane l -> row iy0 + l, pairs of modes (k, k + 1)
+            const int q = lane >> 1, odd = lane & 1;
+            if (iy < b1) {
+                float2 *Z = z1 + d.z1_off + (((long long)l * b0 + ix) * b1 + iy) * H;
+                for (int k = 2 * w; k < H; k += 2 * (TB / 32)) {
+                    float2 o[2];
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const int kk = k + u;
+                        const float2 zk = res[kk * CL + q];
+                        const float2 zn = res[(kk == 0 ? 0 : NF - kk) * CL + q];
+                        o[u] = odd ? make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x))
+                                   : make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+                    }
+                    *reinterpret_cast<float4 *>(Z + k) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+                }
             }
             __syncthreads();
         }
-        rs.rot += nblk;
+        rs.rot += items;
     }
 }
 
 // ------------------------------------------------------------------ fft y
-// For each (level, ix) plane and a chunk of C z-modes: transform along y over
-// the support rows only; keep m_y in (-N/2, N/2) at FFT index j (m_y = -N/2,
-// j = N/2, is stored as zero).
+// Item: (level, ix) plane and a chunk of 16 z-modes.  Rows iy of the chunk
+// (16 complex = 128 bytes) land at tile position (pos0_y + iy) mod n; the
+// transform runs along y; m_y in (-N/2, N/2) is kept at FFT index j
+// (j = N/2, m_y = -N/2, stored as zero).
 template <int NF>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(TB)
 k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
         const float2 *__restrict__ z1, float2 *y1)
 {
-    constexpr int C = 16;
-    constexpr int LS = NF + 1;
-    extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + NF, *B = A + C * LS;
+    extern __shared__ float4 sm4[];
+    float2 *tw = reinterpret_cast<float2 *>(sm4);
+    float2 *A = tw + NF, *B = A + NF * CL;
     load_twiddles<NF>(tw, tb.tw_n);
     const int H = g.H, L = g.L, N = g.N;
-    const int Cc = H < C ? H : C;
-    const int nch = H / Cc;
+    const int nch = H / CL;
+    const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3; // 8 float4 per 128-byte row
     RotStart rs;
     for (int i = 0; i < ninst; i++) {
         const InstPlan p = plan[i];
@@ -418,24 +509,34 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
         for (int it = rs.first(); it < items; it += gridDim.x) {
             const int l = it / (b0 * nch), rem = it - l * (b0 * nch);
             const int ix = rem / nch, ch = rem - ix * nch;
-            for (int e = threadIdx.x; e < Cc * NF; e += blockDim.x) A[(e / NF) * LS + (e % NF)] = make_float2(0.f, 0.f);
+            zero_tile<NF>(A);
             __syncthreads();
-            const float2 *Z = z1 + d.z1_off + ((long long)l * b0 + ix) * b1 * H + ch * Cc;
-            for (int e = threadIdx.x; e < b1 * Cc; e += blockDim.x) {
-                const int iy = e / Cc, c = e - iy * Cc;
-                int pos = p.pos0[1] + iy;
-                if (pos >= NF) pos -= NF;
-                A[c * LS + pos] = Z[(long long)iy * H + c];
+            const float2 *Z = z1 + d.z1_off + ((long long)l * b0 + ix) * b1 * H + ch * CL + 2 * part;
+            for (int iyb = r8; iyb < b1; iyb += 4 * (TB / 8)) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int iy = iyb + u * (TB / 8);
+                    v[u] = iy < b1 ? *reinterpret_cast<const float4 *>(Z + (long long)iy * H) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int iy = iyb + u * (TB / 8);
+                    if (iy < b1) {
+                        int pos = p.pos0[1] + iy;
+                        if (pos >= NF) pos -= NF;
+                        *reinterpret_cast<float4 *>(A + pos * CL + 2 * part) = v[u];
+                    }
+                }
             }
             __syncthreads();
-            float2 *res = fft_lines<NF, false>(A, B, Cc, LS, tw);
-            float2 *Y = y1 + d.y1_off + ((long long)l * b0 + ix) * N * H + ch * Cc;
-            for (int e = threadIdx.x; e < N * Cc; e += blockDim.x) {
-                const int j = e / Cc, c = e - j * Cc;
+            const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
+            float2 *Y = y1 + d.y1_off + ((long long)l * b0 + ix) * N * H + ch * CL + 2 * part;
+            for (int j = r8; j < N; j += TB / 8) {
                 const int m = mode_of(j, N);
-                float2 v = make_float2(0.f, 0.f);
-                if (j != N / 2) v = res[c * LS + (m < 0 ? m + NF : m)];
-                Y[(long long)j * H + c] = v;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j != N / 2) v = *reinterpret_cast<const float4 *>(res + (m < 0 ? m + NF : m) * CL + 2 * part);
+                *reinterpret_cast<float4 *>(Y + (long long)j * H) = v;
             }
             __syncthreads();
         }
@@ -443,106 +544,132 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     }
 }
 
+// Level-summed spectrum of one instance for the modes (j_x = jx0 + 16 u, j_y,
+// m_z = 16 ch + c) owned by this thread: for each level, the y-transformed
+// rows over the support box are placed in a zero tile, transformed along x,
+// and the kept modes are weighted by T_l(|m|^2) D(m) and added.
+template <int NF, int NI, int NU>
+__device__ __forceinline__ void spectrum_x(float2 (&F)[NU], const Geometry &g, const Tables &tb,
+                                           const InstDesc *__restrict__ inst, const InstPlan *__restrict__ plan,
+                                           int si, const float2 *__restrict__ y1, int jy, int ch,
+                                           const float2 *twF, float2 *A, float2 *B)
+{
+    const int H = g.H, L = g.L, N = NI;
+    const int Q = tb.qmax + 1;
+    const int c = threadIdx.x & (CL - 1), jx0 = threadIdx.x / CL;
+    const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3;
+    const int my = mode_of(jy, N), mz = ch * CL + c;
+    const float dyz = tb.deconv[jy] * tb.deconv[mz];
+#pragma unroll
+    for (int u = 0; u < NU; u++) F[u] = make_float2(0.f, 0.f);
+    const InstPlan p = plan[si];
+    if (p.b[0] == 0) return;
+    const InstDesc d = inst[si];
+    const int b0 = p.b[0];
+    for (int l = 0; l < L; l++) {
+        zero_tile<NF>(A);
+        __syncthreads();
+        const float2 *Y = y1 + d.y1_off + (long long)l * b0 * N * H + (long long)jy * H + ch * CL + 2 * part;
+        for (int ixb = r8; ixb < b0; ixb += 4 * (TB / 8)) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int ix = ixb + u * (TB / 8);
+                v[u] = ix < b0 ? *reinterpret_cast<const float4 *>(Y + (long long)ix * N * H)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int ix = ixb + u * (TB / 8);
+                if (ix < b0) {
+                    int pos = p.pos0[0] + ix;
+                    if (pos >= NF) pos -= NF;
+                    *reinterpret_cast<float4 *>(A + pos * CL + 2 * part) = v[u];
+                }
+            }
+        }
+        __syncthreads();
+        const float2 *res = il_fft<NF, false, CL, TB>(A, B, twF);
+        const float *T = tb.ballft + (long long)l * Q;
+#pragma unroll
+        for (int u = 0; u < NU; u++) {
+            const int jx = jx0 + u * (TB / CL);
+            const int mx = mode_of(jx, N);
+            const float Mv = T[mx * mx + my * my + mz * mz] * tb.deconv[jx] * dyz;
+            const float2 v = res[(mx < 0 ? mx + NF : mx) * CL + c];
+            F[u] = make_float2(fmaf(Mv, v.x, F[u].x), fmaf(Mv, v.y, F[u].y));
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ fft x + combine
-// For each pair and each (j_y, chunk of C z-modes):
-//   F_s(m) = sum_l T_l(|m|^2) D(m) FFT_x[Y1_{s,l}](m)    (s = A, B)
+// For each pair and each (j_y, chunk of 16 z-modes):
+//   F_s(m) = sum_l T_l(|m|^2) D(m) FFT_x[Y_{s,l}](m)    (s = A, B)
 //   g'(m)  = P^-3 (-1)^(m_x+m_y+m_z) F_A(m) conj(F_B(m)), zero on the Nyquist planes
 //   H(k_x, j_y, m_z) = sum_{j_x} g'(m) exp(+2 pi i j_x k_x / N)
 // D(m) = deconv[j_x] deconv[j_y] deconv[m_z].  The sign moves the origin of the
 // translation grid to t = -P/2: exp(2 pi i m (-P/2) / P) = (-1)^m.
-// With pair.a < 0, F_A comes from the cached spectrum; with pair.b < 0, F_A is
-// written to `fa_out` and nothing else happens.
+// Thread t accumulates the modes (j_x = t/16 + 16 u, column t mod 16) in
+// registers.  With pair.a < 0, F_A comes from the cached spectrum; with
+// pair.b < 0, F_A is written to `fa_out` and nothing else happens.
 template <int NF, int NI>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(TB)
 k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan *__restrict__ plan,
         const PairDesc *__restrict__ pairs, int npairs, const float2 *__restrict__ y1,
         const float2 *__restrict__ fa_cache, float2 *fa_out, float2 *h)
 {
-    constexpr int C = 16;
-    constexpr int LSF = NF + 1, LSI = NI + 1;
-    extern __shared__ float2 sm[];
-    float2 *twF = sm, *twI = twF + NF, *A = twI + NI, *B = A + C * LSF, *FA = B + C * LSF, *FB = FA + C * NI;
+    constexpr int NU = NI / (TB / CL); // accumulated modes per thread
+    extern __shared__ float4 sm4[];
+    float2 *twF = reinterpret_cast<float2 *>(sm4);
+    float2 *twI = twF + NF, *A = twI + NI, *B = A + NF * CL;
     load_twiddles<NF>(twF, tb.tw_n);
     load_twiddles<NI>(twI, tb.tw_N);
-    const int H = g.H, L = g.L, N = NI;
-    const int Cc = H < C ? H : C;
-    const int nch = H / Cc;
+    const int H = g.H, N = NI;
+    const int nch = H / CL;
     const int items = N * nch;
-    const int Q = tb.qmax + 1;
+    const int c = threadIdx.x & (CL - 1), jx0 = threadIdx.x / CL;
+    const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3;
     RotStart rs;
     for (int pi = 0; pi < npairs; pi++) {
         const PairDesc pr = pairs[pi];
         for (int it = rs.first(); it < items; it += gridDim.x) {
             const int jy = it / nch, ch = it - jy * nch;
-            const int my = mode_of(jy, N);
-            const float djy = tb.deconv[jy];
-            for (int side = 0; side < 2; side++) {
-                float2 *acc = side ? FB : FA;
-                const int si = side ? pr.b : pr.a;
-                if (side == 1 && si < 0) break;
-                if (si < 0) {
-                    for (int e = threadIdx.x; e < Cc * NI; e += blockDim.x) {
-                        const int c = e / NI, jx = e - c * NI;
-                        acc[e] = fa_cache[((long long)jx * N + jy) * H + ch * Cc + c];
-                    }
-                    continue;
-                }
-                for (int e = threadIdx.x; e < Cc * NI; e += blockDim.x) acc[e] = make_float2(0.f, 0.f);
-                const InstPlan p = plan[si];
-                if (p.b[0] == 0) continue;
-                const InstDesc d = inst[si];
-                const int b0 = p.b[0];
-                for (int l = 0; l < L; l++) {
-                    for (int e = threadIdx.x; e < Cc * NF; e += blockDim.x) A[(e / NF) * LSF + (e % NF)] = make_float2(0.f, 0.f);
-                    __syncthreads();
-                    const float2 *Y = y1 + d.y1_off + (long long)l * b0 * N * H + (long long)jy * H + ch * Cc;
-                    for (int e = threadIdx.x; e < b0 * Cc; e += blockDim.x) {
-                        const int ix = e / Cc, c = e - ix * Cc;
-                        int pos = p.pos0[0] + ix;
-                        if (pos >= NF) pos -= NF;
-                        A[c * LSF + pos] = Y[(long long)ix * N * H + c];
-                    }
-                    __syncthreads();
-                    float2 *res = fft_lines<NF, false>(A, B, Cc, LSF, twF);
-                    const float *T = tb.ballft + (long long)l * Q;
-                    for (int e = threadIdx.x; e < Cc * NI; e += blockDim.x) {
-                        const int c = e / NI, jx = e - c * NI;
-                        if (jx == N / 2) continue;
-                        const int mx = mode_of(jx, N), mz = ch * Cc + c;
-                        const float Mv = T[mx * mx + my * my + mz * mz] * tb.deconv[jx] * djy * tb.deconv[mz];
-                        const float2 v = res[c * LSF + (mx < 0 ? mx + NF : mx)];
-                        acc[e] = make_float2(fmaf(Mv, v.x, acc[e].x), fmaf(Mv, v.y, acc[e].y));
-                    }
-                    __syncthreads();
-                }
+            const int my = mode_of(jy, N), mz = ch * CL + c;
+            float2 FA[NU], FB[NU];
+            if (pr.a < 0) {
+#pragma unroll
+                for (int u = 0; u < NU; u++)
+                    FA[u] = fa_cache[((long long)(jx0 + u * (TB / CL)) * N + jy) * H + mz];
+            } else {
+                spectrum_x<NF, NI, NU>(FA, g, tb, inst, plan, pr.a, y1, jy, ch, twF, A, B);
             }
-            __syncthreads();
+            if (pr.b >= 0) spectrum_x<NF, NI, NU>(FB, g, tb, inst, plan, pr.b, y1, jy, ch, twF, A, B);
             if (pr.b < 0) {
-                for (int e = threadIdx.x; e < Cc * NI; e += blockDim.x) {
-                    const int jx = e / Cc, c = e - jx * Cc;
-                    fa_out[((long long)jx * N + jy) * H + ch * Cc + c] = FA[c * NI + jx];
+#pragma unroll
+                for (int u = 0; u < NU; u++) {
+                    const int jx = jx0 + u * (TB / CL);
+                    fa_out[((long long)jx * N + jy) * H + mz] = FA[u];
                 }
-                __syncthreads();
                 continue;
             }
-            for (int e = threadIdx.x; e < Cc * NI; e += blockDim.x) {
-                const int c = e / NI, jx = e - c * NI;
-                const int mx = mode_of(jx, N), mz = ch * Cc + c;
+#pragma unroll
+            for (int u = 0; u < NU; u++) {
+                const int jx = jx0 + u * (TB / CL);
+                const int mx = mode_of(jx, N);
                 float2 v = make_float2(0.f, 0.f);
                 if (jx != N / 2 && jy != N / 2) {
-                    v = cmulc(FA[e], FB[e]);
+                    v = cmulc(FA[u], FB[u]);
                     const float sg = ((mx + my + mz) & 1) ? -g.inv_P3 : g.inv_P3;
                     v = cscale(v, sg);
                 }
-                A[c * LSI + jx] = v;
+                A[jx * CL + c] = v;
             }
             __syncthreads();
-            float2 *res = fft_lines<NI, true>(A, B, Cc, LSI, twI);
-            float2 *Hp = h + pr.h_off + (long long)jy * H + ch * Cc;
-            for (int e = threadIdx.x; e < Cc * NI; e += blockDim.x) {
-                const int kx = e / Cc, c = e - kx * Cc;
-                Hp[(long long)kx * N * H + c] = res[c * LSI + kx];
-            }
+            const float2 *res = il_fft<NI, true, CL, TB>(A, B, twI);
+            float2 *Hp = h + pr.h_off + (long long)jy * H + ch * CL + 2 * part;
+            for (int kx = r8; kx < N; kx += TB / 8)
+                *reinterpret_cast<float4 *>(Hp + (long long)kx * N * H) = *reinterpret_cast<const float4 *>(res + kx * CL + 2 * part);
             __syncthreads();
         }
         rs.rot += items;
@@ -551,35 +678,41 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
 
 // ------------------------------------------------------------------ inverse y
 template <int NI>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(TB)
 k_ifft_y(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, float2 *h)
 {
-    constexpr int C = 16;
-    constexpr int LS = NI + 1;
-    extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + NI, *B = A + C * LS;
+    extern __shared__ float4 sm4[];
+    float2 *tw = reinterpret_cast<float2 *>(sm4);
+    float2 *A = tw + NI, *B = A + NI * CL;
     load_twiddles<NI>(tw, tb.tw_N);
     const int H = g.H, N = NI;
-    const int Cc = H < C ? H : C;
-    const int nch = H / Cc;
+    const int nch = H / CL;
     const int items = N * nch;
+    const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3;
     RotStart rs;
     for (int pi = 0; pi < npairs; pi++) {
         const PairDesc pr = pairs[pi];
         if (pr.b < 0) continue;
         for (int it = rs.first(); it < items; it += gridDim.x) {
             const int kx = it / nch, ch = it - kx * nch;
-            float2 *Hp = h + pr.h_off + (long long)kx * N * H + ch * Cc;
-            for (int e = threadIdx.x; e < N * Cc; e += blockDim.x) {
-                const int jy = e / Cc, c = e - jy * Cc;
-                A[c * LS + jy] = Hp[(long long)jy * H + c];
+            float2 *Hp = h + pr.h_off + (long long)kx * N * H + ch * CL + 2 * part;
+            for (int jyb = r8; jyb < N; jyb += 4 * (TB / 8)) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int jy = jyb + u * (TB / 8);
+                    v[u] = jy < N ? *reinterpret_cast<const float4 *>(Hp + (long long)jy * H) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int jy = jyb + u * (TB / 8);
+                    if (jy < N) *reinterpret_cast<float4 *>(A + jy * CL + 2 * part) = v[u];
+                }
             }
             __syncthreads();
-            float2 *res = fft_lines<NI, true>(A, B, Cc, LS, tw);
-            for (int e = threadIdx.x; e < N * Cc; e += blockDim.x) {
-                const int ky = e / Cc, c = e - ky * Cc;
-                Hp[(long long)ky * H + c] = res[c * LS + ky];
-            }
+            const float2 *res = il_fft<NI, true, CL, TB>(A, B, tw);
+            for (int ky = r8; ky < N; ky += TB / 8)
+                *reinterpret_cast<float4 *>(Hp + (long long)ky * H) = *reinterpret_cast<const float4 *>(res + ky * CL + 2 * part);
             __syncthreads();
         }
         rs.rot += items;
@@ -587,66 +720,77 @@ k_ifft_y(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
 }
 
 // ------------------------------------------------------------------ inverse z (c2r)
-// Rows a (k_y even) and b (k_y + 1) of the half spectrum are packed as
-// Z_k = A_k + i B_k over the full range (A_{N-k} = conj A_k, A_0 taken real,
-// the m_z = N/2 term zero); the inverse transform of Z is a + i b.
+// Item: 32 output rows (k_x, k_y0 .. k_y0+31) as 16 complex lines; lane l of a
+// warp owns row k_y0 + l.  Rows a = 2q and b = 2q+1 of the half spectrum are
+// packed as Z_k = A_k + i B_k over the full range (A_{N-k} = conj A_k, A_0
+// taken real, the m_z = N/2 term zero); the inverse transform of Z is a + i b.
+// The even lane of each pair writes Z_k, the odd lane Z_{N-k}.
 template <int NI>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(TB)
 k_ifft_z(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, const float2 *__restrict__ h,
          float *out)
 {
-    constexpr int LINES = (4096 / NI) < 4 ? 4 : (4096 / NI);
-    constexpr int LS = NI + 1;
-    extern __shared__ float2 sm[];
-    float2 *tw = sm, *A = sm + NI, *B = A + LINES * LS;
+    extern __shared__ float4 sm4[];
+    float2 *tw = reinterpret_cast<float2 *>(sm4);
+    float2 *A = tw + NI, *B = A + NI * CL;
     load_twiddles<NI>(tw, tb.tw_N);
     const int H = g.H, N = NI;
-    const int items = N * (N / 2);
-    const int nblk = (items + LINES - 1) / LINES;
+    const int nyb = N / 32;
+    const int items = N * nyb;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane >> 1, odd = lane & 1;
     RotStart rs;
     for (int pi = 0; pi < npairs; pi++) {
         const PairDesc pr = pairs[pi];
         if (pr.b < 0) continue;
-        for (int blk = rs.first(); blk < nblk; blk += gridDim.x) {
-            for (int e = threadIdx.x; e < LINES * NI; e += blockDim.x) {
-                const int q = e / NI, k = e - q * NI;
-                const int item = blk * LINES + q;
-                float2 z = make_float2(0.f, 0.f);
-                if (item < items) {
-                    const int kx = item / (N / 2), ky0 = 2 * (item - kx * (N / 2));
-                    const float2 *r0 = h + pr.h_off + ((long long)kx * N + ky0) * H;
-                    const float2 *r1 = r0 + H;
-                    if (k == 0) {
-                        z = make_float2(r0[0].x, r1[0].x);
-                    } else if (k < H) {
-                        const float2 a = r0[k], b = r1[k];
-                        z = make_float2(a.x - b.y, a.y + b.x);
-                    } else if (k > H) {
-                        const float2 a = r0[NI - k], b = r1[NI - k];
-                        z = make_float2(a.x + b.y, b.x - a.y);
+        for (int it = rs.first(); it < items; it += gridDim.x) {
+            const int kx = it / nyb, ky0 = (it - kx * nyb) << 5;
+            const float2 *row = h + pr.h_off + ((long long)kx * N + ky0 + lane) * H;
+            if (threadIdx.x < CL) A[H * CL + threadIdx.x] = make_float2(0.f, 0.f); // m_z = N/2
+            for (int k = 2 * w; k < H; k += 2 * (TB / 32)) {
+                const float4 v = *reinterpret_cast<const float4 *>(row + k);
+                const float4 o = make_float4(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1),
+                                             __shfl_xor_sync(0xffffffffu, v.z, 1), __shfl_xor_sync(0xffffffffu, v.w, 1));
+                const float4 a = odd ? o : v, b = odd ? v : o; // rows 2q and 2q+1 at modes k, k+1
+#pragma unroll
+                for (int u = 0; u < 2; u++) {
+                    const float ax = u ? a.z : a.x, ay = u ? a.w : a.y, bx = u ? b.z : b.x, by = u ? b.w : b.y;
+                    const int kk = k + u;
+                    if (!odd) {
+                        A[kk * CL + q] = kk == 0 ? make_float2(ax, bx) : make_float2(ax - by, ay + bx);
+                    } else if (kk != 0) {
+                        A[(N - kk) * CL + q] = make_float2(ax + by, bx - ay);
                     }
                 }
-                A[q * LS + k] = z;
             }
             __syncthreads();
-            float2 *res = fft_lines<NI, true>(A, B, LINES, LS, tw);
-            for (int e = threadIdx.x; e < LINES * NI; e += blockDim.x) {
-                const int q = e / NI, kz = e - q * NI;
-                const int item = blk * LINES + q;
-                if (item >= items) continue;
-                const int kx = item / (N / 2), ky0 = 2 * (item - kx * (N / 2));
-                float *o = out + pr.out_off + ((long long)kx * N + ky0) * N;
-                const float2 v = res[q * LS + kz];
-                o[kz] = v.x;
-                o[N + kz] = v.y;
+            const float2 *res = il_fft<NI, true, CL, TB>(A, B, tw);
+            float *o = out + pr.out_off + ((long long)kx * N + ky0 + lane) * N;
+            for (int kz = 4 * w; kz < N; kz += 4 * (TB / 32)) {
+                float r[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const float2 v = res[(kz + u) * CL + q];
+                    r[u] = odd ? v.y : v.x;
+                }
+                *reinterpret_cast<float4 *>(o + kz) = make_float4(r[0], r[1], r[2], r[3]);
             }
             __syncthreads();
         }
-        rs.rot += nblk;
+        rs.rot += items;
     }
 }
 
 // ------------------------------------------------------------------ launchers
+// Blocks per launch: the number that can be resident on the device at once.
+template <typename K>
+static int resident_blocks(K kernel, size_t smem, int nsm)
+{
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, TB, smem) != cudaSuccess || per < 1) per = 1;
+    return per * nsm;
+}
+
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes)
 {
@@ -658,11 +802,10 @@ template <int NF>
 static cudaError_t fft_z_t(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
                            float *grid, float2 *z1, int nsm, cudaStream_t s)
 {
-    constexpr int LINES = (4096 / NF) < 4 ? 4 : (4096 / NF);
-    size_t smem = sizeof(float2) * (NF + 2 * LINES * (NF + 1));
+    const size_t smem = sizeof(float2) * (NF + 2 * NF * CL);
     cudaError_t e = set_smem(k_fft_z<NF>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_z<NF><<<2 * nsm, 256, smem, s>>>(g, t, inst, ninst, plan, grid, z1);
+    k_fft_z<NF><<<resident_blocks(k_fft_z<NF>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, grid, z1);
     return cudaGetLastError();
 }
 
@@ -683,10 +826,10 @@ template <int NF>
 static cudaError_t fft_y_t(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
                            const float2 *z1, float2 *y1, int nsm, cudaStream_t s)
 {
-    size_t smem = sizeof(float2) * (NF + 2 * 16 * (NF + 1));
+    const size_t smem = sizeof(float2) * (NF + 2 * NF * CL);
     cudaError_t e = set_smem(k_fft_y<NF>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_y<NF><<<2 * nsm, 256, smem, s>>>(g, t, inst, ninst, plan, z1, y1);
+    k_fft_y<NF><<<resident_blocks(k_fft_y<NF>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, z1, y1);
     return cudaGetLastError();
 }
 
@@ -708,10 +851,11 @@ static cudaError_t fft_x_t(const Geometry &g, const Tables &t, const InstDesc *i
                            const PairDesc *pairs, int npairs, const float2 *y1, const float2 *fa_cache, float2 *fa_out,
                            float2 *h, int nsm, cudaStream_t s)
 {
-    size_t smem = sizeof(float2) * (NF + NI + 2 * 16 * (NF + 1) + 2 * 16 * NI);
+    const size_t smem = sizeof(float2) * (NF + NI + 2 * NF * CL);
     cudaError_t e = set_smem(k_fft_x<NF, NI>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_x<NF, NI><<<2 * nsm, 256, smem, s>>>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h);
+    k_fft_x<NF, NI><<<resident_blocks(k_fft_x<NF, NI>, smem, nsm), TB, smem, s>>>(g, t, inst, plan, pairs, npairs, y1,
+                                                                                fa_cache, fa_out, h);
     return cudaGetLastError();
 }
 
@@ -733,10 +877,10 @@ template <int NI>
 static cudaError_t ifft_y_t(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, float2 *h, int nsm,
                             cudaStream_t s)
 {
-    size_t smem = sizeof(float2) * (NI + 2 * 16 * (NI + 1));
+    const size_t smem = sizeof(float2) * (NI + 2 * NI * CL);
     cudaError_t e = set_smem(k_ifft_y<NI>, smem);
     if (e != cudaSuccess) return e;
-    k_ifft_y<NI><<<2 * nsm, 256, smem, s>>>(g, t, pairs, npairs, h);
+    k_ifft_y<NI><<<resident_blocks(k_ifft_y<NI>, smem, nsm), TB, smem, s>>>(g, t, pairs, npairs, h);
     return cudaGetLastError();
 }
 
@@ -757,11 +901,10 @@ template <int NI>
 static cudaError_t ifft_z_t(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, const float2 *h,
                             float *out, int nsm, cudaStream_t s)
 {
-    constexpr int LINES = (4096 / NI) < 4 ? 4 : (4096 / NI);
-    size_t smem = sizeof(float2) * (NI + 2 * LINES * (NI + 1));
+    const size_t smem = sizeof(float2) * (NI + 2 * NI * CL);
     cudaError_t e = set_smem(k_ifft_z<NI>, smem);
     if (e != cudaSuccess) return e;
-    k_ifft_z<NI><<<2 * nsm, 256, smem, s>>>(g, t, pairs, npairs, h, out);
+    k_ifft_z<NI><<<resident_blocks(k_ifft_z<NI>, smem, nsm), TB, smem, s>>>(g, t, pairs, npairs, h, out);
     return cudaGetLastError();
 }
 

@@ -14,8 +14,8 @@
 // The kernels are the ones bc_correlate launches; only their scratch pointers
 // differ.  All calls share the one array: two calls whose work overlaps on
 // the GPU (different streams, or different host threads) race on it and give
-// wrong results.  The parts that must start at zero (the spreading boxes, the
-// status words) are cleared by every call.
+// wrong results.  The parts that must start at a known state (the spreading
+// boxes, the support-box accumulators, the status words) are reset by every call.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -45,7 +45,8 @@ constexpr size_t oTwN = al(oTwn + sizeof(float2) * kn);
 constexpr size_t oConsts = al(oTwN + sizeof(float2) * kN);
 constexpr size_t oErr = al(oConsts + sizeof(float) * 4);
 constexpr size_t oStats = al(oErr + sizeof(int));
-constexpr size_t oInst = al(oStats + sizeof(unsigned) * 4);
+constexpr size_t oBoxes = al(oStats + sizeof(unsigned) * 4);
+constexpr size_t oInst = al(oBoxes + sizeof(int) * 8 * 2);
 constexpr size_t oPairs = al(oInst + sizeof(InstDesc) * 2);
 constexpr size_t oPlan = al(oPairs + sizeof(PairDesc));
 constexpr size_t oKnots = al(oPlan + sizeof(InstPlan) * 2);
@@ -152,6 +153,7 @@ extern "C" bc_status bc_correlate_noalloc(const bc_params *p, const float *xyzA,
         float2 *twn = (float2 *)(base + oTwn), *twN = (float2 *)(base + oTwN);
         float *consts = (float *)(base + oConsts);
         int *err = (int *)(base + oErr);
+        int *boxes = (int *)(base + oBoxes);
         unsigned *stats = (unsigned *)(base + oStats);
         InstDesc *dinst = (InstDesc *)(base + oInst);
         PairDesc *dpairs = (PairDesc *)(base + oPairs);
@@ -165,6 +167,7 @@ extern "C" bc_status bc_correlate_noalloc(const bc_params *p, const float *xyzA,
         if ((e = cudaMemsetAsync(err, 0, sizeof(int), st)) != cudaSuccess) return ncuda(e, "clear err");
         if ((e = cudaMemsetAsync(stats, 0, sizeof(unsigned) * 4, st)) != cudaSuccess) return ncuda(e, "clear stats");
         if ((e = cudaMemsetAsync(grid, 0, kGridBytes, st)) != cudaSuccess) return ncuda(e, "clear grid");
+        if ((e = launch_reset_boxes(boxes, 2, st)) != cudaSuccess) return ncuda(e, "reset boxes");
         // tables for this call's parameters
         if ((e = cudaMemcpyAsync(radii, p->level_radii, sizeof(double) * g.L, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return ncuda(e, "copy radii");
@@ -212,7 +215,8 @@ extern "C" bc_status bc_correlate_noalloc(const bc_params *p, const float *xyzA,
         t.tw_N = twN;
         t.qmax = kQ - 1;
         t.consts = consts;
-        if ((e = launch_prepare(g, dinst, 2, ku, dplan, err, st)) != cudaSuccess) return ncuda(e, "prepare");
+        if ((e = launch_prepare(g, dinst, 2, nA > nB ? nA : nB, ku, boxes, dplan, err, st)) != cudaSuccess)
+            return ncuda(e, "prepare");
         if ((e = launch_spread(g, t, dinst, nA + nB, ku, dplan, grid, st)) != cudaSuccess) return ncuda(e, "spread");
         if ((e = launch_fft_z(g, t, dinst, 2, dplan, grid, z1, nsm, st)) != cudaSuccess) return ncuda(e, "fft z");
         if ((e = launch_fft_y(g, t, dinst, 2, dplan, z1, y1, nsm, st)) != cudaSuccess) return ncuda(e, "fft y");
