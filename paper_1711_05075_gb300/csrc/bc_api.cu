@@ -454,7 +454,7 @@ bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quat
                 for (int a = 0; a < 4; a++) d.q[a] = quats[4 * (i - 1) + a];
             }
             koff += s->n;
-            goff += (long long)L * e * e * ((e + 3) & ~3);
+            goff += (long long)L * e * (((e + 31) / 32) * 32) * e; // block-transposed boxes, y padded to 32
             zoff += (long long)L * e * e * H;
             yoff += (long long)L * e * N * H;
         }

@@ -10,7 +10,7 @@
 // applies an R-point DFT and writes y[(j div Ns) Ns R + (j mod Ns) + r Ns].
 // Output is in natural order after the last stage; stages ping-pong between
 // two shared-memory tiles.  Radix schedules: 32 = 4.8, 64 = 8.8,
-// 96 = 3.4.8, 128 = 2.8.8, 192 = 3.8.8, 256 = 4.8.8, 512 = 8.8.8.
+// 96 = 3.4.8, 128 = 8.16, 192 = 3.8.8, 256 = 16.16, 512 = 8.8.8.
 //
 // Direction: forward uses exp(-2 pi i jk/NF), inverse exp(+2 pi i jk/NF); no
 // scaling.  The twiddle table holds exp(-2 pi i k/NF), k < NF, rounded once
@@ -41,6 +41,26 @@ __device__ __forceinline__ float2 mul_mi(float2 a)
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
+// exp(-+2 pi i e / 16) for the exponents a radix-16 butterfly uses (e = 0..9)
+template <bool INV>
+__device__ __forceinline__ float2 tw16(int e)
+{
+    const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, h = 0.70710678118654752440f;
+    float2 w;
+    switch (e) {
+    case 0: w = make_float2(1.f, 0.f); break;
+    case 1: w = make_float2(c1, -s1); break;
+    case 2: w = make_float2(h, -h); break;
+    case 3: w = make_float2(s1, -c1); break;
+    case 4: w = make_float2(0.f, -1.f); break;
+    case 6: w = make_float2(-h, -h); break;
+    case 9: w = make_float2(-c1, s1); break;
+    default: w = make_float2(1.f, 0.f); break; // not used
+    }
+    if (INV) w.y = -w.y;
+    return w;
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft_small(float2 *v)
 {
@@ -65,6 +85,24 @@ __device__ __forceinline__ void dft_small(float2 *v)
         v[2] = csub(a0, b0);
         v[1] = cadd(a1, b1);
         v[3] = csub(a1, b1);
+    } else if constexpr (R == 16) {
+        // 16 = 4 x 4: index n = 4 n1 + n2, k = k1 + 4 k2; 4-point DFTs over n1,
+        // twiddles exp(-+2 pi i n2 k1 / 16), then 4-point DFTs over n2.
+        float2 y[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; n2++) {
+            float2 t[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+            dft_small<4, INV>(t);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; k1++) y[n2][k1] = cmul(t[k1], tw16<INV>(n2 * k1));
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < 4; k1++) {
+            float2 t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+            dft_small<4, INV>(t);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; k2++) v[k1 + 4 * k2] = t[k2];
+        }
     } else if constexpr (R == 8) {
         const float h = 0.70710678118654752440f;
         float2 a[4], b[4];
@@ -94,9 +132,9 @@ struct Radix;
 template <> struct Radix<32>  { static constexpr int r0 = 4, r1 = 8, r2 = 1; };
 template <> struct Radix<64>  { static constexpr int r0 = 8, r1 = 8, r2 = 1; };
 template <> struct Radix<96>  { static constexpr int r0 = 3, r1 = 4, r2 = 8; };
-template <> struct Radix<128> { static constexpr int r0 = 2, r1 = 8, r2 = 8; };
+template <> struct Radix<128> { static constexpr int r0 = 8, r1 = 16, r2 = 1; };
 template <> struct Radix<192> { static constexpr int r0 = 3, r1 = 8, r2 = 8; };
-template <> struct Radix<256> { static constexpr int r0 = 4, r1 = 8, r2 = 8; };
+template <> struct Radix<256> { static constexpr int r0 = 16, r1 = 16, r2 = 1; };
 template <> struct Radix<512> { static constexpr int r0 = 8, r1 = 8, r2 = 8; };
 
 // ---------------------------------------------------------------------------

@@ -275,13 +275,22 @@ cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, i
 }
 
 // ------------------------------------------------------------------ spread
+// Spreading boxes are stored block-transposed: per (instance, level)
+// [ix][iy / 32][iz][iy mod 32], so that the 32 rows of a z-transform tile are
+// one contiguous 128-byte run per z position.
+//
 // One warp per knot.  Lanes 0..3W-1 evaluate the separable window weights
-// phi(u_a - g) for the W cells of each axis; each lane then takes rows
-// (dx, dy) of the stencil and adds the W z-cells of a row with 16-byte vector
-// atomics aligned to the padded z extent (zero weights fill the unused lanes
-// of the first and last vector).  A row that wraps around the period (only
-// possible when the box spans all n cells) falls back to scalar atomics.
+// phi(u_a - g) for the W cells of each axis; each lane then takes stencil
+// columns (dx, dz) and adds the W y-cells of a column with 16-byte vector
+// atomics on 4-aligned groups (zero weights fill the unused slots of the first
+// and last group; a group never crosses a 32-row block).  A column that wraps
+// around the period (only when the box spans all n cells) uses scalar atomics.
 constexpr int SPREAD_WARPS = 8;
+
+__device__ __forceinline__ long long level_box_floats(const InstPlan &p)
+{
+    return (long long)p.b[0] * ((p.b[1] + 31) >> 5) * p.b[2] * 32;
+}
 
 __global__ void __launch_bounds__(SPREAD_WARPS * 32)
 k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restrict__ inst,
@@ -318,34 +327,33 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
             wts[wib][a][t] = expf(-g.beta * s2 / (1.f + sq)) * scaled_i0 * inv_scaled_i0beta;
         }
         __syncwarp();
-        const long long boxsz = (long long)p.b[0] * p.b[1] * p.bzp;
-        float *G = grid + inst[i].grid_off + (long long)level * boxsz;
-        const int iz0 = g0[2] - p.lo[2];
-        const bool zwrap = iz0 + W - 1 >= g.n;
-        const int a0 = iz0 & ~3, a1 = (iz0 + W - 1) | 3; // aligned vector span [a0, a1]
+        const int nyb = (p.b[1] + 31) >> 5, bz = p.b[2];
+        float *G = grid + inst[i].grid_off + (long long)level * level_box_floats(p);
+        const int iy0 = g0[1] - p.lo[1];
+        const bool ywrap = iy0 + W - 1 >= g.n;
         for (int r = lane; r < W2; r += 32) {
-            const int dx = r / W, dy = r - dx * W;
+            const int dx = r / W, dz = r - dx * W;
             int ix = g0[0] + dx - p.lo[0];
-            int iy = g0[1] + dy - p.lo[1];
+            int iz = g0[2] + dz - p.lo[2];
             if (ix >= g.n) ix -= g.n;
-            if (iy >= g.n) iy -= g.n;
-            const float rw = wts[wib][0][dx] * wts[wib][1][dy];
-            float *row = G + ((long long)ix * p.b[1] + iy) * p.bzp;
-            if (!zwrap) {
-                for (int t = a0; t <= a1; t += 4) {
+            if (iz >= g.n) iz -= g.n;
+            const float cw = wts[wib][0][dx] * wts[wib][2][dz];
+            float *col = G + ((long long)ix * nyb * bz + iz) * 32;
+            if (!ywrap) {
+                for (int a = iy0 & ~3; a <= iy0 + W - 1; a += 4) {
+                    const int e0 = a - iy0;
                     float4 val;
-                    const int e0 = t - iz0;
-                    val.x = (e0 >= 0 && e0 < W) ? rw * wts[wib][2][e0] : 0.f;
-                    val.y = (e0 + 1 >= 0 && e0 + 1 < W) ? rw * wts[wib][2][e0 + 1] : 0.f;
-                    val.z = (e0 + 2 >= 0 && e0 + 2 < W) ? rw * wts[wib][2][e0 + 2] : 0.f;
-                    val.w = (e0 + 3 >= 0 && e0 + 3 < W) ? rw * wts[wib][2][e0 + 3] : 0.f;
-                    atomicAdd(reinterpret_cast<float4 *>(row + t), val);
+                    val.x = (e0 >= 0 && e0 < W) ? cw * wts[wib][1][e0] : 0.f;
+                    val.y = (e0 + 1 >= 0 && e0 + 1 < W) ? cw * wts[wib][1][e0 + 1] : 0.f;
+                    val.z = (e0 + 2 >= 0 && e0 + 2 < W) ? cw * wts[wib][1][e0 + 2] : 0.f;
+                    val.w = (e0 + 3 >= 0 && e0 + 3 < W) ? cw * wts[wib][1][e0 + 3] : 0.f;
+                    atomicAdd(reinterpret_cast<float4 *>(col + (long long)(a >> 5) * bz * 32 + (a & 31)), val);
                 }
             } else {
-                for (int dz = 0; dz < W; dz++) {
-                    int iz = iz0 + dz;
-                    if (iz >= g.n) iz -= g.n;
-                    atomicAdd(row + iz, rw * wts[wib][2][dz]);
+                for (int dy = 0; dy < W; dy++) {
+                    int iy = iy0 + dy;
+                    if (iy >= g.n) iy -= g.n;
+                    atomicAdd(col + (long long)(iy >> 5) * bz * 32 + (iy & 31), cw * wts[wib][1][dy]);
                 }
             }
         }
@@ -381,25 +389,65 @@ __device__ __forceinline__ void load_twiddles(float2 *dst, const float2 *__restr
     for (int k = threadIdx.x; k < NF; k += blockDim.x) dst[k] = src[k];
 }
 
-// Zero an NF x 16 complex tile with 16-byte stores.
-template <int NF>
-__device__ __forceinline__ void zero_tile(float2 *t)
-{
-    float4 *t4 = reinterpret_cast<float4 *>(t);
-    for (int e = threadIdx.x; e < NF * 8; e += blockDim.x) t4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-}
-
 constexpr int TB = 256;  // threads per transform block
-constexpr int CL = 16;   // interleaved lines per tile
+constexpr int CL = 16;   // interleaved lines per tile (16 complex = 128 bytes per tile row)
+
+// Register-staged gather of one NF x 16 complex tile.  Tile row `pos` comes
+// from source row i = (pos - pos0) mod NF when i < b (8 float4 at
+// base + i * stride, in float4 units) and is zero otherwise, so every tile row
+// is written exactly once and no separate clearing pass is needed.  load()
+// only issues global loads (it can run while the previous tile is being
+// transformed); store() writes the registers to shared memory.
+template <int NF>
+struct TileGather {
+    static constexpr int PER = NF * 8 / TB; // float4 per thread
+    float4 v[PER];
+    __device__ __forceinline__ void load(const float4 *base, long long stride, int pos0, int b)
+    {
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int e = (int)threadIdx.x + u * TB;
+            const int pos = e >> 3, part = e & 7;
+            int i = pos - pos0;
+            if (i < 0) i += NF;
+            v[u] = i < b ? base[i * stride + part] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    // Same, and resets every source float4 it read to zero.
+    __device__ __forceinline__ void load_and_clear(float4 *base, long long stride, int pos0, int b)
+    {
+#pragma unroll
+        for (int u = 0; u < PER; u++) {
+            const int e = (int)threadIdx.x + u * TB;
+            const int pos = e >> 3, part = e & 7;
+            int i = pos - pos0;
+            if (i < 0) i += NF;
+            if (i < b) {
+                float4 *src = base + i * stride + part;
+                v[u] = *src;
+                *src = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+    __device__ __forceinline__ void store(float2 *tile) const
+    {
+        float4 *t4 = reinterpret_cast<float4 *>(tile);
+#pragma unroll
+        for (int u = 0; u < PER; u++) t4[threadIdx.x + u * TB] = v[u];
+    }
+};
+
 
 // ------------------------------------------------------------------ fft z
-// 32 real rows (iy0 .. iy0+31) of one (level, ix) plane per item, packed as 16
+// Item: 32 real rows (iy0 .. iy0+31) of one (level, ix) plane, packed as 16
 // complex lines (row 2q in the real part, row 2q+1 in the imaginary part of
-// line q).  Lane l of a warp owns row iy0 + l: it reads 16 bytes of its row
-// and writes them to tile floats [pos][l], so the shared-memory writes of a
-// warp are 32 consecutive floats.  Compact index iz lands at position
-// (pos0_z + iz) mod n; the rest of the line is zero.  Every cell read is reset
-// to zero, so the spreading boxes are clean for the next launch.
+// line q): in the block-transposed box layout each z position of the item is
+// one 128-byte tile row.  Compact index iz lands at position (pos0_z + iz) mod
+// n; the rest of the line is zero.  Every cell read is reset to zero, so the
+// spreading boxes are clean for the next launch.  The next item's rows are
+// loaded while the current one is transformed.
 // Output rows: with Z = FFT(a + i b), A_k = (Z_k + conj Z_{n-k}) / 2,
 // B_k = (Z_k - conj Z_{n-k}) / (2i), for m_z = k in [0, N/2).
 template <int NF>
@@ -412,69 +460,44 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     float2 *A = tw + NF, *B = A + NF * CL;
     load_twiddles<NF>(tw, tb.tw_n);
     const int H = g.H, L = g.L;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *Af = reinterpret_cast<float *>(A);
+    TileGather<NF> tg;
     RotStart rs;
     for (int i = 0; i < ninst; i++) {
         const InstPlan p = plan[i];
         if (p.b[0] == 0) continue;
-        const int b0 = p.b[0], b1 = p.b[1], bz = p.b[2], bzp = p.bzp;
+        const int b0 = p.b[0], b1 = p.b[1], bz = p.b[2];
         const int nyb = (b1 + 31) >> 5;
         const int items = L * b0 * nyb;
         const InstDesc d = inst[i];
-        for (int it = rs.first(); it < items; it += gridDim.x) {
+        float4 *G4 = reinterpret_cast<float4 *>(grid + d.grid_off);
+        // item (l, ix, iyb) -> float4 offset of its first tile row
+        auto src = [&](int it) { return G4 + (long long)it * bz * 8; };
+        int it = rs.first();
+        if (it < items) tg.load_and_clear(src(it), 8, p.pos0[2], bz);
+        for (; it < items; it += gridDim.x) {
             const int l = it / (b0 * nyb), rem = it - l * (b0 * nyb);
             const int ix = rem / nyb, iy0 = (rem - ix * nyb) << 5;
-            zero_tile<NF>(A);
+            tg.store(A);
             __syncthreads();
-            const int iy = iy0 + lane;
-            float *row = grid + d.grid_off + (long long)l * b0 * b1 * bzp + ((long long)ix * b1 + iy) * bzp;
-            if (iy < b1) {
-                // 4 floats per warp per step, warps interleaved along z
-                for (int z4 = w * 4; z4 < bzp; z4 += 4 * (TB / 32) * 4) {
-                    float4 v[4];
-#pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        const int zz = z4 + u * 4 * (TB / 32);
-                        v[u] = zz < bzp ? *reinterpret_cast<const float4 *>(row + zz) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        const int zz = z4 + u * 4 * (TB / 32);
-                        if (zz < bzp) {
-                            *reinterpret_cast<float4 *>(row + zz) = make_float4(0.f, 0.f, 0.f, 0.f);
-                            const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-                            for (int s = 0; s < 4; s++) {
-                                const int iz = zz + s;
-                                if (iz < bz) {
-                                    int pos = p.pos0[2] + iz;
-                                    if (pos >= NF) pos -= NF;
-                                    Af[pos * 32 + lane] = vv[s];
-                                }
-                            }
-                        }
-                    }
-                }
+            if (it + (int)gridDim.x < items) tg.load_and_clear(src(it + gridDim.x), 8, p.pos0[2], bz);
+            const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
+            // unpack into a staging area [row][k] (row stride H + 1), then write
+            // each 8H-byte row of z1 with consecutive threads on consecutive k
+            float2 *S = (res == A) ? B : A;
+            for (int e = threadIdx.x; e < 32 * H; e += TB) {
+                const int r = e & 31, kk = e >> 5;
+                const int qq = r >> 1;
+                const float2 zk = res[kk * CL + qq];
+                const float2 zn = res[(kk == 0 ? 0 : NF - kk) * CL + qq];
+                S[r * (H + 1) + kk] = (r & 1) ? make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x))
+                                              : make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
             }
             __syncthreads();
-            const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
-            // unpack: lane l -> row iy0 + l, pairs of modes (k, k + 1)
-            const int q = lane >> 1, odd = lane & 1;
-            if (iy < b1) {
-                float2 *Z = z1 + d.z1_off + (((long long)l * b0 + ix) * b1 + iy) * H;
-                for (int k = 2 * w; k < H; k += 2 * (TB / 32)) {
-                    float2 o[2];
-#pragma unroll
-                    for (int u = 0; u < 2; u++) {
-                        const int kk = k + u;
-                        const float2 zk = res[kk * CL + q];
-                        const float2 zn = res[(kk == 0 ? 0 : NF - kk) * CL + q];
-                        o[u] = odd ? make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x))
-                                   : make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-                    }
-                    *reinterpret_cast<float4 *>(Z + k) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-                }
+            float2 *Z = z1 + d.z1_off + (((long long)l * b0 + ix) * b1 + iy0) * H;
+            const int rows = min(32, b1 - iy0);
+            for (int e = threadIdx.x; e < rows * H; e += TB) {
+                const int r = e / H, kk = e - r * H;
+                Z[(long long)r * H + kk] = S[r * (H + 1) + kk];
             }
             __syncthreads();
         }
@@ -483,10 +506,11 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
 }
 
 // ------------------------------------------------------------------ fft y
-// Item: (level, ix) plane and a chunk of 16 z-modes.  Rows iy of the chunk
-// (16 complex = 128 bytes) land at tile position (pos0_y + iy) mod n; the
-// transform runs along y; m_y in (-N/2, N/2) is kept at FFT index j
-// (j = N/2, m_y = -N/2, stored as zero).
+// Item: (level, ix) plane and a chunk of 16 z-modes.  Row iy of the chunk (16
+// complex = 128 bytes) is tile row (pos0_y + iy) mod n; the transform runs
+// along y; m_y in (-N/2, N/2) is kept at FFT index j (j = N/2, m_y = -N/2,
+// stored as zero).  The next item is loaded while the current one is
+// transformed.
 template <int NF>
 __global__ void __launch_bounds__(TB)
 k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
@@ -499,6 +523,7 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     const int H = g.H, L = g.L, N = g.N;
     const int nch = H / CL;
     const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3; // 8 float4 per 128-byte row
+    TileGather<NF> tg;
     RotStart rs;
     for (int i = 0; i < ninst; i++) {
         const InstPlan p = plan[i];
@@ -506,32 +531,20 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
         const int b0 = p.b[0], b1 = p.b[1];
         const int items = L * b0 * nch;
         const InstDesc d = inst[i];
-        for (int it = rs.first(); it < items; it += gridDim.x) {
-            const int l = it / (b0 * nch), rem = it - l * (b0 * nch);
-            const int ix = rem / nch, ch = rem - ix * nch;
-            zero_tile<NF>(A);
+        // item (l, ix, ch) -> float4 offset of row 0 of its chunk
+        auto src = [&](int it) {
+            const int lx = it / nch, ch = it - lx * nch;
+            return reinterpret_cast<const float4 *>(z1 + d.z1_off + (long long)lx * b1 * H + ch * CL);
+        };
+        int it = rs.first();
+        if (it < items) tg.load(src(it), H / 2, p.pos0[1], b1);
+        for (; it < items; it += gridDim.x) {
+            const int lx = it / nch, ch = it - lx * nch;
+            tg.store(A);
             __syncthreads();
-            const float2 *Z = z1 + d.z1_off + ((long long)l * b0 + ix) * b1 * H + ch * CL + 2 * part;
-            for (int iyb = r8; iyb < b1; iyb += 4 * (TB / 8)) {
-                float4 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int iy = iyb + u * (TB / 8);
-                    v[u] = iy < b1 ? *reinterpret_cast<const float4 *>(Z + (long long)iy * H) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int iy = iyb + u * (TB / 8);
-                    if (iy < b1) {
-                        int pos = p.pos0[1] + iy;
-                        if (pos >= NF) pos -= NF;
-                        *reinterpret_cast<float4 *>(A + pos * CL + 2 * part) = v[u];
-                    }
-                }
-            }
-            __syncthreads();
+            if (it + (int)gridDim.x < items) tg.load(src(it + gridDim.x), H / 2, p.pos0[1], b1);
             const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
-            float2 *Y = y1 + d.y1_off + ((long long)l * b0 + ix) * N * H + ch * CL + 2 * part;
+            float2 *Y = y1 + d.y1_off + (long long)lx * N * H + ch * CL + 2 * part;
             for (int j = r8; j < N; j += TB / 8) {
                 const int m = mode_of(j, N);
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -546,8 +559,9 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
 
 // Level-summed spectrum of one instance for the modes (j_x = jx0 + 16 u, j_y,
 // m_z = 16 ch + c) owned by this thread: for each level, the y-transformed
-// rows over the support box are placed in a zero tile, transformed along x,
-// and the kept modes are weighted by T_l(|m|^2) D(m) and added.
+// rows over the support box fill a tile (zero outside it), the tile is
+// transformed along x, and the kept modes are weighted by T_l(|m|^2) D(m) and
+// added.  Level l + 1 is loaded while level l is transformed.
 template <int NF, int NI, int NU>
 __device__ __forceinline__ void spectrum_x(float2 (&F)[NU], const Geometry &g, const Tables &tb,
                                            const InstDesc *__restrict__ inst, const InstPlan *__restrict__ plan,
@@ -557,7 +571,6 @@ __device__ __forceinline__ void spectrum_x(float2 (&F)[NU], const Geometry &g, c
     const int H = g.H, L = g.L, N = NI;
     const int Q = tb.qmax + 1;
     const int c = threadIdx.x & (CL - 1), jx0 = threadIdx.x / CL;
-    const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3;
     const int my = mode_of(jy, N), mz = ch * CL + c;
     const float dyz = tb.deconv[jy] * tb.deconv[mz];
 #pragma unroll
@@ -566,29 +579,16 @@ __device__ __forceinline__ void spectrum_x(float2 (&F)[NU], const Geometry &g, c
     if (p.b[0] == 0) return;
     const InstDesc d = inst[si];
     const int b0 = p.b[0];
+    const long long stride = (long long)N * H / 2; // float4 between consecutive ix rows
+    auto src = [&](int l) {
+        return reinterpret_cast<const float4 *>(y1 + d.y1_off + (long long)l * b0 * N * H + (long long)jy * H + ch * CL);
+    };
+    TileGather<NF> tg;
+    tg.load(src(0), stride, p.pos0[0], b0);
     for (int l = 0; l < L; l++) {
-        zero_tile<NF>(A);
+        tg.store(A);
         __syncthreads();
-        const float2 *Y = y1 + d.y1_off + (long long)l * b0 * N * H + (long long)jy * H + ch * CL + 2 * part;
-        for (int ixb = r8; ixb < b0; ixb += 4 * (TB / 8)) {
-            float4 v[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int ix = ixb + u * (TB / 8);
-                v[u] = ix < b0 ? *reinterpret_cast<const float4 *>(Y + (long long)ix * N * H)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int ix = ixb + u * (TB / 8);
-                if (ix < b0) {
-                    int pos = p.pos0[0] + ix;
-                    if (pos >= NF) pos -= NF;
-                    *reinterpret_cast<float4 *>(A + pos * CL + 2 * part) = v[u];
-                }
-            }
-        }
-        __syncthreads();
+        if (l + 1 < L) tg.load(src(l + 1), stride, p.pos0[0], b0);
         const float2 *res = il_fft<NF, false, CL, TB>(A, B, twF);
         const float *T = tb.ballft + (long long)l * Q;
 #pragma unroll
@@ -677,6 +677,7 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
 }
 
 // ------------------------------------------------------------------ inverse y
+// Item: (k_x, chunk of 16 z-modes); in place on the half-spectrum planes.
 template <int NI>
 __global__ void __launch_bounds__(TB)
 k_ifft_y(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, float2 *h)
@@ -689,28 +690,24 @@ k_ifft_y(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
     const int nch = H / CL;
     const int items = N * nch;
     const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3;
+    TileGather<NI> tg;
     RotStart rs;
     for (int pi = 0; pi < npairs; pi++) {
         const PairDesc pr = pairs[pi];
         if (pr.b < 0) continue;
-        for (int it = rs.first(); it < items; it += gridDim.x) {
+        auto src = [&](int it) {
             const int kx = it / nch, ch = it - kx * nch;
-            float2 *Hp = h + pr.h_off + (long long)kx * N * H + ch * CL + 2 * part;
-            for (int jyb = r8; jyb < N; jyb += 4 * (TB / 8)) {
-                float4 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int jy = jyb + u * (TB / 8);
-                    v[u] = jy < N ? *reinterpret_cast<const float4 *>(Hp + (long long)jy * H) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const int jy = jyb + u * (TB / 8);
-                    if (jy < N) *reinterpret_cast<float4 *>(A + jy * CL + 2 * part) = v[u];
-                }
-            }
+            return reinterpret_cast<const float4 *>(h + pr.h_off + (long long)kx * N * H + ch * CL);
+        };
+        int it = rs.first();
+        if (it < items) tg.load(src(it), H / 2, 0, N);
+        for (; it < items; it += gridDim.x) {
+            const int kx = it / nch, ch = it - kx * nch;
+            tg.store(A);
             __syncthreads();
+            if (it + (int)gridDim.x < items) tg.load(src(it + gridDim.x), H / 2, 0, N);
             const float2 *res = il_fft<NI, true, CL, TB>(A, B, tw);
+            float2 *Hp = h + pr.h_off + (long long)kx * N * H + ch * CL + 2 * part;
             for (int ky = r8; ky < N; ky += TB / 8)
                 *reinterpret_cast<float4 *>(Hp + (long long)ky * H) = *reinterpret_cast<const float4 *>(res + ky * CL + 2 * part);
             __syncthreads();
@@ -765,15 +762,19 @@ k_ifft_z(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
             }
             __syncthreads();
             const float2 *res = il_fft<NI, true, CL, TB>(A, B, tw);
-            float *o = out + pr.out_off + ((long long)kx * N + ky0 + lane) * N;
-            for (int kz = 4 * w; kz < N; kz += 4 * (TB / 32)) {
-                float r[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) {
-                    const float2 v = res[(kz + u) * CL + q];
-                    r[u] = odd ? v.y : v.x;
-                }
-                *reinterpret_cast<float4 *>(o + kz) = make_float4(r[0], r[1], r[2], r[3]);
+            // rows through a staging area [row][kz ^ row] (XOR swizzle: conflict-free
+            // in both phases), then each 4N-byte output row written coalesced
+            float *S = reinterpret_cast<float *>((res == A) ? B : A);
+            for (int e = threadIdx.x; e < 32 * N; e += TB) {
+                const int r = e & 31, kz = e >> 5;
+                const float2 v = res[kz * CL + (r >> 1)];
+                S[r * N + (kz ^ r)] = (r & 1) ? v.y : v.x;
+            }
+            __syncthreads();
+            float *o = out + pr.out_off + ((long long)kx * N + ky0) * N;
+            for (int e = threadIdx.x; e < 32 * N; e += TB) {
+                const int r = e / N, kz = e - r * N;
+                o[(long long)r * N + kz] = S[r * N + (kz ^ r)];
             }
             __syncthreads();
         }
