@@ -413,8 +413,9 @@ struct TileGather {
             v[u] = i < b ? base[i * stride + part] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    // Same, and resets every source float4 it read to zero.
-    __device__ __forceinline__ void load_and_clear(float4 *base, long long stride, int pos0, int b)
+    // Resets to zero every source float4 that load() with the same arguments
+    // reads (stores only; call it once those loads have completed).
+    __device__ __forceinline__ void clear(float4 *base, long long stride, int pos0, int b) const
     {
 #pragma unroll
         for (int u = 0; u < PER; u++) {
@@ -422,13 +423,7 @@ struct TileGather {
             const int pos = e >> 3, part = e & 7;
             int i = pos - pos0;
             if (i < 0) i += NF;
-            if (i < b) {
-                float4 *src = base + i * stride + part;
-                v[u] = *src;
-                *src = make_float4(0.f, 0.f, 0.f, 0.f);
-            } else {
-                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            if (i < b) base[i * stride + part] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
     __device__ __forceinline__ void store(float2 *tile) const
@@ -473,13 +468,14 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
         // item (l, ix, iyb) -> float4 offset of its first tile row
         auto src = [&](int it) { return G4 + (long long)it * bz * 8; };
         int it = rs.first();
-        if (it < items) tg.load_and_clear(src(it), 8, p.pos0[2], bz);
+        if (it < items) tg.load(src(it), 8, p.pos0[2], bz);
         for (; it < items; it += gridDim.x) {
             const int l = it / (b0 * nyb), rem = it - l * (b0 * nyb);
             const int ix = rem / nyb, iy0 = (rem - ix * nyb) << 5;
             tg.store(A);
+            tg.clear(src(it), 8, p.pos0[2], bz);
             __syncthreads();
-            if (it + (int)gridDim.x < items) tg.load_and_clear(src(it + gridDim.x), 8, p.pos0[2], bz);
+            if (it + (int)gridDim.x < items) tg.load(src(it + gridDim.x), 8, p.pos0[2], bz);
             const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
             // unpack into a staging area [row][k] (row stride H + 1), then write
             // each 8H-byte row of z1 with consecutive threads on consecutive k
@@ -614,7 +610,7 @@ __device__ __forceinline__ void spectrum_x(float2 (&F)[NU], const Geometry &g, c
 // registers.  With pair.a < 0, F_A comes from the cached spectrum; with
 // pair.b < 0, F_A is written to `fa_out` and nothing else happens.
 template <int NF, int NI>
-__global__ void __launch_bounds__(TB)
+__global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan *__restrict__ plan,
         const PairDesc *__restrict__ pairs, int npairs, const float2 *__restrict__ y1,
         const float2 *__restrict__ fa_cache, float2 *fa_out, float2 *h)
