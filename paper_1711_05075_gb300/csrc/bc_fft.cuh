@@ -193,4 +193,119 @@ __device__ __forceinline__ float2 *il_fft(float2 *a, float2 *b, const float2 *tw
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident first and last stages.  A transform of C interleaved lines
+// runs as: first stage (inputs held in registers, loaded straight from global
+// memory by the caller) -> shared tile -> middle stage (only for three-stage
+// schedules, shared -> shared) -> last stage (shared -> registers -> a sink
+// functor).  Shared memory then carries each value once per exchange instead
+// of once per stage plus a gather and a scatter.
+
+// Inputs of the first stage owned by the calling thread: butterfly (c, j) of
+// iteration `it` needs positions j + r NF/R, r < R.
+template <int NF, int R, int C, int NT>
+struct FirstInputs {
+    static constexpr int NB = NF / R, TOT = NB * C, IT = (TOT + NT - 1) / NT;
+    float2 v[IT][R];
+    // src(c, pos) -> float2: value of line c at position pos (issue the loads only).
+    template <class Src>
+    __device__ __forceinline__ void load(Src src)
+    {
+#pragma unroll
+        for (int it = 0; it < IT; it++) {
+            const int idx = (int)threadIdx.x + it * NT;
+            const int c = idx % C, j = idx / C;
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                v[it][r] = ((TOT % NT) == 0 || idx < TOT) ? src(c, j + r * NB) : make_float2(0.f, 0.f);
+        }
+    }
+    // visit(c, pos) for every position load() read.
+    template <class Vis>
+    __device__ __forceinline__ void for_each(Vis visit) const
+    {
+#pragma unroll
+        for (int it = 0; it < IT; it++) {
+            const int idx = (int)threadIdx.x + it * NT;
+            if ((TOT % NT) != 0 && idx >= TOT) break;
+            const int c = idx % C, j = idx / C;
+#pragma unroll
+            for (int r = 0; r < R; r++) visit(c, j + r * NB);
+        }
+    }
+};
+
+// First stage (Ns = 1, no twiddles): registers -> out[pos * C + c].
+template <int NF, int R, bool INV, int C, int NT>
+__device__ __forceinline__ void rr_first(const FirstInputs<NF, R, C, NT> &in, float2 *__restrict__ out)
+{
+    using FI = FirstInputs<NF, R, C, NT>;
+#pragma unroll
+    for (int it = 0; it < FI::IT; it++) {
+        const int idx = (int)threadIdx.x + it * NT;
+        if ((FI::TOT % NT) != 0 && idx >= FI::TOT) break;
+        const int c = idx % C, j = idx / C;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = in.v[it][r];
+        dft_small<R, INV>(v);
+#pragma unroll
+        for (int r = 0; r < R; r++) out[(j * R + r) * C + c] = v[r];
+    }
+}
+
+// Last stage: in[pos * C + c] -> registers -> sink(it, r, c, pos, value), where
+// the output position is pos = j + r NS for butterfly j (< NS) of iteration it.
+template <int NF, int R, int NS, bool INV, int C, int NT, class Sink>
+__device__ __forceinline__ void rr_last(const float2 *__restrict__ in, const float2 *__restrict__ tw, Sink sink)
+{
+    constexpr int NB = NF / R;
+    static_assert(NB == NS, "last stage");
+    constexpr int TOT = NB * C;
+    constexpr int IT = (TOT + NT - 1) / NT;
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int idx = (int)threadIdx.x + it * NT;
+        if ((TOT % NT) != 0 && idx >= TOT) break;
+        const int c = idx % C, j = idx / C;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            float2 x = in[(j + r * NB) * C + c];
+            if (r > 0) {
+                float2 w = tw[r * j * (NF / (NS * R))];
+                if (INV) w.y = -w.y;
+                x = cmul(x, w);
+            }
+            v[r] = x;
+        }
+        dft_small<R, INV>(v);
+#pragma unroll
+        for (int r = 0; r < R; r++) sink(it, r, c, j + r * NS, v[r]);
+    }
+}
+
+// Radix of the last stage of a schedule and its output stride.
+template <int NF>
+struct LastStage {
+    static constexpr int R = Radix<NF>::r2 > 1 ? Radix<NF>::r2 : Radix<NF>::r1;
+    static constexpr int NS = NF / R;
+};
+
+// The middle (three-stage schedules) and last stages after rr_first has
+// written tile s0; s1 is scratch for three-stage schedules.  All threads call
+// it; the caller adds a barrier before s0/s1 are written again.
+template <int NF, bool INV, int C, int NT, class Sink>
+__device__ __forceinline__ void rr_rest(float2 *s0, float2 *s1, const float2 *tw, Sink sink)
+{
+    using R = Radix<NF>;
+    if constexpr (R::r2 > 1) {
+        il_stage<NF, R::r1, R::r0, INV, C, NT>(s0, s1, tw);
+        __syncthreads();
+        rr_last<NF, R::r2, R::r0 * R::r1, INV, C, NT>(s1, tw, sink);
+    } else {
+        rr_last<NF, R::r1, R::r0, INV, C, NT>(s0, tw, sink);
+    }
+}
+
 } // namespace bc

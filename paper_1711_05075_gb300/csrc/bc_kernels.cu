@@ -392,108 +392,82 @@ __device__ __forceinline__ void load_twiddles(float2 *dst, const float2 *__restr
 constexpr int TB = 256;  // threads per transform block
 constexpr int CL = 16;   // interleaved lines per tile (16 complex = 128 bytes per tile row)
 
-// Register-staged gather of one NF x 16 complex tile.  Tile row `pos` comes
-// from source row i = (pos - pos0) mod NF when i < b (8 float4 at
-// base + i * stride, in float4 units) and is zero otherwise, so every tile row
-// is written exactly once and no separate clearing pass is needed.  load()
-// only issues global loads (it can run while the previous tile is being
-// transformed); store() writes the registers to shared memory.
-template <int NF>
-struct TileGather {
-    static constexpr int PER = NF * 8 / TB; // float4 per thread
-    float4 v[PER];
-    __device__ __forceinline__ void load(const float4 *base, long long stride, int pos0, int b)
-    {
-#pragma unroll
-        for (int u = 0; u < PER; u++) {
-            const int e = (int)threadIdx.x + u * TB;
-            const int pos = e >> 3, part = e & 7;
-            int i = pos - pos0;
-            if (i < 0) i += NF;
-            v[u] = i < b ? base[i * stride + part] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
-    // Resets to zero every source float4 that load() with the same arguments
-    // reads (stores only; call it once those loads have completed).
-    __device__ __forceinline__ void clear(float4 *base, long long stride, int pos0, int b) const
-    {
-#pragma unroll
-        for (int u = 0; u < PER; u++) {
-            const int e = (int)threadIdx.x + u * TB;
-            const int pos = e >> 3, part = e & 7;
-            int i = pos - pos0;
-            if (i < 0) i += NF;
-            if (i < b) base[i * stride + part] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    }
-    __device__ __forceinline__ void store(float2 *tile) const
-    {
-        float4 *t4 = reinterpret_cast<float4 *>(tile);
-#pragma unroll
-        for (int u = 0; u < PER; u++) t4[threadIdx.x + u * TB] = v[u];
-    }
-};
-
-
 // ------------------------------------------------------------------ fft z
 // Item: 32 real rows (iy0 .. iy0+31) of one (level, ix) plane, packed as 16
 // complex lines (row 2q in the real part, row 2q+1 in the imaginary part of
-// line q): in the block-transposed box layout each z position of the item is
-// one 128-byte tile row.  Compact index iz lands at position (pos0_z + iz) mod
-// n; the rest of the line is zero.  Every cell read is reset to zero, so the
-// spreading boxes are clean for the next launch.  The next item's rows are
-// loaded while the current one is transformed.
+// line q): in the block-transposed box layout, line q at z position iz is one
+// float2 of a contiguous 128-byte run.  Compact index iz sits at position
+// (pos0_z + iz) mod n of the length-n line; the rest of the line is zero.  The
+// first transform stage reads its inputs straight from the box (and the next
+// item's inputs are loaded while the current one finishes); every cell read is
+// then reset to zero so the boxes are clean for the next launch.
 // Output rows: with Z = FFT(a + i b), A_k = (Z_k + conj Z_{n-k}) / 2,
 // B_k = (Z_k - conj Z_{n-k}) / (2i), for m_z = k in [0, N/2).
 template <int NF>
-__global__ void __launch_bounds__(TB)
+__global__ void __launch_bounds__(TB, 2)
 k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
         float *grid, float2 *z1)
 {
+    constexpr bool three = Radix<NF>::r2 > 1;
     extern __shared__ float4 sm4[];
     float2 *tw = reinterpret_cast<float2 *>(sm4);
-    float2 *A = tw + NF, *B = A + NF * CL;
+    float2 *S0 = tw + NF, *S1 = S0 + NF * CL;
+    float2 *OUT = three ? S0 : S1; // tile the last stage writes (not the one it reads)
+    float2 *STG = three ? S1 : S0; // staging for the output rows
     load_twiddles<NF>(tw, tb.tw_n);
     const int H = g.H, L = g.L;
-    TileGather<NF> tg;
+    FirstInputs<NF, Radix<NF>::r0, CL, TB> in;
     RotStart rs;
     for (int i = 0; i < ninst; i++) {
         const InstPlan p = plan[i];
         if (p.b[0] == 0) continue;
-        const int b0 = p.b[0], b1 = p.b[1], bz = p.b[2];
+        const int b0 = p.b[0], b1 = p.b[1], bz = p.b[2], pz = p.pos0[2];
         const int nyb = (b1 + 31) >> 5;
         const int items = L * b0 * nyb;
         const InstDesc d = inst[i];
-        float4 *G4 = reinterpret_cast<float4 *>(grid + d.grid_off);
-        // item (l, ix, iyb) -> float4 offset of its first tile row
-        auto src = [&](int it) { return G4 + (long long)it * bz * 8; };
+        float2 *G2 = reinterpret_cast<float2 *>(grid + d.grid_off);
+        auto src = [&](int it) {
+            float2 *base = G2 + (long long)it * bz * 16;
+            return [=](int c, int pos) {
+                int iz = pos - pz;
+                if (iz < 0) iz += NF;
+                return iz < bz ? base[iz * 16 + c] : make_float2(0.f, 0.f);
+            };
+        };
         int it = rs.first();
-        if (it < items) tg.load(src(it), 8, p.pos0[2], bz);
+        if (it < items) in.load(src(it));
         for (; it < items; it += gridDim.x) {
             const int l = it / (b0 * nyb), rem = it - l * (b0 * nyb);
             const int ix = rem / nyb, iy0 = (rem - ix * nyb) << 5;
-            tg.store(A);
-            tg.clear(src(it), 8, p.pos0[2], bz);
+            rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
+            {
+                float2 *base = G2 + (long long)it * bz * 16;
+                in.for_each([&](int c, int pos) {
+                    int iz = pos - pz;
+                    if (iz < 0) iz += NF;
+                    if (iz < bz) base[iz * 16 + c] = make_float2(0.f, 0.f);
+                });
+            }
             __syncthreads();
-            if (it + (int)gridDim.x < items) tg.load(src(it + gridDim.x), 8, p.pos0[2], bz);
-            const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
+            if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
+            rr_rest<NF, false, CL, TB>(S0, S1, tw, [&](int, int, int c, int pos, float2 v) { OUT[pos * CL + c] = v; });
+            __syncthreads();
             // unpack into a staging area [row][k] (row stride H + 1), then write
             // each 8H-byte row of z1 with consecutive threads on consecutive k
-            float2 *S = (res == A) ? B : A;
             for (int e = threadIdx.x; e < 32 * H; e += TB) {
                 const int r = e & 31, kk = e >> 5;
                 const int qq = r >> 1;
-                const float2 zk = res[kk * CL + qq];
-                const float2 zn = res[(kk == 0 ? 0 : NF - kk) * CL + qq];
-                S[r * (H + 1) + kk] = (r & 1) ? make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x))
-                                              : make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+                const float2 zk = OUT[kk * CL + qq];
+                const float2 zn = OUT[(kk == 0 ? 0 : NF - kk) * CL + qq];
+                STG[r * (H + 1) + kk] = (r & 1) ? make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x))
+                                                : make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
             }
             __syncthreads();
             float2 *Z = z1 + d.z1_off + (((long long)l * b0 + ix) * b1 + iy0) * H;
             const int rows = min(32, b1 - iy0);
             for (int e = threadIdx.x; e < rows * H; e += TB) {
                 const int r = e / H, kk = e - r * H;
-                Z[(long long)r * H + kk] = S[r * (H + 1) + kk];
+                Z[(long long)r * H + kk] = STG[r * (H + 1) + kk];
             }
             __syncthreads();
         }
@@ -503,99 +477,136 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
 
 // ------------------------------------------------------------------ fft y
 // Item: (level, ix) plane and a chunk of 16 z-modes.  Row iy of the chunk (16
-// complex = 128 bytes) is tile row (pos0_y + iy) mod n; the transform runs
-// along y; m_y in (-N/2, N/2) is kept at FFT index j (j = N/2, m_y = -N/2,
-// stored as zero).  The next item is loaded while the current one is
-// transformed.
+// complex = 128 bytes) is position (pos0_y + iy) mod n of the lines; the
+// transform runs along y; m_y in (-N/2, N/2) is kept at FFT index j (j = N/2,
+// m_y = -N/2, stored as zero).  First-stage inputs come straight from z1 and
+// last-stage outputs go straight to y1; the next item is loaded while the
+// current one finishes.
 template <int NF>
-__global__ void __launch_bounds__(TB)
+__global__ void __launch_bounds__(TB, 2)
 k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
         const float2 *__restrict__ z1, float2 *y1)
 {
     extern __shared__ float4 sm4[];
     float2 *tw = reinterpret_cast<float2 *>(sm4);
-    float2 *A = tw + NF, *B = A + NF * CL;
+    float2 *S0 = tw + NF, *S1 = S0 + NF * CL;
     load_twiddles<NF>(tw, tb.tw_n);
     const int H = g.H, L = g.L, N = g.N;
     const int nch = H / CL;
-    const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3; // 8 float4 per 128-byte row
-    TileGather<NF> tg;
+    FirstInputs<NF, Radix<NF>::r0, CL, TB> in;
     RotStart rs;
     for (int i = 0; i < ninst; i++) {
         const InstPlan p = plan[i];
         if (p.b[0] == 0) continue;
-        const int b0 = p.b[0], b1 = p.b[1];
+        const int b0 = p.b[0], b1 = p.b[1], py = p.pos0[1];
         const int items = L * b0 * nch;
         const InstDesc d = inst[i];
-        // item (l, ix, ch) -> float4 offset of row 0 of its chunk
         auto src = [&](int it) {
             const int lx = it / nch, ch = it - lx * nch;
-            return reinterpret_cast<const float4 *>(z1 + d.z1_off + (long long)lx * b1 * H + ch * CL);
+            const float2 *base = z1 + d.z1_off + (long long)lx * b1 * H + ch * CL;
+            return [=](int c, int pos) {
+                int iy = pos - py;
+                if (iy < 0) iy += NF;
+                return iy < b1 ? base[(long long)iy * H + c] : make_float2(0.f, 0.f);
+            };
         };
         int it = rs.first();
-        if (it < items) tg.load(src(it), H / 2, p.pos0[1], b1);
+        if (it < items) in.load(src(it));
         for (; it < items; it += gridDim.x) {
             const int lx = it / nch, ch = it - lx * nch;
-            tg.store(A);
+            rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
             __syncthreads();
-            if (it + (int)gridDim.x < items) tg.load(src(it + gridDim.x), H / 2, p.pos0[1], b1);
-            const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
-            float2 *Y = y1 + d.y1_off + (long long)lx * N * H + ch * CL + 2 * part;
-            for (int j = r8; j < N; j += TB / 8) {
-                const int m = mode_of(j, N);
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j != N / 2) v = *reinterpret_cast<const float4 *>(res + (m < 0 ? m + NF : m) * CL + 2 * part);
-                *reinterpret_cast<float4 *>(Y + (long long)j * H) = v;
-            }
+            if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
+            float2 *Y = y1 + d.y1_off + (long long)lx * N * H + ch * CL;
+            rr_rest<NF, false, CL, TB>(S0, S1, tw, [&](int, int, int c, int pos, float2 v) {
+                int jy;
+                if (pos < N / 2) jy = pos;
+                else if (pos >= NF - N / 2) jy = pos - NF + N;
+                else return;
+                Y[(long long)jy * H + c] = jy == N / 2 ? make_float2(0.f, 0.f) : v;
+            });
             __syncthreads();
         }
         rs.rot += items;
     }
 }
 
-// Level-summed spectrum of one instance for the modes (j_x = jx0 + 16 u, j_y,
-// m_z = 16 ch + c) owned by this thread: for each level, the y-transformed
-// rows over the support box fill a tile (zero outside it), the tile is
-// transformed along x, and the kept modes are weighted by T_l(|m|^2) D(m) and
-// added.  Level l + 1 is loaded while level l is transformed.
-template <int NF, int NI, int NU>
-__device__ __forceinline__ void spectrum_x(float2 (&F)[NU], const Geometry &g, const Tables &tb,
-                                           const InstDesc *__restrict__ inst, const InstPlan *__restrict__ plan,
-                                           int si, const float2 *__restrict__ y1, int jy, int ch,
-                                           const float2 *twF, float2 *A, float2 *B)
+// Level-summed spectrum of one instance for the modes owned by this thread
+// after the last stage of the x transform: output position pos = j + r NS of
+// butterfly (c, j) is kept when r < R/4 (m_x = pos) or r >= 3R/4
+// (m_x = pos - n), i.e. exactly m_x in [-N/2, N/2); those slots of F hold
+// sum_l T_l(|m|^2) D(m) FFT_x[Y_l](m) for m_y = mode(j_y), m_z = 16 ch + c.
+// Level l + 1 is loaded while level l is transformed.
+template <int NF>
+struct XModes {
+    static constexpr int R = LastStage<NF>::R, NS = LastStage<NF>::NS;
+    static constexpr int IT = (NS * CL + TB - 1) / TB;
+    static __device__ __forceinline__ constexpr bool kept(int r) { return r < R / 4 || r >= 3 * R / 4; }
+};
+
+template <int NF, int NI>
+__device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF>::IT][XModes<NF>::R], const Geometry &g,
+                                           const Tables &tb, const InstDesc *__restrict__ inst,
+                                           const InstPlan *__restrict__ plan, int si, const float2 *__restrict__ y1,
+                                           int jy, int ch, const float2 *tw, float2 *S0, float2 *S1)
 {
+    using XM = XModes<NF>;
     const int H = g.H, L = g.L, N = NI;
     const int Q = tb.qmax + 1;
-    const int c = threadIdx.x & (CL - 1), jx0 = threadIdx.x / CL;
-    const int my = mode_of(jy, N), mz = ch * CL + c;
-    const float dyz = tb.deconv[jy] * tb.deconv[mz];
+    const int my = mode_of(jy, N);
+    const float djy = tb.deconv[jy];
 #pragma unroll
-    for (int u = 0; u < NU; u++) F[u] = make_float2(0.f, 0.f);
+    for (int it = 0; it < XM::IT; it++)
+#pragma unroll
+        for (int r = 0; r < XM::R; r++) F[it][r] = make_float2(0.f, 0.f);
     const InstPlan p = plan[si];
     if (p.b[0] == 0) return;
     const InstDesc d = inst[si];
-    const int b0 = p.b[0];
-    const long long stride = (long long)N * H / 2; // float4 between consecutive ix rows
+    const int b0 = p.b[0], px = p.pos0[0];
     auto src = [&](int l) {
-        return reinterpret_cast<const float4 *>(y1 + d.y1_off + (long long)l * b0 * N * H + (long long)jy * H + ch * CL);
+        const float2 *base = y1 + d.y1_off + (long long)l * b0 * N * H + (long long)jy * H + ch * CL;
+        return [=](int c, int pos) {
+            int ix = pos - px;
+            if (ix < 0) ix += NF;
+            return ix < b0 ? base[(long long)ix * N * H + c] : make_float2(0.f, 0.f);
+        };
     };
-    TileGather<NF> tg;
-    tg.load(src(0), stride, p.pos0[0], b0);
+    FirstInputs<NF, Radix<NF>::r0, CL, TB> in;
+    in.load(src(0));
     for (int l = 0; l < L; l++) {
-        tg.store(A);
+        rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
         __syncthreads();
-        if (l + 1 < L) tg.load(src(l + 1), stride, p.pos0[0], b0);
-        const float2 *res = il_fft<NF, false, CL, TB>(A, B, twF);
+        if (l + 1 < L) in.load(src(l + 1));
         const float *T = tb.ballft + (long long)l * Q;
-#pragma unroll
-        for (int u = 0; u < NU; u++) {
-            const int jx = jx0 + u * (TB / CL);
-            const int mx = mode_of(jx, N);
-            const float Mv = T[mx * mx + my * my + mz * mz] * tb.deconv[jx] * dyz;
-            const float2 v = res[(mx < 0 ? mx + NF : mx) * CL + c];
-            F[u] = make_float2(fmaf(Mv, v.x, F[u].x), fmaf(Mv, v.y, F[u].y));
-        }
+        rr_rest<NF, false, CL, TB>(S0, S1, tw, [&](int it, int r, int c, int pos, float2 v) {
+            if (!XM::kept(r)) return;
+            const int mx = r < XM::R / 4 ? pos : pos - NF;
+            const int jx = mx < 0 ? mx + N : mx;
+            const int mz = ch * CL + c;
+            const float Mv = T[mx * mx + my * my + mz * mz] * tb.deconv[jx] * djy * tb.deconv[mz];
+            F[it][r] = make_float2(fmaf(Mv, v.x, F[it][r].x), fmaf(Mv, v.y, F[it][r].y));
+        });
         __syncthreads();
+    }
+}
+
+// Calls f(it, r, c, jx) for every kept mode slot of the calling thread.
+template <int NF, int NI, class Fn>
+__device__ __forceinline__ void for_kept(Fn f)
+{
+    using XM = XModes<NF>;
+#pragma unroll
+    for (int it = 0; it < XM::IT; it++) {
+        const int idx = (int)threadIdx.x + it * TB;
+        if ((XM::NS * CL) % TB != 0 && idx >= XM::NS * CL) break;
+        const int c = idx % CL, j = idx / CL;
+#pragma unroll
+        for (int r = 0; r < XM::R; r++) {
+            if (!XM::kept(r)) continue;
+            const int pos = j + r * XM::NS;
+            const int mx = r < XM::R / 4 ? pos : pos - NF;
+            f(it, r, c, mx < 0 ? mx + NI : mx);
+        }
     }
 }
 
@@ -606,63 +617,62 @@ __device__ __forceinline__ void spectrum_x(float2 (&F)[NU], const Geometry &g, c
 //   H(k_x, j_y, m_z) = sum_{j_x} g'(m) exp(+2 pi i j_x k_x / N)
 // D(m) = deconv[j_x] deconv[j_y] deconv[m_z].  The sign moves the origin of the
 // translation grid to t = -P/2: exp(2 pi i m (-P/2) / P) = (-1)^m.
-// Thread t accumulates the modes (j_x = t/16 + 16 u, column t mod 16) in
-// registers.  With pair.a < 0, F_A comes from the cached spectrum; with
-// pair.b < 0, F_A is written to `fa_out` and nothing else happens.
+// With pair.a < 0, F_A comes from the cached spectrum; with pair.b < 0, F_A is
+// written to `fa_out` and nothing else happens.
 template <int NF, int NI>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan *__restrict__ plan,
         const PairDesc *__restrict__ pairs, int npairs, const float2 *__restrict__ y1,
         const float2 *__restrict__ fa_cache, float2 *fa_out, float2 *h)
 {
-    constexpr int NU = NI / (TB / CL); // accumulated modes per thread
+    using XM = XModes<NF>;
     extern __shared__ float4 sm4[];
     float2 *twF = reinterpret_cast<float2 *>(sm4);
-    float2 *twI = twF + NF, *A = twI + NI, *B = A + NF * CL;
+    float2 *twI = twF + NF, *S0 = twI + NI, *S1 = S0 + NF * CL, *FAt = S1 + NF * CL;
     load_twiddles<NF>(twF, tb.tw_n);
     load_twiddles<NI>(twI, tb.tw_N);
     const int H = g.H, N = NI;
     const int nch = H / CL;
     const int items = N * nch;
-    const int c = threadIdx.x & (CL - 1), jx0 = threadIdx.x / CL;
     const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3;
     RotStart rs;
     for (int pi = 0; pi < npairs; pi++) {
         const PairDesc pr = pairs[pi];
         for (int it = rs.first(); it < items; it += gridDim.x) {
             const int jy = it / nch, ch = it - jy * nch;
-            const int my = mode_of(jy, N), mz = ch * CL + c;
-            float2 FA[NU], FB[NU];
-            if (pr.a < 0) {
-#pragma unroll
-                for (int u = 0; u < NU; u++)
-                    FA[u] = fa_cache[((long long)(jx0 + u * (TB / CL)) * N + jy) * H + mz];
-            } else {
-                spectrum_x<NF, NI, NU>(FA, g, tb, inst, plan, pr.a, y1, jy, ch, twF, A, B);
-            }
-            if (pr.b >= 0) spectrum_x<NF, NI, NU>(FB, g, tb, inst, plan, pr.b, y1, jy, ch, twF, A, B);
-            if (pr.b < 0) {
-#pragma unroll
-                for (int u = 0; u < NU; u++) {
-                    const int jx = jx0 + u * (TB / CL);
-                    fa_out[((long long)jx * N + jy) * H + mz] = FA[u];
+            const int my = mode_of(jy, N);
+            // F_A waits in its own tile (each thread reads back only what it wrote)
+            // while F_B is accumulated in registers.
+            {
+                float2 FA[XM::IT][XM::R];
+                if (pr.a < 0) {
+                    for_kept<NF, NI>([&](int i2, int r, int c, int jx) {
+                        FAt[jx * CL + c] = fa_cache[((long long)jx * N + jy) * H + ch * CL + c];
+                    });
+                } else {
+                    spectrum_x<NF, NI>(FA, g, tb, inst, plan, pr.a, y1, jy, ch, twF, S0, S1);
+                    for_kept<NF, NI>([&](int i2, int r, int c, int jx) { FAt[jx * CL + c] = FA[i2][r]; });
                 }
+            }
+            if (pr.b < 0) {
+                for_kept<NF, NI>([&](int i2, int r, int c, int jx) {
+                    fa_out[((long long)jx * N + jy) * H + ch * CL + c] = FAt[jx * CL + c];
+                });
                 continue;
             }
-#pragma unroll
-            for (int u = 0; u < NU; u++) {
-                const int jx = jx0 + u * (TB / CL);
-                const int mx = mode_of(jx, N);
+            float2 FB[XM::IT][XM::R];
+            spectrum_x<NF, NI>(FB, g, tb, inst, plan, pr.b, y1, jy, ch, twF, S0, S1);
+            for_kept<NF, NI>([&](int i2, int r, int c, int jx) {
+                const int mx = mode_of(jx, N), mz = ch * CL + c;
                 float2 v = make_float2(0.f, 0.f);
                 if (jx != N / 2 && jy != N / 2) {
-                    v = cmulc(FA[u], FB[u]);
-                    const float sg = ((mx + my + mz) & 1) ? -g.inv_P3 : g.inv_P3;
-                    v = cscale(v, sg);
+                    v = cmulc(FAt[jx * CL + c], FB[i2][r]);
+                    v = cscale(v, ((mx + my + mz) & 1) ? -g.inv_P3 : g.inv_P3);
                 }
-                A[jx * CL + c] = v;
-            }
+                S0[jx * CL + c] = v;
+            });
             __syncthreads();
-            const float2 *res = il_fft<NI, true, CL, TB>(A, B, twI);
+            const float2 *res = il_fft<NI, true, CL, TB>(S0, S1, twI);
             float2 *Hp = h + pr.h_off + (long long)jy * H + ch * CL + 2 * part;
             for (int kx = r8; kx < N; kx += TB / 8)
                 *reinterpret_cast<float4 *>(Hp + (long long)kx * N * H) = *reinterpret_cast<const float4 *>(res + kx * CL + 2 * part);
@@ -673,39 +683,41 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
 }
 
 // ------------------------------------------------------------------ inverse y
-// Item: (k_x, chunk of 16 z-modes); in place on the half-spectrum planes.
+// Item: (k_x, chunk of 16 z-modes); in place on the half-spectrum planes: the
+// first stage reads the item's rows into registers, the last stage writes them
+// back; the next item is loaded while the current one finishes.
 template <int NI>
-__global__ void __launch_bounds__(TB)
+__global__ void __launch_bounds__(TB, 2)
 k_ifft_y(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, float2 *h)
 {
     extern __shared__ float4 sm4[];
     float2 *tw = reinterpret_cast<float2 *>(sm4);
-    float2 *A = tw + NI, *B = A + NI * CL;
+    float2 *S0 = tw + NI, *S1 = S0 + NI * CL;
     load_twiddles<NI>(tw, tb.tw_N);
     const int H = g.H, N = NI;
     const int nch = H / CL;
     const int items = N * nch;
-    const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3;
-    TileGather<NI> tg;
+    FirstInputs<NI, Radix<NI>::r0, CL, TB> in;
     RotStart rs;
     for (int pi = 0; pi < npairs; pi++) {
         const PairDesc pr = pairs[pi];
         if (pr.b < 0) continue;
-        auto src = [&](int it) {
+        auto base_of = [&](int it) {
             const int kx = it / nch, ch = it - kx * nch;
-            return reinterpret_cast<const float4 *>(h + pr.h_off + (long long)kx * N * H + ch * CL);
+            return h + pr.h_off + (long long)kx * N * H + ch * CL;
+        };
+        auto src = [&](int it) {
+            const float2 *base = base_of(it);
+            return [=](int c, int pos) { return base[(long long)pos * H + c]; };
         };
         int it = rs.first();
-        if (it < items) tg.load(src(it), H / 2, 0, N);
+        if (it < items) in.load(src(it));
         for (; it < items; it += gridDim.x) {
-            const int kx = it / nch, ch = it - kx * nch;
-            tg.store(A);
+            rr_first<NI, Radix<NI>::r0, true, CL, TB>(in, S0);
             __syncthreads();
-            if (it + (int)gridDim.x < items) tg.load(src(it + gridDim.x), H / 2, 0, N);
-            const float2 *res = il_fft<NI, true, CL, TB>(A, B, tw);
-            float2 *Hp = h + pr.h_off + (long long)kx * N * H + ch * CL + 2 * part;
-            for (int ky = r8; ky < N; ky += TB / 8)
-                *reinterpret_cast<float4 *>(Hp + (long long)ky * H) = *reinterpret_cast<const float4 *>(res + ky * CL + 2 * part);
+            if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
+            float2 *Hp = base_of(it);
+            rr_rest<NI, true, CL, TB>(S0, S1, tw, [&](int, int, int c, int pos, float2 v) { Hp[(long long)pos * H + c] = v; });
             __syncthreads();
         }
         rs.rot += items;
@@ -848,7 +860,7 @@ static cudaError_t fft_x_t(const Geometry &g, const Tables &t, const InstDesc *i
                            const PairDesc *pairs, int npairs, const float2 *y1, const float2 *fa_cache, float2 *fa_out,
                            float2 *h, int nsm, cudaStream_t s)
 {
-    const size_t smem = sizeof(float2) * (NF + NI + 2 * NF * CL);
+    const size_t smem = sizeof(float2) * (NF + NI + 2 * NF * CL + NI * CL);
     cudaError_t e = set_smem(k_fft_x<NF, NI>, smem);
     if (e != cudaSuccess) return e;
     k_fft_x<NF, NI><<<resident_blocks(k_fft_x<NF, NI>, smem, nsm), TB, smem, s>>>(g, t, inst, plan, pairs, npairs, y1,
