@@ -111,6 +111,20 @@ bc_status bc_shape_destroy(bc_shape_t shape);
 bc_status bc_correlate(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quats, int k,
                        float *out, int out_on_device);
 
+/* Rotation sweep: for each of k rotations of B, the peak of the correlation
+ * over the translation grid,
+ *     peak[r]   = max_t g(R(q_r), t),
+ *     argmax[r] = the lowest linear index (kx*N + ky)*N + kz attaining it,
+ * without writing the N^3 grids.  A's spectrum is computed once per call and
+ * reused; the rotations run in batches of `batch` (0 = 64) through the same
+ * kernels as bc_correlate, the last of which folds each batch's grids into
+ * 64-bit peak keys.  quats: k x 4 FP32 host memory.  peak (k floats) and
+ * argmax (k ints) are device (out_on_device = 1, asynchronous) or host
+ * (0, synchronous) memory.  Errors: BC_ERR_ARG (null pointer, k < 1, zero
+ * quaternion, shapes from another context), BC_ERR_OOM, BC_ERR_CUDA. */
+bc_status bc_sweep(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quats, int k, int batch, float *peak,
+                   int *argmax, int out_on_device);
+
 /* Waits for the context stream and reports any device-side error raised by
  * earlier asynchronous calls (BC_ERR_INTERNAL, BC_ERR_TIMEOUT) or CUDA error. */
 bc_status bc_sync(bc_ctx_t ctx);

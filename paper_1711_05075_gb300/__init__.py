@@ -64,6 +64,8 @@ def lib():
         L.bc_shape_destroy.argtypes = [vp]
         L.bc_correlate.argtypes = [vp, vp, vp, vp, i, vp, i]
         L.bc_sync.argtypes = [vp]
+        L.bc_sweep.argtypes = [vp, vp, vp, vp, i, i, vp, vp, i]
+        L.bc_sweep.restype = st
         for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sync"):
             getattr(L, f).restype = st
         L.bc_last_error.restype = ctypes.c_char_p
@@ -123,6 +125,10 @@ def bc_shape_destroy(shape):
 
 def bc_correlate(ctx, A, B, quats, k, out, out_on_device):
     _check(lib().bc_correlate(ctx, A, B, _ptr(quats), int(k), _ptr(out), int(out_on_device)))
+
+
+def bc_sweep(ctx, A, B, quats, k, batch, peak, argmax, out_on_device):
+    _check(lib().bc_sweep(ctx, A, B, _ptr(quats), int(k), int(batch), _ptr(peak), _ptr(argmax), int(out_on_device)))
 
 
 def bc_sync(ctx):
@@ -197,6 +203,17 @@ class Context:
         assert out.is_cuda and out.is_contiguous() and out.dtype == torch.float32 and out.numel() == k * self.N ** 3
         bc_correlate(self.handle, A.handle, B.handle, q, k, out, 1)
         return out
+
+    def sweep(self, A, B, quats, batch=0):
+        """Peak value and lowest argmax index over the translation grid per rotation:
+        (float32 [k], int32 [k]) CUDA tensors."""
+        import torch
+        q = np.ascontiguousarray(np.asarray(quats, dtype=np.float32).reshape(-1, 4))
+        k = q.shape[0]
+        peak = torch.empty(k, dtype=torch.float32, device="cuda")
+        arg = torch.empty(k, dtype=torch.int32, device="cuda")
+        bc_sweep(self.handle, A.handle, B.handle, q, k, batch, peak, arg, 1)
+        return peak, arg
 
     def correlate_host(self, A, B, quats, out):
         """Same, writing into host memory `out` (numpy array or pinned tensor); synchronous."""

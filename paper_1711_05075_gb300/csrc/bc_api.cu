@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <set>
 #include <string>
@@ -88,7 +89,7 @@ struct bc_ctx_s {
     // device status word
     int *err_dev = nullptr;
     // workspaces
-    DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, outbuf, stats, boxes;
+    DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, outbuf, stats, boxes, keys;
     bool boxes_dirty = true; // support-box accumulators need their reset state
     std::vector<char> last_desc;            // descriptors the device copies hold
     void *last_inst_p = nullptr, *last_pairs_p = nullptr;
@@ -250,7 +251,7 @@ bc_status bc_destroy(bc_ctx_t c)
             s->ctx = nullptr;
         }
         c->shapes.clear();
-        DevBuf *bufs[] = {&c->ku, &c->plan, &c->inst, &c->pairs, &c->grid, &c->z1, &c->y1, &c->h, &c->fa, &c->outbuf, &c->stats, &c->boxes};
+        DevBuf *bufs[] = {&c->ku, &c->plan, &c->inst, &c->pairs, &c->grid, &c->z1, &c->y1, &c->h, &c->fa, &c->outbuf, &c->stats, &c->boxes, &c->keys};
         for (DevBuf *b : bufs) b->release();
         delete c;
         return BC_OK;
@@ -413,6 +414,170 @@ bc_status bc_profile_end(bc_ctx_t c, bc_profile *out)
     return BC_OK;
 }
 
+} // extern "C"
+
+// Enqueues one pass of the pipeline over `shapes` (instance i is shapes[i]
+// rotated by quats[i], identity when null) and `pairs`.  With cache_first,
+// pairs[0] = (a, -1) writes instance a's spectrum into the context's cache and
+// the remaining pairs follow; pairs with a = -1 read that cache.  dout (device,
+// N^3 floats at each pair's out_off) and keys (device peak keys at each pair's
+// key) may be null.
+static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std::vector<const float *> &quats,
+                         const std::vector<PairDesc> &pairs, bool cache_first, float *dout, unsigned long long *keys)
+{
+    cudaStream_t st = c->stream;
+    const Geometry &g = c->g;
+    const int N = g.N, H = g.H, L = g.L;
+    const int ninst = (int)shapes.size();
+    const int npairs = (int)pairs.size();
+    const int nmain = npairs - (cache_first ? 1 : 0);
+
+    std::vector<InstDesc> inst(ninst);
+    long long goff = 0, zoff = 0, yoff = 0;
+    int koff = 0, max_knots = 0;
+    for (int i = 0; i < ninst; i++) {
+        bc_shape_t s = shapes[i];
+        InstDesc &d = inst[i];
+        std::memset(&d, 0, sizeof(d));
+        d.knot_off = koff;
+        d.nknots = s->n;
+        d.src_off = 0;
+        d.knots = s->knots;
+        const int e = cap_extent(c, s->rmax);
+        d.cap_e = e;
+        d.grid_off = goff;
+        d.z1_off = zoff;
+        d.y1_off = yoff;
+        if (quats[i]) {
+            for (int q = 0; q < 4; q++) d.q[q] = quats[i][q];
+        } else {
+            d.q[0] = 1.f;
+        }
+        koff += s->n;
+        max_knots = s->n > max_knots ? s->n : max_knots;
+        goff += (long long)L * e * (((e + 31) / 32) * 32) * e; // block-transposed boxes, y padded to 32
+        zoff += (long long)L * e * e * H;
+        yoff += (long long)L * e * N * H;
+    }
+    long long hpairs = 0;
+    for (const PairDesc &p : pairs)
+        if (p.b >= 0) hpairs = std::max(hpairs, p.h_off / ((long long)N * N * H) + 1);
+
+    cudaError_t e;
+    if ((e = c->ku.ensure(sizeof(float4) * (size_t)(koff > 0 ? koff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "ku");
+    if ((e = c->plan.ensure(sizeof(InstPlan) * ninst, false, st)) != cudaSuccess) return cuda_fail(e, "plan");
+    {
+        const size_t before = c->boxes.bytes;
+        if ((e = c->boxes.ensure(sizeof(int) * 8 * (size_t)ninst, false, st)) != cudaSuccess) return cuda_fail(e, "boxes");
+        if (c->boxes.bytes != before || c->boxes_dirty) {
+            if ((e = launch_reset_boxes((int *)c->boxes.p, (int)(c->boxes.bytes / (8 * sizeof(int))), st)) != cudaSuccess)
+                return cuda_fail(e, "reset boxes");
+            c->boxes_dirty = false;
+        }
+    }
+    if ((e = c->inst.ensure(sizeof(InstDesc) * ninst, false, st)) != cudaSuccess) return cuda_fail(e, "inst");
+    if ((e = c->pairs.ensure(sizeof(PairDesc) * npairs, false, st)) != cudaSuccess) return cuda_fail(e, "pairs");
+    const size_t grid_before = c->grid.bytes;
+    if ((e = c->grid.ensure(sizeof(float) * (size_t)(goff > 0 ? goff : 1), true, st)) != cudaSuccess) return cuda_fail(e, "grid");
+    if (c->grid_dirty && c->grid.bytes == grid_before) {
+        if ((e = cudaMemsetAsync(c->grid.p, 0, c->grid.bytes, st)) != cudaSuccess) return cuda_fail(e, "grid clear");
+    }
+    c->grid_dirty = false;
+    if ((e = c->z1.ensure(sizeof(float2) * (size_t)(zoff > 0 ? zoff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "z1");
+    if ((e = c->y1.ensure(sizeof(float2) * (size_t)(yoff > 0 ? yoff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "y1");
+    if (hpairs > 0 && (e = c->h.ensure(sizeof(float2) * (size_t)hpairs * N * N * H, false, st)) != cudaSuccess)
+        return cuda_fail(e, "h");
+    if ((e = c->fa.ensure(sizeof(float2) * (size_t)N * N * H, false, st)) != cudaSuccess) return cuda_fail(e, "fa");
+
+    // descriptors -> device, only when they differ from what the device already holds
+    const size_t inst_bytes = sizeof(InstDesc) * ninst, pair_bytes = sizeof(PairDesc) * npairs;
+    std::vector<char> desc(inst_bytes + pair_bytes);
+    std::memcpy(desc.data(), inst.data(), inst_bytes);
+    std::memcpy(desc.data() + inst_bytes, pairs.data(), pair_bytes);
+    if (desc != c->last_desc || c->inst.p != c->last_inst_p || c->pairs.p != c->last_pairs_p) {
+        if ((e = cudaMemcpyAsync(c->inst.p, desc.data(), inst_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "copy inst");
+        if ((e = cudaMemcpyAsync(c->pairs.p, desc.data() + inst_bytes, pair_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "copy pairs");
+        c->last_desc.swap(desc);
+        c->last_inst_p = c->inst.p;
+        c->last_pairs_p = c->pairs.p;
+    }
+
+    const InstDesc *dinst = (const InstDesc *)c->inst.p;
+    const Tables t = tables_of(c);
+    InstPlan *dplan = (InstPlan *)c->plan.p;
+    const PairDesc *dpairs = (const PairDesc *)c->pairs.p;
+    const PairDesc *pmain = dpairs + (cache_first ? 1 : 0);
+    int launches = 0;
+    c->grid_dirty = true; // until the z pass has consumed the spreading boxes
+    const bool prof = c->prof_on && c->prof_calls < c->prof_max;
+    prof_mark(c, -1);
+    c->boxes_dirty = true; // until k_plan has consumed and reset the accumulators
+    if ((e = launch_prepare(g, dinst, ninst, max_knots, (float4 *)c->ku.p, (int *)c->boxes.p, dplan, c->err_dev, st)) != cudaSuccess)
+        return cuda_fail(e, "prepare");
+    c->boxes_dirty = false;
+    launches += 2;
+    prof_mark(c, 0);
+    if ((e = launch_spread(g, t, dinst, koff, (const float4 *)c->ku.p, dplan, (float *)c->grid.p, st)) != cudaSuccess)
+        return cuda_fail(e, "spread");
+    launches += koff > 0;
+    prof_mark(c, 1);
+    if ((e = launch_fft_z(g, t, dinst, ninst, dplan, (float *)c->grid.p, (float2 *)c->z1.p, c->nsm, st)) != cudaSuccess)
+        return cuda_fail(e, "fft z");
+    c->grid_dirty = false;
+    launches++;
+    prof_mark(c, 2);
+    if ((e = launch_fft_y(g, t, dinst, ninst, dplan, (const float2 *)c->z1.p, (float2 *)c->y1.p, c->nsm, st)) != cudaSuccess)
+        return cuda_fail(e, "fft y");
+    launches++;
+    prof_mark(c, 3);
+    if (cache_first) {
+        if ((e = launch_fft_x(g, t, dinst, dplan, dpairs, 1, (const float2 *)c->y1.p, nullptr, (float2 *)c->fa.p,
+                              (float2 *)c->h.p, c->nsm, st)) != cudaSuccess)
+            return cuda_fail(e, "fft x (cache)");
+        launches++;
+    }
+    if (nmain > 0) {
+        if ((e = launch_fft_x(g, t, dinst, dplan, pmain, nmain, (const float2 *)c->y1.p, (const float2 *)c->fa.p,
+                              nullptr, (float2 *)c->h.p, c->nsm, st)) != cudaSuccess)
+            return cuda_fail(e, "fft x");
+        launches++;
+    }
+    prof_mark(c, 4);
+    if (nmain > 0) {
+        if ((e = launch_ifft_y(g, t, pmain, nmain, (float2 *)c->h.p, c->nsm, st)) != cudaSuccess) return cuda_fail(e, "ifft y");
+        launches++;
+    }
+    prof_mark(c, 5);
+    if (nmain > 0) {
+        if ((e = launch_ifft_z(g, t, pmain, nmain, (const float2 *)c->h.p, dout, keys, c->nsm, st)) != cudaSuccess)
+            return cuda_fail(e, "ifft z");
+        launches++;
+    }
+    prof_mark(c, 6);
+    if (prof) {
+        c->prof_calls++;
+        c->prof_launches += launches;
+        c->last_ninst = ninst;
+        c->last_npairs = nmain;
+        c->last_inst = inst;
+    }
+    return BC_OK;
+}
+
+static bc_status check_quats(const float *quats, int k, const char *who)
+{
+    for (int r = 0; r < k; r++) {
+        const float *q = quats + 4 * r;
+        const double n2 = (double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] + (double)q[3] * q[3];
+        if (!(n2 > 1e-30) || !std::isfinite(n2)) return fail(BC_ERR_ARG, std::string(who) + ": zero or non-finite quaternion");
+    }
+    return BC_OK;
+}
+
+extern "C" {
+
 bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, int k, float *out,
                        int out_on_device)
 {
@@ -420,150 +585,90 @@ bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quat
         if (!c || !A || !B || !quats || !out) return fail(BC_ERR_ARG, "bc_correlate: null argument");
         if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_correlate: shapes belong to another context");
         if (k < 1 || k > 65534) return fail(BC_ERR_ARG, "bc_correlate: k must be in [1, 65534]");
-        for (int r = 0; r < k; r++) {
-            const float *q = quats + 4 * r;
-            double n2 = (double)q[0] * q[0] + (double)q[1] * q[1] + (double)q[2] * q[2] + (double)q[3] * q[3];
-            if (!(n2 > 1e-30) || !std::isfinite(n2)) return fail(BC_ERR_ARG, "bc_correlate: zero or non-finite quaternion");
-        }
-        cudaStream_t st = c->stream;
-        const Geometry &g = c->g;
-        const int N = g.N, H = g.H, L = g.L;
-        const int ninst = 1 + k;
+        if (bc_status s = check_quats(quats, k, "bc_correlate")) return s;
+        const int N = c->g.N, H = c->g.H;
         const long long N3 = (long long)N * N * N;
-
-        // host-side descriptors
-        std::vector<InstDesc> inst(ninst);
-        long long goff = 0, zoff = 0, yoff = 0;
-        int koff = 0;
-        for (int i = 0; i < ninst; i++) {
-            bc_shape_t s = i == 0 ? A : B;
-            InstDesc &d = inst[i];
-            d.knot_off = koff;
-            d.nknots = s->n;
-            d.src_off = 0;
-            d.knots = s->knots;
-            const int e = cap_extent(c, s->rmax);
-            d.cap_e = e;
-            d.grid_off = goff;
-            d.z1_off = zoff;
-            d.y1_off = yoff;
-            if (i == 0) {
-                d.q[0] = 1.f;
-                d.q[1] = d.q[2] = d.q[3] = 0.f;
-            } else {
-                for (int a = 0; a < 4; a++) d.q[a] = quats[4 * (i - 1) + a];
-            }
-            koff += s->n;
-            goff += (long long)L * e * (((e + 31) / 32) * 32) * e; // block-transposed boxes, y padded to 32
-            zoff += (long long)L * e * e * H;
-            yoff += (long long)L * e * N * H;
-        }
+        std::vector<bc_shape_t> shapes(1 + k, B);
+        shapes[0] = A;
+        std::vector<const float *> q(1 + k, nullptr);
+        for (int r = 0; r < k; r++) q[1 + r] = quats + 4 * r;
         const bool fused = (k == 1);
-        const int npairs_main = k;
         std::vector<PairDesc> pairs;
-        if (!fused) pairs.push_back(PairDesc{0, -1, 0, 0}); // spectrum of A into the cache
+        if (!fused) pairs.push_back(PairDesc{0, -1, 0, 0, 0}); // spectrum of A into the cache
         for (int r = 0; r < k; r++)
-            pairs.push_back(PairDesc{fused ? 0 : -1, 1 + r, (long long)r * N * N * H, (long long)r * N3});
-        const int npairs = (int)pairs.size();
-
-        cudaError_t e;
-        if ((e = c->ku.ensure(sizeof(float4) * (size_t)(koff > 0 ? koff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "ku");
-        if ((e = c->plan.ensure(sizeof(InstPlan) * ninst, false, st)) != cudaSuccess) return cuda_fail(e, "plan");
-        {
-            const size_t before = c->boxes.bytes;
-            if ((e = c->boxes.ensure(sizeof(int) * 8 * (size_t)ninst, false, st)) != cudaSuccess) return cuda_fail(e, "boxes");
-            if (c->boxes.bytes != before || c->boxes_dirty) {
-                if ((e = launch_reset_boxes((int *)c->boxes.p, (int)(c->boxes.bytes / (8 * sizeof(int))), st)) != cudaSuccess)
-                    return cuda_fail(e, "reset boxes");
-                c->boxes_dirty = false;
-            }
-        }
-        if ((e = c->inst.ensure(sizeof(InstDesc) * ninst, false, st)) != cudaSuccess) return cuda_fail(e, "inst");
-        if ((e = c->pairs.ensure(sizeof(PairDesc) * npairs, false, st)) != cudaSuccess) return cuda_fail(e, "pairs");
-        const size_t grid_before = c->grid.bytes;
-        if ((e = c->grid.ensure(sizeof(float) * (size_t)(goff > 0 ? goff : 1), true, st)) != cudaSuccess) return cuda_fail(e, "grid");
-        if (c->grid_dirty && c->grid.bytes == grid_before) {
-            if ((e = cudaMemsetAsync(c->grid.p, 0, c->grid.bytes, st)) != cudaSuccess) return cuda_fail(e, "grid clear");
-        }
-        c->grid_dirty = false;
-        if ((e = c->z1.ensure(sizeof(float2) * (size_t)(zoff > 0 ? zoff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "z1");
-        if ((e = c->y1.ensure(sizeof(float2) * (size_t)(yoff > 0 ? yoff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "y1");
-        if ((e = c->h.ensure(sizeof(float2) * (size_t)k * N * N * H, false, st)) != cudaSuccess) return cuda_fail(e, "h");
-        if (!fused && (e = c->fa.ensure(sizeof(float2) * (size_t)N * N * H, false, st)) != cudaSuccess) return cuda_fail(e, "fa");
+            pairs.push_back(PairDesc{fused ? 0 : -1, 1 + r, (long long)r * N * N * H, (long long)r * N3, r});
         float *dout = out;
+        cudaError_t e;
         if (!out_on_device) {
-            if ((e = c->outbuf.ensure(sizeof(float) * (size_t)k * N3, false, st)) != cudaSuccess) return cuda_fail(e, "outbuf");
+            if ((e = c->outbuf.ensure(sizeof(float) * (size_t)k * N3, false, c->stream)) != cudaSuccess) return cuda_fail(e, "outbuf");
             dout = (float *)c->outbuf.p;
         }
-
-        // descriptors -> device, only when they differ from what the device already holds
-        const size_t inst_bytes = sizeof(InstDesc) * ninst, pair_bytes = sizeof(PairDesc) * npairs;
-        std::vector<char> desc(inst_bytes + pair_bytes);
-        std::memcpy(desc.data(), inst.data(), inst_bytes);
-        std::memcpy(desc.data() + inst_bytes, pairs.data(), pair_bytes);
-        if (desc != c->last_desc || c->inst.p != c->last_inst_p || c->pairs.p != c->last_pairs_p) {
-            if ((e = cudaMemcpyAsync(c->inst.p, desc.data(), inst_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-                return cuda_fail(e, "copy inst");
-            if ((e = cudaMemcpyAsync(c->pairs.p, desc.data() + inst_bytes, pair_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-                return cuda_fail(e, "copy pairs");
-            c->last_desc.swap(desc);
-            c->last_inst_p = c->inst.p;
-            c->last_pairs_p = c->pairs.p;
-        }
-
-        const InstDesc *dinst = (const InstDesc *)c->inst.p;
-        const Tables t = tables_of(c);
-        InstPlan *dplan = (InstPlan *)c->plan.p;
-        const PairDesc *dpairs = (const PairDesc *)c->pairs.p;
-        c->grid_dirty = true; // until the z pass has consumed the spreading boxes
-        const bool prof = c->prof_on && c->prof_calls < c->prof_max;
-        prof_mark(c, -1);
-        const int max_knots = A->n > B->n ? A->n : B->n;
-        c->boxes_dirty = true; // until k_plan has consumed and reset the accumulators
-        if ((e = launch_prepare(g, dinst, ninst, max_knots, (float4 *)c->ku.p, (int *)c->boxes.p, dplan, c->err_dev, st)) != cudaSuccess)
-            return cuda_fail(e, "prepare");
-        c->boxes_dirty = false;
-        prof_mark(c, 0);
-        if ((e = launch_spread(g, t, dinst, koff, (const float4 *)c->ku.p, dplan, (float *)c->grid.p, st)) != cudaSuccess)
-            return cuda_fail(e, "spread");
-        prof_mark(c, 1);
-        if ((e = launch_fft_z(g, t, dinst, ninst, dplan, (float *)c->grid.p, (float2 *)c->z1.p, c->nsm, st)) != cudaSuccess)
-            return cuda_fail(e, "fft z");
-        c->grid_dirty = false;
-        prof_mark(c, 2);
-        if ((e = launch_fft_y(g, t, dinst, ninst, dplan, (const float2 *)c->z1.p, (float2 *)c->y1.p, c->nsm, st)) != cudaSuccess)
-            return cuda_fail(e, "fft y");
-        prof_mark(c, 3);
-        if (!fused) {
-            if ((e = launch_fft_x(g, t, dinst, dplan, dpairs, 1, (const float2 *)c->y1.p, nullptr, (float2 *)c->fa.p,
-                                  (float2 *)c->h.p, c->nsm, st)) != cudaSuccess)
-                return cuda_fail(e, "fft x (A)");
-        }
-        const PairDesc *pmain = dpairs + (fused ? 0 : 1);
-        if ((e = launch_fft_x(g, t, dinst, dplan, pmain, npairs_main, (const float2 *)c->y1.p, (const float2 *)c->fa.p,
-                              nullptr, (float2 *)c->h.p, c->nsm, st)) != cudaSuccess)
-            return cuda_fail(e, "fft x");
-        prof_mark(c, 4);
-        if ((e = launch_ifft_y(g, t, pmain, npairs_main, (float2 *)c->h.p, c->nsm, st)) != cudaSuccess) return cuda_fail(e, "ifft y");
-        prof_mark(c, 5);
-        if ((e = launch_ifft_z(g, t, pmain, npairs_main, (const float2 *)c->h.p, dout, c->nsm, st)) != cudaSuccess)
-            return cuda_fail(e, "ifft z");
-        prof_mark(c, 6);
-        if (prof) {
-            c->prof_calls++;
-            c->prof_launches += fused ? 8 : 9;
-            c->last_ninst = ninst;
-            c->last_npairs = npairs_main;
-            c->last_inst = inst;
-        }
+        if (bc_status s = enqueue(c, shapes, q, pairs, !fused, dout, nullptr)) return s;
         if (!out_on_device) {
-            if ((e = cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)k * N3, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            if ((e = cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)k * N3, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
                 return cuda_fail(e, "copy out");
             return bc_sync(c);
         }
         return BC_OK;
     } catch (...) {
         return fail(BC_ERR_INTERNAL, "bc_correlate: unexpected exception");
+    }
+}
+
+bc_status bc_sweep(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, int k, int batch, float *peak,
+                   int *argmax, int out_on_device)
+{
+    try {
+        if (!c || !A || !B || !quats || !peak || !argmax) return fail(BC_ERR_ARG, "bc_sweep: null argument");
+        if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_sweep: shapes belong to another context");
+        if (k < 1 || k > (1 << 24)) return fail(BC_ERR_ARG, "bc_sweep: k must be in [1, 2^24]");
+        if (batch < 0 || batch > 65534) return fail(BC_ERR_ARG, "bc_sweep: batch must be in [0, 65534]");
+        if (bc_status s = check_quats(quats, k, "bc_sweep")) return s;
+        if (batch == 0) batch = 64;
+        const int N = c->g.N, H = c->g.H;
+        cudaStream_t st = c->stream;
+        cudaError_t e;
+        // one peak key per rotation, then the decoded peaks (device scratch when the caller wants host output)
+        const size_t key_bytes = sizeof(unsigned long long) * (size_t)k;
+        const size_t out_bytes = out_on_device ? 0 : (sizeof(float) + sizeof(int)) * (size_t)k;
+        if ((e = c->keys.ensure(key_bytes + out_bytes, false, st)) != cudaSuccess) return cuda_fail(e, "keys");
+        unsigned long long *keys = (unsigned long long *)c->keys.p;
+        if ((e = cudaMemsetAsync(keys, 0, key_bytes, st)) != cudaSuccess) return cuda_fail(e, "clear keys");
+        // A's spectrum once
+        {
+            std::vector<bc_shape_t> shapes(1, A);
+            std::vector<const float *> q(1, nullptr);
+            std::vector<PairDesc> pairs(1, PairDesc{0, -1, 0, 0, 0});
+            if (bc_status s = enqueue(c, shapes, q, pairs, true, nullptr, nullptr)) return s;
+        }
+        for (int r0 = 0; r0 < k; r0 += batch) {
+            const int nb = std::min(batch, k - r0);
+            std::vector<bc_shape_t> shapes(nb, B);
+            std::vector<const float *> q(nb);
+            std::vector<PairDesc> pairs(nb);
+            for (int i = 0; i < nb; i++) {
+                q[i] = quats + 4 * (size_t)(r0 + i);
+                pairs[i] = PairDesc{-1, i, (long long)i * N * N * H, 0, (long long)(r0 + i)};
+            }
+            if (bc_status s = enqueue(c, shapes, q, pairs, false, nullptr, keys)) return s;
+        }
+        float *dpeak = peak;
+        int *darg = argmax;
+        if (!out_on_device) {
+            dpeak = (float *)((char *)c->keys.p + key_bytes);
+            darg = (int *)(dpeak + k);
+        }
+        if ((e = launch_decode_peaks(keys, k, dpeak, darg, st)) != cudaSuccess) return cuda_fail(e, "decode peaks");
+        if (!out_on_device) {
+            if ((e = cudaMemcpyAsync(peak, dpeak, sizeof(float) * (size_t)k, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return cuda_fail(e, "copy peaks");
+            if ((e = cudaMemcpyAsync(argmax, darg, sizeof(int) * (size_t)k, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return cuda_fail(e, "copy argmax");
+            return bc_sync(c);
+        }
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_sweep: unexpected exception");
     }
 }
 

@@ -34,7 +34,8 @@ struct InstPlan {
 struct PairDesc {
     int a, b;
     long long h_off;    // float2 offset of this pair's inverse-transform planes
-    long long out_off;  // float offset of this pair's output grid
+    long long out_off;  // float offset of this pair's output grid (when a grid is written)
+    long long key;      // slot of this pair's peak key (when peaks are taken)
 };
 
 struct Tables {
@@ -73,8 +74,11 @@ cudaError_t launch_fft_x(const Geometry &g, const Tables &t, const InstDesc *ins
                          float2 *fa_out, float2 *h, int nsm, cudaStream_t s);
 cudaError_t launch_ifft_y(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, float2 *h,
                           int nsm, cudaStream_t s);
+// out (N^3 floats per pair) and keys (one 64-bit peak key per pair slot) may each be null.
 cudaError_t launch_ifft_z(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs,
-                          const float2 *h, float *out, int nsm, cudaStream_t s);
+                          const float2 *h, float *out, unsigned long long *keys, int nsm, cudaStream_t s);
+// keys[i] -> peak[i], argmax[i] (i < n).
+cudaError_t launch_decode_peaks(const unsigned long long *keys, int n, float *peak, int *argmax, cudaStream_t s);
 
 bool supported_N(int N);
 

@@ -725,16 +725,48 @@ k_ifft_y(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
 }
 
 // ------------------------------------------------------------------ inverse z (c2r)
+// Peak keys: an order-preserving map of the FP32 value to the high 32 bits
+// (negative values bit-inverted, non-negative ones with the sign bit set) and
+// the complement of the linear grid index in the low 32 bits, so that the
+// maximum key is the largest value and, among equal values, the lowest index.
+__device__ __forceinline__ unsigned long long peak_key(float v, unsigned idx)
+{
+    unsigned u = __float_as_uint(v);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)u << 32) | (unsigned long long)(0xFFFFFFFFu - idx);
+}
+
+__global__ void k_decode_peaks(const unsigned long long *__restrict__ keys, int n, float *peak, int *argmax)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long key = keys[i];
+    unsigned u = (unsigned)(key >> 32);
+    u = (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+    peak[i] = __uint_as_float(u);
+    argmax[i] = (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
+}
+
+cudaError_t launch_decode_peaks(const unsigned long long *keys, int n, float *peak, int *argmax, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_decode_peaks<<<(n + 255) / 256, 256, 0, s>>>(keys, n, peak, argmax);
+    return cudaGetLastError();
+}
+
 // Item: 32 output rows (k_x, k_y0 .. k_y0+31) as 16 complex lines; lane l of a
 // warp owns row k_y0 + l.  Rows a = 2q and b = 2q+1 of the half spectrum are
 // packed as Z_k = A_k + i B_k over the full range (A_{N-k} = conj A_k, A_0
 // taken real, the m_z = N/2 term zero); the inverse transform of Z is a + i b.
-// The even lane of each pair writes Z_k, the odd lane Z_{N-k}.
+// The even lane of each pair writes Z_k, the odd lane Z_{N-k}.  With `keys`,
+// the item's largest value (lowest index on ties) is folded into the pair's
+// peak key with one 64-bit atomic max; with `out` null no grid is written.
 template <int NI>
 __global__ void __launch_bounds__(TB)
 k_ifft_z(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, const float2 *__restrict__ h,
-         float *out)
+         float *out, unsigned long long *keys)
 {
+    __shared__ unsigned long long red[TB / 32];
     extern __shared__ float4 sm4[];
     float2 *tw = reinterpret_cast<float2 *>(sm4);
     float2 *A = tw + NI, *B = A + NI * CL;
@@ -779,10 +811,28 @@ k_ifft_z(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
                 S[r * N + (kz ^ r)] = (r & 1) ? v.y : v.x;
             }
             __syncthreads();
-            float *o = out + pr.out_off + ((long long)kx * N + ky0) * N;
+            float *o = out ? out + pr.out_off + ((long long)kx * N + ky0) * N : nullptr;
+            unsigned long long best = 0ull;
             for (int e = threadIdx.x; e < 32 * N; e += TB) {
                 const int r = e / N, kz = e - r * N;
-                o[(long long)r * N + kz] = S[r * N + (kz ^ r)];
+                const float v = S[r * N + (kz ^ r)];
+                if (o) o[(long long)r * N + kz] = v;
+                if (keys) {
+                    const unsigned long long kk = peak_key(v, (unsigned)(((long long)kx * N + ky0 + r) * N + kz));
+                    best = kk > best ? kk : best;
+                }
+            }
+            if (keys) {
+                for (int off = 16; off > 0; off >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, off);
+                    best = other > best ? other : best;
+                }
+                if (lane == 0) red[w] = best;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    for (int i2 = 1; i2 < TB / 32; i2++) best = red[i2] > best ? red[i2] : best;
+                    atomicMax(keys + pr.key, best);
+                }
             }
             __syncthreads();
         }
@@ -908,24 +958,24 @@ cudaError_t launch_ifft_y(const Geometry &g, const Tables &t, const PairDesc *pa
 
 template <int NI>
 static cudaError_t ifft_z_t(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, const float2 *h,
-                            float *out, int nsm, cudaStream_t s)
+                            float *out, unsigned long long *keys, int nsm, cudaStream_t s)
 {
     const size_t smem = sizeof(float2) * (NI + 2 * NI * CL);
     cudaError_t e = set_smem(k_ifft_z<NI>, smem);
     if (e != cudaSuccess) return e;
-    k_ifft_z<NI><<<resident_blocks(k_ifft_z<NI>, smem, nsm), TB, smem, s>>>(g, t, pairs, npairs, h, out);
+    k_ifft_z<NI><<<resident_blocks(k_ifft_z<NI>, smem, nsm), TB, smem, s>>>(g, t, pairs, npairs, h, out, keys);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ifft_z(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, const float2 *h,
-                          float *out, int nsm, cudaStream_t s)
+                          float *out, unsigned long long *keys, int nsm, cudaStream_t s)
 {
     switch (g.N) {
-    case 32: return ifft_z_t<32>(g, t, pairs, npairs, h, out, nsm, s);
-    case 64: return ifft_z_t<64>(g, t, pairs, npairs, h, out, nsm, s);
-    case 96: return ifft_z_t<96>(g, t, pairs, npairs, h, out, nsm, s);
-    case 128: return ifft_z_t<128>(g, t, pairs, npairs, h, out, nsm, s);
-    case 256: return ifft_z_t<256>(g, t, pairs, npairs, h, out, nsm, s);
+    case 32: return ifft_z_t<32>(g, t, pairs, npairs, h, out, keys, nsm, s);
+    case 64: return ifft_z_t<64>(g, t, pairs, npairs, h, out, keys, nsm, s);
+    case 96: return ifft_z_t<96>(g, t, pairs, npairs, h, out, keys, nsm, s);
+    case 128: return ifft_z_t<128>(g, t, pairs, npairs, h, out, keys, nsm, s);
+    case 256: return ifft_z_t<256>(g, t, pairs, npairs, h, out, keys, nsm, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -202,7 +202,7 @@ extern "C" bc_status bc_correlate_noalloc(const bc_params *p, const float *xyzA,
         }
         inst[0].q[0] = 1.f;
         for (int a = 0; a < 4; a++) inst[1].q[a] = quat[a];
-        const PairDesc pr{0, 1, 0, 0};
+        const PairDesc pr{0, 1, 0, 0, 0};
         if ((e = cudaMemcpyAsync(dinst, inst, sizeof(inst), cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return ncuda(e, "copy descriptors");
         if ((e = cudaMemcpyAsync(dpairs, &pr, sizeof(pr), cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -223,7 +223,7 @@ extern "C" bc_status bc_correlate_noalloc(const bc_params *p, const float *xyzA,
         if ((e = launch_fft_x(g, t, dinst, dplan, dpairs, 1, y1, nullptr, nullptr, h, nsm, st)) != cudaSuccess)
             return ncuda(e, "fft x");
         if ((e = launch_ifft_y(g, t, dpairs, 1, h, nsm, st)) != cudaSuccess) return ncuda(e, "ifft y");
-        if ((e = launch_ifft_z(g, t, dpairs, 1, h, out, nsm, st)) != cudaSuccess) return ncuda(e, "ifft z");
+        if ((e = launch_ifft_z(g, t, dpairs, 1, h, out, nullptr, nsm, st)) != cudaSuccess) return ncuda(e, "ifft z");
         return BC_OK;
     } catch (...) {
         return nfail(BC_ERR_INTERNAL, "bc_correlate_noalloc: unexpected exception");
