@@ -125,6 +125,18 @@ bc_status bc_correlate(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *qu
 bc_status bc_sweep(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quats, int k, int batch, float *peak,
                    int *argmax, int out_on_device);
 
+/* Ragged batch of independent pairs: pair i correlates As[i] with Bs[i]
+ * rotated by quats[i] (npairs x 4 FP32, host).  Shapes may have any knot
+ * counts; every instance gets its own support box.  Outputs (either may be
+ * NULL, not both): out[i][kx][ky][kz] (npairs * N^3 floats) and
+ * peak[i] / argmax[i] as in bc_sweep.  All output pointers are device memory
+ * (on_device = 1, asynchronous) or host memory (0, synchronous).
+ * Errors: BC_ERR_ARG (null shape or quaternion array, zero quaternion, both
+ * outputs null, peak without argmax, npairs outside [1, 32767], shapes from
+ * another context), BC_ERR_OOM, BC_ERR_CUDA. */
+bc_status bc_pairs(bc_ctx_t ctx, const bc_shape_t *As, const bc_shape_t *Bs, const float *quats, int npairs,
+                   float *out, float *peak, int *argmax, int on_device);
+
 /* Waits for the context stream and reports any device-side error raised by
  * earlier asynchronous calls (BC_ERR_INTERNAL, BC_ERR_TIMEOUT) or CUDA error. */
 bc_status bc_sync(bc_ctx_t ctx);

@@ -66,6 +66,8 @@ def lib():
         L.bc_sync.argtypes = [vp]
         L.bc_sweep.argtypes = [vp, vp, vp, vp, i, i, vp, vp, i]
         L.bc_sweep.restype = st
+        L.bc_pairs.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, i]
+        L.bc_pairs.restype = st
         for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sync"):
             getattr(L, f).restype = st
         L.bc_last_error.restype = ctypes.c_char_p
@@ -129,6 +131,14 @@ def bc_correlate(ctx, A, B, quats, k, out, out_on_device):
 
 def bc_sweep(ctx, A, B, quats, k, batch, peak, argmax, out_on_device):
     _check(lib().bc_sweep(ctx, A, B, _ptr(quats), int(k), int(batch), _ptr(peak), _ptr(argmax), int(out_on_device)))
+
+
+def bc_pairs(ctx, As, Bs, quats, npairs, out, peak, argmax, on_device):
+    """As, Bs: sequences of shape handles (marshalled into C arrays of pointers)."""
+    arrA = (ctypes.c_void_p * npairs)(*[h.value for h in As])
+    arrB = (ctypes.c_void_p * npairs)(*[h.value for h in Bs])
+    _check(lib().bc_pairs(ctx, arrA, arrB, _ptr(quats), int(npairs), _ptr(out), _ptr(peak), _ptr(argmax),
+                          int(on_device)))
 
 
 def bc_sync(ctx):
@@ -214,6 +224,17 @@ class Context:
         arg = torch.empty(k, dtype=torch.int32, device="cuda")
         bc_sweep(self.handle, A.handle, B.handle, q, k, batch, peak, arg, 1)
         return peak, arg
+
+    def pairs(self, As, Bs, quats, grids=False, peaks=True):
+        """Ragged batch of independent pairs; returns (grids or None, peak or None, argmax or None)."""
+        import torch
+        q = np.ascontiguousarray(np.asarray(quats, dtype=np.float32).reshape(-1, 4))
+        n = q.shape[0]
+        out = torch.empty((n, self.N, self.N, self.N), dtype=torch.float32, device="cuda") if grids else None
+        peak = torch.empty(n, dtype=torch.float32, device="cuda") if peaks else None
+        arg = torch.empty(n, dtype=torch.int32, device="cuda") if peaks else None
+        bc_pairs(self.handle, [a.handle for a in As], [b.handle for b in Bs], q, n, out, peak, arg, 1)
+        return out, peak, arg
 
     def correlate_host(self, A, B, quats, out):
         """Same, writing into host memory `out` (numpy array or pinned tensor); synchronous."""

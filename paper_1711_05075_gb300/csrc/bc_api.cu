@@ -615,6 +615,69 @@ bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quat
     }
 }
 
+bc_status bc_pairs(bc_ctx_t c, const bc_shape_t *As, const bc_shape_t *Bs, const float *quats, int npairs,
+                   float *out, float *peak, int *argmax, int on_device)
+{
+    try {
+        if (!c || !As || !Bs || !quats) return fail(BC_ERR_ARG, "bc_pairs: null argument");
+        if (!out && !peak) return fail(BC_ERR_ARG, "bc_pairs: nothing to compute (out and peak are null)");
+        if ((peak == nullptr) != (argmax == nullptr)) return fail(BC_ERR_ARG, "bc_pairs: peak and argmax go together");
+        if (npairs < 1 || npairs > 32767) return fail(BC_ERR_ARG, "bc_pairs: npairs must be in [1, 32767]");
+        for (int i = 0; i < npairs; i++) {
+            if (!As[i] || !Bs[i]) return fail(BC_ERR_ARG, "bc_pairs: null shape");
+            if (As[i]->ctx != c || Bs[i]->ctx != c) return fail(BC_ERR_ARG, "bc_pairs: shapes belong to another context");
+        }
+        if (bc_status s = check_quats(quats, npairs, "bc_pairs")) return s;
+        const int N = c->g.N, H = c->g.H;
+        const long long N3 = (long long)N * N * N;
+        cudaStream_t st = c->stream;
+        cudaError_t e;
+        const size_t key_bytes = peak ? sizeof(unsigned long long) * (size_t)npairs : 0;
+        const size_t pk_bytes = (peak && !on_device) ? (sizeof(float) + sizeof(int)) * (size_t)npairs : 0;
+        if (key_bytes && (e = c->keys.ensure(key_bytes + pk_bytes, false, st)) != cudaSuccess) return cuda_fail(e, "keys");
+        unsigned long long *keys = key_bytes ? (unsigned long long *)c->keys.p : nullptr;
+        if (keys && (e = cudaMemsetAsync(keys, 0, key_bytes, st)) != cudaSuccess) return cuda_fail(e, "clear keys");
+        float *dout = out;
+        if (out && !on_device) {
+            if ((e = c->outbuf.ensure(sizeof(float) * (size_t)npairs * N3, false, st)) != cudaSuccess) return cuda_fail(e, "outbuf");
+            dout = (float *)c->outbuf.p;
+        }
+        std::vector<bc_shape_t> shapes(2 * (size_t)npairs);
+        std::vector<const float *> q(2 * (size_t)npairs, nullptr);
+        std::vector<PairDesc> pairs(npairs);
+        for (int i = 0; i < npairs; i++) {
+            shapes[2 * i] = As[i];
+            shapes[2 * i + 1] = Bs[i];
+            q[2 * i + 1] = quats + 4 * (size_t)i;
+            pairs[i] = PairDesc{2 * i, 2 * i + 1, (long long)i * N * N * H, (long long)i * N3, i};
+        }
+        if (bc_status s = enqueue(c, shapes, q, pairs, false, dout, keys)) return s;
+        if (peak) {
+            float *dpeak = peak;
+            int *darg = argmax;
+            if (!on_device) {
+                dpeak = (float *)((char *)c->keys.p + key_bytes);
+                darg = (int *)(dpeak + npairs);
+            }
+            if ((e = launch_decode_peaks(keys, npairs, dpeak, darg, st)) != cudaSuccess) return cuda_fail(e, "decode peaks");
+            if (!on_device) {
+                if ((e = cudaMemcpyAsync(peak, dpeak, sizeof(float) * npairs, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                    return cuda_fail(e, "copy peaks");
+                if ((e = cudaMemcpyAsync(argmax, darg, sizeof(int) * npairs, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                    return cuda_fail(e, "copy argmax");
+            }
+        }
+        if (out && !on_device) {
+            if ((e = cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)npairs * N3, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return cuda_fail(e, "copy out");
+        }
+        if (!on_device) return bc_sync(c);
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_pairs: unexpected exception");
+    }
+}
+
 bc_status bc_sweep(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, int k, int batch, float *peak,
                    int *argmax, int out_on_device)
 {

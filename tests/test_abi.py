@@ -20,7 +20,7 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sweep", "bc_sync",
+    for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sweep", "bc_pairs", "bc_sync",
               "bc_last_error", "bc_version", "bc_profile_begin", "bc_profile_end", "bc_stage_name"):
         assert f in names
 

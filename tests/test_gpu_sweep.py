@@ -93,3 +93,33 @@ def test_sweep_receptor_ligand_sampled_rotations(bc):
         grids.append(O.inverse_grid(O.corr_spectrum(fa, fb)))
     check_peaks(peak[pick], arg[pick], grids, "receptor/ligand")
     A.close(); B.close(); ctx.close()
+
+
+def test_ragged_pairs_match_oracle(bc):
+    # Pairs of uneven knot counts (log-uniform in [100, 3000]) in one call; grids and peaks.
+    rng = synth.SplitMix64(77)
+    counts = np.exp(np.log(100) + rng.uniform(8) * (np.log(3000) - np.log(100))).astype(int)
+    N, W = 32, 6
+    ctx = bc.Context(N, W, synth.RADII_2)
+    shapesA, shapesB, hA, hB = [], [], [], []
+    for i in range(4):
+        a = synth.ellipsoid_shape(int(counts[2 * i]), 100 + i)
+        b = synth.torus_shape(int(counts[2 * i + 1]), 200 + i)
+        shapesA.append(a); shapesB.append(b)
+        hA.append(ctx.shape(a.xyz, a.level)); hB.append(ctx.shape(b.xyz, b.level))
+    q = synth.shoemake_quaternions(synth.SplitMix64(78), 4).astype(np.float32)
+    grids, peak, arg = ctx.pairs(hA, hB, q, grids=True, peaks=True)
+    ctx.sync()
+    grids = grids.double().cpu().numpy()
+    peak, arg = peak.cpu().numpy(), arg.cpu().numpy()
+    ref = []
+    for i in range(4):
+        g = O.band_limited_corr(f32(shapesA[i]), f32(shapesB[i]), q[i].astype(np.float64), N)
+        rel = np.linalg.norm(grids[i] - g) / np.linalg.norm(g)
+        print(f"pair {i} ({shapesA[i].n}+{shapesB[i].n} knots): rel-L2 {rel:.3e}")
+        assert rel <= REL_TOL
+        ref.append(g)
+    check_peaks(peak, arg, ref, "ragged pairs")
+    for h in hA + hB:
+        h.close()
+    ctx.close()
