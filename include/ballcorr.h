@@ -137,6 +137,71 @@ bc_status bc_sweep(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quats,
 bc_status bc_pairs(bc_ctx_t ctx, const bc_shape_t *As, const bc_shape_t *Bs, const float *quats, int npairs,
                    float *out, float *peak, int *argmax, int on_device);
 
+/* ---------------------------------------------------------------- learned proposal
+ * Not in the paper: a small network ranks rotations so that only the best
+ * ranked ones get full correlations.  Features of a (rotation, pair):
+ * x = [q / |q| with w >= 0 (4); m_A (BC_MOMENTS); m_B (BC_MOMENTS)], where
+ * m_S[i] = |f^_S(m_i)| / f^_S(0) over the BC_MOMENTS lowest modes of the half
+ * spectrum (m_z >= 0, m != 0, components inside (-N/2, N/2)) ordered by
+ * (|m|^2, m_x, m_y, m_z), for the unrotated shape.  Network: 132 -> H -> H -> 1,
+ * ReLU, FP32 master weights, BF16 operands on the tensor cores with FP32
+ * accumulation, mean squared error, Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Parameter layout (FP32): W1 [H][132], b1 [H], W2 [H][H], b2 [H], w3 [H], b3 [1]. */
+#define BC_MOMENTS 64
+#define BC_MLP_IN 132
+#define BC_TOPK_MAX 16384
+typedef struct bc_mlp_s *bc_mlp_t;
+
+/* out (device, BC_MOMENTS floats) = m_S as above.  Computes S's spectrum with
+ * the correlation kernels (overwrites the context's cached spectrum).
+ * Errors: BC_ERR_ARG (null pointer, empty shape, foreign shape), BC_ERR_CUDA. */
+bc_status bc_shape_moments(bc_ctx_t ctx, bc_shape_t shape, float *out);
+
+/* Number of FP32 parameters of a network with H hidden units. */
+long long bc_mlp_param_count(int hidden);
+
+/* Creates a network on ctx's device and stream; `init` (host) holds the
+ * initial parameters in the layout above.  hidden: multiple of 16 in [16, 1024].
+ * Destroying the context first frees the network's device memory; the handle
+ * then only accepts bc_mlp_destroy. */
+bc_status bc_mlp_create(bc_ctx_t ctx, int hidden, const float *init, bc_mlp_t *out);
+bc_status bc_mlp_destroy(bc_mlp_t net);
+
+/* X (device, n x 144 floats; columns 132..143 are zero) from n device
+ * quaternions (n x 4) and the two moment vectors (device).  A zero quaternion
+ * is reported by the next bc_sync as BC_ERR_ARG. */
+bc_status bc_mlp_features(bc_mlp_t net, const float *quats, int n, const float *moments_a, const float *moments_b,
+                          float *X);
+
+/* y (device, n) = network(X). */
+bc_status bc_mlp_predict(bc_mlp_t net, const float *X, int n, float *y);
+
+/* Gradients of mean((y - t)^2) for targets t (device, n): grads (device, the
+ * parameter layout; may be NULL) and loss (device, 1 float; may be NULL). */
+bc_status bc_mlp_grads(bc_mlp_t net, const float *X, const float *t, int n, float *grads, float *loss);
+
+/* One Adam step on mean((y - t)^2) with learning rate lr; loss as above. */
+bc_status bc_mlp_train_step(bc_mlp_t net, const float *X, const float *t, int n, float lr, float *loss);
+
+/* Reads (get = 1) or writes (get = 0) the parameters and the two Adam moment
+ * vectors (host arrays in the parameter layout; any may be NULL) and the step
+ * count (may be NULL): checkpoint and resume.  Synchronous. */
+bc_status bc_mlp_state(bc_mlp_t net, float *params, float *adam_m, float *adam_v, long long *step, int get);
+
+/* Learned sweep: scores n rotations (device quats, n <= BC_TOPK_MAX) with the
+ * network, keeps the topk best (ties to the lowest index), and computes the
+ * peaks of their full correlations as bc_sweep does.  Outputs (device):
+ * idx[topk] (rotation indices, best score first), peak[topk], argmax[topk],
+ * and scores[n] when not NULL.  Asynchronous.
+ * Errors: BC_ERR_ARG (null pointer, n or topk out of range), BC_ERR_CUDA. */
+bc_status bc_learned_sweep(bc_ctx_t ctx, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
+                           int topk, int *idx, float *peak, int *argmax, float *scores);
+
+/* Top-k selection: idx[0..k) (device) = indices of the k largest of scores[0..n)
+ * (device), largest first, equal scores ordered by lower index.  n <= BC_TOPK_MAX.
+ * Asynchronous on ctx's stream.  Errors: BC_ERR_ARG, BC_ERR_CUDA. */
+bc_status bc_topk(bc_ctx_t ctx, const float *scores, int n, int k, int *idx);
+
 /* Waits for the context stream and reports any device-side error raised by
  * earlier asynchronous calls (BC_ERR_INTERNAL, BC_ERR_TIMEOUT) or CUDA error. */
 bc_status bc_sync(bc_ctx_t ctx);

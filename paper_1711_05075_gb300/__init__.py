@@ -68,6 +68,22 @@ def lib():
         L.bc_sweep.restype = st
         L.bc_pairs.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, i]
         L.bc_pairs.restype = st
+        L.bc_shape_moments.argtypes = [vp, vp, vp]
+        L.bc_mlp_param_count.argtypes = [i]
+        L.bc_mlp_param_count.restype = ctypes.c_longlong
+        L.bc_mlp_create.argtypes = [vp, i, vp, ctypes.POINTER(vp)]
+        L.bc_mlp_destroy.argtypes = [vp]
+        L.bc_mlp_features.argtypes = [vp, vp, i, vp, vp, vp]
+        L.bc_mlp_predict.argtypes = [vp, vp, i, vp]
+        L.bc_mlp_grads.argtypes = [vp, vp, vp, i, vp, vp]
+        L.bc_mlp_train_step.argtypes = [vp, vp, vp, i, ctypes.c_float, vp]
+        L.bc_mlp_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_longlong), i]
+        L.bc_learned_sweep.argtypes = [vp, vp, vp, vp, vp, i, i, vp, vp, vp, vp]
+        L.bc_topk.argtypes = [vp, vp, i, i, vp]
+        L.bc_topk.restype = st
+        for f in ("bc_shape_moments", "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
+                  "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep"):
+            getattr(L, f).restype = st
         for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sync"):
             getattr(L, f).restype = st
         L.bc_last_error.restype = ctypes.c_char_p
@@ -141,6 +157,55 @@ def bc_pairs(ctx, As, Bs, quats, npairs, out, peak, argmax, on_device):
                           int(on_device)))
 
 
+def bc_shape_moments(ctx, shape, out):
+    _check(lib().bc_shape_moments(ctx, shape, _ptr(out)))
+
+
+def bc_mlp_param_count(hidden):
+    return int(lib().bc_mlp_param_count(int(hidden)))
+
+
+def bc_mlp_create(ctx, hidden, init):
+    h = ctypes.c_void_p()
+    init = np.ascontiguousarray(init, dtype=np.float32)
+    _check(lib().bc_mlp_create(ctx, int(hidden), _ptr(init), ctypes.byref(h)))
+    return h
+
+
+def bc_mlp_destroy(net):
+    _check(lib().bc_mlp_destroy(net))
+
+
+def bc_mlp_features(net, quats, n, fa, fb, X):
+    _check(lib().bc_mlp_features(net, _ptr(quats), int(n), _ptr(fa), _ptr(fb), _ptr(X)))
+
+
+def bc_mlp_predict(net, X, n, y):
+    _check(lib().bc_mlp_predict(net, _ptr(X), int(n), _ptr(y)))
+
+
+def bc_mlp_grads(net, X, t, n, grads, loss):
+    _check(lib().bc_mlp_grads(net, _ptr(X), _ptr(t), int(n), _ptr(grads), _ptr(loss)))
+
+
+def bc_mlp_train_step(net, X, t, n, lr, loss):
+    _check(lib().bc_mlp_train_step(net, _ptr(X), _ptr(t), int(n), float(lr), _ptr(loss)))
+
+
+def bc_mlp_state(net, params, m, v, step, get):
+    """step: a ctypes.c_longlong (read or written in place)."""
+    _check(lib().bc_mlp_state(net, _ptr(params), _ptr(m), _ptr(v), ctypes.byref(step), int(get)))
+
+
+def bc_learned_sweep(ctx, net, A, B, quats, n, topk, idx, peak, argmax, scores):
+    _check(lib().bc_learned_sweep(ctx, net, A, B, _ptr(quats), int(n), int(topk), _ptr(idx), _ptr(peak),
+                                  _ptr(argmax), _ptr(scores)))
+
+
+def bc_topk(ctx, scores, n, k, idx):
+    _check(lib().bc_topk(ctx, _ptr(scores), int(n), int(k), _ptr(idx)))
+
+
 def bc_sync(ctx):
     _check(lib().bc_sync(ctx))
 
@@ -197,6 +262,7 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = bc_create(N, W, radii, period, beta, stream=self.stream.cuda_stream)
         self._shapes = weakref.WeakSet()
+        self._nets = weakref.WeakSet()
 
     def shape(self, xyz, level):
         s = Shape(self, xyz, level)
@@ -249,6 +315,8 @@ class Context:
         if self.handle is not None:
             for s in list(self._shapes):
                 s.close()
+            for net in list(self._nets):
+                net.close()
             bc_destroy(self.handle)
             self.handle = None
 
@@ -257,6 +325,86 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+class MLP:
+    """The learned rotation proposal (132 -> H -> H -> 1) on a context's device and stream."""
+
+    def __init__(self, ctx: Context, hidden: int, init):
+        self.ctx, self.hidden = ctx, int(hidden)
+        self.nparams = bc_mlp_param_count(hidden)
+        init = np.ascontiguousarray(init, dtype=np.float32).reshape(-1)
+        assert init.size == self.nparams
+        self.handle = bc_mlp_create(ctx.handle, hidden, init)
+        ctx._nets.add(self)
+
+    def features(self, quats_dev, fa, fb):
+        import torch
+        n = quats_dev.shape[0]
+        X = torch.empty((n, 144), dtype=torch.float32, device="cuda")
+        bc_mlp_features(self.handle, quats_dev, n, fa, fb, X)
+        return X
+
+    def predict(self, X):
+        import torch
+        y = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+        bc_mlp_predict(self.handle, X, X.shape[0], y)
+        return y
+
+    def grads(self, X, t):
+        import torch
+        g = torch.empty(self.nparams, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        bc_mlp_grads(self.handle, X, t, X.shape[0], g, loss)
+        return g, loss
+
+    def train_step(self, X, t, lr, loss=None):
+        bc_mlp_train_step(self.handle, X, t, X.shape[0], lr, loss)
+
+    def state(self):
+        p = np.empty(self.nparams, np.float32)
+        m = np.empty_like(p)
+        v = np.empty_like(p)
+        step = ctypes.c_longlong(0)
+        bc_mlp_state(self.handle, p, m, v, step, 1)
+        return {"params": p, "adam_m": m, "adam_v": v, "step": step.value}
+
+    def load_state(self, st):
+        step = ctypes.c_longlong(int(st["step"]))
+        bc_mlp_state(self.handle, np.ascontiguousarray(st["params"], np.float32),
+                     np.ascontiguousarray(st["adam_m"], np.float32), np.ascontiguousarray(st["adam_v"], np.float32),
+                     step, 0)
+
+    def close(self):
+        if self.handle is not None:
+            bc_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def moments(ctx: Context, shape) -> "torch.Tensor":
+    import torch
+    out = torch.empty(64, dtype=torch.float32, device="cuda")
+    bc_shape_moments(ctx.handle, shape.handle, out)
+    return out
+
+
+def learned_sweep(ctx: Context, net: MLP, A, B, quats_dev, topk):
+    """(idx, peak, argmax, scores) CUDA tensors: network scores of all rotations, the topk
+    best, and the correlation peaks of those."""
+    import torch
+    n = quats_dev.shape[0]
+    idx = torch.empty(topk, dtype=torch.int32, device="cuda")
+    peak = torch.empty(topk, dtype=torch.float32, device="cuda")
+    arg = torch.empty(topk, dtype=torch.int32, device="cuda")
+    scores = torch.empty(n, dtype=torch.float32, device="cuda")
+    bc_learned_sweep(ctx.handle, net.handle, A.handle, B.handle, quats_dev, n, topk, idx, peak, arg, scores)
+    return idx, peak, arg, scores
 
 
 class Shape:

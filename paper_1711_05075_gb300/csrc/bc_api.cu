@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <array>
 #include <new>
 #include <set>
 #include <string>
@@ -85,16 +86,18 @@ struct bc_ctx_s {
     float *deconv = nullptr, *ballft = nullptr;
     float2 *tw_n = nullptr, *tw_N = nullptr;
     float *consts = nullptr; // [0] = exp(beta) / I0(beta)
+    int *modes = nullptr;    // BC_MOMENTS lowest modes of the half spectrum, (m_x, m_y, m_z) each
     int qmax = 0;
     // device status word
     int *err_dev = nullptr;
     // workspaces
-    DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, outbuf, stats, boxes, keys;
+    DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, outbuf, stats, boxes, keys, learn;
     bool boxes_dirty = true; // support-box accumulators need their reset state
     std::vector<char> last_desc;            // descriptors the device copies hold
     void *last_inst_p = nullptr, *last_pairs_p = nullptr;
     bool grid_dirty = false;
     std::set<bc_shape_s *> shapes; // live shapes; orphaned (device memory freed) by bc_destroy
+    std::set<bc_mlp_s *> nets;     // live networks; orphaned the same way
     // profiling
     bool prof_on = false;
     int prof_max = 0, prof_calls = 0;
@@ -110,6 +113,11 @@ struct bc_shape_s {
     float4 *knots = nullptr;
     float rmax = 0.f;
 };
+
+cudaStream_t bc::ctx_stream(bc_ctx_s *c) { return c->stream; }
+void bc::ctx_register_mlp(bc_ctx_s *c, bc_mlp_s *net) { c->nets.insert(net); }
+void bc::ctx_unregister_mlp(bc_ctx_s *c, bc_mlp_s *net) { c->nets.erase(net); }
+int *bc::ctx_err(bc_ctx_s *c) { return c->err_dev; }
 
 static const char *kStageNames[BC_NUM_STAGES] = {"prepare", "spread", "fft_z", "fft_y", "fft_x", "ifft_y", "ifft_z"};
 
@@ -218,6 +226,23 @@ bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
         if ((e = cudaMalloc(&c->tw_n, sizeof(float2) * g.n)) != cudaSuccess) return bail(e, "cudaMalloc tw_n");
         if ((e = cudaMalloc(&c->tw_N, sizeof(float2) * g.N)) != cudaSuccess) return bail(e, "cudaMalloc tw_N");
         if ((e = cudaMalloc(&c->consts, sizeof(float) * 4)) != cudaSuccess) return bail(e, "cudaMalloc consts");
+        {
+            // the BC_MOMENTS lowest modes of the half spectrum (m_z >= 0, m != 0, components
+            // inside (-N/2, N/2)), ordered by (|m|^2, m_x, m_y, m_z)
+            std::vector<std::array<int, 4>> all;
+            const int h = g.N / 2;
+            for (int mx = -h + 1; mx < h; mx++)
+                for (int my = -h + 1; my < h; my++)
+                    for (int mz = 0; mz < h; mz++)
+                        if (mx || my || mz) all.push_back({mx * mx + my * my + mz * mz, mx, my, mz});
+            std::sort(all.begin(), all.end());
+            std::vector<int> tab(3 * BC_MOMENTS);
+            for (int i = 0; i < BC_MOMENTS; i++)
+                for (int j = 0; j < 3; j++) tab[3 * i + j] = all[i][1 + j];
+            if ((e = cudaMalloc(&c->modes, sizeof(int) * tab.size())) != cudaSuccess) return bail(e, "cudaMalloc modes");
+            if ((e = cudaMemcpy(c->modes, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+                return bail(e, "copy modes");
+        }
         if ((e = cudaMalloc(&c->err_dev, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc err");
         if ((e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream)) != cudaSuccess) return bail(e, "memset err");
         if ((e = cudaMemcpyAsync(c->radii_dev, c->radii.data(), sizeof(double) * g.L, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
@@ -244,6 +269,7 @@ bc_status bc_destroy(bc_ctx_t c)
         cudaFree(c->tw_N);
         cudaFree(c->err_dev);
         cudaFree(c->consts);
+        cudaFree(c->modes);
         prof_free(c);
         for (bc_shape_s *s : c->shapes) {
             if (s->knots) cudaFree(s->knots);
@@ -251,7 +277,9 @@ bc_status bc_destroy(bc_ctx_t c)
             s->ctx = nullptr;
         }
         c->shapes.clear();
-        DevBuf *bufs[] = {&c->ku, &c->plan, &c->inst, &c->pairs, &c->grid, &c->z1, &c->y1, &c->h, &c->fa, &c->outbuf, &c->stats, &c->boxes, &c->keys};
+        for (bc_mlp_s *net : c->nets) mlp_orphan(net);
+        c->nets.clear();
+        DevBuf *bufs[] = {&c->ku, &c->plan, &c->inst, &c->pairs, &c->grid, &c->z1, &c->y1, &c->h, &c->fa, &c->outbuf, &c->stats, &c->boxes, &c->keys, &c->learn};
         for (DevBuf *b : bufs) b->release();
         delete c;
         return BC_OK;
@@ -353,6 +381,7 @@ bc_status bc_sync(bc_ctx_t c)
     CK(cudaMemcpy(&herr, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr) {
         CK(cudaMemset(c->err_dev, 0, sizeof(int)));
+        if (herr & 4) return fail(BC_ERR_ARG, "a device-resident rotation had zero norm");
         return fail(BC_ERR_INTERNAL, "device-side check failed (support box exceeded its capacity)");
     }
     return BC_OK;
@@ -423,7 +452,8 @@ bc_status bc_profile_end(bc_ctx_t c, bc_profile *out)
 // N^3 floats at each pair's out_off) and keys (device peak keys at each pair's
 // key) may be null.
 static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std::vector<const float *> &quats,
-                         const std::vector<PairDesc> &pairs, bool cache_first, float *dout, unsigned long long *keys)
+                         const std::vector<PairDesc> &pairs, bool cache_first, float *dout, unsigned long long *keys,
+                         const std::vector<const float *> *qdev = nullptr)
 {
     cudaStream_t st = c->stream;
     const Geometry &g = c->g;
@@ -453,6 +483,7 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
         } else {
             d.q[0] = 1.f;
         }
+        if (qdev) d.qdev = (*qdev)[i];
         koff += s->n;
         max_knots = s->n > max_knots ? s->n : max_knots;
         goff += (long long)L * e * (((e + 31) / 32) * 32) * e; // block-transposed boxes, y padded to 32
@@ -562,6 +593,56 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
         c->last_ninst = ninst;
         c->last_npairs = nmain;
         c->last_inst = inst;
+    }
+    return BC_OK;
+}
+
+// Peaks for k rotations of B (host quaternions qhost, or device quaternions
+// qdev) against A: A's spectrum once into the cache, then batches of
+// rotations folded into peak keys, then keys -> peak / argmax.
+static bc_status sweep_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *qhost, const float *qdev, int k,
+                            int batch, float *peak, int *argmax, int out_on_device)
+{
+    if (batch == 0) batch = 64;
+    const int N = c->g.N, H = c->g.H;
+    cudaStream_t st = c->stream;
+    cudaError_t e;
+    const size_t key_bytes = sizeof(unsigned long long) * (size_t)k;
+    const size_t out_bytes = out_on_device ? 0 : (sizeof(float) + sizeof(int)) * (size_t)k;
+    if ((e = c->keys.ensure(key_bytes + out_bytes, false, st)) != cudaSuccess) return cuda_fail(e, "keys");
+    unsigned long long *keys = (unsigned long long *)c->keys.p;
+    if ((e = cudaMemsetAsync(keys, 0, key_bytes, st)) != cudaSuccess) return cuda_fail(e, "clear keys");
+    {
+        std::vector<bc_shape_t> shapes(1, A);
+        std::vector<const float *> q(1, nullptr);
+        std::vector<PairDesc> pairs(1, PairDesc{0, -1, 0, 0, 0});
+        if (bc_status s = enqueue(c, shapes, q, pairs, true, nullptr, nullptr)) return s;
+    }
+    for (int r0 = 0; r0 < k; r0 += batch) {
+        const int nb = std::min(batch, k - r0);
+        std::vector<bc_shape_t> shapes(nb, B);
+        std::vector<const float *> q(nb, nullptr), qd(nb, nullptr);
+        std::vector<PairDesc> pairs(nb);
+        for (int i = 0; i < nb; i++) {
+            if (qhost) q[i] = qhost + 4 * (size_t)(r0 + i);
+            else qd[i] = qdev + 4 * (size_t)(r0 + i);
+            pairs[i] = PairDesc{-1, i, (long long)i * N * N * H, 0, (long long)(r0 + i)};
+        }
+        if (bc_status s = enqueue(c, shapes, q, pairs, false, nullptr, keys, qhost ? nullptr : &qd)) return s;
+    }
+    float *dpeak = peak;
+    int *darg = argmax;
+    if (!out_on_device) {
+        dpeak = (float *)((char *)c->keys.p + key_bytes);
+        darg = (int *)(dpeak + k);
+    }
+    if ((e = launch_decode_peaks(keys, k, dpeak, darg, st)) != cudaSuccess) return cuda_fail(e, "decode peaks");
+    if (!out_on_device) {
+        if ((e = cudaMemcpyAsync(peak, dpeak, sizeof(float) * (size_t)k, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(e, "copy peaks");
+        if ((e = cudaMemcpyAsync(argmax, darg, sizeof(int) * (size_t)k, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(e, "copy argmax");
+        return bc_sync(c);
     }
     return BC_OK;
 }
@@ -687,51 +768,64 @@ bc_status bc_sweep(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, i
         if (k < 1 || k > (1 << 24)) return fail(BC_ERR_ARG, "bc_sweep: k must be in [1, 2^24]");
         if (batch < 0 || batch > 65534) return fail(BC_ERR_ARG, "bc_sweep: batch must be in [0, 65534]");
         if (bc_status s = check_quats(quats, k, "bc_sweep")) return s;
-        if (batch == 0) batch = 64;
-        const int N = c->g.N, H = c->g.H;
-        cudaStream_t st = c->stream;
-        cudaError_t e;
-        // one peak key per rotation, then the decoded peaks (device scratch when the caller wants host output)
-        const size_t key_bytes = sizeof(unsigned long long) * (size_t)k;
-        const size_t out_bytes = out_on_device ? 0 : (sizeof(float) + sizeof(int)) * (size_t)k;
-        if ((e = c->keys.ensure(key_bytes + out_bytes, false, st)) != cudaSuccess) return cuda_fail(e, "keys");
-        unsigned long long *keys = (unsigned long long *)c->keys.p;
-        if ((e = cudaMemsetAsync(keys, 0, key_bytes, st)) != cudaSuccess) return cuda_fail(e, "clear keys");
-        // A's spectrum once
-        {
-            std::vector<bc_shape_t> shapes(1, A);
-            std::vector<const float *> q(1, nullptr);
-            std::vector<PairDesc> pairs(1, PairDesc{0, -1, 0, 0, 0});
-            if (bc_status s = enqueue(c, shapes, q, pairs, true, nullptr, nullptr)) return s;
-        }
-        for (int r0 = 0; r0 < k; r0 += batch) {
-            const int nb = std::min(batch, k - r0);
-            std::vector<bc_shape_t> shapes(nb, B);
-            std::vector<const float *> q(nb);
-            std::vector<PairDesc> pairs(nb);
-            for (int i = 0; i < nb; i++) {
-                q[i] = quats + 4 * (size_t)(r0 + i);
-                pairs[i] = PairDesc{-1, i, (long long)i * N * N * H, 0, (long long)(r0 + i)};
-            }
-            if (bc_status s = enqueue(c, shapes, q, pairs, false, nullptr, keys)) return s;
-        }
-        float *dpeak = peak;
-        int *darg = argmax;
-        if (!out_on_device) {
-            dpeak = (float *)((char *)c->keys.p + key_bytes);
-            darg = (int *)(dpeak + k);
-        }
-        if ((e = launch_decode_peaks(keys, k, dpeak, darg, st)) != cudaSuccess) return cuda_fail(e, "decode peaks");
-        if (!out_on_device) {
-            if ((e = cudaMemcpyAsync(peak, dpeak, sizeof(float) * (size_t)k, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-                return cuda_fail(e, "copy peaks");
-            if ((e = cudaMemcpyAsync(argmax, darg, sizeof(int) * (size_t)k, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-                return cuda_fail(e, "copy argmax");
-            return bc_sync(c);
-        }
-        return BC_OK;
+        return sweep_impl(c, A, B, quats, nullptr, k, batch, peak, argmax, out_on_device);
     } catch (...) {
         return fail(BC_ERR_INTERNAL, "bc_sweep: unexpected exception");
+    }
+}
+
+bc_status bc_shape_moments(bc_ctx_t c, bc_shape_t S, float *out)
+{
+    try {
+        if (!c || !S || !out) return fail(BC_ERR_ARG, "bc_shape_moments: null argument");
+        if (S->ctx != c) return fail(BC_ERR_ARG, "bc_shape_moments: shape belongs to another context");
+        if (S->n == 0) return fail(BC_ERR_ARG, "bc_shape_moments: empty shape (f(0) = 0)");
+        std::vector<bc_shape_t> shapes(1, S);
+        std::vector<const float *> q(1, nullptr);
+        std::vector<PairDesc> pairs(1, PairDesc{0, -1, 0, 0, 0});
+        if (bc_status s = enqueue(c, shapes, q, pairs, true, nullptr, nullptr)) return s;
+        cudaError_t e = launch_moments((const float2 *)c->fa.p, c->modes, BC_MOMENTS, c->g.N, c->g.H, out, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "moments");
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_shape_moments: unexpected exception");
+    }
+}
+
+bc_status bc_topk(bc_ctx_t c, const float *scores, int n, int k, int *idx)
+{
+    if (!c || !scores || !idx) return fail(BC_ERR_ARG, "bc_topk: null argument");
+    if (n < 1 || n > BC_TOPK_MAX || k < 1 || k > n) return fail(BC_ERR_ARG, "bc_topk: need 1 <= k <= n <= 16384");
+    cudaError_t e = launch_topk(scores, n, k, idx, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "top-k");
+    return BC_OK;
+}
+
+bc_status bc_learned_sweep(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n, int topk,
+                           int *idx, float *peak, int *argmax, float *scores)
+{
+    try {
+        if (!c || !net || !A || !B || !quats || !idx || !peak || !argmax)
+            return fail(BC_ERR_ARG, "bc_learned_sweep: null argument");
+        if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_learned_sweep: shapes belong to another context");
+        if (n < 1 || n > BC_TOPK_MAX) return fail(BC_ERR_ARG, "bc_learned_sweep: n must be in [1, 16384]");
+        if (topk < 1 || topk > n) return fail(BC_ERR_ARG, "bc_learned_sweep: topk must be in [1, n]");
+        cudaStream_t st = c->stream;
+        cudaError_t e;
+        // scratch: moments (2 x 64), features (n x 144), scores (n), selected rotations (topk x 4)
+        const size_t fbytes = sizeof(float) * (2 * BC_MOMENTS + (size_t)n * 144 + n + 4 * (size_t)topk);
+        if ((e = c->learn.ensure(fbytes, false, st)) != cudaSuccess) return cuda_fail(e, "learned scratch");
+        float *fa = (float *)c->learn.p, *fb = fa + BC_MOMENTS, *X = fb + BC_MOMENTS;
+        float *sc = X + (size_t)n * 144, *qsel = sc + n;
+        if (bc_status s = bc_shape_moments(c, A, fa)) return s;
+        if (bc_status s = bc_shape_moments(c, B, fb)) return s;
+        if (bc_status s = bc_mlp_features(net, quats, n, fa, fb, X)) return s;
+        if (bc_status s = bc_mlp_predict(net, X, n, scores ? scores : sc)) return s;
+        if ((e = launch_topk(scores ? scores : sc, n, topk, idx, st)) != cudaSuccess) return cuda_fail(e, "top-k");
+        if ((e = launch_gather_quats(quats, idx, topk, qsel, st)) != cudaSuccess) return cuda_fail(e, "gather rotations");
+        return sweep_impl(c, A, B, nullptr, qsel, topk, 0, peak, argmax, 1);
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_learned_sweep: unexpected exception");
     }
 }
 

@@ -5,6 +5,9 @@
 #include <string>
 #include <cuda_runtime.h>
 
+struct bc_ctx_s;
+struct bc_mlp_s;
+
 namespace bc {
 
 // Per-instance description: one shape (A, or B under one rotation) whose
@@ -19,6 +22,7 @@ struct InstDesc {
     long long y1_off;   // float2 offset of its y-transformed planes
     float q[4];         // rotation (w, x, y, z), unit; identity for A
     const float4 *knots; // the shape's knots (x, y, z, level bits)
+    const float *qdev;   // when not null: the rotation is read from this device address instead of q
 };
 
 // Device-computed support box of one instance in fine-grid cells.
@@ -84,5 +88,20 @@ bool supported_N(int N);
 
 // Sets the calling thread's message returned by bc_last_error() (bc_api.cu).
 void set_last_error(const std::string &msg);
+
+// Context accessors for the other translation units (bc_api.cu).
+cudaStream_t ctx_stream(bc_ctx_s *c);
+int *ctx_err(bc_ctx_s *c);
+// Networks are registered with their context; destroying the context orphans
+// them (their device memory is freed and their context pointer cleared).
+void ctx_register_mlp(bc_ctx_s *c, bc_mlp_s *net);
+void ctx_unregister_mlp(bc_ctx_s *c, bc_mlp_s *net);
+void mlp_orphan(bc_mlp_s *net); // bc_mlp.cu
+
+// Learned-proposal helpers (bc_mlp.cu).
+cudaError_t launch_topk(const float *scores, int n, int k, int *idx, cudaStream_t s);
+cudaError_t launch_gather_quats(const float *q, const int *idx, int k, float *out, cudaStream_t s);
+// out[i] = |F(m_i)| / F(0) for the modes[i] = (m_x, m_y, m_z), i < count, of a cached half spectrum.
+cudaError_t launch_moments(const float2 *F, const int *modes, int count, int N, int H, float *out, cudaStream_t s);
 
 } // namespace bc

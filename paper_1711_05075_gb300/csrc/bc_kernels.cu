@@ -168,6 +168,12 @@ k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 *ku, int *bb)
     const int j = blockIdx.x * PREP_THREADS + threadIdx.x;
     if (blockIdx.x * PREP_THREADS >= d.nknots) return; // whole block beyond this instance
     float qw = d.q[0], qx = d.q[1], qy = d.q[2], qz = d.q[3];
+    if (d.qdev) {
+        qw = d.qdev[0];
+        qx = d.qdev[1];
+        qy = d.qdev[2];
+        qz = d.qdev[3];
+    }
     const float s = 1.0f / sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
     qw *= s; qx *= s; qy *= s; qz *= s;
     const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);

@@ -246,3 +246,17 @@ def translation_sample(N: int, count: int, seed: int = 0) -> np.ndarray:
                 if len(out) == count:
                     break
     return np.sort(np.asarray(out, dtype=np.int64))
+
+
+def mlp_init(hidden: int, seed: int, in_features: int = 132) -> np.ndarray:
+    """Initial network parameters (FP32, layout W1 [H][132], b1, W2 [H][H], b2, w3, b3):
+    He-uniform weights U(-sqrt(6/fan_in), sqrt(6/fan_in)) from splitmix64, zero biases."""
+    rng = SplitMix64(seed)
+    H = hidden
+
+    def u(fan_in, count):
+        lim = math.sqrt(6.0 / fan_in)
+        return (rng.uniform(count) * 2.0 - 1.0) * lim
+
+    parts = [u(in_features, H * in_features), np.zeros(H), u(H, H * H), np.zeros(H), u(H, H), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)

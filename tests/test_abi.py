@@ -15,13 +15,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "ballcorr.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(bc_[a-z_]+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:[a-z_]+\s+)*[a-z_]+\s*\*?\s*(bc_[a-z_]+)\s*\(", src, flags=re.M)))
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sweep", "bc_pairs", "bc_sync",
-              "bc_last_error", "bc_version", "bc_profile_begin", "bc_profile_end", "bc_stage_name"):
+              "bc_last_error", "bc_version", "bc_profile_begin", "bc_profile_end", "bc_stage_name",
+              "bc_shape_moments", "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
+              "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep", "bc_mlp_param_count", "bc_topk"):
         assert f in names
 
 
@@ -70,3 +72,6 @@ def test_null_arguments_are_rejected():
     assert [bc.lib().bc_stage_name(i).decode() for i in range(7)] == [
         "prepare", "spread", "fft_z", "fft_y", "fft_x", "ifft_y", "ifft_z"]
     assert bc.lib().bc_stage_name(7).decode() == ""
+    assert L.bc_mlp_create(None, 64, None, None) == 1
+    assert L.bc_mlp_destroy(None) == 0
+    assert bc.bc_mlp_param_count(256) == 256 * 132 + 256 + 256 * 256 + 256 + 256 + 1

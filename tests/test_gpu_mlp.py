@@ -1,0 +1,172 @@
+"""GPU learned proposal: forward, gradients and Adam against the FP64 MLP oracle
+(BF16 rounding emulated where the GPU rounds), moment features against the
+spectrum oracle, top-k against a stable sort, checkpoint/resume, and the
+learned sweep against the plain sweep of the same rotations."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp as M
+from paper_1711_05075_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-2  # rel-L2 per parameter tensor (BF16 operands, FP32 accumulation)
+
+
+@pytest.fixture(scope="module")
+def bc():
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+    torch.cuda.set_device(0)
+    import paper_1711_05075_gb300 as m
+    return m
+
+
+def split(flat, H):
+    o = 0
+    out = {}
+    for k, shape in (("W1", (H, 132)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)), ("b3", (1,))):
+        size = int(np.prod(shape))
+        out[k] = np.asarray(flat[o:o + size], dtype=np.float64).reshape(shape)
+        o += size
+    return out
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-30))
+
+
+def problem(H=64, n=200, seed=0):
+    init = synth.mlp_init(H, seed)
+    rng = synth.SplitMix64(seed + 1)
+    q = synth.shoemake_quaternions(rng, n)
+    fa, fb = rng.uniform(64), rng.uniform(64)
+    t = (np.sin(3 * q[:, 1]) + q[:, 2] * q[:, 3] + 0.1 * fa.sum()).astype(np.float32)
+    return init, q.astype(np.float32), fa.astype(np.float32), fb.astype(np.float32), t
+
+
+@pytest.mark.parametrize("H", [64, 256])
+def test_forward_and_gradients_match_oracle(bc, H):
+    init, q, fa, fb, t = problem(H)
+    ctx = bc.Context(32, 6, synth.RADII_2)
+    net = bc.MLP(ctx, H, init)
+    dev = torch.device("cuda")
+    X = net.features(torch.tensor(q, device=dev), torch.tensor(fa, device=dev), torch.tensor(fb, device=dev))
+    Xh = X.cpu().numpy()
+    Xo = M.features(q.astype(np.float64), fa.astype(np.float64), fb.astype(np.float64))
+    np.testing.assert_allclose(Xh[:, :132], Xo, rtol=1e-6, atol=1e-7)
+    assert np.all(Xh[:, 132:] == 0)
+    y = net.predict(X).cpu().numpy()
+    p = split(init, H)
+    yo, _ = M.forward(p, Xh[:, :132].astype(np.float64), bf=True)
+    assert rel(y, yo) < 1e-3, rel(y, yo)  # FP32 accumulation of BF16 products
+    g, loss = net.grads(X, torch.tensor(t, device=dev))
+    g = split(g.cpu().numpy(), H)
+    lo, go = M.loss_and_grads(p, Xh[:, :132].astype(np.float64), t.astype(np.float64), bf=True)
+    assert abs(float(loss.item()) - lo) <= 1e-4 * abs(lo)
+    for k in go:
+        r = rel(g[k], go[k])
+        print(f"H={H} grad {k}: rel-L2 {r:.2e}")
+        assert r < GRAD_TOL, (k, r)
+    net.close()
+    ctx.close()
+
+
+def test_adam_step_matches_oracle(bc):
+    H = 64
+    init, q, fa, fb, t = problem(H, seed=3)
+    ctx = bc.Context(32, 6, synth.RADII_2)
+    net = bc.MLP(ctx, H, init)
+    dev = torch.device("cuda")
+    X = net.features(torch.tensor(q, device=dev), torch.tensor(fa, device=dev), torch.tensor(fb, device=dev))
+    g, _ = net.grads(X, torch.tensor(t, device=dev))
+    net.train_step(X, torch.tensor(t, device=dev), 1e-3)
+    st = net.state()
+    p = split(init, H)
+    M.adam_step(p, split(g.cpu().numpy(), H), {}, lr=1e-3)
+    got = split(st["params"], H)
+    for k in p:
+        np.testing.assert_allclose(got[k], p[k], rtol=1e-5, atol=1e-6)
+    assert st["step"] == 1
+    net.close()
+    ctx.close()
+
+
+def test_training_reduces_loss_and_resume_is_exact(bc):
+    H = 64
+    init, q, fa, fb, t = problem(H, n=512, seed=5)
+    ctx = bc.Context(32, 6, synth.RADII_2)
+    dev = torch.device("cuda")
+    qd, fad, fbd, td = (torch.tensor(a, device=dev) for a in (q, fa, fb, t))
+    net = bc.MLP(ctx, H, init)
+    X = net.features(qd, fad, fbd)
+    loss = torch.empty(1, device=dev)
+    net.grads(X, td)
+    first = None
+    for i in range(200):
+        net.train_step(X, td, 3e-3, loss)
+        if i == 0:
+            first = float(loss.item())
+        if i == 99:
+            ckpt = net.state()
+    last = float(loss.item())
+    final = net.state()["params"]
+    print(f"loss {first:.4f} -> {last:.4f}")
+    assert last < 0.3 * first
+    net2 = bc.MLP(ctx, H, init)
+    net2.load_state(ckpt)
+    for i in range(100):
+        net2.train_step(X, td, 3e-3)
+    np.testing.assert_array_equal(net2.state()["params"], final)  # deterministic resume
+    net.close()
+    net2.close()
+    ctx.close()
+
+
+def test_moments_match_oracle(bc):
+    wl = synth.small_pair(2)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    for S in (wl.A, wl.B):
+        h = ctx.shape(S.xyz, S.level)
+        got = bc.moments(ctx, h).cpu().numpy()
+        spec = O.shape_spectrum(S.xyz.astype(np.float32).astype(np.float64), S.level, S.radii, wl.N)
+        ref = M.moments(spec, M.moment_modes(wl.N))
+        np.testing.assert_allclose(got, ref, rtol=5e-5, atol=1e-7)
+        h.close()
+    ctx.close()
+
+
+def test_topk_is_a_stable_descending_selection(bc):
+    rng = np.random.default_rng(0)
+    ctx = bc.Context(32, 6, synth.RADII_2)
+    for n, k in ((1000, 10), (16384, 256), (5, 5), (3, 1)):
+        s = rng.integers(0, 50, size=n).astype(np.float32) * 0.5 - 7.0  # many ties, negatives
+        ref = np.lexsort((np.arange(n), -s))[:k]
+        idx = torch.empty(k, dtype=torch.int32, device="cuda")
+        bc.bc_topk(ctx.handle, torch.tensor(s, device="cuda"), n, k, idx)
+        np.testing.assert_array_equal(idx.cpu().numpy(), ref)
+    ctx.close()
+
+
+def test_learned_sweep_selects_and_scores_consistently(bc):
+    wl = synth.small_pair(7)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    A, B = ctx.shape(wl.A.xyz, wl.A.level), ctx.shape(wl.B.xyz, wl.B.level)
+    net = bc.MLP(ctx, 64, synth.mlp_init(64, 9))
+    q = torch.tensor(synth.shoemake_quaternions(synth.SplitMix64(4), 3000).astype(np.float32), device="cuda")
+    idx, peak, arg, scores = bc.learned_sweep(ctx, net, A, B, q, 40)
+    s = scores.cpu().numpy()
+    ref = np.lexsort((np.arange(s.size), -s))[:40]
+    np.testing.assert_array_equal(idx.cpu().numpy(), ref)
+    # the network's scores are its prediction on the documented features
+    fa, fb = bc.moments(ctx, A), bc.moments(ctx, B)
+    np.testing.assert_allclose(s, net.predict(net.features(q, fa, fb)).cpu().numpy(), rtol=1e-6)
+    # the selected rotations' peaks equal the plain sweep's peaks for the same rotations
+    sel = q.cpu().numpy()[ref]
+    p2, a2 = ctx.sweep(A, B, sel)
+    np.testing.assert_allclose(peak.cpu().numpy(), p2.cpu().numpy(), rtol=1e-5)
+    net.close(); A.close(); B.close(); ctx.close()
