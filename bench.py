@@ -316,6 +316,157 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ learned proposal
+def run_learned(args):
+    """Train the rotation-proposal network on peaks from the batched sweep and measure,
+    on held-out receptor/ligand pairs, the recall of the exhaustive best rotation within
+    the network's top-k and the effective poses/s of the learned sweep."""
+    import torch
+    import paper_1711_05075_gb300 as bc
+    from paper_1711_05075_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    N, W, H = 96, 8, 256
+    stream = torch.cuda.current_stream(dev)
+    ctx = bc.Context(N, W, synth.RADII_4, stream=stream)
+    net = bc.MLP(ctx, H, synth.mlp_init(H, 7))
+
+    def pair(seed):
+        return (synth.ellipsoid_union_shape(50000, seed),
+                synth.torus_shape(5000, seed + 100000, synth.RADII_4, synth.PROBS_4))
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # ---- training data from the batched sweep
+    t_data = time.perf_counter()
+    Xs, ts = [], []
+    for seed in range(1, 1 + args.train_pairs):
+        A, B = pair(seed)
+        hA, hB = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
+        q = synth.shoemake_quaternions(synth.SplitMix64(seed + 200000), args.train_rot).astype(np.float32)
+        peak, _ = ctx.sweep(hA, hB, q, batch=256)
+        fa, fb = bc.moments(ctx, hA), bc.moments(ctx, hB)
+        Xs.append(net.features(torch.tensor(q, device=dev), fa, fb))
+        z = (peak - peak.mean()) / peak.std()
+        ts.append(z)
+        # rotation augmentation: (S A, S R B) has the same peak over translations as (A, R B)
+        rng_aug = synth.SplitMix64(seed + 500000)
+        for s_q in synth.shoemake_quaternions(rng_aug, args.augment):
+            hS = ctx.shape(synth.rotate_points(A.xyz, s_q), A.level)
+            Xs.append(net.features(torch.tensor(synth.compose_quaternions(s_q, q).astype(np.float32), device=dev),
+                                   bc.moments(ctx, hS), fb))
+            ts.append(z)
+            hS.close()
+        hA.close()
+        hB.close()
+    X, T = torch.cat(Xs), torch.cat(ts)
+    torch.cuda.synchronize(dev)
+    t_data = time.perf_counter() - t_data
+
+    # ---- training (Adam, mini-batches in a seeded order)
+    n = X.shape[0]
+    bs, lr = args.batch, args.lr
+    order_rng = synth.SplitMix64(99)
+    loss = torch.empty(1, device=dev)
+    t_train = time.perf_counter()
+    steps = 0
+    for ep in range(args.epochs):
+        perm = torch.tensor(np.argsort(order_rng.uniform(n)), device=dev)
+        lr_ep = lr * 0.5 * (1 + math.cos(math.pi * ep / args.epochs))
+        for b0 in range(0, n - bs + 1, bs):
+            sel = perm[b0:b0 + bs]
+            net.train_step(X[sel].contiguous(), T[sel].contiguous(), lr_ep, loss)
+            steps += 1
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t_train
+    final_loss = float(loss.item())
+
+    # ---- held-out evaluation
+    K, R = args.topk, args.eval_rot
+    hits, hits_tol, rand_hits, regrets, test_mse = 0, 0, 0, [], []
+    ms_ex, ms_learn = [], []
+    for seed in range(1001, 1001 + args.eval_pairs):
+        A, B = pair(seed)
+        hA, hB = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
+        qn = synth.shoemake_quaternions(synth.SplitMix64(seed + 300000), R).astype(np.float32)
+        qd = torch.tensor(qn, device=dev)
+        e0, e1, e2 = ev(), ev(), ev()
+        e0.record(stream)
+        peak, _ = ctx.sweep(hA, hB, qn, batch=256)
+        e1.record(stream)
+        idx, psel, _, _ = bc.learned_sweep(ctx, net, hA, hB, qd, K)
+        e2.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_ex.append(e0.elapsed_time(e1))
+        ms_learn.append(e1.elapsed_time(e2))
+        p = peak.cpu().numpy()
+        # held-out fit of the network on this pair's standardised peaks
+        fa, fb = bc.moments(ctx, hA), bc.moments(ctx, hB)
+        pred = net.predict(net.features(qd, fa, fb)).cpu().numpy()
+        z = (p - p.mean()) / p.std()
+        test_mse.append(float(np.mean((pred - z) ** 2)))
+        best = int(np.argmax(p))  # first maximum = lowest index on ties
+        chosen = set(idx.cpu().numpy().tolist())
+        hits += best in chosen
+        top = p[list(chosen)].max()
+        regrets.append(float(top / p[best]))
+        hits_tol += top >= p[best] * (1 - 1e-3)
+        rnd = set(np.argsort(synth.SplitMix64(seed + 400000).uniform(R))[:K].tolist())
+        rand_hits += best in rnd
+        hA.close()
+        hB.close()
+
+    # ---- plain per-rotation reference (one bc_correlate call per rotation, A recomputed)
+    A, B = pair(1001)
+    hA, hB = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
+    qn = synth.shoemake_quaternions(synth.SplitMix64(5), 64).astype(np.float32)
+    out = torch.empty((1, N, N, N), device=dev)
+    for r in range(3):
+        ctx.correlate(hA, hB, qn[r:r + 1], out)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    for r in range(64):
+        ctx.correlate(hA, hB, qn[r:r + 1], out)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_plain = e0.elapsed_time(e1) / 64
+    hA.close()
+    hB.close()
+
+    poses = R * N ** 3
+    plain = N ** 3 / (ms_plain * 1e-3)
+    batched = poses / (np.mean(ms_ex) * 1e-3)
+    learned = poses / (np.mean(ms_learn) * 1e-3)
+    line = {
+        "metric": METRIC, "workload": "learned rotation proposal", "unit": UNIT, "n_gpus": 1,
+        "config": {"N": N, "W": W, "receptor_knots": 50000, "ligand_knots": 5000, "levels": list(synth.RADII_4),
+                   "train_pairs": args.train_pairs, "train_rotations_per_pair": args.train_rot,
+                   "eval_pairs": args.eval_pairs, "eval_rotations_per_pair": R, "topk": K, "hidden": H,
+                   "epochs": args.epochs, "adam_steps": steps, "batch": bs, "lr": lr,
+                   "rotation_augmentation_per_pair": args.augment},
+        "plain_per_rotation_poses_s": plain,
+        "batched_exhaustive_poses_s": batched,
+        "learned_effective_poses_s": learned,
+        "learned_vs_plain": learned / plain, "batched_vs_plain": batched / plain,
+        "recall_best_in_topk": hits / args.eval_pairs,
+        "recall_within_1e-3_of_best": hits_tol / args.eval_pairs,
+        "random_topk_recall": rand_hits / args.eval_pairs,
+        "mean_peak_ratio_topk_over_best": float(np.mean(regrets)),
+        "min_peak_ratio_topk_over_best": float(np.min(regrets)),
+        "ms_exhaustive_sweep": float(np.mean(ms_ex)), "ms_learned_sweep": float(np.mean(ms_learn)),
+        "ms_plain_per_rotation": ms_plain, "final_train_loss": final_loss,
+        "heldout_mse_standardised": float(np.mean(test_mse)),
+        "s_label_generation": t_data, "s_training": t_train,
+        "dtype": "f32 correlation, bf16 x bf16 -> f32 network", "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -325,6 +476,18 @@ def main():
     ap.add_argument("--ref-fraction", type=float, default=0.25,
                     help="knot fraction of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["scale", "learned"], default="scale",
+                    help="scale: the 20k+20k-ball N=128 correlation (default); learned: the rotation-proposal study")
+    ap.add_argument("--train-pairs", type=int, default=100)
+    ap.add_argument("--train-rot", type=int, default=2000)
+    ap.add_argument("--eval-pairs", type=int, default=20)
+    ap.add_argument("--eval-rot", type=int, default=16384)
+    ap.add_argument("--topk", type=int, default=256)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--augment", type=int, default=32,
+                    help="extra random orientations of each training receptor (rotation augmentation)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
 
@@ -333,6 +496,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "learned":
+        return run_learned(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

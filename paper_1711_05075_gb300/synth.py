@@ -260,3 +260,26 @@ def mlp_init(hidden: int, seed: int, in_features: int = 132) -> np.ndarray:
 
     parts = [u(in_features, H * in_features), np.zeros(H), u(H, H * H), np.zeros(H), u(H, H), np.zeros(1)]
     return np.concatenate(parts).astype(np.float32)
+
+
+def compose_quaternions(s, q) -> np.ndarray:
+    """Hamilton products s * q_i (rotation by q_i followed by s), canonicalised to w >= 0."""
+    s = np.asarray(s, dtype=np.float64).reshape(4)
+    q = np.asarray(q, dtype=np.float64).reshape(-1, 4)
+    w1, x1, y1, z1 = s
+    w2, x2, y2, z2 = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    out = np.stack([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2,
+                    w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                    w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2,
+                    w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2], axis=1)
+    out[out[:, 0] < 0] *= -1.0
+    return out
+
+
+def rotate_points(xyz, q) -> np.ndarray:
+    """Input transform for augmentation: points rotated by the unit quaternion q (w, x, y, z)."""
+    w, x, y, z = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
+    R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+    return np.asarray(xyz, dtype=np.float64) @ R.T
