@@ -73,7 +73,9 @@ typedef struct {
     double period;             /* P > 0: the translation grid covers [-P/2, P/2)^3 */
     int level_count;           /* L, 1..BC_MAX_LEVELS */
     const double *level_radii; /* host array of L radii (> 0); copied */
-    int precision;             /* 0 = FP32 (the only value accepted) */
+    int precision;             /* 0 = FP32; 1 = the radix-8 stages of the forward transforms run as
+                                  BF16 hi+lo split DFT matmuls on the tensor cores with FP32
+                                  accumulation (built for N = 32 and 256) */
 } bc_params;
 
 /* Creates a context on the current CUDA device bound to `cuda_stream`

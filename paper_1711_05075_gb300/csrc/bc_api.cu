@@ -171,7 +171,9 @@ bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
     try {
         if (!p || !out) return fail(BC_ERR_ARG, "bc_create: null pointer");
         *out = nullptr;
-        if (p->precision != 0) return fail(BC_ERR_UNSUPPORTED, "bc_create: only precision 0 (FP32) is supported");
+        if (p->precision != 0 && p->precision != 1) return fail(BC_ERR_UNSUPPORTED, "bc_create: precision must be 0 or 1");
+        if (p->precision == 1 && !supported_split(p->N))
+            return fail(BC_ERR_UNSUPPORTED, "bc_create: precision 1 (split BF16) is built for N = 32 and 256");
         if (p->sigma != 2) return fail(BC_ERR_UNSUPPORTED, "bc_create: sigma must be 2");
         if (!supported_N(p->N)) return fail(BC_ERR_UNSUPPORTED, "bc_create: N must be one of 32, 64, 96, 128, 256");
         if (p->W < 2 || p->W > 10 || p->W > p->N) return fail(BC_ERR_ARG, "bc_create: W must be in [2, 10] and <= N");
@@ -210,6 +212,7 @@ bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
         g.W = p->W;
         g.L = p->level_count;
         g.H = p->N / 2;
+        g.prec = p->precision;
         g.beta = (float)beta;
         g.n_over_P = (float)(g.n / p->period);
         g.inv_P3 = (float)(1.0 / (p->period * p->period * p->period));

@@ -16,6 +16,7 @@
 // scaling.  The twiddle table holds exp(-2 pi i k/NF), k < NF, rounded once
 // from FP64; the inverse conjugates it.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace bc {
@@ -220,6 +221,18 @@ struct FirstInputs {
                 v[it][r] = ((TOT % NT) == 0 || idx < TOT) ? src(c, j + r * NB) : make_float2(0.f, 0.f);
         }
     }
+    // Writes the loaded values to their positions of a tile (tile[pos * C + c]).
+    __device__ __forceinline__ void scatter(float2 *tile) const
+    {
+#pragma unroll
+        for (int it = 0; it < IT; it++) {
+            const int idx = (int)threadIdx.x + it * NT;
+            if ((TOT % NT) != 0 && idx >= TOT) break;
+            const int c = idx % C, j = idx / C;
+#pragma unroll
+            for (int r = 0; r < R; r++) tile[(j + r * NB) * C + c] = v[it][r];
+        }
+    }
     // visit(c, pos) for every position load() read.
     template <class Vis>
     __device__ __forceinline__ void for_each(Vis visit) const
@@ -305,6 +318,149 @@ __device__ __forceinline__ void rr_rest(float2 *s0, float2 *s1, const float2 *tw
         rr_last<NF, R::r2, R::r0 * R::r1, INV, C, NT>(s1, tw, sink);
     } else {
         rr_last<NF, R::r1, R::r0, INV, C, NT>(s0, tw, sink);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Split-precision radix-8 stage on the tensor cores.  The 8-point DFT of a
+// butterfly is y = F x with F[r'][r] = exp(-+2 pi i r r' / 8); with complex
+// numbers as (re, im) pairs it is a 16 x 16 real matrix acting on a 16-vector,
+// so one mma.m16n8k16 (A = F, B = the inputs of 8 butterflies, one per column)
+// transforms 8 butterflies.  Both F and the twiddled inputs are split into
+// BF16 hi + lo parts (hi = bf16(v), lo = bf16(v - hi)); the product is formed
+// as F_hi x_hi + F_hi x_lo + F_lo x_hi with FP32 accumulation (the lo x lo term,
+// of relative size 2^-32, is dropped).  Lane (g, t) of a warp loads inputs
+// r = t and r = t + 4 of butterfly g of the group (the B fragment layout) and
+// receives output components g and g + 8 of butterflies 2t and 2t + 1.
+__device__ __forceinline__ float dft8_entry(int m, int k, bool inv)
+{
+    // A[m][k], m = 2 r' + p, k = 2 r + q: the 2 x 2 real block of exp(-+i theta), theta = 2 pi r r' / 8
+    const float h = 0.70710678118654752440f;
+    const int e = ((m >> 1) * (k >> 1)) & 7;
+    // cos and sin of e pi / 4
+    const float c = e == 0 ? 1.f : e == 4 ? -1.f : (e == 2 || e == 6) ? 0.f : (e == 1 || e == 7) ? h : -h;
+    const float sv = e == 2 ? 1.f : e == 6 ? -1.f : (e == 0 || e == 4) ? 0.f : (e == 1 || e == 3) ? h : -h;
+    const float s = inv ? -sv : sv;
+    const int p = m & 1, q = k & 1;
+    return p == 0 ? (q == 0 ? c : s) : (q == 0 ? -s : c);
+}
+
+__device__ __forceinline__ unsigned bf2(float lo_elem, float hi_elem)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem); // .x = first (lower 16 bits)
+    return *reinterpret_cast<unsigned *>(&v);
+}
+
+__device__ __forceinline__ void split_bf16(float v, float &hi, float &lo)
+{
+    hi = __bfloat162float(__float2bfloat16_rn(v));
+    lo = v - hi;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int NF, int NS, bool INV, int C, int NT>
+__device__ __forceinline__ void tc_stage8(const float2 *__restrict__ in, float2 *__restrict__ out,
+                                          const float2 *__restrict__ tw)
+{
+    constexpr int R = 8, NB = NF / R, TOT = NB * C, GROUPS = TOT / 8;
+    static_assert(TOT % 8 == 0, "groups of 8 butterflies");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    // A fragments of F, split into hi and lo
+    unsigned ahi[4], alo[4];
+    {
+        const int mm[4] = {g, g + 8, g, g + 8};
+        const int kk[4] = {2 * t, 2 * t, 2 * t + 8, 2 * t + 8};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            float h0, l0, h1, l1;
+            split_bf16(dft8_entry(mm[i], kk[i], INV), h0, l0);
+            split_bf16(dft8_entry(mm[i], kk[i] + 1, INV), h1, l1);
+            ahi[i] = bf2(h0, h1);
+            alo[i] = bf2(l0, l1);
+        }
+    }
+    float *outf = reinterpret_cast<float *>(out);
+    for (int grp = warp; grp < GROUPS; grp += NT / 32) {
+        // inputs r = t and r = t + 4 of butterfly b = 8 grp + g
+        const int b = grp * 8 + g;
+        const int c = b % C, j = b / C, k = j % NS;
+        float2 x0 = in[(j + t * NB) * C + c];
+        float2 x1 = in[(j + (t + 4) * NB) * C + c];
+        if (NS > 1) {
+            if (t > 0) {
+                float2 w = tw[t * k * (NF / (NS * R))];
+                if (INV) w.y = -w.y;
+                x0 = cmul(x0, w);
+            }
+            float2 w = tw[(t + 4) * k * (NF / (NS * R))];
+            if (INV) w.y = -w.y;
+            x1 = cmul(x1, w);
+        }
+        float h0, l0, h1, l1, h2, l2, h3, l3;
+        split_bf16(x0.x, h0, l0);
+        split_bf16(x0.y, h1, l1);
+        split_bf16(x1.x, h2, l2);
+        split_bf16(x1.y, h3, l3);
+        const unsigned bh0 = bf2(h0, h1), bh1 = bf2(h2, h3), bl0 = bf2(l0, l1), bl1 = bf2(l2, l3);
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_bf16(d, ahi, bh0, bh1);
+        mma_bf16(d, ahi, bl0, bl1);
+        mma_bf16(d, alo, bh0, bh1);
+        // d[0] = C[g][2t], d[1] = C[g][2t+1], d[2] = C[g+8][2t], d[3] = C[g+8][2t+1]
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int bb = grp * 8 + 2 * t + u;
+            const int cc = bb % C, jj = bb / C, kk2 = jj % NS;
+            const int base = (jj / NS) * NS * R + kk2;
+            const int p = g & 1, r0 = g >> 1;
+            outf[((base + r0 * NS) * C + cc) * 2 + p] = d[u];
+            outf[((base + (r0 + 4) * NS) * C + cc) * 2 + p] = d[2 + u];
+        }
+    }
+}
+
+// A stage of the split-precision schedule: tensor-core DFT for radix 8, FP32 otherwise.
+template <int NF, int R, int NS, bool INV, int C, int NT>
+__device__ __forceinline__ void sp_stage(const float2 *in, float2 *out, const float2 *tw)
+{
+    if constexpr (R == 8) tc_stage8<NF, NS, INV, C, NT>(in, out, tw);
+    else il_stage<NF, R, NS, INV, C, NT>(in, out, tw);
+}
+
+// Split-precision transform of a tile whose inputs were scattered into s0 by
+// FirstInputs::scatter; then sink(it, r, c, pos, value) in the thread mapping
+// of rr_last.  All threads call it; the caller adds a barrier before s0/s1 are
+// written again.
+template <int NF, bool INV, int C, int NT, class Sink>
+__device__ __forceinline__ void sp_all(float2 *s0, float2 *s1, const float2 *tw, Sink sink)
+{
+    using R = Radix<NF>;
+    sp_stage<NF, R::r0, 1, INV, C, NT>(s0, s1, tw);
+    __syncthreads();
+    sp_stage<NF, R::r1, R::r0, INV, C, NT>(s1, s0, tw);
+    __syncthreads();
+    const float2 *fin = s0;
+    if constexpr (R::r2 > 1) {
+        sp_stage<NF, R::r2, R::r0 * R::r1, INV, C, NT>(s0, s1, tw);
+        __syncthreads();
+        fin = s1;
+    }
+    constexpr int RL = LastStage<NF>::R, NSL = LastStage<NF>::NS, TOT = NSL * C, IT = (TOT + NT - 1) / NT;
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int idx = (int)threadIdx.x + it * NT;
+        if ((TOT % NT) != 0 && idx >= TOT) break;
+        const int c = idx % C, j = idx / C;
+#pragma unroll
+        for (int r = 0; r < RL; r++) sink(it, r, c, j + r * NSL, fin[(j + r * NSL) * C + c]);
     }
 }
 

@@ -54,6 +54,7 @@ struct Tables {
 struct Geometry {
     int N, n, W, L, H;  // H = N/2 kept z modes
     float beta, n_over_P, inv_P3;
+    int prec;           // 0: FP32 transforms; 1: radix-8 stages as split BF16 tensor-core DFTs
 };
 
 // Kernel launchers (bc_kernels.cu).  All return cudaGetLastError() after launch.
@@ -85,6 +86,7 @@ cudaError_t launch_ifft_z(const Geometry &g, const Tables &t, const PairDesc *pa
 cudaError_t launch_decode_peaks(const unsigned long long *keys, int n, float *peak, int *argmax, cudaStream_t s);
 
 bool supported_N(int N);
+bool supported_split(int N); // N for which precision 1 is built
 
 // Sets the calling thread's message returned by bc_last_error() (bc_api.cu).
 void set_last_error(const std::string &msg);

@@ -36,6 +36,8 @@
 
 namespace bc {
 
+bool supported_split(int N) { return N == 32 || N == 256; }
+
 bool supported_N(int N)
 {
     return N == 32 || N == 64 || N == 96 || N == 128 || N == 256;
@@ -409,7 +411,7 @@ constexpr int CL = 16;   // interleaved lines per tile (16 complex = 128 bytes p
 // then reset to zero so the boxes are clean for the next launch.
 // Output rows: with Z = FFT(a + i b), A_k = (Z_k + conj Z_{n-k}) / 2,
 // B_k = (Z_k - conj Z_{n-k}) / (2i), for m_z = k in [0, N/2).
-template <int NF>
+template <int NF, bool SP>
 __global__ void __launch_bounds__(TB, 2)
 k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
         float *grid, float2 *z1)
@@ -445,7 +447,8 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
         for (; it < items; it += gridDim.x) {
             const int l = it / (b0 * nyb), rem = it - l * (b0 * nyb);
             const int ix = rem / nyb, iy0 = (rem - ix * nyb) << 5;
-            rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
+            if constexpr (SP) in.scatter(S0);
+            else rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
             {
                 float2 *base = G2 + (long long)it * bz * 16;
                 in.for_each([&](int c, int pos) {
@@ -456,7 +459,9 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
             }
             __syncthreads();
             if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
-            rr_rest<NF, false, CL, TB>(S0, S1, tw, [&](int, int, int c, int pos, float2 v) { OUT[pos * CL + c] = v; });
+            auto sink = [&](int, int, int c, int pos, float2 v) { OUT[pos * CL + c] = v; };
+            if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
+            else rr_rest<NF, false, CL, TB>(S0, S1, tw, sink);
             __syncthreads();
             // unpack into a staging area [row][k] (row stride H + 1), then write
             // each 8H-byte row of z1 with consecutive threads on consecutive k
@@ -488,7 +493,7 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
 // m_y = -N/2, stored as zero).  First-stage inputs come straight from z1 and
 // last-stage outputs go straight to y1; the next item is loaded while the
 // current one finishes.
-template <int NF>
+template <int NF, bool SP>
 __global__ void __launch_bounds__(TB, 2)
 k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
         const float2 *__restrict__ z1, float2 *y1)
@@ -520,17 +525,20 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
         if (it < items) in.load(src(it));
         for (; it < items; it += gridDim.x) {
             const int lx = it / nch, ch = it - lx * nch;
-            rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
+            if constexpr (SP) in.scatter(S0);
+            else rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
             __syncthreads();
             if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
             float2 *Y = y1 + d.y1_off + (long long)lx * N * H + ch * CL;
-            rr_rest<NF, false, CL, TB>(S0, S1, tw, [&](int, int, int c, int pos, float2 v) {
+            auto sink = [&](int, int, int c, int pos, float2 v) {
                 int jy;
                 if (pos < N / 2) jy = pos;
                 else if (pos >= NF - N / 2) jy = pos - NF + N;
                 else return;
                 Y[(long long)jy * H + c] = jy == N / 2 ? make_float2(0.f, 0.f) : v;
-            });
+            };
+            if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
+            else rr_rest<NF, false, CL, TB>(S0, S1, tw, sink);
             __syncthreads();
         }
         rs.rot += items;
@@ -550,7 +558,7 @@ struct XModes {
     static __device__ __forceinline__ constexpr bool kept(int r) { return r < R / 4 || r >= 3 * R / 4; }
 };
 
-template <int NF, int NI>
+template <int NF, int NI, bool SP>
 __device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF>::IT][XModes<NF>::R], const Geometry &g,
                                            const Tables &tb, const InstDesc *__restrict__ inst,
                                            const InstPlan *__restrict__ plan, int si, const float2 *__restrict__ y1,
@@ -580,18 +588,21 @@ __device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF>::IT][XModes<NF
     FirstInputs<NF, Radix<NF>::r0, CL, TB> in;
     in.load(src(0));
     for (int l = 0; l < L; l++) {
-        rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
+        if constexpr (SP) in.scatter(S0);
+        else rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
         __syncthreads();
         if (l + 1 < L) in.load(src(l + 1));
         const float *T = tb.ballft + (long long)l * Q;
-        rr_rest<NF, false, CL, TB>(S0, S1, tw, [&](int it, int r, int c, int pos, float2 v) {
+        auto sink = [&](int it, int r, int c, int pos, float2 v) {
             if (!XM::kept(r)) return;
             const int mx = r < XM::R / 4 ? pos : pos - NF;
             const int jx = mx < 0 ? mx + N : mx;
             const int mz = ch * CL + c;
             const float Mv = T[mx * mx + my * my + mz * mz] * tb.deconv[jx] * djy * tb.deconv[mz];
             F[it][r] = make_float2(fmaf(Mv, v.x, F[it][r].x), fmaf(Mv, v.y, F[it][r].y));
-        });
+        };
+        if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
+        else rr_rest<NF, false, CL, TB>(S0, S1, tw, sink);
         __syncthreads();
     }
 }
@@ -625,7 +636,7 @@ __device__ __forceinline__ void for_kept(Fn f)
 // translation grid to t = -P/2: exp(2 pi i m (-P/2) / P) = (-1)^m.
 // With pair.a < 0, F_A comes from the cached spectrum; with pair.b < 0, F_A is
 // written to `fa_out` and nothing else happens.
-template <int NF, int NI>
+template <int NF, int NI, bool SP>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan *__restrict__ plan,
         const PairDesc *__restrict__ pairs, int npairs, const float2 *__restrict__ y1,
@@ -656,7 +667,7 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
                         FAt[jx * CL + c] = fa_cache[((long long)jx * N + jy) * H + ch * CL + c];
                     });
                 } else {
-                    spectrum_x<NF, NI>(FA, g, tb, inst, plan, pr.a, y1, jy, ch, twF, S0, S1);
+                    spectrum_x<NF, NI, SP>(FA, g, tb, inst, plan, pr.a, y1, jy, ch, twF, S0, S1);
                     for_kept<NF, NI>([&](int i2, int r, int c, int jx) { FAt[jx * CL + c] = FA[i2][r]; });
                 }
             }
@@ -667,7 +678,7 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
                 continue;
             }
             float2 FB[XM::IT][XM::R];
-            spectrum_x<NF, NI>(FB, g, tb, inst, plan, pr.b, y1, jy, ch, twF, S0, S1);
+            spectrum_x<NF, NI, SP>(FB, g, tb, inst, plan, pr.b, y1, jy, ch, twF, S0, S1);
             for_kept<NF, NI>([&](int i2, int r, int c, int jx) {
                 const int mx = mode_of(jx, N), mz = ch * CL + c;
                 float2 v = make_float2(0.f, 0.f);
@@ -863,20 +874,25 @@ static cudaError_t set_smem(K kernel, size_t bytes)
     return cudaSuccess;
 }
 
-template <int NF>
+template <int NF, bool SP = false>
 static cudaError_t fft_z_t(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
                            float *grid, float2 *z1, int nsm, cudaStream_t s)
 {
     const size_t smem = sizeof(float2) * (NF + 2 * NF * CL);
-    cudaError_t e = set_smem(k_fft_z<NF>, smem);
+    cudaError_t e = set_smem(k_fft_z<NF, SP>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_z<NF><<<resident_blocks(k_fft_z<NF>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, grid, z1);
+    k_fft_z<NF, SP><<<resident_blocks(k_fft_z<NF, SP>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, grid, z1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
                          float *grid, float2 *z1, int nsm, cudaStream_t s)
 {
+    if (g.prec == 1) {
+        if (g.n == 64) return fft_z_t<64, true>(g, t, inst, ninst, plan, grid, z1, nsm, s);
+        if (g.n == 512) return fft_z_t<512, true>(g, t, inst, ninst, plan, grid, z1, nsm, s);
+        return cudaErrorInvalidValue;
+    }
     switch (g.n) {
     case 64: return fft_z_t<64>(g, t, inst, ninst, plan, grid, z1, nsm, s);
     case 128: return fft_z_t<128>(g, t, inst, ninst, plan, grid, z1, nsm, s);
@@ -887,20 +903,25 @@ cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *ins
     }
 }
 
-template <int NF>
+template <int NF, bool SP = false>
 static cudaError_t fft_y_t(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
                            const float2 *z1, float2 *y1, int nsm, cudaStream_t s)
 {
     const size_t smem = sizeof(float2) * (NF + 2 * NF * CL);
-    cudaError_t e = set_smem(k_fft_y<NF>, smem);
+    cudaError_t e = set_smem(k_fft_y<NF, SP>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_y<NF><<<resident_blocks(k_fft_y<NF>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, z1, y1);
+    k_fft_y<NF, SP><<<resident_blocks(k_fft_y<NF, SP>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, z1, y1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fft_y(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
                          const float2 *z1, float2 *y1, int nsm, cudaStream_t s)
 {
+    if (g.prec == 1) {
+        if (g.n == 64) return fft_y_t<64, true>(g, t, inst, ninst, plan, z1, y1, nsm, s);
+        if (g.n == 512) return fft_y_t<512, true>(g, t, inst, ninst, plan, z1, y1, nsm, s);
+        return cudaErrorInvalidValue;
+    }
     switch (g.n) {
     case 64: return fft_y_t<64>(g, t, inst, ninst, plan, z1, y1, nsm, s);
     case 128: return fft_y_t<128>(g, t, inst, ninst, plan, z1, y1, nsm, s);
@@ -911,16 +932,16 @@ cudaError_t launch_fft_y(const Geometry &g, const Tables &t, const InstDesc *ins
     }
 }
 
-template <int NF, int NI>
+template <int NF, int NI, bool SP = false>
 static cudaError_t fft_x_t(const Geometry &g, const Tables &t, const InstDesc *inst, const InstPlan *plan,
                            const PairDesc *pairs, int npairs, const float2 *y1, const float2 *fa_cache, float2 *fa_out,
                            float2 *h, int nsm, cudaStream_t s)
 {
     const size_t smem = sizeof(float2) * (NF + NI + 2 * NF * CL + NI * CL);
-    cudaError_t e = set_smem(k_fft_x<NF, NI>, smem);
+    cudaError_t e = set_smem(k_fft_x<NF, NI, SP>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_x<NF, NI><<<resident_blocks(k_fft_x<NF, NI>, smem, nsm), TB, smem, s>>>(g, t, inst, plan, pairs, npairs, y1,
-                                                                                fa_cache, fa_out, h);
+    k_fft_x<NF, NI, SP><<<resident_blocks(k_fft_x<NF, NI, SP>, smem, nsm), TB, smem, s>>>(g, t, inst, plan, pairs, npairs,
+                                                                                        y1, fa_cache, fa_out, h);
     return cudaGetLastError();
 }
 
@@ -928,6 +949,11 @@ cudaError_t launch_fft_x(const Geometry &g, const Tables &t, const InstDesc *ins
                          const PairDesc *pairs, int npairs, const float2 *y1, const float2 *fa_cache, float2 *fa_out,
                          float2 *h, int nsm, cudaStream_t s)
 {
+    if (g.prec == 1) {
+        if (g.N == 32) return fft_x_t<64, 32, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
+        if (g.N == 256) return fft_x_t<512, 256, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
+        return cudaErrorInvalidValue;
+    }
     switch (g.N) {
     case 32: return fft_x_t<64, 32>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
     case 64: return fft_x_t<128, 64>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);

@@ -270,7 +270,6 @@ __global__ void k_features(const float *__restrict__ q, int n, const float *__re
 // integer in the high half, the complement of the index in the low half) with
 // a bitonic network in shared memory, descending; the first k indices are the
 // k best scores, ties to the lowest index.
-constexpr int TOPK_MAX = 16384;
 
 __global__ void __launch_bounds__(1024) k_topk(const float *__restrict__ s, int n, int P, int k, int *idx)
 {

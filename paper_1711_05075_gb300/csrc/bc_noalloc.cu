@@ -144,6 +144,7 @@ extern "C" bc_status bc_correlate_noalloc(const bc_params *p, const float *xyzA,
         g.W = p->W;
         g.L = p->level_count;
         g.H = kH;
+        g.prec = 0;
         g.beta = (float)beta;
         g.n_over_P = (float)(kn / p->period);
         g.inv_P3 = (float)(1.0 / (p->period * p->period * p->period));
