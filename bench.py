@@ -45,7 +45,12 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic per launch measured by ncu for the kernels below (one capture
 # each; see profiles/).  An entry counts only while the kernel source it was
 # measured on is unchanged (sha256 of csrc/bc_kernels.cu, first 16 hex digits).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    "k_spread": {"bytes": 1.839e+07, "kernel_hash": "ee4428456c7f0572", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_fft_z": {"bytes": 7.3e+07, "kernel_hash": "ee4428456c7f0572", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_fft_y": {"bytes": 9.376e+07, "kernel_hash": "ee4428456c7f0572", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_fft_x": {"bytes": 7.548e+07, "kernel_hash": "ee4428456c7f0572", "source": "profiles/ncu_full_scale_pair_N128.md"},
+}
 
 
 def kernel_source_hash():
@@ -316,6 +321,26 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ profiler runs
+def run_profile(args):
+    """N plain correlations of the bench workload and nothing else (a profiler target)."""
+    import torch
+    import paper_1711_05075_gb300 as bc
+    torch.cuda.set_device(0)
+    wl = workload()
+    ctx = bc.Context(wl.N, wl.W, wl.radii, wl.period)
+    A = ctx.shape(wl.A.xyz, wl.A.level)
+    B = ctx.shape(wl.B.xyz, wl.B.level)
+    out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device="cuda")
+    for _ in range(args.profile_correlations):
+        ctx.correlate(A, B, wl.quats.astype(np.float32), out)
+    ctx.sync()
+    A.close()
+    B.close()
+    ctx.close()
+    return 0
+
+
 # ------------------------------------------------------------------ learned proposal
 def run_learned(args):
     """Train the rotation-proposal network on peaks from the batched sweep and measure,
@@ -476,6 +501,8 @@ def main():
     ap.add_argument("--ref-fraction", type=float, default=0.25,
                     help="knot fraction of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-correlations", type=int, default=0,
+                    help="only run this many correlations of the workload (for a profiler), print nothing else")
     ap.add_argument("--workload", choices=["scale", "learned"], default="scale",
                     help="scale: the 20k+20k-ball N=128 correlation (default); learned: the rotation-proposal study")
     ap.add_argument("--train-pairs", type=int, default=100)
@@ -498,6 +525,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "learned":
         return run_learned(args)
+    if args.profile_correlations > 0:
+        return run_profile(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
