@@ -192,6 +192,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
     import paper_1711_05075_gb300 as bc
+    from paper_1711_05075_gb300.dist import max_over_ranks
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -233,11 +234,7 @@ def run_ours(args, rank, world, local_rank):
     prof = bc.bc_profile_end(ctx.handle)
     clk = clocks.stop() if rank == 0 else None
     ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms_total = float(sum(ms_steps))
-    t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_total = float(t.item())
+    ms_total = max_over_ranks(float(sum(ms_steps)))
     ms_per_step = ms_total / args.steps
     poses = world * args.steps * wl.N ** 3
     value = poses / (ms_total * 1e-3)
@@ -270,10 +267,7 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
         e_sum += time.perf_counter() - s0
     barrier()
-    te = torch.tensor([e_sum], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps * wl.N ** 3 / float(te.item())
+    e2e_value = world * args.steps * wl.N ** 3 / max_over_ranks(e_sum)
 
     # ---- roofline of the dominant stage
     peak, peak_src = load_peaks()
