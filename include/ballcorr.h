@@ -127,6 +127,19 @@ bc_status bc_correlate(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *qu
 bc_status bc_sweep(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quats, int k, int batch, float *peak,
                    int *argmax, int out_on_device);
 
+/* Captured sweep: the whole of bc_sweep(ctx, A, B, quats, k, batch, peak,
+ * argmax, 1) -- clearing the peak keys, A's spectrum, every batch of rotations
+ * and the decoding -- recorded once as a CUDA graph over workspaces the plan
+ * owns, so that each bc_plan_run is a single graph launch on ctx's stream.
+ * quats (host) are copied at plan time; peak and argmax are device buffers
+ * fixed at plan time; A and B must outlive the plan.  Planning synchronises
+ * the stream.  Errors as bc_sweep, plus BC_ERR_CUDA from graph capture. */
+typedef struct bc_plan_s *bc_plan_t;
+bc_status bc_sweep_plan(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quats, int k, int batch, float *peak,
+                        int *argmax, bc_plan_t *out);
+bc_status bc_plan_run(bc_plan_t plan);
+bc_status bc_plan_destroy(bc_plan_t plan);
+
 /* Ragged batch of independent pairs: pair i correlates As[i] with Bs[i]
  * rotated by quats[i] (npairs x 4 FP32, host).  Shapes may have any knot
  * counts; every instance gets its own support box.  Outputs (either may be

@@ -80,6 +80,11 @@ def lib():
         L.bc_mlp_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_longlong), i]
         L.bc_learned_sweep.argtypes = [vp, vp, vp, vp, vp, i, i, vp, vp, vp, vp]
         L.bc_topk.argtypes = [vp, vp, i, i, vp]
+        L.bc_sweep_plan.argtypes = [vp, vp, vp, vp, i, i, vp, vp, ctypes.POINTER(vp)]
+        L.bc_plan_run.argtypes = [vp]
+        L.bc_plan_destroy.argtypes = [vp]
+        for f in ("bc_sweep_plan", "bc_plan_run", "bc_plan_destroy"):
+            getattr(L, f).restype = st
         L.bc_topk.restype = st
         for f in ("bc_shape_moments", "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
                   "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep"):
@@ -200,6 +205,20 @@ def bc_mlp_state(net, params, m, v, step, get):
 def bc_learned_sweep(ctx, net, A, B, quats, n, topk, idx, peak, argmax, scores):
     _check(lib().bc_learned_sweep(ctx, net, A, B, _ptr(quats), int(n), int(topk), _ptr(idx), _ptr(peak),
                                   _ptr(argmax), _ptr(scores)))
+
+
+def bc_sweep_plan(ctx, A, B, quats, k, batch, peak, argmax):
+    h = ctypes.c_void_p()
+    _check(lib().bc_sweep_plan(ctx, A, B, _ptr(quats), int(k), int(batch), _ptr(peak), _ptr(argmax), ctypes.byref(h)))
+    return h
+
+
+def bc_plan_run(plan):
+    _check(lib().bc_plan_run(plan))
+
+
+def bc_plan_destroy(plan):
+    _check(lib().bc_plan_destroy(plan))
 
 
 def bc_topk(ctx, scores, n, k, idx):

@@ -72,6 +72,22 @@ struct DevBuf {
     }
 };
 
+// Device workspaces of one pipeline: the context's own, or a captured plan's.
+struct Workspace {
+    DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, boxes, keys;
+    bool grid_dirty = false;  // spreading boxes may hold values (an enqueue failed midway)
+    bool boxes_dirty = true;  // support-box accumulators need their reset state
+    std::vector<char> last_desc; // descriptors the device copies hold
+    void *last_inst_p = nullptr, *last_pairs_p = nullptr;
+    void release()
+    {
+        DevBuf *b[] = {&ku, &plan, &inst, &pairs, &grid, &z1, &y1, &h, &fa, &boxes, &keys};
+        for (DevBuf *x : b) x->release();
+        last_desc.clear();
+        last_inst_p = last_pairs_p = nullptr;
+    }
+};
+
 } // namespace
 
 struct bc_ctx_s {
@@ -91,11 +107,8 @@ struct bc_ctx_s {
     // device status word
     int *err_dev = nullptr;
     // workspaces
-    DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, outbuf, stats, boxes, keys, learn;
-    bool boxes_dirty = true; // support-box accumulators need their reset state
-    std::vector<char> last_desc;            // descriptors the device copies hold
-    void *last_inst_p = nullptr, *last_pairs_p = nullptr;
-    bool grid_dirty = false;
+    Workspace ws;                 // pipeline workspaces of direct calls
+    DevBuf outbuf, stats, learn;  // host-output staging, shape checks, learned-sweep scratch
     std::set<bc_shape_s *> shapes; // live shapes; orphaned (device memory freed) by bc_destroy
     std::set<bc_mlp_s *> nets;     // live networks; orphaned the same way
     // profiling
@@ -105,6 +118,16 @@ struct bc_ctx_s {
     std::vector<cudaEvent_t> prof_ev; // prof_max x (BC_NUM_STAGES + 1)
     int last_ninst = 0, last_npairs = 0;
     std::vector<InstDesc> last_inst;
+};
+
+// A rotation sweep captured as one CUDA graph over its own workspaces.
+struct bc_plan_s {
+    bc_ctx_t ctx = nullptr;
+    Workspace ws;
+    DevBuf desc;               // every pass's instance and pair descriptors
+    cudaGraphExec_t exec = nullptr;
+    int k = 0;
+    long long launches = 0;    // kernels per replay
 };
 
 struct bc_shape_s {
@@ -282,7 +305,8 @@ bc_status bc_destroy(bc_ctx_t c)
         c->shapes.clear();
         for (bc_mlp_s *net : c->nets) mlp_orphan(net);
         c->nets.clear();
-        DevBuf *bufs[] = {&c->ku, &c->plan, &c->inst, &c->pairs, &c->grid, &c->z1, &c->y1, &c->h, &c->fa, &c->outbuf, &c->stats, &c->boxes, &c->keys, &c->learn};
+        c->ws.release();
+        DevBuf *bufs[] = {&c->outbuf, &c->stats, &c->learn};
         for (DevBuf *b : bufs) b->release();
         delete c;
         return BC_OK;
@@ -423,7 +447,7 @@ bc_status bc_profile_end(bc_ctx_t c, bc_profile *out)
     // algorithmic bytes of the last call, from its device plan
     if (c->prof_calls > 0 && c->last_ninst > 0) {
         std::vector<InstPlan> pl(c->last_ninst);
-        CK(cudaMemcpy(pl.data(), c->plan.p, sizeof(InstPlan) * c->last_ninst, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(pl.data(), c->ws.plan.p, sizeof(InstPlan) * c->last_ninst, cudaMemcpyDeviceToHost));
         const double L = c->g.L, N = c->g.N, H = c->g.H;
         double knots = 0, cells = 0, zc = 0, yc = 0;
         for (int i = 0; i < c->last_ninst; i++) {
@@ -448,156 +472,192 @@ bc_status bc_profile_end(bc_ctx_t c, bc_profile *out)
 
 } // extern "C"
 
-// Enqueues one pass of the pipeline over `shapes` (instance i is shapes[i]
-// rotated by quats[i], identity when null) and `pairs`.  With cache_first,
-// pairs[0] = (a, -1) writes instance a's spectrum into the context's cache and
-// the remaining pairs follow; pairs with a = -1 read that cache.  dout (device,
-// N^3 floats at each pair's out_off) and keys (device peak keys at each pair's
-// key) may be null.
-static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std::vector<const float *> &quats,
-                         const std::vector<PairDesc> &pairs, bool cache_first, float *dout, unsigned long long *keys,
-                         const std::vector<const float *> *qdev = nullptr)
+// One pass of the pipeline over `shapes` (instance i is shapes[i] rotated by
+// quats[i], identity when null, or by the device quaternion qdev[i]) and
+// `pairs`.  With cache_first, pairs[0] = (a, -1) writes instance a's spectrum
+// into the workspace's cache and the remaining pairs follow; pairs with
+// a = -1 read that cache.
+struct Job {
+    std::vector<InstDesc> inst;
+    std::vector<PairDesc> pairs;
+    bool cache_first = false;
+    int nmain = 0, koff = 0, max_knots = 0;
+    long long goff = 0, zoff = 0, yoff = 0, hpairs = 0;
+};
+
+static Job plan_job(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std::vector<const float *> &quats,
+                    const std::vector<PairDesc> &pairs, bool cache_first, const std::vector<const float *> *qdev)
 {
-    cudaStream_t st = c->stream;
     const Geometry &g = c->g;
     const int N = g.N, H = g.H, L = g.L;
-    const int ninst = (int)shapes.size();
-    const int npairs = (int)pairs.size();
-    const int nmain = npairs - (cache_first ? 1 : 0);
-
-    std::vector<InstDesc> inst(ninst);
-    long long goff = 0, zoff = 0, yoff = 0;
-    int koff = 0, max_knots = 0;
-    for (int i = 0; i < ninst; i++) {
+    Job j;
+    j.pairs = pairs;
+    j.cache_first = cache_first;
+    j.nmain = (int)pairs.size() - (cache_first ? 1 : 0);
+    j.inst.resize(shapes.size());
+    for (size_t i = 0; i < shapes.size(); i++) {
         bc_shape_t s = shapes[i];
-        InstDesc &d = inst[i];
+        InstDesc &d = j.inst[i];
         std::memset(&d, 0, sizeof(d));
-        d.knot_off = koff;
+        d.knot_off = j.koff;
         d.nknots = s->n;
         d.src_off = 0;
         d.knots = s->knots;
         const int e = cap_extent(c, s->rmax);
         d.cap_e = e;
-        d.grid_off = goff;
-        d.z1_off = zoff;
-        d.y1_off = yoff;
+        d.grid_off = j.goff;
+        d.z1_off = j.zoff;
+        d.y1_off = j.yoff;
         if (quats[i]) {
             for (int q = 0; q < 4; q++) d.q[q] = quats[i][q];
         } else {
             d.q[0] = 1.f;
         }
         if (qdev) d.qdev = (*qdev)[i];
-        koff += s->n;
-        max_knots = s->n > max_knots ? s->n : max_knots;
-        goff += (long long)L * e * (((e + 31) / 32) * 32) * e; // block-transposed boxes, y padded to 32
-        zoff += (long long)L * e * e * H;
-        yoff += (long long)L * e * N * H;
+        j.koff += s->n;
+        j.max_knots = std::max(j.max_knots, s->n);
+        j.goff += (long long)L * e * (((e + 31) / 32) * 32) * e; // block-transposed boxes, y padded to 32
+        j.zoff += (long long)L * e * e * H;
+        j.yoff += (long long)L * e * N * H;
     }
-    long long hpairs = 0;
     for (const PairDesc &p : pairs)
-        if (p.b >= 0) hpairs = std::max(hpairs, p.h_off / ((long long)N * N * H) + 1);
+        if (p.b >= 0) j.hpairs = std::max(j.hpairs, p.h_off / ((long long)N * N * H) + 1);
+    return j;
+}
 
+// Grows the workspace to hold passes of up to these sizes (may synchronise the
+// stream and allocate; never called while a stream is being captured).
+static bc_status ensure_ws(bc_ctx_t c, Workspace &ws, long long koff, long long ninst, long long npairs, long long goff,
+                           long long zoff, long long yoff, long long hpairs)
+{
+    cudaStream_t st = c->stream;
+    const int N = c->g.N, H = c->g.H;
     cudaError_t e;
-    if ((e = c->ku.ensure(sizeof(float4) * (size_t)(koff > 0 ? koff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "ku");
-    if ((e = c->plan.ensure(sizeof(InstPlan) * ninst, false, st)) != cudaSuccess) return cuda_fail(e, "plan");
+    if ((e = ws.ku.ensure(sizeof(float4) * (size_t)std::max(koff, 1LL), false, st)) != cudaSuccess) return cuda_fail(e, "ku");
+    if ((e = ws.plan.ensure(sizeof(InstPlan) * (size_t)std::max(ninst, 1LL), false, st)) != cudaSuccess) return cuda_fail(e, "plan");
     {
-        const size_t before = c->boxes.bytes;
-        if ((e = c->boxes.ensure(sizeof(int) * 8 * (size_t)ninst, false, st)) != cudaSuccess) return cuda_fail(e, "boxes");
-        if (c->boxes.bytes != before || c->boxes_dirty) {
-            if ((e = launch_reset_boxes((int *)c->boxes.p, (int)(c->boxes.bytes / (8 * sizeof(int))), st)) != cudaSuccess)
+        const size_t before = ws.boxes.bytes;
+        if ((e = ws.boxes.ensure(sizeof(int) * 8 * (size_t)std::max(ninst, 1LL), false, st)) != cudaSuccess)
+            return cuda_fail(e, "boxes");
+        if (ws.boxes.bytes != before || ws.boxes_dirty) {
+            if ((e = launch_reset_boxes((int *)ws.boxes.p, (int)(ws.boxes.bytes / (8 * sizeof(int))), st)) != cudaSuccess)
                 return cuda_fail(e, "reset boxes");
-            c->boxes_dirty = false;
+            ws.boxes_dirty = false;
         }
     }
-    if ((e = c->inst.ensure(sizeof(InstDesc) * ninst, false, st)) != cudaSuccess) return cuda_fail(e, "inst");
-    if ((e = c->pairs.ensure(sizeof(PairDesc) * npairs, false, st)) != cudaSuccess) return cuda_fail(e, "pairs");
-    const size_t grid_before = c->grid.bytes;
-    if ((e = c->grid.ensure(sizeof(float) * (size_t)(goff > 0 ? goff : 1), true, st)) != cudaSuccess) return cuda_fail(e, "grid");
-    if (c->grid_dirty && c->grid.bytes == grid_before) {
-        if ((e = cudaMemsetAsync(c->grid.p, 0, c->grid.bytes, st)) != cudaSuccess) return cuda_fail(e, "grid clear");
+    if ((e = ws.inst.ensure(sizeof(InstDesc) * (size_t)std::max(ninst, 1LL), false, st)) != cudaSuccess) return cuda_fail(e, "inst");
+    if ((e = ws.pairs.ensure(sizeof(PairDesc) * (size_t)std::max(npairs, 1LL), false, st)) != cudaSuccess) return cuda_fail(e, "pairs");
+    const size_t grid_before = ws.grid.bytes;
+    if ((e = ws.grid.ensure(sizeof(float) * (size_t)std::max(goff, 1LL), true, st)) != cudaSuccess) return cuda_fail(e, "grid");
+    if (ws.grid_dirty && ws.grid.bytes == grid_before) {
+        if ((e = cudaMemsetAsync(ws.grid.p, 0, ws.grid.bytes, st)) != cudaSuccess) return cuda_fail(e, "grid clear");
     }
-    c->grid_dirty = false;
-    if ((e = c->z1.ensure(sizeof(float2) * (size_t)(zoff > 0 ? zoff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "z1");
-    if ((e = c->y1.ensure(sizeof(float2) * (size_t)(yoff > 0 ? yoff : 1), false, st)) != cudaSuccess) return cuda_fail(e, "y1");
-    if (hpairs > 0 && (e = c->h.ensure(sizeof(float2) * (size_t)hpairs * N * N * H, false, st)) != cudaSuccess)
+    ws.grid_dirty = false;
+    if ((e = ws.z1.ensure(sizeof(float2) * (size_t)std::max(zoff, 1LL), false, st)) != cudaSuccess) return cuda_fail(e, "z1");
+    if ((e = ws.y1.ensure(sizeof(float2) * (size_t)std::max(yoff, 1LL), false, st)) != cudaSuccess) return cuda_fail(e, "y1");
+    if (hpairs > 0 && (e = ws.h.ensure(sizeof(float2) * (size_t)hpairs * N * N * H, false, st)) != cudaSuccess)
         return cuda_fail(e, "h");
-    if ((e = c->fa.ensure(sizeof(float2) * (size_t)N * N * H, false, st)) != cudaSuccess) return cuda_fail(e, "fa");
+    if ((e = ws.fa.ensure(sizeof(float2) * (size_t)N * N * H, false, st)) != cudaSuccess) return cuda_fail(e, "fa");
+    return BC_OK;
+}
 
-    // descriptors -> device, only when they differ from what the device already holds
-    const size_t inst_bytes = sizeof(InstDesc) * ninst, pair_bytes = sizeof(PairDesc) * npairs;
-    std::vector<char> desc(inst_bytes + pair_bytes);
-    std::memcpy(desc.data(), inst.data(), inst_bytes);
-    std::memcpy(desc.data() + inst_bytes, pairs.data(), pair_bytes);
-    if (desc != c->last_desc || c->inst.p != c->last_inst_p || c->pairs.p != c->last_pairs_p) {
-        if ((e = cudaMemcpyAsync(c->inst.p, desc.data(), inst_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return cuda_fail(e, "copy inst");
-        if ((e = cudaMemcpyAsync(c->pairs.p, desc.data() + inst_bytes, pair_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-            return cuda_fail(e, "copy pairs");
-        c->last_desc.swap(desc);
-        c->last_inst_p = c->inst.p;
-        c->last_pairs_p = c->pairs.p;
-    }
-
-    const InstDesc *dinst = (const InstDesc *)c->inst.p;
+// The kernel launches of one planned pass, with its descriptors already on the
+// device at dinst / dpairs.  Launches only (legal while a stream is captured).
+static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const InstDesc *dinst, const PairDesc *dpairs,
+                            float *dout, unsigned long long *keys, bool profile, cudaStream_t st)
+{
+    const Geometry &g = c->g;
+    const int ninst = (int)job.inst.size();
     const Tables t = tables_of(c);
-    InstPlan *dplan = (InstPlan *)c->plan.p;
-    const PairDesc *dpairs = (const PairDesc *)c->pairs.p;
-    const PairDesc *pmain = dpairs + (cache_first ? 1 : 0);
+    InstPlan *dplan = (InstPlan *)ws.plan.p;
+    const PairDesc *pmain = dpairs + (job.cache_first ? 1 : 0);
+    const int nmain = job.nmain;
+    cudaError_t e;
     int launches = 0;
-    c->grid_dirty = true; // until the z pass has consumed the spreading boxes
-    const bool prof = c->prof_on && c->prof_calls < c->prof_max;
-    prof_mark(c, -1);
-    c->boxes_dirty = true; // until k_plan has consumed and reset the accumulators
-    if ((e = launch_prepare(g, dinst, ninst, max_knots, (float4 *)c->ku.p, (int *)c->boxes.p, dplan, c->err_dev, st)) != cudaSuccess)
+    const bool prof = profile && c->prof_on && c->prof_calls < c->prof_max;
+    auto mark = [&](int s) {
+        if (profile) prof_mark(c, s);
+    };
+    ws.grid_dirty = true; // until the z pass has consumed the spreading boxes
+    mark(-1);
+    ws.boxes_dirty = true; // until k_plan has consumed and reset the accumulators
+    if ((e = launch_prepare(g, dinst, ninst, job.max_knots, (float4 *)ws.ku.p, (int *)ws.boxes.p, dplan, c->err_dev, st)) != cudaSuccess)
         return cuda_fail(e, "prepare");
-    c->boxes_dirty = false;
+    ws.boxes_dirty = false;
     launches += 2;
-    prof_mark(c, 0);
-    if ((e = launch_spread(g, t, dinst, koff, (const float4 *)c->ku.p, dplan, (float *)c->grid.p, st)) != cudaSuccess)
+    mark(0);
+    if ((e = launch_spread(g, t, dinst, job.koff, (const float4 *)ws.ku.p, dplan, (float *)ws.grid.p, st)) != cudaSuccess)
         return cuda_fail(e, "spread");
-    launches += koff > 0;
-    prof_mark(c, 1);
-    if ((e = launch_fft_z(g, t, dinst, ninst, dplan, (float *)c->grid.p, (float2 *)c->z1.p, c->nsm, st)) != cudaSuccess)
+    launches += job.koff > 0;
+    mark(1);
+    if ((e = launch_fft_z(g, t, dinst, ninst, dplan, (float *)ws.grid.p, (float2 *)ws.z1.p, c->nsm, st)) != cudaSuccess)
         return cuda_fail(e, "fft z");
-    c->grid_dirty = false;
+    ws.grid_dirty = false;
     launches++;
-    prof_mark(c, 2);
-    if ((e = launch_fft_y(g, t, dinst, ninst, dplan, (const float2 *)c->z1.p, (float2 *)c->y1.p, c->nsm, st)) != cudaSuccess)
+    mark(2);
+    if ((e = launch_fft_y(g, t, dinst, ninst, dplan, (const float2 *)ws.z1.p, (float2 *)ws.y1.p, c->nsm, st)) != cudaSuccess)
         return cuda_fail(e, "fft y");
     launches++;
-    prof_mark(c, 3);
-    if (cache_first) {
-        if ((e = launch_fft_x(g, t, dinst, dplan, dpairs, 1, (const float2 *)c->y1.p, nullptr, (float2 *)c->fa.p,
-                              (float2 *)c->h.p, c->nsm, st)) != cudaSuccess)
+    mark(3);
+    if (job.cache_first) {
+        if ((e = launch_fft_x(g, t, dinst, dplan, dpairs, 1, (const float2 *)ws.y1.p, nullptr, (float2 *)ws.fa.p,
+                              (float2 *)ws.h.p, c->nsm, st)) != cudaSuccess)
             return cuda_fail(e, "fft x (cache)");
         launches++;
     }
     if (nmain > 0) {
-        if ((e = launch_fft_x(g, t, dinst, dplan, pmain, nmain, (const float2 *)c->y1.p, (const float2 *)c->fa.p,
-                              nullptr, (float2 *)c->h.p, c->nsm, st)) != cudaSuccess)
+        if ((e = launch_fft_x(g, t, dinst, dplan, pmain, nmain, (const float2 *)ws.y1.p, (const float2 *)ws.fa.p,
+                              nullptr, (float2 *)ws.h.p, c->nsm, st)) != cudaSuccess)
             return cuda_fail(e, "fft x");
         launches++;
     }
-    prof_mark(c, 4);
+    mark(4);
     if (nmain > 0) {
-        if ((e = launch_ifft_y(g, t, pmain, nmain, (float2 *)c->h.p, c->nsm, st)) != cudaSuccess) return cuda_fail(e, "ifft y");
+        if ((e = launch_ifft_y(g, t, pmain, nmain, (float2 *)ws.h.p, c->nsm, st)) != cudaSuccess) return cuda_fail(e, "ifft y");
         launches++;
     }
-    prof_mark(c, 5);
+    mark(5);
     if (nmain > 0) {
-        if ((e = launch_ifft_z(g, t, pmain, nmain, (const float2 *)c->h.p, dout, keys, c->nsm, st)) != cudaSuccess)
+        if ((e = launch_ifft_z(g, t, pmain, nmain, (const float2 *)ws.h.p, dout, keys, c->nsm, st)) != cudaSuccess)
             return cuda_fail(e, "ifft z");
         launches++;
     }
-    prof_mark(c, 6);
+    mark(6);
     if (prof) {
         c->prof_calls++;
         c->prof_launches += launches;
         c->last_ninst = ninst;
         c->last_npairs = nmain;
-        c->last_inst = inst;
+        c->last_inst = job.inst;
     }
     return BC_OK;
+}
+
+// Plans, uploads the descriptors (only when they changed) and launches one pass
+// on the context's own workspace.
+static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std::vector<const float *> &quats,
+                         const std::vector<PairDesc> &pairs, bool cache_first, float *dout, unsigned long long *keys,
+                         const std::vector<const float *> *qdev = nullptr)
+{
+    Workspace &ws = c->ws;
+    const Job job = plan_job(c, shapes, quats, pairs, cache_first, qdev);
+    const long long ninst = (long long)job.inst.size(), npairs = (long long)job.pairs.size();
+    if (bc_status s = ensure_ws(c, ws, job.koff, ninst, npairs, job.goff, job.zoff, job.yoff, job.hpairs)) return s;
+    const size_t inst_bytes = sizeof(InstDesc) * ninst, pair_bytes = sizeof(PairDesc) * npairs;
+    std::vector<char> desc(inst_bytes + pair_bytes);
+    std::memcpy(desc.data(), job.inst.data(), inst_bytes);
+    std::memcpy(desc.data() + inst_bytes, job.pairs.data(), pair_bytes);
+    if (desc != ws.last_desc || ws.inst.p != ws.last_inst_p || ws.pairs.p != ws.last_pairs_p) {
+        cudaError_t e;
+        if ((e = cudaMemcpyAsync(ws.inst.p, desc.data(), inst_bytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+            return cuda_fail(e, "copy inst");
+        if ((e = cudaMemcpyAsync(ws.pairs.p, desc.data() + inst_bytes, pair_bytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+            return cuda_fail(e, "copy pairs");
+        ws.last_desc.swap(desc);
+        ws.last_inst_p = ws.inst.p;
+        ws.last_pairs_p = ws.pairs.p;
+    }
+    return launch_job(c, ws, job, (const InstDesc *)ws.inst.p, (const PairDesc *)ws.pairs.p, dout, keys, true, c->stream);
 }
 
 // Peaks for k rotations of B (host quaternions qhost, or device quaternions
@@ -612,8 +672,8 @@ static bc_status sweep_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float 
     cudaError_t e;
     const size_t key_bytes = sizeof(unsigned long long) * (size_t)k;
     const size_t out_bytes = out_on_device ? 0 : (sizeof(float) + sizeof(int)) * (size_t)k;
-    if ((e = c->keys.ensure(key_bytes + out_bytes, false, st)) != cudaSuccess) return cuda_fail(e, "keys");
-    unsigned long long *keys = (unsigned long long *)c->keys.p;
+    if ((e = c->ws.keys.ensure(key_bytes + out_bytes, false, st)) != cudaSuccess) return cuda_fail(e, "keys");
+    unsigned long long *keys = (unsigned long long *)c->ws.keys.p;
     if ((e = cudaMemsetAsync(keys, 0, key_bytes, st)) != cudaSuccess) return cuda_fail(e, "clear keys");
     {
         std::vector<bc_shape_t> shapes(1, A);
@@ -636,7 +696,7 @@ static bc_status sweep_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float 
     float *dpeak = peak;
     int *darg = argmax;
     if (!out_on_device) {
-        dpeak = (float *)((char *)c->keys.p + key_bytes);
+        dpeak = (float *)((char *)c->ws.keys.p + key_bytes);
         darg = (int *)(dpeak + k);
     }
     if ((e = launch_decode_peaks(keys, k, dpeak, darg, st)) != cudaSuccess) return cuda_fail(e, "decode peaks");
@@ -718,8 +778,8 @@ bc_status bc_pairs(bc_ctx_t c, const bc_shape_t *As, const bc_shape_t *Bs, const
         cudaError_t e;
         const size_t key_bytes = peak ? sizeof(unsigned long long) * (size_t)npairs : 0;
         const size_t pk_bytes = (peak && !on_device) ? (sizeof(float) + sizeof(int)) * (size_t)npairs : 0;
-        if (key_bytes && (e = c->keys.ensure(key_bytes + pk_bytes, false, st)) != cudaSuccess) return cuda_fail(e, "keys");
-        unsigned long long *keys = key_bytes ? (unsigned long long *)c->keys.p : nullptr;
+        if (key_bytes && (e = c->ws.keys.ensure(key_bytes + pk_bytes, false, st)) != cudaSuccess) return cuda_fail(e, "keys");
+        unsigned long long *keys = key_bytes ? (unsigned long long *)c->ws.keys.p : nullptr;
         if (keys && (e = cudaMemsetAsync(keys, 0, key_bytes, st)) != cudaSuccess) return cuda_fail(e, "clear keys");
         float *dout = out;
         if (out && !on_device) {
@@ -740,7 +800,7 @@ bc_status bc_pairs(bc_ctx_t c, const bc_shape_t *As, const bc_shape_t *Bs, const
             float *dpeak = peak;
             int *darg = argmax;
             if (!on_device) {
-                dpeak = (float *)((char *)c->keys.p + key_bytes);
+                dpeak = (float *)((char *)c->ws.keys.p + key_bytes);
                 darg = (int *)(dpeak + npairs);
             }
             if ((e = launch_decode_peaks(keys, npairs, dpeak, darg, st)) != cudaSuccess) return cuda_fail(e, "decode peaks");
@@ -777,6 +837,141 @@ bc_status bc_sweep(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, i
     }
 }
 
+bc_status bc_sweep_plan(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, int k, int batch, float *peak,
+                        int *argmax, bc_plan_t *out)
+{
+    bc_plan_s *pl = nullptr;
+    bool capturing = false;
+    try {
+        if (!c || !A || !B || !quats || !peak || !argmax || !out) return fail(BC_ERR_ARG, "bc_sweep_plan: null argument");
+        *out = nullptr;
+        if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_sweep_plan: shapes belong to another context");
+        if (k < 1 || k > (1 << 24)) return fail(BC_ERR_ARG, "bc_sweep_plan: k must be in [1, 2^24]");
+        if (batch < 0 || batch > 65534) return fail(BC_ERR_ARG, "bc_sweep_plan: batch must be in [0, 65534]");
+        if (bc_status s = check_quats(quats, k, "bc_sweep_plan")) return s;
+        if (batch == 0) batch = 64;
+        const int N = c->g.N, H = c->g.H;
+        cudaStream_t st = c->stream;
+        cudaError_t e;
+        pl = new bc_plan_s();
+        pl->ctx = c;
+        pl->k = k;
+        // plan every pass on the host
+        std::vector<Job> jobs;
+        jobs.push_back(plan_job(c, std::vector<bc_shape_t>(1, A), std::vector<const float *>(1, nullptr),
+                                std::vector<PairDesc>(1, PairDesc{0, -1, 0, 0, 0}), true, nullptr));
+        for (int r0 = 0; r0 < k; r0 += batch) {
+            const int nb = std::min(batch, k - r0);
+            std::vector<const float *> q(nb);
+            std::vector<PairDesc> pairs(nb);
+            for (int i = 0; i < nb; i++) {
+                q[i] = quats + 4 * (size_t)(r0 + i);
+                pairs[i] = PairDesc{-1, i, (long long)i * N * N * H, 0, (long long)(r0 + i)};
+            }
+            jobs.push_back(plan_job(c, std::vector<bc_shape_t>(nb, B), q, pairs, false, nullptr));
+        }
+        long long mk = 0, mi = 0, mp = 0, mg = 0, mz = 0, my = 0, mh = 0;
+        std::vector<size_t> doff(jobs.size());
+        size_t dbytes = 0;
+        for (size_t j = 0; j < jobs.size(); j++) {
+            const Job &jb = jobs[j];
+            mk = std::max(mk, (long long)jb.koff);
+            mi = std::max(mi, (long long)jb.inst.size());
+            mp = std::max(mp, (long long)jb.pairs.size());
+            mg = std::max(mg, jb.goff);
+            mz = std::max(mz, jb.zoff);
+            my = std::max(my, jb.yoff);
+            mh = std::max(mh, jb.hpairs);
+            doff[j] = dbytes;
+            dbytes += (sizeof(InstDesc) * jb.inst.size() + sizeof(PairDesc) * jb.pairs.size() + 255) & ~size_t(255);
+        }
+        if (bc_status s = ensure_ws(c, pl->ws, mk, mi, mp, mg, mz, my, mh)) {
+            bc_plan_destroy(pl);
+            return s;
+        }
+        if ((e = pl->ws.keys.ensure(sizeof(unsigned long long) * (size_t)k, false, st)) != cudaSuccess ||
+            (e = pl->desc.ensure(dbytes, false, st)) != cudaSuccess) {
+            bc_plan_destroy(pl);
+            return cuda_fail(e, "bc_sweep_plan: workspace");
+        }
+        std::vector<char> host(dbytes);
+        for (size_t j = 0; j < jobs.size(); j++) {
+            const size_t ib = sizeof(InstDesc) * jobs[j].inst.size();
+            std::memcpy(host.data() + doff[j], jobs[j].inst.data(), ib);
+            std::memcpy(host.data() + doff[j] + ib, jobs[j].pairs.data(), sizeof(PairDesc) * jobs[j].pairs.size());
+        }
+        if ((e = cudaMemcpyAsync(pl->desc.p, host.data(), dbytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            bc_plan_destroy(pl);
+            return cuda_fail(e, "bc_sweep_plan: descriptors");
+        }
+        // capture: clear keys, A's spectrum, every batch, decode -- on a private stream (the
+        // legacy default stream cannot be captured); the graph later runs on ctx's stream
+        unsigned long long *keys = (unsigned long long *)pl->ws.keys.p;
+        cudaStream_t cs = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) {
+            bc_plan_destroy(pl);
+            return cuda_fail(e, "bc_sweep_plan: capture stream");
+        }
+        if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed)) != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            bc_plan_destroy(pl);
+            return cuda_fail(e, "bc_sweep_plan: begin capture");
+        }
+        capturing = true;
+        bc_status s = BC_OK;
+        if ((e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)k, cs)) != cudaSuccess)
+            s = cuda_fail(e, "bc_sweep_plan: clear keys");
+        for (size_t j = 0; s == BC_OK && j < jobs.size(); j++) {
+            const char *base = (const char *)pl->desc.p + doff[j];
+            s = launch_job(c, pl->ws, jobs[j], (const InstDesc *)base,
+                           (const PairDesc *)(base + sizeof(InstDesc) * jobs[j].inst.size()), nullptr,
+                           j == 0 ? nullptr : keys, false, cs);
+        }
+        if (s == BC_OK && (e = launch_decode_peaks(keys, k, peak, argmax, cs)) != cudaSuccess)
+            s = cuda_fail(e, "bc_sweep_plan: decode");
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        capturing = false;
+        cudaStreamDestroy(cs);
+        if (s == BC_OK && e != cudaSuccess) s = cuda_fail(e, "bc_sweep_plan: end capture");
+        if (s == BC_OK && (e = cudaGraphInstantiate(&pl->exec, graph, 0)) != cudaSuccess)
+            s = cuda_fail(e, "bc_sweep_plan: instantiate");
+        if (graph) cudaGraphDestroy(graph);
+        if (s != BC_OK) {
+            bc_plan_destroy(pl);
+            return s;
+        }
+        size_t nodes = 0;
+        pl->launches = (long long)jobs.size() * 8; // upper bound, for reporting
+        (void)nodes;
+        *out = pl;
+        return BC_OK;
+    } catch (...) {
+        (void)capturing;
+        if (pl) bc_plan_destroy(pl);
+        return fail(BC_ERR_INTERNAL, "bc_sweep_plan: unexpected exception");
+    }
+}
+
+bc_status bc_plan_run(bc_plan_t pl)
+{
+    if (!pl || !pl->exec) return fail(BC_ERR_ARG, "bc_plan_run: null or empty plan");
+    CK(cudaGraphLaunch(pl->exec, pl->ctx->stream));
+    return BC_OK;
+}
+
+bc_status bc_plan_destroy(bc_plan_t pl)
+{
+    if (!pl) return BC_OK;
+    if (pl->ctx) cudaStreamSynchronize(pl->ctx->stream);
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    pl->ws.release();
+    pl->desc.release();
+    delete pl;
+    return BC_OK;
+}
+
 bc_status bc_shape_moments(bc_ctx_t c, bc_shape_t S, float *out)
 {
     try {
@@ -787,7 +982,7 @@ bc_status bc_shape_moments(bc_ctx_t c, bc_shape_t S, float *out)
         std::vector<const float *> q(1, nullptr);
         std::vector<PairDesc> pairs(1, PairDesc{0, -1, 0, 0, 0});
         if (bc_status s = enqueue(c, shapes, q, pairs, true, nullptr, nullptr)) return s;
-        cudaError_t e = launch_moments((const float2 *)c->fa.p, c->modes, BC_MOMENTS, c->g.N, c->g.H, out, c->stream);
+        cudaError_t e = launch_moments((const float2 *)c->ws.fa.p, c->modes, BC_MOMENTS, c->g.N, c->g.H, out, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "moments");
         return BC_OK;
     } catch (...) {

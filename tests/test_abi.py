@@ -23,7 +23,8 @@ def test_header_declares_the_boundary():
     for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sweep", "bc_pairs", "bc_sync",
               "bc_last_error", "bc_version", "bc_profile_begin", "bc_profile_end", "bc_stage_name",
               "bc_shape_moments", "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
-              "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep", "bc_mlp_param_count", "bc_topk"):
+              "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep", "bc_mlp_param_count", "bc_topk", "bc_sweep_plan", "bc_plan_run",
+              "bc_plan_destroy"):
         assert f in names
 
 

@@ -123,3 +123,28 @@ def test_ragged_pairs_match_oracle(bc):
     for h in hA + hB:
         h.close()
     ctx.close()
+
+
+def test_captured_sweep_plan_replays(bc):
+    # The same sweep as one CUDA graph: identical peaks to bc_sweep, replayable.
+    wl = synth.small_pair(9)
+    q = synth.shoemake_quaternions(synth.SplitMix64(41), 10).astype(np.float32)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    A = ctx.shape(wl.A.xyz, wl.A.level)
+    B = ctx.shape(wl.B.xyz, wl.B.level)
+    ref_p, ref_a = ctx.sweep(A, B, q, batch=4)
+    peak = torch.empty(10, dtype=torch.float32, device="cuda")
+    arg = torch.empty(10, dtype=torch.int32, device="cuda")
+    plan = bc.bc_sweep_plan(ctx.handle, A.handle, B.handle, q, 10, 4, peak, arg)
+    for _ in range(3):
+        peak.fill_(-1.0)
+        bc.bc_plan_run(plan)
+        ctx.sync()
+        np.testing.assert_allclose(peak.cpu().numpy(), ref_p.cpu().numpy(), rtol=1e-6)
+    # the context's own calls in between do not disturb the plan's workspaces
+    ctx.correlate(A, B, q[:2])
+    bc.bc_plan_run(plan)
+    ctx.sync()
+    np.testing.assert_allclose(peak.cpu().numpy(), ref_p.cpu().numpy(), rtol=1e-6)
+    bc.bc_plan_destroy(plan)
+    A.close(); B.close(); ctx.close()
