@@ -43,8 +43,9 @@ UNIT = "poses/s"
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM traffic per launch measured by ncu for the kernels below (one capture
-# each; see profiles/).  An entry counts only while the kernel source it was
-# measured on is unchanged (sha256 of csrc/bc_kernels.cu, first 16 hex digits).
+# each; see profiles/).  An entry counts only while the kernel sources it was
+# measured on are unchanged (sha256 over csrc/*.cu and csrc/*.cuh of the
+# package, first 16 hex digits).
 NCU_TRAFFIC = {
     "k_spread": {"bytes": 1.839e+07, "kernel_hash": "ee4428456c7f0572", "source": "profiles/ncu_full_scale_pair_N128.md"},
     "k_fft_z": {"bytes": 7.3e+07, "kernel_hash": "ee4428456c7f0572", "source": "profiles/ncu_full_scale_pair_N128.md"},
@@ -54,8 +55,41 @@ NCU_TRAFFIC = {
 
 
 def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_1711_05075_gb300", "csrc", "bc_kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    import glob
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1711_05075_gb300", "csrc")
+    for p in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def cufft_baseline(wl, dev, stream, reps=5):
+    """cuFFT (through torch.fft) on the same transforms without pruning: the
+    real-to-complex 3D FFT of all 2L full n^3 level grids of both shapes and
+    the complex-to-real inverse onto the N^3 grid.  Timed with CUDA events on
+    `stream` after one warm-up; a baseline beside the library's own transform
+    stages, not part of the correlation path."""
+    import torch
+    n, L, N = 2 * wl.N, len(wl.radii), wl.N
+    with torch.cuda.stream(stream):
+        grids = torch.rand((2 * L, n, n, n), dtype=torch.float32, device=dev)
+        spec = torch.rand((N, N, N // 2 + 1), dtype=torch.complex64, device=dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ts = []
+        for i in range(reps + 1):
+            e0.record(stream)
+            torch.fft.rfftn(grids, dim=(1, 2, 3))
+            torch.fft.irfftn(spec, s=(N, N, N))
+            e1.record(stream)
+            e1.synchronize()
+            if i:
+                ts.append(e0.elapsed_time(e1))
+    del grids, spec
+    torch.cuda.empty_cache()
+    return {"ms": float(np.median(ts)), "what": f"torch.fft (cuFFT) rfftn of {2 * L} x {n}^3 real grids + irfftn "
+                                                f"onto {N}^3, no pruning"}
 
 
 def load_peaks():
@@ -202,6 +236,11 @@ def run_ours(args, rank, world, local_rank):
     A = ctx.shape(wl.A.xyz, wl.A.level)
     B = ctx.shape(wl.B.xyz, wl.B.level)
     q = wl.quats.astype(np.float32)
+    if args.spread is not None:
+        ctx.set_tuning(spread=args.spread)
+        tuning = ctx.tuning
+    else:
+        tuning = ctx.autotune(A, B) if not args.no_autotune else ctx.tuning
     out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -276,11 +315,21 @@ def run_ours(args, rank, world, local_rank):
     calls = max(prof["calls"], 1)
     dom_ms = dom["ms"] / calls
     achieved = dom["bytes"] / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0
-    kname = {"prepare": "k_prepare", "spread": "k_spread", "fft_z": "k_fft_z", "fft_y": "k_fft_y",
+    binned = tuning["spread"] == 1
+    kname = {"prepare": "k_prepare", "spread": "k_bin" if binned else "k_spread",
+             "fft_z": "k_fft_z_binned" if binned else "k_fft_z", "fft_y": "k_fft_y",
              "fft_x": "k_fft_x", "ifft_y": "k_ifft_y", "ifft_z": "k_ifft_z"}[dom["name"]]
     tr = NCU_TRAFFIC.get(kname)
     traffic = tr["bytes"] if tr and tr.get("kernel_hash") == kernel_source_hash() else None
     stage_share = {s["name"]: round(s["ms"] / max(sum(x["ms"] for x in stages), 1e-12), 4) for s in stages}
+    fft_stages = ("fft_z", "fft_y", "fft_x", "ifft_y", "ifft_z")
+    ours_fft_ms = sum(s["ms"] for s in stages if s["name"] in fft_stages) / calls
+    cufft = None
+    if rank == 0 and not args.no_cufft:
+        cufft = cufft_baseline(wl, dev, stream)
+        cufft["ours_fft_ms"] = ours_fft_ms
+        cufft["ours_note"] = ("the library's five transform stages (pruned; the x stage includes deconvolution, "
+                              "ball transform, level sum and conjugate product)")
 
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
@@ -303,6 +352,8 @@ def run_ours(args, rank, world, local_rank):
                          "note": f"peak {peak_src}; achieved = algorithmic bytes per launch / mean launch time "
                                  f"({dom['bytes'] / 1e6:.1f} MB / {dom_ms * 1e3:.1f} us)"},
             "stage_ms": {s["name"]: round(s["ms"] / calls, 5) for s in stages},
+            "tuning": tuning,
+            "cufft_baseline": cufft,
             "stage_share": stage_share,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -323,6 +374,7 @@ def run_profile(args):
     torch.cuda.set_device(0)
     wl = workload()
     ctx = bc.Context(wl.N, wl.W, wl.radii, wl.period)
+    ctx.set_tuning(spread=args.spread if args.spread is not None else 0)
     A = ctx.shape(wl.A.xyz, wl.A.level)
     B = ctx.shape(wl.B.xyz, wl.B.level)
     out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device="cuda")
@@ -495,6 +547,10 @@ def main():
     ap.add_argument("--ref-fraction", type=float, default=0.25,
                     help="knot fraction of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the context's default tuning")
+    ap.add_argument("--spread", type=int, choices=[0, 1], default=None,
+                    help="force the spreading implementation (default: autotuned; 0 for --profile-correlations)")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT baseline timing")
     ap.add_argument("--profile-correlations", type=int, default=0,
                     help="only run this many correlations of the workload (for a profiler), print nothing else")
     ap.add_argument("--workload", choices=["scale", "learned"], default="scale",

@@ -118,7 +118,8 @@ bc_status bc_correlate(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *qu
  *     peak[r]   = max_t g(R(q_r), t),
  *     argmax[r] = the lowest linear index (kx*N + ky)*N + kz attaining it,
  * without writing the N^3 grids.  A's spectrum is computed once per call and
- * reused; the rotations run in batches of `batch` (0 = 64) through the same
+ * reused; the rotations run in batches of `batch` (0 = the context's
+ * sweep_batch, see bc_set_tuning) through the same
  * kernels as bc_correlate, the last of which folds each batch's grids into
  * 64-bit peak keys.  quats: k x 4 FP32 host memory.  peak (k floats) and
  * argmax (k ints) are device (out_on_device = 1, asynchronous) or host
@@ -151,6 +152,36 @@ bc_status bc_plan_destroy(bc_plan_t plan);
  * another context), BC_ERR_OOM, BC_ERR_CUDA. */
 bc_status bc_pairs(bc_ctx_t ctx, const bc_shape_t *As, const bc_shape_t *Bs, const float *quats, int npairs,
                    float *out, float *peak, int *argmax, int on_device);
+
+/* ---------------------------------------------------------------- tuning
+ * Not in the paper: implementation choices that change speed, not results
+ * (beyond the FP32 rounding order of the spreading sums).
+ *   spread       0: every knot's W^3 stencil is added to its level's spreading
+ *                   box in device memory with global vector atomics, and the
+ *                   z transform reads the boxes back;
+ *                1: the knots are sorted into bins by their first stencil cell
+ *                   along x, and each z-transform item (level, x-cell, 32
+ *                   y-rows) adds the (y, z) stencil columns of the knots that
+ *                   reach it in shared memory before transforming them; no
+ *                   spreading box is kept in device memory.
+ *   sweep_batch  rotations per pass of bc_sweep, bc_sweep_plan and
+ *                bc_learned_sweep when their batch is 0 (1 .. 65534).
+ * A new context starts with {0, 64}.  Plans keep the choices in force when
+ * they were made.  bc_autotune times the candidates on the given shapes --
+ * bc_correlate of A with B (identity) for `spread`; when rotations > 0, a
+ * sweep of that many fixed rotations of B for each sweep_batch in
+ * {16, 32, 64, 128, 256} not above it -- keeps the fastest in the context and
+ * returns them in out (may be NULL).  It synchronises the stream and grows
+ * the context's workspaces to the largest candidate.  Errors: BC_ERR_ARG (null context or
+ * shape, shapes from another context, rotations outside [0, 65534], a value
+ * out of range in bc_set_tuning), BC_ERR_OOM, BC_ERR_CUDA. */
+typedef struct {
+    int spread;
+    int sweep_batch;
+} bc_tuning;
+bc_status bc_get_tuning(bc_ctx_t ctx, bc_tuning *out);
+bc_status bc_set_tuning(bc_ctx_t ctx, const bc_tuning *t);
+bc_status bc_autotune(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, int rotations, bc_tuning *out);
 
 /* ---------------------------------------------------------------- learned proposal
  * Not in the paper: a small network ranks rotations so that only the best

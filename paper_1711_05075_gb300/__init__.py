@@ -33,6 +33,10 @@ class bc_profile(ctypes.Structure):
                 ("bytes", ctypes.c_double * BC_NUM_STAGES)]
 
 
+class bc_tuning(ctypes.Structure):
+    _fields_ = [("spread", ctypes.c_int), ("sweep_batch", ctypes.c_int)]
+
+
 class BallCorrError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{BC_STATUS.get(status, status)}: {msg}")
@@ -103,6 +107,11 @@ def lib():
         L.bc_stage_name.restype = ctypes.c_char_p
         L.bc_correlate_noalloc.argtypes = [ctypes.POINTER(bc_params), vp, vp, i, vp, vp, i, vp, vp, vp]
         L.bc_correlate_noalloc.restype = st
+        L.bc_get_tuning.argtypes = [vp, ctypes.POINTER(bc_tuning)]
+        L.bc_set_tuning.argtypes = [vp, ctypes.POINTER(bc_tuning)]
+        L.bc_autotune.argtypes = [vp, vp, vp, i, ctypes.POINTER(bc_tuning)]
+        for f in ("bc_get_tuning", "bc_set_tuning", "bc_autotune"):
+            getattr(L, f).restype = st
         _lib = L
     return _lib
 
@@ -264,6 +273,23 @@ def bc_profile_end(ctx):
                        for s in range(BC_NUM_STAGES)]}
 
 
+def bc_get_tuning(ctx):
+    t = bc_tuning()
+    _check(lib().bc_get_tuning(ctx, ctypes.byref(t)))
+    return {"spread": t.spread, "sweep_batch": t.sweep_batch}
+
+
+def bc_set_tuning(ctx, spread, sweep_batch):
+    t = bc_tuning(int(spread), int(sweep_batch))
+    _check(lib().bc_set_tuning(ctx, ctypes.byref(t)))
+
+
+def bc_autotune(ctx, A, B, rotations=0):
+    t = bc_tuning()
+    _check(lib().bc_autotune(ctx, A, B, int(rotations), ctypes.byref(t)))
+    return {"spread": t.spread, "sweep_batch": t.sweep_batch}
+
+
 # ---------------------------------------------------------------- convenience
 def default_beta(W, sigma=2):
     return math.pi * math.sqrt((W / sigma) ** 2 * (sigma - 0.5) ** 2 - 0.8)
@@ -329,6 +355,20 @@ class Context:
 
     def sync(self):
         bc_sync(self.handle)
+
+    @property
+    def tuning(self):
+        """The context's implementation choices: {"spread": 0|1, "sweep_batch": int}."""
+        return bc_get_tuning(self.handle)
+
+    def set_tuning(self, spread=None, sweep_batch=None):
+        t = self.tuning
+        bc_set_tuning(self.handle, t["spread"] if spread is None else spread,
+                      t["sweep_batch"] if sweep_batch is None else sweep_batch)
+
+    def autotune(self, A, B, rotations=0):
+        """Times the candidates on these shapes and keeps the fastest (see bc_autotune)."""
+        return bc_autotune(self.handle, A.handle, B.handle, rotations)
 
     def close(self):
         if self.handle is not None:

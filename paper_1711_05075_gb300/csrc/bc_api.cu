@@ -75,13 +75,15 @@ struct DevBuf {
 // Device workspaces of one pipeline: the context's own, or a captured plan's.
 struct Workspace {
     DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, boxes, keys;
+    DevBuf cnt, cur, rec;     // binned spreading: bin counts (kept zeroed), bin cursors, knot records
     bool grid_dirty = false;  // spreading boxes may hold values (an enqueue failed midway)
     bool boxes_dirty = true;  // support-box accumulators need their reset state
+    bool bins_dirty = false;  // bin counts may be non-zero (an enqueue failed midway)
     std::vector<char> last_desc; // descriptors the device copies hold
     void *last_inst_p = nullptr, *last_pairs_p = nullptr;
     void release()
     {
-        DevBuf *b[] = {&ku, &plan, &inst, &pairs, &grid, &z1, &y1, &h, &fa, &boxes, &keys};
+        DevBuf *b[] = {&ku, &plan, &inst, &pairs, &grid, &z1, &y1, &h, &fa, &boxes, &keys, &cnt, &cur, &rec};
         for (DevBuf *x : b) x->release();
         last_desc.clear();
         last_inst_p = last_pairs_p = nullptr;
@@ -106,9 +108,12 @@ struct bc_ctx_s {
     int qmax = 0;
     // device status word
     int *err_dev = nullptr;
+    // implementation choices (bc_set_tuning / bc_autotune)
+    int spread_mode = 0;  // 0: spreading boxes in HBM (k_spread + k_fft_z); 1: binned, fused into the z pass
+    int sweep_batch = 64; // rotations per pass when a sweep's batch argument is 0
     // workspaces
     Workspace ws;                 // pipeline workspaces of direct calls
-    DevBuf outbuf, stats, learn;  // host-output staging, shape checks, learned-sweep scratch
+    DevBuf outbuf, stats, learn, tune; // host-output staging, shape checks, learned-sweep and tuning scratch
     std::set<bc_shape_s *> shapes; // live shapes; orphaned (device memory freed) by bc_destroy
     std::set<bc_mlp_s *> nets;     // live networks; orphaned the same way
     // profiling
@@ -116,7 +121,7 @@ struct bc_ctx_s {
     int prof_max = 0, prof_calls = 0;
     long long prof_launches = 0;
     std::vector<cudaEvent_t> prof_ev; // prof_max x (BC_NUM_STAGES + 1)
-    int last_ninst = 0, last_npairs = 0;
+    int last_ninst = 0, last_npairs = 0, last_mode = 0;
     std::vector<InstDesc> last_inst;
 };
 
@@ -306,7 +311,7 @@ bc_status bc_destroy(bc_ctx_t c)
         for (bc_mlp_s *net : c->nets) mlp_orphan(net);
         c->nets.clear();
         c->ws.release();
-        DevBuf *bufs[] = {&c->outbuf, &c->stats, &c->learn};
+        DevBuf *bufs[] = {&c->outbuf, &c->stats, &c->learn, &c->tune};
         for (DevBuf *b : bufs) b->release();
         delete c;
         return BC_OK;
@@ -459,8 +464,13 @@ bc_status bc_profile_end(bc_ctx_t c, bc_profile *out)
         }
         const double P = c->last_npairs, half = N * N * H;
         out->bytes[0] = knots * 16.0 * 2.0;                 // knots in, prepared knots out
-        out->bytes[1] = knots * 16.0 + cells * 4.0;         // prepared knots in, boxes out
-        out->bytes[2] = cells * 4.0 + zc * 8.0;
+        if (c->last_mode == 1) {
+            out->bytes[1] = knots * (16.0 + 4.0 * BIN_REC); // prepared knots in, binned records out
+            out->bytes[2] = knots * 4.0 * BIN_REC + zc * 8.0; // records in (once), z rows out
+        } else {
+            out->bytes[1] = knots * 16.0 + cells * 4.0;     // prepared knots in, boxes out
+            out->bytes[2] = cells * 4.0 + zc * 8.0;
+        }
         out->bytes[3] = zc * 8.0 + yc * 8.0;
         out->bytes[4] = yc * 8.0 + P * half * 8.0;
         out->bytes[5] = 2.0 * P * half * 8.0;
@@ -481,6 +491,7 @@ struct Job {
     std::vector<InstDesc> inst;
     std::vector<PairDesc> pairs;
     bool cache_first = false;
+    int mode = 0; // spreading: 0 boxes in HBM, 1 binned (fused into the z pass)
     int nmain = 0, koff = 0, max_knots = 0;
     long long goff = 0, zoff = 0, yoff = 0, hpairs = 0;
 };
@@ -493,6 +504,7 @@ static Job plan_job(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std
     Job j;
     j.pairs = pairs;
     j.cache_first = cache_first;
+    j.mode = c->spread_mode;
     j.nmain = (int)pairs.size() - (cache_first ? 1 : 0);
     j.inst.resize(shapes.size());
     for (size_t i = 0; i < shapes.size(); i++) {
@@ -527,12 +539,25 @@ static Job plan_job(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std
 
 // Grows the workspace to hold passes of up to these sizes (may synchronise the
 // stream and allocate; never called while a stream is being captured).
-static bc_status ensure_ws(bc_ctx_t c, Workspace &ws, long long koff, long long ninst, long long npairs, long long goff,
-                           long long zoff, long long yoff, long long hpairs)
+static bc_status ensure_ws(bc_ctx_t c, Workspace &ws, int mode, long long koff, long long ninst, long long npairs,
+                           long long goff, long long zoff, long long yoff, long long hpairs)
 {
     cudaStream_t st = c->stream;
     const int N = c->g.N, H = c->g.H;
     cudaError_t e;
+    if (mode == 1) {
+        goff = 1; // no spreading boxes
+        const size_t nbins = (size_t)std::max(ninst, 1LL) * c->g.L * c->g.n;
+        const size_t before = ws.cnt.bytes;
+        if ((e = ws.cnt.ensure(sizeof(int) * nbins, true, st)) != cudaSuccess) return cuda_fail(e, "bin counts");
+        if (ws.bins_dirty && ws.cnt.bytes == before) {
+            if ((e = cudaMemsetAsync(ws.cnt.p, 0, ws.cnt.bytes, st)) != cudaSuccess) return cuda_fail(e, "bin counts clear");
+        }
+        ws.bins_dirty = false;
+        if ((e = ws.cur.ensure(sizeof(int) * nbins, false, st)) != cudaSuccess) return cuda_fail(e, "bin cursors");
+        if ((e = ws.rec.ensure(sizeof(float) * BIN_REC * (size_t)std::max(koff, 1LL), false, st)) != cudaSuccess)
+            return cuda_fail(e, "knot records");
+    }
     if ((e = ws.ku.ensure(sizeof(float4) * (size_t)std::max(koff, 1LL), false, st)) != cudaSuccess) return cuda_fail(e, "ku");
     if ((e = ws.plan.ensure(sizeof(InstPlan) * (size_t)std::max(ninst, 1LL), false, st)) != cudaSuccess) return cuda_fail(e, "plan");
     {
@@ -564,7 +589,8 @@ static bc_status ensure_ws(bc_ctx_t c, Workspace &ws, long long koff, long long 
 // The kernel launches of one planned pass, with its descriptors already on the
 // device at dinst / dpairs.  Launches only (legal while a stream is captured).
 static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const InstDesc *dinst, const PairDesc *dpairs,
-                            float *dout, unsigned long long *keys, bool profile, cudaStream_t st)
+                            float *dout, unsigned long long *keys, bool profile, cudaStream_t st,
+                            long long *nlaunch = nullptr)
 {
     const Geometry &g = c->g;
     const int ninst = (int)job.inst.size();
@@ -578,21 +604,43 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
     auto mark = [&](int s) {
         if (profile) prof_mark(c, s);
     };
-    ws.grid_dirty = true; // until the z pass has consumed the spreading boxes
+    const bool binned = job.mode == 1;
     mark(-1);
     ws.boxes_dirty = true; // until k_plan has consumed and reset the accumulators
-    if ((e = launch_prepare(g, dinst, ninst, job.max_knots, (float4 *)ws.ku.p, (int *)ws.boxes.p, dplan, c->err_dev, st)) != cudaSuccess)
-        return cuda_fail(e, "prepare");
+    if (binned) {
+        ws.bins_dirty = true; // until the bin scan has consumed and cleared the counts
+        if ((e = launch_prepare(g, dinst, ninst, job.max_knots, (float4 *)ws.ku.p, (int *)ws.boxes.p, dplan,
+                                c->err_dev, (int *)ws.cnt.p, (int *)ws.cur.p, st)) != cudaSuccess)
+            return cuda_fail(e, "prepare");
+        ws.bins_dirty = false;
+        launches += 3;
+    } else {
+        ws.grid_dirty = true; // until the z pass has consumed the spreading boxes
+        if ((e = launch_prepare(g, dinst, ninst, job.max_knots, (float4 *)ws.ku.p, (int *)ws.boxes.p, dplan,
+                                c->err_dev, nullptr, nullptr, st)) != cudaSuccess)
+            return cuda_fail(e, "prepare");
+        launches += 2;
+    }
     ws.boxes_dirty = false;
-    launches += 2;
     mark(0);
-    if ((e = launch_spread(g, t, dinst, job.koff, (const float4 *)ws.ku.p, dplan, (float *)ws.grid.p, st)) != cudaSuccess)
-        return cuda_fail(e, "spread");
+    if (binned) {
+        if ((e = launch_bin(g, t, dinst, job.koff, (const float4 *)ws.ku.p, dplan, (int *)ws.cur.p, (float *)ws.rec.p, st)) != cudaSuccess)
+            return cuda_fail(e, "bin");
+    } else {
+        if ((e = launch_spread(g, t, dinst, job.koff, (const float4 *)ws.ku.p, dplan, (float *)ws.grid.p, st)) != cudaSuccess)
+            return cuda_fail(e, "spread");
+    }
     launches += job.koff > 0;
     mark(1);
-    if ((e = launch_fft_z(g, t, dinst, ninst, dplan, (float *)ws.grid.p, (float2 *)ws.z1.p, c->nsm, st)) != cudaSuccess)
-        return cuda_fail(e, "fft z");
-    ws.grid_dirty = false;
+    if (binned) {
+        if ((e = launch_fft_z_binned(g, t, dinst, ninst, dplan, (const int *)ws.cur.p, (const float *)ws.rec.p,
+                                     (float2 *)ws.z1.p, c->nsm, st)) != cudaSuccess)
+            return cuda_fail(e, "fft z (binned)");
+    } else {
+        if ((e = launch_fft_z(g, t, dinst, ninst, dplan, (float *)ws.grid.p, (float2 *)ws.z1.p, c->nsm, st)) != cudaSuccess)
+            return cuda_fail(e, "fft z");
+        ws.grid_dirty = false;
+    }
     launches++;
     mark(2);
     if ((e = launch_fft_y(g, t, dinst, ninst, dplan, (const float2 *)ws.z1.p, (float2 *)ws.y1.p, c->nsm, st)) != cudaSuccess)
@@ -623,11 +671,13 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
         launches++;
     }
     mark(6);
+    if (nlaunch) *nlaunch += launches;
     if (prof) {
         c->prof_calls++;
         c->prof_launches += launches;
         c->last_ninst = ninst;
         c->last_npairs = nmain;
+        c->last_mode = job.mode;
         c->last_inst = job.inst;
     }
     return BC_OK;
@@ -642,7 +692,7 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
     Workspace &ws = c->ws;
     const Job job = plan_job(c, shapes, quats, pairs, cache_first, qdev);
     const long long ninst = (long long)job.inst.size(), npairs = (long long)job.pairs.size();
-    if (bc_status s = ensure_ws(c, ws, job.koff, ninst, npairs, job.goff, job.zoff, job.yoff, job.hpairs)) return s;
+    if (bc_status s = ensure_ws(c, ws, job.mode, job.koff, ninst, npairs, job.goff, job.zoff, job.yoff, job.hpairs)) return s;
     const size_t inst_bytes = sizeof(InstDesc) * ninst, pair_bytes = sizeof(PairDesc) * npairs;
     std::vector<char> desc(inst_bytes + pair_bytes);
     std::memcpy(desc.data(), job.inst.data(), inst_bytes);
@@ -666,7 +716,7 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
 static bc_status sweep_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *qhost, const float *qdev, int k,
                             int batch, float *peak, int *argmax, int out_on_device)
 {
-    if (batch == 0) batch = 64;
+    if (batch == 0) batch = c->sweep_batch;
     const int N = c->g.N, H = c->g.H;
     cudaStream_t st = c->stream;
     cudaError_t e;
@@ -841,7 +891,6 @@ bc_status bc_sweep_plan(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *qua
                         int *argmax, bc_plan_t *out)
 {
     bc_plan_s *pl = nullptr;
-    bool capturing = false;
     try {
         if (!c || !A || !B || !quats || !peak || !argmax || !out) return fail(BC_ERR_ARG, "bc_sweep_plan: null argument");
         *out = nullptr;
@@ -849,7 +898,7 @@ bc_status bc_sweep_plan(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *qua
         if (k < 1 || k > (1 << 24)) return fail(BC_ERR_ARG, "bc_sweep_plan: k must be in [1, 2^24]");
         if (batch < 0 || batch > 65534) return fail(BC_ERR_ARG, "bc_sweep_plan: batch must be in [0, 65534]");
         if (bc_status s = check_quats(quats, k, "bc_sweep_plan")) return s;
-        if (batch == 0) batch = 64;
+        if (batch == 0) batch = c->sweep_batch;
         const int N = c->g.N, H = c->g.H;
         cudaStream_t st = c->stream;
         cudaError_t e;
@@ -885,7 +934,7 @@ bc_status bc_sweep_plan(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *qua
             doff[j] = dbytes;
             dbytes += (sizeof(InstDesc) * jb.inst.size() + sizeof(PairDesc) * jb.pairs.size() + 255) & ~size_t(255);
         }
-        if (bc_status s = ensure_ws(c, pl->ws, mk, mi, mp, mg, mz, my, mh)) {
+        if (bc_status s = ensure_ws(c, pl->ws, jobs[0].mode, mk, mi, mp, mg, mz, my, mh)) {
             bc_plan_destroy(pl);
             return s;
         }
@@ -918,7 +967,6 @@ bc_status bc_sweep_plan(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *qua
             bc_plan_destroy(pl);
             return cuda_fail(e, "bc_sweep_plan: begin capture");
         }
-        capturing = true;
         bc_status s = BC_OK;
         if ((e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)k, cs)) != cudaSuccess)
             s = cuda_fail(e, "bc_sweep_plan: clear keys");
@@ -926,13 +974,12 @@ bc_status bc_sweep_plan(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *qua
             const char *base = (const char *)pl->desc.p + doff[j];
             s = launch_job(c, pl->ws, jobs[j], (const InstDesc *)base,
                            (const PairDesc *)(base + sizeof(InstDesc) * jobs[j].inst.size()), nullptr,
-                           j == 0 ? nullptr : keys, false, cs);
+                           j == 0 ? nullptr : keys, false, cs, &pl->launches);
         }
         if (s == BC_OK && (e = launch_decode_peaks(keys, k, peak, argmax, cs)) != cudaSuccess)
             s = cuda_fail(e, "bc_sweep_plan: decode");
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(cs, &graph);
-        capturing = false;
         cudaStreamDestroy(cs);
         if (s == BC_OK && e != cudaSuccess) s = cuda_fail(e, "bc_sweep_plan: end capture");
         if (s == BC_OK && (e = cudaGraphInstantiate(&pl->exec, graph, 0)) != cudaSuccess)
@@ -942,13 +989,10 @@ bc_status bc_sweep_plan(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *qua
             bc_plan_destroy(pl);
             return s;
         }
-        size_t nodes = 0;
-        pl->launches = (long long)jobs.size() * 8; // upper bound, for reporting
-        (void)nodes;
+        pl->launches += 1; // the peak decode
         *out = pl;
         return BC_OK;
     } catch (...) {
-        (void)capturing;
         if (pl) bc_plan_destroy(pl);
         return fail(BC_ERR_INTERNAL, "bc_sweep_plan: unexpected exception");
     }
@@ -1024,6 +1068,133 @@ bc_status bc_learned_sweep(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B,
         return sweep_impl(c, A, B, nullptr, qsel, topk, 0, peak, argmax, 1);
     } catch (...) {
         return fail(BC_ERR_INTERNAL, "bc_learned_sweep: unexpected exception");
+    }
+}
+
+// ------------------------------------------------------------------ tuning
+
+bc_status bc_get_tuning(bc_ctx_t c, bc_tuning *out)
+{
+    if (!c || !out) return fail(BC_ERR_ARG, "bc_get_tuning: null argument");
+    out->spread = c->spread_mode;
+    out->sweep_batch = c->sweep_batch;
+    return BC_OK;
+}
+
+bc_status bc_set_tuning(bc_ctx_t c, const bc_tuning *t)
+{
+    if (!c || !t) return fail(BC_ERR_ARG, "bc_set_tuning: null argument");
+    if (t->spread != 0 && t->spread != 1) return fail(BC_ERR_ARG, "bc_set_tuning: spread must be 0 or 1");
+    if (t->sweep_batch < 1 || t->sweep_batch > 65534) return fail(BC_ERR_ARG, "bc_set_tuning: sweep_batch must be in [1, 65534]");
+    c->spread_mode = t->spread;
+    c->sweep_batch = t->sweep_batch;
+    return BC_OK;
+}
+
+} // extern "C"
+
+// Median device time (ms) of `reps` calls of fn after `warm` untimed ones,
+// each bracketed by events on the context stream.
+template <class F>
+static bc_status time_median(bc_ctx_t c, F fn, int warm, int reps, float *ms)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e, "tuning events");
+    }
+    bc_status s = BC_OK;
+    std::vector<float> t;
+    for (int i = 0; s == BC_OK && i < warm + reps; i++) {
+        if (i >= warm && (e = cudaEventRecord(e0, c->stream)) != cudaSuccess) s = cuda_fail(e, "tuning record");
+        if (s == BC_OK) s = fn();
+        if (s == BC_OK && i >= warm) {
+            float x = 0.f;
+            if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                (e = cudaEventElapsedTime(&x, e0, e1)) != cudaSuccess)
+                s = cuda_fail(e, "tuning timing");
+            t.push_back(x);
+        }
+    }
+    if (s == BC_OK) s = bc_sync(c);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != BC_OK) return s;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return BC_OK;
+}
+
+extern "C" {
+
+bc_status bc_autotune(bc_ctx_t c, bc_shape_t A, bc_shape_t B, int rotations, bc_tuning *out)
+{
+    try {
+        if (!c || !A || !B) return fail(BC_ERR_ARG, "bc_autotune: null argument");
+        if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_autotune: shapes belong to another context");
+        if (rotations < 0 || rotations > 65534) return fail(BC_ERR_ARG, "bc_autotune: rotations must be in [0, 65534]");
+        CK(cudaStreamSynchronize(c->stream));
+        const long long N3 = (long long)c->g.N * c->g.N * c->g.N;
+        cudaError_t e;
+        if ((e = c->tune.ensure(sizeof(float) * (size_t)std::max<long long>(N3, 2LL * rotations), false, c->stream)) != cudaSuccess)
+            return cuda_fail(e, "bc_autotune: scratch");
+        float *dout = (float *)c->tune.p;
+        // spreading: one correlation of A with B, unrotated
+        static const float ident[4] = {1.f, 0.f, 0.f, 0.f};
+        float best = 0.f;
+        int best_mode = c->spread_mode;
+        for (int mode = 0; mode <= 1; mode++) {
+            c->spread_mode = mode;
+            float ms = 0.f;
+            bc_status s = time_median(c, [&]() { return bc_correlate(c, A, B, ident, 1, dout, 1); }, 3, 7, &ms);
+            if (s != BC_OK) {
+                c->spread_mode = best_mode;
+                return s;
+            }
+            if (mode == 0 || ms < best) {
+                best = ms;
+                best_mode = mode;
+            }
+        }
+        c->spread_mode = best_mode;
+        if (rotations > 0) {
+            // fixed rotations: Shoemake's map of a golden-ratio (Weyl) sequence in [0, 1)^3
+            std::vector<float> q(4 * (size_t)rotations);
+            for (int r = 0; r < rotations; r++) {
+                const double u1 = std::fmod(0.5 + r * 0.6180339887498949, 1.0);
+                const double u2 = std::fmod(0.5 + r * 0.7548776662466927, 1.0);
+                const double u3 = std::fmod(0.5 + r * 0.5698402909980532, 1.0);
+                const double a = std::sqrt(1.0 - u1), b = std::sqrt(u1);
+                q[4 * r + 0] = (float)(a * std::sin(2 * M_PI * u2));
+                q[4 * r + 1] = (float)(a * std::cos(2 * M_PI * u2));
+                q[4 * r + 2] = (float)(b * std::sin(2 * M_PI * u3));
+                q[4 * r + 3] = (float)(b * std::cos(2 * M_PI * u3));
+            }
+            float *dpeak = dout;
+            int *darg = (int *)(dout + rotations);
+            static const int cand[] = {16, 32, 64, 128, 256};
+            int best_batch = c->sweep_batch;
+            bool first = true;
+            for (int b : cand) {
+                if (b > std::max(rotations, 16)) break;
+                float ms = 0.f;
+                bc_status s = time_median(
+                    c, [&]() { return sweep_impl(c, A, B, q.data(), nullptr, rotations, b, dpeak, darg, 1); }, 1, 3, &ms);
+                if (s != BC_OK) return s;
+                if (first || ms < best) {
+                    best = ms;
+                    best_batch = b;
+                    first = false;
+                }
+            }
+            c->sweep_batch = best_batch;
+        }
+        if (out) bc_get_tuning(c, out);
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_autotune: unexpected exception");
     }
 }
 

@@ -1,0 +1,65 @@
+// Device helpers shared by the kernel translation units (bc_kernels.cu,
+// bc_binned.cu).  Not part of the public interface.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "bc_fft.cuh"
+#include "bc_internal.h"
+
+namespace bc {
+
+constexpr int TB = 256; // threads per transform block
+constexpr int CL = 16;  // interleaved lines per tile (16 complex = 128 bytes per tile row)
+
+// Block loop over the work items of a sequence of instances (or pairs),
+// giving each block of the grid an even share across them.
+struct RotStart {
+    int rot = 0;
+    __device__ __forceinline__ int first() const
+    {
+        const int st = rot % (int)gridDim.x;
+        return ((int)blockIdx.x - st + (int)gridDim.x) % (int)gridDim.x;
+    }
+};
+
+template <int NF>
+__device__ __forceinline__ void load_twiddles(float2 *dst, const float2 *__restrict__ src)
+{
+    for (int k = threadIdx.x; k < NF; k += blockDim.x) dst[k] = src[k];
+}
+
+// Kaiser-Bessel window phi(v) = I0(beta sqrt(1 - s^2)) / I0(beta), s = 2v/W,
+// zero for |s| > 1 (the clamp makes it 1/I0(beta) there, which callers never
+// reach: every stencil offset satisfies |s| <= 1).
+//
+// Evaluated as exp(beta (sq - 1)) * [exp(-x) I0(x)] / [exp(-beta) I0(beta)],
+// x = beta sq: I0 grows like e^x, so I0(x) alone carries the FP32 rounding of
+// x as a relative error of about x 2^-24, whereas exp(-x) I0(x) varies slowly
+// and the exponent beta (sq - 1) = -beta s^2 / (1 + sq) is small where phi is
+// large.  inv_scaled_i0beta = exp(beta) / I0(beta), built in FP64.
+__device__ __forceinline__ float kb_window(float s, float beta, float inv_scaled_i0beta)
+{
+    const float s2 = fminf(s * s, 1.f);
+    const float sq = sqrtf(1.f - s2);
+    const float x = beta * sq;
+    const float scaled_i0 = cyl_bessel_i0f(x) * expf(-x);
+    return expf(-beta * s2 / (1.f + sq)) * scaled_i0 * inv_scaled_i0beta;
+}
+
+// Blocks per launch: the number that can be resident on the device at once.
+template <typename K>
+static int resident_blocks(K kernel, size_t smem, int nsm, int threads = TB)
+{
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess || per < 1) per = 1;
+    return per * nsm;
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes)
+{
+    if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+} // namespace bc

@@ -42,25 +42,34 @@ __device__ __forceinline__ float2 mul_mi(float2 a)
     return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-// exp(-+2 pi i e / 16) for the exponents a radix-16 butterfly uses (e = 0..9)
-template <bool INV>
-__device__ __forceinline__ float2 tw16(int e)
+// x * exp(-+2 pi i E / 16) for the exponents a radix-16 butterfly uses
+// (E = n2 k1, n2, k1 < 4).  E = 0 and 4 are exact (identity, -+i); E = 2 and 6
+// take two adds and two multiplies by sqrt(1/2); the rest a complex multiply.
+template <int E, bool INV>
+__device__ __forceinline__ float2 tw16_mul(float2 x)
 {
     const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, h = 0.70710678118654752440f;
-    float2 w;
-    switch (e) {
-    case 0: w = make_float2(1.f, 0.f); break;
-    case 1: w = make_float2(c1, -s1); break;
-    case 2: w = make_float2(h, -h); break;
-    case 3: w = make_float2(s1, -c1); break;
-    case 4: w = make_float2(0.f, -1.f); break;
-    case 6: w = make_float2(-h, -h); break;
-    case 9: w = make_float2(-c1, s1); break;
-    default: w = make_float2(1.f, 0.f); break; // not used
+    const float sg = INV ? -1.f : 1.f; // imaginary part of the twiddle flips for the inverse
+    if constexpr (E == 0) {
+        return x;
+    } else if constexpr (E == 4) {
+        return mul_mi<INV>(x);
+    } else if constexpr (E == 2) { // (1 -+ i) h
+        return INV ? make_float2(h * (x.x - x.y), h * (x.x + x.y)) : make_float2(h * (x.x + x.y), h * (x.y - x.x));
+    } else if constexpr (E == 6) { // (-1 -+ i) h
+        return INV ? make_float2(-h * (x.x + x.y), h * (x.x - x.y)) : make_float2(h * (x.y - x.x), -h * (x.x + x.y));
+    } else if constexpr (E == 1) {
+        return cmul(x, make_float2(c1, -sg * s1));
+    } else if constexpr (E == 3) {
+        return cmul(x, make_float2(s1, -sg * c1));
+    } else {
+        static_assert(E == 9, "radix-16 twiddle exponent");
+        return cmul(x, make_float2(-c1, sg * s1));
     }
-    if (INV) w.y = -w.y;
-    return w;
 }
+
+template <int N2, int K1, bool INV>
+__device__ __forceinline__ float2 tw16_apply(float2 x) { return tw16_mul<N2 * K1, INV>(x); }
 
 template <int R, bool INV>
 __device__ __forceinline__ void dft_small(float2 *v)
@@ -95,8 +104,17 @@ __device__ __forceinline__ void dft_small(float2 *v)
             float2 t[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
             dft_small<4, INV>(t);
 #pragma unroll
-            for (int k1 = 0; k1 < 4; k1++) y[n2][k1] = cmul(t[k1], tw16<INV>(n2 * k1));
+            for (int k1 = 0; k1 < 4; k1++) y[n2][k1] = t[k1];
         }
+        y[1][1] = tw16_apply<1, 1, INV>(y[1][1]);
+        y[1][2] = tw16_apply<1, 2, INV>(y[1][2]);
+        y[1][3] = tw16_apply<1, 3, INV>(y[1][3]);
+        y[2][1] = tw16_apply<2, 1, INV>(y[2][1]);
+        y[2][2] = tw16_apply<2, 2, INV>(y[2][2]);
+        y[2][3] = tw16_apply<2, 3, INV>(y[2][3]);
+        y[3][1] = tw16_apply<3, 1, INV>(y[3][1]);
+        y[3][2] = tw16_apply<3, 2, INV>(y[3][2]);
+        y[3][3] = tw16_apply<3, 3, INV>(y[3][3]);
 #pragma unroll
         for (int k1 = 0; k1 < 4; k1++) {
             float2 t[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};

@@ -66,8 +66,24 @@ cudaError_t launch_pack_knots(const float *xyz, const int *level, int n, int L, 
 // bb: 8 ints per instance (support-box accumulators); they must hold the reset
 // state (launch_reset_boxes) before the first launch and are left reset.
 cudaError_t launch_reset_boxes(int *bb, int ninst, cudaStream_t s);
+// With cnt (ninst * L * n zeroed ints) the knots are also counted per bin
+// (instance, level, first stencil cell along x mod n) and the counts turned
+// into bin cursors cur (same size; cnt is left zeroed) for launch_bin.
 cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, int max_knots, float4 *ku, int *bb,
-                           InstPlan *plan, int *err, cudaStream_t s);
+                           InstPlan *plan, int *err, int *cnt, int *cur, cudaStream_t s);
+// Binned spreading (bc_binned.cu).  cur[b] = first slot of bin b (the
+// instance's knot_off plus the counts of the bins before it in the instance);
+// launch_bin writes one BIN_REC-float record per knot into its bin (cur[b] is
+// then the end of bin b); launch_fft_z_binned spreads each z-transform item's
+// knots in shared memory and transforms them (no spreading grid in HBM).
+constexpr int MAX_W = 10;   // widest window (bc_create checks)
+constexpr int BIN_REC = 32; // floats per binned knot: g0_y, g0_z (int bits), W x-, W y-, W z-weights
+cudaError_t launch_bin_scan(const Geometry &g, const InstDesc *inst, int ninst, int *cnt, int *cur, cudaStream_t s);
+cudaError_t launch_bin(const Geometry &g, const Tables &t, const InstDesc *inst, int total_knots, const float4 *ku,
+                       const InstPlan *plan, int *cur, float *rec, cudaStream_t s);
+cudaError_t launch_fft_z_binned(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
+                                const InstPlan *plan, const int *cur, const float *rec, float2 *z1, int nsm,
+                                cudaStream_t s);
 cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *inst, int total_knots,
                           const float4 *ku, const InstPlan *plan, float *grid, cudaStream_t s);
 cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,

@@ -31,8 +31,7 @@
 #include <climits>
 #include <cstdint>
 
-#include "bc_fft.cuh"
-#include "bc_internal.h"
+#include "bc_device.cuh"
 
 namespace bc {
 
@@ -163,7 +162,7 @@ cudaError_t launch_pack_knots(const float *xyz, const int *level, int n, int L, 
 constexpr int PREP_THREADS = 256;
 
 __global__ void __launch_bounds__(PREP_THREADS)
-k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 *ku, int *bb)
+k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 *ku, int *bb, int *cnt)
 {
     const int i = blockIdx.y;
     const InstDesc d = inst[i];
@@ -201,6 +200,10 @@ k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 *ku, int *bb)
         }
         const int tag = __float_as_int(c.w) | (i << 4);
         ku[d.knot_off + j] = make_float4(u[0], u[1], u[2], __int_as_float(tag));
+        if (cnt) { // knot count per (instance, level, first stencil cell along x mod n)
+            const int gx = lo[0] < 0 ? lo[0] + g.n : lo[0];
+            atomicAdd(&cnt[((long long)i * g.L + __float_as_int(c.w)) * g.n + gx], 1);
+        }
     }
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -271,15 +274,17 @@ cudaError_t launch_reset_boxes(int *bb, int ninst, cudaStream_t s)
 }
 
 cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, int max_knots, float4 *ku, int *bb,
-                           InstPlan *plan, int *err, cudaStream_t s)
+                           InstPlan *plan, int *err, int *cnt, int *cur, cudaStream_t s)
 {
     if (ninst <= 0) return cudaSuccess;
     const int bx = max_knots > 0 ? (max_knots + PREP_THREADS - 1) / PREP_THREADS : 1;
-    k_prepare<<<dim3(bx, ninst), PREP_THREADS, 0, s>>>(g, inst, ku, bb);
+    k_prepare<<<dim3(bx, ninst), PREP_THREADS, 0, s>>>(g, inst, ku, bb, cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_plan<<<(ninst + 127) / 128, 128, 0, s>>>(g, inst, ninst, bb, plan, err);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (cnt) return launch_bin_scan(g, inst, ninst, cnt, cur, s);
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ spread
@@ -315,24 +320,13 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
         const int level = tag & 15, i = tag >> 4;
         const InstPlan p = plan[i];
         if (p.b[0] == 0) continue;
-        const float u[3] = {v.x, v.y, v.z};
-        int g0[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) g0[a] = (int)ceilf(u[a] - halfW);
+        const float u0 = v.x, u1 = v.y, u2 = v.z;
+        const int g0[3] = {(int)ceilf(u0 - halfW), (int)ceilf(u1 - halfW), (int)ceilf(u2 - halfW)};
         if (lane < 3 * W) {
-            // phi = I0(beta sq) / I0(beta), sq = sqrt(1 - s^2), evaluated as
-            // exp(beta (sq - 1)) * [exp(-x) I0(x)] / [exp(-beta) I0(beta)], x = beta sq.
-            // I0 grows like e^x, so I0(x) alone carries the FP32 rounding of x as a
-            // relative error of about x * 2^-24; exp(-x) I0(x) varies slowly and
-            // the exponent beta (sq - 1) = -beta s^2 / (1 + sq) is small where
-            // phi is large.
             const int a = lane / W, t = lane - a * W;
-            const float s = (u[a] - (float)(g0[a] + t)) * twoOverW;
-            const float s2 = fminf(s * s, 1.f);
-            const float sq = sqrtf(1.f - s2);
-            const float x = g.beta * sq;
-            const float scaled_i0 = cyl_bessel_i0f(x) * expf(-x);
-            wts[wib][a][t] = expf(-g.beta * s2 / (1.f + sq)) * scaled_i0 * inv_scaled_i0beta;
+            const float ua = a == 0 ? u0 : (a == 1 ? u1 : u2);
+            const int ga = a == 0 ? g0[0] : (a == 1 ? g0[1] : g0[2]);
+            wts[wib][a][t] = kb_window((ua - (float)(ga + t)) * twoOverW, g.beta, inv_scaled_i0beta);
         }
         __syncwarp();
         const int nyb = (p.b[1] + 31) >> 5, bz = p.b[2];
@@ -379,27 +373,6 @@ cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *in
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ helpers
-// Block loop over the work items of a sequence of instances (or pairs),
-// giving each block of the grid an even share across them.
-struct RotStart {
-    int rot = 0;
-    __device__ __forceinline__ int first() const
-    {
-        const int st = rot % (int)gridDim.x;
-        return ((int)blockIdx.x - st + (int)gridDim.x) % (int)gridDim.x;
-    }
-};
-
-template <int NF>
-__device__ __forceinline__ void load_twiddles(float2 *dst, const float2 *__restrict__ src)
-{
-    for (int k = threadIdx.x; k < NF; k += blockDim.x) dst[k] = src[k];
-}
-
-constexpr int TB = 256;  // threads per transform block
-constexpr int CL = 16;   // interleaved lines per tile (16 complex = 128 bytes per tile row)
-
 // ------------------------------------------------------------------ fft z
 // Item: 32 real rows (iy0 .. iy0+31) of one (level, ix) plane, packed as 16
 // complex lines (row 2q in the real part, row 2q+1 in the imaginary part of
@@ -412,7 +385,7 @@ constexpr int CL = 16;   // interleaved lines per tile (16 complex = 128 bytes p
 // Output rows: with Z = FFT(a + i b), A_k = (Z_k + conj Z_{n-k}) / 2,
 // B_k = (Z_k - conj Z_{n-k}) / (2i), for m_z = k in [0, N/2).
 template <int NF, bool SP>
-__global__ void __launch_bounds__(TB, 2)
+__global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
         float *grid, float2 *z1)
 {
@@ -423,7 +396,8 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     float2 *OUT = three ? S0 : S1; // tile the last stage writes (not the one it reads)
     float2 *STG = three ? S1 : S0; // staging for the output rows
     load_twiddles<NF>(tw, tb.tw_n);
-    const int H = g.H, L = g.L;
+    constexpr int H = NF / 4; // kept z modes (N/2, n = 2N)
+    const int L = g.L;
     FirstInputs<NF, Radix<NF>::r0, CL, TB> in;
     RotStart rs;
     for (int i = 0; i < ninst; i++) {
@@ -494,7 +468,7 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
 // last-stage outputs go straight to y1; the next item is loaded while the
 // current one finishes.
 template <int NF, bool SP>
-__global__ void __launch_bounds__(TB, 2)
+__global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
         const float2 *__restrict__ z1, float2 *y1)
 {
@@ -502,8 +476,9 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     float2 *tw = reinterpret_cast<float2 *>(sm4);
     float2 *S0 = tw + NF, *S1 = S0 + NF * CL;
     load_twiddles<NF>(tw, tb.tw_n);
-    const int H = g.H, L = g.L, N = g.N;
-    const int nch = H / CL;
+    constexpr int H = NF / 4, N = NF / 2;
+    const int L = g.L;
+    constexpr int nch = H / CL;
     FirstInputs<NF, Radix<NF>::r0, CL, TB> in;
     RotStart rs;
     for (int i = 0; i < ninst; i++) {
@@ -565,7 +540,8 @@ __device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF>::IT][XModes<NF
                                            int jy, int ch, const float2 *tw, float2 *S0, float2 *S1)
 {
     using XM = XModes<NF>;
-    const int H = g.H, L = g.L, N = NI;
+    constexpr int H = NI / 2, N = NI;
+    const int L = g.L;
     const int Q = tb.qmax + 1;
     const int my = mode_of(jy, N);
     const float djy = tb.deconv[jy];
@@ -648,8 +624,8 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
     float2 *twI = twF + NF, *S0 = twI + NI, *S1 = S0 + NF * CL, *FAt = S1 + NF * CL;
     load_twiddles<NF>(twF, tb.tw_n);
     load_twiddles<NI>(twI, tb.tw_N);
-    const int H = g.H, N = NI;
-    const int nch = H / CL;
+    constexpr int H = NI / 2, N = NI;
+    constexpr int nch = H / CL;
     const int items = N * nch;
     const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3;
     RotStart rs;
@@ -711,8 +687,8 @@ k_ifft_y(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
     float2 *tw = reinterpret_cast<float2 *>(sm4);
     float2 *S0 = tw + NI, *S1 = S0 + NI * CL;
     load_twiddles<NI>(tw, tb.tw_N);
-    const int H = g.H, N = NI;
-    const int nch = H / CL;
+    constexpr int H = NI / 2, N = NI;
+    constexpr int nch = H / CL;
     const int items = N * nch;
     FirstInputs<NI, Radix<NI>::r0, CL, TB> in;
     RotStart rs;
@@ -788,7 +764,7 @@ k_ifft_z(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
     float2 *tw = reinterpret_cast<float2 *>(sm4);
     float2 *A = tw + NI, *B = A + NI * CL;
     load_twiddles<NI>(tw, tb.tw_N);
-    const int H = g.H, N = NI;
+    constexpr int H = NI / 2, N = NI;
     const int nyb = N / 32;
     const int items = N * nyb;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -858,22 +834,6 @@ k_ifft_z(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
 }
 
 // ------------------------------------------------------------------ launchers
-// Blocks per launch: the number that can be resident on the device at once.
-template <typename K>
-static int resident_blocks(K kernel, size_t smem, int nsm)
-{
-    int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, TB, smem) != cudaSuccess || per < 1) per = 1;
-    return per * nsm;
-}
-
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes)
-{
-    if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    return cudaSuccess;
-}
-
 template <int NF, bool SP = false>
 static cudaError_t fft_z_t(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
                            float *grid, float2 *z1, int nsm, cudaStream_t s)

@@ -216,7 +216,7 @@ extern "C" bc_status bc_correlate_noalloc(const bc_params *p, const float *xyzA,
         t.tw_N = twN;
         t.qmax = kQ - 1;
         t.consts = consts;
-        if ((e = launch_prepare(g, dinst, 2, nA > nB ? nA : nB, ku, boxes, dplan, err, st)) != cudaSuccess)
+        if ((e = launch_prepare(g, dinst, 2, nA > nB ? nA : nB, ku, boxes, dplan, err, nullptr, nullptr, st)) != cudaSuccess)
             return ncuda(e, "prepare");
         if ((e = launch_spread(g, t, dinst, nA + nB, ku, dplan, grid, st)) != cudaSuccess) return ncuda(e, "spread");
         if ((e = launch_fft_z(g, t, dinst, 2, dplan, grid, z1, nsm, st)) != cudaSuccess) return ncuda(e, "fft z");

@@ -3,7 +3,10 @@
 Both sides get identical inputs: the seeded knots and quaternions rounded once
 to FP32 (the library's input type) and widened back to FP64 for the oracle.
 Bar: rel-L2 <= 1e-5 over the compared points (FP32 path), as the method's
-accuracy target states; max-abs is reported beside it.
+accuracy target states; max-abs is reported beside it.  Every workload runs
+with both spreading implementations (spread 0: boxes in HBM with global
+atomics; spread 1: knots binned by x-cell and spread in shared memory inside
+the z transform).
 """
 import math
 
@@ -36,10 +39,14 @@ def f32(shape):
     return synth.Shape(shape.xyz.astype(np.float32).astype(np.float64), shape.level, shape.radii, shape.name)
 
 
-def run_gpu(A, B, quats, N, W, radii=None, period=2.0):
+SPREADS = (0, 1)
+
+
+def run_gpu(A, B, quats, N, W, radii=None, period=2.0, spread=1):
     bc = bcmod()
     radii = A.radii if radii is None else radii
     ctx = bc.Context(N, W, radii, period)
+    ctx.set_tuning(spread=spread)
     try:
         sa = ctx.shape(A.xyz.astype(np.float32), A.level)
         sb = ctx.shape(B.xyz.astype(np.float32), B.level)
@@ -51,6 +58,12 @@ def run_gpu(A, B, quats, N, W, radii=None, period=2.0):
     finally:
         ctx.close()
     return out
+
+
+def run_modes(*args, **kw):
+    """(spread, grids) for each spreading implementation."""
+    for sp in SPREADS:
+        yield sp, run_gpu(*args, spread=sp, **kw)
 
 
 def oracle_grid(A, B, q, N, period=2.0):
@@ -72,29 +85,30 @@ def check(got, ref, tol=REL_TOL, what=""):
 # ------------------------------------------------------------------ workloads
 def test_small_pair_full_grid():
     wl = synth.small_pair(0)
-    got = run_gpu(wl.A, wl.B, wl.quats, wl.N, wl.W)[0]
     ref = oracle_grid(wl.A, wl.B, wl.quats[0], wl.N)
-    check(got, ref, what=wl.name)
+    for sp, got in run_modes(wl.A, wl.B, wl.quats, wl.N, wl.W):
+        check(got[0], ref, what=f"{wl.name} spread {sp}")
 
 
 def test_scale_pair_full_grid_and_sampled():
     wl = synth.scale_pair(0)
-    got = run_gpu(wl.A, wl.B, wl.quats, wl.N, wl.W)[0]
     g = O.band_limited_spectrum(f32(wl.A), f32(wl.B), wl.quats[0].astype(np.float32).astype(np.float64), wl.N)
     ref = O.inverse_grid(g)
-    check(got, ref, what=wl.name + " full grid")
     idx = synth.translation_sample(wl.N, 4096, seed=0)
     pts = O.inverse_at(g, O.grid_points(wl.N, idx=idx))
-    check(got.reshape(-1)[idx], pts, what=wl.name + " 4096 sampled t")
+    for sp, got in run_modes(wl.A, wl.B, wl.quats, wl.N, wl.W):
+        check(got[0], ref, what=f"{wl.name} full grid, spread {sp}")
+        check(got[0].reshape(-1)[idx], pts, what=f"{wl.name} 4096 sampled t, spread {sp}")
 
 
 @pytest.mark.parametrize("k", [1, 3])
 def test_rotations(k):
     wl = synth.small_pair(1)
     q = synth.shoemake_quaternions(synth.SplitMix64(99), k)
-    got = run_gpu(wl.A, wl.B, q, wl.N, wl.W)
-    for r in range(k):
-        check(got[r], oracle_grid(wl.A, wl.B, q[r], wl.N), what=f"rotation {r} of {k}")
+    refs = [oracle_grid(wl.A, wl.B, q[r], wl.N) for r in range(k)]
+    for sp, got in run_modes(wl.A, wl.B, q, wl.N, wl.W):
+        for r in range(k):
+            check(got[r], refs[r], what=f"rotation {r} of {k}, spread {sp}")
 
 
 @pytest.mark.parametrize("N,W,n", [(32, 8, 300), (64, 8, 400), (96, 8, 500), (128, 6, 300)])
@@ -102,9 +116,10 @@ def test_grid_sizes(N, W, n):
     A = synth.ellipsoid_shape(n, 5, synth.RADII_4, synth.PROBS_4)
     B = synth.torus_shape(n, 6, synth.RADII_4, synth.PROBS_4)
     q = synth.shoemake_quaternions(synth.SplitMix64(3), 2)
-    got = run_gpu(A, B, q, N, W)
-    for r in range(2):
-        check(got[r], oracle_grid(A, B, q[r], N), what=f"N={N} W={W} rot {r}")
+    refs = [oracle_grid(A, B, q[r], N) for r in range(2)]
+    for sp, got in run_modes(A, B, q, N, W):
+        for r in range(2):
+            check(got[r], refs[r], what=f"N={N} W={W} rot {r} spread {sp}")
 
 
 def test_grid_size_256_sampled():
@@ -112,19 +127,22 @@ def test_grid_size_256_sampled():
     A = synth.ellipsoid_shape(300, 7, synth.RADII_4, synth.PROBS_4)
     B = synth.torus_shape(300, 8, synth.RADII_4, synth.PROBS_4)
     q = synth.IDENTITY_QUAT
-    got = run_gpu(A, B, q, N, W)[0]
     g = O.band_limited_spectrum(f32(A), f32(B), q[0], N)
     idx = synth.translation_sample(N, 4096, seed=1)
-    check(got.reshape(-1)[idx], O.inverse_at(g, O.grid_points(N, idx=idx)), what="N=256 sampled")
+    ref = O.inverse_at(g, O.grid_points(N, idx=idx))
+    for sp, got in run_modes(A, B, q, N, W):
+        check(got[0].reshape(-1)[idx], ref, what=f"N=256 sampled, spread {sp}")
 
 
 # ------------------------------------------------------------------ edge cases
-def test_repeated_calls_are_identical():
-    # The spreading boxes are cleared by the pass that consumes them; a second
-    # call on the same context must not see the first call's grids.
+@pytest.mark.parametrize("spread", SPREADS)
+def test_repeated_calls_are_identical(spread):
+    # The spreading boxes (bin counts) are cleared by the pass that consumes
+    # them; a second call on the same context must not see the first call's.
     bc = bcmod()
     wl = synth.small_pair(2)
     ctx = bc.Context(wl.N, wl.W, wl.radii)
+    ctx.set_tuning(spread=spread)
     sa = ctx.shape(wl.A.xyz, wl.A.level)
     sb = ctx.shape(wl.B.xyz, wl.B.level)
     g1 = ctx.correlate(sa, sb, wl.quats).clone()
@@ -179,16 +197,18 @@ def test_single_balls_and_two_ball_closed_form():
     A = synth.Shape(np.array([[0.1, -0.2, 0.05]]), np.array([1], np.int32), (0.04, 0.08))
     B = synth.Shape(np.array([[-0.3, 0.1, 0.2]]), np.array([0], np.int32), (0.04, 0.08))
     q = synth.shoemake_quaternions(synth.SplitMix64(5), 1)
-    got = run_gpu(A, B, q, 32, 6)[0]
-    check(got, oracle_grid(A, B, q[0], 32), what="one ball each")
+    ref = oracle_grid(A, B, q[0], 32)
+    for sp, got in run_modes(A, B, q, 32, 6):
+        check(got[0], ref, what=f"one ball each, spread {sp}")
 
 
 def test_empty_level_and_single_level():
     A = synth.ellipsoid_shape(200, 11)
     A0 = synth.Shape(A.xyz, np.zeros_like(A.level), A.radii)  # level 1 empty
     B = synth.torus_shape(150, 12)
-    got = run_gpu(A0, B, synth.IDENTITY_QUAT, 32, 6)[0]
-    check(got, oracle_grid(A0, B, synth.IDENTITY_QUAT[0], 32), what="empty level")
+    ref = oracle_grid(A0, B, synth.IDENTITY_QUAT[0], 32)
+    for sp, got in run_modes(A0, B, synth.IDENTITY_QUAT, 32, 6):
+        check(got[0], ref, what=f"empty level, spread {sp}")
 
 
 def test_knots_outside_the_box_wrap():
@@ -196,10 +216,12 @@ def test_knots_outside_the_box_wrap():
     B = synth.torus_shape(150, 14)
     shift = np.array([2.0, -2.0, 4.0])  # whole periods: same periodic shape
     A2 = synth.Shape(A.xyz + shift, A.level, A.radii)
-    g1 = run_gpu(A, B, synth.IDENTITY_QUAT, 32, 6)[0]
-    g2 = run_gpu(A2, B, synth.IDENTITY_QUAT, 32, 6)[0]
-    check(g2, oracle_grid(A, B, synth.IDENTITY_QUAT[0], 32), what="shifted by periods")
-    assert rel_l2(g2, g1) < 2e-6
+    ref = oracle_grid(A, B, synth.IDENTITY_QUAT[0], 32)
+    for sp in SPREADS:
+        g1 = run_gpu(A, B, synth.IDENTITY_QUAT, 32, 6, spread=sp)[0]
+        g2 = run_gpu(A2, B, synth.IDENTITY_QUAT, 32, 6, spread=sp)[0]
+        check(g2, ref, what=f"shifted by periods, spread {sp}")
+        assert rel_l2(g2, g1) < 2e-6
 
 
 def test_shape_straddling_the_periodic_boundary():
@@ -207,9 +229,10 @@ def test_shape_straddling_the_periodic_boundary():
     A2 = synth.Shape(A.xyz + np.array([0.85, 0.0, -0.9]), A.level, A.radii)  # wraps in x and z
     B = synth.torus_shape(200, 16)
     q = synth.shoemake_quaternions(synth.SplitMix64(8), 2)
-    got = run_gpu(A2, B, q, 32, 6)
-    for r in range(2):
-        check(got[r], oracle_grid(A2, B, q[r], 32), what=f"straddling, rot {r}")
+    refs = [oracle_grid(A2, B, q[r], 32) for r in range(2)]
+    for sp, got in run_modes(A2, B, q, 32, 6):
+        for r in range(2):
+            check(got[r], refs[r], what=f"straddling, rot {r}, spread {sp}")
 
 
 def test_invalid_arguments_raise():
@@ -227,3 +250,43 @@ def test_invalid_arguments_raise():
     assert e.value.status == 1
     sa.close()
     ctx.close()
+
+
+def test_spreading_modes_agree_on_a_dense_shape_and_switch_on_one_context():
+    # Many knots in few cells (long bins, several hit chunks per item) and a
+    # context switched between the two implementations between calls.
+    bc = bcmod()
+    rng = synth.SplitMix64(21)
+    n = 6000
+    xyz = (rng.uniform(3 * n).reshape(n, 3) - 0.5) * 0.2  # a 0.2-wide cube: about 20 knots per x-cell
+    A = synth.Shape(xyz, (rng.uniform(n) * 2).astype(np.int32), synth.RADII_2)
+    B = synth.torus_shape(300, 22)
+    q = synth.shoemake_quaternions(synth.SplitMix64(23), 1)
+    ref = oracle_grid(A, B, q[0], 32)
+    ctx = bc.Context(32, 6, synth.RADII_2)
+    sa = ctx.shape(A.xyz.astype(np.float32), A.level)
+    sb = ctx.shape(B.xyz.astype(np.float32), B.level)
+    outs = []
+    for sp in (1, 0, 1):
+        ctx.set_tuning(spread=sp)
+        outs.append(ctx.correlate(sa, sb, q).double().cpu().numpy()[0])
+        check(outs[-1], ref, what=f"dense cube, spread {sp}")
+    assert rel_l2(outs[2], outs[0]) < 1e-6
+    sa.close(); sb.close(); ctx.close()
+
+
+def test_autotune_keeps_a_valid_choice():
+    bc = bcmod()
+    wl = synth.small_pair(4)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    sa = ctx.shape(wl.A.xyz, wl.A.level)
+    sb = ctx.shape(wl.B.xyz, wl.B.level)
+    t = ctx.autotune(sa, sb, rotations=40)
+    assert t == ctx.tuning and t["spread"] in (0, 1) and t["sweep_batch"] in (16, 32, 64)
+    got = ctx.correlate(sa, sb, wl.quats).double().cpu().numpy()[0]
+    check(got, oracle_grid(wl.A, wl.B, wl.quats[0], wl.N), what=f"after autotune {t}")
+    with pytest.raises(bc.BallCorrError):
+        ctx.set_tuning(spread=2)
+    with pytest.raises(bc.BallCorrError):
+        ctx.set_tuning(sweep_batch=0)
+    sa.close(); sb.close(); ctx.close()
