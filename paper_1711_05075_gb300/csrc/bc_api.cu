@@ -613,7 +613,7 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
                                 c->err_dev, (int *)ws.cnt.p, (int *)ws.cur.p, st)) != cudaSuccess)
             return cuda_fail(e, "prepare");
         ws.bins_dirty = false;
-        launches += 3;
+        launches += 2;
     } else {
         ws.grid_dirty = true; // until the z pass has consumed the spreading boxes
         if ((e = launch_prepare(g, dinst, ninst, job.max_knots, (float4 *)ws.ku.p, (int *)ws.boxes.p, dplan,

@@ -1,24 +1,25 @@
 // Binned spreading fused into the z transform (type-1 NUFFT steps 1 and 2,
 // first axis), an alternative to k_spread + k_fft_z that keeps no spreading
-// grid in HBM.
+// grid in HBM and adds no float atomics.
 //
 //   k_prepare (with counts)  counts the knots of every bin: (instance, level,
 //                            g0_x mod n), g0 the first stencil cell per axis;
-//   k_bin_scan               counts -> first slot of every bin (per instance);
-//   k_bin                    one warp per knot: the 3W separable window weights
-//                            phi(u_a - g) (Kaiser-Bessel, as in k_spread) and
-//                            the stencil origin, written as one 128-byte record
-//                            into the knot's bin;
+//   k_plan_bins              plans each instance (as k_plan) and turns its
+//                            counts into the first slot of every bin;
+//   k_bin                    the 3W separable window weights phi(u_a - g)
+//                            (Kaiser-Bessel, as in k_spread) and the stencil
+//                            origin of every knot, written as one 128-byte
+//                            record into the knot's bin;
 //   k_fft_z_binned           per z-transform item (level, x-cell, 32 y-rows):
 //                            the knots of the W bins that reach the x-cell are
-//                            filtered by their y rows, their W x W (y, z)
-//                            stencil columns added with shared-memory atomics
-//                            into the item's tile, and the tile transformed
-//                            along z exactly as k_fft_z does.
+//                            filtered by their y rows and their (y, z) stencil
+//                            columns added into the item's shared-memory tile
+//                            (fixed point, integer atomics); the tile is then
+//                            transformed along z exactly as k_fft_z does.
 //
-// The tile holds the same values k_spread would have left in the spreading
-// box rows of the item (sums of the same products, in another order), so the
-// z-transformed rows equal those of the grid path up to FP32 rounding order.
+// The tile holds the values k_spread would have left in the spreading box rows
+// of the item, accumulated in fixed point (see k_fft_z_binned), so the
+// z-transformed rows equal those of the grid path up to rounding.
 #include <climits>
 #include <cstdint>
 
@@ -26,15 +27,17 @@
 
 namespace bc {
 
-// ------------------------------------------------------------------ bin scan
-// One block per instance: cur[b] = knot_off + sum of the counts of the bins
-// before b in the instance (bins ordered by level, then x-cell); cnt is
-// cleared for the next launch.
+// ------------------------------------------------------------------ plan + bin scan
+// One block per instance: its plan (thread 0), and cur[b] = knot_off + the
+// counts of the bins before b in the instance (bins ordered by level, then
+// x-cell); cnt is cleared for the next launch.
 constexpr int SCAN_THREADS = 256;
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_bin_scan(Geometry g, const InstDesc *__restrict__ inst, int *cnt, int *cur)
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_plan_bins(Geometry g, const InstDesc *__restrict__ inst, int *bb, InstPlan *plan, int *err, int *cnt, int *cur)
 {
     const int i = blockIdx.x;
+    if (threadIdx.x == 0) plan_instance(g, inst, i, bb, plan, err);
     const int nb = g.L * g.n;
     const long long base = (long long)i * nb;
     const int per = (nb + SCAN_THREADS - 1) / SCAN_THREADS;
@@ -64,17 +67,20 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_bin_scan(Geometry g, const Ins
     }
 }
 
-cudaError_t launch_bin_scan(const Geometry &g, const InstDesc *inst, int ninst, int *cnt, int *cur, cudaStream_t s)
+cudaError_t launch_plan_bins(const Geometry &g, const InstDesc *inst, int ninst, int *bb, InstPlan *plan, int *err,
+                             int *cnt, int *cur, cudaStream_t s)
 {
     if (ninst <= 0) return cudaSuccess;
-    k_bin_scan<<<ninst, SCAN_THREADS, 0, s>>>(g, inst, cnt, cur);
+    k_plan_bins<<<ninst, SCAN_THREADS, 0, s>>>(g, inst, bb, plan, err, cnt, cur);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ knot records
 // Record of a knot (BIN_REC floats): [0] g0_y, [1] g0_z (int bits, the first
 // stencil cell, g0 = ceil(u - W/2)), [2 + a W + t] = phi(u_a - (g0_a + t)) for
-// axis a (x, y, z) and t < W.  Lane l of the knot's warp writes float l.
+// axis a (x, y, z) and t < W.  Each warp takes 32 knots: lane j claims a slot
+// for knot j, then the warp writes the 32 records one by one, lane l writing
+// float l.
 constexpr int BIN_WARPS = 8;
 
 __global__ void __launch_bounds__(BIN_WARPS * 32)
@@ -85,27 +91,38 @@ k_bin(Geometry g, const float *__restrict__ consts, const float4 *__restrict__ k
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int W = g.W, L = g.L, n = g.n;
     const float halfW = 0.5f * (float)W, twoOverW = 2.0f / (float)W;
-    for (int k = blockIdx.x * BIN_WARPS + wib; k < total; k += gridDim.x * BIN_WARPS) {
-        const float4 v = ku[k];
-        const int tag = __float_as_int(v.w);
-        const int level = tag & 15, i = tag >> 4;
-        if (plan[i].b[0] == 0) continue; // instance dropped by its plan (the z pass skips it)
-        const int gx = (int)ceilf(v.x - halfW), gy = (int)ceilf(v.y - halfW), gz = (int)ceilf(v.z - halfW);
-        int slot = 0;
-        if (lane == 0) slot = atomicAdd(&cur[((long long)i * L + level) * n + (gx < 0 ? gx + n : gx)], 1);
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        float val = 0.f;
-        if (lane == 0) {
-            val = __int_as_float(gy);
-        } else if (lane == 1) {
-            val = __int_as_float(gz);
-        } else if (lane - 2 < 3 * W) {
-            const int a = (lane - 2) / W, t = (lane - 2) - a * W;
-            const float ua = a == 0 ? v.x : (a == 1 ? v.y : v.z);
-            const int ga = a == 0 ? gx : (a == 1 ? gy : gz);
-            val = kb_window((ua - (float)(ga + t)) * twoOverW, g.beta, inv_scaled_i0beta);
+    const int a = lane < 2 ? 0 : (lane - 2) / W, t = lane < 2 ? 0 : (lane - 2) - a * W; // this lane's weight
+    for (int base = (blockIdx.x * BIN_WARPS + wib) * 32; base < total; base += gridDim.x * BIN_WARPS * 32) {
+        const int k = base + lane;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        int slot = -1;
+        if (k < total) {
+            v = ku[k];
+            const int tag = __float_as_int(v.w);
+            const int level = tag & 15, i = tag >> 4;
+            if (plan[i].b[0] != 0) { // instances dropped by their plan are skipped by the z pass too
+                const int gx = (int)ceilf(v.x - halfW);
+                slot = atomicAdd(&cur[((long long)i * L + level) * n + (gx < 0 ? gx + n : gx)], 1);
+            }
         }
-        rec[(long long)slot * BIN_REC + lane] = val;
+        for (int j = 0; j < 32; j++) {
+            const int sj = __shfl_sync(0xffffffffu, slot, j);
+            const float ux = __shfl_sync(0xffffffffu, v.x, j), uy = __shfl_sync(0xffffffffu, v.y, j),
+                        uz = __shfl_sync(0xffffffffu, v.z, j);
+            if (sj < 0) continue;
+            const int gx = (int)ceilf(ux - halfW), gy = (int)ceilf(uy - halfW), gz = (int)ceilf(uz - halfW);
+            float val = 0.f;
+            if (lane == 0) {
+                val = __int_as_float(gy);
+            } else if (lane == 1) {
+                val = __int_as_float(gz);
+            } else if (lane - 2 < 3 * W) {
+                const float ua = a == 0 ? ux : (a == 1 ? uy : uz);
+                const int ga = a == 0 ? gx : (a == 1 ? gy : gz);
+                val = kb_window((ua - (float)(ga + t)) * twoOverW, g.beta, inv_scaled_i0beta);
+            }
+            rec[(long long)sj * BIN_REC + lane] = val;
+        }
     }
 }
 
@@ -114,7 +131,7 @@ cudaError_t launch_bin(const Geometry &g, const Tables &t, const InstDesc *inst,
 {
     (void)inst;
     if (total_knots <= 0) return cudaSuccess;
-    int blocks = (total_knots + BIN_WARPS - 1) / BIN_WARPS;
+    int blocks = (total_knots + BIN_WARPS * 32 - 1) / (BIN_WARPS * 32);
     if (blocks > 65535) blocks = 65535;
     k_bin<<<blocks, BIN_WARPS * 32, 0, s>>>(g, t.consts, ku, plan, cur, rec, total_knots);
     return cudaGetLastError();
@@ -122,15 +139,24 @@ cudaError_t launch_bin(const Geometry &g, const Tables &t, const InstDesc *inst,
 
 // ------------------------------------------------------------------ fused spread + fft z
 // Item: (level l, compact x-cell ix, 32 compact y-rows iy0 ..), as in k_fft_z.
-// Tile X[pos][row] (32 floats per z position, i.e. the interleaved complex
-// layout [pos][16 lines] with rows 2q / 2q + 1 in the real / imaginary part of
-// line q); z position = absolute cell mod n.  The knots reaching x-cell
-// xa = (lo_x + ix) mod n are those of bins xa - dx (mod n), dx < W, with
-// x-weight index dx.  A knot adds phi_x[dx] phi_y[dy] phi_z[dz] at row
-// (g0_y + dy - lo_y) mod n - iy0 (when in [0, 32)) and position
-// (g0_z + dz) mod n.  Scanned knots go through a shared hit list (appended with
-// warp-aggregated atomics) in chunks of TB; each hit is spread by W threads,
-// one per y-offset, each adding its W z-cells.
+// Tile: 32 rows per z position (the interleaved complex layout [pos][16
+// lines], rows 2q / 2q + 1 in the real / imaginary part of line q), z
+// position = absolute cell mod n.
+//
+// The knots reaching x-cell xa = (lo_x + ix) mod n are those of bins xa - dx
+// (mod n), dx < W, with x-weight index dx.  A knot adds
+// phi_x[dx] phi_y[dy] phi_z[dz] at row (g0_y + dy - lo_y) mod n - iy0 (when in
+// [0, 32)) and position (g0_z + dz) mod n.  The scanned knots go, in chunks of
+// TB, through a shared hit list (appended with warp-aggregated atomics); each
+// hit is spread by W threads, one per y offset, each adding its W z-cells.
+//
+// The tile accumulates in 32-bit fixed point with integer shared-memory
+// atomics: every contribution lies in [0, 1] and a cell receives at most one
+// contribution per scanned knot, so with 2^s = 2^30 / 2^ceil(log2(T + 1)) for
+// T scanned knots no sum can overflow; each contribution is rounded to the
+// nearest multiple of 2^-s (error <= 2^-(s+1), 2^-22 for T = 255) and the
+// integer sums do not depend on the order of the additions.  The first
+// transform stage reads the tile back as FP32 (value = sum 2^-s).
 template <int NF, bool SP>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
@@ -143,7 +169,7 @@ k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int nin
     float2 *S0 = tw + NF, *S1 = S0 + NF * CL;
     float2 *OUT = three ? S0 : S1; // tile the last stage writes (not the one it reads)
     float2 *STG = three ? S1 : S0; // staging for the output rows
-    float *X = reinterpret_cast<float *>(S1);
+    int *X = reinterpret_cast<int *>(S1); // fixed-point tile [pos][32 rows]
     int *hslot = reinterpret_cast<int *>(S1 + NF * CL);
     int *hinfo = hslot + TB;
     __shared__ int bst[MAX_W], bpre[MAX_W + 1], nhit[2];
@@ -166,7 +192,7 @@ k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int nin
         for (int it = rs.first(); it < items; it += gridDim.x) {
             const int l = it / (b0 * nyb), rem = it - l * (b0 * nyb);
             const int ix = rem / nyb, iy0 = (rem - ix * nyb) << 5;
-            for (int e = threadIdx.x; e < NF * 8; e += TB) reinterpret_cast<float4 *>(X)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int e = threadIdx.x; e < NF * 8; e += TB) reinterpret_cast<int4 *>(X)[e] = make_int4(0, 0, 0, 0);
             if (threadIdx.x < W) {
                 int xa = p.lo[0] + ix;
                 if (xa < 0) xa += NF;
@@ -185,6 +211,8 @@ k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int nin
             }
             __syncthreads();
             const int total = bpre[W];
+            const int sh = 30 - (32 - __clz(total)); // 2^sh * total < 2^30
+            const float scale = ldexpf(1.f, sh);
             for (int base = 0; base < total; base += TB) {
                 const int k = base + (int)threadIdx.x;
                 bool hit = false;
@@ -220,12 +248,12 @@ k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int nin
                     if (row >= NF) row -= NF;
                     if (row < 32) {
                         const float *R = rec + (long long)hslot[h] * BIN_REC;
-                        const float cxy = R[2 + (inf & 15)] * R[2 + W + dy];
+                        const float cxy = R[2 + (inf & 15)] * R[2 + W + dy] * scale;
                         const float *wz = R + 2 + 2 * W;
                         int pos = __float_as_int(R[1]);
                         if (pos < 0) pos += NF;
                         for (int dz = 0; dz < W; dz++) {
-                            atomicAdd(&X[pos * 32 + row], cxy * wz[dz]);
+                            atomicAdd(&X[pos * 32 + row], __float2int_rn(cxy * wz[dz]));
                             if (++pos == NF) pos = 0;
                         }
                     }
@@ -234,7 +262,12 @@ k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int nin
                 chunk++;
             }
             __syncthreads();
-            in.load([&](int c, int pos) { return S1[pos * CL + c]; });
+            const float inv_scale = ldexpf(1.f, -sh);
+            in.load([&](int c, int pos) {
+                const int2 v = reinterpret_cast<const int2 *>(X)[pos * CL + c];
+                return make_float2((float)v.x * inv_scale, (float)v.y * inv_scale);
+            });
+            __syncthreads(); // the tile is in registers; S1 is free for the transform
             if constexpr (SP) in.scatter(S0);
             else rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
             __syncthreads();

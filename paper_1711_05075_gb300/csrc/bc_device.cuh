@@ -1,6 +1,7 @@
 // Device helpers shared by the kernel translation units (bc_kernels.cu,
 // bc_binned.cu).  Not part of the public interface.
 #pragma once
+#include <climits>
 #include <cuda_runtime.h>
 
 #include "bc_fft.cuh"
@@ -44,6 +45,38 @@ __device__ __forceinline__ float kb_window(float s, float beta, float inv_scaled
     const float x = beta * sq;
     const float scaled_i0 = cyl_bessel_i0f(x) * expf(-x);
     return expf(-beta * s2 / (1.f + sq)) * scaled_i0 * inv_scaled_i0beta;
+}
+
+// Support box of instance i -> its plan (the box accumulators are reset for
+// the next launch).  A box larger than the instance's capacity raises the
+// error word and the instance is treated as empty.
+__device__ __forceinline__ void plan_instance(const Geometry &g, const InstDesc *__restrict__ inst, int i, int *bb,
+                                              InstPlan *plan, int *err)
+{
+    int L0[3], H0[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        L0[a] = bb[8 * i + a];
+        H0[a] = bb[8 * i + 3 + a];
+        bb[8 * i + a] = INT_MAX;
+        bb[8 * i + 3 + a] = INT_MIN;
+    }
+    InstPlan pl;
+    bool empty = inst[i].nknots <= 0 || L0[0] == INT_MAX;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int b = empty ? 0 : min(H0[a] - L0[a] + 1, g.n);
+        if (b > inst[i].cap_e) {
+            atomicOr(err, 1);
+            empty = true;
+        }
+        pl.lo[a] = empty ? 0 : L0[a];
+        pl.b[a] = b;
+        pl.pos0[a] = empty ? 0 : ((L0[a] % g.n) + g.n) % g.n;
+    }
+    if (empty) pl.b[0] = pl.b[1] = pl.b[2] = 0;
+    pl.bzp = (pl.b[2] + 3) & ~3;
+    plan[i] = pl;
 }
 
 // Blocks per launch: the number that can be resident on the device at once.

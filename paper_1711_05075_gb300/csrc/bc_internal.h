@@ -78,7 +78,9 @@ cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, i
 // knots in shared memory and transforms them (no spreading grid in HBM).
 constexpr int MAX_W = 10;   // widest window (bc_create checks)
 constexpr int BIN_REC = 32; // floats per binned knot: g0_y, g0_z (int bits), W x-, W y-, W z-weights
-cudaError_t launch_bin_scan(const Geometry &g, const InstDesc *inst, int ninst, int *cnt, int *cur, cudaStream_t s);
+// Plans (as k_plan) and turns the counts into cursors, one block per instance.
+cudaError_t launch_plan_bins(const Geometry &g, const InstDesc *inst, int ninst, int *bb, InstPlan *plan, int *err,
+                             int *cnt, int *cur, cudaStream_t s);
 cudaError_t launch_bin(const Geometry &g, const Tables &t, const InstDesc *inst, int total_knots, const float4 *ku,
                        const InstPlan *plan, int *cur, float *rec, cudaStream_t s);
 cudaError_t launch_fft_z_binned(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,

@@ -235,31 +235,8 @@ k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 *ku, int *bb, in
 __global__ void k_plan(Geometry g, const InstDesc *__restrict__ inst, int ninst, int *bb, InstPlan *plan, int *err)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ninst) return;
-    int L0[3], H0[3];
-    for (int a = 0; a < 3; a++) {
-        L0[a] = bb[8 * i + a];
-        H0[a] = bb[8 * i + 3 + a];
-        bb[8 * i + a] = INT_MAX;
-        bb[8 * i + 3 + a] = INT_MIN;
-    }
-    InstPlan pl;
-    bool empty = inst[i].nknots <= 0 || L0[0] == INT_MAX;
-    for (int a = 0; a < 3; a++) {
-        const int b = empty ? 0 : min(H0[a] - L0[a] + 1, g.n);
-        if (b > inst[i].cap_e) {
-            atomicOr(err, 1);
-            empty = true;
-        }
-        pl.lo[a] = empty ? 0 : L0[a];
-        pl.b[a] = b;
-        pl.pos0[a] = empty ? 0 : ((L0[a] % g.n) + g.n) % g.n;
-    }
-    if (empty) pl.b[0] = pl.b[1] = pl.b[2] = 0;
-    pl.bzp = (pl.b[2] + 3) & ~3;
-    plan[i] = pl;
+    if (i < ninst) plan_instance(g, inst, i, bb, plan, err);
 }
-
 __global__ void k_reset_boxes(int *bb, int ninst)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -281,10 +258,9 @@ cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, i
     k_prepare<<<dim3(bx, ninst), PREP_THREADS, 0, s>>>(g, inst, ku, bb, cnt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (cnt) return launch_plan_bins(g, inst, ninst, bb, plan, err, cnt, cur, s);
     k_plan<<<(ninst + 127) / 128, 128, 0, s>>>(g, inst, ninst, bb, plan, err);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (cnt) return launch_bin_scan(g, inst, ninst, cnt, cur, s);
-    return cudaSuccess;
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ spread
