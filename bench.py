@@ -387,6 +387,82 @@ def run_profile(args):
     return 0
 
 
+# ------------------------------------------------------------------ score and queries
+def run_score(args):
+    """The shape-complementarity score (Sec. 4.2) of the 20k+20k-ball pair at N = 128: one
+    band-limited score grid per step (r0 = 0.02, lambda = 2), device-timed like the
+    correlation, L2 flushed between steps."""
+    import torch
+    import paper_1711_05075_gb300 as bc
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    wl = workload()
+    ctx = bc.Context(wl.N, wl.W, wl.radii, wl.period, stream=stream)
+    A, B = ctx.shape(wl.A.xyz, wl.A.level), ctx.shape(wl.B.xyz, wl.B.level)
+    tuning = ctx.autotune(A, B)
+    q = wl.quats.astype(np.float32)
+    out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        ctx.score(A, B, q, args.r0, args.lam, out)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        ctx.score(A, B, q, args.r0, args.lam, out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    line = {"metric": "complementarity-score poses/sec", "value": wl.N ** 3 / (ms * 1e-3), "unit": "poses/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic", "config": dict(config_of(wl), r0=args.r0, lam=args.lam),
+            "tuning": tuning}
+    print(json.dumps(line), flush=True)
+    A.close(); B.close(); ctx.close()
+    return 0
+
+
+def run_query(args):
+    """Truncated single-configuration queries (Sec. 4.1) on the 20k+20k-ball pair at N = 128:
+    spectra once per configuration (bc_query_create, timed on the host: it is synchronous),
+    then batches of queries and single queries at m' modes, device-timed."""
+    import torch
+    import paper_1711_05075_gb300 as bc
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    wl = workload()
+    ctx = bc.Context(wl.N, wl.W, wl.radii, wl.period, stream=stream)
+    A, B = ctx.shape(wl.A.xyz, wl.A.level), ctx.shape(wl.B.xyz, wl.B.level)
+    for _ in range(args.warmup):
+        ctx.query(A, B, wl.quats[0], args.mprime).close()
+    t0 = time.perf_counter()
+    qu = ctx.query(A, B, wl.quats[0], args.mprime)
+    create_ms = 1e3 * (time.perf_counter() - t0)
+    rng = np.random.default_rng(0)
+    res = {}
+    for npts in (1, args.query_points):
+        t = torch.tensor(rng.uniform(-1, 1, (npts, 3)).astype(np.float32), device="cuda")
+        for _ in range(args.warmup):
+            qu.eval(t)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            qu.eval(t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[npts] = e0.elapsed_time(e1) / args.steps
+    line = {"metric": "single-configuration queries/sec", "value": args.query_points / (res[args.query_points] * 1e-3),
+            "unit": "queries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": dict(config_of(wl), mprime=args.mprime, query_points=args.query_points),
+            "batch_ms": res[args.query_points], "single_query_ms": res[1], "create_ms_host": create_ms}
+    print(json.dumps(line), flush=True)
+    qu.close(); A.close(); B.close(); ctx.close()
+    return 0
+
+
 # ------------------------------------------------------------------ learned proposal
 def run_learned(args):
     """Train the rotation-proposal network on peaks from the batched sweep and measure,
@@ -553,8 +629,14 @@ def main():
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT baseline timing")
     ap.add_argument("--profile-correlations", type=int, default=0,
                     help="only run this many correlations of the workload (for a profiler), print nothing else")
-    ap.add_argument("--workload", choices=["scale", "learned"], default="scale",
-                    help="scale: the 20k+20k-ball N=128 correlation (default); learned: the rotation-proposal study")
+    ap.add_argument("--workload", choices=["scale", "learned", "score", "query"], default="scale",
+                    help="scale: the 20k+20k-ball N=128 correlation (default); learned: the rotation-proposal "
+                         "study; score: the complementarity score of the same pair; query: truncated "
+                         "single-configuration queries of the same pair")
+    ap.add_argument("--r0", type=float, default=0.02, help="score offset radius")
+    ap.add_argument("--lam", type=float, default=2.0, help="score penalty factor")
+    ap.add_argument("--mprime", type=int, default=4096, help="modes kept by a query")
+    ap.add_argument("--query-points", type=int, default=4096, help="translations per query batch")
     ap.add_argument("--train-pairs", type=int, default=100)
     ap.add_argument("--train-rot", type=int, default=2000)
     ap.add_argument("--eval-pairs", type=int, default=20)
@@ -575,6 +657,10 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "score":
+        return run_score(args)
+    if args.workload == "query":
+        return run_query(args)
     if args.profile_correlations > 0:
         return run_profile(args)
     if world > 1:

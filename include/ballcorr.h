@@ -153,6 +153,53 @@ bc_status bc_plan_destroy(bc_plan_t plan);
 bc_status bc_pairs(bc_ctx_t ctx, const bc_shape_t *As, const bc_shape_t *Bs, const float *quats, int npairs,
                    float *out, float *peak, int *argmax, int on_device);
 
+/* ---------------------------------------------------------------- shape complementarity
+ * Score of Sec. 4.2, Eq. (score): with the affinity F_S = i (f_{S+B0} -
+ * lambda f_S) (S + B0 the offset of S by the ball of radius r0, which for a
+ * union of balls is the same knots with every radius grown by r0) and the
+ * correlation of the two affinity functions taken without conjugation,
+ *     G(R, t) = -lambda^2 g_{A,RB}(t) + lambda g_{A+B0,RB}(t)
+ *               + lambda g_{A,RB+B0}(t) - g_{A+B0,RB+B0}(t),
+ * i.e. a penalty for core-core overlap, a reward for offset-core overlap and
+ * a smaller penalty for offset-offset overlap (the signs the paper's text
+ * gives the three terms of its expansion).  Computed as one band-limited
+ * correlation whose per-level multiplier is h^(rho_l + r0, k) -
+ * lambda h^(rho_l, k) (built in FP64 for each new (r0, lambda)) and whose
+ * product is negated.  bc_score has the layout, memory and error behaviour of
+ * bc_correlate, bc_score_sweep those of bc_sweep (peak = max_t G).
+ * Errors additionally: BC_ERR_ARG when r0 or lambda is negative or not finite. */
+bc_status bc_score(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quats, int k, double r0, double lambda,
+                   float *out, int out_on_device);
+bc_status bc_score_sweep(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quats, int k, int batch, double r0,
+                         double lambda, float *peak, int *argmax, int out_on_device);
+
+/* ---------------------------------------------------------------- single-configuration queries
+ * Time-critical evaluation at arbitrary translations (Sec. 4.1, Eq. (single)):
+ * the inner product of f_A with f_RB shifted by t is, by Parseval, a sum over
+ * the modes of g^ = f^_A conj(f^_RB) (Eq. (ccghat)), which is truncated to
+ * the m' modes nearest the origin -- the traversal of the frequency grid
+ * outward from the dominant low modes --
+ *     g'(R, t) = P^-3 sum_{m in M'} w_m Re( g^(m) exp(2 pi i m.t / P) ),
+ * M' = the first m' modes of the canonical half space (m_z > 0, or m_z = 0 and
+ * (m_y > 0, or m_y = 0 and m_x >= 0)) with components in (-N/2, N/2), ordered
+ * by (|m|^2, m_x, m_y, m_z); w_m = 1 for m = 0 and 2 otherwise (the mode and
+ * its conjugate -m).  With m' = ((N-1)^3 + 1) / 2 (all modes) g' is the
+ * band-limited correlation itself, at any t; a collision predicate is g' > 0.
+ *
+ * bc_query_create computes both spectra once (the pipeline of bc_correlate up
+ * to the spectra; quat: 4 FP32 host values) and keeps g^ at the m' modes.
+ * Synchronous.  Errors: BC_ERR_ARG (null pointer, zero quaternion, shapes from
+ * another context, m' outside [1, ((N-1)^3 + 1) / 2]), BC_ERR_OOM, BC_ERR_CUDA.
+ * bc_query_eval: t = npts x 3 FP32 translations, g = npts FP32 results, both
+ * device (on_device = 1, asynchronous on ctx's stream) or host (0,
+ * synchronous) memory; any t is allowed (g' is P-periodic).  Errors:
+ * BC_ERR_ARG (null pointer, npts outside [1, 2^26], context destroyed),
+ * BC_ERR_CUDA.  bc_query_destroy waits for the context stream. */
+typedef struct bc_query_s *bc_query_t;
+bc_status bc_query_create(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quat, int mprime, bc_query_t *out);
+bc_status bc_query_eval(bc_query_t q, const float *t, int npts, float *g, int on_device);
+bc_status bc_query_destroy(bc_query_t q);
+
 /* ---------------------------------------------------------------- tuning
  * Not in the paper: implementation choices that change speed, not results
  * (beyond the FP32 rounding order of the spreading sums).

@@ -7,6 +7,9 @@ code with the CUDA path.  See oracle.c for the two layers and their citations.
 Parity status: every function here is pinned by a CPU test against something
 other than itself (closed forms, quadrature, Monte Carlo, library rotations,
 invariants, and convergence of layer (b) to layer (a)); none is "parity unpinned".
+The complementarity score (Sec. 4.2) is pinned by its exact zero mode, its
+reduction to the correlation at r0 = 0 and its convergence to the exact
+lens-volume score.
 """
 from __future__ import annotations
 
@@ -192,3 +195,70 @@ def band_limited_corr(A, B, q, N, period=2.0, idx=None):
     if idx is None:
         return inverse_grid(g, period)
     return inverse_at(g, grid_points(N, period, idx), period)
+
+
+# ------------------------------------------------------------------ shape complementarity (Sec. 4.2)
+# Reading of Eq. (score): the affinity F_S = i (f_{S+B0} - lambda f_S), the
+# offset S + B0 of a union of balls taken as the same knots with every radius
+# grown by r0 (Sec. 4.2 observes that the offset raises the radii of the
+# primitive balls), and the correlation of F_A with F_RB taken without complex
+# conjugation, so that i * i = -1 and
+#     G = -lambda^2 g_{A,B} + lambda g_{A+B0,B} + lambda g_{A,B+B0} - g_{A+B0,B+B0},
+# which carries the signs the text assigns to the three terms (core-core
+# penalty ~ -lambda^2, offset-core reward ~ +lambda, offset-offset penalty ~ -1).
+def score_spectrum(A, B, q, N, r0, lam, period=2.0):
+    """G^(m) on the Hermitian half: -W_A(m) conj(W_RB(m)), W_X = f^_{X+B0} - lambda f^_X,
+    Nyquist planes zeroed."""
+    ra, rb = _f64(A.radii), _f64(B.radii)
+    wa = shape_spectrum(A.xyz, A.level, ra + r0, N, None, period) - lam * shape_spectrum(A.xyz, A.level, ra, N, None, period)
+    wb = shape_spectrum(B.xyz, B.level, rb + r0, N, q, period) - lam * shape_spectrum(B.xyz, B.level, rb, N, q, period)
+    return -corr_spectrum(wa, wb)
+
+
+def band_limited_score(A, B, q, N, r0, lam, period=2.0, idx=None):
+    """Layer (b) of the score on the full translation grid (idx None) or at sampled linear indices."""
+    g = score_spectrum(A, B, q, N, r0, lam, period)
+    if idx is None:
+        return inverse_grid(g, period)
+    return inverse_at(g, grid_points(N, period, idx), period)
+
+
+def exact_score(xa, ra, xb, rb, t, r0, lam, q=None, period=2.0):
+    """Layer (a) of the score: the four periodised lens-volume sums of Eq. (score)."""
+    ra, rb = _f64(ra), _f64(rb)
+
+    def E(a, b):
+        return exact_corr(xa, a, xb, b, t, q, period)
+
+    return -lam ** 2 * E(ra, rb) + lam * E(ra + r0, rb) + lam * E(ra, rb + r0) - E(ra + r0, rb + r0)
+
+
+# ------------------------------------------------------------------ single-configuration queries (Sec. 4.1)
+# Reading of the truncation in Eq. (single): the modes are taken outward from
+# the origin (where the spectrum's magnitude concentrates), ordered by
+# (|m|^2, m_x, m_y, m_z) over the canonical half space m_z > 0, or m_z = 0 and
+# (m_y > 0, or m_y = 0 and m_x >= 0); each mode but m = 0 also stands for its
+# conjugate -m (weight 2), so the truncated sum stays real.
+def query_modes(N, mprime):
+    """The first m' canonical modes (m' x 3 ints) and their weights."""
+    h = N // 2 - 1
+    r = np.arange(-h, h + 1)
+    mx, my, mz = (a.ravel() for a in np.meshgrid(r, r, np.arange(0, h + 1), indexing="ij"))
+    canon = (mz > 0) | (my > 0) | ((my == 0) & (mx >= 0))
+    mx, my, mz = mx[canon], my[canon], mz[canon]
+    q = mx * mx + my * my + mz * mz
+    sel = np.lexsort((mz, my, mx, q))[:mprime]
+    return np.stack([mx[sel], my[sel], mz[sel]], axis=1), np.where(q[sel] == 0, 1.0, 2.0)
+
+
+def query_at(ghat, modes, w, t, period=2.0, chunk=4096):
+    """g'(t) = P^-3 sum_i w_i Re(g^(m_i) exp(2 pi i m_i.t / P)), direct FP64 sum over the listed modes."""
+    N = ghat.shape[0]
+    t = _f64(t).reshape(-1, 3)
+    modes = np.asarray(modes, dtype=np.int64)
+    gm = ghat[modes[:, 0] % N, modes[:, 1] % N, modes[:, 2]] * np.asarray(w, dtype=np.float64)
+    out = np.zeros(t.shape[0], dtype=np.float64)
+    for s in range(0, modes.shape[0], chunk):
+        ph = np.exp(2j * np.pi * (t @ modes[s:s + chunk].T.astype(np.float64)) / period)
+        out += (ph * gm[s:s + chunk]).real.sum(axis=1)
+    return out / period ** 3

@@ -112,6 +112,16 @@ def lib():
         L.bc_autotune.argtypes = [vp, vp, vp, i, ctypes.POINTER(bc_tuning)]
         for f in ("bc_get_tuning", "bc_set_tuning", "bc_autotune"):
             getattr(L, f).restype = st
+        d = ctypes.c_double
+        L.bc_score.argtypes = [vp, vp, vp, vp, i, d, d, vp, i]
+        L.bc_score_sweep.argtypes = [vp, vp, vp, vp, i, i, d, d, vp, vp, i]
+        L.bc_score.restype = st
+        L.bc_score_sweep.restype = st
+        L.bc_query_create.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(vp)]
+        L.bc_query_eval.argtypes = [vp, vp, i, vp, i]
+        L.bc_query_destroy.argtypes = [vp]
+        for f in ("bc_query_create", "bc_query_eval", "bc_query_destroy"):
+            getattr(L, f).restype = st
         _lib = L
     return _lib
 
@@ -273,6 +283,30 @@ def bc_profile_end(ctx):
                        for s in range(BC_NUM_STAGES)]}
 
 
+def bc_score(ctx, A, B, quats, k, r0, lam, out, out_on_device):
+    _check(lib().bc_score(ctx, A, B, _ptr(quats), int(k), float(r0), float(lam), _ptr(out), int(out_on_device)))
+
+
+def bc_score_sweep(ctx, A, B, quats, k, batch, r0, lam, peak, argmax, out_on_device):
+    _check(lib().bc_score_sweep(ctx, A, B, _ptr(quats), int(k), int(batch), float(r0), float(lam), _ptr(peak),
+                                _ptr(argmax), int(out_on_device)))
+
+
+def bc_query_create(ctx, A, B, quat, mprime):
+    q = np.ascontiguousarray(np.asarray(quat, dtype=np.float32).reshape(4))
+    h = ctypes.c_void_p()
+    _check(lib().bc_query_create(ctx, A, B, _ptr(q), int(mprime), ctypes.byref(h)))
+    return h
+
+
+def bc_query_eval(q, t, npts, g, on_device):
+    _check(lib().bc_query_eval(q, _ptr(t), int(npts), _ptr(g), int(on_device)))
+
+
+def bc_query_destroy(q):
+    _check(lib().bc_query_destroy(q))
+
+
 def bc_get_tuning(ctx):
     t = bc_tuning()
     _check(lib().bc_get_tuning(ctx, ctypes.byref(t)))
@@ -308,6 +342,7 @@ class Context:
         self.handle = bc_create(N, W, radii, period, beta, stream=self.stream.cuda_stream)
         self._shapes = weakref.WeakSet()
         self._nets = weakref.WeakSet()
+        self._queries = weakref.WeakSet()
 
     def shape(self, xyz, level):
         s = Shape(self, xyz, level)
@@ -335,6 +370,33 @@ class Context:
         arg = torch.empty(k, dtype=torch.int32, device="cuda")
         bc_sweep(self.handle, A.handle, B.handle, q, k, batch, peak, arg, 1)
         return peak, arg
+
+    def score(self, A, B, quats, r0, lam, out=None):
+        """Complementarity score G (Sec. 4.2) for each rotation: (k, N, N, N) float32 CUDA tensor."""
+        import torch
+        q = np.ascontiguousarray(np.asarray(quats, dtype=np.float32).reshape(-1, 4))
+        k = q.shape[0]
+        if out is None:
+            out = torch.empty((k, self.N, self.N, self.N), dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.is_contiguous() and out.dtype == torch.float32 and out.numel() == k * self.N ** 3
+        bc_score(self.handle, A.handle, B.handle, q, k, r0, lam, out, 1)
+        return out
+
+    def score_sweep(self, A, B, quats, r0, lam, batch=0):
+        """Best score over the translation grid and its lowest index per rotation (CUDA tensors)."""
+        import torch
+        q = np.ascontiguousarray(np.asarray(quats, dtype=np.float32).reshape(-1, 4))
+        k = q.shape[0]
+        peak = torch.empty(k, dtype=torch.float32, device="cuda")
+        arg = torch.empty(k, dtype=torch.int32, device="cuda")
+        bc_score_sweep(self.handle, A.handle, B.handle, q, k, batch, r0, lam, peak, arg, 1)
+        return peak, arg
+
+    def query(self, A, B, quat, mprime):
+        """Truncated single-configuration queries of g for one rotation (see Query)."""
+        q = Query(self, A, B, quat, mprime)
+        self._queries.add(q)
+        return q
 
     def pairs(self, As, Bs, quats, grids=False, peaks=True):
         """Ragged batch of independent pairs; returns (grids or None, peak or None, argmax or None)."""
@@ -376,6 +438,8 @@ class Context:
                 s.close()
             for net in list(self._nets):
                 net.close()
+            for q in list(self._queries):
+                q.close()
             bc_destroy(self.handle)
             self.handle = None
 
@@ -486,6 +550,39 @@ class Shape:
     def close(self):
         if self.handle is not None:
             bc_shape_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Query:
+    """g at arbitrary translations from the m' lowest modes of one configuration's spectrum."""
+
+    def __init__(self, ctx: Context, A, B, quat, mprime: int):
+        self.ctx = ctx
+        self.mprime = int(mprime)
+        self.handle = bc_query_create(ctx.handle, A.handle, B.handle, quat, mprime)
+
+    def eval(self, t):
+        """t: (n, 3) float32 CUDA tensor (asynchronous) or array-like (host, synchronous)."""
+        import torch
+        if isinstance(t, torch.Tensor) and t.is_cuda:
+            t = t.contiguous().float()
+            g = torch.empty(t.shape[0], dtype=torch.float32, device=t.device)
+            bc_query_eval(self.handle, t, t.shape[0], g, 1)
+            return g
+        th = np.ascontiguousarray(np.asarray(t, dtype=np.float32).reshape(-1, 3))
+        g = np.empty(th.shape[0], dtype=np.float32)
+        bc_query_eval(self.handle, th, th.shape[0], g, 0)
+        return g
+
+    def close(self):
+        if self.handle is not None:
+            bc_query_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

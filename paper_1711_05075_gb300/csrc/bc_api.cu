@@ -114,8 +114,11 @@ struct bc_ctx_s {
     // workspaces
     Workspace ws;                 // pipeline workspaces of direct calls
     DevBuf outbuf, stats, learn, tune; // host-output staging, shape checks, learned-sweep and tuning scratch
+    DevBuf score_ft;                   // shape-complementarity weights for (score_r0, score_lambda)
+    double score_r0 = -1.0, score_lambda = 0.0;
     std::set<bc_shape_s *> shapes; // live shapes; orphaned (device memory freed) by bc_destroy
     std::set<bc_mlp_s *> nets;     // live networks; orphaned the same way
+    std::set<bc_query_s *> queries; // live single-configuration queries; orphaned the same way
     // profiling
     bool prof_on = false;
     int prof_max = 0, prof_calls = 0;
@@ -140,6 +143,19 @@ struct bc_shape_s {
     int n = 0;
     float4 *knots = nullptr;
     float rmax = 0.f;
+};
+
+// A configuration's truncated correlation spectrum (bc_query_create).
+struct bc_query_s {
+    bc_ctx_t ctx = nullptr;
+    int count = 0;          // m'
+    DevBuf modes, ghat, io; // int4 modes, their g^ values, staging for host points and results
+    void release()
+    {
+        modes.release();
+        ghat.release();
+        io.release();
+    }
 };
 
 cudaStream_t bc::ctx_stream(bc_ctx_s *c) { return c->stream; }
@@ -310,8 +326,13 @@ bc_status bc_destroy(bc_ctx_t c)
         c->shapes.clear();
         for (bc_mlp_s *net : c->nets) mlp_orphan(net);
         c->nets.clear();
+        for (bc_query_s *q : c->queries) {
+            q->release();
+            q->ctx = nullptr;
+        }
+        c->queries.clear();
         c->ws.release();
-        DevBuf *bufs[] = {&c->outbuf, &c->stats, &c->learn, &c->tune};
+        DevBuf *bufs[] = {&c->outbuf, &c->stats, &c->learn, &c->tune, &c->score_ft};
         for (DevBuf *b : bufs) b->release();
         delete c;
         return BC_OK;
@@ -487,11 +508,20 @@ bc_status bc_profile_end(bc_ctx_t c, bc_profile *out)
 // `pairs`.  With cache_first, pairs[0] = (a, -1) writes instance a's spectrum
 // into the workspace's cache and the remaining pairs follow; pairs with
 // a = -1 read that cache.
+// Per-level multiplier of the spectra and the sign of the product: the ball
+// transforms for a correlation; the complementarity weights, negated, for a
+// score.
+struct Weights {
+    const float *ballft = nullptr; // null: the context's ball transform table
+    float sign = 1.f;
+};
+
 struct Job {
     std::vector<InstDesc> inst;
     std::vector<PairDesc> pairs;
     bool cache_first = false;
     int mode = 0; // spreading: 0 boxes in HBM, 1 binned (fused into the z pass)
+    Weights w;
     int nmain = 0, koff = 0, max_knots = 0;
     long long goff = 0, zoff = 0, yoff = 0, hpairs = 0;
 };
@@ -592,9 +622,11 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
                             float *dout, unsigned long long *keys, bool profile, cudaStream_t st,
                             long long *nlaunch = nullptr)
 {
-    const Geometry &g = c->g;
+    Geometry g = c->g;
+    g.inv_P3 *= job.w.sign;
     const int ninst = (int)job.inst.size();
-    const Tables t = tables_of(c);
+    Tables t = tables_of(c);
+    if (job.w.ballft) t.ballft = job.w.ballft;
     InstPlan *dplan = (InstPlan *)ws.plan.p;
     const PairDesc *pmain = dpairs + (job.cache_first ? 1 : 0);
     const int nmain = job.nmain;
@@ -687,10 +719,11 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
 // on the context's own workspace.
 static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std::vector<const float *> &quats,
                          const std::vector<PairDesc> &pairs, bool cache_first, float *dout, unsigned long long *keys,
-                         const std::vector<const float *> *qdev = nullptr)
+                         const std::vector<const float *> *qdev = nullptr, Weights w = Weights())
 {
     Workspace &ws = c->ws;
-    const Job job = plan_job(c, shapes, quats, pairs, cache_first, qdev);
+    Job job = plan_job(c, shapes, quats, pairs, cache_first, qdev);
+    job.w = w;
     const long long ninst = (long long)job.inst.size(), npairs = (long long)job.pairs.size();
     if (bc_status s = ensure_ws(c, ws, job.mode, job.koff, ninst, npairs, job.goff, job.zoff, job.yoff, job.hpairs)) return s;
     const size_t inst_bytes = sizeof(InstDesc) * ninst, pair_bytes = sizeof(PairDesc) * npairs;
@@ -714,7 +747,7 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
 // qdev) against A: A's spectrum once into the cache, then batches of
 // rotations folded into peak keys, then keys -> peak / argmax.
 static bc_status sweep_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *qhost, const float *qdev, int k,
-                            int batch, float *peak, int *argmax, int out_on_device)
+                            int batch, float *peak, int *argmax, int out_on_device, Weights w = Weights())
 {
     if (batch == 0) batch = c->sweep_batch;
     const int N = c->g.N, H = c->g.H;
@@ -729,7 +762,7 @@ static bc_status sweep_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float 
         std::vector<bc_shape_t> shapes(1, A);
         std::vector<const float *> q(1, nullptr);
         std::vector<PairDesc> pairs(1, PairDesc{0, -1, 0, 0, 0});
-        if (bc_status s = enqueue(c, shapes, q, pairs, true, nullptr, nullptr)) return s;
+        if (bc_status s = enqueue(c, shapes, q, pairs, true, nullptr, nullptr, nullptr, w)) return s;
     }
     for (int r0 = 0; r0 < k; r0 += batch) {
         const int nb = std::min(batch, k - r0);
@@ -741,7 +774,7 @@ static bc_status sweep_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float 
             else qd[i] = qdev + 4 * (size_t)(r0 + i);
             pairs[i] = PairDesc{-1, i, (long long)i * N * N * H, 0, (long long)(r0 + i)};
         }
-        if (bc_status s = enqueue(c, shapes, q, pairs, false, nullptr, keys, qhost ? nullptr : &qd)) return s;
+        if (bc_status s = enqueue(c, shapes, q, pairs, false, nullptr, keys, qhost ? nullptr : &qd, w)) return s;
     }
     float *dpeak = peak;
     int *darg = argmax;
@@ -772,14 +805,14 @@ static bc_status check_quats(const float *quats, int k, const char *who)
 
 extern "C" {
 
-bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, int k, float *out,
-                       int out_on_device)
+static bc_status correlate_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, int k, float *out,
+                                int out_on_device, Weights w, const char *who)
 {
     try {
-        if (!c || !A || !B || !quats || !out) return fail(BC_ERR_ARG, "bc_correlate: null argument");
-        if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_correlate: shapes belong to another context");
-        if (k < 1 || k > 65534) return fail(BC_ERR_ARG, "bc_correlate: k must be in [1, 65534]");
-        if (bc_status s = check_quats(quats, k, "bc_correlate")) return s;
+        if (!c || !A || !B || !quats || !out) return fail(BC_ERR_ARG, std::string(who) + ": null argument");
+        if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, std::string(who) + ": shapes belong to another context");
+        if (k < 1 || k > 65534) return fail(BC_ERR_ARG, std::string(who) + ": k must be in [1, 65534]");
+        if (bc_status s = check_quats(quats, k, who)) return s;
         const int N = c->g.N, H = c->g.H;
         const long long N3 = (long long)N * N * N;
         std::vector<bc_shape_t> shapes(1 + k, B);
@@ -797,7 +830,7 @@ bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quat
             if ((e = c->outbuf.ensure(sizeof(float) * (size_t)k * N3, false, c->stream)) != cudaSuccess) return cuda_fail(e, "outbuf");
             dout = (float *)c->outbuf.p;
         }
-        if (bc_status s = enqueue(c, shapes, q, pairs, !fused, dout, nullptr)) return s;
+        if (bc_status s = enqueue(c, shapes, q, pairs, !fused, dout, nullptr, nullptr, w)) return s;
         if (!out_on_device) {
             if ((e = cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)k * N3, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
                 return cuda_fail(e, "copy out");
@@ -805,7 +838,47 @@ bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quat
         }
         return BC_OK;
     } catch (...) {
-        return fail(BC_ERR_INTERNAL, "bc_correlate: unexpected exception");
+        return fail(BC_ERR_INTERNAL, std::string(who) + ": unexpected exception");
+    }
+}
+
+bc_status bc_correlate(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, int k, float *out,
+                       int out_on_device)
+{
+    return correlate_impl(c, A, B, quats, k, out, out_on_device, Weights(), "bc_correlate");
+}
+
+// The complementarity weights for (r0, lambda), rebuilt on the context stream
+// when the parameters change (stream order keeps earlier calls on the old ones).
+static bc_status score_weights(bc_ctx_t c, double r0, double lambda, const char *who, Weights *w)
+{
+    if (!(r0 >= 0) || !std::isfinite(r0) || !(lambda >= 0) || !std::isfinite(lambda))
+        return fail(BC_ERR_ARG, std::string(who) + ": r0 and lambda must be finite and >= 0");
+    const size_t n = (size_t)c->g.L * (c->qmax + 1);
+    cudaError_t e;
+    const size_t before = c->score_ft.bytes;
+    if ((e = c->score_ft.ensure(sizeof(float) * n, false, c->stream)) != cudaSuccess) return cuda_fail(e, who);
+    if (c->score_ft.bytes != before || r0 != c->score_r0 || lambda != c->score_lambda) {
+        if ((e = launch_build_score_table(c->g, c->period, c->radii_dev, r0, lambda, (float *)c->score_ft.p, c->stream)) != cudaSuccess)
+            return cuda_fail(e, who);
+        c->score_r0 = r0;
+        c->score_lambda = lambda;
+    }
+    w->ballft = (const float *)c->score_ft.p;
+    w->sign = -1.f;
+    return BC_OK;
+}
+
+bc_status bc_score(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, int k, double r0, double lambda,
+                   float *out, int out_on_device)
+{
+    try {
+        if (!c) return fail(BC_ERR_ARG, "bc_score: null context");
+        Weights w;
+        if (bc_status s = score_weights(c, r0, lambda, "bc_score", &w)) return s;
+        return correlate_impl(c, A, B, quats, k, out, out_on_device, w, "bc_score");
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_score: unexpected exception");
     }
 }
 
@@ -884,6 +957,23 @@ bc_status bc_sweep(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, i
         return sweep_impl(c, A, B, quats, nullptr, k, batch, peak, argmax, out_on_device);
     } catch (...) {
         return fail(BC_ERR_INTERNAL, "bc_sweep: unexpected exception");
+    }
+}
+
+bc_status bc_score_sweep(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quats, int k, int batch, double r0,
+                         double lambda, float *peak, int *argmax, int out_on_device)
+{
+    try {
+        if (!c || !A || !B || !quats || !peak || !argmax) return fail(BC_ERR_ARG, "bc_score_sweep: null argument");
+        if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_score_sweep: shapes belong to another context");
+        if (k < 1 || k > (1 << 24)) return fail(BC_ERR_ARG, "bc_score_sweep: k must be in [1, 2^24]");
+        if (batch < 0 || batch > 65534) return fail(BC_ERR_ARG, "bc_score_sweep: batch must be in [0, 65534]");
+        if (bc_status s = check_quats(quats, k, "bc_score_sweep")) return s;
+        Weights w;
+        if (bc_status s = score_weights(c, r0, lambda, "bc_score_sweep", &w)) return s;
+        return sweep_impl(c, A, B, quats, nullptr, k, batch, peak, argmax, out_on_device, w);
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_score_sweep: unexpected exception");
     }
 }
 
@@ -1195,6 +1285,148 @@ bc_status bc_autotune(bc_ctx_t c, bc_shape_t A, bc_shape_t B, int rotations, bc_
         return BC_OK;
     } catch (...) {
         return fail(BC_ERR_INTERNAL, "bc_autotune: unexpected exception");
+    }
+}
+
+} // extern "C"
+
+// ------------------------------------------------------------------ single-configuration queries
+// The first m' modes of the canonical half space -- m_z > 0, or m_z = 0 and
+// (m_y > 0, or m_y = 0 and m_x >= 0) -- with components in (-N/2, N/2),
+// ordered by (|m|^2, m_x, m_y, m_z); w = 1 for m = 0, 2 otherwise.
+static std::vector<std::array<int, 4>> query_modes(int N, int mprime)
+{
+    const int h = N / 2 - 1; // largest |component|
+    int R = (int)std::ceil(std::cbrt(3.0 * mprime / (2.0 * M_PI))) + 2;
+    std::vector<std::array<int, 5>> cand;
+    for (;;) {
+        if (R > h) R = h;
+        cand.clear();
+        const long long R2 = (long long)R * R;
+        for (int mx = -R; mx <= R; mx++)
+            for (int my = -R; my <= R; my++)
+                for (int mz = 0; mz <= R; mz++) {
+                    const long long q = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
+                    if (R < h && q > R2) continue;
+                    const bool canon = mz > 0 || (my > 0 || (my == 0 && mx >= 0));
+                    if (canon) cand.push_back({(int)q, mx, my, mz, 0});
+                }
+        if ((long long)cand.size() >= mprime || R == h) break;
+        R = R * 2;
+    }
+    std::sort(cand.begin(), cand.end());
+    std::vector<std::array<int, 4>> out;
+    for (int i = 0; i < mprime && i < (int)cand.size(); i++)
+        out.push_back({cand[i][1], cand[i][2], cand[i][3], cand[i][0] == 0 ? 1 : 2});
+    return out;
+}
+
+extern "C" {
+
+bc_status bc_query_create(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float *quat, int mprime, bc_query_t *out)
+{
+    bc_query_s *qo = nullptr;
+    try {
+        if (!c || !A || !B || !quat || !out) return fail(BC_ERR_ARG, "bc_query_create: null argument");
+        *out = nullptr;
+        if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_query_create: shapes belong to another context");
+        if (bc_status s = check_quats(quat, 1, "bc_query_create")) return s;
+        const int N = c->g.N;
+        const long long total = ((long long)(N - 1) * (N - 1) * (N - 1) + 1) / 2;
+        if (mprime < 1 || mprime > total)
+            return fail(BC_ERR_ARG, "bc_query_create: m' must be in [1, ((N-1)^3 + 1) / 2]");
+        const std::vector<std::array<int, 4>> modes = query_modes(N, mprime);
+        if ((int)modes.size() != mprime) return fail(BC_ERR_INTERNAL, "bc_query_create: mode enumeration");
+        cudaStream_t st = c->stream;
+        cudaError_t e;
+        qo = new bc_query_s();
+        qo->ctx = c;
+        qo->count = mprime;
+        const size_t spec = sizeof(float2) * (size_t)N * N * c->g.H;
+        auto bail = [&](bc_status s) {
+            qo->release();
+            delete qo;
+            return s;
+        };
+        if ((e = qo->modes.ensure(sizeof(int4) * mprime, false, st)) != cudaSuccess ||
+            (e = qo->ghat.ensure(sizeof(float2) * mprime, false, st)) != cudaSuccess ||
+            (e = qo->io.ensure(spec, false, st)) != cudaSuccess)
+            return bail(cuda_fail(e, "bc_query_create: buffers"));
+        if ((e = cudaMemcpyAsync(qo->modes.p, modes.data(), sizeof(int4) * mprime, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return bail(cuda_fail(e, "bc_query_create: modes"));
+        // f^_A into the workspace cache, kept in io; then f^_RB into the cache
+        std::vector<PairDesc> pairs(1, PairDesc{0, -1, 0, 0, 0});
+        if (bc_status s = enqueue(c, std::vector<bc_shape_t>(1, A), std::vector<const float *>(1, nullptr), pairs, true,
+                                  nullptr, nullptr))
+            return bail(s);
+        if ((e = cudaMemcpyAsync(qo->io.p, c->ws.fa.p, spec, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return bail(cuda_fail(e, "bc_query_create: copy spectrum"));
+        if (bc_status s = enqueue(c, std::vector<bc_shape_t>(1, B), std::vector<const float *>(1, quat), pairs, true,
+                                  nullptr, nullptr))
+            return bail(s);
+        if ((e = launch_query_gather((const float2 *)qo->io.p, (const float2 *)c->ws.fa.p, (const int4 *)qo->modes.p,
+                                     mprime, N, (float2 *)qo->ghat.p, st)) != cudaSuccess)
+            return bail(cuda_fail(e, "bc_query_create: gather"));
+        if (bc_status s = bc_sync(c)) return bail(s);
+        c->queries.insert(qo);
+        *out = qo;
+        return BC_OK;
+    } catch (...) {
+        if (qo) {
+            qo->release();
+            delete qo;
+        }
+        return fail(BC_ERR_INTERNAL, "bc_query_create: unexpected exception");
+    }
+}
+
+bc_status bc_query_eval(bc_query_t q, const float *t, int npts, float *g, int on_device)
+{
+    try {
+        if (!q || !t || !g) return fail(BC_ERR_ARG, "bc_query_eval: null argument");
+        if (!q->ctx) return fail(BC_ERR_ARG, "bc_query_eval: the query's context was destroyed");
+        if (npts < 1 || npts > (1 << 26)) return fail(BC_ERR_ARG, "bc_query_eval: npts must be in [1, 2^26]");
+        bc_ctx_t c = q->ctx;
+        cudaStream_t st = c->stream;
+        cudaError_t e;
+        const float *dt = t;
+        float *dg = g;
+        if (!on_device) {
+            const size_t need = sizeof(float) * 4 * (size_t)npts;
+            if ((e = q->io.ensure(need, false, st)) != cudaSuccess) return cuda_fail(e, "bc_query_eval: staging");
+            float *stage = (float *)q->io.p;
+            if ((e = cudaMemcpyAsync(stage, t, sizeof(float) * 3 * (size_t)npts, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(e, "bc_query_eval: copy points");
+            dt = stage;
+            dg = stage + 3 * (size_t)npts;
+        }
+        if ((e = launch_query_eval((const float2 *)q->ghat.p, (const int4 *)q->modes.p, q->count, c->g.N, c->period, dt,
+                                   npts, dg, st)) != cudaSuccess)
+            return cuda_fail(e, "bc_query_eval: launch");
+        if (!on_device) {
+            if ((e = cudaMemcpyAsync(g, dg, sizeof(float) * (size_t)npts, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return cuda_fail(e, "bc_query_eval: copy results");
+            CK(cudaStreamSynchronize(st));
+        }
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_query_eval: unexpected exception");
+    }
+}
+
+bc_status bc_query_destroy(bc_query_t q)
+{
+    if (!q) return BC_OK;
+    try {
+        if (q->ctx) {
+            cudaStreamSynchronize(q->ctx->stream);
+            q->ctx->queries.erase(q);
+        }
+        q->release();
+        delete q;
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_query_destroy: unexpected exception");
     }
 }
 

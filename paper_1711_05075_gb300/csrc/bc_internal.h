@@ -61,6 +61,9 @@ struct Geometry {
 cudaError_t launch_build_tables(const Geometry &g, double beta, double period, const double *radii_dev,
                                 float *deconv, float *ballft, float2 *tw_n, float2 *tw_N, float *consts,
                                 cudaStream_t s);
+// out[l][q] = h^(rho_l + r0, k) - lambda h^(rho_l, k), k = 2 pi sqrt(q) / P (FP64, rounded once).
+cudaError_t launch_build_score_table(const Geometry &g, double period, const double *radii_dev, double r0,
+                                     double lambda, float *out, cudaStream_t s);
 cudaError_t launch_pack_knots(const float *xyz, const int *level, int n, int L, float4 *knots,
                               unsigned int *stats, cudaStream_t s);
 // bb: 8 ints per instance (support-box accumulators); they must hold the reset
@@ -117,6 +120,12 @@ int *ctx_err(bc_ctx_s *c);
 void ctx_register_mlp(bc_ctx_s *c, bc_mlp_s *net);
 void ctx_unregister_mlp(bc_ctx_s *c, bc_mlp_s *net);
 void mlp_orphan(bc_mlp_s *net); // bc_mlp.cu
+
+// Single-configuration queries (bc_query.cu).  modes[i] = (m_x, m_y, m_z, w).
+cudaError_t launch_query_gather(const float2 *fa, const float2 *fb, const int4 *modes, int count, int N, float2 *ghat,
+                                cudaStream_t s);
+cudaError_t launch_query_eval(const float2 *ghat, const int4 *modes, int count, int N, double period, const float *t,
+                              int npts, float *g, cudaStream_t s);
 
 // Learned-proposal helpers (bc_mlp.cu).
 cudaError_t launch_topk(const float *scores, int n, int k, int *idx, cudaStream_t s);

@@ -57,6 +57,18 @@ __device__ __forceinline__ int mode_of(int j, int N) { return j < N / 2 ? j : j 
 // h^(r, k) = 4 pi (sin kr - kr cos kr) / k^3 with k = 2 pi sqrt(q) / P, and for
 // x = kr < 0.5 the Maclaurin series 4 pi r^3 (1/3 - x^2/30 + x^4/840 -
 // x^6/45360 + x^8/3991680), indexed by the integer q = |m|^2.
+__device__ double ball_ft64(double r, double k)
+{
+    const double pi = 3.14159265358979323846;
+    const double x = k * r;
+    if (x < 0.5) {
+        const double x2 = x * x;
+        return 4.0 * pi * r * r * r *
+               (1.0 / 3.0 - x2 / 30.0 + x2 * x2 / 840.0 - x2 * x2 * x2 / 45360.0 + x2 * x2 * x2 * x2 / 3991680.0);
+    }
+    return 4.0 * pi * (sin(x) - x * cos(x)) / (k * k * k);
+}
+
 __global__ void k_build_tables(int N, int n, int W, int L, int qmax, double beta, double period,
                                const double *__restrict__ radii, float *deconv, float *ballft, float2 *tw_n,
                                float2 *tw_N, float *consts)
@@ -79,18 +91,7 @@ __global__ void k_build_tables(int N, int n, int W, int L, int qmax, double beta
         } else if (t < N + L * (qmax + 1)) {
             int u = t - N;
             int l = u / (qmax + 1), q = u - l * (qmax + 1);
-            double r = radii[l];
-            double k = 2.0 * pi * sqrt((double)q) / period;
-            double x = k * r, v;
-            if (x < 0.5) {
-                double x2 = x * x;
-                v = 4.0 * pi * r * r * r *
-                    (1.0 / 3.0 - x2 / 30.0 + x2 * x2 / 840.0 - x2 * x2 * x2 / 45360.0 +
-                     x2 * x2 * x2 * x2 / 3991680.0);
-            } else {
-                v = 4.0 * pi * (sin(x) - x * cos(x)) / (k * k * k);
-            }
-            ballft[u] = (float)v;
+            ballft[u] = (float)ball_ft64(radii[l], 2.0 * pi * sqrt((double)q) / period);
         } else if (t < N + L * (qmax + 1) + n) {
             int k = t - N - L * (qmax + 1);
             double a = 2.0 * pi * k / n;
@@ -111,6 +112,31 @@ cudaError_t launch_build_tables(const Geometry &g, double beta, double period, c
     const int total = g.N + g.L * (qmax + 1) + g.n + g.N;
     k_build_tables<<<(total + 255) / 256, 256, 0, s>>>(g.N, g.n, g.W, g.L, qmax, beta, period, radii_dev, deconv,
                                                         ballft, tw_n, tw_N, consts);
+    return cudaGetLastError();
+}
+
+// Shape-complementarity weights (Sec. 4.2): the offset S + B0 of a union of
+// balls is the union of the balls grown by r0, so the affinity function's
+// real part f_{S+B0} - lambda f_S has, per level, the transform
+// [h^(rho_l + r0, k) - lambda h^(rho_l, k)] S_l(m).  out[l][q], built in FP64
+// and rounded once, replaces the ball transform table for a score.
+__global__ void k_build_score_table(int L, int qmax, double period, const double *__restrict__ radii, double r0,
+                                    double lambda, float *out)
+{
+    const double pi = 3.14159265358979323846;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < L * (qmax + 1); u += gridDim.x * blockDim.x) {
+        const int l = u / (qmax + 1), q = u - l * (qmax + 1);
+        const double k = 2.0 * pi * sqrt((double)q) / period;
+        out[u] = (float)(ball_ft64(radii[l] + r0, k) - lambda * ball_ft64(radii[l], k));
+    }
+}
+
+cudaError_t launch_build_score_table(const Geometry &g, double period, const double *radii_dev, double r0,
+                                     double lambda, float *out, cudaStream_t s)
+{
+    const int qmax = 3 * (g.N / 2) * (g.N / 2);
+    const int total = g.L * (qmax + 1);
+    k_build_score_table<<<(total + 255) / 256, 256, 0, s>>>(g.L, qmax, period, radii_dev, r0, lambda, out);
     return cudaGetLastError();
 }
 
