@@ -34,7 +34,7 @@ class bc_profile(ctypes.Structure):
 
 
 class bc_tuning(ctypes.Structure):
-    _fields_ = [("spread", ctypes.c_int), ("sweep_batch", ctypes.c_int)]
+    _fields_ = [("spread", ctypes.c_int), ("sweep_batch", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 class BallCorrError(RuntimeError):
@@ -307,21 +307,25 @@ def bc_query_destroy(q):
     _check(lib().bc_query_destroy(q))
 
 
+def _tuning_dict(t):
+    return {"spread": t.spread, "sweep_batch": t.sweep_batch, "graphs": t.graphs}
+
+
 def bc_get_tuning(ctx):
     t = bc_tuning()
     _check(lib().bc_get_tuning(ctx, ctypes.byref(t)))
-    return {"spread": t.spread, "sweep_batch": t.sweep_batch}
+    return _tuning_dict(t)
 
 
-def bc_set_tuning(ctx, spread, sweep_batch):
-    t = bc_tuning(int(spread), int(sweep_batch))
+def bc_set_tuning(ctx, spread, sweep_batch, graphs=1):
+    t = bc_tuning(int(spread), int(sweep_batch), int(graphs))
     _check(lib().bc_set_tuning(ctx, ctypes.byref(t)))
 
 
 def bc_autotune(ctx, A, B, rotations=0):
     t = bc_tuning()
     _check(lib().bc_autotune(ctx, A, B, int(rotations), ctypes.byref(t)))
-    return {"spread": t.spread, "sweep_batch": t.sweep_batch}
+    return _tuning_dict(t)
 
 
 # ---------------------------------------------------------------- convenience
@@ -332,14 +336,15 @@ def default_beta(W, sigma=2):
 class Context:
     """Correlation context on the current CUDA device and a torch stream."""
 
-    def __init__(self, N, W, radii, period=2.0, beta=0.0, stream=None):
+    def __init__(self, N, W, radii, period=2.0, beta=0.0, stream=None, precision=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
         self.N, self.W, self.period = int(N), int(W), float(period)
         self.radii = tuple(float(r) for r in radii)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self.handle = bc_create(N, W, radii, period, beta, stream=self.stream.cuda_stream)
+        self.handle = None
+        self.handle = bc_create(N, W, radii, period, beta, precision=precision, stream=self.stream.cuda_stream)
         self._shapes = weakref.WeakSet()
         self._nets = weakref.WeakSet()
         self._queries = weakref.WeakSet()
@@ -420,13 +425,14 @@ class Context:
 
     @property
     def tuning(self):
-        """The context's implementation choices: {"spread": 0|1, "sweep_batch": int}."""
+        """The context's implementation choices: {"spread": 0|1, "sweep_batch": int, "graphs": 0|1}."""
         return bc_get_tuning(self.handle)
 
-    def set_tuning(self, spread=None, sweep_batch=None):
+    def set_tuning(self, spread=None, sweep_batch=None, graphs=None):
         t = self.tuning
         bc_set_tuning(self.handle, t["spread"] if spread is None else spread,
-                      t["sweep_batch"] if sweep_batch is None else sweep_batch)
+                      t["sweep_batch"] if sweep_batch is None else sweep_batch,
+                      t["graphs"] if graphs is None else graphs)
 
     def autotune(self, A, B, rotations=0):
         """Times the candidates on these shapes and keeps the fastest (see bc_autotune)."""

@@ -81,8 +81,18 @@ struct Workspace {
     bool bins_dirty = false;  // bin counts may be non-zero (an enqueue failed midway)
     std::vector<char> last_desc; // descriptors the device copies hold
     void *last_inst_p = nullptr, *last_pairs_p = nullptr;
+    // the last pass recorded as a CUDA graph, and what it was recorded for
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<char> gkey;
+    void drop_graph()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        gkey.clear();
+    }
     void release()
     {
+        drop_graph();
         DevBuf *b[] = {&ku, &plan, &inst, &pairs, &grid, &z1, &y1, &h, &fa, &boxes, &keys, &cnt, &cur, &rec};
         for (DevBuf *x : b) x->release();
         last_desc.clear();
@@ -125,6 +135,8 @@ struct bc_ctx_s {
     long long prof_launches = 0;
     std::vector<cudaEvent_t> prof_ev; // prof_max x (BC_NUM_STAGES + 1)
     int last_ninst = 0, last_npairs = 0, last_mode = 0;
+    cudaStream_t capture_stream = nullptr; // private stream for recording graphs (the legacy stream cannot be captured)
+    bool replay = true;                    // repeated identical passes of direct calls replay a recorded graph
     std::vector<InstDesc> last_inst;
 };
 
@@ -332,6 +344,7 @@ bc_status bc_destroy(bc_ctx_t c)
         }
         c->queries.clear();
         c->ws.release();
+        if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
         DevBuf *bufs[] = {&c->outbuf, &c->stats, &c->learn, &c->tune, &c->score_ft};
         for (DevBuf *b : bufs) b->release();
         delete c;
@@ -740,7 +753,40 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
         ws.last_inst_p = ws.inst.p;
         ws.last_pairs_p = ws.pairs.p;
     }
-    return launch_job(c, ws, job, (const InstDesc *)ws.inst.p, (const PairDesc *)ws.pairs.p, dout, keys, true, c->stream);
+    const bool profiling = c->prof_on && c->prof_calls < c->prof_max;
+    if (profiling || !c->replay)
+        return launch_job(c, ws, job, (const InstDesc *)ws.inst.p, (const PairDesc *)ws.pairs.p, dout, keys, true, c->stream);
+    // Replay: a pass whose descriptors, outputs, weights and workspaces match the
+    // recorded one is the same sequence of launches with the same arguments.
+    std::vector<char> key(ws.last_desc);
+    auto add = [&](const void *v, size_t n) { key.insert(key.end(), (const char *)v, (const char *)v + n); };
+    const void *ptrs[] = {dout, keys, job.w.ballft, ws.ku.p, ws.plan.p, ws.inst.p, ws.pairs.p, ws.grid.p, ws.z1.p, ws.y1.p,
+                          ws.h.p, ws.fa.p, ws.boxes.p, ws.cnt.p, ws.cur.p, ws.rec.p, c->stream};
+    add(ptrs, sizeof(ptrs));
+    add(&job.w.sign, sizeof(job.w.sign));
+    add(&job.mode, sizeof(job.mode));
+    cudaError_t e;
+    if (!ws.gexec || key != ws.gkey) {
+        ws.drop_graph();
+        if (!c->capture_stream && (e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "capture stream");
+        if ((e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+            return cuda_fail(e, "begin capture");
+        bc_status s = launch_job(c, ws, job, (const InstDesc *)ws.inst.p, (const PairDesc *)ws.pairs.p, dout, keys, false,
+                                 c->capture_stream);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(c->capture_stream, &graph);
+        if (s == BC_OK && e != cudaSuccess) s = cuda_fail(e, "end capture");
+        if (s == BC_OK && (e = cudaGraphInstantiate(&ws.gexec, graph, 0)) != cudaSuccess) {
+            ws.gexec = nullptr;
+            s = cuda_fail(e, "instantiate");
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (s != BC_OK) return s;
+        ws.gkey.swap(key);
+    }
+    if ((e = cudaGraphLaunch(ws.gexec, c->stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    return BC_OK;
 }
 
 // Peaks for k rotations of B (host quaternions qhost, or device quaternions
@@ -1168,6 +1214,7 @@ bc_status bc_get_tuning(bc_ctx_t c, bc_tuning *out)
     if (!c || !out) return fail(BC_ERR_ARG, "bc_get_tuning: null argument");
     out->spread = c->spread_mode;
     out->sweep_batch = c->sweep_batch;
+    out->graphs = c->replay ? 1 : 0;
     return BC_OK;
 }
 
@@ -1176,8 +1223,11 @@ bc_status bc_set_tuning(bc_ctx_t c, const bc_tuning *t)
     if (!c || !t) return fail(BC_ERR_ARG, "bc_set_tuning: null argument");
     if (t->spread != 0 && t->spread != 1) return fail(BC_ERR_ARG, "bc_set_tuning: spread must be 0 or 1");
     if (t->sweep_batch < 1 || t->sweep_batch > 65534) return fail(BC_ERR_ARG, "bc_set_tuning: sweep_batch must be in [1, 65534]");
+    if (t->graphs != 0 && t->graphs != 1) return fail(BC_ERR_ARG, "bc_set_tuning: graphs must be 0 or 1");
     c->spread_mode = t->spread;
     c->sweep_batch = t->sweep_batch;
+    c->replay = t->graphs == 1;
+    if (!c->replay) c->ws.drop_graph();
     return BC_OK;
 }
 

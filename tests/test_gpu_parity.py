@@ -282,11 +282,34 @@ def test_autotune_keeps_a_valid_choice():
     sa = ctx.shape(wl.A.xyz, wl.A.level)
     sb = ctx.shape(wl.B.xyz, wl.B.level)
     t = ctx.autotune(sa, sb, rotations=40)
-    assert t == ctx.tuning and t["spread"] in (0, 1) and t["sweep_batch"] in (16, 32, 64)
+    assert t == ctx.tuning and t["spread"] in (0, 1) and t["sweep_batch"] in (16, 32, 64) and t["graphs"] == 1
     got = ctx.correlate(sa, sb, wl.quats).double().cpu().numpy()[0]
     check(got, oracle_grid(wl.A, wl.B, wl.quats[0], wl.N), what=f"after autotune {t}")
     with pytest.raises(bc.BallCorrError):
         ctx.set_tuning(spread=2)
     with pytest.raises(bc.BallCorrError):
         ctx.set_tuning(sweep_batch=0)
+    sa.close(); sb.close(); ctx.close()
+
+
+@pytest.mark.parametrize("spread", SPREADS)
+def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread):
+    # Identical passes (same descriptors and buffers) replay the recorded graph;
+    # a changed rotation re-records; switching replay off launches kernel by kernel.
+    bc = bcmod()
+    wl = synth.small_pair(5)
+    q = synth.shoemake_quaternions(synth.SplitMix64(31), 2).astype(np.float32)
+    refs = [oracle_grid(wl.A, wl.B, q[r], wl.N) for r in range(2)]
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    ctx.set_tuning(spread=spread, graphs=1)
+    sa = ctx.shape(wl.A.xyz, wl.A.level)
+    sb = ctx.shape(wl.B.xyz, wl.B.level)
+    out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device="cuda")
+    for r in (0, 0, 0, 1, 1, 0):
+        ctx.correlate(sa, sb, q[r:r + 1], out)
+        check(out.double().cpu().numpy()[0], refs[r], what=f"graph replay, rotation {r}, spread {spread}")
+    ctx.set_tuning(graphs=0)
+    assert ctx.tuning["graphs"] == 0
+    ctx.correlate(sa, sb, q[1:2], out)
+    check(out.double().cpu().numpy()[0], refs[1], what=f"kernel by kernel, spread {spread}")
     sa.close(); sb.close(); ctx.close()

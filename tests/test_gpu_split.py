@@ -28,13 +28,7 @@ def f32(S):
 
 
 def run(bc, A, B, q, N, W, precision):
-    radii = np.ascontiguousarray(A.radii, dtype=np.float64)
-    ctx = bc.Context.__new__(bc.Context)
-    ctx.N, ctx.W, ctx.period, ctx.radii = N, W, 2.0, tuple(A.radii)
-    ctx.stream = torch.cuda.current_stream()
-    ctx.handle = bc.bc_create(N, W, radii, 2.0, 0.0, precision=precision, stream=ctx.stream.cuda_stream)
-    import weakref
-    ctx._shapes, ctx._nets = weakref.WeakSet(), weakref.WeakSet()
+    ctx = bc.Context(N, W, A.radii, precision=precision)
     sa, sb = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
     g = ctx.correlate(sa, sb, np.asarray(q, np.float32))
     ctx.sync()
