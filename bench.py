@@ -46,24 +46,26 @@ UNIT = "poses/s"
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM traffic per launch measured by ncu for the kernels below (one capture
-# each; see profiles/).  An entry counts only while the kernel sources it was
-# measured on are unchanged (sha256 over csrc/*.cu and csrc/*.cuh of the
-# package, first 16 hex digits).
+# each; see profiles/).  An entry counts only while the device-code sources it
+# was measured on are unchanged (sha256 over KERNEL_SOURCES, first 16 hex
+# digits).
 NCU_TRAFFIC = {
-    "k_spread": {"bytes": 1.839e+07, "kernel_hash": "ee4428456c7f0572", "source": "profiles/ncu_full_scale_pair_N128.md"},
-    "k_fft_z": {"bytes": 7.3e+07, "kernel_hash": "ee4428456c7f0572", "source": "profiles/ncu_full_scale_pair_N128.md"},
-    "k_fft_y": {"bytes": 9.376e+07, "kernel_hash": "ee4428456c7f0572", "source": "profiles/ncu_full_scale_pair_N128.md"},
-    "k_fft_x": {"bytes": 7.548e+07, "kernel_hash": "ee4428456c7f0572", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_spread": {"bytes": 1.838e+07, "kernel_hash": "37b755c63debb1d6", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_fft_z": {"bytes": 7.295e+07, "kernel_hash": "37b755c63debb1d6", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_fft_y": {"bytes": 9.452e+07, "kernel_hash": "37b755c63debb1d6", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_fft_x": {"bytes": 7.375e+07, "kernel_hash": "37b755c63debb1d6", "source": "profiles/ncu_full_scale_pair_N128.md"},
 }
 
 
+KERNEL_SOURCES = ("bc_kernels.cu", "bc_binned.cu", "bc_query.cu", "bc_fft.cuh", "bc_device.cuh", "bc_internal.h")
+
+
 def kernel_source_hash():
-    import glob
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1711_05075_gb300", "csrc")
-    for p in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
-        with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode() + b"\0" + f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 
