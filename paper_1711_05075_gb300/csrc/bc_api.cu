@@ -81,14 +81,22 @@ struct Workspace {
     bool bins_dirty = false;  // bin counts may be non-zero (an enqueue failed midway)
     std::vector<char> last_desc; // descriptors the device copies hold
     void *last_inst_p = nullptr, *last_pairs_p = nullptr;
-    // the last pass recorded as a CUDA graph, and what it was recorded for
-    cudaGraphExec_t gexec = nullptr;
-    std::vector<char> gkey;
+    // passes recorded as CUDA graphs, by launch signature (least recently used
+    // first out), and signatures seen once but not yet recorded
+    struct Graph {
+        std::vector<char> key;
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long used = 0;
+    };
+    std::vector<Graph> graphs;
+    std::vector<std::vector<char>> seen;
+    unsigned long long tick = 0;
     void drop_graph()
     {
-        if (gexec) cudaGraphExecDestroy(gexec);
-        gexec = nullptr;
-        gkey.clear();
+        for (Graph &g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+        seen.clear();
     }
     void release()
     {
@@ -756,18 +764,36 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
     const bool profiling = c->prof_on && c->prof_calls < c->prof_max;
     if (profiling || !c->replay)
         return launch_job(c, ws, job, (const InstDesc *)ws.inst.p, (const PairDesc *)ws.pairs.p, dout, keys, true, c->stream);
-    // Replay: a pass whose descriptors, outputs, weights and workspaces match the
-    // recorded one is the same sequence of launches with the same arguments.
-    std::vector<char> key(ws.last_desc);
+    // Replay.  The kernels read the instance and pair descriptors from device
+    // memory, so two passes with the same launch signature -- counts and sizes
+    // that set grids and kernel arguments, output and workspace buffers,
+    // weights, spreading implementation -- are the same launches, whatever the
+    // descriptors hold.  A signature is recorded as a graph when it is seen the
+    // second time, and replayed from then on.
+    std::vector<char> key;
     auto add = [&](const void *v, size_t n) { key.insert(key.end(), (const char *)v, (const char *)v + n); };
+    const long long sig[] = {(long long)job.inst.size(), (long long)job.pairs.size(), (long long)job.nmain,
+                             (long long)job.cache_first, (long long)job.koff, (long long)job.max_knots,
+                             (long long)job.mode};
+    add(sig, sizeof(sig));
     const void *ptrs[] = {dout, keys, job.w.ballft, ws.ku.p, ws.plan.p, ws.inst.p, ws.pairs.p, ws.grid.p, ws.z1.p, ws.y1.p,
                           ws.h.p, ws.fa.p, ws.boxes.p, ws.cnt.p, ws.cur.p, ws.rec.p, c->stream};
     add(ptrs, sizeof(ptrs));
     add(&job.w.sign, sizeof(job.w.sign));
-    add(&job.mode, sizeof(job.mode));
+    constexpr size_t kMaxGraphs = 8;
     cudaError_t e;
-    if (!ws.gexec || key != ws.gkey) {
-        ws.drop_graph();
+    Workspace::Graph *hit = nullptr;
+    for (Workspace::Graph &g : ws.graphs)
+        if (g.key == key) hit = &g;
+    if (!hit) {
+        auto it = std::find(ws.seen.begin(), ws.seen.end(), key);
+        if (it == ws.seen.end()) { // first sighting: launch kernel by kernel
+            if (ws.seen.size() >= kMaxGraphs) ws.seen.erase(ws.seen.begin());
+            ws.seen.push_back(key);
+            return launch_job(c, ws, job, (const InstDesc *)ws.inst.p, (const PairDesc *)ws.pairs.p, dout, keys, true,
+                              c->stream);
+        }
+        ws.seen.erase(it);
         if (!c->capture_stream && (e = cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e, "capture stream");
         if ((e = cudaStreamBeginCapture(c->capture_stream, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
@@ -777,15 +803,21 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(c->capture_stream, &graph);
         if (s == BC_OK && e != cudaSuccess) s = cuda_fail(e, "end capture");
-        if (s == BC_OK && (e = cudaGraphInstantiate(&ws.gexec, graph, 0)) != cudaSuccess) {
-            ws.gexec = nullptr;
-            s = cuda_fail(e, "instantiate");
-        }
+        cudaGraphExec_t exec = nullptr;
+        if (s == BC_OK && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess) s = cuda_fail(e, "instantiate");
         if (graph) cudaGraphDestroy(graph);
         if (s != BC_OK) return s;
-        ws.gkey.swap(key);
+        if (ws.graphs.size() >= kMaxGraphs) { // evict the least recently used
+            auto lru = std::min_element(ws.graphs.begin(), ws.graphs.end(),
+                                        [](const Workspace::Graph &x, const Workspace::Graph &y) { return x.used < y.used; });
+            cudaGraphExecDestroy(lru->exec);
+            ws.graphs.erase(lru);
+        }
+        ws.graphs.push_back(Workspace::Graph{std::move(key), exec, 0});
+        hit = &ws.graphs.back();
     }
-    if ((e = cudaGraphLaunch(ws.gexec, c->stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+    hit->used = ++ws.tick;
+    if ((e = cudaGraphLaunch(hit->exec, c->stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
     return BC_OK;
 }
 
