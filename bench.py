@@ -509,6 +509,8 @@ def run_learned(args):
         fa, fb = bc.moments(ctx, hA), bc.moments(ctx, hB)
         Xs.append(net.features(torch.tensor(q, device=dev), fa, fb))
         z = (peak - peak.mean()) / peak.std()
+        if args.target_alpha > 0:  # monotone stretch of the top: same ranking, MSE weighted toward it
+            z = torch.exp(args.target_alpha * (z - 3.0))
         ts.append(z)
         # rotation augmentation: (S A, S R B) has the same peak over translations as (A, R B)
         rng_aug = synth.SplitMix64(seed + 500000)
@@ -565,6 +567,8 @@ def run_learned(args):
         fa, fb = bc.moments(ctx, hA), bc.moments(ctx, hB)
         pred = net.predict(net.features(qd, fa, fb)).cpu().numpy()
         z = (p - p.mean()) / p.std()
+        if args.target_alpha > 0:
+            z = np.exp(args.target_alpha * (z - 3.0))
         test_mse.append(float(np.mean((pred - z) ** 2)))
         best = int(np.argmax(p))  # first maximum = lowest index on ties
         chosen = set(idx.cpu().numpy().tolist())
@@ -604,7 +608,8 @@ def run_learned(args):
                    "train_pairs": args.train_pairs, "train_rotations_per_pair": args.train_rot,
                    "eval_pairs": args.eval_pairs, "eval_rotations_per_pair": R, "topk": K, "hidden": H,
                    "epochs": args.epochs, "adam_steps": steps, "batch": bs, "lr": lr,
-                   "rotation_augmentation_per_pair": args.augment},
+                   "rotation_augmentation_per_pair": args.augment,
+                   "target": "exp(%g (z - 3))" % args.target_alpha if args.target_alpha > 0 else "z"},
         "plain_per_rotation_poses_s": plain,
         "batched_exhaustive_poses_s": batched,
         "learned_effective_poses_s": learned,
@@ -657,6 +662,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--target-alpha", type=float, default=0.0,
+                    help="train on exp(alpha (z - 3)) of the standardised peak z instead of z (0: z)")
     ap.add_argument("--augment", type=int, default=32,
                     help="extra random orientations of each training receptor (rotation augmentation)")
     args = ap.parse_args()
