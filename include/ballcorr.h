@@ -213,26 +213,35 @@ bc_status bc_query_destroy(bc_query_t q);
  *                   spreading box is kept in device memory.
  *   sweep_batch  rotations per pass of bc_sweep, bc_sweep_plan and
  *                bc_learned_sweep when their batch is 0 (1 .. 65534).
+ *   fft_schedule bit mask of the forward FP32 passes (1: z, 2: y, 4: x) that
+ *                use an alternative radix schedule (64 = 4.16, 128 = 16.8,
+ *                192 = 3.4.16, 256 = 4.8.8, 512 = 8.4.16) instead of the default
+ *                of their length (32 = 4.8, 64 = 8.8, 96 = 3.4.8, 128 = 8.16,
+ *                192 = 3.8.8, 256 = 16.16, 512 = 8.8.8); 0 .. 7.  Same
+ *                transform, other rounding order.
  *   graphs       1: a pass of a direct call (bc_correlate, bc_score, bc_pairs,
  *                ...) whose descriptors, output buffers and workspaces equal
  *                those of the previous pass is replayed from a CUDA graph
  *                recorded on its first run (one graph launch instead of the
  *                kernel launches); 0: always launch kernel by kernel.  Passes
  *                recorded by bc_profile_begin always launch kernel by kernel.
- * A new context starts with {0, 64, 1}.  Plans keep the choices in force when
+ * A new context starts with {0, 64, 1, 0}.  Plans keep the choices in force when
  * they were made.  bc_autotune times the candidates on the given shapes --
- * bc_correlate of A with B (identity) for `spread`; when rotations > 0, a
- * sweep of that many fixed rotations of B for each sweep_batch in
- * {16, 32, 64, 128, 256} not above it -- keeps the fastest in the context and
- * returns them in out (may be NULL).  It synchronises the stream and grows
- * the context's workspaces to the largest candidate.  Errors: BC_ERR_ARG (null context or
- * shape, shapes from another context, rotations outside [0, 65534], a value
- * out of range in bc_set_tuning), BC_ERR_OOM, BC_ERR_CUDA.  bc_autotune
- * leaves `graphs` as it is. */
+ * bc_correlate of A with B (identity) for `spread`; in FP32 contexts the
+ * per-stage times of profiled correlations under each schedule, pass by pass,
+ * for `fft_schedule`; when rotations > 0, a sweep of that many fixed rotations
+ * of B for each sweep_batch in {16, 32, 64, 128, 256} not above it -- keeps
+ * the fastest in the context and returns them in out (may be NULL).  It
+ * synchronises the stream, grows the context's workspaces to the largest
+ * candidate and ends any profiling started with bc_profile_begin; it leaves
+ * `graphs` as it is.  Errors: BC_ERR_ARG (null context
+ * or shape, shapes from another context, rotations outside [0, 65534], a
+ * value out of range in bc_set_tuning), BC_ERR_OOM, BC_ERR_CUDA. */
 typedef struct {
     int spread;
     int sweep_batch;
     int graphs;
+    int fft_schedule;
 } bc_tuning;
 bc_status bc_get_tuning(bc_ctx_t ctx, bc_tuning *out);
 bc_status bc_set_tuning(bc_ctx_t ctx, const bc_tuning *t);

@@ -129,6 +129,7 @@ struct bc_ctx_s {
     // implementation choices (bc_set_tuning / bc_autotune)
     int spread_mode = 0;  // 0: spreading boxes in HBM (k_spread + k_fft_z); 1: binned, fused into the z pass
     int sweep_batch = 64; // rotations per pass when a sweep's batch argument is 0
+    int fft_sched = 0;    // alternative radix schedule per forward FP32 pass: bit 0 z, bit 1 y, bit 2 x
     // workspaces
     Workspace ws;                 // pipeline workspaces of direct calls
     DevBuf outbuf, stats, learn, tune; // host-output staging, shape checks, learned-sweep and tuning scratch
@@ -541,7 +542,8 @@ struct Job {
     std::vector<InstDesc> inst;
     std::vector<PairDesc> pairs;
     bool cache_first = false;
-    int mode = 0; // spreading: 0 boxes in HBM, 1 binned (fused into the z pass)
+    int mode = 0;  // spreading: 0 boxes in HBM, 1 binned (fused into the z pass)
+    int sched = 0; // radix schedule of the forward passes
     Weights w;
     int nmain = 0, koff = 0, max_knots = 0;
     long long goff = 0, zoff = 0, yoff = 0, hpairs = 0;
@@ -556,6 +558,7 @@ static Job plan_job(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std
     j.pairs = pairs;
     j.cache_first = cache_first;
     j.mode = c->spread_mode;
+    j.sched = c->fft_sched;
     j.nmain = (int)pairs.size() - (cache_first ? 1 : 0);
     j.inst.resize(shapes.size());
     for (size_t i = 0; i < shapes.size(); i++) {
@@ -645,6 +648,7 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
 {
     Geometry g = c->g;
     g.inv_P3 *= job.w.sign;
+    g.sched = job.sched;
     const int ninst = (int)job.inst.size();
     Tables t = tables_of(c);
     if (job.w.ballft) t.ballft = job.w.ballft;
@@ -774,7 +778,7 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
     auto add = [&](const void *v, size_t n) { key.insert(key.end(), (const char *)v, (const char *)v + n); };
     const long long sig[] = {(long long)job.inst.size(), (long long)job.pairs.size(), (long long)job.nmain,
                              (long long)job.cache_first, (long long)job.koff, (long long)job.max_knots,
-                             (long long)job.mode};
+                             (long long)job.mode, (long long)job.sched};
     add(sig, sizeof(sig));
     const void *ptrs[] = {dout, keys, job.w.ballft, ws.ku.p, ws.plan.p, ws.inst.p, ws.pairs.p, ws.grid.p, ws.z1.p, ws.y1.p,
                           ws.h.p, ws.fa.p, ws.boxes.p, ws.cnt.p, ws.cur.p, ws.rec.p, c->stream};
@@ -1247,6 +1251,7 @@ bc_status bc_get_tuning(bc_ctx_t c, bc_tuning *out)
     out->spread = c->spread_mode;
     out->sweep_batch = c->sweep_batch;
     out->graphs = c->replay ? 1 : 0;
+    out->fft_schedule = c->fft_sched;
     return BC_OK;
 }
 
@@ -1256,6 +1261,8 @@ bc_status bc_set_tuning(bc_ctx_t c, const bc_tuning *t)
     if (t->spread != 0 && t->spread != 1) return fail(BC_ERR_ARG, "bc_set_tuning: spread must be 0 or 1");
     if (t->sweep_batch < 1 || t->sweep_batch > 65534) return fail(BC_ERR_ARG, "bc_set_tuning: sweep_batch must be in [1, 65534]");
     if (t->graphs != 0 && t->graphs != 1) return fail(BC_ERR_ARG, "bc_set_tuning: graphs must be 0 or 1");
+    if (t->fft_schedule < 0 || t->fft_schedule > 7) return fail(BC_ERR_ARG, "bc_set_tuning: fft_schedule must be in [0, 7]");
+    c->fft_sched = t->fft_schedule;
     c->spread_mode = t->spread;
     c->sweep_batch = t->sweep_batch;
     c->replay = t->graphs == 1;
@@ -1331,6 +1338,31 @@ bc_status bc_autotune(bc_ctx_t c, bc_shape_t A, bc_shape_t B, int rotations, bc_
             }
         }
         c->spread_mode = best_mode;
+        // radix schedule per forward pass (the split-precision passes have their own):
+        // the stage times of profiled correlations under each schedule, pass by pass
+        if (c->g.prec == 0) {
+            double stage_ms[2][BC_NUM_STAGES] = {};
+            const int saved = c->fft_sched;
+            for (int sched = 0; sched <= 1; sched++) {
+                c->fft_sched = sched ? 7 : 0;
+                bc_status s = BC_OK;
+                for (int i = 0; s == BC_OK && i < 3; i++) s = bc_correlate(c, A, B, ident, 1, dout, 1); // warm-up
+                bc_profile prof;
+                if (s == BC_OK) s = bc_profile_begin(c, 7);
+                for (int i = 0; s == BC_OK && i < 7; i++) s = bc_correlate(c, A, B, ident, 1, dout, 1);
+                if (s == BC_OK) s = bc_profile_end(c, &prof);
+                if (s != BC_OK) {
+                    c->fft_sched = saved;
+                    return s;
+                }
+                for (int st = 0; st < BC_NUM_STAGES; st++) stage_ms[sched][st] = prof.ms[st];
+            }
+            int mask = 0;
+            const int stage_of_bit[3] = {2, 3, 4}; // fft_z, fft_y, fft_x
+            for (int b = 0; b < 3; b++)
+                if (stage_ms[1][stage_of_bit[b]] < 0.98 * stage_ms[0][stage_of_bit[b]]) mask |= 1 << b; // beyond noise
+            c->fft_sched = mask;
+        }
         if (rotations > 0) {
             // fixed rotations: Shoemake's map of a golden-ratio (Weyl) sequence in [0, 1)^3
             std::vector<float> q(4 * (size_t)rotations);

@@ -157,12 +157,12 @@ cudaError_t launch_bin(const Geometry &g, const Tables &t, const InstDesc *inst,
 // nearest multiple of 2^-s (error <= 2^-(s+1), 2^-22 for T = 255) and the
 // integer sums do not depend on the order of the additions.  The first
 // transform stage reads the tile back as FP32 (value = sum 2^-s).
-template <int NF, bool SP>
+template <int NF, bool SP, int S>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
                const int *__restrict__ cur, const float *__restrict__ rec, float2 *z1)
 {
-    constexpr bool three = Radix<NF>::r2 > 1;
+    constexpr bool three = Radix<NF, S>::r2 > 1;
     constexpr int H = NF / 4; // kept z modes (N/2, n = 2N)
     extern __shared__ float4 sm4[];
     float2 *tw = reinterpret_cast<float2 *>(sm4);
@@ -178,7 +178,7 @@ k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int nin
     const int L = g.L, W = g.W;
     const unsigned magicW = 0xFFFFFFFFu / (unsigned)W + 1u; // e / W = umulhi(e, magicW) for e < 2^16
     const int lane = threadIdx.x & 31;
-    FirstInputs<NF, Radix<NF>::r0, CL, TB> in;
+    FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
     RotStart rs;
     int chunk = 0;
     for (int i = 0; i < ninst; i++) {
@@ -269,11 +269,11 @@ k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int nin
             });
             __syncthreads(); // the tile is in registers; S1 is free for the transform
             if constexpr (SP) in.scatter(S0);
-            else rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
+            else rr_first<NF, Radix<NF, S>::r0, false, CL, TB>(in, S0);
             __syncthreads();
             auto sink = [&](int, int, int c, int pos, float2 v) { OUT[pos * CL + c] = v; };
             if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
-            else rr_rest<NF, false, CL, TB>(S0, S1, tw, sink);
+            else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
             __syncthreads();
             // Z = FFT(a + i b) -> A_k = (Z_k + conj Z_{n-k}) / 2, B_k = (Z_k - conj Z_{n-k}) / (2i),
             // unpacked into a staging area [row][k] (row stride H + 1), then each
@@ -299,16 +299,17 @@ k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int nin
     }
 }
 
-template <int NF, bool SP = false>
+template <int NF, bool SP = false, int S = 0>
 static cudaError_t fft_z_binned_t(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
                                   const InstPlan *plan, const int *cur, const float *rec, float2 *z1, int nsm,
                                   cudaStream_t s)
 {
+    if (!SP && S == 0 && (g.sched & 1)) return fft_z_binned_t<NF, false, 1>(g, t, inst, ninst, plan, cur, rec, z1, nsm, s);
     const size_t smem = sizeof(float2) * (NF + 2 * NF * CL) + sizeof(int) * 2 * TB;
-    cudaError_t e = set_smem(k_fft_z_binned<NF, SP>, smem);
+    cudaError_t e = set_smem(k_fft_z_binned<NF, SP, S>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_z_binned<NF, SP><<<resident_blocks(k_fft_z_binned<NF, SP>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan,
-                                                                                               cur, rec, z1);
+    k_fft_z_binned<NF, SP, S><<<resident_blocks(k_fft_z_binned<NF, SP, S>, smem, nsm), TB, smem, s>>>(
+        g, t, inst, ninst, plan, cur, rec, z1);
     return cudaGetLastError();
 }
 

@@ -146,15 +146,23 @@ __device__ __forceinline__ void dft_small(float2 *v)
     }
 }
 
-template <int NF>
+// Radix schedules: S = 0 the default of each size, S = 1 an alternative for
+// the forward passes (chosen by measurement; every last stage has a radix
+// divisible by 4, which the pruned x pass needs).
+template <int NF, int S = 0>
 struct Radix;
-template <> struct Radix<32>  { static constexpr int r0 = 4, r1 = 8, r2 = 1; };
-template <> struct Radix<64>  { static constexpr int r0 = 8, r1 = 8, r2 = 1; };
-template <> struct Radix<96>  { static constexpr int r0 = 3, r1 = 4, r2 = 8; };
-template <> struct Radix<128> { static constexpr int r0 = 8, r1 = 16, r2 = 1; };
-template <> struct Radix<192> { static constexpr int r0 = 3, r1 = 8, r2 = 8; };
-template <> struct Radix<256> { static constexpr int r0 = 16, r1 = 16, r2 = 1; };
-template <> struct Radix<512> { static constexpr int r0 = 8, r1 = 8, r2 = 8; };
+template <> struct Radix<32, 0>  { static constexpr int r0 = 4, r1 = 8, r2 = 1; };
+template <> struct Radix<64, 0>  { static constexpr int r0 = 8, r1 = 8, r2 = 1; };
+template <> struct Radix<96, 0>  { static constexpr int r0 = 3, r1 = 4, r2 = 8; };
+template <> struct Radix<128, 0> { static constexpr int r0 = 8, r1 = 16, r2 = 1; };
+template <> struct Radix<192, 0> { static constexpr int r0 = 3, r1 = 8, r2 = 8; };
+template <> struct Radix<256, 0> { static constexpr int r0 = 16, r1 = 16, r2 = 1; };
+template <> struct Radix<512, 0> { static constexpr int r0 = 8, r1 = 8, r2 = 8; };
+template <> struct Radix<64, 1>  { static constexpr int r0 = 4, r1 = 16, r2 = 1; };
+template <> struct Radix<128, 1> { static constexpr int r0 = 16, r1 = 8, r2 = 1; };
+template <> struct Radix<192, 1> { static constexpr int r0 = 3, r1 = 4, r2 = 16; };
+template <> struct Radix<256, 1> { static constexpr int r0 = 4, r1 = 8, r2 = 8; };
+template <> struct Radix<512, 1> { static constexpr int r0 = 8, r1 = 4, r2 = 16; };
 
 // ---------------------------------------------------------------------------
 // Interleaved tiles: C lines stored as x[pos * C + c].  Consecutive threads take
@@ -317,19 +325,19 @@ __device__ __forceinline__ void rr_last(const float2 *__restrict__ in, const flo
 }
 
 // Radix of the last stage of a schedule and its output stride.
-template <int NF>
+template <int NF, int S = 0>
 struct LastStage {
-    static constexpr int R = Radix<NF>::r2 > 1 ? Radix<NF>::r2 : Radix<NF>::r1;
+    static constexpr int R = Radix<NF, S>::r2 > 1 ? Radix<NF, S>::r2 : Radix<NF, S>::r1;
     static constexpr int NS = NF / R;
 };
 
 // The middle (three-stage schedules) and last stages after rr_first has
 // written tile s0; s1 is scratch for three-stage schedules.  All threads call
 // it; the caller adds a barrier before s0/s1 are written again.
-template <int NF, bool INV, int C, int NT, class Sink>
+template <int NF, bool INV, int C, int NT, int S = 0, class Sink>
 __device__ __forceinline__ void rr_rest(float2 *s0, float2 *s1, const float2 *tw, Sink sink)
 {
-    using R = Radix<NF>;
+    using R = Radix<NF, S>;
     if constexpr (R::r2 > 1) {
         il_stage<NF, R::r1, R::r0, INV, C, NT>(s0, s1, tw);
         __syncthreads();

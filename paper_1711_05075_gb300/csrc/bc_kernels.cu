@@ -386,12 +386,12 @@ cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *in
 // then reset to zero so the boxes are clean for the next launch.
 // Output rows: with Z = FFT(a + i b), A_k = (Z_k + conj Z_{n-k}) / 2,
 // B_k = (Z_k - conj Z_{n-k}) / (2i), for m_z = k in [0, N/2).
-template <int NF, bool SP>
+template <int NF, bool SP, int S>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
         float *grid, float2 *z1)
 {
-    constexpr bool three = Radix<NF>::r2 > 1;
+    constexpr bool three = Radix<NF, S>::r2 > 1;
     extern __shared__ float4 sm4[];
     float2 *tw = reinterpret_cast<float2 *>(sm4);
     float2 *S0 = tw + NF, *S1 = S0 + NF * CL;
@@ -400,7 +400,7 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     load_twiddles<NF>(tw, tb.tw_n);
     constexpr int H = NF / 4; // kept z modes (N/2, n = 2N)
     const int L = g.L;
-    FirstInputs<NF, Radix<NF>::r0, CL, TB> in;
+    FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
     RotStart rs;
     for (int i = 0; i < ninst; i++) {
         const InstPlan p = plan[i];
@@ -424,7 +424,7 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
             const int l = it / (b0 * nyb), rem = it - l * (b0 * nyb);
             const int ix = rem / nyb, iy0 = (rem - ix * nyb) << 5;
             if constexpr (SP) in.scatter(S0);
-            else rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
+            else rr_first<NF, Radix<NF, S>::r0, false, CL, TB>(in, S0);
             {
                 float2 *base = G2 + (long long)it * bz * 16;
                 in.for_each([&](int c, int pos) {
@@ -437,7 +437,7 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
             if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
             auto sink = [&](int, int, int c, int pos, float2 v) { OUT[pos * CL + c] = v; };
             if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
-            else rr_rest<NF, false, CL, TB>(S0, S1, tw, sink);
+            else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
             __syncthreads();
             // unpack into a staging area [row][k] (row stride H + 1), then write
             // each 8H-byte row of z1 with consecutive threads on consecutive k
@@ -469,7 +469,7 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
 // m_y = -N/2, stored as zero).  First-stage inputs come straight from z1 and
 // last-stage outputs go straight to y1; the next item is loaded while the
 // current one finishes.
-template <int NF, bool SP>
+template <int NF, bool SP, int S>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
         const float2 *__restrict__ z1, float2 *y1)
@@ -481,7 +481,7 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     constexpr int H = NF / 4, N = NF / 2;
     const int L = g.L;
     constexpr int nch = H / CL;
-    FirstInputs<NF, Radix<NF>::r0, CL, TB> in;
+    FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
     RotStart rs;
     for (int i = 0; i < ninst; i++) {
         const InstPlan p = plan[i];
@@ -503,7 +503,7 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
         for (; it < items; it += gridDim.x) {
             const int lx = it / nch, ch = it - lx * nch;
             if constexpr (SP) in.scatter(S0);
-            else rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
+            else rr_first<NF, Radix<NF, S>::r0, false, CL, TB>(in, S0);
             __syncthreads();
             if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
             float2 *Y = y1 + d.y1_off + (long long)lx * N * H + ch * CL;
@@ -515,7 +515,7 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
                 Y[(long long)jy * H + c] = jy == N / 2 ? make_float2(0.f, 0.f) : v;
             };
             if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
-            else rr_rest<NF, false, CL, TB>(S0, S1, tw, sink);
+            else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
             __syncthreads();
         }
         rs.rot += items;
@@ -528,20 +528,20 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
 // (m_x = pos - n), i.e. exactly m_x in [-N/2, N/2); those slots of F hold
 // sum_l T_l(|m|^2) D(m) FFT_x[Y_l](m) for m_y = mode(j_y), m_z = 16 ch + c.
 // Level l + 1 is loaded while level l is transformed.
-template <int NF>
+template <int NF, int S>
 struct XModes {
-    static constexpr int R = LastStage<NF>::R, NS = LastStage<NF>::NS;
+    static constexpr int R = LastStage<NF, S>::R, NS = LastStage<NF, S>::NS;
     static constexpr int IT = (NS * CL + TB - 1) / TB;
     static __device__ __forceinline__ constexpr bool kept(int r) { return r < R / 4 || r >= 3 * R / 4; }
 };
 
-template <int NF, int NI, bool SP>
-__device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF>::IT][XModes<NF>::R], const Geometry &g,
+template <int NF, int NI, bool SP, int S>
+__device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF, S>::IT][XModes<NF, S>::R], const Geometry &g,
                                            const Tables &tb, const InstDesc *__restrict__ inst,
                                            const InstPlan *__restrict__ plan, int si, const float2 *__restrict__ y1,
                                            int jy, int ch, const float2 *tw, float2 *S0, float2 *S1)
 {
-    using XM = XModes<NF>;
+    using XM = XModes<NF, S>;
     constexpr int H = NI / 2, N = NI;
     const int L = g.L;
     const int Q = tb.qmax + 1;
@@ -563,11 +563,11 @@ __device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF>::IT][XModes<NF
             return ix < b0 ? base[(long long)ix * N * H + c] : make_float2(0.f, 0.f);
         };
     };
-    FirstInputs<NF, Radix<NF>::r0, CL, TB> in;
+    FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
     in.load(src(0));
     for (int l = 0; l < L; l++) {
         if constexpr (SP) in.scatter(S0);
-        else rr_first<NF, Radix<NF>::r0, false, CL, TB>(in, S0);
+        else rr_first<NF, Radix<NF, S>::r0, false, CL, TB>(in, S0);
         __syncthreads();
         if (l + 1 < L) in.load(src(l + 1));
         const float *T = tb.ballft + (long long)l * Q;
@@ -580,16 +580,16 @@ __device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF>::IT][XModes<NF
             F[it][r] = make_float2(fmaf(Mv, v.x, F[it][r].x), fmaf(Mv, v.y, F[it][r].y));
         };
         if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
-        else rr_rest<NF, false, CL, TB>(S0, S1, tw, sink);
+        else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
         __syncthreads();
     }
 }
 
 // Calls f(it, r, c, jx) for every kept mode slot of the calling thread.
-template <int NF, int NI, class Fn>
+template <int NF, int NI, int S, class Fn>
 __device__ __forceinline__ void for_kept(Fn f)
 {
-    using XM = XModes<NF>;
+    using XM = XModes<NF, S>;
 #pragma unroll
     for (int it = 0; it < XM::IT; it++) {
         const int idx = (int)threadIdx.x + it * TB;
@@ -614,13 +614,13 @@ __device__ __forceinline__ void for_kept(Fn f)
 // translation grid to t = -P/2: exp(2 pi i m (-P/2) / P) = (-1)^m.
 // With pair.a < 0, F_A comes from the cached spectrum; with pair.b < 0, F_A is
 // written to `fa_out` and nothing else happens.
-template <int NF, int NI, bool SP>
+template <int NF, int NI, bool SP, int S>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan *__restrict__ plan,
         const PairDesc *__restrict__ pairs, int npairs, const float2 *__restrict__ y1,
         const float2 *__restrict__ fa_cache, float2 *fa_out, float2 *h)
 {
-    using XM = XModes<NF>;
+    using XM = XModes<NF, S>;
     extern __shared__ float4 sm4[];
     float2 *twF = reinterpret_cast<float2 *>(sm4);
     float2 *twI = twF + NF, *S0 = twI + NI, *S1 = S0 + NF * CL, *FAt = S1 + NF * CL;
@@ -641,23 +641,23 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
             {
                 float2 FA[XM::IT][XM::R];
                 if (pr.a < 0) {
-                    for_kept<NF, NI>([&](int i2, int r, int c, int jx) {
+                    for_kept<NF, NI, S>([&](int i2, int r, int c, int jx) {
                         FAt[jx * CL + c] = fa_cache[((long long)jx * N + jy) * H + ch * CL + c];
                     });
                 } else {
-                    spectrum_x<NF, NI, SP>(FA, g, tb, inst, plan, pr.a, y1, jy, ch, twF, S0, S1);
-                    for_kept<NF, NI>([&](int i2, int r, int c, int jx) { FAt[jx * CL + c] = FA[i2][r]; });
+                    spectrum_x<NF, NI, SP, S>(FA, g, tb, inst, plan, pr.a, y1, jy, ch, twF, S0, S1);
+                    for_kept<NF, NI, S>([&](int i2, int r, int c, int jx) { FAt[jx * CL + c] = FA[i2][r]; });
                 }
             }
             if (pr.b < 0) {
-                for_kept<NF, NI>([&](int i2, int r, int c, int jx) {
+                for_kept<NF, NI, S>([&](int i2, int r, int c, int jx) {
                     fa_out[((long long)jx * N + jy) * H + ch * CL + c] = FAt[jx * CL + c];
                 });
                 continue;
             }
             float2 FB[XM::IT][XM::R];
-            spectrum_x<NF, NI, SP>(FB, g, tb, inst, plan, pr.b, y1, jy, ch, twF, S0, S1);
-            for_kept<NF, NI>([&](int i2, int r, int c, int jx) {
+            spectrum_x<NF, NI, SP, S>(FB, g, tb, inst, plan, pr.b, y1, jy, ch, twF, S0, S1);
+            for_kept<NF, NI, S>([&](int i2, int r, int c, int jx) {
                 const int mx = mode_of(jx, N), mz = ch * CL + c;
                 float2 v = make_float2(0.f, 0.f);
                 if (jx != N / 2 && jy != N / 2) {
@@ -836,14 +836,15 @@ k_ifft_z(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
 }
 
 // ------------------------------------------------------------------ launchers
-template <int NF, bool SP = false>
+template <int NF, bool SP = false, int S = 0>
 static cudaError_t fft_z_t(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
                            float *grid, float2 *z1, int nsm, cudaStream_t s)
 {
+    if (!SP && S == 0 && (g.sched & 1)) return fft_z_t<NF, false, 1>(g, t, inst, ninst, plan, grid, z1, nsm, s);
     const size_t smem = sizeof(float2) * (NF + 2 * NF * CL);
-    cudaError_t e = set_smem(k_fft_z<NF, SP>, smem);
+    cudaError_t e = set_smem(k_fft_z<NF, SP, S>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_z<NF, SP><<<resident_blocks(k_fft_z<NF, SP>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, grid, z1);
+    k_fft_z<NF, SP, S><<<resident_blocks(k_fft_z<NF, SP, S>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, grid, z1);
     return cudaGetLastError();
 }
 
@@ -865,14 +866,15 @@ cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *ins
     }
 }
 
-template <int NF, bool SP = false>
+template <int NF, bool SP = false, int S = 0>
 static cudaError_t fft_y_t(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
                            const float2 *z1, float2 *y1, int nsm, cudaStream_t s)
 {
+    if (!SP && S == 0 && (g.sched & 2)) return fft_y_t<NF, false, 1>(g, t, inst, ninst, plan, z1, y1, nsm, s);
     const size_t smem = sizeof(float2) * (NF + 2 * NF * CL);
-    cudaError_t e = set_smem(k_fft_y<NF, SP>, smem);
+    cudaError_t e = set_smem(k_fft_y<NF, SP, S>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_y<NF, SP><<<resident_blocks(k_fft_y<NF, SP>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, z1, y1);
+    k_fft_y<NF, SP, S><<<resident_blocks(k_fft_y<NF, SP, S>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, z1, y1);
     return cudaGetLastError();
 }
 
@@ -894,16 +896,18 @@ cudaError_t launch_fft_y(const Geometry &g, const Tables &t, const InstDesc *ins
     }
 }
 
-template <int NF, int NI, bool SP = false>
+template <int NF, int NI, bool SP = false, int S = 0>
 static cudaError_t fft_x_t(const Geometry &g, const Tables &t, const InstDesc *inst, const InstPlan *plan,
                            const PairDesc *pairs, int npairs, const float2 *y1, const float2 *fa_cache, float2 *fa_out,
                            float2 *h, int nsm, cudaStream_t s)
 {
+    if (!SP && S == 0 && (g.sched & 4))
+        return fft_x_t<NF, NI, false, 1>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
     const size_t smem = sizeof(float2) * (NF + NI + 2 * NF * CL + NI * CL);
-    cudaError_t e = set_smem(k_fft_x<NF, NI, SP>, smem);
+    cudaError_t e = set_smem(k_fft_x<NF, NI, SP, S>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_x<NF, NI, SP><<<resident_blocks(k_fft_x<NF, NI, SP>, smem, nsm), TB, smem, s>>>(g, t, inst, plan, pairs, npairs,
-                                                                                        y1, fa_cache, fa_out, h);
+    k_fft_x<NF, NI, SP, S><<<resident_blocks(k_fft_x<NF, NI, SP, S>, smem, nsm), TB, smem, s>>>(
+        g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h);
     return cudaGetLastError();
 }
 

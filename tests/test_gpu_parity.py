@@ -42,11 +42,11 @@ def f32(shape):
 SPREADS = (0, 1)
 
 
-def run_gpu(A, B, quats, N, W, radii=None, period=2.0, spread=1):
+def run_gpu(A, B, quats, N, W, radii=None, period=2.0, spread=1, fft_schedule=0):
     bc = bcmod()
     radii = A.radii if radii is None else radii
     ctx = bc.Context(N, W, radii, period)
-    ctx.set_tuning(spread=spread)
+    ctx.set_tuning(spread=spread, fft_schedule=fft_schedule)
     try:
         sa = ctx.shape(A.xyz.astype(np.float32), A.level)
         sb = ctx.shape(B.xyz.astype(np.float32), B.level)
@@ -283,6 +283,7 @@ def test_autotune_keeps_a_valid_choice():
     sb = ctx.shape(wl.B.xyz, wl.B.level)
     t = ctx.autotune(sa, sb, rotations=40)
     assert t == ctx.tuning and t["spread"] in (0, 1) and t["sweep_batch"] in (16, 32, 64) and t["graphs"] == 1
+    assert 0 <= t["fft_schedule"] <= 7
     got = ctx.correlate(sa, sb, wl.quats).double().cpu().numpy()[0]
     check(got, oracle_grid(wl.A, wl.B, wl.quats[0], wl.N), what=f"after autotune {t}")
     with pytest.raises(bc.BallCorrError):
@@ -313,3 +314,27 @@ def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread):
     ctx.correlate(sa, sb, q[1:2], out)
     check(out.double().cpu().numpy()[0], refs[1], what=f"kernel by kernel, spread {spread}")
     sa.close(); sb.close(); ctx.close()
+
+
+@pytest.mark.parametrize("N,W,n", [(32, 8, 300), (64, 8, 400), (96, 8, 500), (128, 8, 300)])
+def test_alternative_radix_schedules(N, W, n):
+    # fft_schedule 1: 64 = 4.16, 128 = 16.8, 192 = 3.4.16, 256 = 4.8.8 for the forward passes
+    A = synth.ellipsoid_shape(n, 25, synth.RADII_4, synth.PROBS_4)
+    B = synth.torus_shape(n, 26, synth.RADII_4, synth.PROBS_4)
+    q = synth.shoemake_quaternions(synth.SplitMix64(27), 1)
+    ref = oracle_grid(A, B, q[0], N)
+    for sp in SPREADS:
+        got = run_gpu(A, B, q, N, W, spread=sp, fft_schedule=7)
+        check(got[0], ref, what=f"schedule 1, N={N}, spread {sp}")
+
+
+def test_alternative_radix_schedule_512_sampled():
+    N, W = 256, 8
+    A = synth.ellipsoid_shape(300, 28, synth.RADII_4, synth.PROBS_4)
+    B = synth.torus_shape(300, 29, synth.RADII_4, synth.PROBS_4)
+    q = synth.IDENTITY_QUAT
+    g = O.band_limited_spectrum(f32(A), f32(B), q[0], N)
+    idx = synth.translation_sample(N, 4096, seed=2)
+    ref = O.inverse_at(g, O.grid_points(N, idx=idx))
+    got = run_gpu(A, B, q, N, W, spread=0, fft_schedule=7)[0]
+    check(got.reshape(-1)[idx], ref, what="schedule 1 (512 = 8.4.16), N=256 sampled")
