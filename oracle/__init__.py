@@ -57,6 +57,10 @@ def lib():
         L.bco_corr_spectrum.argtypes = [i, vp, vp, vp]
         L.bco_inverse_at.argtypes = [i, d, vp, i, vp, vp]
         L.bco_inverse_grid.argtypes = [i, d, vp, vp]
+        L.bco_lifted_pair.restype = d
+        L.bco_lifted_pair.argtypes = [d, d, d, d, d]
+        L.bco_lifted_exact.restype = i
+        L.bco_lifted_exact.argtypes = [i, vp, vp, i, vp, vp, vp, d, d, d, i, vp, vp]
         _lib = L
     return _lib
 
@@ -262,3 +266,103 @@ def query_at(ghat, modes, w, t, period=2.0, chunk=4096):
         ph = np.exp(2j * np.pi * (t @ modes[s:s + chunk].T.astype(np.float64)) / period)
         out += (ph * gm[s:s + chunk]).real.sum(axis=1)
     return out / period ** 3
+
+
+
+# ------------------------------------------------------------------ lifted (4D) correlation (Sec. 3.2)
+# Knots carry their own radii: knot (x, r) lifts to the trimmed half-cone
+# D(x, r) = {(y, s) : |y - x| <= r - s, r - L <= s <= r} (Eq. (L2cone)), whose
+# r = 0 section is the ball of radius r.  B is rotated and mirrored in r
+# before the correlation (the pre-reflection of Sec. 3.2), and the lifted
+# correlation g(t, r) is the 4D overlap volume of the two cone unions at the
+# lifted translation (t, r).  Its r = 0 section is positive exactly where the
+# two ball unions intersect (Lemma 2); r != 0 sections are the obstacles of
+# offset shapes.  Fourier form (Eqs. (rhoAhat), (fconehat), (ccghat)):
+#     rho^_X(xi, eta) = sum_i exp(-2 pi i (xi . x_i / P + eta r_i / P_r))
+#     g^(xi, eta)     = rho^_A(xi, eta) conj(rho^_{R B mirrored}(xi, eta)) f^_D0(xi, eta)^2
+#     f^_D0(xi, eta)  = int_0^L h^(s, 2 pi |xi| / P) exp(+2 pi i eta s / P_r) ds
+#     g(t, r)         = P^-3 P_r^-1 sum g^(xi, eta) exp(2 pi i (xi . t / P + eta r / P_r)),
+# xi in [-N/2, N/2)^3, eta in [-N_r/2, N_r/2), every mode with a component at
+# the lower edge (-N/2 or -N_r/2) set to zero.
+def lifted_pair(ri, rj, rs, d, L):
+    """4D overlap volume of one cone pair at lifted offset rs, centre distance d (closed form)."""
+    return lib().bco_lifted_pair(float(ri), float(rj), float(rs), float(d), float(L))
+
+
+def lifted_exact(xa, ra, xb, rb, t, rs, L, q=None, period=2.0):
+    """Layer (a): the lifted correlation at translations t (nt x 3) and lifted offset rs."""
+    xa, ra, xb, rb = _f64(xa).reshape(-1, 3), _f64(ra), _f64(xb).reshape(-1, 3), _f64(rb)
+    t = _f64(t).reshape(-1, 3)
+    out = np.empty(t.shape[0], dtype=np.float64)
+    qa = None if q is None else _f64(q).reshape(4)
+    rc = lib().bco_lifted_exact(int(xa.shape[0]), _ptr(xa), _ptr(ra), int(xb.shape[0]), _ptr(xb), _ptr(rb),
+                                None if qa is None else _ptr(qa), float(L), float(period), float(rs),
+                                int(t.shape[0]), _ptr(t), _ptr(out))
+    if rc == -2:
+        raise ValueError("r_i + r_j + |r_s| must stay below P/2")
+    if rc:
+        raise ValueError("zero quaternion")
+    return out
+
+
+def _fft_modes(n):
+    j = np.arange(n)
+    return np.where(j < n // 2, j, j - n)
+
+
+def lifted_spectrum(xyz, r, N, Nr, period=2.0, period_r=0.4, q=None, mirror=False):
+    """rho^(xi, eta) as complex128 [N, N, N/2, Nr]: xi_x, xi_y and eta in FFT order, xi_z in [0, N/2)."""
+    x = _f64(xyz).reshape(-1, 3)
+    if q is not None:
+        x = rotate(x, q)
+    rr = -_f64(r) if mirror else _f64(r)
+    m = _fft_modes(N).astype(np.float64)
+    e = _fft_modes(Nr).astype(np.float64)
+    Ex = np.exp(-2j * np.pi * np.outer(m, x[:, 0]) / period)
+    Ey = np.exp(-2j * np.pi * np.outer(m, x[:, 1]) / period)
+    Ez = np.exp(-2j * np.pi * np.outer(np.arange(N // 2), x[:, 2]) / period)
+    Er = np.exp(-2j * np.pi * np.outer(e, rr) / period_r)
+    E1 = (Ex[:, None, :] * Ey[None, :, :]).reshape(N * N, -1)
+    E2 = (Ez[:, None, :] * Er[None, :, :]).reshape((N // 2) * Nr, -1)
+    return (E1 @ E2.T).reshape(N, N, N // 2, Nr)
+
+
+def cone_ft(k, alpha, L, nodes=64):
+    """f^_D0 = int_0^L h^(s, k) exp(i alpha s) ds for arrays k (angular wavenumber) and alpha,
+    by Gauss-Legendre quadrature (numpy's nodes) in FP64; broadcasts."""
+    k, alpha = np.broadcast_arrays(_f64(k), _f64(alpha))
+    xg, wg = np.polynomial.legendre.leggauss(nodes)
+    s = 0.5 * L * (xg + 1.0)
+    w = 0.5 * L * wg
+    kk = k[..., None] * np.ones_like(s)
+    h = ball_ft(np.broadcast_to(s, kk.shape), kk)
+    return np.sum(w * h * np.exp(1j * alpha[..., None] * s), axis=-1)
+
+
+def lifted_corr_spectrum(A, B, q, N, Nr, L, period=2.0, period_r=0.4):
+    """g^(xi, eta) [N, N, N/2, Nr]; A and B are (xyz, r) pairs; lower-edge modes zeroed."""
+    ra = lifted_spectrum(A[0], A[1], N, Nr, period, period_r)
+    rb = lifted_spectrum(B[0], B[1], N, Nr, period, period_r, q=q, mirror=True)
+    m = _fft_modes(N).astype(np.float64)
+    mz = np.arange(N // 2, dtype=np.float64)
+    e = _fft_modes(Nr).astype(np.float64)
+    q2 = m[:, None, None] ** 2 + m[None, :, None] ** 2 + mz[None, None, :] ** 2
+    k = 2.0 * np.pi * np.sqrt(q2) / period
+    f = cone_ft(k[..., None], 2.0 * np.pi * e[None, None, None, :] / period_r, L)
+    g = ra * np.conj(rb) * f * f
+    g[N // 2, :, :, :] = 0.0
+    g[:, N // 2, :, :] = 0.0
+    g[:, :, :, Nr // 2] = 0.0
+    return g
+
+
+def lifted_slices(ghat, slices, period=2.0, period_r=0.4):
+    """g(t_k, r_s) on the N^3 translation grid for each r_s: [len(slices), N, N, N]."""
+    N, Nr = ghat.shape[0], ghat.shape[3]
+    e = _fft_modes(Nr).astype(np.float64)
+    out = []
+    for rs in slices:
+        G = np.zeros((N, N, N // 2 + 1), dtype=np.complex128)
+        G[:, :, : N // 2] = (ghat * np.exp(2j * np.pi * e * float(rs) / period_r)).sum(axis=-1) / period_r
+        out.append(inverse_grid(G, period))
+    return np.stack(out)

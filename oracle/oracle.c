@@ -24,6 +24,10 @@
  *      -N/2 set to zero (so g^ is exactly Hermitian and g exactly real), and
  *      the translation grid t_k = -P/2 + k P / N.
  *
+ * The lifted (4D) nonequiradius correlation of Sec. 3.2 has its own exact
+ * layer at the end of this file (bco_lifted_exact); its band-limited layer is
+ * a direct 4D NDFT written with numpy in oracle/__init__.py.
+ *
  * Conventions: knots are (x, y, z) triples; B is rotated by the unit quaternion
  * q = (w, x, y, z) about its own origin and then translated by t (App. B, the
  * action (R, t)x = Rx + t).  Spectra are stored as the Hermitian half
@@ -365,4 +369,87 @@ void bco_inverse_grid(int N, double P, const double *g, double *out)
                 out[((size_t)kx * N + ky) * N + kz] = sr / (P * P * P);
             }
     free(er); free(ei); free(Br); free(Bi); free(Cr); free(Ci);
+}
+
+/* ------------------------------------------- lifted (4D) correlation, layer (a) */
+/* Nonequiradius correlation of Sec. 3.2 (Eq. (convgA), Lemma 2): knot (x, r) of
+ * A lifts to the trimmed half-cone D(x, r) = {(y, s) : |y - x| <= r - s,
+ * r - L <= s <= r}; B is rotated and mirrored in r (its knot (c, r') lifts to
+ * {(y, s) : |y - R c| <= s + r', -r' <= s <= L - r'}).  The correlation of the
+ * two lifted indicator sums at the lifted translation (t, r_s) is the 4D volume
+ * of overlap, summed over knot pairs.  At height s the two sections are balls
+ * of radii rho1 = r_i - s and rho2 = s + r_j - r_s whose sum S = r_i + r_j - r_s
+ * does not depend on s, at centre distance d = |x_i - R c_j - t| (nearest
+ * periodic image); so the lens volume is a polynomial in s on each of three
+ * pieces (ball 2 inside ball 1, lens, ball 1 inside ball 2) and the integral
+ * over s is taken in closed form.  Nonzero only when d < S (Lemma 2 at r_s = 0:
+ * the balls intersect).  Requires r_i + r_j + |r_s| < P/2. */
+static double lifted_pair(double ri, double rj, double rs, double d, double L)
+{
+    const double S = ri + rj - rs;
+    if (S <= 0.0 || d >= S) return 0.0;
+    double lo = ri - L > rs - rj ? ri - L : rs - rj;
+    double hi = ri < rs - rj + L ? ri : rs - rj + L;
+    if (hi <= lo) return 0.0;
+    const double c = ri - rj + rs; /* delta(s) = rho1 - rho2 = c - 2 s */
+    const double b1 = 0.5 * (c - d), b2 = 0.5 * (c + d);
+    double v = 0.0;
+    /* s < b1: delta > d, ball 2 inside ball 1: (4/3) pi rho2^3, d rho2 / ds = 1 */
+    {
+        double a = lo, b = hi < b1 ? hi : b1;
+        if (b > a) {
+            double p = a + rj - rs, q = b + rj - rs;
+            v += M_PI / 3.0 * (q * q * q * q - p * p * p * p);
+        }
+    }
+    /* b1 < s < b2: the lens pi (S - d)^2 (d^2 + 2 d S - 3 delta^2) / (12 d) */
+    if (d > 0.0) {
+        double a = lo > b1 ? lo : b1, b = hi < b2 ? hi : b2;
+        if (b > a) {
+            double da = c - 2.0 * a, db = c - 2.0 * b;
+            double int_delta2 = (da * da * da - db * db * db) / 6.0;
+            v += M_PI * (S - d) * (S - d) / (12.0 * d) * ((d * d + 2.0 * d * S) * (b - a) - 3.0 * int_delta2);
+        }
+    }
+    /* s > b2: delta < -d, ball 1 inside ball 2: (4/3) pi rho1^3, d rho1 / ds = -1 */
+    {
+        double a = lo > b2 ? lo : b2, b = hi;
+        if (b > a) {
+            double p = ri - a, q = ri - b;
+            v += M_PI / 3.0 * (p * p * p * p - q * q * q * q);
+        }
+    }
+    return v;
+}
+
+double bco_lifted_pair(double ri, double rj, double rs, double d, double L) { return lifted_pair(ri, rj, rs, d, L); }
+
+int bco_lifted_exact(int na, const double *xa, const double *ra, int nb, const double *xb, const double *rb,
+                     const double *q, double L, double P, double rs, int nt, const double *t, double *out)
+{
+    double rmax_a = 0, rmax_b = 0;
+    for (int i = 0; i < na; i++) if (ra[i] > rmax_a) rmax_a = ra[i];
+    for (int j = 0; j < nb; j++) if (rb[j] > rmax_b) rmax_b = rb[j];
+    if (rmax_a + rmax_b + fabs(rs) >= 0.5 * P) return -2;
+    double *yb = (double *)malloc(sizeof(double) * 3 * (size_t)(nb > 0 ? nb : 1));
+    if (q) {
+        if (bco_rotate(nb, xb, q, yb)) { free(yb); return -1; }
+    } else {
+        memcpy(yb, xb, sizeof(double) * 3 * (size_t)nb);
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < nt; k++) {
+        double acc = 0.0;
+        for (int i = 0; i < na; i++) {
+            for (int j = 0; j < nb; j++) {
+                double dx = min_image(xa[3 * i] - yb[3 * j] - t[3 * k], P);
+                double dy = min_image(xa[3 * i + 1] - yb[3 * j + 1] - t[3 * k + 1], P);
+                double dz = min_image(xa[3 * i + 2] - yb[3 * j + 2] - t[3 * k + 2], P);
+                acc += lifted_pair(ra[i], rb[j], rs, sqrt(dx * dx + dy * dy + dz * dz), L);
+            }
+        }
+        out[k] = acc;
+    }
+    free(yb);
+    return 0;
 }
