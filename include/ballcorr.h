@@ -200,6 +200,45 @@ bc_status bc_query_create(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float 
 bc_status bc_query_eval(bc_query_t q, const float *t, int npts, float *g, int on_device);
 bc_status bc_query_destroy(bc_query_t q);
 
+/* ---------------------------------------------------------------- lifted (4D) correlation
+ * Nonequiradius correlation of Sec. 3.2 (Eqs. (L2cone), (rhoA), (rhoAhat),
+ * (fconehat), (convgA); Lemma 2) for knots with individual radii.  Knot
+ * (x, r) lifts to the trimmed half-cone D(x, r) = {(y, s) : |y - x| <= r - s,
+ * r - L <= s <= r}, whose s = 0 section is the ball of radius r; B is rotated
+ * and then mirrored in r (s -> -s), and the lifted correlation g(t, r) is the
+ * correlation of the two cone unions' indicator sums at the lifted translation
+ * (t, r): the summed 4D overlap volume of the cone pairs.  Its r = 0 section
+ * is positive exactly at the translations where a ball of A meets a ball of
+ * t + RB (Lemma 2); a section r != 0 is the obstacle of the shapes offset by
+ * a total of -r.  Computed by a direct 4D NDFT (Eq. (rhoAhat)) on the modes
+ * xi in [-N/2, N/2)^3, eta in [-Nr/2, Nr/2) (lower-edge modes zero), times the
+ * squared cone transform f^_D0 (FP64-built table), then for each requested
+ * section the sum over eta and the inverse 3D transform onto the N^3 grid
+ * t_k = -P/2 + k P/N:
+ *     g(t, r) = P^-3 P_r^-1 sum g^(xi, eta) exp(2 pi i (xi . t / P + eta r / P_r)),
+ *     g^      = rho^_A conj(rho^_{RB mirrored}) f^_D0^2.
+ * Radii should lie in (0, L) (every cone reaches s = 0) and P_r should exceed
+ * 4 L so that sections do not wrap.  Not in the correlation context: a lifted
+ * context owns its tables and workspace.
+ * bc_lift_correlate: A, B = n x 4 FP32 (x, y, z, r), quat = 4 FP32 host values,
+ * slices = nslices (1 .. 16) FP32 host values r_s, out = nslices x N^3 FP32
+ * ([s][kx][ky][kz]); A, B and out are device (on_device = 1) or host (0)
+ * memory.  Synchronous.  Errors: BC_ERR_ARG (null pointer, counts out of
+ * range, zero quaternion, non-finite section), BC_ERR_UNSUPPORTED (N not 32 or
+ * 64, Nr not 8, 16, 32 or 64), BC_ERR_OOM, BC_ERR_CUDA. */
+typedef struct bc_lift_s *bc_lift_t;
+typedef struct {
+    int N;           /* modes per axis and translation grid N^3: 32 or 64 */
+    int Nr;          /* modes along the lifted axis: 8, 16, 32 or 64 */
+    double L;        /* cone height */
+    double period;   /* P, translation period */
+    double period_r; /* P_r, period along the lifted axis */
+} bc_lift_params;
+bc_status bc_lift_create(const bc_lift_params *params, void *cuda_stream, bc_lift_t *out);
+bc_status bc_lift_correlate(bc_lift_t lift, const float *A, int nA, const float *B, int nB, const float *quat,
+                            const float *slices, int nslices, float *out, int on_device);
+bc_status bc_lift_destroy(bc_lift_t lift);
+
 /* ---------------------------------------------------------------- tuning
  * Not in the paper: implementation choices that change speed, not results
  * (beyond the FP32 rounding order of the spreading sums).

@@ -38,6 +38,11 @@ class bc_tuning(ctypes.Structure):
                 ("fft_schedule", ctypes.c_int)]
 
 
+class bc_lift_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("Nr", ctypes.c_int), ("L", ctypes.c_double), ("period", ctypes.c_double),
+                ("period_r", ctypes.c_double)]
+
+
 class BallCorrError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{BC_STATUS.get(status, status)}: {msg}")
@@ -122,6 +127,11 @@ def lib():
         L.bc_query_eval.argtypes = [vp, vp, i, vp, i]
         L.bc_query_destroy.argtypes = [vp]
         for f in ("bc_query_create", "bc_query_eval", "bc_query_destroy"):
+            getattr(L, f).restype = st
+        L.bc_lift_create.argtypes = [ctypes.POINTER(bc_lift_params), vp, ctypes.POINTER(vp)]
+        L.bc_lift_correlate.argtypes = [vp, vp, i, vp, i, vp, vp, i, vp, i]
+        L.bc_lift_destroy.argtypes = [vp]
+        for f in ("bc_lift_create", "bc_lift_correlate", "bc_lift_destroy"):
             getattr(L, f).restype = st
         _lib = L
     return _lib
@@ -591,6 +601,69 @@ class Query:
     def close(self):
         if self.handle is not None:
             bc_query_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bc_lift_create(N, Nr, L, period=2.0, period_r=None, stream=None):
+    p = bc_lift_params(int(N), int(Nr), float(L), float(period), float(4 * L if period_r is None else period_r))
+    h = ctypes.c_void_p()
+    _check(lib().bc_lift_create(ctypes.byref(p), None if stream is None else ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h
+
+
+def bc_lift_correlate(lf, A, nA, B, nB, quat, slices, nslices, out, on_device):
+    _check(lib().bc_lift_correlate(lf, _ptr(A), int(nA), _ptr(B), int(nB), _ptr(quat), _ptr(slices), int(nslices),
+                                   _ptr(out), int(on_device)))
+
+
+def bc_lift_destroy(lf):
+    _check(lib().bc_lift_destroy(lf))
+
+
+class Lift:
+    """Lifted (4D) nonequiradius correlation (Sec. 3.2) on the current CUDA device and stream."""
+
+    def __init__(self, N, Nr, L, period=2.0, period_r=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        self.N, self.Nr, self.L = int(N), int(Nr), float(L)
+        self.period = float(period)
+        self.period_r = float(4 * L if period_r is None else period_r)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = None
+        self.handle = bc_lift_create(N, Nr, L, period, self.period_r, stream=self.stream.cuda_stream)
+
+    def correlate(self, A, B, quat, slices=(0.0,)):
+        """A, B: (n, 4) (x, y, z, r) float32 CUDA tensors or arrays; returns (len(slices), N, N, N) CUDA tensor."""
+        import torch
+        q = np.ascontiguousarray(np.asarray(quat, dtype=np.float32).reshape(4))
+        sl = np.ascontiguousarray(np.asarray(slices, dtype=np.float32).reshape(-1))
+        dev = lambda x: (x if isinstance(x, torch.Tensor) else torch.as_tensor(np.asarray(x, np.float32))).to(
+            device="cuda", dtype=torch.float32).contiguous()
+        Ad, Bd = dev(A), dev(B)
+        out = torch.empty((sl.size, self.N, self.N, self.N), dtype=torch.float32, device="cuda")
+        bc_lift_correlate(self.handle, Ad, Ad.shape[0], Bd, Bd.shape[0], q, sl, sl.size, out, 1)
+        return out
+
+    def correlate_host(self, A, B, quat, slices=(0.0,)):
+        q = np.ascontiguousarray(np.asarray(quat, dtype=np.float32).reshape(4))
+        sl = np.ascontiguousarray(np.asarray(slices, dtype=np.float32).reshape(-1))
+        Ah = np.ascontiguousarray(np.asarray(A, dtype=np.float32).reshape(-1, 4))
+        Bh = np.ascontiguousarray(np.asarray(B, dtype=np.float32).reshape(-1, 4))
+        out = np.empty((sl.size, self.N, self.N, self.N), dtype=np.float32)
+        bc_lift_correlate(self.handle, Ah, Ah.shape[0], Bh, Bh.shape[0], q, sl, sl.size, out, 0)
+        return out
+
+    def close(self):
+        if self.handle is not None:
+            bc_lift_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -47,6 +47,22 @@ __device__ __forceinline__ float kb_window(float s, float beta, float inv_scaled
     return expf(-beta * s2 / (1.f + sq)) * scaled_i0 * inv_scaled_i0beta;
 }
 
+// Transform of the indicator of a ball of radius r at angular wavenumber k
+// (Sec. 2.5): 4 pi (sin kr - kr cos kr) / k^3, and for x = kr < 0.5 the
+// Maclaurin series 4 pi r^3 (1/3 - x^2/30 + x^4/840 - x^6/45360 + x^8/3991680)
+// (the next term is below 2e-12 relative).  FP64.
+__device__ __forceinline__ double ball_ft64(double r, double k)
+{
+    const double pi = 3.14159265358979323846;
+    const double x = k * r;
+    if (x < 0.5) {
+        const double x2 = x * x;
+        return 4.0 * pi * r * r * r *
+               (1.0 / 3.0 - x2 / 30.0 + x2 * x2 / 840.0 - x2 * x2 * x2 / 45360.0 + x2 * x2 * x2 * x2 / 3991680.0);
+    }
+    return 4.0 * pi * (sin(x) - x * cos(x)) / (k * k * k);
+}
+
 // Support box of instance i -> its plan (the box accumulators are reset for
 // the next launch).  A box larger than the instance's capacity raises the
 // error word and the instance is treated as empty.

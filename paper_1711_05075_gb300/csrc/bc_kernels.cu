@@ -57,17 +57,6 @@ __device__ __forceinline__ int mode_of(int j, int N) { return j < N / 2 ? j : j 
 // h^(r, k) = 4 pi (sin kr - kr cos kr) / k^3 with k = 2 pi sqrt(q) / P, and for
 // x = kr < 0.5 the Maclaurin series 4 pi r^3 (1/3 - x^2/30 + x^4/840 -
 // x^6/45360 + x^8/3991680), indexed by the integer q = |m|^2.
-__device__ double ball_ft64(double r, double k)
-{
-    const double pi = 3.14159265358979323846;
-    const double x = k * r;
-    if (x < 0.5) {
-        const double x2 = x * x;
-        return 4.0 * pi * r * r * r *
-               (1.0 / 3.0 - x2 / 30.0 + x2 * x2 / 840.0 - x2 * x2 * x2 / 45360.0 + x2 * x2 * x2 * x2 / 3991680.0);
-    }
-    return 4.0 * pi * (sin(x) - x * cos(x)) / (k * k * k);
-}
 
 __global__ void k_build_tables(int N, int n, int W, int L, int qmax, double beta, double period,
                                const double *__restrict__ radii, float *deconv, float *ballft, float2 *tw_n,

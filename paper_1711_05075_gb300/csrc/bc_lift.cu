@@ -1,0 +1,472 @@
+// Lifted (4D) nonequiradius correlation of Sec. 3.2 (Eqs. (rhoA), (rhoAhat),
+// (fconehat), (convgA); Lemma 2), computed as a direct 4D NDFT.
+//
+// Knot (x, r) of a shape lifts to the trimmed half-cone D(x, r) (Eq. (L2cone))
+// whose r = 0 section is the ball of radius r; B is rotated and mirrored in r
+// (the pre-reflection of Sec. 3.2).  In the Fourier domain
+//     rho^_X(xi, eta) = sum_i exp(-2 pi i (xi . x_i / P + eta r_i / P_r))     (Eq. (rhoAhat))
+//     g^(xi, eta)     = rho^_A conj(rho^_{R B mirrored}) f^_D0(xi, eta)^2       (Eq. (convgA) in Fourier form)
+//     f^_D0(xi, eta)  = int_0^L h^(s, 2 pi |xi| / P) exp(+2 pi i eta s / P_r) ds
+//     g(t, r_s)       = P^-3 P_r^-1 sum g^ exp(2 pi i (xi . t / P + eta r_s / P_r))
+// with xi in [-N/2, N/2)^3, eta in [-N_r/2, N_r/2), lower-edge modes zero.
+// The r = 0 section of g is the 4D overlap volume of the two cone unions,
+// positive exactly where the two ball unions meet (Lemma 2); other sections
+// are the obstacles of offset shapes.
+//
+//   k_lift_gauss      Gauss-Legendre nodes on [-1, 1] (Newton on the Legendre
+//                     three-term recurrence; Golub & Welsch 1969 give the same
+//                     nodes) for the cone transform, FP64;
+//   k_lift_cone       f^_D0 per (|xi|^2, eta) by that quadrature, FP64, rounded once;
+//   k_lift_twiddles   exp(-2 pi i k / N), FP64, rounded once;
+//   k_lift_phases     per knot and axis the factors exp(-2 pi i m x_a / P) and
+//                     exp(-2 pi i eta r / P_r) (FP64 arguments, rounded once),
+//                     knot-major, after rotating and mirroring B;
+//   k_lift_ndft       rho^ as a contraction over the knots of the separable
+//                     factors: rows (xi_x, xi_y), columns (xi_z, eta), 64 x 64
+//                     output tiles, knots split across blocks (FP32, partial
+//                     sums added with vector atomics);
+//   k_lift_collapse   per translation mode and section r_s the sum over eta of
+//                     rho^_A conj(rho^_B) f^_D0^2 exp(2 pi i eta r_s / P_r), with
+//                     the P^-3 P_r^-1 scale and the grid-origin sign;
+//   k_lift_ifft_x     inverse transform along x; the inverse along y and the
+//                     complex-to-real inverse along z are the correlation's own
+//                     passes (k_ifft_y, k_ifft_z).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ballcorr.h"
+#include "bc_device.cuh"
+
+namespace bc {
+
+constexpr int LIFT_GAUSS = 48;   // quadrature nodes of the cone transform
+constexpr int LIFT_TILE = 64;    // output tile of the contraction (rows and columns)
+constexpr int LIFT_KC = 32;      // knots staged per step
+constexpr int LIFT_MAX_SLICES = 16;
+
+__device__ __forceinline__ int lift_mode(int j, int n) { return j < n / 2 ? j : j - n; }
+
+// Node k of the n-point Gauss-Legendre rule and its weight.
+__global__ void k_lift_gauss(int n, double *x, double *w)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double pi = 3.14159265358979323846;
+    double z = cos(pi * (k + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; it++) {
+        double p0 = 1.0, p1 = z;
+        for (int j = 1; j < n; j++) {
+            const double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        const double dz = p1 / dp;
+        z -= dz;
+        if (fabs(dz) < 1e-16) break;
+    }
+    x[k] = z;
+    w[k] = 2.0 / ((1.0 - z * z) * dp * dp);
+}
+
+// cone[q * Nr + e] = f^_D0 at |xi|^2 = q and eta = mode(e).
+__global__ void k_lift_cone(int qmax, int Nr, double L, double period, double period_r, const double *__restrict__ gx,
+                            const double *__restrict__ gw, float2 *cone)
+{
+    const double pi = 3.14159265358979323846;
+    const int total = (qmax + 1) * Nr;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+        const int q = u / Nr, e = u - q * Nr;
+        const double k = 2.0 * pi * sqrt((double)q) / period;
+        const double alpha = 2.0 * pi * lift_mode(e, Nr) / period_r;
+        double re = 0.0, im = 0.0;
+        for (int j = 0; j < LIFT_GAUSS; j++) {
+            const double s = 0.5 * L * (gx[j] + 1.0);
+            const double h = 0.5 * L * gw[j] * ball_ft64(s, k);
+            double sn, cs;
+            sincos(alpha * s, &sn, &cs);
+            re += h * cs;
+            im += h * sn;
+        }
+        cone[u] = make_float2((float)re, (float)im);
+    }
+}
+
+__global__ void k_lift_twiddles(int N, float2 *tw)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    double sn, cs;
+    sincospi(2.0 * k / N, &sn, &cs);
+    tw[k] = make_float2((float)cs, (float)-sn);
+}
+
+// Per knot: E[i * T + m] for the T = N + N + N/2 + Nr factors of knot i
+// (x modes, y modes in FFT order; z modes 0 .. N/2 - 1; eta modes in FFT order).
+__global__ void k_lift_phases(const float4 *__restrict__ knots, int n, double qw, double qx, double qy, double qz,
+                              int mirror, int N, int Nr, double period, double period_r, float2 *E)
+{
+    const int T = 2 * N + N / 2 + Nr;
+    const int i = blockIdx.x;
+    if (i >= n) return;
+    const float4 c = knots[i];
+    // R from the unit quaternion (w, x, y, z)
+    const double R00 = 1 - 2 * (qy * qy + qz * qz), R01 = 2 * (qx * qy - qw * qz), R02 = 2 * (qx * qz + qw * qy);
+    const double R10 = 2 * (qx * qy + qw * qz), R11 = 1 - 2 * (qx * qx + qz * qz), R12 = 2 * (qy * qz - qw * qx);
+    const double R20 = 2 * (qx * qz - qw * qy), R21 = 2 * (qy * qz + qw * qx), R22 = 1 - 2 * (qx * qx + qy * qy);
+    const double x = R00 * c.x + R01 * c.y + R02 * c.z;
+    const double y = R10 * c.x + R11 * c.y + R12 * c.z;
+    const double z = R20 * c.x + R21 * c.y + R22 * c.z;
+    const double r = mirror ? -(double)c.w : (double)c.w;
+    for (int m = threadIdx.x; m < T; m += blockDim.x) {
+        double v, arg;
+        if (m < N) {
+            v = x / period;
+            arg = lift_mode(m, N) * v;
+        } else if (m < 2 * N) {
+            v = y / period;
+            arg = lift_mode(m - N, N) * v;
+        } else if (m < 2 * N + N / 2) {
+            v = z / period;
+            arg = (m - 2 * N) * v;
+        } else {
+            v = r / period_r;
+            arg = lift_mode(m - 2 * N - N / 2, Nr) * v;
+        }
+        arg -= rint(arg); // exp(-2 pi i arg) depends on arg mod 1 only
+        double sn, cs;
+        sincospi(2.0 * arg, &sn, &cs);
+        E[(long long)i * T + m] = make_float2((float)cs, (float)-sn);
+    }
+}
+
+// out[a][b] += sum_{i in this block's knot range} E1[a][i] E2[b][i], a = (xi_x, xi_y)
+// (rows, N * N), b = (xi_z, eta) (columns, N/2 * Nr), E1 = Ex Ey, E2 = Ez Er.
+// Thread t owns the 4 x 4 outputs rows 4 (t / 16) .., columns 4 (t % 16) ...
+__global__ void __launch_bounds__(256)
+k_lift_ndft(const float2 *__restrict__ E, int n, int N, int Nr, int kper, float2 *out)
+{
+    __shared__ float2 E1s[LIFT_KC][LIFT_TILE], E2s[LIFT_KC][LIFT_TILE];
+    const int T = 2 * N + N / 2 + Nr;
+    const int C = (N / 2) * Nr;
+    const int a0 = blockIdx.y * LIFT_TILE, b0 = blockIdx.x * LIFT_TILE;
+    const int k_begin = blockIdx.z * kper, k_end = min(n, k_begin + kper);
+    const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+    float2 acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++) acc[r][c] = make_float2(0.f, 0.f);
+    for (int k0 = k_begin; k0 < k_end; k0 += LIFT_KC) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < LIFT_KC * LIFT_TILE; e += blockDim.x) {
+            const int kk = e / LIFT_TILE, j = e - kk * LIFT_TILE;
+            const int i = k0 + kk;
+            float2 v1 = make_float2(0.f, 0.f), v2 = make_float2(0.f, 0.f);
+            if (i < k_end) {
+                const float2 *Ei = E + (long long)i * T;
+                const int a = a0 + j, ax = a / N, ay = a - ax * N;
+                v1 = cmul(Ei[ax], Ei[N + ay]);
+                const int b = b0 + j, bz = b / Nr, be = b - bz * Nr;
+                v2 = cmul(Ei[2 * N + bz], Ei[2 * N + N / 2 + be]);
+            }
+            E1s[kk][j] = v1;
+            E2s[kk][j] = v2;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < LIFT_KC; kk++) {
+            float2 x[4], y[4];
+#pragma unroll
+            for (int r = 0; r < 4; r++) x[r] = E1s[kk][4 * tr + r];
+#pragma unroll
+            for (int c = 0; c < 4; c++) y[c] = E2s[kk][4 * tc + c];
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    acc[r][c].x = fmaf(x[r].x, y[c].x, fmaf(-x[r].y, y[c].y, acc[r][c].x));
+                    acc[r][c].y = fmaf(x[r].x, y[c].y, fmaf(x[r].y, y[c].x, acc[r][c].y));
+                }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            atomicAdd(out + (long long)(a0 + 4 * tr + r) * C + b0 + 4 * tc + c, acc[r][c]);
+}
+
+// h[s][jx][jy][mz] = sign scale sum_eta rho^_A conj(rho^_B) cone^2 exp(2 pi i eta r_s / P_r),
+// zero on the lower-edge modes; scale = P^-3 P_r^-1, sign = (-1)^(m_x + m_y + m_z).
+__global__ void k_lift_collapse(const float2 *__restrict__ ra, const float2 *__restrict__ rb,
+                                const float2 *__restrict__ cone, int N, int Nr, const float *__restrict__ slices,
+                                int nslices, double period_r, float scale, float2 *h)
+{
+    __shared__ float2 ph[LIFT_MAX_SLICES][64];
+    for (int e = threadIdx.x; e < nslices * Nr; e += blockDim.x) {
+        const int s = e / Nr, k = e - s * Nr;
+        double arg = lift_mode(k, Nr) * (double)slices[s] / period_r;
+        arg -= rint(arg);
+        double sn, cs;
+        sincospi(2.0 * arg, &sn, &cs);
+        ph[s][k] = make_float2((float)cs, (float)sn);
+    }
+    __syncthreads();
+    const int H = N / 2;
+    const int total = N * N * H;
+    const long long plane = (long long)N * N * H;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+        const int jx = u / (N * H), rem = u - jx * (N * H);
+        const int jy = rem / H, mz = rem - jy * H;
+        float2 acc[LIFT_MAX_SLICES];
+        for (int s = 0; s < nslices; s++) acc[s] = make_float2(0.f, 0.f);
+        if (jx != N / 2 && jy != N / 2) {
+            const int mx = lift_mode(jx, N), my = lift_mode(jy, N);
+            const int q = mx * mx + my * my + mz * mz;
+            const long long base = (long long)(jx * N + jy) * (H * Nr) + (long long)mz * Nr;
+            for (int k = 0; k < Nr; k++) {
+                if (k == Nr / 2) continue;
+                const float2 f = cone[q * Nr + k];
+                const float2 p = cmul(cmulc(ra[base + k], rb[base + k]), cmul(f, f));
+                for (int s = 0; s < nslices; s++) acc[s] = cadd(acc[s], cmul(p, ph[s][k]));
+            }
+            const float sg = ((mx + my + mz) & 1) ? -scale : scale;
+            for (int s = 0; s < nslices; s++) acc[s] = cscale(acc[s], sg);
+        }
+        for (int s = 0; s < nslices; s++) h[s * plane + u] = acc[s];
+    }
+}
+
+// Inverse along x, in place: item (slice, jy, chunk of 16 z-modes); 16 lines
+// of N values at stride N H.
+template <int NI>
+__global__ void __launch_bounds__(TB) k_lift_ifft_x(float2 *h, int nslices, const float2 *__restrict__ twg)
+{
+    __shared__ float2 tw[NI], A[NI * CL], B[NI * CL];
+    constexpr int H = NI / 2, nch = H / CL;
+    for (int k = threadIdx.x; k < NI; k += blockDim.x) tw[k] = twg[k];
+    const int items = nslices * NI * nch;
+    for (int it = blockIdx.x; it < items; it += gridDim.x) {
+        const int s = it / (NI * nch), rem = it - s * (NI * nch);
+        const int jy = rem / nch, ch = rem - jy * nch;
+        float2 *base = h + (long long)s * NI * NI * H + (long long)jy * H + ch * CL;
+        __syncthreads();
+        for (int e = threadIdx.x; e < NI * CL; e += blockDim.x) {
+            const int jx = e / CL, c = e - jx * CL;
+            A[jx * CL + c] = base[(long long)jx * NI * H + c];
+        }
+        __syncthreads();
+        const float2 *res = il_fft<NI, true, CL, TB>(A, B, tw);
+        for (int e = threadIdx.x; e < NI * CL; e += blockDim.x) {
+            const int kx = e / CL, c = e - kx * CL;
+            base[(long long)kx * NI * H + c] = res[kx * CL + c];
+        }
+    }
+}
+
+} // namespace bc
+
+using namespace bc;
+
+// ------------------------------------------------------------------ C ABI
+struct bc_lift_s {
+    int device = 0, nsm = 1;
+    cudaStream_t stream = nullptr;
+    int N = 0, Nr = 0, qmax = 0;
+    double L = 0, period = 2, period_r = 0;
+    float2 *cone = nullptr, *tw = nullptr;
+    void *ws = nullptr; // rho^_A, rho^_B, phase tables, h planes, slices, pair descriptors, staging
+    size_t ws_bytes = 0;
+};
+
+static bc_status lift_fail(bc_status s, const std::string &msg)
+{
+    set_last_error(msg);
+    return s;
+}
+
+static bc_status lift_cuda(cudaError_t e, const char *where)
+{
+    set_last_error(std::string(where) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BC_ERR_OOM : BC_ERR_CUDA;
+}
+
+extern "C" {
+
+bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *out)
+{
+    if (!p || !out) return lift_fail(BC_ERR_ARG, "bc_lift_create: null pointer");
+    *out = nullptr;
+    if (p->N != 32 && p->N != 64) return lift_fail(BC_ERR_UNSUPPORTED, "bc_lift_create: N must be 32 or 64");
+    if (p->Nr != 8 && p->Nr != 16 && p->Nr != 32 && p->Nr != 64)
+        return lift_fail(BC_ERR_UNSUPPORTED, "bc_lift_create: Nr must be 8, 16, 32 or 64");
+    if (!(p->L > 0) || !std::isfinite(p->L)) return lift_fail(BC_ERR_ARG, "bc_lift_create: L must be > 0");
+    if (!(p->period > 0) || !std::isfinite(p->period)) return lift_fail(BC_ERR_ARG, "bc_lift_create: period must be > 0");
+    if (!(p->period_r > 0) || !std::isfinite(p->period_r)) return lift_fail(BC_ERR_ARG, "bc_lift_create: period_r must be > 0");
+    bc_lift_s *lf = new (std::nothrow) bc_lift_s();
+    if (!lf) return lift_fail(BC_ERR_OOM, "bc_lift_create: host allocation");
+    lf->stream = (cudaStream_t)cuda_stream;
+    lf->N = p->N;
+    lf->Nr = p->Nr;
+    lf->L = p->L;
+    lf->period = p->period;
+    lf->period_r = p->period_r;
+    lf->qmax = 3 * (p->N / 2) * (p->N / 2);
+    cudaError_t e;
+    double *g = nullptr;
+    auto bail = [&](cudaError_t err, const char *w) {
+        if (g) cudaFree(g);
+        bc_lift_destroy(lf);
+        return lift_cuda(err, w);
+    };
+    if ((e = cudaGetDevice(&lf->device)) != cudaSuccess) return bail(e, "bc_lift_create: device");
+    if ((e = cudaDeviceGetAttribute(&lf->nsm, cudaDevAttrMultiProcessorCount, lf->device)) != cudaSuccess)
+        return bail(e, "bc_lift_create: device");
+    if ((e = cudaMalloc(&lf->cone, sizeof(float2) * (lf->qmax + 1) * lf->Nr)) != cudaSuccess) return bail(e, "cudaMalloc cone");
+    if ((e = cudaMalloc(&lf->tw, sizeof(float2) * lf->N)) != cudaSuccess) return bail(e, "cudaMalloc twiddles");
+    if ((e = cudaMalloc(&g, sizeof(double) * 2 * LIFT_GAUSS)) != cudaSuccess) return bail(e, "cudaMalloc nodes");
+    k_lift_gauss<<<1, 64, 0, lf->stream>>>(LIFT_GAUSS, g, g + LIFT_GAUSS);
+    const int total = (lf->qmax + 1) * lf->Nr;
+    k_lift_cone<<<(total + 255) / 256, 256, 0, lf->stream>>>(lf->qmax, lf->Nr, lf->L, lf->period, lf->period_r, g,
+                                                             g + LIFT_GAUSS, lf->cone);
+    k_lift_twiddles<<<1, 64, 0, lf->stream>>>(lf->N, lf->tw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "bc_lift_create: tables");
+    if ((e = cudaStreamSynchronize(lf->stream)) != cudaSuccess) return bail(e, "bc_lift_create: sync");
+    cudaFree(g);
+    g = nullptr;
+    *out = lf;
+    return BC_OK;
+}
+
+bc_status bc_lift_destroy(bc_lift_t lf)
+{
+    if (!lf) return BC_OK;
+    cudaStreamSynchronize(lf->stream);
+    if (lf->cone) cudaFree(lf->cone);
+    if (lf->tw) cudaFree(lf->tw);
+    if (lf->ws) cudaFree(lf->ws);
+    delete lf;
+    return BC_OK;
+}
+
+bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B, int nB, const float *quat,
+                            const float *slices, int nslices, float *out, int on_device)
+{
+    if (!lf || !quat || !slices || !out || (nA > 0 && !A) || (nB > 0 && !B))
+        return lift_fail(BC_ERR_ARG, "bc_lift_correlate: null argument");
+    if (nA < 0 || nB < 0 || nA > (1 << 22) || nB > (1 << 22))
+        return lift_fail(BC_ERR_ARG, "bc_lift_correlate: knot counts must be in [0, 2^22]");
+    if (nslices < 1 || nslices > LIFT_MAX_SLICES)
+        return lift_fail(BC_ERR_ARG, "bc_lift_correlate: nslices must be in [1, 16]");
+    double qn = 0;
+    for (int k = 0; k < 4; k++) qn += (double)quat[k] * quat[k];
+    if (!(qn > 1e-30) || !std::isfinite(qn)) return lift_fail(BC_ERR_ARG, "bc_lift_correlate: zero or non-finite quaternion");
+    for (int s = 0; s < nslices; s++)
+        if (!std::isfinite(slices[s])) return lift_fail(BC_ERR_ARG, "bc_lift_correlate: non-finite section");
+    const double inv = 1.0 / std::sqrt(qn);
+    const int N = lf->N, Nr = lf->Nr, H = N / 2;
+    const int T = 2 * N + H + Nr;
+    const size_t M = (size_t)N * N, C = (size_t)H * Nr;
+    const size_t rho_bytes = sizeof(float2) * M * C;
+    const size_t nmax = (size_t)(nA > nB ? nA : nB);
+    const size_t e_bytes = sizeof(float2) * (size_t)T * (nmax > 0 ? nmax : 1);
+    const size_t plane = (size_t)N * N * H;
+    const size_t h_bytes = sizeof(float2) * plane * nslices;
+    const size_t knot_bytes = on_device ? 0 : sizeof(float4) * (size_t)(nA + nB);
+    const size_t out_bytes = on_device ? 0 : sizeof(float) * (size_t)N * N * N * nslices;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t need = al(rho_bytes) * 2 + al(e_bytes) + al(h_bytes) + al(sizeof(float) * LIFT_MAX_SLICES) +
+                        al(sizeof(PairDesc) * LIFT_MAX_SLICES) + al(knot_bytes) + al(out_bytes);
+    cudaStream_t st = lf->stream;
+    cudaError_t e;
+    if (need > lf->ws_bytes) {
+        if (lf->ws) {
+            cudaStreamSynchronize(st);
+            cudaFree(lf->ws);
+            lf->ws = nullptr;
+            lf->ws_bytes = 0;
+        }
+        if ((e = cudaMalloc(&lf->ws, need)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: workspace");
+        lf->ws_bytes = need;
+    }
+    char *w = (char *)lf->ws;
+    float2 *rhoA = (float2 *)w;
+    w += al(rho_bytes);
+    float2 *rhoB = (float2 *)w;
+    w += al(rho_bytes);
+    float2 *E = (float2 *)w;
+    w += al(e_bytes);
+    float2 *h = (float2 *)w;
+    w += al(h_bytes);
+    float *dsl = (float *)w;
+    w += al(sizeof(float) * LIFT_MAX_SLICES);
+    PairDesc *dpairs = (PairDesc *)w;
+    w += al(sizeof(PairDesc) * LIFT_MAX_SLICES);
+    const float4 *kA = (const float4 *)A, *kB = (const float4 *)B;
+    if (!on_device) {
+        float4 *stage = (float4 *)w;
+        if (nA > 0 && (e = cudaMemcpyAsync(stage, A, sizeof(float4) * nA, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return lift_cuda(e, "bc_lift_correlate: copy A");
+        if (nB > 0 && (e = cudaMemcpyAsync(stage + nA, B, sizeof(float4) * nB, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return lift_cuda(e, "bc_lift_correlate: copy B");
+        kA = stage;
+        kB = stage + nA;
+        w += al(knot_bytes);
+    }
+    float *dout = on_device ? out : (float *)w;
+    std::vector<PairDesc> pairs(nslices);
+    for (int s = 0; s < nslices; s++)
+        pairs[s] = PairDesc{0, 0, (long long)(s * plane), (long long)s * N * N * N, 0};
+    if ((e = cudaMemcpyAsync(dsl, slices, sizeof(float) * nslices, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dpairs, pairs.data(), sizeof(PairDesc) * nslices, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return lift_cuda(e, "bc_lift_correlate: descriptors");
+    // the two lifted spectra
+    const dim3 tiles((unsigned)(C / LIFT_TILE), (unsigned)(M / LIFT_TILE));
+    for (int side = 0; side < 2; side++) {
+        const float4 *kn = side ? kB : kA;
+        const int n = side ? nB : nA;
+        float2 *rho = side ? rhoB : rhoA;
+        if ((e = cudaMemsetAsync(rho, 0, rho_bytes, st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: clear");
+        if (n == 0) continue;
+        if (side == 0)
+            k_lift_phases<<<n, 64, 0, st>>>(kn, n, 1.0, 0.0, 0.0, 0.0, 0, N, Nr, lf->period, lf->period_r, E);
+        else
+            k_lift_phases<<<n, 64, 0, st>>>(kn, n, quat[0] * inv, quat[1] * inv, quat[2] * inv, quat[3] * inv, 1, N, Nr,
+                                            lf->period, lf->period_r, E);
+        // split the knots so that about four blocks per SM run
+        const int ntile = (int)(tiles.x * tiles.y);
+        int split = (4 * lf->nsm + ntile - 1) / ntile;
+        int kper = (n + split - 1) / split;
+        kper = ((kper + LIFT_KC - 1) / LIFT_KC) * LIFT_KC;
+        split = (n + kper - 1) / kper;
+        k_lift_ndft<<<dim3(tiles.x, tiles.y, split), 256, 0, st>>>(E, n, N, Nr, kper, rho);
+        if ((e = cudaGetLastError()) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: spectrum");
+    }
+    const float scale = (float)(1.0 / (lf->period * lf->period * lf->period * lf->period_r));
+    k_lift_collapse<<<(int)((plane + 255) / 256), 256, 0, st>>>(rhoA, rhoB, lf->cone, N, Nr, dsl, nslices, lf->period_r,
+                                                                 scale, h);
+    if (N == 32) k_lift_ifft_x<32><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw);
+    else k_lift_ifft_x<64><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw);
+    if ((e = cudaGetLastError()) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: collapse");
+    Geometry g{};
+    g.N = N;
+    g.n = 2 * N;
+    g.H = H;
+    Tables t{};
+    t.tw_N = lf->tw;
+    if ((e = launch_ifft_y(g, t, dpairs, nslices, h, lf->nsm, st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: ifft y");
+    if ((e = launch_ifft_z(g, t, dpairs, nslices, h, dout, nullptr, lf->nsm, st)) != cudaSuccess)
+        return lift_cuda(e, "bc_lift_correlate: ifft z");
+    if (!on_device) {
+        if ((e = cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)N * N * N * nslices, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return lift_cuda(e, "bc_lift_correlate: copy out");
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: sync");
+    return BC_OK;
+}
+
+} // extern "C"
