@@ -233,6 +233,8 @@ typedef struct {
     double L;        /* cone height */
     double period;   /* P, translation period */
     double period_r; /* P_r, period along the lifted axis */
+    int contraction; /* 4D NDFT contraction: 1 tensor cores, 3-pass split TF32 (FP32-level
+                        accuracy); 0 FP32 on the CUDA cores */
 } bc_lift_params;
 bc_status bc_lift_create(const bc_lift_params *params, void *cuda_stream, bc_lift_t *out);
 bc_status bc_lift_correlate(bc_lift_t lift, const float *A, int nA, const float *B, int nB, const float *quat,

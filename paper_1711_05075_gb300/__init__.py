@@ -40,7 +40,7 @@ class bc_tuning(ctypes.Structure):
 
 class bc_lift_params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("Nr", ctypes.c_int), ("L", ctypes.c_double), ("period", ctypes.c_double),
-                ("period_r", ctypes.c_double)]
+                ("period_r", ctypes.c_double), ("contraction", ctypes.c_int)]
 
 
 class BallCorrError(RuntimeError):
@@ -610,8 +610,9 @@ class Query:
             pass
 
 
-def bc_lift_create(N, Nr, L, period=2.0, period_r=None, stream=None):
-    p = bc_lift_params(int(N), int(Nr), float(L), float(period), float(4 * L if period_r is None else period_r))
+def bc_lift_create(N, Nr, L, period=2.0, period_r=None, stream=None, tensor_cores=True):
+    p = bc_lift_params(int(N), int(Nr), float(L), float(period), float(4 * L if period_r is None else period_r),
+                       1 if tensor_cores else 0)
     h = ctypes.c_void_p()
     _check(lib().bc_lift_create(ctypes.byref(p), None if stream is None else ctypes.c_void_p(stream), ctypes.byref(h)))
     return h
@@ -629,7 +630,7 @@ def bc_lift_destroy(lf):
 class Lift:
     """Lifted (4D) nonequiradius correlation (Sec. 3.2) on the current CUDA device and stream."""
 
-    def __init__(self, N, Nr, L, period=2.0, period_r=None, stream=None):
+    def __init__(self, N, Nr, L, period=2.0, period_r=None, stream=None, tensor_cores=True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -638,7 +639,8 @@ class Lift:
         self.period_r = float(4 * L if period_r is None else period_r)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = None
-        self.handle = bc_lift_create(N, Nr, L, period, self.period_r, stream=self.stream.cuda_stream)
+        self.handle = bc_lift_create(N, Nr, L, period, self.period_r, stream=self.stream.cuda_stream,
+                                     tensor_cores=tensor_cores)
 
     def correlate(self, A, B, quat, slices=(0.0,)):
         """A, B: (n, 4) (x, y, z, r) float32 CUDA tensors or arrays; returns (len(slices), N, N, N) CUDA tensor."""

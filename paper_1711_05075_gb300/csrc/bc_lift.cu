@@ -23,8 +23,13 @@
 //                     knot-major, after rotating and mirroring B;
 //   k_lift_ndft       rho^ as a contraction over the knots of the separable
 //                     factors: rows (xi_x, xi_y), columns (xi_z, eta), 64 x 64
-//                     output tiles, knots split across blocks (FP32, partial
-//                     sums added with vector atomics);
+//                     output tiles, knots split across blocks (FP32 on the
+//                     CUDA cores, partial sums added with vector atomics);
+//   k_lift_scale,     the default path: the phase matrices written out as
+//   k_lift_planes     real / imaginary planes (rows (xi_x, xi_y) and
+//                     (xi_z, eta), knots contiguous), then
+//   k_lift_gemm_tc    their complex product on the tensor cores in 3-pass split
+//                     TF32 with cp.async double buffering;
 //   k_lift_collapse   per translation mode and section r_s the sum over eta of
 //                     rho^_A conj(rho^_B) f^_D0^2 exp(2 pi i eta r_s / P_r), with
 //                     the P^-3 P_r^-1 scale and the grid-origin sign;
@@ -200,6 +205,208 @@ k_lift_ndft(const float2 *__restrict__ E, int n, int N, int Nr, int kper, float2
             atomicAdd(out + (long long)(a0 + 4 * tr + r) * C + b0 + 4 * tc + c, acc[r][c]);
 }
 
+// Split TF32 on the tensor cores: each FP32 factor is split into TF32 parts
+// x = x_hi + x_lo (x_hi = tf32(x), x_lo = tf32(x - x_hi)) and each real
+// product formed as a_hi b_hi + a_hi b_lo + a_lo b_hi with FP32 accumulation
+// (mma.sync m16n8k8 .tf32; the a_lo b_lo term, 2^-22 relative, is dropped).
+struct LiftU { // a knot's coordinates over the periods: x / P, y / P, z / P, r / P_r
+    double x, y, z, w;
+};
+
+__device__ __forceinline__ unsigned to_tf32(float x)
+{
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo)
+{
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d += a b in split TF32 (three products)
+__device__ __forceinline__ void mma3(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4], unsigned bh0,
+                                     unsigned bh1, unsigned bl0, unsigned bl1)
+{
+    mma_tf32(d, ah, bh0, bh1);
+    mma_tf32(d, ah, bl0, bl1);
+    mma_tf32(d, al, bh0, bh1);
+}
+
+// Phase matrices as real / imaginary planes, knots contiguous (leading
+// dimension ld >= n, columns n .. ld - 1 zero): rows a < M = N^2 of P1 hold
+// exp(-2 pi i (m_x x + m_y y) / P) for a = (j_x, j_y); rows b < C = N/2 Nr of
+// P2 hold exp(-2 pi i (m_z z / P + eta r / P_r)) for b = (m_z, j_eta).  The
+// argument is formed and reduced mod 1 in FP64 from the knot's scaled
+// coordinates (u = x / P etc., rotated and mirrored for B), then sincospi runs
+// in FP32 on the reduced value.
+__global__ void k_lift_scale(const float4 *__restrict__ knots, int n, double qw, double qx, double qy, double qz,
+                             int mirror, double period, double period_r, LiftU *u)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 c = knots[i];
+    const double R00 = 1 - 2 * (qy * qy + qz * qz), R01 = 2 * (qx * qy - qw * qz), R02 = 2 * (qx * qz + qw * qy);
+    const double R10 = 2 * (qx * qy + qw * qz), R11 = 1 - 2 * (qx * qx + qz * qz), R12 = 2 * (qy * qz - qw * qx);
+    const double R20 = 2 * (qx * qz - qw * qy), R21 = 2 * (qy * qz + qw * qx), R22 = 1 - 2 * (qx * qx + qy * qy);
+    u[i] = LiftU{(R00 * c.x + R01 * c.y + R02 * c.z) / period, (R10 * c.x + R11 * c.y + R12 * c.z) / period,
+                 (R20 * c.x + R21 * c.y + R22 * c.z) / period, (mirror ? -(double)c.w : (double)c.w) / period_r};
+}
+
+__global__ void k_lift_planes(const LiftU *__restrict__ u, int n, int ld, int N, int Nr, float *p1re, float *p1im,
+                              float *p2re, float *p2im)
+{
+    const int M = N * N;
+    const int row = blockIdx.y; // < M + C
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ld) return;
+    float re = 0.f, im = 0.f;
+    if (i < n) {
+        const LiftU v = u[i];
+        double arg;
+        if (row < M) {
+            const int jx = row / N, jy = row - jx * N;
+            arg = lift_mode(jx, N) * v.x + lift_mode(jy, N) * v.y;
+        } else {
+            const int b = row - M, mz = b / Nr, je = b - mz * Nr;
+            arg = mz * v.z + lift_mode(je, Nr) * v.w;
+        }
+        const float r = (float)(arg - rint(arg));
+        float sn, cs;
+        sincospif(2.0f * r, &sn, &cs);
+        re = cs;
+        im = -sn;
+    }
+    if (row < M) {
+        p1re[(long long)row * ld + i] = re;
+        p1im[(long long)row * ld + i] = im;
+    } else {
+        p2re[(long long)(row - M) * ld + i] = re;
+        p2im[(long long)(row - M) * ld + i] = im;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int K>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(K)); }
+
+// out[a][b] += sum_{i in this block's knot range} P1[a][i] P2[b][i] (complex) on
+// the tensor cores.  64 x 64 output tile; the four planes' 64 x 32 tiles of a
+// knot chunk are copied with cp.async into a two-stage shared ring (row stride
+// LIFT_TS = 36 floats: 16-byte aligned rows, and fragment loads -- lanes
+// (g, t) reading row g, column t -- fall on banks 4 g + t, all distinct).
+constexpr int LIFT_TS = 36;
+constexpr int LIFT_STAGE = 4 * LIFT_TILE * LIFT_TS; // floats per stage (four planes)
+
+__global__ void __launch_bounds__(256)
+k_lift_gemm_tc(const float *__restrict__ p1re, const float *__restrict__ p1im, const float *__restrict__ p2re,
+               const float *__restrict__ p2im, int ld, int C, int kper, float2 *out)
+{
+    extern __shared__ float4 lift_sm[];
+    float *ring = reinterpret_cast<float *>(lift_sm);
+    const int a0 = blockIdx.y * LIFT_TILE, b0 = blockIdx.x * LIFT_TILE;
+    const int k_begin = blockIdx.z * kper, k_end = min(ld, k_begin + kper);
+    const int nchunk = (k_end - k_begin + LIFT_KC - 1) / LIFT_KC;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wm = warp & 3, wn = warp >> 2;
+    const int g = lane >> 2, t = lane & 3;
+    // one chunk = 4 planes x 64 rows x 32 floats = 2048 16-byte pieces, 8 per
+    // thread: piece q of thread t is plane q / 2, row ((q mod 2) 256 + t) / 8
+    auto issue = [&](int c, int stage) {
+        float *dst = ring + stage * LIFT_STAGE;
+        const int k0 = k_begin + c * LIFT_KC;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int plane = q >> 1, rem = ((q & 1) << 8) + (int)threadIdx.x, row = rem >> 3, piece = rem & 7;
+            const float *src = plane == 0 ? p1re + (long long)(a0 + row) * ld
+                             : plane == 1 ? p1im + (long long)(a0 + row) * ld
+                             : plane == 2 ? p2re + (long long)(b0 + row) * ld
+                                          : p2im + (long long)(b0 + row) * ld;
+            cp_async16(dst + plane * LIFT_TILE * LIFT_TS + row * LIFT_TS + piece * 4, src + k0 + piece * 4);
+        }
+        cp_async_commit();
+    };
+    float cre[4][4], cim[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) cre[j][q] = cim[j][q] = 0.f;
+    if (nchunk > 0) issue(0, 0);
+    for (int c = 0; c < nchunk; c++) {
+        if (c + 1 < nchunk) {
+            issue(c + 1, (c + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float *st = ring + (c & 1) * LIFT_STAGE;
+        const float *Are = st, *Aim = st + LIFT_TILE * LIFT_TS, *Bre = st + 2 * LIFT_TILE * LIFT_TS,
+                    *Bim = st + 3 * LIFT_TILE * LIFT_TS;
+#pragma unroll
+        for (int ks = 0; ks < LIFT_KC; ks += 8) {
+            const int r0 = 16 * wm + g;
+            unsigned arh[4], arl[4], aih[4], ail[4];
+            split_tf32(Are[r0 * LIFT_TS + ks + t], arh[0], arl[0]);
+            split_tf32(Are[(r0 + 8) * LIFT_TS + ks + t], arh[1], arl[1]);
+            split_tf32(Are[r0 * LIFT_TS + ks + t + 4], arh[2], arl[2]);
+            split_tf32(Are[(r0 + 8) * LIFT_TS + ks + t + 4], arh[3], arl[3]);
+            split_tf32(Aim[r0 * LIFT_TS + ks + t], aih[0], ail[0]);
+            split_tf32(Aim[(r0 + 8) * LIFT_TS + ks + t], aih[1], ail[1]);
+            split_tf32(Aim[r0 * LIFT_TS + ks + t + 4], aih[2], ail[2]);
+            split_tf32(Aim[(r0 + 8) * LIFT_TS + ks + t + 4], aih[3], ail[3]);
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++) {
+                const int col = 32 * wn + 8 * nt + g;
+                unsigned brh0, brl0, brh1, brl1, bih0, bil0, bih1, bil1;
+                split_tf32(Bre[col * LIFT_TS + ks + t], brh0, brl0);
+                split_tf32(Bre[col * LIFT_TS + ks + t + 4], brh1, brl1);
+                split_tf32(Bim[col * LIFT_TS + ks + t], bih0, bil0);
+                split_tf32(Bim[col * LIFT_TS + ks + t + 4], bih1, bil1);
+                const unsigned nih0 = bih0 ^ 0x80000000u, nil0 = bil0 ^ 0x80000000u; // -B_im (exact)
+                const unsigned nih1 = bih1 ^ 0x80000000u, nil1 = bil1 ^ 0x80000000u;
+                // a fresh accumulator per 8-knot step, added to the running sum with
+                // round-to-nearest adds (the tensor cores truncate when they accumulate)
+                float dre[4] = {0.f, 0.f, 0.f, 0.f}, dim[4] = {0.f, 0.f, 0.f, 0.f};
+                mma3(dre, arh, arl, brh0, brh1, brl0, brl1);
+                mma3(dre, aih, ail, nih0, nih1, nil0, nil1);
+                mma3(dim, arh, arl, bih0, bih1, bil0, bil1);
+                mma3(dim, aih, ail, brh0, brh1, brl0, brl1);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    cre[nt][q] += dre[q];
+                    cim[nt][q] += dim[q];
+                }
+            }
+        }
+        __syncthreads(); // the stage is refilled two chunks later
+    }
+    const int row = a0 + 16 * wm + g;
+#pragma unroll
+    for (int nt = 0; nt < 4; nt++) {
+        const int col = b0 + 32 * wn + 8 * nt + 2 * t;
+        atomicAdd(out + (long long)row * C + col, make_float2(cre[nt][0], cim[nt][0]));
+        atomicAdd(out + (long long)row * C + col + 1, make_float2(cre[nt][1], cim[nt][1]));
+        atomicAdd(out + (long long)(row + 8) * C + col, make_float2(cre[nt][2], cim[nt][2]));
+        atomicAdd(out + (long long)(row + 8) * C + col + 1, make_float2(cre[nt][3], cim[nt][3]));
+    }
+}
+
 // h[s][jx][jy][mz] = sign scale sum_eta rho^_A conj(rho^_B) cone^2 exp(2 pi i eta r_s / P_r),
 // zero on the lower-edge modes; scale = P^-3 P_r^-1, sign = (-1)^(m_x + m_y + m_z).
 __global__ void k_lift_collapse(const float2 *__restrict__ ra, const float2 *__restrict__ rb,
@@ -277,6 +484,7 @@ struct bc_lift_s {
     int device = 0, nsm = 1;
     cudaStream_t stream = nullptr;
     int N = 0, Nr = 0, qmax = 0;
+    int tensor_cores = 1;
     double L = 0, period = 2, period_r = 0;
     float2 *cone = nullptr, *tw = nullptr;
     void *ws = nullptr; // rho^_A, rho^_B, phase tables, h planes, slices, pair descriptors, staging
@@ -307,6 +515,7 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
     if (!(p->L > 0) || !std::isfinite(p->L)) return lift_fail(BC_ERR_ARG, "bc_lift_create: L must be > 0");
     if (!(p->period > 0) || !std::isfinite(p->period)) return lift_fail(BC_ERR_ARG, "bc_lift_create: period must be > 0");
     if (!(p->period_r > 0) || !std::isfinite(p->period_r)) return lift_fail(BC_ERR_ARG, "bc_lift_create: period_r must be > 0");
+    if (p->contraction != 0 && p->contraction != 1) return lift_fail(BC_ERR_ARG, "bc_lift_create: contraction must be 0 or 1");
     bc_lift_s *lf = new (std::nothrow) bc_lift_s();
     if (!lf) return lift_fail(BC_ERR_OOM, "bc_lift_create: host allocation");
     lf->stream = (cudaStream_t)cuda_stream;
@@ -315,6 +524,7 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
     lf->L = p->L;
     lf->period = p->period;
     lf->period_r = p->period_r;
+    lf->tensor_cores = p->contraction == 0 ? 0 : 1;
     lf->qmax = 3 * (p->N / 2) * (p->N / 2);
     cudaError_t e;
     double *g = nullptr;
@@ -373,7 +583,10 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
     const size_t M = (size_t)N * N, C = (size_t)H * Nr;
     const size_t rho_bytes = sizeof(float2) * M * C;
     const size_t nmax = (size_t)(nA > nB ? nA : nB);
-    const size_t e_bytes = sizeof(float2) * (size_t)T * (nmax > 0 ? nmax : 1);
+    const int ld = (int)((nmax + LIFT_KC - 1) / LIFT_KC) * LIFT_KC > 0 ? (int)((nmax + LIFT_KC - 1) / LIFT_KC) * LIFT_KC
+                                                                       : LIFT_KC;
+    const size_t e_bytes = lf->tensor_cores ? sizeof(float) * 2 * (M + C) * (size_t)ld + sizeof(LiftU) * (nmax + 1)
+                                            : sizeof(float2) * (size_t)T * (nmax > 0 ? nmax : 1);
     const size_t plane = (size_t)N * N * H;
     const size_t h_bytes = sizeof(float2) * plane * nslices;
     const size_t knot_bytes = on_device ? 0 : sizeof(float4) * (size_t)(nA + nB);
@@ -432,18 +645,29 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
         float2 *rho = side ? rhoB : rhoA;
         if ((e = cudaMemsetAsync(rho, 0, rho_bytes, st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: clear");
         if (n == 0) continue;
-        if (side == 0)
-            k_lift_phases<<<n, 64, 0, st>>>(kn, n, 1.0, 0.0, 0.0, 0.0, 0, N, Nr, lf->period, lf->period_r, E);
-        else
-            k_lift_phases<<<n, 64, 0, st>>>(kn, n, quat[0] * inv, quat[1] * inv, quat[2] * inv, quat[3] * inv, 1, N, Nr,
-                                            lf->period, lf->period_r, E);
+        const double qw = side ? quat[0] * inv : 1.0, qx = side ? quat[1] * inv : 0.0, qy = side ? quat[2] * inv : 0.0,
+                     qz = side ? quat[3] * inv : 0.0;
         // split the knots so that about four blocks per SM run
         const int ntile = (int)(tiles.x * tiles.y);
+        const int kn_len = lf->tensor_cores ? ld : n;
         int split = (4 * lf->nsm + ntile - 1) / ntile;
-        int kper = (n + split - 1) / split;
+        int kper = (kn_len + split - 1) / split;
         kper = ((kper + LIFT_KC - 1) / LIFT_KC) * LIFT_KC;
-        split = (n + kper - 1) / kper;
-        k_lift_ndft<<<dim3(tiles.x, tiles.y, split), 256, 0, st>>>(E, n, N, Nr, kper, rho);
+        split = (kn_len + kper - 1) / kper;
+        if (lf->tensor_cores) {
+            float *p1re = (float *)E, *p1im = p1re + M * (size_t)ld, *p2re = p1im + M * (size_t)ld,
+                  *p2im = p2re + C * (size_t)ld;
+            LiftU *u = (LiftU *)(p2im + C * (size_t)ld);
+            k_lift_scale<<<(n + 255) / 256, 256, 0, st>>>(kn, n, qw, qx, qy, qz, side, lf->period, lf->period_r, u);
+            k_lift_planes<<<dim3((ld + 255) / 256, (unsigned)(M + C)), 256, 0, st>>>(u, n, ld, N, Nr, p1re, p1im, p2re, p2im);
+            const size_t smem = sizeof(float) * 2 * LIFT_STAGE;
+            if ((e = cudaFuncSetAttribute(k_lift_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+                return lift_cuda(e, "bc_lift_correlate: shared memory");
+            k_lift_gemm_tc<<<dim3(tiles.x, tiles.y, split), 256, smem, st>>>(p1re, p1im, p2re, p2im, ld, (int)C, kper, rho);
+        } else {
+            k_lift_phases<<<n, 64, 0, st>>>(kn, n, qw, qx, qy, qz, side, N, Nr, lf->period, lf->period_r, E);
+            k_lift_ndft<<<dim3(tiles.x, tiles.y, split), 256, 0, st>>>(E, n, N, Nr, kper, rho);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: spectrum");
     }
     const float scale = (float)(1.0 / (lf->period * lf->period * lf->period * lf->period_r));

@@ -42,19 +42,20 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+@pytest.mark.parametrize("tc", [True, False], ids=["split-tf32-tensor-cores", "fp32-cuda-cores"])
 @pytest.mark.parametrize("N,Nr,nA,nB,slices", [(32, 32, 6, 6, (0.0, 0.03, -0.02)),
                                                  (32, 16, 2000, 1500, (0.0, 0.04)),
                                                  (64, 16, 800, 600, (0.0,))])
-def test_lifted_sections_match_oracle(bc, N, Nr, nA, nB, slices):
+def test_lifted_sections_match_oracle(bc, N, Nr, nA, nB, slices, tc):
     A = knots(synth.ellipsoid_shape(nA, 40 + nA), 1)
     B = knots(synth.torus_shape(nB, 41 + nB), 2)
     q = synth.shoemake_quaternions(synth.SplitMix64(42), 1)[0].astype(np.float32)
-    lf = bc.Lift(N, Nr, L, P, PR)
+    lf = bc.Lift(N, Nr, L, P, PR, tensor_cores=tc)
     got = lf.correlate(A, B, q, slices).double().cpu().numpy()
     ref = oracle(A, B, q, N, Nr, slices)
     for s, rs in enumerate(slices):
         e = rel(got[s], ref[s])
-        print(f"lifted N={N} Nr={Nr} {nA}+{nB} knots, section {rs}: rel-L2 {e:.3e}")
+        print(f"lifted N={N} Nr={Nr} {nA}+{nB} knots, tensor cores {tc}, section {rs}: rel-L2 {e:.3e}")
         assert e <= REL_TOL
     host = lf.correlate_host(A, B, q, slices)
     assert rel(host.astype(np.float64), got) < 1e-6  # split-knot partial sums add in another order
