@@ -24,7 +24,9 @@ def test_header_declares_the_boundary():
               "bc_last_error", "bc_version", "bc_profile_begin", "bc_profile_end", "bc_stage_name",
               "bc_shape_moments", "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
               "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep", "bc_mlp_param_count", "bc_topk", "bc_sweep_plan", "bc_plan_run",
-              "bc_plan_destroy"):
+              "bc_plan_destroy", "bc_score", "bc_score_sweep", "bc_query_create", "bc_query_eval", "bc_query_destroy",
+              "bc_lift_create", "bc_lift_correlate", "bc_lift_destroy", "bc_get_tuning", "bc_set_tuning", "bc_autotune",
+              "bc_correlate_noalloc"):
         assert f in names
 
 
@@ -77,3 +79,38 @@ def test_null_arguments_are_rejected():
     assert L.bc_mlp_create(None, 64, None, None) == 1
     assert L.bc_mlp_destroy(None) == 0
     assert bc.bc_mlp_param_count(256) == 256 * 132 + 256 + 256 * 256 + 256 + 256 + 1
+
+    # added entry points: null arguments fail before any device work
+    assert L.bc_score(None, None, None, None, 1, ctypes.c_double(0.1), ctypes.c_double(2.0), None, 1) == 1
+    assert L.bc_score_sweep(None, None, None, None, 1, 0, ctypes.c_double(0.1), ctypes.c_double(2.0), None, None, 1) == 1
+    assert L.bc_query_create(None, None, None, None, 10, None) == 1
+    assert L.bc_query_eval(None, None, 1, None, 1) == 1
+    assert L.bc_query_destroy(None) == 0
+    assert L.bc_lift_correlate(None, None, 0, None, 0, None, None, 1, None, 1) == 1
+    assert L.bc_lift_destroy(None) == 0
+    assert L.bc_get_tuning(None, None) == 1
+    assert L.bc_set_tuning(None, None) == 1
+    assert L.bc_autotune(None, None, None, 0, None) == 1
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(N=48, Nr=16, L=0.1), 5),
+    (dict(N=32, Nr=12, L=0.1), 5),
+    (dict(N=32, Nr=16, L=0.0), 1),
+    (dict(N=32, Nr=16, L=0.1, period=-1.0), 1),
+    (dict(N=32, Nr=16, L=0.1, period_r=0.0), 1),
+])
+def test_lift_create_rejects_bad_parameters_before_device_work(kw, status):
+    st, msg = _status(lambda: bc.bc_lift_create(**kw))
+    assert st == status, msg
+
+
+def test_tuning_struct_matches_the_header():
+    src = open(os.path.join(ROOT, "include", "ballcorr.h")).read()
+    body = re.search(r"typedef struct \{([^}]*)\} bc_tuning;", src).group(1)
+    fields = re.findall(r"int\s+(\w+);", body)
+    assert fields == [f for f, _ in bc.bc_tuning._fields_]
+    body = re.search(r"typedef struct \{([^}]*)\} bc_lift_params;", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"(?:int|double)\s+(\w+);", body)
+    assert fields == [f for f, _ in bc.bc_lift_params._fields_]
