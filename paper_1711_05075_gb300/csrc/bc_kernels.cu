@@ -371,8 +371,9 @@ cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *in
 // float2 of a contiguous 128-byte run.  Compact index iz sits at position
 // (pos0_z + iz) mod n of the length-n line; the rest of the line is zero.  The
 // first transform stage reads its inputs straight from the box (and the next
-// item's inputs are loaded while the current one finishes); every cell read is
-// then reset to zero so the boxes are clean for the next launch.
+// item's inputs are loaded while the current one finishes); once every thread
+// has consumed them the item's box rows (one contiguous run) are reset to zero
+// so the boxes are clean for the next launch.
 // Output rows: with Z = FFT(a + i b), A_k = (Z_k + conj Z_{n-k}) / 2,
 // B_k = (Z_k - conj Z_{n-k}) / (2i), for m_z = k in [0, N/2).
 template <int NF, bool SP, int S>
@@ -414,15 +415,12 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
             const int ix = rem / nyb, iy0 = (rem - ix * nyb) << 5;
             if constexpr (SP) in.scatter(S0);
             else rr_first<NF, Radix<NF, S>::r0, false, CL, TB>(in, S0);
+            __syncthreads(); // every thread has consumed its loads of this item
             {
-                float2 *base = G2 + (long long)it * bz * 16;
-                in.for_each([&](int c, int pos) {
-                    int iz = pos - pz;
-                    if (iz < 0) iz += NF;
-                    if (iz < bz) base[iz * 16 + c] = make_float2(0.f, 0.f);
-                });
+                // the item's box rows are one contiguous run of bz x 128 bytes
+                float4 *run = reinterpret_cast<float4 *>(G2 + (long long)it * bz * 16);
+                for (int e = threadIdx.x; e < bz * 8; e += TB) run[e] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            __syncthreads();
             if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
             auto sink = [&](int, int, int c, int pos, float2 v) { OUT[pos * CL + c] = v; };
             if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
