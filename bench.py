@@ -591,6 +591,7 @@ def run_learned(args):
     K, R = args.topk, args.eval_rot
     hits, hits_tol, rand_hits, regrets, test_mse = 0, 0, 0, [], []
     ms_ex, ms_learn = [], []
+    hits_ref, hits_ref_tol, ms_ref = 0, 0, []
     for seed in range(1001, 1001 + args.eval_pairs):
         A, B = pair(seed)
         hA, hB = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
@@ -621,6 +622,34 @@ def run_learned(args):
         hits_tol += top >= p[best] * (1 - 1e-3)
         rnd = set(np.argsort(synth.SplitMix64(seed + 400000).uniform(R))[:K].tolist())
         rand_hits += best in rnd
+        if args.refine > 0:
+            # two stages within the same K full correlations: the network's top K - refine, then
+            # the nearest rotations (largest |q . q'|) of the best peaks found, round robin
+            K1, K2 = K - args.refine, args.refine
+            e3, e4 = ev(), ev()
+            e3.record(stream)
+            i1, p1, _, _ = bc.learned_sweep(ctx, net, hA, hB, qd, K1)
+            seeds = i1[torch.argsort(p1, descending=True)[:args.refine_seeds]].long()
+            sim = (qd[seeds] @ qd.T).abs()
+            sim[:, i1.long()] = -1.0
+            order = torch.argsort(sim, dim=1, descending=True)  # [seeds, R]
+            cand = order.T.reshape(-1)  # round robin over the seeds
+            taken = torch.zeros(R, dtype=torch.bool, device=dev)
+            taken[i1.long()] = True
+            first = torch.zeros_like(cand, dtype=torch.bool)
+            u, inv = torch.unique(cand, return_inverse=True)
+            pos = torch.full((u.numel(),), cand.numel(), dtype=torch.long, device=dev)
+            pos.scatter_reduce_(0, inv, torch.arange(cand.numel(), device=dev), reduce="amin")
+            first[pos] = True
+            cand = cand[first & ~taken[cand]][:K2]
+            p2, _ = ctx.sweep(hA, hB, qd[cand].cpu().numpy(), batch=256)
+            e4.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_ref.append(e3.elapsed_time(e4))
+            chosen2 = set(i1.cpu().numpy().tolist()) | set(cand.cpu().numpy().tolist())
+            hits_ref += best in chosen2
+            top2 = max(float(p1.max()), float(p2.max()))
+            hits_ref_tol += top2 >= p[best] * (1 - 1e-3)
         hA.close()
         hB.close()
 
@@ -658,6 +687,10 @@ def run_learned(args):
         "learned_effective_poses_s": learned,
         "learned_vs_plain": learned / plain, "batched_vs_plain": batched / plain,
         "recall_best_in_topk": hits / args.eval_pairs,
+        "refine": {"correlations_on_neighbours": args.refine, "seeds": args.refine_seeds,
+                   "recall_best": hits_ref / args.eval_pairs, "recall_within_1e-3": hits_ref_tol / args.eval_pairs,
+                   "ms": float(np.mean(ms_ref)), "effective_poses_s": poses / (np.mean(ms_ref) * 1e-3)}
+        if args.refine > 0 else None,
         "recall_within_1e-3_of_best": hits_tol / args.eval_pairs,
         "random_topk_recall": rand_hits / args.eval_pairs,
         "mean_peak_ratio_topk_over_best": float(np.mean(regrets)),
@@ -710,6 +743,9 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--refine", type=int, default=0,
+                    help="of the top-k full correlations, spend this many on the nearest rotations of the best peaks")
+    ap.add_argument("--refine-seeds", type=int, default=8)
     ap.add_argument("--target-alpha", type=float, default=0.0,
                     help="train on exp(alpha (z - 3)) of the standardised peak z instead of z (0: z)")
     ap.add_argument("--augment", type=int, default=32,
