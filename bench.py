@@ -493,7 +493,7 @@ def run_lifted(args):
     A = knots(synth.ellipsoid_union_shape(args.lift_knots, 1), 11)
     B = knots(synth.torus_shape(args.lift_knots, 2), 12)
     q = synth.shoemake_quaternions(synth.SplitMix64(13), 1)[0]
-    lf = bc.Lift(N, Nr, L, 2.0, 4 * L, stream=stream, tensor_cores=not args.lift_cuda_cores)
+    lf = bc.Lift(N, Nr, L, 2.0, 4 * L, stream=stream, contraction=args.lift_contraction)
     for _ in range(args.warmup):
         lf.correlate(A, B, q)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -510,7 +510,9 @@ def run_lifted(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "lifted union-of-ellipsoids vs torus", "N": N, "Nr": Nr, "L": L, "period_r": 4 * L,
                        "knots": [args.lift_knots, args.lift_knots], "radii": "uniform [0.01, 0.09)"},
-            "contraction": "FP32 CUDA cores" if args.lift_cuda_cores else "split TF32 tensor cores (3 products)",
+            "contraction": {"tcgen05": "split TF32 (3 products), tcgen05.mma, tensor-memory accumulators",
+                            "mma": "split TF32 (3 products), legacy mma.sync",
+                            "cuda": "FP32 CUDA cores"}[args.lift_contraction],
             "ndft_tflops_lower_bound": flops / (ms * 1e-3) / 1e12,
             "note": "direct 4D NDFT; the contraction's rate is counted against the whole call's time"}
     print(json.dumps(line), flush=True)
@@ -730,7 +732,8 @@ def main():
     ap.add_argument("--lift-n", type=int, default=32)
     ap.add_argument("--lift-nr", type=int, default=16)
     ap.add_argument("--lift-knots", type=int, default=5000)
-    ap.add_argument("--lift-cuda-cores", action="store_true", help="FP32 CUDA-core contraction instead of split TF32")
+    ap.add_argument("--lift-contraction", choices=["tcgen05", "mma", "cuda"], default="tcgen05",
+                    help="lifted NDFT contraction: tcgen05 tensor cores (default), legacy mma.sync, FP32 CUDA cores")
     ap.add_argument("--r0", type=float, default=0.02, help="score offset radius")
     ap.add_argument("--lam", type=float, default=2.0, help="score penalty factor")
     ap.add_argument("--mprime", type=int, default=4096, help="modes kept by a query")

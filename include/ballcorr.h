@@ -225,7 +225,8 @@ bc_status bc_query_destroy(bc_query_t q);
  * ([s][kx][ky][kz]); A, B and out are device (on_device = 1) or host (0)
  * memory.  Synchronous.  Errors: BC_ERR_ARG (null pointer, counts out of
  * range, zero quaternion, non-finite section), BC_ERR_UNSUPPORTED (N not 32 or
- * 64, Nr not 8, 16, 32 or 64), BC_ERR_OOM, BC_ERR_CUDA. */
+ * 64, Nr not 8, 16, 32 or 64), BC_ERR_OOM, BC_ERR_CUDA, BC_ERR_TIMEOUT (a
+ * bounded wait inside the tcgen05 contraction expired; out is incomplete). */
 typedef struct bc_lift_s *bc_lift_t;
 typedef struct {
     int N;           /* modes per axis and translation grid N^3: 32 or 64 */
@@ -233,8 +234,11 @@ typedef struct {
     double L;        /* cone height */
     double period;   /* P, translation period */
     double period_r; /* P_r, period along the lifted axis */
-    int contraction; /* 4D NDFT contraction: 1 tensor cores, 3-pass split TF32 (FP32-level
-                        accuracy); 0 FP32 on the CUDA cores */
+    int contraction; /* 4D NDFT contraction, all at FP32-level accuracy:
+                        2 tcgen05.mma tensor cores (accumulators in tensor memory, operands
+                          staged by bulk copies), 3-pass split TF32;
+                        1 mma.sync tensor cores, 3-pass split TF32;
+                        0 FP32 on the CUDA cores */
 } bc_lift_params;
 bc_status bc_lift_create(const bc_lift_params *params, void *cuda_stream, bc_lift_t *out);
 bc_status bc_lift_correlate(bc_lift_t lift, const float *A, int nA, const float *B, int nB, const float *quat,

@@ -610,9 +610,13 @@ class Query:
             pass
 
 
-def bc_lift_create(N, Nr, L, period=2.0, period_r=None, stream=None, tensor_cores=True):
-    p = bc_lift_params(int(N), int(Nr), float(L), float(period), float(4 * L if period_r is None else period_r),
-                       1 if tensor_cores else 0)
+LIFT_CONTRACTIONS = {"tcgen05": 2, "mma": 1, "cuda": 0}
+
+
+def bc_lift_create(N, Nr, L, period=2.0, period_r=None, stream=None, contraction="tcgen05"):
+    """contraction: "tcgen05" (default), "mma" (legacy mma.sync) or "cuda" (FP32 CUDA cores), or 2 / 1 / 0."""
+    c = LIFT_CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
+    p = bc_lift_params(int(N), int(Nr), float(L), float(period), float(4 * L if period_r is None else period_r), c)
     h = ctypes.c_void_p()
     _check(lib().bc_lift_create(ctypes.byref(p), None if stream is None else ctypes.c_void_p(stream), ctypes.byref(h)))
     return h
@@ -630,7 +634,7 @@ def bc_lift_destroy(lf):
 class Lift:
     """Lifted (4D) nonequiradius correlation (Sec. 3.2) on the current CUDA device and stream."""
 
-    def __init__(self, N, Nr, L, period=2.0, period_r=None, stream=None, tensor_cores=True):
+    def __init__(self, N, Nr, L, period=2.0, period_r=None, stream=None, contraction="tcgen05"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")
@@ -640,7 +644,7 @@ class Lift:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = None
         self.handle = bc_lift_create(N, Nr, L, period, self.period_r, stream=self.stream.cuda_stream,
-                                     tensor_cores=tensor_cores)
+                                     contraction=contraction)
 
     def correlate(self, A, B, quat, slices=(0.0,)):
         """A, B: (n, 4) (x, y, z, r) float32 CUDA tensors or arrays; returns (len(slices), N, N, N) CUDA tensor."""

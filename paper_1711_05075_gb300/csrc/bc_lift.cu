@@ -25,11 +25,15 @@
 //                     factors: rows (xi_x, xi_y), columns (xi_z, eta), 64 x 64
 //                     output tiles, knots split across blocks (FP32 on the
 //                     CUDA cores, partial sums added with vector atomics);
-//   k_lift_scale,     the default path: the phase matrices written out as
-//   k_lift_planes     real / imaginary planes (rows (xi_x, xi_y) and
-//                     (xi_z, eta), knots contiguous), then
-//   k_lift_gemm_tc    their complex product on the tensor cores in 3-pass split
-//                     TF32 with cp.async double buffering;
+//   k_lift_scale      each knot's coordinates over the periods, rotated and
+//                     mirrored (FP64, and as 32-bit fixed-point fractions);
+//   k_lift_operands,  the default contraction (bc_umma.cuh): the phase matrices
+//   k_lift_gemm_umma  written as split-TF32 operand blocks in the tensor core's
+//                     shared-memory layout, then their complex product with
+//                     tcgen05.mma, accumulators in tensor memory;
+//   k_lift_planes,    the legacy tensor-core contraction: real / imaginary
+//   k_lift_gemm_tc    planes, then mma.sync in 3-pass split TF32 with cp.async
+//                     double buffering;
 //   k_lift_collapse   per translation mode and section r_s the sum over eta of
 //                     rho^_A conj(rho^_B) f^_D0^2 exp(2 pi i eta r_s / P_r), with
 //                     the P^-3 P_r^-1 scale and the grid-origin sign;
@@ -44,6 +48,7 @@
 
 #include "../../include/ballcorr.h"
 #include "bc_device.cuh"
+#include "bc_umma.cuh"
 
 namespace bc {
 
@@ -251,7 +256,7 @@ __device__ __forceinline__ void mma3(float (&d)[4], const unsigned (&ah)[4], con
 // coordinates (u = x / P etc., rotated and mirrored for B), then sincospi runs
 // in FP32 on the reduced value.
 __global__ void k_lift_scale(const float4 *__restrict__ knots, int n, double qw, double qx, double qy, double qz,
-                             int mirror, double period, double period_r, LiftU *u)
+                             int mirror, double period, double period_r, LiftU *u, LiftQ *fq)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -259,8 +264,10 @@ __global__ void k_lift_scale(const float4 *__restrict__ knots, int n, double qw,
     const double R00 = 1 - 2 * (qy * qy + qz * qz), R01 = 2 * (qx * qy - qw * qz), R02 = 2 * (qx * qz + qw * qy);
     const double R10 = 2 * (qx * qy + qw * qz), R11 = 1 - 2 * (qx * qx + qz * qz), R12 = 2 * (qy * qz - qw * qx);
     const double R20 = 2 * (qx * qz - qw * qy), R21 = 2 * (qy * qz + qw * qx), R22 = 1 - 2 * (qx * qx + qy * qy);
-    u[i] = LiftU{(R00 * c.x + R01 * c.y + R02 * c.z) / period, (R10 * c.x + R11 * c.y + R12 * c.z) / period,
-                 (R20 * c.x + R21 * c.y + R22 * c.z) / period, (mirror ? -(double)c.w : (double)c.w) / period_r};
+    const LiftU v{(R00 * c.x + R01 * c.y + R02 * c.z) / period, (R10 * c.x + R11 * c.y + R12 * c.z) / period,
+                  (R20 * c.x + R21 * c.y + R22 * c.z) / period, (mirror ? -(double)c.w : (double)c.w) / period_r};
+    if (u) u[i] = v;
+    if (fq) fq[i] = LiftQ{lift_fixed(v.x), lift_fixed(v.y), lift_fixed(v.z), lift_fixed(v.w)};
 }
 
 __global__ void k_lift_planes(const LiftU *__restrict__ u, int n, int ld, int N, int Nr, float *p1re, float *p1im,
@@ -484,7 +491,7 @@ struct bc_lift_s {
     int device = 0, nsm = 1;
     cudaStream_t stream = nullptr;
     int N = 0, Nr = 0, qmax = 0;
-    int tensor_cores = 1;
+    int contraction = 2;
     double L = 0, period = 2, period_r = 0;
     float2 *cone = nullptr, *tw = nullptr;
     void *ws = nullptr; // rho^_A, rho^_B, phase tables, h planes, slices, pair descriptors, staging
@@ -515,7 +522,7 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
     if (!(p->L > 0) || !std::isfinite(p->L)) return lift_fail(BC_ERR_ARG, "bc_lift_create: L must be > 0");
     if (!(p->period > 0) || !std::isfinite(p->period)) return lift_fail(BC_ERR_ARG, "bc_lift_create: period must be > 0");
     if (!(p->period_r > 0) || !std::isfinite(p->period_r)) return lift_fail(BC_ERR_ARG, "bc_lift_create: period_r must be > 0");
-    if (p->contraction != 0 && p->contraction != 1) return lift_fail(BC_ERR_ARG, "bc_lift_create: contraction must be 0 or 1");
+    if (p->contraction < 0 || p->contraction > 2) return lift_fail(BC_ERR_ARG, "bc_lift_create: contraction must be 0, 1 or 2");
     bc_lift_s *lf = new (std::nothrow) bc_lift_s();
     if (!lf) return lift_fail(BC_ERR_OOM, "bc_lift_create: host allocation");
     lf->stream = (cudaStream_t)cuda_stream;
@@ -524,7 +531,7 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
     lf->L = p->L;
     lf->period = p->period;
     lf->period_r = p->period_r;
-    lf->tensor_cores = p->contraction == 0 ? 0 : 1;
+    lf->contraction = p->contraction;
     lf->qmax = 3 * (p->N / 2) * (p->N / 2);
     cudaError_t e;
     double *g = nullptr;
@@ -585,15 +592,17 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
     const size_t nmax = (size_t)(nA > nB ? nA : nB);
     const int ld = (int)((nmax + LIFT_KC - 1) / LIFT_KC) * LIFT_KC > 0 ? (int)((nmax + LIFT_KC - 1) / LIFT_KC) * LIFT_KC
                                                                        : LIFT_KC;
-    const size_t e_bytes = lf->tensor_cores ? sizeof(float) * 2 * (M + C) * (size_t)ld + sizeof(LiftU) * (nmax + 1)
-                                            : sizeof(float2) * (size_t)T * (nmax > 0 ? nmax : 1);
+    // contraction 2: A blocks (hi, lo) 16 M ld bytes, B blocks 32 C ld bytes, fixed-point knots
+    const size_t e_bytes = lf->contraction == 2 ? (16 * M + 32 * C) * (size_t)ld + sizeof(LiftQ) * (nmax + 1)
+                         : lf->contraction == 1 ? sizeof(float) * 2 * (M + C) * (size_t)ld + sizeof(LiftU) * (nmax + 1)
+                                                : sizeof(float2) * (size_t)T * (nmax > 0 ? nmax : 1);
     const size_t plane = (size_t)N * N * H;
     const size_t h_bytes = sizeof(float2) * plane * nslices;
     const size_t knot_bytes = on_device ? 0 : sizeof(float4) * (size_t)(nA + nB);
     const size_t out_bytes = on_device ? 0 : sizeof(float) * (size_t)N * N * N * nslices;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t need = al(rho_bytes) * 2 + al(e_bytes) + al(h_bytes) + al(sizeof(float) * LIFT_MAX_SLICES) +
-                        al(sizeof(PairDesc) * LIFT_MAX_SLICES) + al(knot_bytes) + al(out_bytes);
+                        al(sizeof(PairDesc) * LIFT_MAX_SLICES) + al(sizeof(int)) + al(knot_bytes) + al(out_bytes);
     cudaStream_t st = lf->stream;
     cudaError_t e;
     if (need > lf->ws_bytes) {
@@ -619,6 +628,8 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
     w += al(sizeof(float) * LIFT_MAX_SLICES);
     PairDesc *dpairs = (PairDesc *)w;
     w += al(sizeof(PairDesc) * LIFT_MAX_SLICES);
+    int *derr = (int *)w;
+    w += al(sizeof(int));
     const float4 *kA = (const float4 *)A, *kB = (const float4 *)B;
     if (!on_device) {
         float4 *stage = (float4 *)w;
@@ -637,6 +648,7 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
     if ((e = cudaMemcpyAsync(dsl, slices, sizeof(float) * nslices, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(dpairs, pairs.data(), sizeof(PairDesc) * nslices, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return lift_cuda(e, "bc_lift_correlate: descriptors");
+    if ((e = cudaMemsetAsync(derr, 0, sizeof(int), st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: error word");
     // the two lifted spectra
     const dim3 tiles((unsigned)(C / LIFT_TILE), (unsigned)(M / LIFT_TILE));
     for (int side = 0; side < 2; side++) {
@@ -649,16 +661,30 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
                      qz = side ? quat[3] * inv : 0.0;
         // split the knots so that about four blocks per SM run
         const int ntile = (int)(tiles.x * tiles.y);
-        const int kn_len = lf->tensor_cores ? ld : n;
+        const int kn_len = lf->contraction == 1 ? ld : n;
         int split = (4 * lf->nsm + ntile - 1) / ntile;
         int kper = (kn_len + split - 1) / split;
         kper = ((kper + LIFT_KC - 1) / LIFT_KC) * LIFT_KC;
         split = (kn_len + kper - 1) / kper;
-        if (lf->tensor_cores) {
+        if (lf->contraction == 2) {
+            const int nkb = ld / LIFT_KC, mt = (int)(M / 128), ctn = (int)(C / 128);
+            // A hi / lo: mt x nkb x 2 blocks of 128 x 32 floats = 2 M ld floats each;
+            // B hi / lo: ctn x nkb x 2 blocks of 256 x 32 floats = 4 C ld floats each
+            float *ahi = (float *)E, *alo = ahi + 2 * M * (size_t)ld, *bhi = alo + 2 * M * (size_t)ld,
+                  *blo = bhi + 4 * C * (size_t)ld;
+            LiftQ *fq = (LiftQ *)(blo + 4 * C * (size_t)ld);
+            k_lift_scale<<<(n + 255) / 256, 256, 0, st>>>(kn, n, qw, qx, qy, qz, side, lf->period, lf->period_r, nullptr, fq);
+            k_lift_operands<<<dim3((ld + 255) / 256, (unsigned)(M + C)), 256, 0, st>>>(fq, n, nkb, N, Nr, ahi, alo, bhi, blo);
+            if ((e = cudaFuncSetAttribute(k_lift_gemm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_SMEM)) != cudaSuccess)
+                return lift_cuda(e, "bc_lift_correlate: shared memory");
+            const int ns = umma_nsplit(mt * ctn, nkb, lf->nsm), units = mt * ctn * ns;
+            k_lift_gemm_umma<<<units < lf->nsm ? units : lf->nsm, UMMA_THREADS, UMMA_SMEM, st>>>(ahi, alo, bhi, blo, nkb, mt,
+                                                                                               ctn, ns, (int)C, rho, derr);
+        } else if (lf->contraction == 1) {
             float *p1re = (float *)E, *p1im = p1re + M * (size_t)ld, *p2re = p1im + M * (size_t)ld,
                   *p2im = p2re + C * (size_t)ld;
             LiftU *u = (LiftU *)(p2im + C * (size_t)ld);
-            k_lift_scale<<<(n + 255) / 256, 256, 0, st>>>(kn, n, qw, qx, qy, qz, side, lf->period, lf->period_r, u);
+            k_lift_scale<<<(n + 255) / 256, 256, 0, st>>>(kn, n, qw, qx, qy, qz, side, lf->period, lf->period_r, u, nullptr);
             k_lift_planes<<<dim3((ld + 255) / 256, (unsigned)(M + C)), 256, 0, st>>>(u, n, ld, N, Nr, p1re, p1im, p2re, p2im);
             const size_t smem = sizeof(float) * 2 * LIFT_STAGE;
             if ((e = cudaFuncSetAttribute(k_lift_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
@@ -690,6 +716,11 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
             return lift_cuda(e, "bc_lift_correlate: copy out");
     }
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: sync");
+    int herr = 0;
+    if ((e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return lift_cuda(e, "bc_lift_correlate: error word");
+    if (herr) return lift_fail(BC_ERR_TIMEOUT, "bc_lift_correlate: tensor-core contraction stalled (stage " +
+                                                   std::to_string(herr) + "); the spectrum is incomplete");
     return BC_OK;
 }
 

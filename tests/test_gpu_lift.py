@@ -42,20 +42,23 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("tc", [True, False], ids=["split-tf32-tensor-cores", "fp32-cuda-cores"])
+# tcgen05: tcgen05.mma with tensor-memory accumulators; mma: legacy mma.sync; both
+# 3-pass split TF32.  cuda: FP32 on the CUDA cores.
+@pytest.mark.parametrize("contraction", ["tcgen05", "mma", "cuda"])
 @pytest.mark.parametrize("N,Nr,nA,nB,slices", [(32, 32, 6, 6, (0.0, 0.03, -0.02)),
                                                  (32, 16, 2000, 1500, (0.0, 0.04)),
+                                                 (32, 8, 12000, 7000, (0.0, 0.05)),
                                                  (64, 16, 800, 600, (0.0,))])
-def test_lifted_sections_match_oracle(bc, N, Nr, nA, nB, slices, tc):
+def test_lifted_sections_match_oracle(bc, N, Nr, nA, nB, slices, contraction):
     A = knots(synth.ellipsoid_shape(nA, 40 + nA), 1)
     B = knots(synth.torus_shape(nB, 41 + nB), 2)
     q = synth.shoemake_quaternions(synth.SplitMix64(42), 1)[0].astype(np.float32)
-    lf = bc.Lift(N, Nr, L, P, PR, tensor_cores=tc)
+    lf = bc.Lift(N, Nr, L, P, PR, contraction=contraction)
     got = lf.correlate(A, B, q, slices).double().cpu().numpy()
     ref = oracle(A, B, q, N, Nr, slices)
     for s, rs in enumerate(slices):
         e = rel(got[s], ref[s])
-        print(f"lifted N={N} Nr={Nr} {nA}+{nB} knots, tensor cores {tc}, section {rs}: rel-L2 {e:.3e}")
+        print(f"lifted N={N} Nr={Nr} {nA}+{nB} knots, contraction {contraction}, section {rs}: rel-L2 {e:.3e}")
         assert e <= REL_TOL
     host = lf.correlate_host(A, B, q, slices)
     assert rel(host.astype(np.float64), got) < 1e-6  # split-knot partial sums add in another order
@@ -72,6 +75,9 @@ def test_lifted_arguments(bc):
         lf.correlate(A, A, np.zeros(4, np.float32))
     with pytest.raises(bc.BallCorrError):
         lf.correlate(A, A, synth.IDENTITY_QUAT[0], slices=np.zeros(17))
+    with pytest.raises(bc.BallCorrError) as e:
+        bc.Lift(32, 8, L, contraction=3)
+    assert e.value.status == 1
     # empty shapes give zero
     z = lf.correlate(np.zeros((0, 4), np.float32), A, synth.IDENTITY_QUAT[0])
     assert float(z.abs().max()) == 0.0
