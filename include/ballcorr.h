@@ -270,9 +270,19 @@ bc_status bc_lift_destroy(bc_lift_t lift);
  *                recorded on its first run (one graph launch instead of the
  *                kernel launches); 0: always launch kernel by kernel.  Passes
  *                recorded by bc_profile_begin always launch kernel by kernel.
- * A new context starts with {0, 64, 1, 0}.  Plans keep the choices in force when
+ *   z_transform  with spread 0: 0 the z pass is the radix FFT above; 1 it is a
+ *                pruned DFT on the 5th-generation tensor cores: each z line's
+ *                bz box cells times the fixed n-point DFT matrix restricted to
+ *                m_z in [0, N/2) (tcgen05.mma, 3-pass split TF32, FP32
+ *                accumulation restarted every 32 cells), then the phase of the
+ *                box origin.  Same transform, other rounding order.  Available
+ *                in FP32 contexts with N <= 128 (BC_ERR_UNSUPPORTED otherwise);
+ *                a stalled tensor-core wait is reported by bc_sync as
+ *                BC_ERR_TIMEOUT.
+ * A new context starts with {0, 64, 1, 0, 1} (z_transform 0 where 1 is not
+ * available).  Plans keep the choices in force when
  * they were made.  bc_autotune times the candidates on the given shapes --
- * bc_correlate of A with B (identity) for `spread`; in FP32 contexts the
+ * bc_correlate of A with B (identity) for `spread` and then `z_transform`; in FP32 contexts the
  * per-stage times of profiled correlations under each schedule, pass by pass,
  * for `fft_schedule`; when rotations > 0, a sweep of that many fixed rotations
  * of B for each sweep_batch in {16, 32, 64, 128, 256} not above it -- keeps
@@ -287,6 +297,7 @@ typedef struct {
     int sweep_batch;
     int graphs;
     int fft_schedule;
+    int z_transform;
 } bc_tuning;
 bc_status bc_get_tuning(bc_ctx_t ctx, bc_tuning *out);
 bc_status bc_set_tuning(bc_ctx_t ctx, const bc_tuning *t);

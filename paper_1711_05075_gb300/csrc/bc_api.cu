@@ -130,6 +130,8 @@ struct bc_ctx_s {
     int spread_mode = 0;  // 0: spreading boxes in HBM (k_spread + k_fft_z); 1: binned, fused into the z pass
     int sweep_batch = 64; // rotations per pass when a sweep's batch argument is 0
     int fft_sched = 0;    // alternative radix schedule per forward FP32 pass: bit 0 z, bit 1 y, bit 2 x
+    int z_tc = 0;         // z pass as a DFT product on the tensor cores (spread 0; needs zdft)
+    float *zdft = nullptr; // its 32-cell DFT block, split TF32 (hi, then lo), FP32 contexts with N <= 128
     // workspaces
     Workspace ws;                 // pipeline workspaces of direct calls
     DevBuf outbuf, stats, learn, tune; // host-output staging, shape checks, learned-sweep and tuning scratch
@@ -317,6 +319,12 @@ bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
             return bail(e, "copy radii");
         if ((e = launch_build_tables(g, beta, p->period, c->radii_dev, c->deconv, c->ballft, c->tw_n, c->tw_N, c->consts, c->stream)) != cudaSuccess)
             return bail(e, "build tables");
+        if (g.prec == 0 && g.n == 2 * g.N && supported_z_umma(g.N)) {
+            const size_t half = (size_t)(g.n / 2) * 32;
+            if ((e = cudaMalloc(&c->zdft, sizeof(float) * 2 * half)) != cudaSuccess) return bail(e, "cudaMalloc zdft");
+            if ((e = launch_build_zdft(g.n, c->zdft, c->zdft + half, c->stream)) != cudaSuccess) return bail(e, "build zdft");
+            c->z_tc = 1;
+        }
         if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return bail(e, "bc_create sync");
         *out = c;
         return BC_OK;
@@ -338,6 +346,7 @@ bc_status bc_destroy(bc_ctx_t c)
         cudaFree(c->err_dev);
         cudaFree(c->consts);
         cudaFree(c->modes);
+        cudaFree(c->zdft);
         prof_free(c);
         for (bc_shape_s *s : c->shapes) {
             if (s->knots) cudaFree(s->knots);
@@ -457,6 +466,8 @@ bc_status bc_sync(bc_ctx_t c)
     if (herr) {
         CK(cudaMemset(c->err_dev, 0, sizeof(int)));
         if (herr & 4) return fail(BC_ERR_ARG, "a device-resident rotation had zero norm");
+        if (herr & 8)
+            return fail(BC_ERR_TIMEOUT, "the tensor-core z transform stalled (a bounded wait expired); results are incomplete");
         return fail(BC_ERR_INTERNAL, "device-side check failed (support box exceeded its capacity)");
     }
     return BC_OK;
@@ -544,6 +555,7 @@ struct Job {
     bool cache_first = false;
     int mode = 0;  // spreading: 0 boxes in HBM, 1 binned (fused into the z pass)
     int sched = 0; // radix schedule of the forward passes
+    int ztc = 0;   // z pass on the tensor cores (mode 0 only)
     Weights w;
     int nmain = 0, koff = 0, max_knots = 0;
     long long goff = 0, zoff = 0, yoff = 0, hpairs = 0;
@@ -559,6 +571,7 @@ static Job plan_job(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std
     j.cache_first = cache_first;
     j.mode = c->spread_mode;
     j.sched = c->fft_sched;
+    j.ztc = c->z_tc && c->spread_mode == 0 ? 1 : 0;
     j.nmain = (int)pairs.size() - (cache_first ? 1 : 0);
     j.inst.resize(shapes.size());
     for (size_t i = 0; i < shapes.size(); i++) {
@@ -694,8 +707,14 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
                                      (float2 *)ws.z1.p, c->nsm, st)) != cudaSuccess)
             return cuda_fail(e, "fft z (binned)");
     } else {
-        if ((e = launch_fft_z(g, t, dinst, ninst, dplan, (float *)ws.grid.p, (float2 *)ws.z1.p, c->nsm, st)) != cudaSuccess)
+        if (job.ztc) {
+            const size_t half = (size_t)(g.n / 2) * 32;
+            if ((e = launch_fft_z_umma(g, t, dinst, ninst, dplan, (float *)ws.grid.p, (float2 *)ws.z1.p, c->zdft,
+                                       c->zdft + half, c->err_dev, c->nsm, st)) != cudaSuccess)
+                return cuda_fail(e, "fft z (tensor cores)");
+        } else if ((e = launch_fft_z(g, t, dinst, ninst, dplan, (float *)ws.grid.p, (float2 *)ws.z1.p, c->nsm, st)) != cudaSuccess) {
             return cuda_fail(e, "fft z");
+        }
         ws.grid_dirty = false;
     }
     launches++;
@@ -778,7 +797,7 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
     auto add = [&](const void *v, size_t n) { key.insert(key.end(), (const char *)v, (const char *)v + n); };
     const long long sig[] = {(long long)job.inst.size(), (long long)job.pairs.size(), (long long)job.nmain,
                              (long long)job.cache_first, (long long)job.koff, (long long)job.max_knots,
-                             (long long)job.mode, (long long)job.sched};
+                             (long long)job.mode, (long long)job.sched, (long long)job.ztc};
     add(sig, sizeof(sig));
     const void *ptrs[] = {dout, keys, job.w.ballft, ws.ku.p, ws.plan.p, ws.inst.p, ws.pairs.p, ws.grid.p, ws.z1.p, ws.y1.p,
                           ws.h.p, ws.fa.p, ws.boxes.p, ws.cnt.p, ws.cur.p, ws.rec.p, c->stream};
@@ -1252,6 +1271,7 @@ bc_status bc_get_tuning(bc_ctx_t c, bc_tuning *out)
     out->sweep_batch = c->sweep_batch;
     out->graphs = c->replay ? 1 : 0;
     out->fft_schedule = c->fft_sched;
+    out->z_transform = c->z_tc;
     return BC_OK;
 }
 
@@ -1262,6 +1282,10 @@ bc_status bc_set_tuning(bc_ctx_t c, const bc_tuning *t)
     if (t->sweep_batch < 1 || t->sweep_batch > 65534) return fail(BC_ERR_ARG, "bc_set_tuning: sweep_batch must be in [1, 65534]");
     if (t->graphs != 0 && t->graphs != 1) return fail(BC_ERR_ARG, "bc_set_tuning: graphs must be 0 or 1");
     if (t->fft_schedule < 0 || t->fft_schedule > 7) return fail(BC_ERR_ARG, "bc_set_tuning: fft_schedule must be in [0, 7]");
+    if (t->z_transform != 0 && t->z_transform != 1) return fail(BC_ERR_ARG, "bc_set_tuning: z_transform must be 0 or 1");
+    if (t->z_transform == 1 && !c->zdft)
+        return fail(BC_ERR_UNSUPPORTED, "bc_set_tuning: the tensor-core z transform needs an FP32 context with N <= 128");
+    c->z_tc = t->z_transform;
     c->fft_sched = t->fft_schedule;
     c->spread_mode = t->spread;
     c->sweep_batch = t->sweep_batch;
@@ -1338,6 +1362,20 @@ bc_status bc_autotune(bc_ctx_t c, bc_shape_t A, bc_shape_t B, int rotations, bc_
             }
         }
         c->spread_mode = best_mode;
+        // z transform: FFT or tensor-core DFT product (spread 0 only)
+        if (c->zdft && c->spread_mode == 0) {
+            const int saved = c->z_tc;
+            float tz[2] = {0.f, 0.f};
+            for (int z = 0; z <= 1; z++) {
+                c->z_tc = z;
+                bc_status s = time_median(c, [&]() { return bc_correlate(c, A, B, ident, 1, dout, 1); }, 3, 7, &tz[z]);
+                if (s != BC_OK) {
+                    c->z_tc = saved;
+                    return s;
+                }
+            }
+            c->z_tc = tz[1] < tz[0] ? 1 : 0;
+        }
         // radix schedule per forward pass (the split-precision passes have their own):
         // the stage times of profiled correlations under each schedule, pass by pass
         if (c->g.prec == 0) {

@@ -94,6 +94,15 @@ cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *in
                           const float4 *ku, const InstPlan *plan, float *grid, cudaStream_t s);
 cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
                          const InstPlan *plan, float *grid, float2 *z1, int nsm, cudaStream_t s);
+// The z pass as split-TF32 DFT products on the tensor cores (bc_zumma.cu),
+// N in {32, 64, 96, 128} with n = 2N: same output as launch_fft_z, boxes left
+// cleared; a stalled wait sets bit 8 of *err.  bhi / blo: the 32-cell DFT block
+// from launch_build_zdft (n/2 x 32 floats each).
+bool supported_z_umma(int N);
+cudaError_t launch_build_zdft(int n, float *bhi, float *blo, cudaStream_t s);
+cudaError_t launch_fft_z_umma(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
+                              const InstPlan *plan, float *grid, float2 *z1, const float *bhi, const float *blo,
+                              int *err, int nsm, cudaStream_t s);
 cudaError_t launch_fft_y(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
                          const InstPlan *plan, const float2 *z1, float2 *y1, int nsm, cudaStream_t s);
 cudaError_t launch_fft_x(const Geometry &g, const Tables &t, const InstDesc *inst, const InstPlan *plan,

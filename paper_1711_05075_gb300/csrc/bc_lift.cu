@@ -27,7 +27,7 @@
 //                     CUDA cores, partial sums added with vector atomics);
 //   k_lift_scale      each knot's coordinates over the periods, rotated and
 //                     mirrored (FP64, and as 32-bit fixed-point fractions);
-//   k_lift_operands,  the default contraction (bc_umma.cuh): the phase matrices
+//   k_lift_operands,  the default contraction (bc_lift_umma.cuh): the phase matrices
 //   k_lift_gemm_umma  written as split-TF32 operand blocks in the tensor core's
 //                     shared-memory layout, then their complex product with
 //                     tcgen05.mma, accumulators in tensor memory;
@@ -48,7 +48,7 @@
 
 #include "../../include/ballcorr.h"
 #include "bc_device.cuh"
-#include "bc_umma.cuh"
+#include "bc_lift_umma.cuh"
 
 namespace bc {
 
@@ -719,8 +719,9 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
     int herr = 0;
     if ((e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
         return lift_cuda(e, "bc_lift_correlate: error word");
-    if (herr) return lift_fail(BC_ERR_TIMEOUT, "bc_lift_correlate: tensor-core contraction stalled (stage " +
-                                                   std::to_string(herr) + "); the spectrum is incomplete");
+    if (herr) return lift_fail(BC_ERR_TIMEOUT, "bc_lift_correlate: tensor-core contraction stalled (waits " +
+                                                   std::to_string(herr) + ": 1 copy, 2 accumulator, 4 stage, 8 drain); "
+                                                   "the spectrum is incomplete");
     return BC_OK;
 }
 

@@ -6,7 +6,8 @@ Bar: rel-L2 <= 1e-5 over the compared points (FP32 path), as the method's
 accuracy target states; max-abs is reported beside it.  Every workload runs
 with both spreading implementations (spread 0: boxes in HBM with global
 atomics; spread 1: knots binned by x-cell and spread in shared memory inside
-the z transform).
+the z transform), and spread 0 with both z transforms (the radix FFT, and the
+pruned DFT product on the tcgen05 tensor cores where N <= 128).
 """
 import math
 
@@ -40,13 +41,15 @@ def f32(shape):
 
 
 SPREADS = (0, 1)
+# (spread, z_transform): boxes + radix FFT z pass, boxes + tensor-core z pass, binned
+MODES = ((0, 0), (0, 1), (1, 0))
 
 
-def run_gpu(A, B, quats, N, W, radii=None, period=2.0, spread=1, fft_schedule=0):
+def run_gpu(A, B, quats, N, W, radii=None, period=2.0, spread=1, fft_schedule=0, z_transform=0):
     bc = bcmod()
     radii = A.radii if radii is None else radii
     ctx = bc.Context(N, W, radii, period)
-    ctx.set_tuning(spread=spread, fft_schedule=fft_schedule)
+    ctx.set_tuning(spread=spread, fft_schedule=fft_schedule, z_transform=z_transform)
     try:
         sa = ctx.shape(A.xyz.astype(np.float32), A.level)
         sb = ctx.shape(B.xyz.astype(np.float32), B.level)
@@ -60,10 +63,12 @@ def run_gpu(A, B, quats, N, W, radii=None, period=2.0, spread=1, fft_schedule=0)
     return out
 
 
-def run_modes(*args, **kw):
-    """(spread, grids) for each spreading implementation."""
-    for sp in SPREADS:
-        yield sp, run_gpu(*args, spread=sp, **kw)
+def run_modes(A, B, quats, N, W, **kw):
+    """(label, grids) for each implementation: spreading 0 with each z transform, spreading 1."""
+    for sp, zt in MODES:
+        if zt and N > 128:
+            continue
+        yield f"{sp}{' z-tc' if zt else ''}", run_gpu(A, B, quats, N, W, spread=sp, z_transform=zt, **kw)
 
 
 def oracle_grid(A, B, q, N, period=2.0):
@@ -135,14 +140,14 @@ def test_grid_size_256_sampled():
 
 
 # ------------------------------------------------------------------ edge cases
-@pytest.mark.parametrize("spread", SPREADS)
-def test_repeated_calls_are_identical(spread):
+@pytest.mark.parametrize("spread,zt", MODES)
+def test_repeated_calls_are_identical(spread, zt):
     # The spreading boxes (bin counts) are cleared by the pass that consumes
     # them; a second call on the same context must not see the first call's.
     bc = bcmod()
     wl = synth.small_pair(2)
     ctx = bc.Context(wl.N, wl.W, wl.radii)
-    ctx.set_tuning(spread=spread)
+    ctx.set_tuning(spread=spread, z_transform=zt)
     sa = ctx.shape(wl.A.xyz, wl.A.level)
     sb = ctx.shape(wl.B.xyz, wl.B.level)
     g1 = ctx.correlate(sa, sb, wl.quats).clone()
@@ -267,11 +272,11 @@ def test_spreading_modes_agree_on_a_dense_shape_and_switch_on_one_context():
     sa = ctx.shape(A.xyz.astype(np.float32), A.level)
     sb = ctx.shape(B.xyz.astype(np.float32), B.level)
     outs = []
-    for sp in (1, 0, 1):
-        ctx.set_tuning(spread=sp)
+    for sp, zt in ((1, 0), (0, 0), (0, 1), (1, 0)):
+        ctx.set_tuning(spread=sp, z_transform=zt)
         outs.append(ctx.correlate(sa, sb, q).double().cpu().numpy()[0])
-        check(outs[-1], ref, what=f"dense cube, spread {sp}")
-    assert rel_l2(outs[2], outs[0]) < 1e-6
+        check(outs[-1], ref, what=f"dense cube, spread {sp}, z transform {zt}")
+    assert rel_l2(outs[3], outs[0]) < 1e-6
     sa.close(); sb.close(); ctx.close()
 
 
@@ -283,7 +288,7 @@ def test_autotune_keeps_a_valid_choice():
     sb = ctx.shape(wl.B.xyz, wl.B.level)
     t = ctx.autotune(sa, sb, rotations=40)
     assert t == ctx.tuning and t["spread"] in (0, 1) and t["sweep_batch"] in (16, 32, 64) and t["graphs"] == 1
-    assert 0 <= t["fft_schedule"] <= 7
+    assert 0 <= t["fft_schedule"] <= 7 and t["z_transform"] in (0, 1)
     got = ctx.correlate(sa, sb, wl.quats).double().cpu().numpy()[0]
     check(got, oracle_grid(wl.A, wl.B, wl.quats[0], wl.N), what=f"after autotune {t}")
     with pytest.raises(bc.BallCorrError):
@@ -293,8 +298,8 @@ def test_autotune_keeps_a_valid_choice():
     sa.close(); sb.close(); ctx.close()
 
 
-@pytest.mark.parametrize("spread", SPREADS)
-def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread):
+@pytest.mark.parametrize("spread,zt", MODES)
+def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread, zt):
     # Identical passes (same descriptors and buffers) replay the recorded graph;
     # a changed rotation re-records; switching replay off launches kernel by kernel.
     bc = bcmod()
@@ -302,7 +307,7 @@ def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread):
     q = synth.shoemake_quaternions(synth.SplitMix64(31), 2).astype(np.float32)
     refs = [oracle_grid(wl.A, wl.B, q[r], wl.N) for r in range(2)]
     ctx = bc.Context(wl.N, wl.W, wl.radii)
-    ctx.set_tuning(spread=spread, graphs=1)
+    ctx.set_tuning(spread=spread, graphs=1, z_transform=zt)
     sa = ctx.shape(wl.A.xyz, wl.A.level)
     sb = ctx.shape(wl.B.xyz, wl.B.level)
     out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device="cuda")
@@ -314,6 +319,28 @@ def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread):
     ctx.correlate(sa, sb, q[1:2], out)
     check(out.double().cpu().numpy()[0], refs[1], what=f"kernel by kernel, spread {spread}")
     sa.close(); sb.close(); ctx.close()
+
+
+def test_z_transform_availability():
+    # the tensor-core z transform: FP32 contexts with N <= 128 start with it;
+    # elsewhere selecting it is refused (BC_ERR_UNSUPPORTED = 5)
+    bc = bcmod()
+    ctx = bc.Context(128, 8, synth.RADII_4)
+    assert ctx.tuning["z_transform"] == 1
+    ctx.set_tuning(z_transform=0)
+    assert ctx.tuning["z_transform"] == 0
+    with pytest.raises(bc.BallCorrError):
+        ctx.set_tuning(z_transform=2)
+    ctx.close()
+    ctx = bc.Context(256, 8, synth.RADII_4)
+    assert ctx.tuning["z_transform"] == 0
+    with pytest.raises(bc.BallCorrError) as e:
+        ctx.set_tuning(z_transform=1)
+    assert e.value.status == 5
+    ctx.close()
+    ctx = bc.Context(32, 8, synth.RADII_4, precision=1)
+    assert ctx.tuning["z_transform"] == 0
+    ctx.close()
 
 
 @pytest.mark.parametrize("N,W,n", [(32, 8, 300), (64, 8, 400), (96, 8, 500), (128, 8, 300)])
