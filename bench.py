@@ -50,14 +50,15 @@ L2_FLUSH_BYTES = 256 << 20
 # was measured on are unchanged (sha256 over KERNEL_SOURCES, first 16 hex
 # digits).
 NCU_TRAFFIC = {
-    "k_spread": {"bytes": 1.84e+07, "kernel_hash": "839bf8668eb3e865", "source": "profiles/ncu_full_scale_pair_N128.md"},
-    "k_fft_z": {"bytes": 7.333e+07, "kernel_hash": "839bf8668eb3e865", "source": "profiles/ncu_full_scale_pair_N128.md"},
-    "k_fft_y": {"bytes": 9.447e+07, "kernel_hash": "839bf8668eb3e865", "source": "profiles/ncu_full_scale_pair_N128.md"},
-    "k_fft_x": {"bytes": 7.393e+07, "kernel_hash": "839bf8668eb3e865", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_spread": {"bytes": 1.838e+07, "kernel_hash": "5b7b4c0dccc238cf", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_fft_z_umma": {"bytes": 7.870e+07, "kernel_hash": "5b7b4c0dccc238cf", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_fft_y": {"bytes": 9.425e+07, "kernel_hash": "5b7b4c0dccc238cf", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_fft_x": {"bytes": 7.372e+07, "kernel_hash": "5b7b4c0dccc238cf", "source": "profiles/ncu_full_scale_pair_N128.md"},
 }
 
 
-KERNEL_SOURCES = ("bc_kernels.cu", "bc_binned.cu", "bc_query.cu", "bc_fft.cuh", "bc_device.cuh", "bc_internal.h")
+KERNEL_SOURCES = ("bc_kernels.cu", "bc_binned.cu", "bc_query.cu", "bc_zumma.cu", "bc_fft.cuh", "bc_device.cuh",
+                  "bc_umma.cuh", "bc_internal.h")
 
 
 def kernel_source_hash():
@@ -329,7 +330,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = dom["bytes"] / (dom_ms * 1e-3) / 1e9 if dom_ms > 0 else 0.0
     binned = tuning["spread"] == 1
     kname = {"prepare": "k_prepare", "spread": "k_bin" if binned else "k_spread",
-             "fft_z": "k_fft_z_binned" if binned else "k_fft_z", "fft_y": "k_fft_y",
+             "fft_z": "k_fft_z_binned" if binned else ("k_fft_z_umma" if tuning.get("z_transform") else "k_fft_z"),
+             "fft_y": "k_fft_y",
              "fft_x": "k_fft_x", "ifft_y": "k_ifft_y", "ifft_z": "k_ifft_z"}[dom["name"]]
     tr = NCU_TRAFFIC.get(kname)
     traffic = tr["bytes"] if tr and tr.get("kernel_hash") == kernel_source_hash() else None

@@ -282,7 +282,8 @@ bc_status bc_lift_destroy(bc_lift_t lift);
  * A new context starts with {0, 64, 1, 0, 1} (z_transform 0 where 1 is not
  * available).  Plans keep the choices in force when
  * they were made.  bc_autotune times the candidates on the given shapes --
- * bc_correlate of A with B (identity) for `spread` and then `z_transform`; in FP32 contexts the
+ * bc_correlate of A with B (identity) for `spread` and then `z_transform` (when rotations > 0,
+ * `z_transform` is decided again on the sweep with the chosen batch); in FP32 contexts the
  * per-stage times of profiled correlations under each schedule, pass by pass,
  * for `fft_schedule`; when rotations > 0, a sweep of that many fixed rotations
  * of B for each sweep_batch in {16, 32, 64, 128, 256} not above it -- keeps

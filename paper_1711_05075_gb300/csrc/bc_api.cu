@@ -1432,6 +1432,23 @@ bc_status bc_autotune(bc_ctx_t c, bc_shape_t A, bc_shape_t B, int rotations, bc_
                 }
             }
             c->sweep_batch = best_batch;
+            // the z transform again, on the sweep itself (its passes batch many
+            // rotations of the smaller shape, which can favour the other transform)
+            if (c->zdft && c->spread_mode == 0) {
+                const int saved = c->z_tc;
+                float tz[2] = {0.f, 0.f};
+                for (int z = 0; z <= 1; z++) {
+                    c->z_tc = z;
+                    bc_status s = time_median(
+                        c, [&]() { return sweep_impl(c, A, B, q.data(), nullptr, rotations, best_batch, dpeak, darg, 1); },
+                        1, 3, &tz[z]);
+                    if (s != BC_OK) {
+                        c->z_tc = saved;
+                        return s;
+                    }
+                }
+                c->z_tc = tz[1] < tz[0] ? 1 : 0;
+            }
         }
         if (out) bc_get_tuning(c, out);
         return BC_OK;
