@@ -33,11 +33,13 @@
 //   warps 6-13       one line and half of the modes each (tensor-memory lanes
 //                    32 (w mod 4) .., columns of half (w - 6) / 4): add each
 //                    chunk's accumulator, turned by its phase, into FP32 running
-//                    sums; after the tile's last chunk the warp's 32 half lines
-//                    go out through a shared-memory staging area in 64-byte
-//                    row pieces, 8 lines x 64 contiguous bytes per store
-//                    instruction (a line per thread would scatter every store
-//                    over 32 half-filled sectors).
+//                    sums; after the tile's last chunk the sums are parked in a
+//                    third tensor-memory region and written out one 64-byte
+//                    row piece per pass after each chunk of the next tile (the
+//                    whole tile at once stalled the next tile's first chunk),
+//                    through a shared-memory staging area: 8 lines x 64
+//                    contiguous bytes per store instruction (a line per thread
+//                    would scatter every store over 32 half-filled sectors).
 // Every mbarrier wait is bounded (about 2 s); on expiry the block sets bit 8 of
 // the context's error word, stops, waits (bounded) for its copies and MMAs in
 // flight and frees its tensor memory.
@@ -61,7 +63,7 @@ struct ZU {
     static constexpr int RAW = 4 * 32 * 128;                  // raw stage: 4 items x 32 cells x 32 lines
     static constexpr int STG = 32 * 80;                       // output staging per epilogue warp: 32 rows x 64 B (+16)
     static constexpr int SMEM = 2 * B_BYTES + OPD * 2 * A_BYTES + RAWD * RAW + 8 * STG + 1024 + 256 + NF * 8;
-    static constexpr int TMEM_COLS = 2 * NC <= 64 ? 64 : 2 * NC <= 128 ? 128 : 256;
+    static constexpr int TMEM_COLS = 3 * NC <= 128 ? 128 : 3 * NC <= 256 ? 256 : 512; // 2 accumulators + parked sums
     static constexpr uint32_t IDESC = umma_idesc_tf32(NC);
     static_assert(NC % 32 == 0 && NC <= 128, "accumulator width");
     static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -298,10 +300,32 @@ k_fft_z_umma(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst
             rs.rot += w.tiles;
         }
     } else { // epilogue: line 32 (warp mod 4) + lane of the tile, modes of half (warp - 6) / 4
-        constexpr int HC = NC / 2;  // accumulator columns per half
-        constexpr int HM = H / 2;   // modes per half
+        constexpr int HC = NC / 2;   // accumulator columns per half
+        constexpr int HM = H / 2;    // modes per half
+        constexpr int PASSES = HM / 8; // 64-byte row pieces per half line
         const int q = warp & 3, half = (warp - 6) >> 2;
         const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * HC);
+        const uint32_t tpark = tl + (uint32_t)(2 * NC); // parked sums of the previous tile
+        float4 *stg = reinterpret_cast<float4 *>(stg_all + (warp - 6) * Z::STG); // [row][5] float4
+        // the parked tile: its first z row for this warp's item (null: none), rows, passes written
+        float4 *pk_out = nullptr;
+        int pk_rows = 0, pk_done = PASSES;
+        // writes pass p of the parked tile: 32 rows x 64 bytes through the staging area
+        auto emit = [&](int p) {
+            uint32_t v[16];
+            tmem_ld16(tpark + (uint32_t)(16 * p), v);
+#pragma unroll
+            for (int c4 = 0; c4 < 4; c4++)
+                stg[lane * 5 + c4] = make_float4(__uint_as_float(v[4 * c4]), __uint_as_float(v[4 * c4 + 1]),
+                                                 __uint_as_float(v[4 * c4 + 2]), __uint_as_float(v[4 * c4 + 3]));
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int row = (lane >> 2) + 8 * k, c4 = lane & 3;
+                if (row < pk_rows) pk_out[(long long)row * (H / 2) + 4 * p + c4] = stg[row * 5 + c4];
+            }
+            __syncwarp();
+        };
         float sum[HC];
 #pragma unroll
         for (int j = 0; j < HC; j++) sum[j] = 0.f;
@@ -333,36 +357,40 @@ k_fft_z_umma(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst
                     }
                     tc_fence_before();
                     mbar_arrive(ACCE + 8 * b);
+                    // part of the parked tile goes out after each chunk: all of it by this tile's last chunk
+                    const int upto = kz == w.nkz - 1 ? PASSES : min(PASSES, pk_done + (PASSES + w.nkz - 1) / w.nkz);
+                    if (pk_out)
+                        for (; pk_done < upto; pk_done++) emit(pk_done);
+                    pk_done = upto;
                 }
                 if (!ok) break;
+                // park this tile's sums (the previous tile is fully written by now)
+#pragma unroll
+                for (int cc = 0; cc < HC / 16; cc++) {
+                    uint32_t v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; j++) v[j] = __float_as_uint(sum[16 * cc + j]);
+                    tmem_st16(tpark + (uint32_t)(16 * cc), v);
+                }
+                tmem_wait_st();
                 const int item = 4 * t + q; // the warp's 32 lines are the rows of one item
+                pk_out = nullptr;
+                pk_rows = 0;
                 if (item < w.items) {
                     const int l = item / (w.b0 * w.nyb), rem = item - l * (w.b0 * w.nyb);
                     const int ix = rem / w.nyb, iy0 = (rem - ix * w.nyb) << 5;
-                    float4 *out0 = reinterpret_cast<float4 *>(z1 + zoff + ((long long)(l * w.b0 + ix) * w.b1 + iy0) * H +
-                                                              half * HM);
-                    float4 *stg = reinterpret_cast<float4 *>(stg_all + (warp - 6) * Z::STG); // [row][5] float4
-#pragma unroll
-                    for (int pass = 0; pass < HM / 8; pass++) { // 8 modes = 64 bytes of each row per pass
-#pragma unroll
-                        for (int c4 = 0; c4 < 4; c4++) {
-                            const int m = 8 * pass + 2 * c4;
-                            stg[lane * 5 + c4] = make_float4(sum[2 * m], sum[2 * m + 1], sum[2 * m + 2], sum[2 * m + 3]);
-                        }
-                        __syncwarp();
-#pragma unroll
-                        for (int k = 0; k < 4; k++) {
-                            const int row = (lane >> 2) + 8 * k, c4 = lane & 3;
-                            if (iy0 + row < w.b1) out0[(long long)row * (H / 2) + 4 * pass + c4] = stg[row * 5 + c4];
-                        }
-                        __syncwarp();
-                    }
+                    pk_out = reinterpret_cast<float4 *>(z1 + zoff + ((long long)(l * w.b0 + ix) * w.b1 + iy0) * H +
+                                                        half * HM);
+                    pk_rows = min(32, w.b1 - iy0);
                 }
+                pk_done = 0;
 #pragma unroll
                 for (int j = 0; j < HC; j++) sum[j] = 0.f;
             }
             rs.rot += w.tiles;
         }
+        if (ok && pk_out)
+            for (; pk_done < PASSES; pk_done++) emit(pk_done); // the last parked tile
     }
     tc_fence_before();
     __syncthreads();
