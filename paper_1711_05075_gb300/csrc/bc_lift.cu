@@ -496,7 +496,10 @@ struct bc_lift_s {
     float2 *cone = nullptr, *tw = nullptr;
     void *ws = nullptr; // rho^_A, rho^_B, phase tables, h planes, slices, pair descriptors, staging
     size_t ws_bytes = 0;
+    char *pin = nullptr; // pinned host staging: sections, pair descriptors, the error word
 };
+
+constexpr size_t LIFT_PIN_BYTES = 4096;
 
 static bc_status lift_fail(bc_status s, const std::string &msg)
 {
@@ -546,6 +549,11 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
     if ((e = cudaMalloc(&lf->cone, sizeof(float2) * (lf->qmax + 1) * lf->Nr)) != cudaSuccess) return bail(e, "cudaMalloc cone");
     if ((e = cudaMalloc(&lf->tw, sizeof(float2) * lf->N)) != cudaSuccess) return bail(e, "cudaMalloc twiddles");
     if ((e = cudaMalloc(&g, sizeof(double) * 2 * LIFT_GAUSS)) != cudaSuccess) return bail(e, "cudaMalloc nodes");
+    if ((e = cudaMallocHost(&lf->pin, LIFT_PIN_BYTES)) != cudaSuccess) return bail(e, "cudaMallocHost staging");
+    if ((e = cudaFuncSetAttribute(k_lift_gemm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_SMEM)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_lift_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(float) * 2 * LIFT_STAGE))) != cudaSuccess)
+        return bail(e, "bc_lift_create: shared memory");
     k_lift_gauss<<<1, 64, 0, lf->stream>>>(LIFT_GAUSS, g, g + LIFT_GAUSS);
     const int total = (lf->qmax + 1) * lf->Nr;
     k_lift_cone<<<(total + 255) / 256, 256, 0, lf->stream>>>(lf->qmax, lf->Nr, lf->L, lf->period, lf->period_r, g,
@@ -566,6 +574,7 @@ bc_status bc_lift_destroy(bc_lift_t lf)
     if (lf->cone) cudaFree(lf->cone);
     if (lf->tw) cudaFree(lf->tw);
     if (lf->ws) cudaFree(lf->ws);
+    if (lf->pin) cudaFreeHost(lf->pin);
     delete lf;
     return BC_OK;
 }
@@ -642,20 +651,27 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
         w += al(knot_bytes);
     }
     float *dout = on_device ? out : (float *)w;
-    std::vector<PairDesc> pairs(nslices);
-    for (int s = 0; s < nslices; s++)
-        pairs[s] = PairDesc{0, 0, (long long)(s * plane), (long long)s * N * N * N, 0};
-    if ((e = cudaMemcpyAsync(dsl, slices, sizeof(float) * nslices, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(dpairs, pairs.data(), sizeof(PairDesc) * nslices, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    // descriptors through pinned staging (the previous call has synchronised, so it is free)
+    float *psl = (float *)lf->pin;
+    PairDesc *ppairs = (PairDesc *)(lf->pin + 256);
+    int *perr = (int *)(lf->pin + 256 + sizeof(PairDesc) * LIFT_MAX_SLICES);
+    for (int s = 0; s < nslices; s++) {
+        psl[s] = slices[s];
+        ppairs[s] = PairDesc{0, 0, (long long)(s * plane), (long long)s * N * N * N, 0};
+    }
+    *perr = 0;
+    if ((e = cudaMemcpyAsync(dsl, psl, sizeof(float) * nslices, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dpairs, ppairs, sizeof(PairDesc) * nslices, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return lift_cuda(e, "bc_lift_correlate: descriptors");
     if ((e = cudaMemsetAsync(derr, 0, sizeof(int), st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: error word");
+    // both spectra are accumulated with atomics: one clear for the pair
+    if ((e = cudaMemsetAsync(rhoA, 0, 2 * al(rho_bytes), st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: clear");
     // the two lifted spectra
     const dim3 tiles((unsigned)(C / LIFT_TILE), (unsigned)(M / LIFT_TILE));
     for (int side = 0; side < 2; side++) {
         const float4 *kn = side ? kB : kA;
         const int n = side ? nB : nA;
         float2 *rho = side ? rhoB : rhoA;
-        if ((e = cudaMemsetAsync(rho, 0, rho_bytes, st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: clear");
         if (n == 0) continue;
         const double qw = side ? quat[0] * inv : 1.0, qx = side ? quat[1] * inv : 0.0, qy = side ? quat[2] * inv : 0.0,
                      qz = side ? quat[3] * inv : 0.0;
@@ -675,8 +691,6 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
             LiftQ *fq = (LiftQ *)(blo + 4 * C * (size_t)ld);
             k_lift_scale<<<(n + 255) / 256, 256, 0, st>>>(kn, n, qw, qx, qy, qz, side, lf->period, lf->period_r, nullptr, fq);
             k_lift_operands<<<dim3((ld + 255) / 256, (unsigned)(M + C)), 256, 0, st>>>(fq, n, nkb, N, Nr, ahi, alo, bhi, blo);
-            if ((e = cudaFuncSetAttribute(k_lift_gemm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, UMMA_SMEM)) != cudaSuccess)
-                return lift_cuda(e, "bc_lift_correlate: shared memory");
             const int ns = umma_nsplit(mt * ctn, nkb, lf->nsm), units = mt * ctn * ns;
             k_lift_gemm_umma<<<units < lf->nsm ? units : lf->nsm, UMMA_THREADS, UMMA_SMEM, st>>>(ahi, alo, bhi, blo, nkb, mt,
                                                                                                ctn, ns, (int)C, rho, derr);
@@ -687,8 +701,6 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
             k_lift_scale<<<(n + 255) / 256, 256, 0, st>>>(kn, n, qw, qx, qy, qz, side, lf->period, lf->period_r, u, nullptr);
             k_lift_planes<<<dim3((ld + 255) / 256, (unsigned)(M + C)), 256, 0, st>>>(u, n, ld, N, Nr, p1re, p1im, p2re, p2im);
             const size_t smem = sizeof(float) * 2 * LIFT_STAGE;
-            if ((e = cudaFuncSetAttribute(k_lift_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-                return lift_cuda(e, "bc_lift_correlate: shared memory");
             k_lift_gemm_tc<<<dim3(tiles.x, tiles.y, split), 256, smem, st>>>(p1re, p1im, p2re, p2im, ld, (int)C, kper, rho);
         } else {
             k_lift_phases<<<n, 64, 0, st>>>(kn, n, qw, qx, qy, qz, side, N, Nr, lf->period, lf->period_r, E);
@@ -715,10 +727,10 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
         if ((e = cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)N * N * N * nslices, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
             return lift_cuda(e, "bc_lift_correlate: copy out");
     }
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: sync");
-    int herr = 0;
-    if ((e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(perr, derr, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return lift_cuda(e, "bc_lift_correlate: error word");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: sync");
+    const int herr = *perr;
     if (herr) return lift_fail(BC_ERR_TIMEOUT, "bc_lift_correlate: tensor-core contraction stalled (waits " +
                                                    std::to_string(herr) + ": 1 copy, 2 accumulator, 4 stage, 8 drain); "
                                                    "the spectrum is incomplete");
