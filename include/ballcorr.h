@@ -373,6 +373,14 @@ bc_status bc_topk(bc_ctx_t ctx, const float *scores, int n, int k, int *idx);
  * earlier asynchronous calls (BC_ERR_INTERNAL, BC_ERR_TIMEOUT) or CUDA error. */
 bc_status bc_sync(bc_ctx_t ctx);
 
+/* Self-test of the bounded device-side waits of the tensor-core kernels:
+ * launches one thread that waits on an mbarrier nothing arrives at.  The wait
+ * gives up after about 2 s and records the expiry in the context's error word,
+ * the kernel returns, and the call (which synchronises) returns BC_ERR_TIMEOUT
+ * with the word cleared; the context stays usable.  Any other status means the
+ * timeout path is broken.  Errors: BC_ERR_ARG (null context), BC_ERR_CUDA. */
+bc_status bc_selftest_wait(bc_ctx_t ctx);
+
 /* ---------------------------------------------------------------- profiling
  * Per-stage device times of bc_correlate, taken with CUDA events recorded on
  * the context stream between the stage launches, and the algorithmic bytes of

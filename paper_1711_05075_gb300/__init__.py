@@ -99,7 +99,9 @@ def lib():
         for f in ("bc_shape_moments", "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
                   "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep"):
             getattr(L, f).restype = st
-        for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sync"):
+        L.bc_selftest_wait.argtypes = [vp]
+        for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sync",
+                  "bc_selftest_wait"):
             getattr(L, f).restype = st
         L.bc_last_error.restype = ctypes.c_char_p
         L.bc_last_error.argtypes = []
@@ -257,6 +259,11 @@ def bc_topk(ctx, scores, n, k, idx):
 
 def bc_sync(ctx):
     _check(lib().bc_sync(ctx))
+
+
+def bc_selftest_wait(ctx):
+    """Status of the bounded-wait self-test: BC_ERR_TIMEOUT (4) when the timeout path works."""
+    return int(lib().bc_selftest_wait(ctx))
 
 
 def bc_version() -> str:
@@ -434,6 +441,10 @@ class Context:
 
     def sync(self):
         bc_sync(self.handle)
+
+    def selftest_wait(self):
+        """Runs bc_selftest_wait: 4 (BC_ERR_TIMEOUT, after about 2 s) when bounded device waits give up cleanly."""
+        return bc_selftest_wait(self.handle)
 
     @property
     def tuning(self):

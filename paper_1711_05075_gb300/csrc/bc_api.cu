@@ -473,6 +473,14 @@ bc_status bc_sync(bc_ctx_t c)
     return BC_OK;
 }
 
+bc_status bc_selftest_wait(bc_ctx_t c)
+{
+    if (!c) return fail(BC_ERR_ARG, "bc_selftest_wait: null context");
+    CK(cudaStreamSynchronize(c->stream));
+    CK(launch_wait_selftest(c->err_dev, c->stream));
+    return bc_sync(c);
+}
+
 const char *bc_stage_name(int i) { return (i >= 0 && i < BC_NUM_STAGES) ? kStageNames[i] : ""; }
 
 bc_status bc_profile_begin(bc_ctx_t c, int max_calls)

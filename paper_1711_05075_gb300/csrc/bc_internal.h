@@ -99,6 +99,8 @@ cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *ins
 // cleared; a stalled wait sets bit 8 of *err.  bhi / blo: the 32-cell DFT block
 // from launch_build_zdft (n/2 x 32 floats each).
 bool supported_z_umma(int N);
+// One thread waits (bounded) on an mbarrier nothing arrives at: sets bit 8 of *err.
+cudaError_t launch_wait_selftest(int *err, cudaStream_t s);
 cudaError_t launch_build_zdft(int n, float *bhi, float *blo, cudaStream_t s);
 cudaError_t launch_fft_z_umma(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
                               const InstPlan *plan, float *grid, float2 *z1, const float *bhi, const float *blo,

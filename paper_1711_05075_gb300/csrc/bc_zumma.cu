@@ -412,6 +412,28 @@ static cudaError_t fft_z_umma_t(const Geometry &g, const Tables &t, const InstDe
     return cudaGetLastError();
 }
 
+// Self-test of the bounded wait the tensor-core kernels use: one thread waits
+// on an mbarrier that nothing arrives at; the wait gives up after
+// UMMA_WAIT_NS and sets bit ZU_ERR of *err, and the kernel returns.
+__global__ void k_wait_selftest(int *err)
+{
+    __shared__ uint64_t bar;
+    __shared__ int stop;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&bar), 1);
+        stop = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) umma_wait(smem_addr(&bar), 0, &stop, err, ZU_ERR);
+}
+
+cudaError_t launch_wait_selftest(int *err, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(err);
+    return cudaGetLastError();
+}
+
 bool supported_z_umma(int N) { return N == 32 || N == 64 || N == 96 || N == 128; }
 
 cudaError_t launch_build_zdft(int n, float *bhi, float *blo, cudaStream_t s)

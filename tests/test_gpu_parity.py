@@ -321,6 +321,22 @@ def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread, zt):
     sa.close(); sb.close(); ctx.close()
 
 
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    # failure detection without a fault: a device wait that nothing satisfies
+    # expires (about 2 s), is reported as BC_ERR_TIMEOUT (4), and the next
+    # correlation on the same context is correct
+    bc = bcmod()
+    wl = synth.small_pair(6)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    assert ctx.selftest_wait() == 4
+    ctx.sync()  # the error word was cleared
+    sa = ctx.shape(wl.A.xyz, wl.A.level)
+    sb = ctx.shape(wl.B.xyz, wl.B.level)
+    got = ctx.correlate(sa, sb, wl.quats).double().cpu().numpy()[0]
+    check(got, oracle_grid(wl.A, wl.B, wl.quats[0], wl.N), what="after an expired wait")
+    sa.close(); sb.close(); ctx.close()
+
+
 def test_z_transform_availability():
     # the tensor-core z transform: FP32 contexts with N <= 128 start with it;
     # elsewhere selecting it is refused (BC_ERR_UNSUPPORTED = 5)
