@@ -684,7 +684,7 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
     };
     const bool binned = job.mode == 1;
     mark(-1);
-    ws.boxes_dirty = true; // until k_plan has consumed and reset the accumulators
+    ws.boxes_dirty = true; // until the plan has consumed and reset the accumulators
     if (binned) {
         ws.bins_dirty = true; // until the bin scan has consumed and cleared the counts
         if ((e = launch_prepare(g, dinst, ninst, job.max_knots, (float4 *)ws.ku.p, (int *)ws.boxes.p, dplan,
@@ -697,7 +697,7 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
         if ((e = launch_prepare(g, dinst, ninst, job.max_knots, (float4 *)ws.ku.p, (int *)ws.boxes.p, dplan,
                                 c->err_dev, nullptr, nullptr, st)) != cudaSuccess)
             return cuda_fail(e, "prepare");
-        launches += 2;
+        launches += 1;
     }
     ws.boxes_dirty = false;
     mark(0);

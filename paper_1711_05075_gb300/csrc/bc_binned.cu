@@ -4,7 +4,7 @@
 //
 //   k_prepare (with counts)  counts the knots of every bin: (instance, level,
 //                            g0_x mod n), g0 the first stencil cell per axis;
-//   k_plan_bins              plans each instance (as k_plan) and turns its
+//   k_plan_bins              plans each instance (as k_prepare does without bins) and turns its
 //                            counts into the first slot of every bin;
 //   k_bin                    the 3W separable window weights phi(u_a - g)
 //                            (Kaiser-Bessel, as in k_spread) and the stencil

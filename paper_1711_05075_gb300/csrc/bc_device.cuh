@@ -72,8 +72,8 @@ __device__ __forceinline__ void plan_instance(const Geometry &g, const InstDesc 
     int L0[3], H0[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        L0[a] = bb[8 * i + a];
-        H0[a] = bb[8 * i + 3 + a];
+        L0[a] = __ldcg(&bb[8 * i + a]); // written by other blocks' atomics: read at L2
+        H0[a] = __ldcg(&bb[8 * i + 3 + a]);
         bb[8 * i + a] = INT_MAX;
         bb[8 * i + 3 + a] = INT_MIN;
     }

@@ -82,7 +82,8 @@ cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, i
 // knots in shared memory and transforms them (no spreading grid in HBM).
 constexpr int MAX_W = 10;   // widest window (bc_create checks)
 constexpr int BIN_REC = 32; // floats per binned knot: g0_y, g0_z (int bits), W x-, W y-, W z-weights
-// Plans (as k_plan) and turns the counts into cursors, one block per instance.
+// Plans each instance (as launch_prepare does without bins) and turns the counts
+// into cursors, one block per instance.
 cudaError_t launch_plan_bins(const Geometry &g, const InstDesc *inst, int ninst, int *bb, InstPlan *plan, int *err,
                              int *cnt, int *cur, cudaStream_t s);
 cudaError_t launch_bin(const Geometry &g, const Tables &t, const InstDesc *inst, int total_knots, const float4 *ku,

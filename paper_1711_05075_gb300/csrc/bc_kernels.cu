@@ -6,7 +6,8 @@
 //   k_prepare   rotate the knots (Eq. (Mink0), Sec. 2.4: a rigid motion only
 //               moves the centres), map them to fine-grid coordinates and find
 //               each instance's support box (the cells its spreading touches);
-//   k_plan      turns the boxes into per-instance plans.
+//               The last block to finish turns the boxes into
+//               per-instance plans.
 //   k_spread    type-1 NUFFT step 1 for the impulse densities of Eq. (rhoP):
 //               Kaiser-Bessel spreading of every knot onto its level's grid,
 //               restricted to the support box (cells outside it stay zero).
@@ -176,13 +177,19 @@ cudaError_t launch_pack_knots(const float *xyz, const int *level, int n, int L, 
 // Grid: (blocks over knots, instance).
 constexpr int PREP_THREADS = 256;
 
+// With plan != null the last block to finish (counted on bb[6], which the
+// reset leaves at 0 and that block puts back) turns every instance's support
+// box into its plan and resets the box accumulators (plan_instance); a box
+// larger than the instance's capacity raises the error word and the instance
+// is treated as empty.
 __global__ void __launch_bounds__(PREP_THREADS)
-k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 *ku, int *bb, int *cnt)
+k_prepare(Geometry g, const InstDesc *__restrict__ inst, int ninst, float4 *ku, int *bb, int *cnt, InstPlan *plan,
+          int *err)
 {
     const int i = blockIdx.y;
     const InstDesc d = inst[i];
     const int j = blockIdx.x * PREP_THREADS + threadIdx.x;
-    if (blockIdx.x * PREP_THREADS >= d.nknots) return; // whole block beyond this instance
+    if (blockIdx.x * PREP_THREADS < d.nknots) { // else the whole block is beyond this instance's knots
     float qw = d.q[0], qx = d.q[1], qy = d.q[2], qz = d.q[3];
     if (d.qdev) {
         qw = d.qdev[0];
@@ -242,20 +249,23 @@ k_prepare(Geometry g, const InstDesc *__restrict__ inst, float4 *ku, int *bb, in
         if (a < 3) atomicMin(&bb[8 * i + a], v);
         else atomicMax(&bb[8 * i + a], v);
     }
+    } // this block's knots
+    if (!plan) return;
+    __shared__ int last;
+    __threadfence(); // this block's box updates precede its count
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&bb[6], 1) == (int)(gridDim.x * gridDim.y) - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int k = threadIdx.x; k < ninst; k += PREP_THREADS) plan_instance(g, inst, k, bb, plan, err);
+    if (threadIdx.x == 0) bb[6] = 0;
 }
 
-// Support boxes -> plans (one thread per instance); the accumulators are reset
-// for the next launch.  A box larger than the instance's capacity raises the
-// error word and the instance is treated as empty.
-__global__ void k_plan(Geometry g, const InstDesc *__restrict__ inst, int ninst, int *bb, InstPlan *plan, int *err)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < ninst) plan_instance(g, inst, i, bb, plan, err);
-}
 __global__ void k_reset_boxes(int *bb, int ninst)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < 8 * ninst) bb[t] = ((t & 7) < 3) ? INT_MAX : INT_MIN;
+    if (t < 8 * ninst) bb[t] = (t & 7) < 3 ? INT_MAX : (t & 7) < 6 ? INT_MIN : 0; // slots 6, 7: counters
 }
 
 cudaError_t launch_reset_boxes(int *bb, int ninst, cudaStream_t s)
@@ -270,12 +280,12 @@ cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, i
 {
     if (ninst <= 0) return cudaSuccess;
     const int bx = max_knots > 0 ? (max_knots + PREP_THREADS - 1) / PREP_THREADS : 1;
-    k_prepare<<<dim3(bx, ninst), PREP_THREADS, 0, s>>>(g, inst, ku, bb, cnt);
+    // binned spreading plans (and scans its bin counts) in its own kernel
+    k_prepare<<<dim3(bx, ninst), PREP_THREADS, 0, s>>>(g, inst, ninst, ku, bb, cnt, cnt ? nullptr : plan, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (cnt) return launch_plan_bins(g, inst, ninst, bb, plan, err, cnt, cur, s);
-    k_plan<<<(ninst + 127) / 128, 128, 0, s>>>(g, inst, ninst, bb, plan, err);
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ spread
