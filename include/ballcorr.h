@@ -223,7 +223,9 @@ bc_status bc_query_destroy(bc_query_t q);
  * bc_lift_correlate: A, B = n x 4 FP32 (x, y, z, r), quat = 4 FP32 host values,
  * slices = nslices (1 .. 16) FP32 host values r_s, out = nslices x N^3 FP32
  * ([s][kx][ky][kz]); A, B and out are device (on_device = 1) or host (0)
- * memory.  Synchronous.  Errors: BC_ERR_ARG (null pointer, counts out of
+ * memory.  Synchronous.  The tensor-core contractions take the knots in
+ * passes of 32,768 (their operands cost 16 N^2 + 16 N Nr bytes per knot), so
+ * the workspace stays bounded for any knot count.  Errors: BC_ERR_ARG (null pointer, counts out of
  * range, zero quaternion, non-finite section), BC_ERR_UNSUPPORTED (N not 32 or
  * 64, Nr not 8, 16, 32 or 64), BC_ERR_OOM, BC_ERR_CUDA, BC_ERR_TIMEOUT (a
  * bounded wait inside the tcgen05 contraction expired; out is incomplete). */

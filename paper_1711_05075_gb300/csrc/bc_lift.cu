@@ -56,6 +56,7 @@ constexpr int LIFT_GAUSS = 48;   // quadrature nodes of the cone transform
 constexpr int LIFT_TILE = 64;    // output tile of the contraction (rows and columns)
 constexpr int LIFT_KC = 32;      // knots staged per step
 constexpr int LIFT_MAX_SLICES = 16;
+constexpr int LIFT_CHUNK = 32768; // knots per pass of the tensor-core contractions (bounds their operand memory)
 
 __device__ __forceinline__ int lift_mode(int j, int n) { return j < n / 2 ? j : j - n; }
 
@@ -599,11 +600,14 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
     const size_t M = (size_t)N * N, C = (size_t)H * Nr;
     const size_t rho_bytes = sizeof(float2) * M * C;
     const size_t nmax = (size_t)(nA > nB ? nA : nB);
-    const int ld = (int)((nmax + LIFT_KC - 1) / LIFT_KC) * LIFT_KC > 0 ? (int)((nmax + LIFT_KC - 1) / LIFT_KC) * LIFT_KC
-                                                                       : LIFT_KC;
+    // the tensor-core contractions take the knots in passes of at most LIFT_CHUNK
+    // (their operands cost 16 M + 32 C, resp. 8 (M + C), bytes per knot); each
+    // pass adds its partial spectrum into rho^ with atomics
+    const size_t nchunk = nmax < (size_t)LIFT_CHUNK ? nmax : (size_t)LIFT_CHUNK;
+    const int ld = nchunk > 0 ? (int)((nchunk + LIFT_KC - 1) / LIFT_KC) * LIFT_KC : LIFT_KC; // padded pass length
     // contraction 2: A blocks (hi, lo) 16 M ld bytes, B blocks 32 C ld bytes, fixed-point knots
-    const size_t e_bytes = lf->contraction == 2 ? (16 * M + 32 * C) * (size_t)ld + sizeof(LiftQ) * (nmax + 1)
-                         : lf->contraction == 1 ? sizeof(float) * 2 * (M + C) * (size_t)ld + sizeof(LiftU) * (nmax + 1)
+    const size_t e_bytes = lf->contraction == 2 ? (16 * M + 32 * C) * (size_t)ld + sizeof(LiftQ) * (nchunk + 1)
+                         : lf->contraction == 1 ? sizeof(float) * 2 * (M + C) * (size_t)ld + sizeof(LiftU) * (nchunk + 1)
                                                 : sizeof(float2) * (size_t)T * (nmax > 0 ? nmax : 1);
     const size_t plane = (size_t)N * N * H;
     const size_t h_bytes = sizeof(float2) * plane * nslices;
@@ -675,34 +679,52 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
         if (n == 0) continue;
         const double qw = side ? quat[0] * inv : 1.0, qx = side ? quat[1] * inv : 0.0, qy = side ? quat[2] * inv : 0.0,
                      qz = side ? quat[3] * inv : 0.0;
-        // split the knots so that about four blocks per SM run
         const int ntile = (int)(tiles.x * tiles.y);
-        const int kn_len = lf->contraction == 1 ? ld : n;
-        int split = (4 * lf->nsm + ntile - 1) / ntile;
-        int kper = (kn_len + split - 1) / split;
-        kper = ((kper + LIFT_KC - 1) / LIFT_KC) * LIFT_KC;
-        split = (kn_len + kper - 1) / kper;
+        // knots split across blocks so that about four blocks per SM run
+        auto split_of = [&](int len, int &kper) {
+            int split = (4 * lf->nsm + ntile - 1) / ntile;
+            kper = (len + split - 1) / split;
+            kper = ((kper + LIFT_KC - 1) / LIFT_KC) * LIFT_KC;
+            return (len + kper - 1) / kper;
+        };
         if (lf->contraction == 2) {
-            const int nkb = ld / LIFT_KC, mt = (int)(M / 128), ctn = (int)(C / 128);
+            const int mt = (int)(M / 128), ctn = (int)(C / 128);
             // A hi / lo: mt x nkb x 2 blocks of 128 x 32 floats = 2 M ld floats each;
             // B hi / lo: ctn x nkb x 2 blocks of 256 x 32 floats = 4 C ld floats each
             float *ahi = (float *)E, *alo = ahi + 2 * M * (size_t)ld, *bhi = alo + 2 * M * (size_t)ld,
                   *blo = bhi + 4 * C * (size_t)ld;
             LiftQ *fq = (LiftQ *)(blo + 4 * C * (size_t)ld);
-            k_lift_scale<<<(n + 255) / 256, 256, 0, st>>>(kn, n, qw, qx, qy, qz, side, lf->period, lf->period_r, nullptr, fq);
-            k_lift_operands<<<dim3((ld + 255) / 256, (unsigned)(M + C)), 256, 0, st>>>(fq, n, nkb, N, Nr, ahi, alo, bhi, blo);
-            const int ns = umma_nsplit(mt * ctn, nkb, lf->nsm), units = mt * ctn * ns;
-            k_lift_gemm_umma<<<units < lf->nsm ? units : lf->nsm, UMMA_THREADS, UMMA_SMEM, st>>>(ahi, alo, bhi, blo, nkb, mt,
-                                                                                               ctn, ns, (int)C, rho, derr);
+            for (int k0 = 0; k0 < n; k0 += LIFT_CHUNK) {
+                const int nc = n - k0 < LIFT_CHUNK ? n - k0 : LIFT_CHUNK;
+                const int nkb = (nc + LIFT_KC - 1) / LIFT_KC;
+                k_lift_scale<<<(nc + 255) / 256, 256, 0, st>>>(kn + k0, nc, qw, qx, qy, qz, side, lf->period, lf->period_r,
+                                                               nullptr, fq);
+                k_lift_operands<<<dim3((nkb * LIFT_KC + 255) / 256, (unsigned)(M + C)), 256, 0, st>>>(fq, nc, nkb, N, Nr, ahi,
+                                                                                                   alo, bhi, blo);
+                const int ns = umma_nsplit(mt * ctn, nkb, lf->nsm), units = mt * ctn * ns;
+                k_lift_gemm_umma<<<units < lf->nsm ? units : lf->nsm, UMMA_THREADS, UMMA_SMEM, st>>>(
+                    ahi, alo, bhi, blo, nkb, mt, ctn, ns, (int)C, rho, derr);
+            }
         } else if (lf->contraction == 1) {
             float *p1re = (float *)E, *p1im = p1re + M * (size_t)ld, *p2re = p1im + M * (size_t)ld,
                   *p2im = p2re + C * (size_t)ld;
             LiftU *u = (LiftU *)(p2im + C * (size_t)ld);
-            k_lift_scale<<<(n + 255) / 256, 256, 0, st>>>(kn, n, qw, qx, qy, qz, side, lf->period, lf->period_r, u, nullptr);
-            k_lift_planes<<<dim3((ld + 255) / 256, (unsigned)(M + C)), 256, 0, st>>>(u, n, ld, N, Nr, p1re, p1im, p2re, p2im);
             const size_t smem = sizeof(float) * 2 * LIFT_STAGE;
-            k_lift_gemm_tc<<<dim3(tiles.x, tiles.y, split), 256, smem, st>>>(p1re, p1im, p2re, p2im, ld, (int)C, kper, rho);
+            for (int k0 = 0; k0 < n; k0 += LIFT_CHUNK) {
+                const int nc = n - k0 < LIFT_CHUNK ? n - k0 : LIFT_CHUNK;
+                const int ldc = ((nc + LIFT_KC - 1) / LIFT_KC) * LIFT_KC; // this pass's plane stride
+                int kper;
+                const int split = split_of(ldc, kper);
+                k_lift_scale<<<(nc + 255) / 256, 256, 0, st>>>(kn + k0, nc, qw, qx, qy, qz, side, lf->period, lf->period_r,
+                                                               u, nullptr);
+                k_lift_planes<<<dim3((ldc + 255) / 256, (unsigned)(M + C)), 256, 0, st>>>(u, nc, ldc, N, Nr, p1re, p1im,
+                                                                                        p2re, p2im);
+                k_lift_gemm_tc<<<dim3(tiles.x, tiles.y, split), 256, smem, st>>>(p1re, p1im, p2re, p2im, ldc, (int)C, kper,
+                                                                                 rho);
+            }
         } else {
+            int kper;
+            const int split = split_of(n, kper);
             k_lift_phases<<<n, 64, 0, st>>>(kn, n, qw, qx, qy, qz, side, N, Nr, lf->period, lf->period_r, E);
             k_lift_ndft<<<dim3(tiles.x, tiles.y, split), 256, 0, st>>>(E, n, N, Nr, kper, rho);
         }

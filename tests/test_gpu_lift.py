@@ -48,6 +48,7 @@ def rel(a, b):
 @pytest.mark.parametrize("N,Nr,nA,nB,slices", [(32, 32, 6, 6, (0.0, 0.03, -0.02)),
                                                  (32, 16, 2000, 1500, (0.0, 0.04)),
                                                  (32, 8, 12000, 7000, (0.0, 0.05)),
+                                                 (32, 8, 40000, 3000, (0.0,)),  # two passes of 32,768 knots
                                                  (64, 16, 800, 600, (0.0,))])
 def test_lifted_sections_match_oracle(bc, N, Nr, nA, nB, slices, contraction):
     A = knots(synth.ellipsoid_shape(nA, 40 + nA), 1)
