@@ -301,8 +301,7 @@ def run_ours(args, rank, world, local_rank):
     d2h = host_out.numel() * 4
 
     def e2e_step():
-        ha = bc.bc_shape_create(ctx.handle, xa, la, wl.A.n, 0)
-        hb = bc.bc_shape_create(ctx.handle, xb, lb, wl.B.n, 0)
+        ha, hb = bc.bc_shapes_create(ctx.handle, [xa, xb], [la, lb], [wl.A.n, wl.B.n], 0)
         bc.bc_correlate(ctx.handle, ha, hb, q, 1, host_out, 0)
         bc.bc_shape_destroy(ha)
         bc.bc_shape_destroy(hb)

@@ -99,6 +99,16 @@ bc_status bc_destroy(bc_ctx_t ctx);
 bc_status bc_shape_create(bc_ctx_t ctx, const float *xyz, const int *level, int n, int on_device,
                           bc_shape_t *out);
 
+/* Uploads `count` shapes with one stream synchronisation for all of them
+ * (bc_shape_create is the count = 1 case): shape i has n[i] knots with
+ * centres xyz[i] and level ids level[i], arrays as in bc_shape_create, all
+ * device (on_device = 1) or all host (0) memory; out[i] receives its handle.
+ * On any error no shape is created (every out[i] is NULL) and the message
+ * names the first failing shape.  Errors as bc_shape_create, and BC_ERR_ARG
+ * for count < 0 or null arrays. */
+bc_status bc_shapes_create(bc_ctx_t ctx, int count, const float *const *xyz, const int *const *level, const int *n,
+                           int on_device, bc_shape_t *out);
+
 /* Frees a shape (stream-ordered after pending work on the context).  NULL is accepted.
  * A shape whose context was destroyed first has already lost its device memory;
  * this call then only releases the handle. */
@@ -108,6 +118,9 @@ bc_status bc_shape_destroy(bc_shape_t shape);
  * FP32 array of k * N^3 values, kz fastest.  quats: k x 4 FP32 (w, x, y, z),
  * normalised internally, host memory.  A is not rotated.  `out_on_device`
  * selects device (1, asynchronous) or host (0, synchronous) output memory.
+ * A host `out` in page-locked memory mapped into the device address space
+ * (cudaMallocHost, cudaHostAlloc, cudaHostRegister) is written by the last
+ * kernel directly; other host memory is staged on the device and copied.
  * Errors: BC_ERR_ARG (k < 1, null pointer, zero quaternion, shapes from
  * another context), BC_ERR_OOM, BC_ERR_CUDA, BC_ERR_INTERNAL. */
 bc_status bc_correlate(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, const float *quats, int k,
@@ -146,7 +159,8 @@ bc_status bc_plan_destroy(bc_plan_t plan);
  * counts; every instance gets its own support box.  Outputs (either may be
  * NULL, not both): out[i][kx][ky][kz] (npairs * N^3 floats) and
  * peak[i] / argmax[i] as in bc_sweep.  All output pointers are device memory
- * (on_device = 1, asynchronous) or host memory (0, synchronous).
+ * (on_device = 1, asynchronous) or host memory (0, synchronous); a host `out`
+ * is written as bc_correlate's.
  * Errors: BC_ERR_ARG (null shape or quaternion array, zero quaternion, both
  * outputs null, peak without argmax, npairs outside [1, 32767], shapes from
  * another context), BC_ERR_OOM, BC_ERR_CUDA. */

@@ -71,6 +71,7 @@ def lib():
         L.bc_create.argtypes = [ctypes.POINTER(bc_params), vp, ctypes.POINTER(vp)]
         L.bc_destroy.argtypes = [vp]
         L.bc_shape_create.argtypes = [vp, vp, vp, i, i, ctypes.POINTER(vp)]
+        L.bc_shapes_create.argtypes = [vp, i, vp, vp, vp, i, vp]
         L.bc_shape_destroy.argtypes = [vp]
         L.bc_correlate.argtypes = [vp, vp, vp, vp, i, vp, i]
         L.bc_sync.argtypes = [vp]
@@ -100,8 +101,8 @@ def lib():
                   "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep"):
             getattr(L, f).restype = st
         L.bc_selftest_wait.argtypes = [vp]
-        for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sync",
-                  "bc_selftest_wait"):
+        for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shapes_create", "bc_shape_destroy", "bc_correlate",
+                  "bc_sync", "bc_selftest_wait"):
             getattr(L, f).restype = st
         L.bc_last_error.restype = ctypes.c_char_p
         L.bc_last_error.argtypes = []
@@ -172,6 +173,17 @@ def bc_shape_create(ctx, xyz, level, n, on_device):
     h = ctypes.c_void_p()
     _check(lib().bc_shape_create(ctx, _ptr(xyz), _ptr(level), int(n), int(on_device), ctypes.byref(h)))
     return h
+
+
+def bc_shapes_create(ctx, xyzs, levels, ns, on_device):
+    """Several shapes with one stream synchronisation; returns their handles."""
+    count = len(ns)
+    px = (ctypes.c_void_p * max(count, 1))(*[_ptr(x) for x in xyzs])
+    pl = (ctypes.c_void_p * max(count, 1))(*[_ptr(l) for l in levels])
+    pn = (ctypes.c_int * max(count, 1))(*[int(n) for n in ns])
+    hs = (ctypes.c_void_p * max(count, 1))()
+    _check(lib().bc_shapes_create(ctx, int(count), px, pl, pn, int(on_device), hs))
+    return [ctypes.c_void_p(hs[i]) for i in range(count)]
 
 
 def bc_shape_destroy(shape):
@@ -373,6 +385,23 @@ class Context:
         self._shapes.add(s)
         return s
 
+    def shapes(self, pairs):
+        """Several shapes [(xyz, level), ...], all host or all CUDA arrays, uploaded
+        with one stream synchronisation (bc_shapes_create)."""
+        arrs = [Shape._arrays(x, l) for x, l in pairs]
+        devs = {d for _, _, d in arrs}
+        if len(devs) > 1:
+            raise ValueError("shapes: mix of host and device arrays")
+        hs = bc_shapes_create(self.handle, [a[0] for a in arrs], [a[1] for a in arrs], [a[0].shape[0] for a in arrs],
+                              devs.pop() if arrs else 0)
+        out = []
+        for (x, l, d), h in zip(arrs, hs):
+            s = Shape.__new__(Shape)
+            s.ctx, s.n, s.handle = self, x.shape[0], h
+            self._shapes.add(s)
+            out.append(s)
+        return out
+
     def correlate(self, A, B, quats, out=None):
         """g for each rotation: a (k, N, N, N) float32 CUDA tensor (or `out`)."""
         import torch
@@ -565,18 +594,20 @@ class Shape:
     """A union of balls uploaded to the device: xyz (n x 3) and level ids (n)."""
 
     def __init__(self, ctx: Context, xyz, level):
-        import torch
         self.ctx = ctx
+        self.handle = None
+        x, l, dev = Shape._arrays(xyz, level)
+        self.n = x.shape[0]
+        self.handle = bc_shape_create(ctx.handle, x, l, self.n, dev)
+
+    @staticmethod
+    def _arrays(xyz, level):
+        """(xyz as contiguous n x 3 FP32, level as contiguous int32, on_device)."""
         if hasattr(xyz, "is_cuda") and xyz.is_cuda:
-            x = xyz.to(torch.float32).contiguous()
-            l = level.to(torch.int32).contiguous()
-            self.n = x.shape[0]
-            self.handle = bc_shape_create(ctx.handle, x, l, self.n, 1)
-        else:
-            x = np.ascontiguousarray(np.asarray(xyz, dtype=np.float32).reshape(-1, 3))
-            l = np.ascontiguousarray(np.asarray(level, dtype=np.int32).reshape(-1))
-            self.n = x.shape[0]
-            self.handle = bc_shape_create(ctx.handle, x, l, self.n, 0)
+            import torch
+            return xyz.to(torch.float32).reshape(-1, 3).contiguous(), level.to(torch.int32).reshape(-1).contiguous(), 1
+        return (np.ascontiguousarray(np.asarray(xyz, dtype=np.float32).reshape(-1, 3)),
+                np.ascontiguousarray(np.asarray(level, dtype=np.int32).reshape(-1)), 0)
 
     def close(self):
         if self.handle is not None:

@@ -72,6 +72,30 @@ struct DevBuf {
     }
 };
 
+// A page-locked host buffer that only grows (no copy may target it when it grows).
+struct PinBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t need)
+    {
+        if (need <= bytes) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMallocHost(&p, need);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = need;
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
 // Device workspaces of one pipeline: the context's own, or a captured plan's.
 struct Workspace {
     DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, boxes, keys;
@@ -126,6 +150,10 @@ struct bc_ctx_s {
     int qmax = 0;
     // device status word
     int *err_dev = nullptr;
+    // page-locked words the host reads after a synchronisation: the status
+    // word, and two per shape of a bc_shapes_create call
+    int *pin = nullptr;
+    PinBuf hstats;
     // implementation choices (bc_set_tuning / bc_autotune)
     int spread_mode = 0;  // 0: spreading boxes in HBM (k_spread + k_fft_z); 1: binned, fused into the z pass
     int sweep_batch = 64; // rotations per pass when a sweep's batch argument is 0
@@ -314,6 +342,8 @@ bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
                 return bail(e, "copy modes");
         }
         if ((e = cudaMalloc(&c->err_dev, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc err");
+        if ((e = cudaMallocHost(&c->pin, sizeof(int))) != cudaSuccess) return bail(e, "cudaMallocHost");
+        *c->pin = 0;
         if ((e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream)) != cudaSuccess) return bail(e, "memset err");
         if ((e = cudaMemcpyAsync(c->radii_dev, c->radii.data(), sizeof(double) * g.L, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
             return bail(e, "copy radii");
@@ -344,6 +374,7 @@ bc_status bc_destroy(bc_ctx_t c)
         cudaFree(c->tw_n);
         cudaFree(c->tw_N);
         cudaFree(c->err_dev);
+        if (c->pin) cudaFreeHost(c->pin);
         cudaFree(c->consts);
         cudaFree(c->modes);
         cudaFree(c->zdft);
@@ -365,6 +396,7 @@ bc_status bc_destroy(bc_ctx_t c)
         if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
         DevBuf *bufs[] = {&c->outbuf, &c->stats, &c->learn, &c->tune, &c->score_ft};
         for (DevBuf *b : bufs) b->release();
+        c->hstats.release();
         delete c;
         return BC_OK;
     } catch (...) {
@@ -372,74 +404,118 @@ bc_status bc_destroy(bc_ctx_t c)
     }
 }
 
-bc_status bc_shape_create(bc_ctx_t c, const float *xyz, const int *level, int n, int on_device, bc_shape_t *out)
+bc_status bc_shapes_create(bc_ctx_t c, int count, const float *const *xyz, const int *const *level, const int *n,
+                           int on_device, bc_shape_t *out)
 {
     try {
-        if (!c || !out) return fail(BC_ERR_ARG, "bc_shape_create: null context or output");
-        *out = nullptr;
-        if (n < 0) return fail(BC_ERR_ARG, "bc_shape_create: n < 0");
-        if (n > 0 && (!xyz || !level)) return fail(BC_ERR_ARG, "bc_shape_create: null knot arrays");
-        if (n >= (1 << 26)) return fail(BC_ERR_ARG, "bc_shape_create: too many knots");
-        bc_shape_t s = new (std::nothrow) bc_shape_s();
-        if (!s) return fail(BC_ERR_OOM, "bc_shape_create: host allocation failed");
-        s->ctx = c;
-        s->n = n;
-        if (n == 0) {
-            c->shapes.insert(s);
-            *out = s;
-            return BC_OK;
+        if (!c || !out || count < 0 || (count > 0 && (!xyz || !level || !n)))
+            return fail(BC_ERR_ARG, "bc_shapes_create: null argument or count < 0");
+        for (int i = 0; i < count; i++) out[i] = nullptr;
+        size_t staged = 0; // staging bytes of the host-resident shapes
+        for (int i = 0; i < count; i++) {
+            const std::string who = "bc_shape_create (shape " + std::to_string(i) + "): ";
+            if (n[i] < 0) return fail(BC_ERR_ARG, who + "n < 0");
+            if (n[i] > 0 && (!xyz[i] || !level[i])) return fail(BC_ERR_ARG, who + "null knot arrays");
+            if (n[i] >= (1 << 26)) return fail(BC_ERR_ARG, who + "too many knots");
+            if (!on_device) staged += (sizeof(float) * 3 + sizeof(int)) * (size_t)n[i];
         }
+        std::vector<bc_shape_t> made(count, nullptr);
         cudaStream_t st = c->stream;
+        void *staging = nullptr;
+        auto drop = [&]() {
+            if (staging) cudaFreeAsync(staging, st);
+            for (bc_shape_t s : made)
+                if (s) {
+                    if (s->knots) cudaFreeAsync(s->knots, st);
+                    delete s;
+                }
+        };
         auto bail = [&](cudaError_t e, const char *w) {
             bc_status r = cuda_fail(e, w);
-            if (s->knots) cudaFreeAsync(s->knots, st);
-            delete s;
+            drop();
             return r;
         };
+        for (int i = 0; i < count; i++) {
+            made[i] = new (std::nothrow) bc_shape_s();
+            if (!made[i]) {
+                drop();
+                return fail(BC_ERR_OOM, "bc_shape_create: host allocation failed");
+            }
+            made[i]->ctx = c;
+            made[i]->n = n[i];
+        }
         cudaError_t e;
-        if ((e = cudaMallocAsync((void **)&s->knots, sizeof(float4) * n, st)) != cudaSuccess) return bail(e, "cudaMallocAsync knots");
-        const float *dx = xyz;
-        const int *dl = level;
-        void *staging = nullptr;
-        if (!on_device) {
-            if ((e = cudaMallocAsync(&staging, sizeof(float) * 3 * n + sizeof(int) * n, st)) != cudaSuccess)
-                return bail(e, "cudaMallocAsync staging");
-            float *sx = (float *)staging;
-            int *sl = (int *)(sx + 3 * (size_t)n);
-            if ((e = cudaMemcpyAsync(sx, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-                return bail(e, "copy xyz");
-            if ((e = cudaMemcpyAsync(sl, level, sizeof(int) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-                return bail(e, "copy level");
-            dx = sx;
-            dl = sl;
-        }
-        if ((e = c->stats.ensure(2 * sizeof(unsigned int), false, st)) != cudaSuccess) return bail(e, "stats");
+        if (staged && (e = cudaMallocAsync(&staging, staged, st)) != cudaSuccess) return bail(e, "cudaMallocAsync staging");
+        if ((e = c->stats.ensure(2 * sizeof(unsigned int) * (size_t)(count > 0 ? count : 1), false, st)) != cudaSuccess)
+            return bail(e, "stats");
+        if ((e = c->hstats.ensure(2 * sizeof(unsigned int) * (size_t)(count > 0 ? count : 1))) != cudaSuccess)
+            return bail(e, "page-locked stats");
         unsigned int *stats = (unsigned int *)c->stats.p;
-        if ((e = cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess) return bail(e, "memset stats");
-        if ((e = launch_pack_knots(dx, dl, n, c->g.L, s->knots, stats, st)) != cudaSuccess) return bail(e, "pack knots");
-        unsigned int hs[2] = {0, 0};
-        if ((e = cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return bail(e, "copy stats");
-        if (staging && (e = cudaFreeAsync(staging, st)) != cudaSuccess) return bail(e, "free staging");
+        if (count && (e = cudaMemsetAsync(stats, 0, 2 * sizeof(unsigned int) * count, st)) != cudaSuccess)
+            return bail(e, "memset stats");
+        char *sp = (char *)staging;
+        for (int i = 0; i < count; i++) {
+            const int ni = n[i];
+            if (ni == 0) continue;
+            bc_shape_t s = made[i];
+            if ((e = cudaMallocAsync((void **)&s->knots, sizeof(float4) * ni, st)) != cudaSuccess)
+                return bail(e, "cudaMallocAsync knots");
+            const float *dx = xyz[i];
+            const int *dl = level[i];
+            if (!on_device) {
+                float *sx = (float *)sp;
+                int *sl = (int *)(sx + 3 * (size_t)ni);
+                sp += (sizeof(float) * 3 + sizeof(int)) * (size_t)ni;
+                if ((e = cudaMemcpyAsync(sx, dx, sizeof(float) * 3 * ni, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                    return bail(e, "copy xyz");
+                if ((e = cudaMemcpyAsync(sl, dl, sizeof(int) * ni, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                    return bail(e, "copy level");
+                dx = sx;
+                dl = sl;
+            }
+            if ((e = launch_pack_knots(dx, dl, ni, c->g.L, s->knots, stats + 2 * i, st)) != cudaSuccess)
+                return bail(e, "pack knots");
+        }
+        // one read-back through page-locked memory and one stream synchronisation
+        // for every shape of the call
+        unsigned int *hs = (unsigned int *)c->hstats.p;
+        if (count && (e = cudaMemcpyAsync(hs, stats, 2 * sizeof(unsigned int) * count, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return bail(e, "copy stats");
+        if (staging) {
+            e = cudaFreeAsync(staging, st);
+            staging = nullptr;
+            if (e != cudaSuccess) return bail(e, "free staging");
+        }
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "bc_shape_create sync");
-        if (hs[1] & 1u) {
-            cudaFreeAsync(s->knots, st);
-            delete s;
-            return fail(BC_ERR_ARG, "bc_shape_create: level id out of range [0, L)");
+        for (int i = 0; i < count; i++) {
+            if (n[i] == 0) continue;
+            const std::string who = "bc_shape_create (shape " + std::to_string(i) + "): ";
+            if (hs[2 * i + 1] & 1u) {
+                drop();
+                return fail(BC_ERR_ARG, who + "level id out of range [0, L)");
+            }
+            if (hs[2 * i + 1] & 2u) {
+                drop();
+                return fail(BC_ERR_ARG, who + "non-finite knot coordinate");
+            }
+            float r2;
+            std::memcpy(&r2, &hs[2 * i], sizeof(float));
+            made[i]->rmax = std::sqrt(r2) * (1.0f + 1e-6f);
         }
-        if (hs[1] & 2u) {
-            cudaFreeAsync(s->knots, st);
-            delete s;
-            return fail(BC_ERR_ARG, "bc_shape_create: non-finite knot coordinate");
+        for (int i = 0; i < count; i++) {
+            c->shapes.insert(made[i]);
+            out[i] = made[i];
         }
-        float r2;
-        std::memcpy(&r2, &hs[0], sizeof(float));
-        s->rmax = std::sqrt(r2) * (1.0f + 1e-6f);
-        c->shapes.insert(s);
-        *out = s;
         return BC_OK;
     } catch (...) {
         return fail(BC_ERR_INTERNAL, "bc_shape_create: unexpected exception");
     }
+}
+
+bc_status bc_shape_create(bc_ctx_t c, const float *xyz, const int *level, int n, int on_device, bc_shape_t *out)
+{
+    if (!out) return fail(BC_ERR_ARG, "bc_shape_create: null output");
+    return bc_shapes_create(c, 1, &xyz, &level, &n, on_device, out);
 }
 
 bc_status bc_shape_destroy(bc_shape_t s)
@@ -460,9 +536,9 @@ bc_status bc_shape_destroy(bc_shape_t s)
 bc_status bc_sync(bc_ctx_t c)
 {
     if (!c) return fail(BC_ERR_ARG, "bc_sync: null context");
+    CK(cudaMemcpyAsync(c->pin, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    int herr = 0;
-    CK(cudaMemcpy(&herr, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    const int herr = c->pin[0];
     if (herr) {
         CK(cudaMemset(c->err_dev, 0, sizeof(int)));
         if (herr & 4) return fail(BC_ERR_ARG, "a device-resident rotation had zero norm");
@@ -902,6 +978,20 @@ static bc_status sweep_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float 
     return BC_OK;
 }
 
+// The device address of a page-locked host buffer mapped into the device
+// address space (cudaMallocHost, cudaHostAlloc, cudaHostRegister), through
+// which the kernels store a host-resident result directly; null for any other
+// host memory, which goes through a device staging buffer and one copy.
+static float *mapped_host(float *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? (float *)a.devicePointer : nullptr;
+}
+
 static bc_status check_quats(const float *quats, int k, const char *who)
 {
     for (int r = 0; r < k; r++) {
@@ -934,14 +1024,18 @@ static bc_status correlate_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const fl
         for (int r = 0; r < k; r++)
             pairs.push_back(PairDesc{fused ? 0 : -1, 1 + r, (long long)r * N * N * H, (long long)r * N3, r});
         float *dout = out;
+        float *mapped = out_on_device ? nullptr : mapped_host(out);
         cudaError_t e;
-        if (!out_on_device) {
+        if (mapped) {
+            dout = mapped;
+        } else if (!out_on_device) {
             if ((e = c->outbuf.ensure(sizeof(float) * (size_t)k * N3, false, c->stream)) != cudaSuccess) return cuda_fail(e, "outbuf");
             dout = (float *)c->outbuf.p;
         }
         if (bc_status s = enqueue(c, shapes, q, pairs, !fused, dout, nullptr, nullptr, w)) return s;
         if (!out_on_device) {
-            if ((e = cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)k * N3, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            if (!mapped &&
+                (e = cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)k * N3, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
                 return cuda_fail(e, "copy out");
             return bc_sync(c);
         }
@@ -1014,7 +1108,10 @@ bc_status bc_pairs(bc_ctx_t c, const bc_shape_t *As, const bc_shape_t *Bs, const
         unsigned long long *keys = key_bytes ? (unsigned long long *)c->ws.keys.p : nullptr;
         if (keys && (e = cudaMemsetAsync(keys, 0, key_bytes, st)) != cudaSuccess) return cuda_fail(e, "clear keys");
         float *dout = out;
-        if (out && !on_device) {
+        float *mapped = (out && !on_device) ? mapped_host(out) : nullptr;
+        if (mapped) {
+            dout = mapped;
+        } else if (out && !on_device) {
             if ((e = c->outbuf.ensure(sizeof(float) * (size_t)npairs * N3, false, st)) != cudaSuccess) return cuda_fail(e, "outbuf");
             dout = (float *)c->outbuf.p;
         }
@@ -1043,7 +1140,7 @@ bc_status bc_pairs(bc_ctx_t c, const bc_shape_t *As, const bc_shape_t *Bs, const
                     return cuda_fail(e, "copy argmax");
             }
         }
-        if (out && !on_device) {
+        if (out && !on_device && !mapped) {
             if ((e = cudaMemcpyAsync(out, dout, sizeof(float) * (size_t)npairs * N3, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
                 return cuda_fail(e, "copy out");
         }

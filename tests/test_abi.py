@@ -20,7 +20,8 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shape_destroy", "bc_correlate", "bc_sweep", "bc_pairs", "bc_sync",
+    for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shapes_create", "bc_shape_destroy", "bc_correlate", "bc_sweep",
+              "bc_pairs", "bc_sync",
               "bc_last_error", "bc_version", "bc_profile_begin", "bc_profile_end", "bc_stage_name",
               "bc_shape_moments", "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
               "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep", "bc_mlp_param_count", "bc_topk", "bc_sweep_plan", "bc_plan_run",
@@ -69,6 +70,7 @@ def test_null_arguments_are_rejected():
     assert L.bc_destroy(None) == 0
     assert L.bc_shape_destroy(None) == 0
     assert L.bc_shape_create(None, None, None, 0, 0, None) == 1
+    assert L.bc_shapes_create(None, 0, None, None, None, 0, None) == 1
     assert L.bc_correlate(None, None, None, None, 1, None, 1) == 1
     assert L.bc_sync(None) == 1
     assert L.bc_selftest_wait(None) == 1

@@ -178,9 +178,54 @@ def test_host_output_matches_device_output():
                     torch.tensor(wl.A.level, dtype=torch.int32, device="cuda"))
     dev2 = ctx.correlate(sa2, sb, wl.quats).cpu().numpy()
     assert rel_l2(dev2.astype(np.float64), dev.astype(np.float64)) < 1e-6
-    for s in (sa, sb, sa2):
+    # page-locked host output (stored by the last kernel through its device
+    # mapping) and page-locked host knots (copied asynchronously); twice, so
+    # that the second call replays a recorded graph writing the same buffer
+    xp = torch.tensor(wl.A.xyz, dtype=torch.float32).pin_memory()
+    lp = torch.tensor(wl.A.level, dtype=torch.int32).pin_memory()
+    sa3 = ctx.shape(xp, lp)
+    for _ in range(3):
+        pinned = torch.full(dev.shape, float("nan"), dtype=torch.float32).pin_memory()
+        ctx.correlate_host(sa3, sb, wl.quats, pinned)
+        assert rel_l2(pinned.numpy().astype(np.float64), dev.astype(np.float64)) < 1e-6
+    # the caller may overwrite its knot arrays once the shape exists
+    xp.fill_(0.5)
+    again = np.empty_like(dev)
+    ctx.correlate_host(sa3, sb, wl.quats, again)
+    assert rel_l2(again.astype(np.float64), dev.astype(np.float64)) < 1e-6
+    for s in (sa, sb, sa2, sa3):
         s.close()
     ctx.close()
+
+
+def test_batched_shape_upload():
+    # bc_shapes_create: several shapes (one of them empty) in one call give the
+    # same correlations as shapes uploaded one by one; a bad shape anywhere in
+    # the batch fails the whole call and creates nothing
+    bc = bcmod()
+    wl = synth.small_pair(4)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    sa, sb = ctx.shape(wl.A.xyz, wl.A.level), ctx.shape(wl.B.xyz, wl.B.level)
+    ref = ctx.correlate(sa, sb, wl.quats).cpu().numpy()
+    empty = (np.zeros((0, 3), np.float32), np.zeros(0, np.int32))
+    for form in ("host", "device"):
+        pairs = [(wl.A.xyz, wl.A.level), empty, (wl.B.xyz, wl.B.level)]
+        if form == "device":
+            pairs = [(torch.tensor(x, dtype=torch.float32, device="cuda"), torch.tensor(l, dtype=torch.int32, device="cuda"))
+                     for x, l in pairs]
+        a, e, b = ctx.shapes(pairs)
+        assert (a.n, e.n, b.n) == (wl.A.n, 0, wl.B.n)
+        got = ctx.correlate(a, b, wl.quats).cpu().numpy()
+        assert rel_l2(got.astype(np.float64), ref.astype(np.float64)) < 1e-6
+        assert float(ctx.correlate(a, e, wl.quats).abs().max()) == 0.0
+        for s in (a, e, b):
+            s.close()
+    bad = (wl.B.xyz, np.full(wl.B.n, 7, np.int32))
+    with pytest.raises(bc.BallCorrError) as err:
+        ctx.shapes([(wl.A.xyz, wl.A.level), bad])
+    assert err.value.status == 1 and "shape 1" in str(err.value)
+    assert ctx.shapes([]) == []
+    sa.close(); sb.close(); ctx.close()
 
 
 def test_empty_shape_gives_zero():
@@ -249,6 +294,20 @@ def test_invalid_arguments_raise():
     with pytest.raises(bc.BallCorrError) as e:
         ctx.shape(np.full((2, 3), np.nan, np.float32), np.array([0, 1], np.int32))
     assert e.value.status == 1
+    # the same checks on host (pageable and page-locked) and device input
+    bad = [(np.array([[0.1, 0.2, np.inf]], np.float32), np.array([0], np.int32)),
+           (np.zeros((3, 3), np.float32), np.array([0, -1, 1], np.int32))]
+    for x, l in bad:
+        for form in ("host", "pinned", "device"):
+            if form == "host":
+                xx, ll = x, l
+            elif form == "pinned":
+                xx, ll = torch.from_numpy(x).pin_memory(), torch.from_numpy(l).pin_memory()
+            else:
+                xx, ll = torch.from_numpy(x).cuda(), torch.from_numpy(l).cuda()
+            with pytest.raises(bc.BallCorrError) as e:
+                ctx.shape(xx, ll)
+            assert e.value.status == 1, form
     sa = ctx.shape(np.zeros((1, 3), np.float32), np.array([0], np.int32))
     with pytest.raises(bc.BallCorrError) as e:
         ctx.correlate(sa, sa, np.zeros((1, 4), np.float32))

@@ -120,6 +120,14 @@ def test_ragged_pairs_match_oracle(bc):
         assert rel <= REL_TOL
         ref.append(g)
     check_peaks(peak, arg, ref, "ragged pairs")
+    # host outputs: grids into page-locked memory (stored through its device
+    # mapping), peaks into pageable arrays
+    hg = torch.empty((4, N, N, N), dtype=torch.float32).pin_memory()
+    hp, ha = np.empty(4, np.float32), np.empty(4, np.int32)
+    bc.bc_pairs(ctx.handle, [h.handle for h in hA], [h.handle for h in hB], q, 4, hg, hp, ha, 0)
+    for i in range(4):
+        assert np.linalg.norm(hg[i].double().numpy() - ref[i]) / np.linalg.norm(ref[i]) <= REL_TOL
+    check_peaks(hp, ha, ref, "ragged pairs, host outputs")
     for h in hA + hB:
         h.close()
     ctx.close()
