@@ -29,6 +29,7 @@
 //
 // The support-box pruning computes exactly the transforms of the full
 // oversampled grids: the cells it skips hold zeros.
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -294,11 +295,16 @@ cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, i
 // one contiguous 128-byte run per z position.
 //
 // One warp per knot.  Lanes 0..3W-1 evaluate the separable window weights
-// phi(u_a - g) for the W cells of each axis; each lane then takes stencil
-// columns (dx, dz) and adds the W y-cells of a column with 16-byte vector
-// atomics on 4-aligned groups (zero weights fill the unused slots of the first
-// and last group; a group never crosses a 32-row block).  A column that wraps
-// around the period (only when the box spans all n cells) uses scalar atomics.
+// phi(u_a - g) for the W cells of each axis; the W y-cells of a stencil column
+// (dx, dz) are then added with 16-byte vector atomics on 4-aligned groups
+// (zero weights fill the unused slots of the first and last group; a group
+// never crosses a 32-row block).  For W <= 9 a column has at most three groups
+// and the lanes take (column, group) tasks, three per column with dz fastest:
+// the lanes of one vector atomic cover the groups of about ten consecutive
+// columns, which are adjacent 128-byte runs, so each run is updated by one
+// coalesced request.  Wider windows give each lane whole columns.  A column
+// that wraps around the period (only when the box spans all n cells) uses
+// scalar atomics.
 constexpr int SPREAD_WARPS = 8;
 
 __device__ __forceinline__ long long level_box_floats(const InstPlan &p)
@@ -314,7 +320,7 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
     __shared__ float wts[SPREAD_WARPS][3][16];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int W = g.W, W2 = W * W;
-    const float halfW = 0.5f * (float)W, twoOverW = 2.0f / (float)W;
+    const float halfW = 0.5f * (float)W, twoOverW = 2.0f / (float)W, invW = 1.0f / (float)W;
     for (int k = blockIdx.x * SPREAD_WARPS + wib; k < total; k += gridDim.x * SPREAD_WARPS) {
         const float4 v = ku[k];
         const int tag = __float_as_int(v.w);
@@ -334,6 +340,31 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
         float *G = grid + inst[i].grid_off + (long long)level * level_box_floats(p);
         const int iy0 = g0[1] - p.lo[1];
         const bool ywrap = iy0 + W - 1 >= g.n;
+        if (!ywrap && W <= 9) {
+            const int a0 = iy0 & ~3;
+            const int ng = ((iy0 + W - 1) >> 2) - (iy0 >> 2) + 1; // groups per column, at most 3
+            for (int t = lane; t < 3 * W2; t += 32) {
+                const int colm = t / 3, grp = t - 3 * colm;
+                if (grp >= ng) continue;
+                const int dx = __float2int_rz(((float)colm + 0.5f) * invW), dz = colm - dx * W;
+                int ix = g0[0] + dx - p.lo[0];
+                int iz = g0[2] + dz - p.lo[2];
+                if (ix >= g.n) ix -= g.n;
+                if (iz >= g.n) iz -= g.n;
+                const float cw = wts[wib][0][dx] * wts[wib][2][dz];
+                const int a = a0 + 4 * grp, e0 = a - iy0;
+                float4 val;
+                val.x = (e0 >= 0 && e0 < W) ? cw * wts[wib][1][e0] : 0.f;
+                val.y = (e0 + 1 >= 0 && e0 + 1 < W) ? cw * wts[wib][1][e0 + 1] : 0.f;
+                val.z = (e0 + 2 >= 0 && e0 + 2 < W) ? cw * wts[wib][1][e0 + 2] : 0.f;
+                val.w = (e0 + 3 >= 0 && e0 + 3 < W) ? cw * wts[wib][1][e0 + 3] : 0.f;
+                atomicAdd(reinterpret_cast<float4 *>(G + ((long long)ix * nyb * bz + iz) * 32 + (long long)(a >> 5) * bz * 32 +
+                                                     (a & 31)),
+                          val);
+            }
+            __syncwarp();
+            continue;
+        }
         for (int r = lane; r < W2; r += 32) {
             const int dx = r / W, dz = r - dx * W;
             int ix = g0[0] + dx - p.lo[0];
@@ -532,18 +563,41 @@ struct XModes {
     static __device__ __forceinline__ constexpr bool kept(int r) { return r < R / 4 || r >= 3 * R / 4; }
 };
 
+// Per-item table of the level weights the x pass applies: for the item's m_y
+// and its 16 z-modes m_z = 16 ch + c, and a = |m_x| in [0, N/2],
+//   Ts[(lg (N/2 + 1) + a) 16 + c] = T_{l0+lg}(a^2 + m_y^2 + m_z^2) D(a) D(m_y) D(m_z),
+// lg < nl.  The window transform is even, so D(-a) = D(a) and one entry serves
+// m_x = a and m_x = -a; the index a = N/2 addresses m_x = -N/2 in the
+// deconvolution table's FFT order.  Built in shared memory by the whole block,
+// it replaces the table gathers of every level of both spectra.
+template <int NI>
+__device__ __forceinline__ void build_xweights(float *Ts, const Tables &tb, int l0, int nl, int jy, int ch)
+{
+    constexpr int A = NI / 2 + 1;
+    const int my = mode_of(jy, NI);
+    const float dy = tb.deconv[jy];
+    const long long Q = tb.qmax + 1;
+    const int tot = nl * A * CL;
+    for (int e = threadIdx.x; e < tot; e += TB) {
+        const int c = e % CL, a = (e / CL) % A, lg = e / (CL * A);
+        const int mz = ch * CL + c;
+        Ts[e] = tb.ballft[(l0 + lg) * Q + a * a + my * my + mz * mz] * (tb.deconv[a] * dy * tb.deconv[mz]);
+    }
+}
+
+// Ts holds the weights of levels [ts_base, ts_base + G) of the current item;
+// a level outside that range rebuilds it (after the barrier that ends the
+// previous level, before the one that publishes the level's first stage).
 template <int NF, int NI, bool SP, int S>
 __device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF, S>::IT][XModes<NF, S>::R], const Geometry &g,
                                            const Tables &tb, const InstDesc *__restrict__ inst,
                                            const InstPlan *__restrict__ plan, int si, const float2 *__restrict__ y1,
-                                           int jy, int ch, const float2 *tw, float2 *S0, float2 *S1)
+                                           int jy, int ch, const float2 *tw, float2 *S0, float2 *S1, float *Ts, int G,
+                                           int &ts_base)
 {
     using XM = XModes<NF, S>;
-    constexpr int H = NI / 2, N = NI;
+    constexpr int H = NI / 2, N = NI, A = NI / 2 + 1;
     const int L = g.L;
-    const int Q = tb.qmax + 1;
-    const int my = mode_of(jy, N);
-    const float djy = tb.deconv[jy];
 #pragma unroll
     for (int it = 0; it < XM::IT; it++)
 #pragma unroll
@@ -563,17 +617,19 @@ __device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF, S>::IT][XModes
     FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
     in.load(src(0));
     for (int l = 0; l < L; l++) {
+        if (l < ts_base || l >= ts_base + G) {
+            ts_base = l;
+            build_xweights<NI>(Ts, tb, l, min(G, L - l), jy, ch);
+        }
         if constexpr (SP) in.scatter(S0);
         else rr_first<NF, Radix<NF, S>::r0, false, CL, TB>(in, S0);
         __syncthreads();
         if (l + 1 < L) in.load(src(l + 1));
-        const float *T = tb.ballft + (long long)l * Q;
+        const float *Tl = Ts + (l - ts_base) * A * CL;
         auto sink = [&](int it, int r, int c, int pos, float2 v) {
             if (!XM::kept(r)) return;
             const int mx = r < XM::R / 4 ? pos : pos - NF;
-            const int jx = mx < 0 ? mx + N : mx;
-            const int mz = ch * CL + c;
-            const float Mv = T[mx * mx + my * my + mz * mz] * tb.deconv[jx] * djy * tb.deconv[mz];
+            const float Mv = Tl[(mx < 0 ? -mx : mx) * CL + c];
             F[it][r] = make_float2(fmaf(Mv, v.x, F[it][r].x), fmaf(Mv, v.y, F[it][r].y));
         };
         if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
@@ -615,12 +671,13 @@ template <int NF, int NI, bool SP, int S>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan *__restrict__ plan,
         const PairDesc *__restrict__ pairs, int npairs, const float2 *__restrict__ y1,
-        const float2 *__restrict__ fa_cache, float2 *fa_out, float2 *h)
+        const float2 *__restrict__ fa_cache, float2 *fa_out, float2 *h, int G)
 {
     using XM = XModes<NF, S>;
     extern __shared__ float4 sm4[];
     float2 *twF = reinterpret_cast<float2 *>(sm4);
     float2 *twI = twF + NF, *S0 = twI + NI, *S1 = S0 + NF * CL, *FAt = S1 + NF * CL;
+    float *Ts = reinterpret_cast<float *>(FAt + NI * CL); // G levels of build_xweights
     load_twiddles<NF>(twF, tb.tw_n);
     load_twiddles<NI>(twI, tb.tw_N);
     constexpr int H = NI / 2, N = NI;
@@ -633,6 +690,7 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
         for (int it = rs.first(); it < items; it += gridDim.x) {
             const int jy = it / nch, ch = it - jy * nch;
             const int my = mode_of(jy, N);
+            int ts_base = INT_MIN / 2; // no level weights built for this item yet
             // F_A waits in its own tile (each thread reads back only what it wrote)
             // while F_B is accumulated in registers.
             {
@@ -642,7 +700,7 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
                         FAt[jx * CL + c] = fa_cache[((long long)jx * N + jy) * H + ch * CL + c];
                     });
                 } else {
-                    spectrum_x<NF, NI, SP, S>(FA, g, tb, inst, plan, pr.a, y1, jy, ch, twF, S0, S1);
+                    spectrum_x<NF, NI, SP, S>(FA, g, tb, inst, plan, pr.a, y1, jy, ch, twF, S0, S1, Ts, G, ts_base);
                     for_kept<NF, NI, S>([&](int i2, int r, int c, int jx) { FAt[jx * CL + c] = FA[i2][r]; });
                 }
             }
@@ -653,7 +711,7 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
                 continue;
             }
             float2 FB[XM::IT][XM::R];
-            spectrum_x<NF, NI, SP, S>(FB, g, tb, inst, plan, pr.b, y1, jy, ch, twF, S0, S1);
+            spectrum_x<NF, NI, SP, S>(FB, g, tb, inst, plan, pr.b, y1, jy, ch, twF, S0, S1, Ts, G, ts_base);
             for_kept<NF, NI, S>([&](int i2, int r, int c, int jx) {
                 const int mx = mode_of(jx, N), mz = ch * CL + c;
                 float2 v = make_float2(0.f, 0.f);
@@ -900,11 +958,17 @@ static cudaError_t fft_x_t(const Geometry &g, const Tables &t, const InstDesc *i
 {
     if (!SP && S == 0 && (g.sched & 4))
         return fft_x_t<NF, NI, false, 1>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
-    const size_t smem = sizeof(float2) * (NF + NI + 2 * NF * CL + NI * CL);
+    // level weights for as many levels as fit beside the tiles at the kernel's
+    // blocks per SM (two up to NF = 256, else one): all of them in the usual cases
+    const size_t base = sizeof(float2) * (NF + NI + 2 * NF * CL + NI * CL);
+    const size_t per_level = sizeof(float) * (NI / 2 + 1) * CL;
+    const size_t room = (NF <= 256 ? 228 * 1024 / 2 : 228 * 1024) - 1024 - base;
+    const int G = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.L, room / per_level));
+    const size_t smem = base + per_level * G;
     cudaError_t e = set_smem(k_fft_x<NF, NI, SP, S>, smem);
     if (e != cudaSuccess) return e;
     k_fft_x<NF, NI, SP, S><<<resident_blocks(k_fft_x<NF, NI, SP, S>, smem, nsm), TB, smem, s>>>(
-        g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h);
+        g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, G);
     return cudaGetLastError();
 }
 
