@@ -318,6 +318,7 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
 {
     const float inv_scaled_i0beta = consts[0];
     __shared__ float wts[SPREAD_WARPS][3][16];
+    __shared__ float4 wy4[SPREAD_WARPS][3];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int W = g.W, W2 = W * W;
     const float halfW = 0.5f * (float)W, twoOverW = 2.0f / (float)W, invW = 1.0f / (float)W;
@@ -341,26 +342,43 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
         const int iy0 = g0[1] - p.lo[1];
         const bool ywrap = iy0 + W - 1 >= g.n;
         if (!ywrap && W <= 9) {
+            // per knot: the y-group weight vectors and the address of stencil cell
+            // (0, 0, group); a column's x and z offsets then add linearly unless
+            // the stencil crosses the end of a full-period box
             const int a0 = iy0 & ~3;
             const int ng = ((iy0 + W - 1) >> 2) - (iy0 >> 2) + 1; // groups per column, at most 3
+            const int ix0 = g0[0] - p.lo[0], iz0 = g0[2] - p.lo[2];
+            const bool xzwrap = ix0 + W - 1 >= g.n || iz0 + W - 1 >= g.n;
+            if (lane < 3) {
+                const int e0 = a0 + 4 * lane - iy0;
+                float4 gv;
+                gv.x = (e0 >= 0 && e0 < W) ? wts[wib][1][e0] : 0.f;
+                gv.y = (e0 + 1 >= 0 && e0 + 1 < W) ? wts[wib][1][e0 + 1] : 0.f;
+                gv.z = (e0 + 2 >= 0 && e0 + 2 < W) ? wts[wib][1][e0 + 2] : 0.f;
+                gv.w = (e0 + 3 >= 0 && e0 + 3 < W) ? wts[wib][1][e0 + 3] : 0.f;
+                wy4[wib][lane] = gv;
+            }
+            __syncwarp();
+            const long long xstride = (long long)nyb * bz * 32;
+            float *G0 = G + (long long)ix0 * xstride + (long long)iz0 * 32;
             for (int t = lane; t < 3 * W2; t += 32) {
                 const int colm = t / 3, grp = t - 3 * colm;
                 if (grp >= ng) continue;
                 const int dx = __float2int_rz(((float)colm + 0.5f) * invW), dz = colm - dx * W;
-                int ix = g0[0] + dx - p.lo[0];
-                int iz = g0[2] + dz - p.lo[2];
-                if (ix >= g.n) ix -= g.n;
-                if (iz >= g.n) iz -= g.n;
+                const int a = a0 + 4 * grp;
+                const long long yoff = (long long)(a >> 5) * bz * 32 + (a & 31);
+                float *cell;
+                if (!xzwrap) {
+                    cell = G0 + dx * xstride + dz * 32 + yoff;
+                } else {
+                    int ix = ix0 + dx, iz = iz0 + dz;
+                    if (ix >= g.n) ix -= g.n;
+                    if (iz >= g.n) iz -= g.n;
+                    cell = G + (long long)ix * xstride + (long long)iz * 32 + yoff;
+                }
                 const float cw = wts[wib][0][dx] * wts[wib][2][dz];
-                const int a = a0 + 4 * grp, e0 = a - iy0;
-                float4 val;
-                val.x = (e0 >= 0 && e0 < W) ? cw * wts[wib][1][e0] : 0.f;
-                val.y = (e0 + 1 >= 0 && e0 + 1 < W) ? cw * wts[wib][1][e0 + 1] : 0.f;
-                val.z = (e0 + 2 >= 0 && e0 + 2 < W) ? cw * wts[wib][1][e0 + 2] : 0.f;
-                val.w = (e0 + 3 >= 0 && e0 + 3 < W) ? cw * wts[wib][1][e0 + 3] : 0.f;
-                atomicAdd(reinterpret_cast<float4 *>(G + ((long long)ix * nyb * bz + iz) * 32 + (long long)(a >> 5) * bz * 32 +
-                                                     (a & 31)),
-                          val);
+                const float4 gv = wy4[wib][grp];
+                atomicAdd(reinterpret_cast<float4 *>(cell), make_float4(cw * gv.x, cw * gv.y, cw * gv.z, cw * gv.w));
             }
             __syncwarp();
             continue;
