@@ -512,9 +512,26 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
 // Item: (level, ix) plane and a chunk of 16 z-modes.  Row iy of the chunk (16
 // complex = 128 bytes) is position (pos0_y + iy) mod n of the lines; the
 // transform runs along y; m_y in (-N/2, N/2) is kept at FFT index j (j = N/2,
-// m_y = -N/2, stored as zero).  First-stage inputs come straight from z1 and
-// last-stage outputs go straight to y1; the next item is loaded while the
+// m_y = -N/2, stored as zero).  Last-stage outputs go straight to y1.  With a
+// two-stage radix schedule (FP32) the item's rows are fetched into one of two
+// shared-memory staging tiles with asynchronous 16-byte copies (zero-filled
+// outside the support box) one whole item ahead; otherwise first-stage inputs
+// come straight from z1 into registers and the next item is loaded while the
 // current one finishes.
+template <int NF, bool SP, int S>
+struct YStaged {
+    static constexpr bool on = !SP && Radix<NF, S>::r2 == 1;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, bool valid)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// all but the most recently committed group have landed (for this thread)
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 template <int NF, bool SP, int S>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
@@ -527,8 +544,56 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     constexpr int H = NF / 4, N = NF / 2;
     const int L = g.L;
     constexpr int nch = H / CL;
-    FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
     RotStart rs;
+    if constexpr (YStaged<NF, SP, S>::on) {
+        // staging tiles: B(0) = S1 (unused by a two-stage schedule) and B(1) after it
+        auto B = [&](int k) { return S1 + k * (NF * CL); };
+        for (int i = 0; i < ninst; i++) {
+            const InstPlan p = plan[i];
+            if (p.b[0] == 0) continue;
+            const int b0 = p.b[0], b1 = p.b[1], py = p.pos0[1];
+            const int items = L * b0 * nch;
+            const InstDesc d = inst[i];
+            // rows of item `it` into tile dst: 16-byte chunks (position, two lines)
+            auto fetch = [&](int it, float2 *dst) {
+                const int lx = it / nch, ch = it - lx * nch;
+                const float2 *base = z1 + d.z1_off + (long long)lx * b1 * H + ch * CL;
+                for (int q = threadIdx.x; q < NF * CL / 2; q += TB) {
+                    const int pos = q / (CL / 2), cc = (q % (CL / 2)) * 2;
+                    int iy = pos - py;
+                    if (iy < 0) iy += NF;
+                    const bool ok = iy < b1;
+                    cp_async16(dst + pos * CL + cc, ok ? base + (long long)iy * H + cc : base, ok);
+                }
+            };
+            int it = rs.first();
+            if (it < items) fetch(it, B(0));
+            cp_async_commit();
+            for (int k = 0; it < items; it += gridDim.x, k ^= 1) {
+                // B(k ^ 1) was last read by the first stage of the previous item
+                if (it + (int)gridDim.x < items) fetch(it + gridDim.x, B(k ^ 1));
+                cp_async_commit();
+                cp_async_wait_prev();
+                __syncthreads();
+                il_stage<NF, Radix<NF, S>::r0, 1, false, CL, TB>(B(k), S0, tw);
+                __syncthreads();
+                const int lx = it / nch, ch = it - lx * nch;
+                float2 *Y = y1 + d.y1_off + (long long)lx * N * H + ch * CL;
+                auto sink = [&](int, int, int c, int pos, float2 v) {
+                    int jy;
+                    if (pos < N / 2) jy = pos;
+                    else if (pos >= NF - N / 2) jy = pos - NF + N;
+                    else return;
+                    Y[(long long)jy * H + c] = jy == N / 2 ? make_float2(0.f, 0.f) : v;
+                };
+                rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
+                __syncthreads();
+            }
+            rs.rot += items;
+        }
+        return;
+    }
+    FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
     for (int i = 0; i < ninst; i++) {
         const InstPlan p = plan[i];
         if (p.b[0] == 0) continue;
@@ -944,7 +1009,7 @@ static cudaError_t fft_y_t(const Geometry &g, const Tables &t, const InstDesc *i
                            const float2 *z1, float2 *y1, int nsm, cudaStream_t s)
 {
     if (!SP && S == 0 && (g.sched & 2)) return fft_y_t<NF, false, 1>(g, t, inst, ninst, plan, z1, y1, nsm, s);
-    const size_t smem = sizeof(float2) * (NF + 2 * NF * CL);
+    const size_t smem = sizeof(float2) * (NF + (YStaged<NF, SP, S>::on ? 3 : 2) * NF * CL);
     cudaError_t e = set_smem(k_fft_y<NF, SP, S>, smem);
     if (e != cudaSuccess) return e;
     k_fft_y<NF, SP, S><<<resident_blocks(k_fft_y<NF, SP, S>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, z1, y1);
