@@ -103,6 +103,9 @@ bc_status bc_shape_create(bc_ctx_t ctx, const float *xyz, const int *level, int 
  * (bc_shape_create is the count = 1 case): shape i has n[i] knots with
  * centres xyz[i] and level ids level[i], arrays as in bc_shape_create, all
  * device (on_device = 1) or all host (0) memory; out[i] receives its handle.
+ * Host arrays in page-locked memory mapped into the device address space are
+ * read by the packing kernel directly; other host arrays are staged on the
+ * device first.
  * On any error no shape is created (every out[i] is NULL) and the message
  * names the first failing shape.  Errors as bc_shape_create, and BC_ERR_ARG
  * for count < 0 or null arrays. */

@@ -404,6 +404,19 @@ bc_status bc_destroy(bc_ctx_t c)
     }
 }
 
+// The device address of a page-locked host buffer mapped into the device
+// address space (cudaMallocHost, cudaHostAlloc, cudaHostRegister), through
+// which kernels read or write it directly; null for any other host memory.
+static void *mapped_host_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 bc_status bc_shapes_create(bc_ctx_t c, int count, const float *const *xyz, const int *const *level, const int *n,
                            int on_device, bc_shape_t *out)
 {
@@ -411,13 +424,26 @@ bc_status bc_shapes_create(bc_ctx_t c, int count, const float *const *xyz, const
         if (!c || !out || count < 0 || (count > 0 && (!xyz || !level || !n)))
             return fail(BC_ERR_ARG, "bc_shapes_create: null argument or count < 0");
         for (int i = 0; i < count; i++) out[i] = nullptr;
-        size_t staged = 0; // staging bytes of the host-resident shapes
+        // Host arrays in mapped page-locked memory are read by the packing kernel
+        // through their device addresses; other host arrays are copied to a device
+        // staging area first.
+        std::vector<const float *> mx(count, nullptr);
+        std::vector<const int *> ml(count, nullptr);
+        size_t staged = 0; // staging bytes of the host-resident shapes that are not mapped
         for (int i = 0; i < count; i++) {
             const std::string who = "bc_shape_create (shape " + std::to_string(i) + "): ";
             if (n[i] < 0) return fail(BC_ERR_ARG, who + "n < 0");
             if (n[i] > 0 && (!xyz[i] || !level[i])) return fail(BC_ERR_ARG, who + "null knot arrays");
             if (n[i] >= (1 << 26)) return fail(BC_ERR_ARG, who + "too many knots");
-            if (!on_device) staged += (sizeof(float) * 3 + sizeof(int)) * (size_t)n[i];
+            if (!on_device && n[i] > 0) {
+                mx[i] = (const float *)mapped_host_ptr(xyz[i]);
+                ml[i] = (const int *)mapped_host_ptr(level[i]);
+                if (!mx[i] || !ml[i]) {
+                    mx[i] = nullptr;
+                    ml[i] = nullptr;
+                    staged += (sizeof(float) * 3 + sizeof(int)) * (size_t)n[i];
+                }
+            }
         }
         std::vector<bc_shape_t> made(count, nullptr);
         cudaStream_t st = c->stream;
@@ -462,7 +488,10 @@ bc_status bc_shapes_create(bc_ctx_t c, int count, const float *const *xyz, const
                 return bail(e, "cudaMallocAsync knots");
             const float *dx = xyz[i];
             const int *dl = level[i];
-            if (!on_device) {
+            if (mx[i]) {
+                dx = mx[i];
+                dl = ml[i];
+            } else if (!on_device) {
                 float *sx = (float *)sp;
                 int *sl = (int *)(sx + 3 * (size_t)ni);
                 sp += (sizeof(float) * 3 + sizeof(int)) * (size_t)ni;
@@ -978,19 +1007,10 @@ static bc_status sweep_impl(bc_ctx_t c, bc_shape_t A, bc_shape_t B, const float 
     return BC_OK;
 }
 
-// The device address of a page-locked host buffer mapped into the device
-// address space (cudaMallocHost, cudaHostAlloc, cudaHostRegister), through
-// which the kernels store a host-resident result directly; null for any other
-// host memory, which goes through a device staging buffer and one copy.
-static float *mapped_host(float *p)
-{
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    return a.type == cudaMemoryTypeHost ? (float *)a.devicePointer : nullptr;
-}
+// A host-resident result in mapped page-locked memory is stored by the kernels
+// directly; any other host memory goes through a device staging buffer and one
+// copy.
+static float *mapped_host(float *p) { return (float *)mapped_host_ptr(p); }
 
 static bc_status check_quats(const float *quats, int k, const char *who)
 {
