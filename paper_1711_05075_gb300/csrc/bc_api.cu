@@ -449,6 +449,8 @@ bc_status bc_shapes_create(bc_ctx_t c, int count, const float *const *xyz, const
         cudaStream_t st = c->stream;
         void *staging = nullptr;
         auto drop = [&]() {
+            // queued copies and packing kernels may still read the caller's arrays
+            cudaStreamSynchronize(st);
             if (staging) cudaFreeAsync(staging, st);
             for (bc_shape_t s : made)
                 if (s) {
