@@ -116,7 +116,10 @@ def test_rotations(k):
             check(got[r], refs[r], what=f"rotation {r} of {k}, spread {sp}")
 
 
-@pytest.mark.parametrize("N,W,n", [(32, 8, 300), (64, 8, 400), (96, 8, 500), (128, 6, 300)])
+# W = 9 is the widest window whose stencil columns the spreading kernel splits
+# into (column, 4-cell group) tasks; W = 10 takes the whole-column path.
+@pytest.mark.parametrize("N,W,n", [(32, 8, 300), (64, 8, 400), (96, 8, 500), (128, 6, 300), (32, 9, 300),
+                                   (32, 10, 300)])
 def test_grid_sizes(N, W, n):
     A = synth.ellipsoid_shape(n, 5, synth.RADII_4, synth.PROBS_4)
     B = synth.torus_shape(n, 6, synth.RADII_4, synth.PROBS_4)
