@@ -591,45 +591,45 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
             }
             rs.rot += items;
         }
-        return;
-    }
-    FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
-    for (int i = 0; i < ninst; i++) {
-        const InstPlan p = plan[i];
-        if (p.b[0] == 0) continue;
-        const int b0 = p.b[0], b1 = p.b[1], py = p.pos0[1];
-        const int items = L * b0 * nch;
-        const InstDesc d = inst[i];
-        auto src = [&](int it) {
-            const int lx = it / nch, ch = it - lx * nch;
-            const float2 *base = z1 + d.z1_off + (long long)lx * b1 * H + ch * CL;
-            return [=](int c, int pos) {
-                int iy = pos - py;
-                if (iy < 0) iy += NF;
-                return iy < b1 ? base[(long long)iy * H + c] : make_float2(0.f, 0.f);
+    } else {
+        FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
+        for (int i = 0; i < ninst; i++) {
+            const InstPlan p = plan[i];
+            if (p.b[0] == 0) continue;
+            const int b0 = p.b[0], b1 = p.b[1], py = p.pos0[1];
+            const int items = L * b0 * nch;
+            const InstDesc d = inst[i];
+            auto src = [&](int it) {
+                const int lx = it / nch, ch = it - lx * nch;
+                const float2 *base = z1 + d.z1_off + (long long)lx * b1 * H + ch * CL;
+                return [=](int c, int pos) {
+                    int iy = pos - py;
+                    if (iy < 0) iy += NF;
+                    return iy < b1 ? base[(long long)iy * H + c] : make_float2(0.f, 0.f);
+                };
             };
-        };
-        int it = rs.first();
-        if (it < items) in.load(src(it));
-        for (; it < items; it += gridDim.x) {
-            const int lx = it / nch, ch = it - lx * nch;
-            if constexpr (SP) in.scatter(S0);
-            else rr_first<NF, Radix<NF, S>::r0, false, CL, TB>(in, S0);
-            __syncthreads();
-            if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
-            float2 *Y = y1 + d.y1_off + (long long)lx * N * H + ch * CL;
-            auto sink = [&](int, int, int c, int pos, float2 v) {
-                int jy;
-                if (pos < N / 2) jy = pos;
-                else if (pos >= NF - N / 2) jy = pos - NF + N;
-                else return;
-                Y[(long long)jy * H + c] = jy == N / 2 ? make_float2(0.f, 0.f) : v;
-            };
-            if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
-            else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
-            __syncthreads();
+            int it = rs.first();
+            if (it < items) in.load(src(it));
+            for (; it < items; it += gridDim.x) {
+                const int lx = it / nch, ch = it - lx * nch;
+                if constexpr (SP) in.scatter(S0);
+                else rr_first<NF, Radix<NF, S>::r0, false, CL, TB>(in, S0);
+                __syncthreads();
+                if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
+                float2 *Y = y1 + d.y1_off + (long long)lx * N * H + ch * CL;
+                auto sink = [&](int, int, int c, int pos, float2 v) {
+                    int jy;
+                    if (pos < N / 2) jy = pos;
+                    else if (pos >= NF - N / 2) jy = pos - NF + N;
+                    else return;
+                    Y[(long long)jy * H + c] = jy == N / 2 ? make_float2(0.f, 0.f) : v;
+                };
+                if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
+                else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
+                __syncthreads();
+            }
+            rs.rot += items;
         }
-        rs.rot += items;
     }
 }
 
