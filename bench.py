@@ -595,6 +595,8 @@ def run_learned(args):
     hits, hits_tol, rand_hits, regrets, test_mse = 0, 0, 0, [], []
     ms_ex, ms_learn = [], []
     hits_ref, hits_ref_tol, ms_ref = 0, 0, []
+    hits_tta, hits_tta_tol, ms_tta = 0, 0, []
+    orients = synth.shoemake_quaternions(synth.SplitMix64(600000), args.tta).astype(np.float32) if args.tta > 0 else None
     for seed in range(1001, 1001 + args.eval_pairs):
         A, B = pair(seed)
         hA, hB = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
@@ -623,6 +625,19 @@ def run_learned(args):
         top = p[list(chosen)].max()
         regrets.append(float(top / p[best]))
         hits_tol += top >= p[best] * (1 - 1e-3)
+        if args.tta > 0:
+            # orientation averaging (bc_learned_sweep_avg): (S A, S R B) has the same peak
+            # as (A, R B); the network's scores for args.tta random orientations S of the
+            # receptor are averaged with the plain ones before the top-k is taken
+            e3, e4 = ev(), ev()
+            e3.record(stream)
+            it_, pt_, _, _ = bc.learned_sweep(ctx, net, hA, hB, qd, K, orientations=orients)
+            e4.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_tta.append(e3.elapsed_time(e4))
+            chosen_t = it_.cpu().numpy()
+            hits_tta += best in set(chosen_t.tolist())
+            hits_tta_tol += float(pt_.max()) >= p[best] * (1 - 1e-3)
         rnd = set(np.argsort(synth.SplitMix64(seed + 400000).uniform(R))[:K].tolist())
         rand_hits += best in rnd
         if args.refine > 0:
@@ -695,6 +710,12 @@ def run_learned(args):
                    "ms": float(np.mean(ms_ref)), "effective_poses_s": poses / (np.mean(ms_ref) * 1e-3)}
         if args.refine > 0 else None,
         "recall_within_1e-3_of_best": hits_tol / args.eval_pairs,
+        "orientation_averaging": {"orientations": args.tta, "recall_best": hits_tta / args.eval_pairs,
+                                  "recall_within_1e-3": hits_tta_tol / args.eval_pairs,
+                                  "ms_learned_sweep": float(np.mean(ms_tta)),
+                                  "effective_poses_s": poses / (np.mean(ms_tta) * 1e-3),
+                                  "vs_plain": poses / (np.mean(ms_tta) * 1e-3) / plain}
+        if args.tta > 0 else None,
         "random_topk_recall": rand_hits / args.eval_pairs,
         "mean_peak_ratio_topk_over_best": float(np.mean(regrets)),
         "min_peak_ratio_topk_over_best": float(np.min(regrets)),
@@ -750,6 +771,8 @@ def main():
     ap.add_argument("--refine", type=int, default=0,
                     help="of the top-k full correlations, spend this many on the nearest rotations of the best peaks")
     ap.add_argument("--refine-seeds", type=int, default=8)
+    ap.add_argument("--tta", type=int, default=16,
+                    help="learned workload: also rank by scores averaged over this many random receptor orientations")
     ap.add_argument("--target-alpha", type=float, default=0.0,
                     help="train on exp(alpha (z - 3)) of the standardised peak z instead of z (0: z)")
     ap.add_argument("--augment", type=int, default=32,

@@ -383,6 +383,19 @@ bc_status bc_mlp_state(bc_mlp_t net, float *params, float *adam_m, float *adam_v
 bc_status bc_learned_sweep(bc_ctx_t ctx, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
                            int topk, int *idx, float *peak, int *argmax, float *scores);
 
+/* Learned sweep with orientation averaging: the score of rotation R is the
+ * mean of the network's scores for (A, R B) and, for each of the norient host
+ * quaternions s_k (w, x, y, z), for (S_k A, S_k R B), which has the same peak
+ * over translations (S_k A's moments come from its spectrum, computed on the
+ * device; the rotations S_k R are composed on the device).  scores, when not
+ * NULL, receives the averaged scores; the rest is bc_learned_sweep, which is
+ * the norient = 0 case.  Asynchronous.  Errors as bc_learned_sweep, and
+ * BC_ERR_ARG for norient < 0, norient > 0 with null orients, a zero
+ * orientation quaternion or an empty shape. */
+bc_status bc_learned_sweep_avg(bc_ctx_t ctx, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
+                               int topk, const float *orients, int norient, int *idx, float *peak, int *argmax,
+                               float *scores);
+
 /* Top-k selection: idx[0..k) (device) = indices of the k largest of scores[0..n)
  * (device), largest first, equal scores ordered by lower index.  n <= BC_TOPK_MAX.
  * Asynchronous on ctx's stream.  Errors: BC_ERR_ARG, BC_ERR_CUDA. */

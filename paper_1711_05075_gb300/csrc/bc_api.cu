@@ -1334,19 +1334,26 @@ bc_status bc_plan_destroy(bc_plan_t pl)
     return BC_OK;
 }
 
+// Moments of S rotated by the host quaternion rot (null: not rotated): the
+// shape's spectrum through the correlation pipeline, then the mode magnitudes.
+static bc_status shape_moments(bc_ctx_t c, bc_shape_t S, const float *rot, float *out)
+{
+    std::vector<bc_shape_t> shapes(1, S);
+    std::vector<const float *> q(1, rot);
+    std::vector<PairDesc> pairs(1, PairDesc{0, -1, 0, 0, 0});
+    if (bc_status s = enqueue(c, shapes, q, pairs, true, nullptr, nullptr)) return s;
+    cudaError_t e = launch_moments((const float2 *)c->ws.fa.p, c->modes, BC_MOMENTS, c->g.N, c->g.H, out, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments");
+    return BC_OK;
+}
+
 bc_status bc_shape_moments(bc_ctx_t c, bc_shape_t S, float *out)
 {
     try {
         if (!c || !S || !out) return fail(BC_ERR_ARG, "bc_shape_moments: null argument");
         if (S->ctx != c) return fail(BC_ERR_ARG, "bc_shape_moments: shape belongs to another context");
         if (S->n == 0) return fail(BC_ERR_ARG, "bc_shape_moments: empty shape (f(0) = 0)");
-        std::vector<bc_shape_t> shapes(1, S);
-        std::vector<const float *> q(1, nullptr);
-        std::vector<PairDesc> pairs(1, PairDesc{0, -1, 0, 0, 0});
-        if (bc_status s = enqueue(c, shapes, q, pairs, true, nullptr, nullptr)) return s;
-        cudaError_t e = launch_moments((const float2 *)c->ws.fa.p, c->modes, BC_MOMENTS, c->g.N, c->g.H, out, c->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "moments");
-        return BC_OK;
+        return shape_moments(c, S, nullptr, out);
     } catch (...) {
         return fail(BC_ERR_INTERNAL, "bc_shape_moments: unexpected exception");
     }
@@ -1361,8 +1368,9 @@ bc_status bc_topk(bc_ctx_t c, const float *scores, int n, int k, int *idx)
     return BC_OK;
 }
 
-bc_status bc_learned_sweep(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n, int topk,
-                           int *idx, float *peak, int *argmax, float *scores)
+bc_status bc_learned_sweep_avg(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
+                               int topk, const float *orients, int norient, int *idx, float *peak, int *argmax,
+                               float *scores)
 {
     try {
         if (!c || !net || !A || !B || !quats || !idx || !peak || !argmax)
@@ -1370,23 +1378,49 @@ bc_status bc_learned_sweep(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B,
         if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, "bc_learned_sweep: shapes belong to another context");
         if (n < 1 || n > BC_TOPK_MAX) return fail(BC_ERR_ARG, "bc_learned_sweep: n must be in [1, 16384]");
         if (topk < 1 || topk > n) return fail(BC_ERR_ARG, "bc_learned_sweep: topk must be in [1, n]");
+        if (norient < 0 || (norient > 0 && !orients))
+            return fail(BC_ERR_ARG, "bc_learned_sweep: norient < 0, or orientations missing");
+        if (A->n == 0 || B->n == 0) return fail(BC_ERR_ARG, "bc_learned_sweep: empty shape (f(0) = 0)");
+        if (norient > 0)
+            if (bc_status s = check_quats(orients, norient, "bc_learned_sweep")) return s;
         cudaStream_t st = c->stream;
         cudaError_t e;
-        // scratch: moments (2 x 64), features (n x 144), scores (n), selected rotations (topk x 4)
-        const size_t fbytes = sizeof(float) * (2 * BC_MOMENTS + (size_t)n * 144 + n + 4 * (size_t)topk);
+        // scratch: moments (2 x 64), features (n x 144), scores (n), score sum (n),
+        // composed rotations (n x 4), selected rotations (topk x 4)
+        const size_t fbytes = sizeof(float) * (2 * BC_MOMENTS + (size_t)n * 144 + 2 * (size_t)n + 4 * (size_t)n +
+                                               4 * (size_t)topk);
         if ((e = c->learn.ensure(fbytes, false, st)) != cudaSuccess) return cuda_fail(e, "learned scratch");
         float *fa = (float *)c->learn.p, *fb = fa + BC_MOMENTS, *X = fb + BC_MOMENTS;
-        float *sc = X + (size_t)n * 144, *qsel = sc + n;
-        if (bc_status s = bc_shape_moments(c, A, fa)) return s;
-        if (bc_status s = bc_shape_moments(c, B, fb)) return s;
+        float *sc = X + (size_t)n * 144, *acc = sc + n, *qs = acc + n, *qsel = qs + 4 * (size_t)n;
+        float *total = scores ? scores : acc;
+        if (bc_status s = shape_moments(c, A, nullptr, fa)) return s;
+        if (bc_status s = shape_moments(c, B, nullptr, fb)) return s;
         if (bc_status s = bc_mlp_features(net, quats, n, fa, fb, X)) return s;
-        if (bc_status s = bc_mlp_predict(net, X, n, scores ? scores : sc)) return s;
-        if ((e = launch_topk(scores ? scores : sc, n, topk, idx, st)) != cudaSuccess) return cuda_fail(e, "top-k");
+        if (bc_status s = bc_mlp_predict(net, X, n, total)) return s;
+        // (S A, S R B) has the same peak over translations as (A, R B): score the
+        // rotations S R of B against the receptor turned by S, and average
+        for (int k = 0; k < norient; k++) {
+            const float *s4 = orients + 4 * (size_t)k;
+            if (bc_status s = shape_moments(c, A, s4, fa)) return s;
+            if ((e = launch_compose_quats(s4, quats, n, qs, st)) != cudaSuccess) return cuda_fail(e, "compose rotations");
+            if (bc_status s = bc_mlp_features(net, qs, n, fa, fb, X)) return s;
+            if (bc_status s = bc_mlp_predict(net, X, n, sc)) return s;
+            if ((e = launch_axpby(total, sc, n, 1.f, 1.f, st)) != cudaSuccess) return cuda_fail(e, "score sum");
+        }
+        if (norient > 0 && (e = launch_axpby(total, total, n, 1.f / (float)(norient + 1), 0.f, st)) != cudaSuccess)
+            return cuda_fail(e, "score mean");
+        if ((e = launch_topk(total, n, topk, idx, st)) != cudaSuccess) return cuda_fail(e, "top-k");
         if ((e = launch_gather_quats(quats, idx, topk, qsel, st)) != cudaSuccess) return cuda_fail(e, "gather rotations");
         return sweep_impl(c, A, B, nullptr, qsel, topk, 0, peak, argmax, 1);
     } catch (...) {
         return fail(BC_ERR_INTERNAL, "bc_learned_sweep: unexpected exception");
     }
+}
+
+bc_status bc_learned_sweep(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n, int topk,
+                           int *idx, float *peak, int *argmax, float *scores)
+{
+    return bc_learned_sweep_avg(c, net, A, B, quats, n, topk, nullptr, 0, idx, peak, argmax, scores);
 }
 
 // ------------------------------------------------------------------ tuning

@@ -143,6 +143,10 @@ cudaError_t launch_query_eval(const float2 *ghat, const int4 *modes, int count, 
 // Learned-proposal helpers (bc_mlp.cu).
 cudaError_t launch_topk(const float *scores, int n, int k, int *idx, cudaStream_t s);
 cudaError_t launch_gather_quats(const float *q, const int *idx, int k, float *out, cudaStream_t s);
+// out_i = sq * q_i (sq: 4 host floats, q and out: n x 4 device floats)
+cudaError_t launch_compose_quats(const float *sq, const float *q, int n, float *out, cudaStream_t s);
+// y = alpha y + beta x (device, n)
+cudaError_t launch_axpby(float *y, const float *x, int n, float alpha, float beta, cudaStream_t s);
 // out[i] = |F(m_i)| / F(0) for the modes[i] = (m_x, m_y, m_z), i < count, of a cached half spectrum.
 cudaError_t launch_moments(const float2 *F, const int *modes, int count, int N, int H, float *out, cudaStream_t s);
 

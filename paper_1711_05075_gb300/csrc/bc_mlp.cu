@@ -307,6 +307,28 @@ __global__ void k_gather_quats(const float *__restrict__ q, const int *__restric
     if (i < 4 * k) out[i] = q[4 * (long long)idx[i >> 2] + (i & 3)];
 }
 
+// out_i = s * q_i (Hamilton product: rotation by q_i, then by s), quaternions (w, x, y, z)
+__global__ void k_compose_quats(float4 sq, const float *__restrict__ q, int n, float *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float w2 = q[4 * (long long)i], x2 = q[4 * (long long)i + 1], y2 = q[4 * (long long)i + 2],
+                z2 = q[4 * (long long)i + 3];
+    const float w1 = sq.x, x1 = sq.y, y1 = sq.z, z1 = sq.w;
+    float *o = out + 4 * (long long)i;
+    o[0] = w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2;
+    o[1] = w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2;
+    o[2] = w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2;
+    o[3] = w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2;
+}
+
+// y = alpha y + beta x
+__global__ void k_axpby(float *y, const float *__restrict__ x, int n, float alpha, float beta)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = alpha * y[i] + beta * x[i];
+}
+
 } // namespace
 
 // ------------------------------------------------------------------ network object
@@ -437,6 +459,20 @@ cudaError_t bc::launch_gather_quats(const float *q, const int *idx, int k, float
 {
     if (k <= 0) return cudaSuccess;
     k_gather_quats<<<(4 * k + 255) / 256, 256, 0, s>>>(q, idx, k, out);
+    return cudaGetLastError();
+}
+
+cudaError_t bc::launch_compose_quats(const float *sq, const float *q, int n, float *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_compose_quats<<<(n + 255) / 256, 256, 0, s>>>(make_float4(sq[0], sq[1], sq[2], sq[3]), q, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t bc::launch_axpby(float *y, const float *x, int n, float alpha, float beta, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_axpby<<<(n + 255) / 256, 256, 0, s>>>(y, x, n, alpha, beta);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ def test_header_declares_the_boundary():
               "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep", "bc_mlp_param_count", "bc_topk", "bc_sweep_plan", "bc_plan_run",
               "bc_plan_destroy", "bc_score", "bc_score_sweep", "bc_query_create", "bc_query_eval", "bc_query_destroy",
               "bc_lift_create", "bc_lift_correlate", "bc_lift_destroy", "bc_get_tuning", "bc_set_tuning", "bc_autotune",
-              "bc_correlate_noalloc", "bc_selftest_wait"):
+              "bc_correlate_noalloc", "bc_selftest_wait", "bc_learned_sweep_avg"):
         assert f in names
 
 
@@ -94,6 +94,7 @@ def test_null_arguments_are_rejected():
     assert L.bc_get_tuning(None, None) == 1
     assert L.bc_set_tuning(None, None) == 1
     assert L.bc_autotune(None, None, None, 0, None) == 1
+    assert L.bc_learned_sweep_avg(None, None, None, None, None, 1, 1, None, 0, None, None, None, None) == 1
 
 
 @pytest.mark.parametrize("kw,status", [

@@ -170,3 +170,42 @@ def test_learned_sweep_selects_and_scores_consistently(bc):
     p2, a2 = ctx.sweep(A, B, sel)
     np.testing.assert_allclose(peak.cpu().numpy(), p2.cpu().numpy(), rtol=1e-5)
     net.close(); A.close(); B.close(); ctx.close()
+
+
+def test_learned_sweep_orientation_averaging(bc):
+    # bc_learned_sweep_avg: with no orientations it is the plain learned sweep; with
+    # two it scores each rotation by the mean of the network's scores for the receptor
+    # as given and turned by each orientation S (rotations S R), which the test forms
+    # on the host: the receptor's knots rotated and uploaded, the rotations composed.
+    wl = synth.small_pair(7)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    A, B = ctx.shape(wl.A.xyz, wl.A.level), ctx.shape(wl.B.xyz, wl.B.level)
+    net = bc.MLP(ctx, 64, synth.mlp_init(64, 9))
+    qn = synth.shoemake_quaternions(synth.SplitMix64(4), 3000).astype(np.float32)
+    q = torch.tensor(qn, device="cuda")
+    i0, p0, a0, s0 = bc.learned_sweep(ctx, net, A, B, q, 40)
+    i1, p1, a1, s1 = bc.learned_sweep(ctx, net, A, B, q, 40, orientations=np.zeros((0, 4), np.float32))
+    # (the moments come from spectra whose spreading sums round in a run-dependent order)
+    np.testing.assert_allclose(s1.cpu().numpy(), s0.cpu().numpy(), rtol=1e-5, atol=1e-6)
+    s1n = s1.cpu().numpy()
+    np.testing.assert_array_equal(i1.cpu().numpy(), np.lexsort((np.arange(s1n.size), -s1n))[:40])
+    S = synth.shoemake_quaternions(synth.SplitMix64(11), 2)
+    fb = bc.moments(ctx, B)
+    per = [s0.cpu().numpy()]
+    for s_q in S:
+        hS = ctx.shape(synth.rotate_points(wl.A.xyz, s_q), wl.A.level)
+        qs = torch.tensor(synth.compose_quaternions(s_q, qn).astype(np.float32), device="cuda")
+        per.append(net.predict(net.features(qs, bc.moments(ctx, hS), fb)).cpu().numpy())
+        hS.close()
+    ref = np.mean(per, axis=0)
+    idx, peak, arg, sc = bc.learned_sweep(ctx, net, A, B, q, 40, orientations=S.astype(np.float32))
+    s = sc.cpu().numpy()
+    # the receptor is turned in FP32 on the device here and in FP64 on the host above
+    np.testing.assert_allclose(s, ref, rtol=1e-3, atol=1e-4 * np.abs(ref).max())
+    assert np.abs(s - s0.cpu().numpy()).max() > 1e-3 * np.abs(ref).max()  # the average differs from one view
+    np.testing.assert_array_equal(idx.cpu().numpy(), np.lexsort((np.arange(s.size), -s))[:40])
+    p2, _ = ctx.sweep(A, B, qn[idx.cpu().numpy()])
+    np.testing.assert_allclose(peak.cpu().numpy(), p2.cpu().numpy(), rtol=1e-5)
+    with pytest.raises(bc.BallCorrError):
+        bc.learned_sweep(ctx, net, A, B, q, 40, orientations=np.zeros((1, 4), np.float32))
+    net.close(); A.close(); B.close(); ctx.close()
