@@ -38,6 +38,8 @@
  *     device; "host" pointers are ordinary or pinned host memory.
  *   - Caller-owned buffers stay caller-owned; the library copies what it keeps
  *     and owns all of its internal workspaces.
+ *   - A context (and everything created on it) is used by one host thread at
+ *     a time; different contexts may be used from different threads.
  */
 #ifndef BALLCORR_H
 #define BALLCORR_H
