@@ -118,3 +118,17 @@ def test_tuning_struct_matches_the_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"(?:int|double)\s+(\w+);", body)
     assert fields == [f for f, _ in bc.bc_lift_params._fields_]
+
+
+def test_shape_arrays_marshalling_on_the_host():
+    # The binding's argument marshalling for shape uploads (no device work): host
+    # arrays of any float/int type and layout become contiguous FP32 (n, 3) and int32 (n).
+    x = np.arange(12, dtype=np.float64).reshape(3, 4)[:, :3]  # non-contiguous float64
+    lv = [0, 1, 1]
+    xa, la, dev = bc.Shape._arrays(x, lv)
+    assert dev == 0 and xa.dtype == np.float32 and la.dtype == np.int32
+    assert xa.shape == (3, 3) and xa.flags["C_CONTIGUOUS"] and la.flags["C_CONTIGUOUS"]
+    np.testing.assert_array_equal(xa, x.astype(np.float32))
+    np.testing.assert_array_equal(la, np.array(lv, np.int32))
+    xe, le, _ = bc.Shape._arrays(np.zeros((0, 3)), np.zeros(0))
+    assert xe.shape == (0, 3) and le.shape == (0,)
