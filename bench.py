@@ -46,14 +46,13 @@ UNIT = "poses/s"
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM traffic per launch measured by ncu for the kernels below (one capture
-# each; see profiles/).  An entry counts only while the device-code sources it
-# was measured on are unchanged (sha256 over KERNEL_SOURCES, first 16 hex
-# digits).
+# each).  An entry counts only while the device-code sources it was measured
+# on are unchanged (sha256 over KERNEL_SOURCES, first 16 hex digits).
 NCU_TRAFFIC = {
-    "k_spread": {"bytes": 1.841e+07, "kernel_hash": "436ce0e99d5123e4", "source": "profiles/ncu_full_scale_pair_N128.md"},
-    "k_fft_z_umma": {"bytes": 7.881e+07, "kernel_hash": "436ce0e99d5123e4", "source": "profiles/ncu_full_scale_pair_N128.md"},
-    "k_fft_y": {"bytes": 9.334e+07, "kernel_hash": "436ce0e99d5123e4", "source": "profiles/ncu_full_scale_pair_N128.md"},
-    "k_fft_x": {"bytes": 7.375e+07, "kernel_hash": "436ce0e99d5123e4", "source": "profiles/ncu_full_scale_pair_N128.md"},
+    "k_spread": {"bytes": 1.841e+07, "kernel_hash": "436ce0e99d5123e4"},
+    "k_fft_z_umma": {"bytes": 7.881e+07, "kernel_hash": "436ce0e99d5123e4"},
+    "k_fft_y": {"bytes": 9.334e+07, "kernel_hash": "436ce0e99d5123e4"},
+    "k_fft_x": {"bytes": 7.375e+07, "kernel_hash": "436ce0e99d5123e4"},
 }
 
 
@@ -163,28 +162,21 @@ def f32_shape(S):
 
 
 # ------------------------------------------------------------------ oracle timing
-def oracle_sample(wl, fraction):
-    """The FP64 oracle on a bounded sample of the workload: the spectra of the
-    first `fraction` of each shape's knots plus the full-grid inverse.  The
-    spectra cost is linear in the knot count, so the full-workload time is
-    extrapolated as t_spectra / fraction + t_inverse."""
+def oracle_full(wl):
+    """The FP64 oracle (layer b) on the whole workload: both shapes' spectra by the
+    direct nonuniform DFT over every knot, the conjugate product and the direct
+    inverse onto the full N^3 translation grid.  Returns (seconds, description)."""
     import oracle as O
-    from paper_1711_05075_gb300 import synth
-    nA = max(1, int(round(wl.A.n * fraction)))
-    nB = max(1, int(round(wl.B.n * fraction)))
     A = f32_shape(wl.A)
     B = f32_shape(wl.B)
-    A = synth.Shape(A.xyz[:nA], A.level[:nA], A.radii)
-    B = synth.Shape(B.xyz[:nB], B.level[:nB], B.radii)
     q = wl.quats[0].astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
     fa = O.shape_spectrum(A.xyz, A.level, A.radii, wl.N, None, wl.period)
     fb = O.shape_spectrum(B.xyz, B.level, B.radii, wl.N, q, wl.period)
-    t1 = time.perf_counter()
     O.inverse_grid(O.corr_spectrum(fa, fb), wl.period)
-    t2 = time.perf_counter()
-    full = (t1 - t0) * (wl.A.n + wl.B.n) / (nA + nB) + (t2 - t1)
-    return full, f"{nA}+{nB} of {wl.A.n}+{wl.B.n} knots (spectra time scaled by the knot ratio) + full {wl.N}^3 inverse"
+    t = time.perf_counter() - t0
+    return t, (f"full workload: spectra of all {wl.A.n}+{wl.B.n} knots (direct FP64 NDFT) + "
+               f"full {wl.N}^3 direct inverse, one correlation per step")
 
 
 def cpu_cores():
@@ -200,13 +192,12 @@ def run_reference(args, rank, world):
     wl = workload()
     import oracle
     oracle.build()
-    frac = args.ref_fraction
     for _ in range(args.warmup):
-        oracle_sample(wl, frac)
+        oracle_full(wl)
     times = []
     desc = ""
     for _ in range(args.steps):
-        t, desc = oracle_sample(wl, frac)
+        t, desc = oracle_full(wl)
         times.append(t)
     ms = 1e3 * float(np.mean(times))
     value = wl.N ** 3 / (ms * 1e-3)
@@ -267,15 +258,38 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize(dev)
     t_wall0 = time.perf_counter()
+    host_ms = []
     for i in range(args.steps):
+        h0 = time.perf_counter()
         flush.fill_(float(i))
         starts[i].record(stream)
         ctx.correlate(A, B, q, out)
         ends[i].record(stream)
+        host_ms.append(1e3 * (time.perf_counter() - h0))
     torch.cuda.synchronize(dev)
     barrier()
     t_wall1 = time.perf_counter()
     clk = clocks.stop() if rank == 0 else None
+
+    # ---- sustained rate: many correlations back to back between one pair of events
+    # (no L2 flush between them), clocks sampled over the same interval
+    sustained = None
+    if args.sustained > 0:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks2 = ClockSampler(local_rank)
+        if rank == 0:
+            clocks2.start()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.sustained):
+            ctx.correlate(A, B, q, out)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        clk2 = clocks2.stop() if rank == 0 else None
+        ms_sus = max_over_ranks(ev0.elapsed_time(ev1)) / args.sustained
+        sustained = {"steps": args.sustained, "ms_per_step": ms_sus,
+                     "value": world * wl.N ** 3 / (ms_sus * 1e-3), "unit": UNIT,
+                     "l2": "not flushed between steps", "clocks": clk2}
     # per-stage times: a separate pass of the same steps with CUDA events between the
     # stage launches (kernel by kernel, so each stage also carries its launch gap)
     n_prof = max(3, min(args.steps, 10))
@@ -349,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        t_full, desc = oracle_sample(wl, args.ref_fraction)
+        t_full, desc = oracle_full(wl)
         cpu = {"value": wl.N ** 3 / t_full, "unit": UNIT,
                "cores": int(os.environ.get("OMP_NUM_THREADS", cpu_cores())), "kind": "oracle", "sample": desc}
 
@@ -365,12 +379,20 @@ def run_ours(args, rank, world, local_rank):
                          "note": f"peak {peak_src}; achieved = algorithmic bytes per launch / mean launch time "
                                  f"({dom['bytes'] / 1e6:.1f} MB / {dom_ms * 1e3:.1f} us)"},
             "stage_ms": {s["name"]: round(s["ms"] / calls, 5) for s in stages},
+            "stage_ms_source": (f"a separate pass of {n_prof} correlations launched kernel by kernel with CUDA "
+                                "events between the stage launches (no graph replay, so each stage also carries "
+                                "its launch gap); the roofline's launch time is that pass's mean"),
+            "sustained": sustained,
             "tuning": tuning,
             "cufft_baseline": cufft,
             "stage_share": stage_share,
             "clocks": clk,
             "cpu_baseline": cpu,
             "wall_s_timed_region": t_wall1 - t_wall0,
+            "host_ms_per_step": {"median": float(np.median(host_ms)), "max": float(np.max(host_ms)),
+                                 "note": "host time to enqueue one step (L2-flush fill, events, the "
+                                         "correlation's graph launch); the device times above do not "
+                                         "include host gaps between steps"},
         }
         print(json.dumps(line), flush=True)
     A.close()
@@ -737,9 +759,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ref-fraction", type=float, default=0.25,
-                    help="knot fraction of the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sustained", type=int, default=2000,
+                    help="correlations timed back to back between one event pair for the sustained rate (0: skip)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the context's default tuning")
     ap.add_argument("--spread", type=int, choices=[0, 1], default=None,
                     help="force the spreading implementation (default: autotuned; 0 for --profile-correlations)")

@@ -445,8 +445,7 @@ const char *bc_stage_name(int i);
 /* ---------------------------------------------------------------- no allocation
  * bc_correlate_noalloc: one correlation of a small pair of shapes that
  * allocates no device memory.  The paper has no counterpart; this is a
- * service for callers that cannot call cudaMalloc -- code that must not add
- * allocations while a stream is being captured, plug-ins living inside an
+ * service for callers that cannot call cudaMalloc -- plug-ins living inside an
  * application that owns the device heap, real-time loops that must never wait
  * on the allocator.  The caller passes device buffers for the inputs and the
  * output; all other memory the computation needs is one static device array
@@ -465,11 +464,13 @@ const char *bc_stage_name(int i);
  *   cuda_stream  stream to run on (NULL = legacy default stream).
  *
  * Larger sizes are rejected with BC_ERR_ARG and a message naming the limit.
- * The call synchronises `cuda_stream` once (to check the level ids) and
- * returns with the rest of the work enqueued.  The first call on a device
- * looks up the array's device address; make that first call before any
- * stream capture.  All calls share the one array and each call clears the
- * parts that must start at zero, so calls whose GPU work overlaps (two
+ * The call synchronises `cuda_stream` twice -- after checking the level ids
+ * and coordinates, before any kernel uses them, and after the last kernel, to
+ * read back the kernels' status word -- and returns with `out` complete.  A
+ * status word that reports a timed-out device wait gives BC_ERR_TIMEOUT, any
+ * other flag BC_ERR_INTERNAL.  The first call on a device looks up the
+ * array's device address.  All calls share the one array and each call clears
+ * the parts that must start at zero, so calls whose GPU work overlaps (two
  * streams, two host threads) race and corrupt each other's results.
  * Errors are reported through bc_last_error(). */
 #define BC_NOALLOC_MAX_N 32

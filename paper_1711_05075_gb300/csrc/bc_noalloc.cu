@@ -1,8 +1,7 @@
 // bc_correlate_noalloc: the correlation of one small pair of shapes without any
 // device allocation.
 //
-// Some callers cannot allocate device memory: code running inside a CUDA
-// stream capture that must not create allocation nodes, plugins hosted by an
+// Some callers cannot allocate device memory: plugins hosted by an
 // application that owns the whole device heap and forbids cudaMalloc, and
 // real-time loops that must not take the allocator's locks.  They hand in
 // device buffers for the inputs and the output; everything else this entry
@@ -16,6 +15,9 @@
 // the GPU (different streams, or different host threads) race on it and give
 // wrong results.  The parts that must start at a known state (the spreading
 // boxes, the support-box accumulators, the status words) are reset by every call.
+// Each call synchronises its stream twice -- after the knot checks, so that no
+// kernel sees an out-of-range level id, and at the end, to read the kernels'
+// status word -- so it cannot be recorded into a CUDA graph.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -225,6 +227,14 @@ extern "C" bc_status bc_correlate_noalloc(const bc_params *p, const float *xyzA,
             return ncuda(e, "fft x");
         if ((e = launch_ifft_y(g, t, dpairs, 1, h, nsm, st)) != cudaSuccess) return ncuda(e, "ifft y");
         if ((e = launch_ifft_z(g, t, dpairs, 1, h, out, nullptr, nsm, st)) != cudaSuccess) return ncuda(e, "ifft z");
+        // the kernels' own status word: bit 0 = a support box beyond its capacity
+        // (the instance was skipped), bit 8 = a bounded wait gave up
+        int herr = 0;
+        if ((e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return ncuda(e, "read status");
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return ncuda(e, "sync");
+        if (herr & 256) return nfail(BC_ERR_TIMEOUT, "bc_correlate_noalloc: a device wait timed out");
+        if (herr) return nfail(BC_ERR_INTERNAL, "bc_correlate_noalloc: a support box exceeded its capacity");
         return BC_OK;
     } catch (...) {
         return nfail(BC_ERR_INTERNAL, "bc_correlate_noalloc: unexpected exception");

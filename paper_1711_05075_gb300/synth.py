@@ -228,6 +228,23 @@ def sweep_pair(seed=0, k=2048, n_rec=50000, n_lig=5000, N=96, W=8) -> Workload:
     return Workload(f"union{n_rec}-torus{n_lig}-rot{k}-N{N}-W{W}", A, B, q, N=N, W=W)
 
 
+def ragged_pairs(seed=0, npairs=64, lo=1000, hi=100000, N=96, W=8):
+    """A ragged batch of `npairs` independent shape pairs whose knot counts are
+    log-uniform in [lo, hi]: A_i a union of 3 random ellipsoids, B_i a torus, both
+    with the L=4 levels of the 20k-ball pair, one Shoemake rotation per pair;
+    96^3 grid, KB width 8.  Returns (pairs, quats) with pairs a list of (A_i, B_i)."""
+    rng = SplitMix64(seed)
+    u = rng.uniform(2 * npairs)
+    counts = np.exp(np.log(lo) + u * (np.log(hi) - np.log(lo))).astype(np.int64)
+    pairs = []
+    for i in range(npairs):
+        A = ellipsoid_union_shape(int(counts[2 * i]), 10000 + 97 * seed + i)
+        B = torus_shape(int(counts[2 * i + 1]), 20000 + 97 * seed + i, RADII_4, PROBS_4)
+        pairs.append((A, B))
+    q = shoemake_quaternions(SplitMix64(seed + 30000), npairs)
+    return pairs, q
+
+
 def translation_sample(N: int, count: int, seed: int = 0) -> np.ndarray:
     """`count` distinct linear indices into the N^3 translation grid (without replacement)."""
     rng = SplitMix64(seed)

@@ -1,5 +1,5 @@
 """Host side of bench.py (CPU): the workload it times, and the reference arm's
-JSON line (the FP64 oracle on a small knot sample, through the same code path
+JSON line (the FP64 oracle on the whole workload, through the same code path
 `bench.py --impl reference` runs)."""
 import json
 import os
@@ -33,8 +33,8 @@ def test_kernel_source_hash_covers_existing_files():
 
 
 def test_reference_arm_prints_the_contract_line():
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                        "--ref-fraction", "0.005"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["unit"] == "poses/s" and line["value"] > 0
@@ -42,4 +42,6 @@ def test_reference_arm_prints_the_contract_line():
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
-    assert "100+100 of 20000+20000" in cb["sample"]
+    assert cb["sample"].startswith("full workload") and "20000+20000 knots" in cb["sample"]
+    # the timed steps are whole oracle runs: the line's time is what was measured
+    assert line["warmup"] >= 3 and line["steps"] == 1 and line["ms_per_step"] > 0

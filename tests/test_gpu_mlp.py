@@ -76,22 +76,37 @@ def test_forward_and_gradients_match_oracle(bc, H):
     ctx.close()
 
 
-def test_adam_step_matches_oracle(bc):
+def test_adam_steps_match_oracle(bc):
+    # Three consecutive updates: from the second step on m^/sqrt(v^) is no longer
+    # sign(g), so swapped betas or a missing bias correction would show.
     H = 64
     init, q, fa, fb, t = problem(H, seed=3)
     ctx = bc.Context(32, 6, synth.RADII_2)
     net = bc.MLP(ctx, H, init)
     dev = torch.device("cuda")
     X = net.features(torch.tensor(q, device=dev), torch.tensor(fa, device=dev), torch.tensor(fb, device=dev))
-    g, _ = net.grads(X, torch.tensor(t, device=dev))
-    net.train_step(X, torch.tensor(t, device=dev), 1e-3)
-    st = net.state()
+    td = torch.tensor(t, device=dev)
     p = split(init, H)
-    M.adam_step(p, split(g.cpu().numpy(), H), {}, lr=1e-3)
-    got = split(st["params"], H)
-    for k in p:
-        np.testing.assert_allclose(got[k], p[k], rtol=1e-5, atol=1e-6)
-    assert st["step"] == 1
+    state = {}
+    for step in range(1, 4):
+        g, _ = net.grads(X, td)  # the gradient the update will use (same parameters, same batch)
+        net.train_step(X, td, 1e-3)
+        st = net.state()
+        # the kernel holds the hyperparameters as FP32 values: 1 - float32(0.999) differs from
+        # 1e-3 by 1.3e-5 relative, so the oracle is given the same rounded betas
+        M.adam_step(p, split(g.cpu().numpy(), H), state, lr=float(np.float32(1e-3)),
+                    beta1=float(np.float32(0.9)), beta2=float(np.float32(0.999)), eps=float(np.float32(1e-8)))
+        got = split(st["params"], H)
+        gm, gv = split(st["adam_m"], H), split(st["adam_v"], H)
+        for k in p:
+            np.testing.assert_allclose(got[k], p[k], rtol=1e-5, atol=1e-6, err_msg=f"step {step} {k}")
+            for name, mine in (("m_", gm), ("v_", gv)):  # the moment recurrences themselves
+                ref = state[name + k]
+                np.testing.assert_allclose(mine[k], ref, rtol=1e-5, atol=1e-6 * float(np.abs(ref).max()),
+                                           err_msg=f"step {step} {name}{k}")
+        assert st["step"] == step
+        # continue the oracle from the GPU's parameters so rounding does not accumulate
+        p = {k: got[k].copy() for k in got}
     net.close()
     ctx.close()
 

@@ -1,6 +1,7 @@
 """Pins for the MLP oracle: gradients against central differences, BF16 rounding
-against its definition, Adam against a hand-evaluated first step, and the moment
-mode list against its ordering rule."""
+against its definition, Adam against hand-evaluated steps (first step, three
+steps with distinct betas, and the unrolled moment sums), and the moment mode
+list against its ordering rule."""
 import numpy as np
 import pytest
 
@@ -51,6 +52,48 @@ def test_adam_first_step_moves_by_lr_sign():
     g = {"a": np.array([0.3, -4.0, 1e-3])}
     M.adam_step(p, g, {}, lr=0.01)
     np.testing.assert_allclose(p["a"], [0.99, -1.99, 0.49], atol=1e-6)
+
+
+def test_adam_three_steps_hand_evaluated():
+    # Kingma & Ba, Algorithm 1, evaluated by hand for one scalar with beta1 = 1/2,
+    # beta2 = 3/4 (distinct, so a swap changes the answer), lr = 0.1, eps = 0 and
+    # gradients 1, -2, 3 from theta0 = 1:
+    #   t=1: m = 1/2,  v = 1/4;      m^ = 1,          v^ = 1          -> step -0.1
+    #   t=2: m = -3/4, v = 19/16;    m^ = -1,         v^ = 19/7       -> step +0.1 / sqrt(19/7)
+    #   t=3: m = 9/8,  v = 201/64;   m^ = 9/7,        v^ = 201/37     -> step -0.1 (9/7) / sqrt(201/37)
+    expected = [0.9, 0.9 + 0.1 / np.sqrt(19 / 7)]
+    expected.append(expected[-1] - 0.1 * (9 / 7) / np.sqrt(201 / 37))
+    p = {"a": np.array([1.0])}
+    st = {}
+    for g, want in zip((1.0, -2.0, 3.0), expected):
+        M.adam_step(p, {"a": np.array([g])}, st, lr=0.1, beta1=0.5, beta2=0.75, eps=0.0)
+        assert p["a"][0] == pytest.approx(want, rel=1e-14), (st["t"], p["a"][0], want)
+    assert st["t"] == 3
+    # the same updates with the betas swapped or without bias correction end elsewhere
+    assert abs(expected[-1] - 0.905535) < 1e-6
+    p2, st2 = {"a": np.array([1.0])}, {}
+    for g in (1.0, -2.0, 3.0):
+        M.adam_step(p2, {"a": np.array([g])}, st2, lr=0.1, beta1=0.75, beta2=0.5, eps=0.0)
+    assert abs(p2["a"][0] - expected[-1]) > 1e-4
+    no_bias_corr_t2 = 0.9 + 0.1 * (3 / 4) / np.sqrt(19 / 16)  # step 2 without the corrections
+    assert abs(no_bias_corr_t2 - expected[1]) > 1e-3
+
+
+def test_adam_matches_closed_form_moment_sums():
+    # After t steps m_t = (1 - b1) sum_s b1^(t-s) g_s and v_t = (1 - b2) sum_s b2^(t-s) g_s^2
+    # (the recurrences unrolled); every step divides their bias-corrected ratio.
+    rng = np.random.default_rng(11)
+    b1, b2, lr, eps = 0.9, 0.999, 1e-2, 1e-8
+    gs = rng.normal(size=(5, 7)) * np.array([1e-3, 1e-2, 0.1, 1, 10, 100, 1e3])
+    p = {"w": rng.normal(size=7)}
+    theta = p["w"].copy()
+    st = {}
+    for t in range(1, 6):
+        M.adam_step(p, {"w": gs[t - 1]}, st, lr=lr, beta1=b1, beta2=b2, eps=eps)
+        m = (1 - b1) * sum(b1 ** (t - s) * gs[s - 1] for s in range(1, t + 1))
+        v = (1 - b2) * sum(b2 ** (t - s) * gs[s - 1] ** 2 for s in range(1, t + 1))
+        theta = theta - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+        np.testing.assert_allclose(p["w"], theta, rtol=1e-12, atol=1e-15)
 
 
 def test_moment_modes_ordering():

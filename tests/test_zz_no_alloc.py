@@ -1,16 +1,18 @@
-"""The allocation-free entry point agrees with the ordinary one.
+"""The allocation-free entry point agrees with the ordinary one and with the oracle.
 
-bc_correlate_noalloc serves callers that cannot allocate device memory (code
-inside a stream capture, plug-ins in an application that owns the device heap,
-real-time loops that must not wait on the allocator): it takes device inputs
-and a device output and keeps its scratch in a static device array inside the
-library.  Here it is called through the C ABI twice in a row, with different
-rotations, and each result is compared with bc_correlate on the same inputs.
-This file is collected last so that a failure here comes after every other test.
+bc_correlate_noalloc serves callers that cannot allocate device memory
+(plug-ins in an application that owns the device heap, real-time loops that
+must not wait on the allocator): it takes device inputs and a device output
+and keeps its scratch in a static device array inside the library.  Here it is
+called through the C ABI twice in a row, with different rotations, and each
+result is compared with bc_correlate on the same inputs and with the FP64
+oracle (layer b).  This file is collected last so that a failure here comes
+after every other test.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1711_05075_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -56,8 +58,13 @@ def test_noalloc_matches_bc_correlate_on_two_calls(bc):
             got = out.double().cpu().numpy()
             ref = ctx.correlate(A, B, quats[r:r + 1])[0].double().cpu().numpy()
             rel = rel_l2(got, ref)
-            print(f"call {r}: rel-L2 vs bc_correlate {rel:.3e}")
+            A64 = synth.Shape(wl.A.xyz.astype(np.float32).astype(np.float64), wl.A.level, wl.A.radii)
+            B64 = synth.Shape(wl.B.xyz.astype(np.float32).astype(np.float64), wl.B.level, wl.B.radii)
+            orc = O.band_limited_corr(A64, B64, quats[r].astype(np.float64), wl.N, wl.period)
+            rel_o = rel_l2(got, orc)
+            print(f"call {r}: rel-L2 vs bc_correlate {rel:.3e}, vs FP64 oracle {rel_o:.3e}")
             assert rel <= REL_TOL, rel
+            assert rel_o <= REL_TOL, rel_o
     finally:
         A.close()
         B.close()
