@@ -56,8 +56,8 @@ NCU_TRAFFIC = {
 }
 
 
-KERNEL_SOURCES = ("bc_kernels.cu", "bc_binned.cu", "bc_query.cu", "bc_zumma.cu", "bc_fft.cuh", "bc_device.cuh",
-                  "bc_umma.cuh", "bc_internal.h")
+KERNEL_SOURCES = ("bc_kernels.cu", "bc_back.cu", "bc_binned.cu", "bc_query.cu", "bc_zumma.cu", "bc_fft.cuh",
+                  "bc_device.cuh", "bc_passes.cuh", "bc_umma.cuh", "bc_internal.h")
 
 
 def kernel_source_hash():
@@ -345,7 +345,8 @@ def run_ours(args, rank, world, local_rank):
     kname = {"prepare": "k_prepare", "spread": "k_bin" if binned else "k_spread",
              "fft_z": "k_fft_z_binned" if binned else ("k_fft_z_umma" if tuning.get("z_transform") else "k_fft_z"),
              "fft_y": "k_fft_y",
-             "fft_x": "k_fft_x", "ifft_y": "k_ifft_y", "ifft_z": "k_ifft_z"}[dom["name"]]
+             "fft_x": "k_back" if tuning.get("persistent") else "k_fft_x", "ifft_y": "k_ifft_y",
+             "ifft_z": "k_ifft_z"}[dom["name"]]
     tr = NCU_TRAFFIC.get(kname)
     traffic = tr["bytes"] if tr and tr.get("kernel_hash") == kernel_source_hash() else None
     stage_share = {s["name"]: round(s["ms"] / max(sum(x["ms"] for x in stages), 1e-12), 4) for s in stages}

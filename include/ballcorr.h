@@ -300,10 +300,17 @@ bc_status bc_lift_destroy(bc_lift_t lift);
  *                in FP32 contexts with N <= 128 (BC_ERR_UNSUPPORTED otherwise);
  *                a stalled tensor-core wait is reported by bc_sync as
  *                BC_ERR_TIMEOUT.
- * A new context starts with {0, 64, 1, 0, 1} (z_transform 0 where 1 is not
+ *   persistent   0: the x pass (with the deconvolution, ball transforms, level
+ *                sum and conjugate product), the inverse y pass and the
+ *                inverse z pass run as three launches; 1: one persistent
+ *                launch whose blocks take the three passes' work units from a
+ *                device queue in order, each unit waiting (bounded, two
+ *                seconds; bc_sync reports an expired wait as BC_ERR_TIMEOUT)
+ *                for the units it reads to finish.  Same arithmetic.
+ * A new context starts with {0, 64, 1, 0, 1, 0} (z_transform 0 where 1 is not
  * available).  Plans keep the choices in force when
  * they were made.  bc_autotune times the candidates on the given shapes --
- * bc_correlate of A with B (identity) for `spread` and then `z_transform` (when rotations > 0,
+ * bc_correlate of A with B (identity) for `spread`, `z_transform` and `persistent` (when rotations > 0,
  * `z_transform` is decided again on the sweep with the chosen batch); in FP32 contexts the
  * per-stage times of profiled correlations under each schedule, pass by pass,
  * for `fft_schedule`; when rotations > 0, a sweep of that many fixed rotations
@@ -320,6 +327,7 @@ typedef struct {
     int graphs;
     int fft_schedule;
     int z_transform;
+    int persistent;
 } bc_tuning;
 bc_status bc_get_tuning(bc_ctx_t ctx, bc_tuning *out);
 bc_status bc_set_tuning(bc_ctx_t ctx, const bc_tuning *t);

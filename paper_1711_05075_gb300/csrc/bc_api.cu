@@ -100,6 +100,7 @@ struct PinBuf {
 struct Workspace {
     DevBuf ku, plan, inst, pairs, grid, z1, y1, h, fa, boxes, keys;
     DevBuf cnt, cur, rec;     // binned spreading: bin counts (kept zeroed), bin cursors, knot records
+    DevBuf sync;              // work-queue and dependency counters of the persistent back-half launch
     bool grid_dirty = false;  // spreading boxes may hold values (an enqueue failed midway)
     bool boxes_dirty = true;  // support-box accumulators need their reset state
     bool bins_dirty = false;  // bin counts may be non-zero (an enqueue failed midway)
@@ -125,7 +126,7 @@ struct Workspace {
     void release()
     {
         drop_graph();
-        DevBuf *b[] = {&ku, &plan, &inst, &pairs, &grid, &z1, &y1, &h, &fa, &boxes, &keys, &cnt, &cur, &rec};
+        DevBuf *b[] = {&ku, &plan, &inst, &pairs, &grid, &z1, &y1, &h, &fa, &boxes, &keys, &cnt, &cur, &rec, &sync};
         for (DevBuf *x : b) x->release();
         last_desc.clear();
         last_inst_p = last_pairs_p = nullptr;
@@ -146,6 +147,7 @@ struct bc_ctx_s {
     float *deconv = nullptr, *ballft = nullptr;
     float2 *tw_n = nullptr, *tw_N = nullptr;
     float *consts = nullptr; // [0] = exp(beta) / I0(beta)
+    float *xw = nullptr;     // x-pass level weights (Tables::xw) of the correlation
     int *modes = nullptr;    // BC_MOMENTS lowest modes of the half spectrum, (m_x, m_y, m_z) each
     int qmax = 0;
     // device status word
@@ -159,11 +161,13 @@ struct bc_ctx_s {
     int sweep_batch = 64; // rotations per pass when a sweep's batch argument is 0
     int fft_sched = 0;    // alternative radix schedule per forward FP32 pass: bit 0 z, bit 1 y, bit 2 x
     int z_tc = 0;         // z pass as a DFT product on the tensor cores (spread 0; needs zdft)
+    int persistent = 0;   // x, inverse-y and inverse-z passes as one persistent launch (bc_back.cu)
     float *zdft = nullptr; // its 32-cell DFT block, split TF32 (hi, then lo), FP32 contexts with N <= 128
     // workspaces
     Workspace ws;                 // pipeline workspaces of direct calls
     DevBuf outbuf, stats, learn, tune; // host-output staging, shape checks, learned-sweep and tuning scratch
     DevBuf score_ft;                   // shape-complementarity weights for (score_r0, score_lambda)
+    DevBuf score_xw;                   // their x-pass level weights
     double score_r0 = -1.0, score_lambda = 0.0;
     std::set<bc_shape_s *> shapes; // live shapes; orphaned (device memory freed) by bc_destroy
     std::set<bc_mlp_s *> nets;     // live networks; orphaned the same way
@@ -173,7 +177,7 @@ struct bc_ctx_s {
     int prof_max = 0, prof_calls = 0;
     long long prof_launches = 0;
     std::vector<cudaEvent_t> prof_ev; // prof_max x (BC_NUM_STAGES + 1)
-    int last_ninst = 0, last_npairs = 0, last_mode = 0;
+    int last_ninst = 0, last_npairs = 0, last_mode = 0, last_back = 0;
     cudaStream_t capture_stream = nullptr; // private stream for recording graphs (the legacy stream cannot be captured)
     bool replay = true;                    // repeated identical passes of direct calls replay a recorded graph
     std::vector<InstDesc> last_inst;
@@ -241,6 +245,7 @@ static Tables tables_of(bc_ctx_t c)
     t.tw_N = c->tw_N;
     t.qmax = c->qmax;
     t.consts = c->consts;
+    t.xw = c->xw;
     return t;
 }
 
@@ -349,6 +354,8 @@ bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
             return bail(e, "copy radii");
         if ((e = launch_build_tables(g, beta, p->period, c->radii_dev, c->deconv, c->ballft, c->tw_n, c->tw_N, c->consts, c->stream)) != cudaSuccess)
             return bail(e, "build tables");
+        if ((e = cudaMalloc(&c->xw, sizeof(float) * xw_floats(g))) != cudaSuccess) return bail(e, "cudaMalloc xw");
+        if ((e = launch_build_xw(g, c->deconv, c->ballft, c->xw, c->stream)) != cudaSuccess) return bail(e, "build x weights");
         if (g.prec == 0 && g.n == 2 * g.N && supported_z_umma(g.N)) {
             const size_t half = (size_t)(g.n / 2) * 32;
             if ((e = cudaMalloc(&c->zdft, sizeof(float) * 2 * half)) != cudaSuccess) return bail(e, "cudaMalloc zdft");
@@ -373,6 +380,7 @@ bc_status bc_destroy(bc_ctx_t c)
         cudaFree(c->ballft);
         cudaFree(c->tw_n);
         cudaFree(c->tw_N);
+        cudaFree(c->xw);
         cudaFree(c->err_dev);
         if (c->pin) cudaFreeHost(c->pin);
         cudaFree(c->consts);
@@ -394,7 +402,7 @@ bc_status bc_destroy(bc_ctx_t c)
         c->queries.clear();
         c->ws.release();
         if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
-        DevBuf *bufs[] = {&c->outbuf, &c->stats, &c->learn, &c->tune, &c->score_ft};
+        DevBuf *bufs[] = {&c->outbuf, &c->stats, &c->learn, &c->tune, &c->score_ft, &c->score_xw};
         for (DevBuf *b : bufs) b->release();
         c->hstats.release();
         delete c;
@@ -575,6 +583,8 @@ bc_status bc_sync(bc_ctx_t c)
         if (herr & 4) return fail(BC_ERR_ARG, "a device-resident rotation had zero norm");
         if (herr & 8)
             return fail(BC_ERR_TIMEOUT, "the tensor-core z transform stalled (a bounded wait expired); results are incomplete");
+        if (herr & 16)
+            return fail(BC_ERR_TIMEOUT, "a dependency wait of the persistent launch expired; results are incomplete");
         return fail(BC_ERR_INTERNAL, "device-side check failed (support box exceeded its capacity)");
     }
     return BC_OK;
@@ -644,6 +654,10 @@ bc_status bc_profile_end(bc_ctx_t c, bc_profile *out)
         out->bytes[4] = yc * 8.0 + P * half * 8.0;
         out->bytes[5] = 2.0 * P * half * 8.0;
         out->bytes[6] = P * half * 8.0 + P * N * N * N * 4.0;
+        if (c->last_back) { // one persistent launch carried the three passes
+            out->bytes[4] += out->bytes[5] + out->bytes[6];
+            out->bytes[5] = out->bytes[6] = 0.0;
+        }
     }
     prof_free(c);
     return BC_OK;
@@ -661,6 +675,7 @@ bc_status bc_profile_end(bc_ctx_t c, bc_profile *out)
 // score.
 struct Weights {
     const float *ballft = nullptr; // null: the context's ball transform table
+    const float *xw = nullptr;     // x-pass level weights built from ballft
     float sign = 1.f;
 };
 
@@ -671,6 +686,7 @@ struct Job {
     int mode = 0;  // spreading: 0 boxes in HBM, 1 binned (fused into the z pass)
     int sched = 0; // radix schedule of the forward passes
     int ztc = 0;   // z pass on the tensor cores (mode 0 only)
+    int back = 0;  // x, inverse-y and inverse-z passes as one persistent launch
     Weights w;
     int nmain = 0, koff = 0, max_knots = 0;
     long long goff = 0, zoff = 0, yoff = 0, hpairs = 0;
@@ -687,6 +703,7 @@ static Job plan_job(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std
     j.mode = c->spread_mode;
     j.sched = c->fft_sched;
     j.ztc = c->z_tc && c->spread_mode == 0 ? 1 : 0;
+    j.back = c->persistent;
     j.nmain = (int)pairs.size() - (cache_first ? 1 : 0);
     j.inst.resize(shapes.size());
     for (size_t i = 0; i < shapes.size(); i++) {
@@ -765,6 +782,8 @@ static bc_status ensure_ws(bc_ctx_t c, Workspace &ws, int mode, long long koff, 
     if (hpairs > 0 && (e = ws.h.ensure(sizeof(float2) * (size_t)hpairs * N * N * H, false, st)) != cudaSuccess)
         return cuda_fail(e, "h");
     if ((e = ws.fa.ensure(sizeof(float2) * (size_t)N * N * H, false, st)) != cudaSuccess) return cuda_fail(e, "fa");
+    if ((e = ws.sync.ensure(sizeof(unsigned) * back_sync_words(N, (int)std::max(npairs, 1LL)), false, st)) != cudaSuccess)
+        return cuda_fail(e, "queue counters");
     return BC_OK;
 }
 
@@ -779,7 +798,10 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
     g.sched = job.sched;
     const int ninst = (int)job.inst.size();
     Tables t = tables_of(c);
-    if (job.w.ballft) t.ballft = job.w.ballft;
+    if (job.w.ballft) {
+        t.ballft = job.w.ballft;
+        t.xw = job.w.xw;
+    }
     InstPlan *dplan = (InstPlan *)ws.plan.p;
     const PairDesc *pmain = dpairs + (job.cache_first ? 1 : 0);
     const int nmain = job.nmain;
@@ -844,24 +866,37 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
             return cuda_fail(e, "fft x (cache)");
         launches++;
     }
-    if (nmain > 0) {
-        if ((e = launch_fft_x(g, t, dinst, dplan, pmain, nmain, (const float2 *)ws.y1.p, (const float2 *)ws.fa.p,
-                              nullptr, (float2 *)ws.h.p, c->nsm, st)) != cudaSuccess)
-            return cuda_fail(e, "fft x");
+    if (job.back && nmain > 0) {
+        // one persistent launch for the three passes; profiled, its time is
+        // the fft_x stage and the two inverse stages read zero
+        if ((e = launch_back(g, t, dinst, dplan, pmain, nmain, (const float2 *)ws.y1.p, (const float2 *)ws.fa.p,
+                             (float2 *)ws.h.p, dout, keys, (unsigned *)ws.sync.p, c->err_dev, c->nsm, st)) != cudaSuccess)
+            return cuda_fail(e, "persistent back half");
         launches++;
+        mark(4);
+        mark(5);
+        mark(6);
+    } else {
+        if (nmain > 0) {
+            if ((e = launch_fft_x(g, t, dinst, dplan, pmain, nmain, (const float2 *)ws.y1.p, (const float2 *)ws.fa.p,
+                                  nullptr, (float2 *)ws.h.p, c->nsm, st)) != cudaSuccess)
+                return cuda_fail(e, "fft x");
+            launches++;
+        }
+        mark(4);
+        if (nmain > 0) {
+            if ((e = launch_ifft_y(g, t, pmain, nmain, (float2 *)ws.h.p, c->nsm, st)) != cudaSuccess)
+                return cuda_fail(e, "ifft y");
+            launches++;
+        }
+        mark(5);
+        if (nmain > 0) {
+            if ((e = launch_ifft_z(g, t, pmain, nmain, (const float2 *)ws.h.p, dout, keys, c->nsm, st)) != cudaSuccess)
+                return cuda_fail(e, "ifft z");
+            launches++;
+        }
+        mark(6);
     }
-    mark(4);
-    if (nmain > 0) {
-        if ((e = launch_ifft_y(g, t, pmain, nmain, (float2 *)ws.h.p, c->nsm, st)) != cudaSuccess) return cuda_fail(e, "ifft y");
-        launches++;
-    }
-    mark(5);
-    if (nmain > 0) {
-        if ((e = launch_ifft_z(g, t, pmain, nmain, (const float2 *)ws.h.p, dout, keys, c->nsm, st)) != cudaSuccess)
-            return cuda_fail(e, "ifft z");
-        launches++;
-    }
-    mark(6);
     if (nlaunch) *nlaunch += launches;
     if (prof) {
         c->prof_calls++;
@@ -869,6 +904,7 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
         c->last_ninst = ninst;
         c->last_npairs = nmain;
         c->last_mode = job.mode;
+        c->last_back = job.back && nmain > 0;
         c->last_inst = job.inst;
     }
     return BC_OK;
@@ -912,10 +948,10 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
     auto add = [&](const void *v, size_t n) { key.insert(key.end(), (const char *)v, (const char *)v + n); };
     const long long sig[] = {(long long)job.inst.size(), (long long)job.pairs.size(), (long long)job.nmain,
                              (long long)job.cache_first, (long long)job.koff, (long long)job.max_knots,
-                             (long long)job.mode, (long long)job.sched, (long long)job.ztc};
+                             (long long)job.mode, (long long)job.sched, (long long)job.ztc, (long long)job.back};
     add(sig, sizeof(sig));
     const void *ptrs[] = {dout, keys, job.w.ballft, ws.ku.p, ws.plan.p, ws.inst.p, ws.pairs.p, ws.grid.p, ws.z1.p, ws.y1.p,
-                          ws.h.p, ws.fa.p, ws.boxes.p, ws.cnt.p, ws.cur.p, ws.rec.p, c->stream};
+                          ws.h.p, ws.fa.p, ws.boxes.p, ws.cnt.p, ws.cur.p, ws.rec.p, ws.sync.p, c->stream};
     add(ptrs, sizeof(ptrs));
     add(&job.w.sign, sizeof(job.w.sign));
     constexpr size_t kMaxGraphs = 8;
@@ -1083,13 +1119,17 @@ static bc_status score_weights(bc_ctx_t c, double r0, double lambda, const char 
     cudaError_t e;
     const size_t before = c->score_ft.bytes;
     if ((e = c->score_ft.ensure(sizeof(float) * n, false, c->stream)) != cudaSuccess) return cuda_fail(e, who);
+    if ((e = c->score_xw.ensure(sizeof(float) * xw_floats(c->g), false, c->stream)) != cudaSuccess) return cuda_fail(e, who);
     if (c->score_ft.bytes != before || r0 != c->score_r0 || lambda != c->score_lambda) {
         if ((e = launch_build_score_table(c->g, c->period, c->radii_dev, r0, lambda, (float *)c->score_ft.p, c->stream)) != cudaSuccess)
+            return cuda_fail(e, who);
+        if ((e = launch_build_xw(c->g, c->deconv, (const float *)c->score_ft.p, (float *)c->score_xw.p, c->stream)) != cudaSuccess)
             return cuda_fail(e, who);
         c->score_r0 = r0;
         c->score_lambda = lambda;
     }
     w->ballft = (const float *)c->score_ft.p;
+    w->xw = (const float *)c->score_xw.p;
     w->sign = -1.f;
     return BC_OK;
 }
@@ -1433,6 +1473,7 @@ bc_status bc_get_tuning(bc_ctx_t c, bc_tuning *out)
     out->graphs = c->replay ? 1 : 0;
     out->fft_schedule = c->fft_sched;
     out->z_transform = c->z_tc;
+    out->persistent = c->persistent;
     return BC_OK;
 }
 
@@ -1444,9 +1485,11 @@ bc_status bc_set_tuning(bc_ctx_t c, const bc_tuning *t)
     if (t->graphs != 0 && t->graphs != 1) return fail(BC_ERR_ARG, "bc_set_tuning: graphs must be 0 or 1");
     if (t->fft_schedule < 0 || t->fft_schedule > 7) return fail(BC_ERR_ARG, "bc_set_tuning: fft_schedule must be in [0, 7]");
     if (t->z_transform != 0 && t->z_transform != 1) return fail(BC_ERR_ARG, "bc_set_tuning: z_transform must be 0 or 1");
+    if (t->persistent != 0 && t->persistent != 1) return fail(BC_ERR_ARG, "bc_set_tuning: persistent must be 0 or 1");
     if (t->z_transform == 1 && !c->zdft)
         return fail(BC_ERR_UNSUPPORTED, "bc_set_tuning: the tensor-core z transform needs an FP32 context with N <= 128");
     c->z_tc = t->z_transform;
+    c->persistent = t->persistent;
     c->fft_sched = t->fft_schedule;
     c->spread_mode = t->spread;
     c->sweep_batch = t->sweep_batch;
@@ -1536,6 +1579,20 @@ bc_status bc_autotune(bc_ctx_t c, bc_shape_t A, bc_shape_t B, int rotations, bc_
                 }
             }
             c->z_tc = tz[1] < tz[0] ? 1 : 0;
+        }
+        // back half: three launches or one persistent launch
+        {
+            const int saved = c->persistent;
+            float tb[2] = {0.f, 0.f};
+            for (int b = 0; b <= 1; b++) {
+                c->persistent = b;
+                bc_status s = time_median(c, [&]() { return bc_correlate(c, A, B, ident, 1, dout, 1); }, 3, 7, &tb[b]);
+                if (s != BC_OK) {
+                    c->persistent = saved;
+                    return s;
+                }
+            }
+            c->persistent = tb[1] < tb[0] ? 1 : 0;
         }
         // radix schedule per forward pass (the split-precision passes have their own):
         // the stage times of profiled correlations under each schedule, pass by pass

@@ -49,6 +49,10 @@ struct Tables {
     const float2 *tw_N;   // N twiddles exp(-2 pi i k / N)
     int qmax;             // 3 (N/2)^2
     const float *consts;  // [0] = exp(beta) / I0(beta), the window normalisation
+    // x-pass level weights, per (j_y, chunk of 16 z-modes) one contiguous slice
+    // [l][a = |m_x| in 0..N/2][16]: ballft_l(a^2 + m_y^2 + m_z^2) D(a) D(m_y) D(m_z)
+    // (null: the x pass builds them from ballft and deconv)
+    const float *xw;
 };
 
 struct Geometry {
@@ -63,6 +67,9 @@ cudaError_t launch_build_tables(const Geometry &g, double beta, double period, c
                                 float *deconv, float *ballft, float2 *tw_n, float2 *tw_N, float *consts,
                                 cudaStream_t s);
 // out[l][q] = h^(rho_l + r0, k) - lambda h^(rho_l, k), k = 2 pi sqrt(q) / P (FP64, rounded once).
+// The x-pass weight table of Tables::xw from `ballft` (N (N/32) L (N/2 + 1) 16 floats).
+cudaError_t launch_build_xw(const Geometry &g, const float *deconv, const float *ballft, float *xw, cudaStream_t s);
+size_t xw_floats(const Geometry &g);
 cudaError_t launch_build_score_table(const Geometry &g, double period, const double *radii_dev, double r0,
                                      double lambda, float *out, cudaStream_t s);
 cudaError_t launch_pack_knots(const float *xyz, const int *level, int n, int L, float4 *knots,
@@ -111,6 +118,14 @@ cudaError_t launch_fft_y(const Geometry &g, const Tables &t, const InstDesc *ins
 cudaError_t launch_fft_x(const Geometry &g, const Tables &t, const InstDesc *inst, const InstPlan *plan,
                          const PairDesc *pairs, int npairs, const float2 *y1, const float2 *fa_cache,
                          float2 *fa_out, float2 *h, int nsm, cudaStream_t s);
+// The x, inverse-y and inverse-z passes of pairs (all with b >= 0) as one
+// persistent launch over a device work queue (bc_back.cu); `sync` holds
+// back_sync_words(N, npairs) counters, cleared by the launcher.  An expired
+// dependency wait sets bit 4 of *err.
+size_t back_sync_words(int N, int npairs);
+cudaError_t launch_back(const Geometry &g, const Tables &t, const InstDesc *inst, const InstPlan *plan,
+                        const PairDesc *pairs, int npairs, const float2 *y1, const float2 *fa_cache, float2 *h,
+                        float *out, unsigned long long *keys, unsigned *sync, int *err, int nsm, cudaStream_t s);
 cudaError_t launch_ifft_y(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, float2 *h,
                           int nsm, cudaStream_t s);
 // out (N^3 floats per pair) and keys (one 64-bit peak key per pair slot) may each be null.

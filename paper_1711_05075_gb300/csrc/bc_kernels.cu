@@ -33,7 +33,7 @@
 #include <climits>
 #include <cstdint>
 
-#include "bc_device.cuh"
+#include "bc_passes.cuh"
 
 namespace bc {
 
@@ -43,8 +43,6 @@ bool supported_N(int N)
 {
     return N == 32 || N == 64 || N == 96 || N == 128 || N == 256;
 }
-
-__device__ __forceinline__ int mode_of(int j, int N) { return j < N / 2 ? j : j - N; }
 
 // ------------------------------------------------------------------ tables
 // FP64 construction of the window-deconvolution, ball-transform and twiddle
@@ -128,6 +126,34 @@ cudaError_t launch_build_score_table(const Geometry &g, double period, const dou
     const int qmax = 3 * (g.N / 2) * (g.N / 2);
     const int total = g.L * (qmax + 1);
     k_build_score_table<<<(total + 255) / 256, 256, 0, s>>>(g.L, qmax, period, radii_dev, r0, lambda, out);
+    return cudaGetLastError();
+}
+
+// The x pass's level weights as one table, laid out so that the weights of
+// an x-pass item (row j_y, z-modes 16 ch .. 16 ch + 15) are one contiguous
+// slice: xw[(((j_y nch + ch) L + l) (N/2 + 1) + a) 16 + c] =
+// ballft_l(a^2 + m_y^2 + m_z^2) (D(a) D(m_y) D(m_z)), m_z = 16 ch + c, the same
+// FP32 expression build_xweights evaluates inside the pass.
+__global__ void k_build_xw(int N, int L, int qmax, const float *__restrict__ deconv, const float *__restrict__ ballft,
+                           float *xw)
+{
+    const int A = N / 2 + 1, nch = N / 2 / CL;
+    const long long total = (long long)N * nch * L * A * CL;
+    const long long Q = qmax + 1;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(e % CL), a = (int)((e / CL) % A), l = (int)((e / ((long long)CL * A)) % L);
+        const long long item = e / ((long long)CL * A * L);
+        const int jy = (int)(item / nch), ch = (int)(item % nch);
+        const int my = jy < N / 2 ? jy : jy - N, mz = ch * CL + c;
+        xw[e] = ballft[l * Q + a * a + my * my + mz * mz] * (deconv[a] * deconv[jy] * deconv[mz]);
+    }
+}
+
+size_t xw_floats(const Geometry &g) { return (size_t)g.N * (g.N / 2 / CL) * g.L * (g.N / 2 + 1) * CL; }
+
+cudaError_t launch_build_xw(const Geometry &g, const float *deconv, const float *ballft, float *xw, cudaStream_t s)
+{
+    k_build_xw<<<1024, 256, 0, s>>>(g.N, g.L, 3 * (g.N / 2) * (g.N / 2), deconv, ballft, xw);
     return cudaGetLastError();
 }
 
@@ -523,15 +549,6 @@ struct YStaged {
     static constexpr bool on = !SP && Radix<NF, S>::r2 == 1;
 };
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, bool valid)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// all but the most recently committed group have landed (for this thread)
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
 template <int NF, bool SP, int S>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
@@ -633,183 +650,29 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     }
 }
 
-// Level-summed spectrum of one instance for the modes owned by this thread
-// after the last stage of the x transform: output position pos = j + r NS of
-// butterfly (c, j) is kept when r < R/4 (m_x = pos) or r >= 3R/4
-// (m_x = pos - n), i.e. exactly m_x in [-N/2, N/2); those slots of F hold
-// sum_l T_l(|m|^2) D(m) FFT_x[Y_l](m) for m_y = mode(j_y), m_z = 16 ch + c.
-// Level l + 1 is loaded while level l is transformed.
-template <int NF, int S>
-struct XModes {
-    static constexpr int R = LastStage<NF, S>::R, NS = LastStage<NF, S>::NS;
-    static constexpr int IT = (NS * CL + TB - 1) / TB;
-    static __device__ __forceinline__ constexpr bool kept(int r) { return r < R / 4 || r >= 3 * R / 4; }
-};
-
-// Per-item table of the level weights the x pass applies: for the item's m_y
-// and its 16 z-modes m_z = 16 ch + c, and a = |m_x| in [0, N/2],
-//   Ts[(lg (N/2 + 1) + a) 16 + c] = T_{l0+lg}(a^2 + m_y^2 + m_z^2) D(a) D(m_y) D(m_z),
-// lg < nl.  The window transform is even, so D(-a) = D(a) and one entry serves
-// m_x = a and m_x = -a; the index a = N/2 addresses m_x = -N/2 in the
-// deconvolution table's FFT order.  Built in shared memory by the whole block,
-// it replaces the table gathers of every level of both spectra.
-template <int NI>
-__device__ __forceinline__ void build_xweights(float *Ts, const Tables &tb, int l0, int nl, int jy, int ch)
-{
-    constexpr int A = NI / 2 + 1;
-    const int my = mode_of(jy, NI);
-    const float dy = tb.deconv[jy];
-    const long long Q = tb.qmax + 1;
-    const int tot = nl * A * CL;
-    for (int e = threadIdx.x; e < tot; e += TB) {
-        const int c = e % CL, a = (e / CL) % A, lg = e / (CL * A);
-        const int mz = ch * CL + c;
-        Ts[e] = tb.ballft[(l0 + lg) * Q + a * a + my * my + mz * mz] * (tb.deconv[a] * dy * tb.deconv[mz]);
-    }
-}
-
-// Ts holds the weights of levels [ts_base, ts_base + G) of the current item;
-// a level outside that range rebuilds it (after the barrier that ends the
-// previous level, before the one that publishes the level's first stage).
-template <int NF, int NI, bool SP, int S>
-__device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF, S>::IT][XModes<NF, S>::R], const Geometry &g,
-                                           const Tables &tb, const InstDesc *__restrict__ inst,
-                                           const InstPlan *__restrict__ plan, int si, const float2 *__restrict__ y1,
-                                           int jy, int ch, const float2 *tw, float2 *S0, float2 *S1, float *Ts, int G,
-                                           int &ts_base)
-{
-    using XM = XModes<NF, S>;
-    constexpr int H = NI / 2, N = NI, A = NI / 2 + 1;
-    const int L = g.L;
-#pragma unroll
-    for (int it = 0; it < XM::IT; it++)
-#pragma unroll
-        for (int r = 0; r < XM::R; r++) F[it][r] = make_float2(0.f, 0.f);
-    const InstPlan p = plan[si];
-    if (p.b[0] == 0) return;
-    const InstDesc d = inst[si];
-    const int b0 = p.b[0], px = p.pos0[0];
-    auto src = [&](int l) {
-        const float2 *base = y1 + d.y1_off + (long long)l * b0 * N * H + (long long)jy * H + ch * CL;
-        return [=](int c, int pos) {
-            int ix = pos - px;
-            if (ix < 0) ix += NF;
-            return ix < b0 ? base[(long long)ix * N * H + c] : make_float2(0.f, 0.f);
-        };
-    };
-    FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
-    in.load(src(0));
-    for (int l = 0; l < L; l++) {
-        if (l < ts_base || l >= ts_base + G) {
-            ts_base = l;
-            build_xweights<NI>(Ts, tb, l, min(G, L - l), jy, ch);
-        }
-        if constexpr (SP) in.scatter(S0);
-        else rr_first<NF, Radix<NF, S>::r0, false, CL, TB>(in, S0);
-        __syncthreads();
-        if (l + 1 < L) in.load(src(l + 1));
-        const float *Tl = Ts + (l - ts_base) * A * CL;
-        auto sink = [&](int it, int r, int c, int pos, float2 v) {
-            if (!XM::kept(r)) return;
-            const int mx = r < XM::R / 4 ? pos : pos - NF;
-            const float Mv = Tl[(mx < 0 ? -mx : mx) * CL + c];
-            F[it][r] = make_float2(fmaf(Mv, v.x, F[it][r].x), fmaf(Mv, v.y, F[it][r].y));
-        };
-        if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
-        else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
-        __syncthreads();
-    }
-}
-
-// Calls f(it, r, c, jx) for every kept mode slot of the calling thread.
-template <int NF, int NI, int S, class Fn>
-__device__ __forceinline__ void for_kept(Fn f)
-{
-    using XM = XModes<NF, S>;
-#pragma unroll
-    for (int it = 0; it < XM::IT; it++) {
-        const int idx = (int)threadIdx.x + it * TB;
-        if ((XM::NS * CL) % TB != 0 && idx >= XM::NS * CL) break;
-        const int c = idx % CL, j = idx / CL;
-#pragma unroll
-        for (int r = 0; r < XM::R; r++) {
-            if (!XM::kept(r)) continue;
-            const int pos = j + r * XM::NS;
-            const int mx = r < XM::R / 4 ? pos : pos - NF;
-            f(it, r, c, mx < 0 ? mx + NI : mx);
-        }
-    }
-}
-
 // ------------------------------------------------------------------ fft x + combine
-// For each pair and each (j_y, chunk of 16 z-modes):
-//   F_s(m) = sum_l T_l(|m|^2) D(m) FFT_x[Y_{s,l}](m)    (s = A, B)
-//   g'(m)  = P^-3 (-1)^(m_x+m_y+m_z) F_A(m) conj(F_B(m)), zero on the Nyquist planes
-//   H(k_x, j_y, m_z) = sum_{j_x} g'(m) exp(+2 pi i j_x k_x / N)
-// D(m) = deconv[j_x] deconv[j_y] deconv[m_z].  The sign moves the origin of the
-// translation grid to t = -P/2: exp(2 pi i m (-P/2) / P) = (-1)^m.
-// With pair.a < 0, F_A comes from the cached spectrum; with pair.b < 0, F_A is
-// written to `fa_out` and nothing else happens.
+// Every (j_y, chunk of 16 z-modes) item of every pair through x_item
+// (bc_passes.cuh): forward x transform of both spectra with the level sum,
+// conjugate product and inverse x transform.
 template <int NF, int NI, bool SP, int S>
 __global__ void __launch_bounds__(TB, (NF <= 256 ? 2 : 1))
 k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan *__restrict__ plan,
         const PairDesc *__restrict__ pairs, int npairs, const float2 *__restrict__ y1,
         const float2 *__restrict__ fa_cache, float2 *fa_out, float2 *h, int G)
 {
-    using XM = XModes<NF, S>;
     extern __shared__ float4 sm4[];
-    float2 *twF = reinterpret_cast<float2 *>(sm4);
-    float2 *twI = twF + NF, *S0 = twI + NI, *S1 = S0 + NF * CL, *FAt = S1 + NF * CL;
-    float *Ts = reinterpret_cast<float *>(FAt + NI * CL); // G levels of build_xweights
-    load_twiddles<NF>(twF, tb.tw_n);
-    load_twiddles<NI>(twI, tb.tw_N);
-    constexpr int H = NI / 2, N = NI;
-    constexpr int nch = H / CL;
-    const int items = N * nch;
-    const int part = threadIdx.x & 7, r8 = threadIdx.x >> 3;
+    using XL = XSmem<NF, NI, SP, S>;
+    const typename XL::Ptr sm = XL::carve(reinterpret_cast<float2 *>(sm4));
+    load_twiddles<NF>(sm.twF, tb.tw_n);
+    load_twiddles<NI>(sm.twI, tb.tw_N);
+    constexpr int nch = NI / 2 / CL;
+    const int items = NI * nch;
     RotStart rs;
     for (int pi = 0; pi < npairs; pi++) {
         const PairDesc pr = pairs[pi];
         for (int it = rs.first(); it < items; it += gridDim.x) {
             const int jy = it / nch, ch = it - jy * nch;
-            const int my = mode_of(jy, N);
-            int ts_base = INT_MIN / 2; // no level weights built for this item yet
-            // F_A waits in its own tile (each thread reads back only what it wrote)
-            // while F_B is accumulated in registers.
-            {
-                float2 FA[XM::IT][XM::R];
-                if (pr.a < 0) {
-                    for_kept<NF, NI, S>([&](int i2, int r, int c, int jx) {
-                        FAt[jx * CL + c] = fa_cache[((long long)jx * N + jy) * H + ch * CL + c];
-                    });
-                } else {
-                    spectrum_x<NF, NI, SP, S>(FA, g, tb, inst, plan, pr.a, y1, jy, ch, twF, S0, S1, Ts, G, ts_base);
-                    for_kept<NF, NI, S>([&](int i2, int r, int c, int jx) { FAt[jx * CL + c] = FA[i2][r]; });
-                }
-            }
-            if (pr.b < 0) {
-                for_kept<NF, NI, S>([&](int i2, int r, int c, int jx) {
-                    fa_out[((long long)jx * N + jy) * H + ch * CL + c] = FAt[jx * CL + c];
-                });
-                continue;
-            }
-            float2 FB[XM::IT][XM::R];
-            spectrum_x<NF, NI, SP, S>(FB, g, tb, inst, plan, pr.b, y1, jy, ch, twF, S0, S1, Ts, G, ts_base);
-            for_kept<NF, NI, S>([&](int i2, int r, int c, int jx) {
-                const int mx = mode_of(jx, N), mz = ch * CL + c;
-                float2 v = make_float2(0.f, 0.f);
-                if (jx != N / 2 && jy != N / 2) {
-                    v = cmulc(FAt[jx * CL + c], FB[i2][r]);
-                    v = cscale(v, ((mx + my + mz) & 1) ? -g.inv_P3 : g.inv_P3);
-                }
-                S0[jx * CL + c] = v;
-            });
-            __syncthreads();
-            const float2 *res = il_fft<NI, true, CL, TB>(S0, S1, twI);
-            float2 *Hp = h + pr.h_off + (long long)jy * H + ch * CL + 2 * part;
-            for (int kx = r8; kx < N; kx += TB / 8)
-                *reinterpret_cast<float4 *>(Hp + (long long)kx * N * H) = *reinterpret_cast<const float4 *>(res + kx * CL + 2 * part);
-            __syncthreads();
+            x_item<NF, NI, SP, S>(g, tb, inst, plan, pr, jy, ch, y1, fa_cache, fa_out, h, G, sm);
         }
         rs.rot += items;
     }
@@ -855,18 +718,6 @@ k_ifft_y(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
         }
         rs.rot += items;
     }
-}
-
-// ------------------------------------------------------------------ inverse z (c2r)
-// Peak keys: an order-preserving map of the FP32 value to the high 32 bits
-// (negative values bit-inverted, non-negative ones with the sign bit set) and
-// the complement of the linear grid index in the low 32 bits, so that the
-// maximum key is the largest value and, among equal values, the lowest index.
-__device__ __forceinline__ unsigned long long peak_key(float v, unsigned idx)
-{
-    unsigned u = __float_as_uint(v);
-    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-    return ((unsigned long long)u << 32) | (unsigned long long)(0xFFFFFFFFu - idx);
 }
 
 __global__ void k_decode_peaks(const unsigned long long *__restrict__ keys, int n, float *peak, int *argmax)
@@ -1043,11 +894,10 @@ static cudaError_t fft_x_t(const Geometry &g, const Tables &t, const InstDesc *i
         return fft_x_t<NF, NI, false, 1>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
     // level weights for as many levels as fit beside the tiles at the kernel's
     // blocks per SM (two up to NF = 256, else one): all of them in the usual cases
-    const size_t base = sizeof(float2) * (NF + NI + 2 * NF * CL + NI * CL);
-    const size_t per_level = sizeof(float) * (NI / 2 + 1) * CL;
-    const size_t room = (NF <= 256 ? 228 * 1024 / 2 : 228 * 1024) - 1024 - base;
-    const int G = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.L, room / per_level));
-    const size_t smem = base + per_level * G;
+    using XL = XSmem<NF, NI, SP, S>;
+    const size_t room = (NF <= 256 ? 228 * 1024 / 2 : 228 * 1024) - 1024 - XL::bytes(0);
+    const int G = (int)std::max<size_t>(1, std::min<size_t>((size_t)g.L, room / XL::per_level));
+    const size_t smem = XL::bytes(G);
     cudaError_t e = set_smem(k_fft_x<NF, NI, SP, S>, smem);
     if (e != cudaSuccess) return e;
     k_fft_x<NF, NI, SP, S><<<resident_blocks(k_fft_x<NF, NI, SP, S>, smem, nsm), TB, smem, s>>>(

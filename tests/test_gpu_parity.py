@@ -41,15 +41,17 @@ def f32(shape):
 
 
 SPREADS = (0, 1)
-# (spread, z_transform): boxes + radix FFT z pass, boxes + tensor-core z pass, binned
-MODES = ((0, 0), (0, 1), (1, 0))
+# (spread, z_transform, persistent): boxes + radix FFT z pass, boxes + tensor-core z
+# pass, binned -- with the back half as one persistent launch -- and boxes + the
+# tensor-core z pass with the back half as three launches
+MODES = ((0, 0, 1), (0, 1, 1), (1, 0, 1), (0, 1, 0))
 
 
-def run_gpu(A, B, quats, N, W, radii=None, period=2.0, spread=1, fft_schedule=0, z_transform=0):
+def run_gpu(A, B, quats, N, W, radii=None, period=2.0, spread=1, fft_schedule=0, z_transform=0, persistent=1):
     bc = bcmod()
     radii = A.radii if radii is None else radii
     ctx = bc.Context(N, W, radii, period)
-    ctx.set_tuning(spread=spread, fft_schedule=fft_schedule, z_transform=z_transform)
+    ctx.set_tuning(spread=spread, fft_schedule=fft_schedule, z_transform=z_transform, persistent=persistent)
     try:
         sa = ctx.shape(A.xyz.astype(np.float32), A.level)
         sb = ctx.shape(B.xyz.astype(np.float32), B.level)
@@ -65,10 +67,11 @@ def run_gpu(A, B, quats, N, W, radii=None, period=2.0, spread=1, fft_schedule=0,
 
 def run_modes(A, B, quats, N, W, **kw):
     """(label, grids) for each implementation: spreading 0 with each z transform, spreading 1."""
-    for sp, zt in MODES:
+    for sp, zt, pe in MODES:
         if zt and N > 128:
-            continue
-        yield f"{sp}{' z-tc' if zt else ''}", run_gpu(A, B, quats, N, W, spread=sp, z_transform=zt, **kw)
+            zt = 0
+        yield (f"{sp}{' z-tc' if zt else ''}{' persistent' if pe else ' 3 launches'}",
+               run_gpu(A, B, quats, N, W, spread=sp, z_transform=zt, persistent=pe, **kw))
 
 
 def oracle_grid(A, B, q, N, period=2.0):
@@ -143,14 +146,14 @@ def test_grid_size_256_sampled():
 
 
 # ------------------------------------------------------------------ edge cases
-@pytest.mark.parametrize("spread,zt", MODES)
-def test_repeated_calls_are_identical(spread, zt):
+@pytest.mark.parametrize("spread,zt,pe", MODES)
+def test_repeated_calls_are_identical(spread, zt, pe):
     # The spreading boxes (bin counts) are cleared by the pass that consumes
     # them; a second call on the same context must not see the first call's.
     bc = bcmod()
     wl = synth.small_pair(2)
     ctx = bc.Context(wl.N, wl.W, wl.radii)
-    ctx.set_tuning(spread=spread, z_transform=zt)
+    ctx.set_tuning(spread=spread, z_transform=zt, persistent=pe)
     sa = ctx.shape(wl.A.xyz, wl.A.level)
     sb = ctx.shape(wl.B.xyz, wl.B.level)
     g1 = ctx.correlate(sa, sb, wl.quats).clone()
@@ -288,6 +291,18 @@ def test_shape_straddling_the_periodic_boundary():
             check(got[r], refs[r], what=f"straddling, rot {r}, spread {sp}")
 
 
+def test_wide_box_takes_the_register_path_at_N128():
+    # An x extent of about 240 of the 256 fine cells is beyond the x pass's
+    # staging tiles (160 rows at n = 256): that pair takes the register-fed path.
+    A = synth.ellipsoid_shape(400, 21, synth.RADII_4, synth.PROBS_4, semi=(0.88, 0.3, 0.25))
+    B = synth.torus_shape(400, 22, synth.RADII_4, synth.PROBS_4)
+    q = synth.shoemake_quaternions(synth.SplitMix64(9), 1)
+    idx = synth.translation_sample(128, 4096, seed=2)
+    ref = O.band_limited_corr(f32(A), f32(B), q[0].astype(np.float32).astype(np.float64), 128, idx=idx)
+    for sp, got in run_modes(A, B, q, 128, 8):
+        check(got[0].reshape(-1)[idx], ref, what=f"wide box N=128, spread {sp}")
+
+
 def test_invalid_arguments_raise():
     bc = bcmod()
     ctx = bc.Context(32, 6, (0.04, 0.08))
@@ -360,8 +375,8 @@ def test_autotune_keeps_a_valid_choice():
     sa.close(); sb.close(); ctx.close()
 
 
-@pytest.mark.parametrize("spread,zt", MODES)
-def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread, zt):
+@pytest.mark.parametrize("spread,zt,pe", MODES)
+def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread, zt, pe):
     # Identical passes (same descriptors and buffers) replay the recorded graph;
     # a changed rotation re-records; switching replay off launches kernel by kernel.
     bc = bcmod()
@@ -369,7 +384,7 @@ def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread, zt):
     q = synth.shoemake_quaternions(synth.SplitMix64(31), 2).astype(np.float32)
     refs = [oracle_grid(wl.A, wl.B, q[r], wl.N) for r in range(2)]
     ctx = bc.Context(wl.N, wl.W, wl.radii)
-    ctx.set_tuning(spread=spread, graphs=1, z_transform=zt)
+    ctx.set_tuning(spread=spread, graphs=1, z_transform=zt, persistent=pe)
     sa = ctx.shape(wl.A.xyz, wl.A.level)
     sb = ctx.shape(wl.B.xyz, wl.B.level)
     out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device="cuda")
