@@ -146,7 +146,7 @@ struct bc_ctx_s {
     double *radii_dev = nullptr;
     float *deconv = nullptr, *ballft = nullptr;
     float2 *tw_n = nullptr, *tw_N = nullptr;
-    float *consts = nullptr; // [0] = exp(beta) / I0(beta)
+    float *consts = nullptr; // [0] = exp(beta) / I0(beta), then the window's piecewise polynomials
     float *xw = nullptr;     // x-pass level weights (Tables::xw) of the correlation
     int *modes = nullptr;    // BC_MOMENTS lowest modes of the half spectrum, (m_x, m_y, m_z) each
     int qmax = 0;
@@ -328,7 +328,7 @@ bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
         if ((e = cudaMalloc(&c->ballft, sizeof(float) * g.L * (c->qmax + 1))) != cudaSuccess) return bail(e, "cudaMalloc ballft");
         if ((e = cudaMalloc(&c->tw_n, sizeof(float2) * g.n)) != cudaSuccess) return bail(e, "cudaMalloc tw_n");
         if ((e = cudaMalloc(&c->tw_N, sizeof(float2) * g.N)) != cudaSuccess) return bail(e, "cudaMalloc tw_N");
-        if ((e = cudaMalloc(&c->consts, sizeof(float) * 4)) != cudaSuccess) return bail(e, "cudaMalloc consts");
+        if ((e = cudaMalloc(&c->consts, sizeof(float) * CONSTS_FLOATS)) != cudaSuccess) return bail(e, "cudaMalloc consts");
         {
             // the BC_MOMENTS lowest modes of the half spectrum (m_z >= 0, m != 0, components
             // inside (-N/2, N/2)), ordered by (|m|^2, m_x, m_y, m_z)

@@ -87,11 +87,12 @@ __global__ void __launch_bounds__(BIN_WARPS * 32)
 k_bin(Geometry g, const float *__restrict__ consts, const float4 *__restrict__ ku, const InstPlan *__restrict__ plan,
       int *cur, float *rec, int total)
 {
-    const float inv_scaled_i0beta = consts[0];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int W = g.W, L = g.L, n = g.n;
-    const float halfW = 0.5f * (float)W, twoOverW = 2.0f / (float)W;
+    const float halfW = 0.5f * (float)W, xoff = 0.5f * (float)W - 1.f;
     const int a = lane < 2 ? 0 : (lane - 2) / W, t = lane < 2 ? 0 : (lane - 2) - a * W; // this lane's weight
+    float kc[KB_NC];
+    kb_load(consts, lane >= 2 && lane - 2 < 3 * W ? t : 0, kc);
     for (int base = (blockIdx.x * BIN_WARPS + wib) * 32; base < total; base += gridDim.x * BIN_WARPS * 32) {
         const int k = base + lane;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -119,7 +120,7 @@ k_bin(Geometry g, const float *__restrict__ consts, const float4 *__restrict__ k
             } else if (lane - 2 < 3 * W) {
                 const float ua = a == 0 ? ux : (a == 1 ? uy : uz);
                 const int ga = a == 0 ? gx : (a == 1 ? gy : gz);
-                val = kb_window((ua - (float)(ga + t)) * twoOverW, g.beta, inv_scaled_i0beta);
+                val = kb_poly(kc, (ua - (float)ga) - xoff);
             }
             rec[(long long)sj * BIN_REC + lane] = val;
         }

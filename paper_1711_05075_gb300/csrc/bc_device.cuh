@@ -30,21 +30,30 @@ __device__ __forceinline__ void load_twiddles(float2 *dst, const float2 *__restr
 }
 
 // Kaiser-Bessel window phi(v) = I0(beta sqrt(1 - s^2)) / I0(beta), s = 2v/W,
-// zero for |s| > 1 (the clamp makes it 1/I0(beta) there, which callers never
-// reach: every stencil offset satisfies |s| <= 1).
-//
-// Evaluated as exp(beta (sq - 1)) * [exp(-x) I0(x)] / [exp(-beta) I0(beta)],
-// x = beta sq: I0 grows like e^x, so I0(x) alone carries the FP32 rounding of
-// x as a relative error of about x 2^-24, whereas exp(-x) I0(x) varies slowly
-// and the exponent beta (sq - 1) = -beta s^2 / (1 + sq) is small where phi is
-// large.  inv_scaled_i0beta = exp(beta) / I0(beta), built in FP64.
-__device__ __forceinline__ float kb_window(float s, float beta, float inv_scaled_i0beta)
+// on |s| <= 1 (fine-grid cells), as piecewise polynomials.  A knot at u has stencil cells
+// g0 + t, t < W, g0 = ceil(u - W/2); with x = u - g0 - (W/2 - 1) in (0, 1] the
+// weight of cell g0 + t is phi(x + W/2 - 1 - t), a smooth function of x on
+// [0, 1] for each t (phi is a power series in 1 - s^2 inside its support).
+// Each piece is replaced by its degree-KB_DEG interpolant at Chebyshev nodes,
+// written in powers of y = x - 1/2 and evaluated by Horner's rule in FP32
+// (piecewise-polynomial kernel evaluation as in Barnett, Magland and af
+// Klinteberg, SIAM J. Sci. Comput. 2019).  The coefficients are built in FP64
+// from the closed form (k_build_tables); for W = 6, 8, 10 at their default
+// beta the FP32 evaluation stays within 1e-7 of phi (phi <= 1).
+__device__ __forceinline__ float kb_poly(const float (&c)[KB_NC], float x)
 {
-    const float s2 = fminf(s * s, 1.f);
-    const float sq = sqrtf(1.f - s2);
-    const float x = beta * sq;
-    const float scaled_i0 = cyl_bessel_i0f(x) * expf(-x);
-    return expf(-beta * s2 / (1.f + sq)) * scaled_i0 * inv_scaled_i0beta;
+    const float y = x - 0.5f;
+    float acc = c[KB_DEG];
+#pragma unroll
+    for (int m = KB_DEG - 1; m >= 0; m--) acc = fmaf(acc, y, c[m]);
+    return acc;
+}
+
+// Coefficients of piece t (consts + KB_OFF + t KB_NC) into registers.
+__device__ __forceinline__ void kb_load(const float *__restrict__ consts, int t, float (&c)[KB_NC])
+{
+#pragma unroll
+    for (int m = 0; m < KB_NC; m++) c[m] = consts[KB_OFF + t * KB_NC + m];
 }
 
 // Transform of the indicator of a ball of radius r at angular wavenumber k

@@ -88,6 +88,11 @@ cudaError_t launch_prepare(const Geometry &g, const InstDesc *inst, int ninst, i
 // then the end of bin b); launch_fft_z_binned spreads each z-transform item's
 // knots in shared memory and transforms them (no spreading grid in HBM).
 constexpr int MAX_W = 10;   // widest window (bc_create checks)
+// Tables::consts: [0] = exp(beta) / I0(beta); from [KB_OFF], per stencil offset
+// t < W, the KB_NC coefficients of the window's piecewise polynomial (see
+// kb_poly in bc_device.cuh).
+constexpr int KB_DEG = 10, KB_NC = KB_DEG + 1, KB_OFF = 4;
+constexpr int CONSTS_FLOATS = KB_OFF + MAX_W * KB_NC;
 constexpr int BIN_REC = 32; // floats per binned knot: g0_y, g0_z (int bits), W x-, W y-, W z-weights
 // Plans each instance (as launch_prepare does without bins) and turns the counts
 // into cursors, one block per instance.

@@ -64,6 +64,41 @@ __global__ void k_build_tables(int N, int n, int W, int L, int qmax, double beta
 {
     const double pi = 3.14159265358979323846;
     if (blockIdx.x == 0 && threadIdx.x == 0) consts[0] = (float)(exp(beta) / cyl_bessel_i0(beta));
+    if (blockIdx.x == 0 && threadIdx.x < W) {
+        // window piece t (kb_poly): interpolate f(y) = phi(y + 1/2 + W/2 - 1 - t),
+        // y in [-1/2, 1/2], at the Chebyshev nodes y_k = cos(pi (k + 1/2) / KB_NC) / 2
+        // as sum_j a_j T_j(2y), then expand in powers of y
+        const int t = threadIdx.x;
+        const double i0b = cyl_bessel_i0(beta);
+        double f[KB_NC], a[KB_NC];
+        for (int k = 0; k < KB_NC; k++) {
+            const double v = 0.5 * cos(pi * (k + 0.5) / KB_NC) + 0.5 + 0.5 * W - 1.0 - t;
+            const double s2 = (2.0 * v / W) * (2.0 * v / W);
+            f[k] = s2 <= 1.0 ? cyl_bessel_i0(beta * sqrt(1.0 - s2)) / i0b : 0.0;
+        }
+        for (int j = 0; j < KB_NC; j++) {
+            double acc = 0.0;
+            for (int k = 0; k < KB_NC; k++) acc += f[k] * cos(pi * j * (k + 0.5) / KB_NC);
+            a[j] = (j == 0 ? 1.0 : 2.0) * acc / KB_NC;
+        }
+        // power coefficients in z = 2y: T_0 = 1, T_1 = z, T_{j+1} = 2 z T_j - T_{j-1}
+        double tm[KB_NC] = {}, tc[KB_NC] = {}, b[KB_NC] = {};
+        tm[0] = 1.0;
+        tc[1] = 1.0;
+        b[0] = a[0];
+        b[1] = a[1];
+        for (int j = 2; j < KB_NC; j++) {
+            double tn[KB_NC];
+            for (int m = 0; m < KB_NC; m++) tn[m] = (m > 0 ? 2.0 * tc[m - 1] : 0.0) - tm[m];
+            for (int m = 0; m < KB_NC; m++) {
+                b[m] += a[j] * tn[m];
+                tm[m] = tc[m];
+                tc[m] = tn[m];
+            }
+        }
+        double scale = 1.0;
+        for (int m = 0; m < KB_NC; m++, scale *= 2.0) consts[KB_OFF + t * KB_NC + m] = (float)(b[m] * scale);
+    }
     const int total = N + L * (qmax + 1) + n + N;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         if (t < N) {
@@ -342,12 +377,15 @@ __global__ void __launch_bounds__(SPREAD_WARPS * 32)
 k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restrict__ inst,
          const float4 *__restrict__ ku, const InstPlan *__restrict__ plan, float *grid, int total)
 {
-    const float inv_scaled_i0beta = consts[0];
     __shared__ float wts[SPREAD_WARPS][3][16];
     __shared__ float4 wy4[SPREAD_WARPS][3];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int W = g.W, W2 = W * W;
-    const float halfW = 0.5f * (float)W, twoOverW = 2.0f / (float)W, invW = 1.0f / (float)W;
+    const float halfW = 0.5f * (float)W, invW = 1.0f / (float)W, xoff = 0.5f * (float)W - 1.f;
+    // lane 0 .. 3W - 1 evaluates the weight of stencil offset t on axis a for every knot
+    const int wa = lane / W, wt = lane - wa * W;
+    float kc[KB_NC];
+    kb_load(consts, lane < 3 * W ? wt : 0, kc);
     for (int k = blockIdx.x * SPREAD_WARPS + wib; k < total; k += gridDim.x * SPREAD_WARPS) {
         const float4 v = ku[k];
         const int tag = __float_as_int(v.w);
@@ -357,10 +395,9 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
         const float u0 = v.x, u1 = v.y, u2 = v.z;
         const int g0[3] = {(int)ceilf(u0 - halfW), (int)ceilf(u1 - halfW), (int)ceilf(u2 - halfW)};
         if (lane < 3 * W) {
-            const int a = lane / W, t = lane - a * W;
-            const float ua = a == 0 ? u0 : (a == 1 ? u1 : u2);
-            const int ga = a == 0 ? g0[0] : (a == 1 ? g0[1] : g0[2]);
-            wts[wib][a][t] = kb_window((ua - (float)(ga + t)) * twoOverW, g.beta, inv_scaled_i0beta);
+            const float ua = wa == 0 ? u0 : (wa == 1 ? u1 : u2);
+            const int ga = wa == 0 ? g0[0] : (wa == 1 ? g0[1] : g0[2]);
+            wts[wib][wa][wt] = kb_poly(kc, (ua - (float)ga) - xoff);
         }
         __syncwarp();
         const int nyb = (p.b[1] + 31) >> 5, bz = p.b[2];

@@ -45,7 +45,7 @@ constexpr size_t oBallft = al(oDeconv + sizeof(float) * kN);
 constexpr size_t oTwn = al(oBallft + sizeof(float) * kL * kQ);
 constexpr size_t oTwN = al(oTwn + sizeof(float2) * kn);
 constexpr size_t oConsts = al(oTwN + sizeof(float2) * kN);
-constexpr size_t oErr = al(oConsts + sizeof(float) * 4);
+constexpr size_t oErr = al(oConsts + sizeof(float) * CONSTS_FLOATS);
 constexpr size_t oStats = al(oErr + sizeof(int));
 constexpr size_t oBoxes = al(oStats + sizeof(unsigned) * 4);
 constexpr size_t oInst = al(oBoxes + sizeof(int) * 8 * 2);
