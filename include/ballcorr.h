@@ -379,6 +379,18 @@ bc_status bc_mlp_grads(bc_mlp_t net, const float *X, const float *t, int n, floa
 /* One Adam step on mean((y - t)^2) with learning rate lr; loss as above. */
 bc_status bc_mlp_train_step(bc_mlp_t net, const float *X, const float *t, int n, float lr, float *loss);
 
+/* Many Adam steps in one call: `epochs` passes over the n samples (X: device,
+ * n rows of the bc_mlp_features layout; t: device, n targets), each pass in a
+ * pseudo-random order perm(i) = (a i + c) mod n (a coprime to n; a and c drawn
+ * from splitmix64 of (seed, pass)), in floor(n / batch) batches of `batch`
+ * rows gathered on the device; learning rate lr 0.5 (1 + cos(pi e / epochs))
+ * in pass e.  loss (device, 1 float; may be NULL) receives the loss of the
+ * last batch.  Deterministic for fixed arguments.  Asynchronous.
+ * Errors: BC_ERR_ARG (null pointer, batch outside [1, n], epochs < 1,
+ * lr <= 0), BC_ERR_OOM, BC_ERR_CUDA. */
+bc_status bc_mlp_train(bc_mlp_t net, const float *X, const float *t, int n, int batch, int epochs, float lr,
+                       unsigned long long seed, float *loss);
+
 /* Reads (get = 1) or writes (get = 0) the parameters and the two Adam moment
  * vectors (host arrays in the parameter layout; any may be NULL) and the step
  * count (may be NULL): checkpoint and resume.  Synchronous. */

@@ -88,6 +88,7 @@ def lib():
         L.bc_mlp_predict.argtypes = [vp, vp, i, vp]
         L.bc_mlp_grads.argtypes = [vp, vp, vp, i, vp, vp]
         L.bc_mlp_train_step.argtypes = [vp, vp, vp, i, ctypes.c_float, vp]
+        L.bc_mlp_train.argtypes = [vp, vp, vp, i, i, i, ctypes.c_float, ctypes.c_ulonglong, vp]
         L.bc_mlp_state.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_longlong), i]
         L.bc_learned_sweep.argtypes = [vp, vp, vp, vp, vp, i, i, vp, vp, vp, vp]
         L.bc_learned_sweep_avg.argtypes = [vp, vp, vp, vp, vp, i, i, vp, i, vp, vp, vp, vp]
@@ -99,7 +100,8 @@ def lib():
             getattr(L, f).restype = st
         L.bc_topk.restype = st
         for f in ("bc_shape_moments", "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
-                  "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep", "bc_learned_sweep_avg"):
+                  "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_train", "bc_mlp_state", "bc_learned_sweep",
+                  "bc_learned_sweep_avg"):
             getattr(L, f).restype = st
         L.bc_selftest_wait.argtypes = [vp]
         for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shapes_create", "bc_shape_destroy", "bc_correlate",
@@ -240,6 +242,10 @@ def bc_mlp_grads(net, X, t, n, grads, loss):
 
 def bc_mlp_train_step(net, X, t, n, lr, loss):
     _check(lib().bc_mlp_train_step(net, _ptr(X), _ptr(t), int(n), float(lr), _ptr(loss)))
+
+
+def bc_mlp_train(net, X, t, n, batch, epochs, lr, seed, loss):
+    _check(lib().bc_mlp_train(net, _ptr(X), _ptr(t), int(n), int(batch), int(epochs), float(lr), int(seed), _ptr(loss)))
 
 
 def bc_mlp_state(net, params, m, v, step, get):
@@ -547,6 +553,10 @@ class MLP:
 
     def train_step(self, X, t, lr, loss=None):
         bc_mlp_train_step(self.handle, X, t, X.shape[0], lr, loss)
+
+    def train(self, X, t, epochs, batch, lr, seed=0, loss=None):
+        """`epochs` passes of Adam steps over (X, t) in device-shuffled batches (bc_mlp_train)."""
+        bc_mlp_train(self.handle, X, t, X.shape[0], batch, epochs, lr, seed, loss)
 
     def state(self):
         p = np.empty(self.nparams, np.float32)

@@ -13,6 +13,7 @@
 // gradients) and accumulates in FP32 on the tensor cores (mma.sync m16n8k16
 // BF16 -> FP32).  All reductions run in a fixed order, so training is
 // deterministic for a fixed launch configuration.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -63,6 +64,8 @@ struct GemmArgs {
     int M, N, K;
     const float *bias;
     int relu;
+    int kchunk = 0;     // split K: slice z of the grid sums k in [z kchunk, (z + 1) kchunk) (0: all of K)
+    long long sCz = 0;  // and writes its partial product at C + z sCz
 };
 
 constexpr int GT = 64, GK = 32, GKP = GK + 8; // smem row pitch in bf16 (80 bytes)
@@ -88,12 +91,14 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g)
 #pragma unroll
             for (int r = 0; r < 4; r++) acc[i][j][r] = 0.f;
 
-    for (int k0 = 0; k0 < g.K; k0 += GK) {
+    const int kb = g.kchunk ? (int)blockIdx.z * g.kchunk : 0;
+    const int ke = g.kchunk ? min(g.K, kb + g.kchunk) : g.K;
+    for (int k0 = kb; k0 < ke; k0 += GK) {
         for (int e = threadIdx.x; e < GT * GK; e += 128) {
             const int r = e / GK, kk = e - r * GK;
             const int m = m0 + r, n = n0 + r, k = k0 + kk;
-            const float a = (m < g.M && k < g.K) ? g.A[m * g.sAm + k * g.sAk] : 0.f;
-            const float b = (n < g.N && k < g.K) ? g.B[k * g.sBk + n * g.sBn] : 0.f;
+            const float a = (m < g.M && k < ke) ? g.A[m * g.sAm + k * g.sAk] : 0.f;
+            const float b = (n < g.N && k < ke) ? g.B[k * g.sBk + n * g.sBn] : 0.f;
             As[r][kk] = __float2bfloat16_rn(a);
             Bs[r][kk] = __float2bfloat16_rn(b);
         }
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g)
                     float v = acc[i][j][r];
                     if (g.bias) v += g.bias[n];
                     if (g.relu) v = fmaxf(v, 0.f);
-                    g.C[m * g.sCm + n * g.sCn] = v;
+                    g.C[blockIdx.z * g.sCz + m * g.sCm + n * g.sCn] = v;
                 }
             }
 }
@@ -148,6 +153,43 @@ cudaError_t gemm(const GemmArgs &a, cudaStream_t s)
 {
     dim3 grid((a.N + GT - 1) / GT, (a.M + GT - 1) / GT);
     k_gemm_bf16<<<grid, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// out[m][n] = sum_z part[z][m][n], z in increasing order (M x N dense partials)
+__global__ void k_sum_partials(const float *__restrict__ part, int nz, int M, int N, float *out, long long sOm)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)M * N) return;
+    float s = 0.f;
+    for (int z = 0; z < nz; z++) s += part[z * (long long)M * N + e];
+    out[(e / N) * sOm + e % N] = s;
+}
+
+// A weight gradient C = A B with a long K (the batch): K split into slices whose
+// partial products land in `part` and are then summed in a fixed order, so the
+// result does not depend on scheduling.  C is M x N with row stride sCm.
+cudaError_t gemm_splitk(GemmArgs a, float *part, long long part_floats, cudaStream_t s)
+{
+    const int tiles = ((a.N + GT - 1) / GT) * ((a.M + GT - 1) / GT);
+    int nz = std::max(1, std::min(32, 256 / std::max(tiles, 1)));
+    nz = (int)std::min<long long>(nz, std::max(1LL, part_floats / ((long long)a.M * a.N)));
+    nz = std::min(nz, (a.K + GK - 1) / GK);
+    const int kchunk = ((a.K + nz - 1) / nz + GK - 1) / GK * GK;
+    nz = (a.K + kchunk - 1) / kchunk;
+    float *C = a.C;
+    const long long sCm = a.sCm;
+    a.C = part;
+    a.sCm = a.N;
+    a.sCn = 1;
+    a.kchunk = kchunk;
+    a.sCz = (long long)a.M * a.N;
+    dim3 grid((a.N + GT - 1) / GT, (a.M + GT - 1) / GT, nz);
+    k_gemm_bf16<<<grid, 128, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long tot = (long long)a.M * a.N;
+    k_sum_partials<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nz, a.M, a.N, C, sCm);
     return cudaGetLastError();
 }
 
@@ -184,27 +226,55 @@ __global__ void k_relu_back(float *dh, const float *__restrict__ h, long long to
     if (e < total) dh[e] = h[e] > 0.f ? rbf(dh[e]) : 0.f;
 }
 
-// out[j] = sum_b bf16(v[b][j]) (or of v[b] when H == 1); fixed order per column
-__global__ void k_colsum(const float *__restrict__ v, int n, int H, int round_bf16, float *out)
+// Column sums over the batch in two fixed-order stages: block c sums rows
+// [c CS, (c + 1) CS) of every column into part[c][j], then the chunks are
+// summed in order.  Terms: bf16(v[b][j]) (round_bf16), v[b][j], or, with w,
+// w[b] bf16(v[b][j]).
+constexpr int CS = 64;
+__global__ void k_colsum_part(const float *__restrict__ v, const float *__restrict__ w, int n, int H, int round_bf16,
+                              float *part)
+{
+    const int c = blockIdx.x, b0 = c * CS, b1 = min(n, b0 + CS);
+    for (int j = threadIdx.x; j < H; j += blockDim.x) {
+        float s = 0.f;
+        for (int b = b0; b < b1; b++) {
+            const float x = v[(long long)b * H + j];
+            if (w) s = fmaf(w[b], rbf(x), s);
+            else s += round_bf16 ? rbf(x) : x;
+        }
+        part[(long long)c * H + j] = s;
+    }
+}
+
+__global__ void k_colsum_fin(const float *__restrict__ part, int nc, int H, float *out)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= H) return;
     float s = 0.f;
-    for (int b = 0; b < n; b++) {
-        const float x = v[(long long)b * H + j];
-        s += round_bf16 ? rbf(x) : x;
-    }
+    for (int c = 0; c < nc; c++) s += part[(long long)c * H + j];
     out[j] = s;
 }
 
-// dW3[j] = sum_b gy[b] bf16(h2[b][j]) (fixed order)
-__global__ void k_head_wgrad(const float *__restrict__ gy, const float *__restrict__ h2, int n, int H, float *dw3)
+cudaError_t colsum(const float *v, const float *w, int n, int H, int round_bf16, float *part, float *out, cudaStream_t s)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= H) return;
-    float s = 0.f;
-    for (int b = 0; b < n; b++) s = fmaf(gy[b], rbf(h2[(long long)b * H + j]), s);
-    dw3[j] = s;
+    const int nc = (n + CS - 1) / CS;
+    k_colsum_part<<<nc, H >= 128 ? 128 : 32, 0, s>>>(v, w, n, H, round_bf16, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_colsum_fin<<<(H + 127) / 128, 128, 0, s>>>(part, nc, H, out);
+    return cudaGetLastError();
+}
+
+// batch row k = row perm(b0 + k) of X (KPAD floats) and t, perm(i) = (a i + c) mod n
+__global__ void k_gather_batch(const float *__restrict__ X, const float *__restrict__ t, int n, long long a,
+                               long long c, int b0, int nb, float *Xb, float *tb)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)nb * KPAD) return;
+    const int k = (int)(e / KPAD), col = (int)(e - (long long)k * KPAD);
+    const long long src = (a * (long long)(b0 + k) + c) % n;
+    Xb[e] = X[src * KPAD + col];
+    if (col == 0) tb[k] = t[src];
 }
 
 // mean of d[b]^2 with d = y - t, one block, fixed order
@@ -341,6 +411,10 @@ struct bc_mlp_s {
     // activations for the current batch capacity
     int cap = 0;
     float *h1 = nullptr, *h2 = nullptr, *y = nullptr, *gy = nullptr, *dh2 = nullptr, *dh1 = nullptr;
+    float *part = nullptr;        // split-K and column-sum partials
+    long long part_floats = 0;
+    float *xb = nullptr, *tb = nullptr; // a gathered training batch (bc_mlp_train)
+    int xb_cap = 0;
     float *loss = nullptr;
 };
 
@@ -378,6 +452,12 @@ bc_status ensure_batch(bc_mlp_t net, int n)
     MCK(cudaMalloc(&net->dh1, sizeof(float) * cap * H));
     MCK(cudaMalloc(&net->y, sizeof(float) * cap));
     MCK(cudaMalloc(&net->gy, sizeof(float) * cap));
+    if (net->part) cudaFree(net->part);
+    // up to 32 split-K slices of the largest weight gradient (H x H or H x 132), and
+    // the column-sum partials (one row of H per CS batch rows)
+    net->part_floats = std::max(32LL * (long long)H * std::max<long long>((long long)H, KIN),
+                                (long long)((cap + CS - 1) / CS) * (long long)H);
+    MCK(cudaMalloc(&net->part, sizeof(float) * net->part_floats));
     net->cap = cap;
     return BC_OK;
 }
@@ -407,20 +487,20 @@ bc_status backward(bc_mlp_t net, const float *X, const float *t, int n, cudaStre
     const long long nh = (long long)n * H;
     k_head_back<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(net->y, t, net->h2, net->p + o.w3, n, H, net->gy, net->dh2);
     MCK(cudaGetLastError());
-    k_head_wgrad<<<(H + 127) / 128, 128, 0, s>>>(net->gy, net->h2, n, H, net->g + o.w3);
-    k_colsum<<<1, 32, 0, s>>>(net->gy, n, 1, 0, net->g + o.b3);
+    MCK(colsum(net->h2, net->gy, n, H, 1, net->part, net->g + o.w3, s)); // dw3[j] = sum_b gy[b] bf16(h2[b][j])
+    MCK(colsum(net->gy, nullptr, n, 1, 0, net->part, net->g + o.b3, s));
     // dW2 = dh2^T h1  (M = H out, N = H in, K = n)
     GemmArgs w2{net->dh2, 1, H, net->h1, H, 1, net->g + o.W2, H, 1, H, H, n, nullptr, 0};
-    MCK(gemm(w2, s));
-    k_colsum<<<(H + 127) / 128, 128, 0, s>>>(net->dh2, n, H, 1, net->g + o.b2);
+    MCK(gemm_splitk(w2, net->part, net->part_floats, s));
+    MCK(colsum(net->dh2, nullptr, n, H, 1, net->part, net->g + o.b2, s));
     // dh1 = (dh2 W2) masked by h1 > 0  (M = n, N = H in, K = H out)
     GemmArgs d1{net->dh2, H, 1, net->p + o.W2, H, 1, net->dh1, H, 1, n, H, H, nullptr, 0};
     MCK(gemm(d1, s));
     k_relu_back<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(net->dh1, net->h1, nh);
     // dW1 = dh1^T X  (M = H, N = 132, K = n)
     GemmArgs w1{net->dh1, 1, H, X, KPAD, 1, net->g + o.W1, KIN, 1, H, KIN, n, nullptr, 0};
-    MCK(gemm(w1, s));
-    k_colsum<<<(H + 127) / 128, 128, 0, s>>>(net->dh1, n, H, 1, net->g + o.b1);
+    MCK(gemm_splitk(w1, net->part, net->part_floats, s));
+    MCK(colsum(net->dh1, nullptr, n, H, 1, net->part, net->g + o.b1, s));
     MCK(cudaGetLastError());
     return BC_OK;
 }
@@ -478,11 +558,14 @@ cudaError_t bc::launch_axpby(float *y, const float *x, int n, float alpha, float
 
 void bc::mlp_orphan(bc_mlp_s *net)
 {
-    float *bufs[] = {net->p, net->m, net->v, net->g, net->h1, net->h2, net->y, net->gy, net->dh2, net->dh1, net->loss};
+    float *bufs[] = {net->p,  net->m,   net->v,    net->g,  net->h1, net->h2,  net->y,
+                     net->gy, net->dh2, net->dh1, net->loss, net->part, net->xb, net->tb};
     for (float *b : bufs)
         if (b) cudaFree(b);
     net->p = net->m = net->v = net->g = net->h1 = net->h2 = net->y = net->gy = net->dh2 = net->dh1 = net->loss = nullptr;
-    net->cap = 0;
+    net->part = net->xb = net->tb = nullptr;
+    net->cap = net->xb_cap = 0;
+    net->part_floats = 0;
     net->ctx = nullptr;
 }
 
@@ -594,6 +677,82 @@ bc_status bc_mlp_train_step(bc_mlp_t net, const float *X, const float *t, int n,
         return BC_OK;
     } catch (...) {
         return mfail(BC_ERR_INTERNAL, "bc_mlp_train_step: unexpected exception");
+    }
+}
+
+// Pseudo-random order of epoch `e`: perm(i) = (a i + c) mod n with a coprime
+// to n, both drawn from splitmix64 of (seed, e) -- a bijection of [0, n).
+static void epoch_order(unsigned long long seed, int e, int n, long long *a, long long *c)
+{
+    auto mix = [](unsigned long long z) {
+        z += 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto gcd = [](long long x, long long y) {
+        while (y) {
+            const long long t = x % y;
+            x = y;
+            y = t;
+        }
+        return x;
+    };
+    long long aa = (long long)(mix(seed * 0x100000001B3ull + 2ull * (unsigned)e) % (unsigned long long)n);
+    if (aa == 0) aa = 1;
+    while (gcd(aa, n) != 1) aa = aa + 1 < n ? aa + 1 : 1;
+    *a = aa;
+    *c = (long long)(mix(seed * 0x100000001B3ull + 2ull * (unsigned)e + 1ull) % (unsigned long long)n);
+}
+
+bc_status bc_mlp_train(bc_mlp_t net, const float *X, const float *t, int n, int batch, int epochs, float lr,
+                       unsigned long long seed, float *loss)
+{
+    try {
+        if (!net || !X || !t || n < 1 || batch < 1 || batch > n || epochs < 1 || !(lr > 0.f))
+            return mfail(BC_ERR_ARG, "bc_mlp_train: bad arguments");
+        if (!net->ctx) return mfail(BC_ERR_ARG, "bc_mlp_train: the network's context was destroyed");
+        if (bc_status st = ensure_batch(net, batch)) return st;
+        cudaStream_t s = ctx_stream(net->ctx);
+        if (batch > net->xb_cap) {
+            if (net->xb) cudaFree(net->xb);
+            if (net->tb) cudaFree(net->tb);
+            net->xb = net->tb = nullptr;
+            net->xb_cap = 0;
+            MCK(cudaMalloc(&net->xb, sizeof(float) * (size_t)batch * KPAD));
+            MCK(cudaMalloc(&net->tb, sizeof(float) * (size_t)batch));
+            net->xb_cap = batch;
+        }
+        const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+        const long long total = net->off.total;
+        const int steps = n / batch;
+        for (int e = 0; e < epochs; e++) {
+            long long a = 1, c = 0;
+            epoch_order(seed, e, n, &a, &c);
+            const float lr_e = (float)(lr * 0.5 * (1.0 + std::cos(M_PI * e / epochs)));
+            for (int st = 0; st < steps; st++) {
+                const long long tot = (long long)batch * KPAD;
+                k_gather_batch<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, t, n, a, c, st * batch, batch, net->xb,
+                                                                             net->tb);
+                MCK(cudaGetLastError());
+                if (bc_status r = forward(net, net->xb, batch, net->y, s)) return r;
+                if (bc_status r = backward(net, net->xb, net->tb, batch, s)) return r;
+                net->step++;
+                const float c1 = (float)(1.0 - std::pow(0.9, (double)net->step));
+                const float c2 = (float)(1.0 - std::pow(0.999, (double)net->step));
+                k_adam<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(net->p, net->m, net->v, net->g, total, lr_e, b1,
+                                                                      b2, eps, c1, c2);
+                MCK(cudaGetLastError());
+            }
+        }
+        if (loss) {
+            // the loss of the last batch at the parameters it was taken with
+            k_loss<<<1, 256, 0, s>>>(net->y, net->tb, batch, loss);
+            MCK(cudaGetLastError());
+        }
+        return BC_OK;
+    } catch (...) {
+        return mfail(BC_ERR_INTERNAL, "bc_mlp_train: unexpected exception");
     }
 }
 

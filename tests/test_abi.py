@@ -24,7 +24,7 @@ def test_header_declares_the_boundary():
               "bc_pairs", "bc_sync",
               "bc_last_error", "bc_version", "bc_profile_begin", "bc_profile_end", "bc_stage_name",
               "bc_shape_moments", "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
-              "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_state", "bc_learned_sweep", "bc_mlp_param_count", "bc_topk", "bc_sweep_plan", "bc_plan_run",
+              "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_train", "bc_mlp_state", "bc_learned_sweep", "bc_mlp_param_count", "bc_topk", "bc_sweep_plan", "bc_plan_run",
               "bc_plan_destroy", "bc_score", "bc_score_sweep", "bc_query_create", "bc_query_eval", "bc_query_destroy",
               "bc_lift_create", "bc_lift_correlate", "bc_lift_destroy", "bc_get_tuning", "bc_set_tuning", "bc_autotune",
               "bc_correlate_noalloc", "bc_selftest_wait", "bc_learned_sweep_avg"):
