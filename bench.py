@@ -123,7 +123,7 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.proc = None
-        time.sleep(0.3)
+        time.sleep(1.0)  # nvidia-smi's start-up (driver queries) stays out of the timed region
 
     def stop(self):
         if self.proc is None:

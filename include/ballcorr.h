@@ -427,12 +427,15 @@ bc_status bc_topk(bc_ctx_t ctx, const float *scores, int n, int k, int *idx);
  * earlier asynchronous calls (BC_ERR_INTERNAL, BC_ERR_TIMEOUT) or CUDA error. */
 bc_status bc_sync(bc_ctx_t ctx);
 
-/* Self-test of the bounded device-side waits of the tensor-core kernels:
- * launches one thread that waits on an mbarrier nothing arrives at.  The wait
- * gives up after about 2 s and records the expiry in the context's error word,
- * the kernel returns, and the call (which synchronises) returns BC_ERR_TIMEOUT
- * with the word cleared; the context stays usable.  Any other status means the
- * timeout path is broken.  Errors: BC_ERR_ARG (null context), BC_ERR_CUDA. */
+/* Self-test of the bounded device-side waits: launches one thread that waits
+ * on an mbarrier nothing arrives at (the wait of the tensor-core kernels), then
+ * one block that waits on a work-queue counter nothing raises (the dependency
+ * wait of the persistent launch).  Each wait gives up after about 2 s and
+ * records its expiry in the context's error word, the kernels return, and the
+ * call (which synchronises) returns BC_ERR_TIMEOUT when both expiries were
+ * recorded, with the word cleared; the context stays usable.  Any other status
+ * means a timeout path is broken (BC_ERR_INTERNAL when an expiry was not
+ * recorded).  Errors: BC_ERR_ARG (null context), BC_ERR_OOM, BC_ERR_CUDA. */
 bc_status bc_selftest_wait(bc_ctx_t ctx);
 
 /* ---------------------------------------------------------------- profiling

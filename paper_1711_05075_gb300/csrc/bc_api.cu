@@ -594,8 +594,18 @@ bc_status bc_selftest_wait(bc_ctx_t c)
 {
     if (!c) return fail(BC_ERR_ARG, "bc_selftest_wait: null context");
     CK(cudaStreamSynchronize(c->stream));
+    if (c->ws.sync.ensure(sizeof(unsigned), false, c->stream) != cudaSuccess)
+        return fail(BC_ERR_OOM, "bc_selftest_wait: counter");
     CK(launch_wait_selftest(c->err_dev, c->stream));
-    return bc_sync(c);
+    CK(launch_queue_wait_selftest((unsigned *)c->ws.sync.p, c->err_dev, c->stream));
+    CK(cudaMemcpyAsync(c->pin, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int herr = c->pin[0];
+    CK(cudaMemset(c->err_dev, 0, sizeof(int)));
+    if ((herr & 8) && (herr & 16))
+        return fail(BC_ERR_TIMEOUT, "both self-test waits expired and reported it (the tensor-core mbarrier wait and "
+                                    "the persistent launch's dependency wait)");
+    return fail(BC_ERR_INTERNAL, "a self-test wait did not report its expiry");
 }
 
 const char *bc_stage_name(int i) { return (i >= 0 && i < BC_NUM_STAGES) ? kStageNames[i] : ""; }
@@ -834,7 +844,7 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
         if ((e = launch_bin(g, t, dinst, job.koff, (const float4 *)ws.ku.p, dplan, (int *)ws.cur.p, (float *)ws.rec.p, st)) != cudaSuccess)
             return cuda_fail(e, "bin");
     } else {
-        if ((e = launch_spread(g, t, dinst, job.koff, (const float4 *)ws.ku.p, dplan, (float *)ws.grid.p, st)) != cudaSuccess)
+        if ((e = launch_spread(g, t, dinst, job.koff, (const float4 *)ws.ku.p, dplan, (float *)ws.grid.p, c->nsm, st)) != cudaSuccess)
             return cuda_fail(e, "spread");
     }
     launches += job.koff > 0;

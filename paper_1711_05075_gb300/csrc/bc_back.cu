@@ -221,7 +221,19 @@ cudaError_t back_t(const Geometry &g, const Tables &t, const InstDesc *inst, con
     return cudaGetLastError();
 }
 
+// One block waits on a count nothing raises: the wait gives up after its two
+// seconds and records the expiry (bit 4 of *err).
+__global__ void k_queue_wait_selftest(const unsigned *c, int *err) { wait_count(c, 1u, err); }
+
 } // namespace
+
+cudaError_t launch_queue_wait_selftest(unsigned *zeroed, int *err, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(zeroed, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    k_queue_wait_selftest<<<1, 32, 0, s>>>(zeroed, err);
+    return cudaGetLastError();
+}
 
 size_t back_sync_words(int N, int npairs) { return 1 + (size_t)npairs * (N / 32) + (size_t)npairs * N; }
 

@@ -104,7 +104,7 @@ cudaError_t launch_fft_z_binned(const Geometry &g, const Tables &t, const InstDe
                                 const InstPlan *plan, const int *cur, const float *rec, float2 *z1, int nsm,
                                 cudaStream_t s);
 cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *inst, int total_knots,
-                          const float4 *ku, const InstPlan *plan, float *grid, cudaStream_t s);
+                          const float4 *ku, const InstPlan *plan, float *grid, int nsm, cudaStream_t s);
 cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
                          const InstPlan *plan, float *grid, float2 *z1, int nsm, cudaStream_t s);
 // The z pass as split-TF32 DFT products on the tensor cores (bc_zumma.cu),
@@ -128,6 +128,9 @@ cudaError_t launch_fft_x(const Geometry &g, const Tables &t, const InstDesc *ins
 // back_sync_words(N, npairs) counters, cleared by the launcher.  An expired
 // dependency wait sets bit 4 of *err.
 size_t back_sync_words(int N, int npairs);
+// One block waits (bounded) on a counter nothing raises (`zeroed` is cleared
+// first): sets bit 4 of *err after about two seconds.
+cudaError_t launch_queue_wait_selftest(unsigned *zeroed, int *err, cudaStream_t s);
 cudaError_t launch_back(const Geometry &g, const Tables &t, const InstDesc *inst, const InstPlan *plan,
                         const PairDesc *pairs, int npairs, const float2 *y1, const float2 *fa_cache, float2 *h,
                         float *out, unsigned long long *keys, unsigned *sync, int *err, int nsm, cudaStream_t s);

@@ -477,9 +477,10 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
 }
 
 cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *inst, int total_knots,
-                          const float4 *ku, const InstPlan *plan, float *grid, cudaStream_t s)
+                          const float4 *ku, const InstPlan *plan, float *grid, int nsm, cudaStream_t s)
 {
     if (total_knots <= 0) return cudaSuccess;
+    (void)nsm; // one warp per knot: measured faster than resident-sized grid-stride loops
     int blocks = (total_knots + SPREAD_WARPS - 1) / SPREAD_WARPS;
     if (blocks > 65535) blocks = 65535;
     k_spread<<<blocks, SPREAD_WARPS * 32, 0, s>>>(g, t.consts, inst, ku, plan, grid, total_knots);

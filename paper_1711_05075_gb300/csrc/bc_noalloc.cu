@@ -220,7 +220,7 @@ extern "C" bc_status bc_correlate_noalloc(const bc_params *p, const float *xyzA,
         t.consts = consts;
         if ((e = launch_prepare(g, dinst, 2, nA > nB ? nA : nB, ku, boxes, dplan, err, nullptr, nullptr, st)) != cudaSuccess)
             return ncuda(e, "prepare");
-        if ((e = launch_spread(g, t, dinst, nA + nB, ku, dplan, grid, st)) != cudaSuccess) return ncuda(e, "spread");
+        if ((e = launch_spread(g, t, dinst, nA + nB, ku, dplan, grid, nsm, st)) != cudaSuccess) return ncuda(e, "spread");
         if ((e = launch_fft_z(g, t, dinst, 2, dplan, grid, z1, nsm, st)) != cudaSuccess) return ncuda(e, "fft z");
         if ((e = launch_fft_y(g, t, dinst, 2, dplan, z1, y1, nsm, st)) != cudaSuccess) return ncuda(e, "fft y");
         if ((e = launch_fft_x(g, t, dinst, dplan, dpairs, 1, y1, nullptr, nullptr, h, nsm, st)) != cudaSuccess)

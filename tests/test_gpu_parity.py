@@ -399,9 +399,11 @@ def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread, zt, pe):
 
 
 def test_bounded_wait_gives_up_and_the_context_stays_usable():
-    # failure detection without a fault: a device wait that nothing satisfies
-    # expires (about 2 s), is reported as BC_ERR_TIMEOUT (4), and the next
-    # correlation on the same context is correct
+    # failure detection without a fault: device waits that nothing satisfies (an
+    # mbarrier of the tensor-core kernels, a work-queue counter of the persistent
+    # launch) expire (about 2 s each), are reported as BC_ERR_TIMEOUT (4), and the
+    # next correlations on the same context -- with the tensor-core z pass and with
+    # the persistent back half -- are correct
     bc = bcmod()
     wl = synth.small_pair(6)
     ctx = bc.Context(wl.N, wl.W, wl.radii)
@@ -409,8 +411,11 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable():
     ctx.sync()  # the error word was cleared
     sa = ctx.shape(wl.A.xyz, wl.A.level)
     sb = ctx.shape(wl.B.xyz, wl.B.level)
-    got = ctx.correlate(sa, sb, wl.quats).double().cpu().numpy()[0]
-    check(got, oracle_grid(wl.A, wl.B, wl.quats[0], wl.N), what="after an expired wait")
+    ref = oracle_grid(wl.A, wl.B, wl.quats[0], wl.N)
+    for pe in (0, 1):
+        ctx.set_tuning(z_transform=1, persistent=pe)
+        got = ctx.correlate(sa, sb, wl.quats).double().cpu().numpy()[0]
+        check(got, ref, what=f"after the expired waits, persistent {pe}")
     sa.close(); sb.close(); ctx.close()
 
 
