@@ -177,7 +177,7 @@ struct bc_ctx_s {
     int prof_max = 0, prof_calls = 0;
     long long prof_launches = 0;
     std::vector<cudaEvent_t> prof_ev; // prof_max x (BC_NUM_STAGES + 1)
-    int last_ninst = 0, last_npairs = 0, last_mode = 0, last_back = 0;
+    int last_ninst = 0, last_npairs = 0, last_mode = 0, last_back = 0, last_yz = 0;
     cudaStream_t capture_stream = nullptr; // private stream for recording graphs (the legacy stream cannot be captured)
     bool replay = true;                    // repeated identical passes of direct calls replay a recorded graph
     std::vector<InstDesc> last_inst;
@@ -667,6 +667,8 @@ bc_status bc_profile_end(bc_ctx_t c, bc_profile *out)
         if (c->last_back) { // one persistent launch carried the three passes
             out->bytes[4] += out->bytes[5] + out->bytes[6];
             out->bytes[5] = out->bytes[6] = 0.0;
+        } else if (c->last_yz) { // planes read once, grids written once
+            out->bytes[5] = 0.0;
         }
     }
     prof_free(c);
@@ -697,6 +699,7 @@ struct Job {
     int sched = 0; // radix schedule of the forward passes
     int ztc = 0;   // z pass on the tensor cores (mode 0 only)
     int back = 0;  // x, inverse-y and inverse-z passes as one persistent launch
+    bool yz = false; // inverse y and z of whole planes in one launch (batches of many pairs)
     Weights w;
     int nmain = 0, koff = 0, max_knots = 0;
     long long goff = 0, zoff = 0, yoff = 0, hpairs = 0;
@@ -743,6 +746,9 @@ static Job plan_job(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std
     }
     for (const PairDesc &p : pairs)
         if (p.b >= 0) j.hpairs = std::max(j.hpairs, p.h_off / ((long long)N * N * H) + 1);
+    // plane-wise inverse passes once there are enough planes to fill the device
+    // (one block each, two per SM) several times over
+    j.yz = !j.back && g.N <= 128 && (long long)j.nmain * N >= 4LL * 2 * c->nsm;
     return j;
 }
 
@@ -894,16 +900,25 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
             launches++;
         }
         mark(4);
-        if (nmain > 0) {
-            if ((e = launch_ifft_y(g, t, pmain, nmain, (float2 *)ws.h.p, c->nsm, st)) != cudaSuccess)
-                return cuda_fail(e, "ifft y");
+        if (job.yz) {
+            // many pairs: both inverse passes plane by plane in shared memory (one
+            // launch, timed as the ifft_z stage)
+            mark(5);
+            if ((e = launch_ifft_yz(g, t, pmain, nmain, (const float2 *)ws.h.p, dout, keys, c->nsm, st)) != cudaSuccess)
+                return cuda_fail(e, "ifft yz");
             launches++;
-        }
-        mark(5);
-        if (nmain > 0) {
-            if ((e = launch_ifft_z(g, t, pmain, nmain, (const float2 *)ws.h.p, dout, keys, c->nsm, st)) != cudaSuccess)
-                return cuda_fail(e, "ifft z");
-            launches++;
+        } else {
+            if (nmain > 0) {
+                if ((e = launch_ifft_y(g, t, pmain, nmain, (float2 *)ws.h.p, c->nsm, st)) != cudaSuccess)
+                    return cuda_fail(e, "ifft y");
+                launches++;
+            }
+            mark(5);
+            if (nmain > 0) {
+                if ((e = launch_ifft_z(g, t, pmain, nmain, (const float2 *)ws.h.p, dout, keys, c->nsm, st)) != cudaSuccess)
+                    return cuda_fail(e, "ifft z");
+                launches++;
+            }
         }
         mark(6);
     }
@@ -915,6 +930,7 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
         c->last_npairs = nmain;
         c->last_mode = job.mode;
         c->last_back = job.back && nmain > 0;
+        c->last_yz = job.yz;
         c->last_inst = job.inst;
     }
     return BC_OK;

@@ -139,6 +139,11 @@ cudaError_t launch_ifft_y(const Geometry &g, const Tables &t, const PairDesc *pa
 // out (N^3 floats per pair) and keys (one 64-bit peak key per pair slot) may each be null.
 cudaError_t launch_ifft_z(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs,
                           const float2 *h, float *out, unsigned long long *keys, int nsm, cudaStream_t s);
+// The inverse y and z passes of whole planes in shared memory, one block per
+// plane (N <= 128): the same result as launch_ifft_y then launch_ifft_z, for
+// batches of many pairs.
+cudaError_t launch_ifft_yz(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, const float2 *h,
+                           float *out, unsigned long long *keys, int nsm, cudaStream_t s);
 // keys[i] -> peak[i], argmax[i] (i < n).
 cudaError_t launch_decode_peaks(const unsigned long long *keys, int n, float *peak, int *argmax, cudaStream_t s);
 

@@ -862,6 +862,107 @@ k_ifft_z(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
     }
 }
 
+// ------------------------------------------------------------------ inverse y and z of whole planes
+// One block per plane k_x of a pair (for batches of many pairs): the plane's
+// N x N/2 half-spectrum values (one contiguous run in h) are copied into
+// shared memory chunk-major ([chunk of 16 z-modes][k_y][16]), transformed along
+// y chunk by chunk in place, and then along z as k_ifft_z does, 32 output rows
+// at a time, from shared memory.  Same arithmetic as k_ifft_y followed by
+// k_ifft_z; the plane never goes back to HBM between the two transforms.
+template <int NI>
+__global__ void __launch_bounds__(TB, 2)
+k_ifft_yz(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, const float2 *__restrict__ h,
+          float *out, unsigned long long *keys)
+{
+    __shared__ unsigned long long red[TB / 32];
+    extern __shared__ float4 sm4[];
+    constexpr int H = NI / 2, N = NI, nch = H / CL, nyb = N / 32;
+    float2 *tw = reinterpret_cast<float2 *>(sm4);
+    float2 *P = tw + NI;           // [nch][N][CL]
+    float2 *A = P + N * H;         // [N + 1][CL] scratch tiles
+    float2 *B = A + NI * CL;
+    load_twiddles<NI>(tw, tb.tw_N);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane >> 1, odd = lane & 1;
+    const int units = npairs * N;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const int pi = u / N, kx = u - pi * N;
+        const PairDesc pr = pairs[pi];
+        if (pr.b < 0) continue; // uniform per pair
+        const float2 *src = h + pr.h_off + (long long)kx * N * H;
+        for (int e = threadIdx.x; e < N * H / 2; e += TB) { // 16-byte pieces: row ky, modes 2e' .. 2e' + 1
+            const int ky = e / (H / 2), m2 = (e - ky * (H / 2)) * 2;
+            cp_async16(P + ((m2 / CL) * N + ky) * CL + (m2 % CL), src + (long long)ky * H + m2, true);
+        }
+        cp_async_commit();
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        for (int ch = 0; ch < nch; ch++) {
+            float2 *T = P + ch * N * CL;
+            const float2 *res = il_fft<NI, true, CL, TB>(T, A, tw);
+            if (res != T) {
+                for (int e = threadIdx.x; e < N * CL; e += TB) T[e] = res[e];
+                __syncthreads();
+            }
+        }
+        for (int kb = 0; kb < nyb; kb++) {
+            const int ky0 = kb * 32;
+            if (threadIdx.x < CL) A[H * CL + threadIdx.x] = make_float2(0.f, 0.f); // m_z = N/2
+            for (int k = 2 * w; k < H; k += 2 * (TB / 32)) {
+                // modes k, k + 1 of row ky0 + lane (both in the chunk of k: k is even and CL is even)
+                const float2 *pr2 = P + ((k / CL) * N + ky0 + lane) * CL + (k % CL);
+                const float4 v = *reinterpret_cast<const float4 *>(pr2);
+                const float4 o = make_float4(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1),
+                                             __shfl_xor_sync(0xffffffffu, v.z, 1), __shfl_xor_sync(0xffffffffu, v.w, 1));
+                const float4 a = odd ? o : v, b = odd ? v : o; // rows 2q and 2q+1 at modes k, k+1
+#pragma unroll
+                for (int uu = 0; uu < 2; uu++) {
+                    const float ax = uu ? a.z : a.x, ay = uu ? a.w : a.y, bx = uu ? b.z : b.x, by = uu ? b.w : b.y;
+                    const int kk = k + uu;
+                    if (!odd) {
+                        A[kk * CL + q] = kk == 0 ? make_float2(ax, bx) : make_float2(ax - by, ay + bx);
+                    } else if (kk != 0) {
+                        A[(N - kk) * CL + q] = make_float2(ax + by, bx - ay);
+                    }
+                }
+            }
+            __syncthreads();
+            const float2 *res = il_fft<NI, true, CL, TB>(A, B, tw);
+            float *S = reinterpret_cast<float *>((res == A) ? B : A);
+            for (int e = threadIdx.x; e < 32 * N; e += TB) {
+                const int r = e & 31, kz = e >> 5;
+                const float2 v = res[kz * CL + (r >> 1)];
+                S[r * N + (kz ^ r)] = (r & 1) ? v.y : v.x;
+            }
+            __syncthreads();
+            float *o = out ? out + pr.out_off + ((long long)kx * N + ky0) * N : nullptr;
+            unsigned long long best = 0ull;
+            for (int e = threadIdx.x; e < 32 * N; e += TB) {
+                const int r = e / N, kz = e - r * N;
+                const float v = S[r * N + (kz ^ r)];
+                if (o) o[(long long)r * N + kz] = v;
+                if (keys) {
+                    const unsigned long long kk = peak_key(v, (unsigned)(((long long)kx * N + ky0 + r) * N + kz));
+                    best = kk > best ? kk : best;
+                }
+            }
+            if (keys) {
+                for (int off = 16; off > 0; off >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, off);
+                    best = other > best ? other : best;
+                }
+                if (lane == 0) red[w] = best;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    for (int i2 = 1; i2 < TB / 32; i2++) best = red[i2] > best ? red[i2] : best;
+                    atomicMax(keys + pr.key, best);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // ------------------------------------------------------------------ launchers
 template <int NF, bool SP = false, int S = 0>
 static cudaError_t fft_z_t(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
@@ -983,6 +1084,29 @@ cudaError_t launch_ifft_y(const Geometry &g, const Tables &t, const PairDesc *pa
     case 128: return ifft_y_t<128>(g, t, pairs, npairs, h, nsm, s);
     case 256: return ifft_y_t<256>(g, t, pairs, npairs, h, nsm, s);
     default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NI>
+static cudaError_t ifft_yz_t(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, const float2 *h,
+                             float *out, unsigned long long *keys, int nsm, cudaStream_t s)
+{
+    const size_t smem = sizeof(float2) * (NI + (size_t)NI * (NI / 2) + 2 * (size_t)NI * CL);
+    cudaError_t e = set_smem(k_ifft_yz<NI>, smem);
+    if (e != cudaSuccess) return e;
+    k_ifft_yz<NI><<<resident_blocks(k_ifft_yz<NI>, smem, nsm), TB, smem, s>>>(g, t, pairs, npairs, h, out, keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ifft_yz(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, const float2 *h,
+                           float *out, unsigned long long *keys, int nsm, cudaStream_t s)
+{
+    switch (g.N) {
+    case 32: return ifft_yz_t<32>(g, t, pairs, npairs, h, out, keys, nsm, s);
+    case 64: return ifft_yz_t<64>(g, t, pairs, npairs, h, out, keys, nsm, s);
+    case 96: return ifft_yz_t<96>(g, t, pairs, npairs, h, out, keys, nsm, s);
+    case 128: return ifft_yz_t<128>(g, t, pairs, npairs, h, out, keys, nsm, s);
+    default: return cudaErrorInvalidValue; // N = 256: a plane (256 KB) exceeds shared memory
     }
 }
 

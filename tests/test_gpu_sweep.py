@@ -169,6 +169,29 @@ def test_ragged_pairs_at_full_size(bc):
     ctx.close()
 
 
+@pytest.mark.parametrize("N,k", [(32, 48), (64, 24), (128, 12)])
+def test_many_pairs_take_the_planewise_inverse(bc, N, k):
+    # With many pairs in one pass (here k rotations of one correlate call) the
+    # inverse y and z transforms run plane by plane in shared memory
+    # (k_ifft_yz); three of the k grids against the oracle, all k against the
+    # same rotations computed one per call (the two inverse kernels).
+    A = synth.ellipsoid_shape(300, 31, synth.RADII_4, synth.PROBS_4)
+    B = synth.torus_shape(250, 32, synth.RADII_4, synth.PROBS_4)
+    q = synth.shoemake_quaternions(synth.SplitMix64(33), k).astype(np.float32)
+    ctx = bc.Context(N, 8, synth.RADII_4)
+    hA, hB = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
+    grids = ctx.correlate(hA, hB, q).double().cpu().numpy()
+    for r in (0, k // 2, k - 1):
+        ref = O.band_limited_corr(f32(A), f32(B), q[r].astype(np.float64), N)
+        rel = np.linalg.norm(grids[r] - ref) / np.linalg.norm(ref)
+        print(f"N={N} k={k} rot {r}: rel-L2 {rel:.3e}")
+        assert rel <= REL_TOL
+    for r in range(k):
+        one = ctx.correlate(hA, hB, q[r:r + 1])[0].double().cpu().numpy()
+        assert np.linalg.norm(grids[r] - one) <= 1e-6 * np.linalg.norm(one), r
+    hA.close(); hB.close(); ctx.close()
+
+
 def test_captured_sweep_plan_replays(bc):
     # The same sweep as one CUDA graph: identical peaks to bc_sweep, replayable.
     wl = synth.small_pair(9)
