@@ -422,12 +422,14 @@ def run_ours(args, rank, world, local_rank):
 
 # ------------------------------------------------------------------ profiler runs
 def run_profile(args):
-    """N plain correlations of the bench workload and nothing else (a profiler target)."""
+    """N plain correlations of the bench workload and nothing else (a profiler target);
+    --profile-n / --profile-precision select the same shapes at another N or precision."""
     import torch
     import paper_1711_05075_gb300 as bc
+    from paper_1711_05075_gb300 import synth
     torch.cuda.set_device(0)
-    wl = workload()
-    ctx = bc.Context(wl.N, wl.W, wl.radii, wl.period)
+    wl = workload() if args.profile_n == 128 else synth.scale_pair(0, N=args.profile_n, W=8)
+    ctx = bc.Context(wl.N, wl.W, wl.radii, wl.period, precision=args.profile_precision)
     ctx.set_tuning(spread=args.spread if args.spread is not None else 0)
     A = ctx.shape(wl.A.xyz, wl.A.level)
     B = ctx.shape(wl.B.xyz, wl.B.level)
@@ -559,6 +561,61 @@ def run_lifted(args):
             "note": "direct 4D NDFT; the contraction's rate is counted against the whole call's time"}
     print(json.dumps(line), flush=True)
     lf.close()
+    return 0
+
+
+# ------------------------------------------------------------------ split precision
+def run_split(args):
+    """The split-precision form (BF16 hi + lo DFT stages on the tensor cores) beside the
+    all-FP32 path on the 20k+20k-ball pair at N = 256 (512^3 oversampled), W = 8: device
+    time per correlation (L2 flushed between steps) and, for each path, rel-L2 and max-abs
+    against the FP64 oracle (layer b) at 4,096 sampled translations."""
+    import torch
+    import oracle as O
+    import paper_1711_05075_gb300 as bc
+    from paper_1711_05075_gb300 import synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    wl = synth.scale_pair(0, N=256, W=8)
+    q = wl.quats.astype(np.float32)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    idx = synth.translation_sample(wl.N, 4096, seed=0)
+    O.build()
+    t0 = time.perf_counter()
+    ghat = O.band_limited_spectrum(f32_shape(wl.A), f32_shape(wl.B), q[0].astype(np.float64), wl.N)
+    ref = O.inverse_at(ghat, O.grid_points(wl.N, idx=idx))
+    s_oracle = time.perf_counter() - t0
+    res = {}
+    for prec, name in ((0, "fp32"), (1, "split_bf16")):
+        ctx = bc.Context(wl.N, wl.W, wl.radii, wl.period, stream=stream, precision=prec)
+        A, B = ctx.shape(wl.A.xyz, wl.A.level), ctx.shape(wl.B.xyz, wl.B.level)
+        out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            ctx.correlate(A, B, q, out)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            ctx.correlate(A, B, q, out)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        got = out.reshape(-1)[torch.as_tensor(idx, device="cuda")].double().cpu().numpy()
+        res[name] = {"ms_per_correlation": ms, "poses_s": wl.N ** 3 / (ms * 1e-3),
+                     "rel_l2_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                     "max_abs_vs_oracle": float(np.abs(got - ref).max()), "ref_max_abs": float(np.abs(ref).max()),
+                     "tuning": ctx.tuning}
+        A.close()
+        B.close()
+        ctx.close()
+    line = {"metric": "split-precision correlation (BF16 hi+lo DFT stages) beside FP32", "workload": "split precision",
+            "unit": "poses/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 x3 / f32",
+            "data": "synthetic", "config": dict(config_of(wl), error_points=4096), "results": res,
+            "split_vs_fp32_time": res["split_bf16"]["ms_per_correlation"] / res["fp32"]["ms_per_correlation"],
+            "s_oracle_reference": s_oracle,
+            "bars": {"fp32_rel_l2": 1e-5, "split_rel_l2": 2e-3}}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -798,11 +855,15 @@ def main():
                     help="skip the learned-proposal study in the default line (about a minute)")
     ap.add_argument("--profile-correlations", type=int, default=0,
                     help="only run this many correlations of the workload (for a profiler), print nothing else")
-    ap.add_argument("--workload", choices=["scale", "learned", "score", "query", "lifted"], default="scale",
+    ap.add_argument("--profile-n", type=int, default=128, choices=[32, 64, 96, 128, 256],
+                    help="grid size of the --profile-correlations workload (the 20k+20k-ball pair)")
+    ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1],
+                    help="precision of the --profile-correlations context (1: split BF16 stages)")
+    ap.add_argument("--workload", choices=["scale", "learned", "score", "query", "lifted", "split"], default="scale",
                     help="scale: the 20k+20k-ball N=128 correlation (default); learned: the rotation-proposal "
                          "study; score: the complementarity score of the same pair; query: truncated "
                          "single-configuration queries of the same pair; lifted: the 4D nonequiradius "
-                         "correlation")
+                         "correlation; split: the split-precision path beside FP32 at N = 256")
     ap.add_argument("--lift-n", type=int, default=32)
     ap.add_argument("--lift-nr", type=int, default=16)
     ap.add_argument("--lift-knots", type=int, default=5000)
@@ -845,6 +906,8 @@ def main():
         return run_query(args)
     if args.workload == "lifted":
         return run_lifted(args)
+    if args.workload == "split":
+        return run_split(args)
     if args.profile_correlations > 0:
         return run_profile(args)
     if world > 1:
