@@ -250,13 +250,16 @@ static Tables tables_of(bc_ctx_t c)
 }
 
 // Per-axis capacity of an instance's support box: the stencil cells of knots
-// with |u| <= U = rmax n / P span at most 2U + W + 1 cells; beyond n/2 the
-// coordinates may wrap and the box is the whole period.
+// with |u| <= U = rmax n / P span at most floor(2U) + W + 1 cells (the lowest
+// cell is at least -U - W/2, the highest below U + W/2); one more cell covers
+// the FP32 rounding of u (rmax is already rounded up).  Beyond n/2 the
+// coordinates may wrap and the box is the whole period.  A box beyond its
+// capacity raises the status word (bc_sync: BC_ERR_INTERNAL).
 static int cap_extent(const bc_ctx_t c, float rmax)
 {
     const double U = (double)rmax * c->g.n / c->period;
     if (U >= 0.5 * c->g.n - 1.0) return c->g.n;
-    int e = (int)std::ceil(2.0 * U) + c->g.W + 3;
+    int e = (int)std::ceil(2.0 * U) + c->g.W + 2;
     return e > c->g.n ? c->g.n : e;
 }
 
@@ -701,7 +704,7 @@ struct Job {
     int back = 0;  // x, inverse-y and inverse-z passes as one persistent launch
     bool yz = false; // inverse y and z of whole planes in one launch (batches of many pairs)
     Weights w;
-    int nmain = 0, koff = 0, max_knots = 0;
+    int nmain = 0, koff = 0, max_knots = 0, max_cap = 0;
     long long goff = 0, zoff = 0, yoff = 0, hpairs = 0;
 };
 
@@ -729,6 +732,7 @@ static Job plan_job(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std
         d.knots = s->knots;
         const int e = cap_extent(c, s->rmax);
         d.cap_e = e;
+        j.max_cap = std::max(j.max_cap, e);
         d.grid_off = j.goff;
         d.z1_off = j.zoff;
         d.y1_off = j.yoff;
@@ -872,7 +876,8 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
     }
     launches++;
     mark(2);
-    if ((e = launch_fft_y(g, t, dinst, ninst, dplan, (const float2 *)ws.z1.p, (float2 *)ws.y1.p, c->nsm, st)) != cudaSuccess)
+    if ((e = launch_fft_y(g, t, dinst, ninst, dplan, (const float2 *)ws.z1.p, (float2 *)ws.y1.p, job.max_cap, c->nsm,
+                          st)) != cudaSuccess)
         return cuda_fail(e, "fft y");
     launches++;
     mark(3);
@@ -974,7 +979,8 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
     auto add = [&](const void *v, size_t n) { key.insert(key.end(), (const char *)v, (const char *)v + n); };
     const long long sig[] = {(long long)job.inst.size(), (long long)job.pairs.size(), (long long)job.nmain,
                              (long long)job.cache_first, (long long)job.koff, (long long)job.max_knots,
-                             (long long)job.mode, (long long)job.sched, (long long)job.ztc, (long long)job.back};
+                             (long long)job.mode, (long long)job.sched, (long long)job.ztc, (long long)job.back,
+                             (long long)job.max_cap};
     add(sig, sizeof(sig));
     const void *ptrs[] = {dout, keys, job.w.ballft, ws.ku.p, ws.plan.p, ws.inst.p, ws.pairs.p, ws.grid.p, ws.z1.p, ws.y1.p,
                           ws.h.p, ws.fa.p, ws.boxes.p, ws.cnt.p, ws.cur.p, ws.rec.p, ws.sync.p, c->stream};

@@ -118,8 +118,10 @@ cudaError_t launch_build_zdft(int n, float *bhi, float *blo, cudaStream_t s);
 cudaError_t launch_fft_z_umma(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
                               const InstPlan *plan, float *grid, float2 *z1, const float *bhi, const float *blo,
                               int *err, int nsm, cudaStream_t s);
+// max_cap: the largest per-axis box capacity (InstDesc::cap_e) of the instances;
+// when it is small enough the pass stages each item's rows from position 0.
 cudaError_t launch_fft_y(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst,
-                         const InstPlan *plan, const float2 *z1, float2 *y1, int nsm, cudaStream_t s);
+                         const InstPlan *plan, const float2 *z1, float2 *y1, int max_cap, int nsm, cudaStream_t s);
 cudaError_t launch_fft_x(const Geometry &g, const Tables &t, const InstDesc *inst, const InstPlan *plan,
                          const PairDesc *pairs, int npairs, const float2 *y1, const float2 *fa_cache,
                          float2 *fa_out, float2 *h, int nsm, cudaStream_t s);

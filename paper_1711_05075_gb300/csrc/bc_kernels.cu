@@ -688,6 +688,100 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     }
 }
 
+// The y pass with each item's rows staged at positions 0 .. b1 - 1 (compact
+// index iy at position iy, zero beyond), for launches whose instances all have
+// y boxes of at most YShift::MAXR cells (known on the host from their
+// capacities): the first stage reads only the RN inputs per butterfly that can
+// be nonzero, the staging tiles are MAXR rows instead of n, and three blocks
+// fit on an SM.  The box origin comes back as exp(-2 pi i m_y pos0_y / n) on
+// every kept output.  Same transform as k_fft_y, other rounding order.
+template <int NF, int S>
+struct YShift {
+    static constexpr int R0 = Radix<NF, S>::r0, NB = NF / R0;
+    static constexpr int MAXR = NF <= 128 ? NF : ((9 * NF / 16 + NB - 1) / NB) * NB;
+    static constexpr bool on = Radix<NF, S>::r2 == 1 && NF <= 256;
+    static constexpr size_t smem = sizeof(float2) * ((size_t)NF + (size_t)NF * CL + 2 * (size_t)MAXR * CL);
+};
+
+// First stage from a staging tile of YShift<NF, S>::MAXR rows.
+template <int NF, int S>
+__device__ __forceinline__ void ys_first(const float2 *__restrict__ stg, float2 *__restrict__ out)
+{
+    using YS = YShift<NF, S>;
+    constexpr int R = YS::R0, NB = YS::NB, RN = YS::MAXR / NB, TOT = NB * CL, IT = (TOT + TB - 1) / TB;
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int idx = (int)threadIdx.x + it * TB;
+        if ((TOT % TB) != 0 && idx >= TOT) break;
+        const int c = idx % CL, j = idx / CL;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = r < RN ? stg[(j + r * NB) * CL + c] : make_float2(0.f, 0.f);
+        dft_small<R, false>(v);
+#pragma unroll
+        for (int r = 0; r < R; r++) out[(j * R + r) * CL + c] = v[r];
+    }
+}
+
+template <int NF, int S>
+__global__ void __launch_bounds__(TB, 3)
+k_fft_y_shift(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, const InstPlan *__restrict__ plan,
+              const float2 *__restrict__ z1, float2 *y1)
+{
+    using YS = YShift<NF, S>;
+    extern __shared__ float4 sm4[];
+    float2 *tw = reinterpret_cast<float2 *>(sm4);
+    float2 *S0 = tw + NF;
+    float2 *T0 = S0 + NF * CL, *T1 = T0 + YS::MAXR * CL; // staging tiles
+    load_twiddles<NF>(tw, tb.tw_n);
+    constexpr int H = NF / 4, N = NF / 2;
+    constexpr int nch = H / CL;
+    const int L = g.L;
+    RotStart rs;
+    for (int i = 0; i < ninst; i++) {
+        const InstPlan p = plan[i];
+        if (p.b[0] == 0) continue;
+        const int b0 = p.b[0], b1 = p.b[1], py = p.pos0[1];
+        const int items = L * b0 * nch;
+        const InstDesc d = inst[i];
+        auto fetch = [&](int it, float2 *dst) {
+            const int lx = it / nch, ch = it - lx * nch;
+            const float2 *base = z1 + d.z1_off + (long long)lx * b1 * H + ch * CL;
+            for (int q = threadIdx.x; q < YS::MAXR * (CL / 2); q += TB) {
+                const int row = q / (CL / 2), cc = (q % (CL / 2)) * 2;
+                const bool ok = row < b1;
+                cp_async16(dst + row * CL + cc, ok ? base + (long long)row * H + cc : base, ok);
+            }
+        };
+        int it = rs.first();
+        if (it < items) fetch(it, T0);
+        cp_async_commit();
+        for (int k = 0; it < items; it += gridDim.x, k ^= 1) {
+            // the other tile was last read by the previous item's first stage
+            if (it + (int)gridDim.x < items) fetch(it + gridDim.x, k ? T0 : T1);
+            cp_async_commit();
+            cp_async_wait_prev();
+            __syncthreads();
+            ys_first<NF, S>(k ? T1 : T0, S0);
+            __syncthreads();
+            const int lx = it / nch, ch = it - lx * nch;
+            float2 *Y = y1 + d.y1_off + (long long)lx * N * H + ch * CL;
+            auto sink = [&](int, int, int c, int pos, float2 v) {
+                int jy, my;
+                if (pos < N / 2) jy = my = pos;
+                else if (pos >= NF - N / 2) {
+                    jy = pos - NF + N;
+                    my = pos - NF;
+                } else return;
+                Y[(long long)jy * H + c] = jy == N / 2 ? make_float2(0.f, 0.f) : cmul(v, box_phase<NF>(tw, my, py));
+            };
+            rr_rest<NF, false, CL, TB, S>(S0, nullptr, tw, sink);
+            __syncthreads();
+        }
+        rs.rot += items;
+    }
+}
+
 // ------------------------------------------------------------------ fft x + combine
 // Every (j_y, chunk of 16 z-modes) item of every pair through x_item
 // (bc_passes.cuh): forward x transform of both spectra with the level sum,
@@ -996,9 +1090,19 @@ cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *ins
 
 template <int NF, bool SP = false, int S = 0>
 static cudaError_t fft_y_t(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
-                           const float2 *z1, float2 *y1, int nsm, cudaStream_t s)
+                           const float2 *z1, float2 *y1, int max_cap, int nsm, cudaStream_t s)
 {
-    if (!SP && S == 0 && (g.sched & 2)) return fft_y_t<NF, false, 1>(g, t, inst, ninst, plan, z1, y1, nsm, s);
+    if (!SP && S == 0 && (g.sched & 2)) return fft_y_t<NF, false, 1>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+    if constexpr (!SP && YShift<NF, S>::on) {
+        if (max_cap <= YShift<NF, S>::MAXR) {
+            const size_t smem = YShift<NF, S>::smem;
+            cudaError_t e = set_smem(k_fft_y_shift<NF, S>, smem);
+            if (e != cudaSuccess) return e;
+            k_fft_y_shift<NF, S><<<resident_blocks(k_fft_y_shift<NF, S>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst,
+                                                                                                    plan, z1, y1);
+            return cudaGetLastError();
+        }
+    }
     const size_t smem = sizeof(float2) * (NF + (YStaged<NF, SP, S>::on ? 3 : 2) * NF * CL);
     cudaError_t e = set_smem(k_fft_y<NF, SP, S>, smem);
     if (e != cudaSuccess) return e;
@@ -1007,19 +1111,19 @@ static cudaError_t fft_y_t(const Geometry &g, const Tables &t, const InstDesc *i
 }
 
 cudaError_t launch_fft_y(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
-                         const float2 *z1, float2 *y1, int nsm, cudaStream_t s)
+                         const float2 *z1, float2 *y1, int max_cap, int nsm, cudaStream_t s)
 {
     if (g.prec == 1) {
-        if (g.n == 64) return fft_y_t<64, true>(g, t, inst, ninst, plan, z1, y1, nsm, s);
-        if (g.n == 512) return fft_y_t<512, true>(g, t, inst, ninst, plan, z1, y1, nsm, s);
+        if (g.n == 64) return fft_y_t<64, true>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+        if (g.n == 512) return fft_y_t<512, true>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
         return cudaErrorInvalidValue;
     }
     switch (g.n) {
-    case 64: return fft_y_t<64>(g, t, inst, ninst, plan, z1, y1, nsm, s);
-    case 128: return fft_y_t<128>(g, t, inst, ninst, plan, z1, y1, nsm, s);
-    case 192: return fft_y_t<192>(g, t, inst, ninst, plan, z1, y1, nsm, s);
-    case 256: return fft_y_t<256>(g, t, inst, ninst, plan, z1, y1, nsm, s);
-    case 512: return fft_y_t<512>(g, t, inst, ninst, plan, z1, y1, nsm, s);
+    case 64: return fft_y_t<64>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+    case 128: return fft_y_t<128>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+    case 192: return fft_y_t<192>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+    case 256: return fft_y_t<256>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+    case 512: return fft_y_t<512>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -222,7 +222,7 @@ extern "C" bc_status bc_correlate_noalloc(const bc_params *p, const float *xyzA,
             return ncuda(e, "prepare");
         if ((e = launch_spread(g, t, dinst, nA + nB, ku, dplan, grid, nsm, st)) != cudaSuccess) return ncuda(e, "spread");
         if ((e = launch_fft_z(g, t, dinst, 2, dplan, grid, z1, nsm, st)) != cudaSuccess) return ncuda(e, "fft z");
-        if ((e = launch_fft_y(g, t, dinst, 2, dplan, z1, y1, nsm, st)) != cudaSuccess) return ncuda(e, "fft y");
+        if ((e = launch_fft_y(g, t, dinst, 2, dplan, z1, y1, kn, nsm, st)) != cudaSuccess) return ncuda(e, "fft y");
         if ((e = launch_fft_x(g, t, dinst, dplan, dpairs, 1, y1, nullptr, nullptr, h, nsm, st)) != cudaSuccess)
             return ncuda(e, "fft x");
         if ((e = launch_ifft_y(g, t, dpairs, 1, h, nsm, st)) != cudaSuccess) return ncuda(e, "ifft y");
