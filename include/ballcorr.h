@@ -245,12 +245,12 @@ bc_status bc_query_destroy(bc_query_t q);
  * memory.  Synchronous.  The tensor-core contractions take the knots in
  * passes of 32,768 (their operands cost 16 N^2 + 16 N Nr bytes per knot), so
  * the workspace stays bounded for any knot count.  Errors: BC_ERR_ARG (null pointer, counts out of
- * range, zero quaternion, non-finite section), BC_ERR_UNSUPPORTED (N not 32 or
- * 64, Nr not 8, 16, 32 or 64), BC_ERR_OOM, BC_ERR_CUDA, BC_ERR_TIMEOUT (a
+ * range, zero quaternion, non-finite section), BC_ERR_UNSUPPORTED (N not 32,
+ * 64, 96 or 128, Nr not 8, 16, 32 or 64), BC_ERR_OOM, BC_ERR_CUDA, BC_ERR_TIMEOUT (a
  * bounded wait inside the tcgen05 contraction expired; out is incomplete). */
 typedef struct bc_lift_s *bc_lift_t;
 typedef struct {
-    int N;           /* modes per axis and translation grid N^3: 32 or 64 */
+    int N;           /* modes per axis and translation grid N^3: 32, 64, 96 or 128 */
     int Nr;          /* modes along the lifted axis: 8, 16, 32 or 64 */
     double L;        /* cone height */
     double period;   /* P, translation period */

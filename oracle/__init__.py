@@ -334,9 +334,10 @@ def cone_ft(k, alpha, L, nodes=64):
     xg, wg = np.polynomial.legendre.leggauss(nodes)
     s = 0.5 * L * (xg + 1.0)
     w = 0.5 * L * wg
-    kk = k[..., None] * np.ones_like(s)
-    h = ball_ft(np.broadcast_to(s, kk.shape), kk)
-    return np.sum(w * h * np.exp(1j * alpha[..., None] * s), axis=-1)
+    out = np.zeros(k.shape, dtype=np.complex128)
+    for sj, wj in zip(s, w):  # one node at a time (bounded memory at large N)
+        out += wj * ball_ft(np.full(k.shape, sj), k) * np.exp(1j * alpha * sj)
+    return out
 
 
 def lifted_corr_spectrum(A, B, q, N, Nr, L, period=2.0, period_r=0.4):

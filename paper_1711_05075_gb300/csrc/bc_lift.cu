@@ -520,7 +520,8 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
 {
     if (!p || !out) return lift_fail(BC_ERR_ARG, "bc_lift_create: null pointer");
     *out = nullptr;
-    if (p->N != 32 && p->N != 64) return lift_fail(BC_ERR_UNSUPPORTED, "bc_lift_create: N must be 32 or 64");
+    if (p->N != 32 && p->N != 64 && p->N != 96 && p->N != 128)
+        return lift_fail(BC_ERR_UNSUPPORTED, "bc_lift_create: N must be 32, 64, 96 or 128");
     if (p->Nr != 8 && p->Nr != 16 && p->Nr != 32 && p->Nr != 64)
         return lift_fail(BC_ERR_UNSUPPORTED, "bc_lift_create: Nr must be 8, 16, 32 or 64");
     if (!(p->L > 0) || !std::isfinite(p->L)) return lift_fail(BC_ERR_ARG, "bc_lift_create: L must be > 0");
@@ -559,7 +560,7 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
     const int total = (lf->qmax + 1) * lf->Nr;
     k_lift_cone<<<(total + 255) / 256, 256, 0, lf->stream>>>(lf->qmax, lf->Nr, lf->L, lf->period, lf->period_r, g,
                                                              g + LIFT_GAUSS, lf->cone);
-    k_lift_twiddles<<<1, 64, 0, lf->stream>>>(lf->N, lf->tw);
+    k_lift_twiddles<<<(lf->N + 63) / 64, 64, 0, lf->stream>>>(lf->N, lf->tw);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "bc_lift_create: tables");
     if ((e = cudaStreamSynchronize(lf->stream)) != cudaSuccess) return bail(e, "bc_lift_create: sync");
     cudaFree(g);
@@ -733,8 +734,12 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
     const float scale = (float)(1.0 / (lf->period * lf->period * lf->period * lf->period_r));
     k_lift_collapse<<<(int)((plane + 255) / 256), 256, 0, st>>>(rhoA, rhoB, lf->cone, N, Nr, dsl, nslices, lf->period_r,
                                                                  scale, h);
-    if (N == 32) k_lift_ifft_x<32><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw);
-    else k_lift_ifft_x<64><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw);
+    switch (N) {
+    case 32: k_lift_ifft_x<32><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw); break;
+    case 64: k_lift_ifft_x<64><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw); break;
+    case 96: k_lift_ifft_x<96><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw); break;
+    default: k_lift_ifft_x<128><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw); break;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: collapse");
     Geometry g{};
     g.N = N;

@@ -49,7 +49,9 @@ def rel(a, b):
                                                  (32, 16, 2000, 1500, (0.0, 0.04)),
                                                  (32, 8, 12000, 7000, (0.0, 0.05)),
                                                  (32, 8, 40000, 3000, (0.0,)),  # two passes of 32,768 knots
-                                                 (64, 16, 800, 600, (0.0,))])
+                                                 (64, 16, 800, 600, (0.0,)),
+                                                 (96, 8, 300, 200, (0.0, 0.03)),
+                                                 (128, 8, 200, 150, (0.0,))])
 def test_lifted_sections_match_oracle(bc, N, Nr, nA, nB, slices, contraction):
     A = knots(synth.ellipsoid_shape(nA, 40 + nA), 1)
     B = knots(synth.torus_shape(nB, 41 + nB), 2)
