@@ -588,6 +588,8 @@ bc_status bc_sync(bc_ctx_t c)
             return fail(BC_ERR_TIMEOUT, "the tensor-core z transform stalled (a bounded wait expired); results are incomplete");
         if (herr & 16)
             return fail(BC_ERR_TIMEOUT, "a dependency wait of the persistent launch expired; results are incomplete");
+        if (herr & 32)
+            return fail(BC_ERR_TIMEOUT, "a tensor-core product of the MLP stalled (a bounded wait expired); results are incomplete");
         return fail(BC_ERR_INTERNAL, "device-side check failed (support box exceeded its capacity)");
     }
     return BC_OK;

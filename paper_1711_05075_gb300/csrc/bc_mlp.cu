@@ -10,8 +10,8 @@
 //
 // Precision: FP32 master weights and Adam moments; every product reads its
 // operands rounded to BF16 (weights, inputs, hidden activations, hidden
-// gradients) and accumulates in FP32 on the tensor cores (mma.sync m16n8k16
-// BF16 -> FP32).  All reductions run in a fixed order, so training is
+// gradients) and accumulates in FP32 on the tensor cores (tcgen05.mma
+// kind::f16, BF16 x BF16 -> FP32 in tensor memory).  All reductions run in a fixed order, so training is
 // deterministic for a fixed launch configuration.
 #include <algorithm>
 #include <cmath>
@@ -24,6 +24,7 @@
 
 #include "../../include/ballcorr.h"
 #include "bc_internal.h"
+#include "bc_umma.cuh"
 
 using namespace bc;
 
@@ -51,9 +52,21 @@ Offsets offsets(int H)
 
 // ------------------------------------------------------------------ BF16 GEMM
 // C[m][n] = sum_k A[m][k] B[k][n] (+ bias[n]) (relu), operands FP32 in global
-// memory addressed through strides and rounded to BF16 when staged in shared
-// memory; FP32 accumulation.  Block: 4 warps, tile 64 x 64, K step 32; each
-// warp owns 32 x 32 as 2 x 4 mma tiles of 16 x 8.
+// memory addressed through strides, rounded to BF16 when staged in shared
+// memory, products on the 5th-generation tensor cores
+// (tcgen05.mma.cta_group::1.kind::f16: A and B BF16, D FP32 in tensor memory;
+// M = 128, N = the tile width, K = 16 per instruction).
+//
+// One block of 256 threads computes a 128 x nt tile of C (nt = 64, 128 or 256
+// columns, chosen per call so that the grid covers the SMs).  Per K step of 64
+// the threads round the A (128 x 64) and B (nt x 64) tiles to BF16 and store
+// them K-major in the 128-byte-swizzled layout (row r's 16-byte chunk j at
+// chunk j xor (r mod 8), 8-row groups 1024 bytes apart); one thread issues the
+// step's four MMAs and commits them to the buffer's barrier while the block
+// converts the next step into the other buffer.  After the last step the warps
+// drain the accumulator (warp w reads lanes 32 (w mod 4) .. + 31, every other
+// 16-column chunk), add the bias, apply the ReLU and store.  Every wait is
+// bounded (bit 32 of the context's error word on expiry).
 struct GemmArgs {
     const float *A;
     long long sAm, sAk;
@@ -66,130 +79,338 @@ struct GemmArgs {
     int relu;
     int kchunk = 0;     // split K: slice z of the grid sums k in [z kchunk, (z + 1) kchunk) (0: all of K)
     long long sCz = 0;  // and writes its partial product at C + z sCz
+    int *err = nullptr; // status word for an expired tensor-core wait (required)
+    int nt = 256;       // tile width (64, 128 or 256; set by the launchers)
+    int bone = -1;      // >= 0: B's row bone is 1 for every k (C's column bone = the row sums of A); B has rows [0, bone)
+    const float *mask = nullptr; // C = bf16(x) where mask > 0, else 0 (mask addressed like C; no bias, ReLU or split K)
 };
 
-constexpr int GT = 64, GK = 32, GKP = GK + 8; // smem row pitch in bf16 (80 bytes)
+constexpr int GU_THREADS = 256, GU_K = 64;
+constexpr int GU_A_BYTES = 128 * 128; // 128 rows of 64 BF16
+constexpr int GU_ERR = 32;
 
-__device__ __forceinline__ unsigned pack2(const __nv_bfloat16 *p)
+int gu_smem(int nt) { return 1024 + 2 * (GU_A_BYTES + nt * 128) + 64; }
+
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int n)
 {
-    return *reinterpret_cast<const unsigned *>(p);
+    // D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major,
+    // N >> 3 at bit 17, M >> 4 at bit 24 (M = 128)
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-__global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g)
+__device__ __forceinline__ void umma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[GT][GKP]; // [m][k]
-    __shared__ __align__(16) __nv_bfloat16 Bs[GT][GKP]; // [n][k]
-    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = warp >> 1, wn = warp & 1;
-    const int gid = lane >> 2, tig = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int r = 0; r < 4; r++) acc[i][j][r] = 0.f;
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                 "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
 
+__device__ __forceinline__ uint32_t bf2(float a, float b)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// the 16-byte chunk j (values 8 j .. 8 j + 7 along k) of row r of a swizzled tile
+__device__ __forceinline__ void st_chunk(uint8_t *dst, int r, int j, float a0, float a1, float a2, float a3, float a4,
+                                         float a5, float a6, float a7)
+{
+    *reinterpret_cast<uint4 *>(dst + r * 128 + ((j ^ (r & 7)) << 4)) =
+        make_uint4(bf2(a0, a1), bf2(a2, a3), bf2(a4, a5), bf2(a6, a7));
+}
+
+// rows x 64 values of a strided FP32 matrix, rounded to BF16 into the swizzled
+// tile at `dst`: element (r, k) = src[(r0 + r) sR + (k0 + k) sK], zero unless
+// r0 + r < rlim and k0 + k < klim, except row r0 + r = rone (if any), which is
+// 1 for every k0 + k < klim.  The global loads stay coalesced, with
+// several in flight per thread:
+//  - rows contiguous (sR = 1, 16-byte aligned groups of 4 rows): a thread takes
+//    4 rows x 8 k as eight float4 loads, neighbouring threads neighbouring rows;
+//  - otherwise pieces of 8 consecutive k of one row (two float4 loads when k is
+//    contiguous and aligned, else 8 scalar loads), neighbouring threads
+//    neighbouring pieces of a row.
+__device__ __forceinline__ void gu_tile(uint8_t *dst, const float *__restrict__ src, long long sR, long long sK, int r0,
+                                        int rows, int rlim, int k0, int klim, int rone)
+{
+    const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+    if (sR == 1 && aligned && (sK & 3) == 0 && (r0 & 3) == 0) {
+        const int groups = rows >> 2, items = groups * 8;
+        for (int c = threadIdx.x; c < items; c += GU_THREADS) {
+            const int gi = c % groups, j = c / groups;
+            const int gr = r0 + 4 * gi;
+            float4 w[8];
+#pragma unroll
+            for (int kk = 0; kk < 8; kk++) {
+                const int k = k0 + 8 * j + kk;
+                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k < klim) {
+                    const float *p = src + gr + (long long)k * sK;
+                    if (gr + 3 < rlim) {
+                        x = __ldg(reinterpret_cast<const float4 *>(p));
+                    } else {
+                        x.x = gr < rlim ? p[0] : (gr == rone ? 1.f : 0.f);
+                        x.y = gr + 1 < rlim ? p[1] : (gr + 1 == rone ? 1.f : 0.f);
+                        x.z = gr + 2 < rlim ? p[2] : (gr + 2 == rone ? 1.f : 0.f);
+                        x.w = gr + 3 == rone ? 1.f : 0.f;
+                    }
+                }
+                w[kk] = x;
+            }
+            st_chunk(dst, 4 * gi, j, w[0].x, w[1].x, w[2].x, w[3].x, w[4].x, w[5].x, w[6].x, w[7].x);
+            st_chunk(dst, 4 * gi + 1, j, w[0].y, w[1].y, w[2].y, w[3].y, w[4].y, w[5].y, w[6].y, w[7].y);
+            st_chunk(dst, 4 * gi + 2, j, w[0].z, w[1].z, w[2].z, w[3].z, w[4].z, w[5].z, w[6].z, w[7].z);
+            st_chunk(dst, 4 * gi + 3, j, w[0].w, w[1].w, w[2].w, w[3].w, w[4].w, w[5].w, w[6].w, w[7].w);
+        }
+        return;
+    }
+    const bool kvec = aligned && sK == 1 && (sR & 3) == 0;
+    const int items = rows * 8;
+    for (int c0 = threadIdx.x; c0 < items; c0 += 4 * GU_THREADS) {
+        float x[4][8];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int c = c0 + u * GU_THREADS;
+            const int gr = r0 + (c >> 3), k = k0 + 8 * (c & 7);
+            const float *p = src + (long long)gr * sR + (long long)k * sK;
+            if (c < items && gr < rlim && kvec && k + 8 <= klim) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(p + 4));
+                x[u][0] = a.x, x[u][1] = a.y, x[u][2] = a.z, x[u][3] = a.w;
+                x[u][4] = b.x, x[u][5] = b.y, x[u][6] = b.z, x[u][7] = b.w;
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < 8; kk++)
+                    x[u][kk] = (c < items && k + kk < klim) ? (gr < rlim ? p[kk * sK] : (gr == rone ? 1.f : 0.f)) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int c = c0 + u * GU_THREADS;
+            if (c < items)
+                st_chunk(dst, c >> 3, c & 7, x[u][0], x[u][1], x[u][2], x[u][3], x[u][4], x[u][5], x[u][6], x[u][7]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(GU_THREADS, 3) k_gemm_umma(GemmArgs g, int err_bit)
+{
+    int *err = g.err;
+    const int nt = g.nt, buf = GU_A_BYTES + nt * 128;
+    extern __shared__ uint8_t gu_raw[];
+    const uint32_t raw = smem_addr(gu_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t *gb = gu_raw + (base - raw);
+    // [A 0 | B 0 | A 1 | B 1] [barriers: done[0], done[1]] [tensor-memory slot] [stop]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gb + 2 * buf);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bars + 2);
+    volatile int *stop = reinterpret_cast<volatile int *>(slot + 1);
+    const uint32_t bar0 = smem_addr(bars);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * 128, n0 = blockIdx.x * nt;
+    const int ncols = min(nt, g.N - n0);
+    const int NT = (ncols + 15) & ~15;
+    const uint32_t idesc = umma_idesc_bf16(NT);
     const int kb = g.kchunk ? (int)blockIdx.z * g.kchunk : 0;
     const int ke = g.kchunk ? min(g.K, kb + g.kchunk) : g.K;
-    for (int k0 = kb; k0 < ke; k0 += GK) {
-        for (int e = threadIdx.x; e < GT * GK; e += 128) {
-            const int r = e / GK, kk = e - r * GK;
-            const int m = m0 + r, n = n0 + r, k = k0 + kk;
-            const float a = (m < g.M && k < ke) ? g.A[m * g.sAm + k * g.sAk] : 0.f;
-            const float b = (n < g.N && k < ke) ? g.B[k * g.sBk + n * g.sBn] : 0.f;
-            As[r][kk] = __float2bfloat16_rn(a);
-            Bs[r][kk] = __float2bfloat16_rn(b);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < GK; ks += 16) {
-            unsigned af[2][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                const int r = wm * 32 + i * 16 + gid;
-                af[i][0] = pack2(&As[r][ks + 2 * tig]);
-                af[i][1] = pack2(&As[r + 8][ks + 2 * tig]);
-                af[i][2] = pack2(&As[r][ks + 2 * tig + 8]);
-                af[i][3] = pack2(&As[r + 8][ks + 2 * tig + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int c = wn * 32 + j * 8 + gid;
-                bfr[j][0] = pack2(&Bs[c][ks + 2 * tig]);
-                bfr[j][1] = pack2(&Bs[c][ks + 2 * tig + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                                 "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                                 : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
-                                 : "r"(af[i][0]), "r"(af[i][1]), "r"(af[i][2]), "r"(af[i][3]), "r"(bfr[j][0]),
-                                   "r"(bfr[j][1]));
-        }
-        __syncthreads();
+    const int steps = ke > kb ? (ke - kb + GU_K - 1) / GU_K : 0;
+    if (threadIdx.x == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        *stop = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)), "r"(nt)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    bool ok = true;
+    int issued = 0; // steps whose MMAs were issued (the same count in every thread)
+    for (int st = 0; st < steps && ok; st++) {
+        const int b = st & 1;
+        // buffer b was last read by the MMAs of step st - 2
+        if (st >= 2) ok = umma_wait(bar0 + 8 * b, ((st - 2) >> 1) & 1, stop, err, err_bit);
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        uint8_t *ta = gb + b * buf, *tbt = ta + GU_A_BYTES;
+        const int k0 = kb + st * GU_K;
+        gu_tile(ta, g.A, g.sAm, g.sAk, m0, 128, g.M, k0, ke, -1);
+        gu_tile(tbt, g.B, g.sBn, g.sBk, n0, NT, g.bone >= 0 ? g.bone : g.N, k0, ke, g.bone);
+        fence_proxy_async_smem(); // the tile stores are visible to the tensor core's reads
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t a = base + b * buf, bb = a + GU_A_BYTES;
 #pragma unroll
-    for (int i = 0; i < 2; i++)
+            for (int k = 0; k < GU_K / 16; k++) // K = 16 BF16 (32 bytes) per MMA
+                umma_bf16(tmem, umma_desc_sw128(a + 32 * k), umma_desc_sw128(bb + 32 * k), idesc,
+                          (st > 0 || k > 0) ? 1 : 0);
+            umma_commit(bar0 + 8 * b);
+        }
+        issued = st + 1;
+    }
+    // the last step's MMAs (all earlier ones complete before it)
+    if (ok && steps > 0) ok = umma_wait(bar0 + 8 * ((steps - 1) & 1), ((steps - 1) >> 1) & 1, stop, err, err_bit);
+    ok = __syncthreads_and(ok);
+    tc_fence_after();
+    if (ok) {
+        const int qd = warp & 3, half = warp >> 2;
+        const int row = m0 + 32 * qd + lane;
+        float *cz = g.C + blockIdx.z * g.sCz;
+        const bool vec = g.sCn == 1 && (g.sCm & 3) == 0 && (reinterpret_cast<uintptr_t>(cz) & 15) == 0;
+        float *crow = cz + (long long)row * g.sCm;
+        for (int c0 = 16 * half; c0 < NT; c0 += 32) {
+            uint32_t v[16];
+            if (steps > 0) {
+                tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)c0, v);
+            } else {
 #pragma unroll
-        for (int j = 0; j < 4; j++)
+                for (int j = 0; j < 16; j++) v[j] = 0u;
+            }
+            if (row < g.M) {
+                float x[16], mk[16];
+                if (g.mask) {
+                    const float *mr = g.mask + (long long)row * g.sCm;
+                    if (vec && c0 + 16 <= ncols) {
 #pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const int m = m0 + wm * 32 + i * 16 + gid + (r >= 2 ? 8 : 0);
-                const int n = n0 + wn * 32 + j * 8 + 2 * tig + (r & 1);
-                if (m < g.M && n < g.N) {
-                    float v = acc[i][j][r];
-                    if (g.bias) v += g.bias[n];
-                    if (g.relu) v = fmaxf(v, 0.f);
-                    g.C[blockIdx.z * g.sCz + m * g.sCm + n * g.sCn] = v;
+                        for (int q = 0; q < 4; q++) {
+                            const float4 m4 = __ldg(reinterpret_cast<const float4 *>(mr + n0 + c0) + q);
+                            mk[4 * q] = m4.x, mk[4 * q + 1] = m4.y, mk[4 * q + 2] = m4.z, mk[4 * q + 3] = m4.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; j++) mk[j] = c0 + j < ncols ? mr[(long long)(n0 + c0 + j) * g.sCn] : 0.f;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    x[j] = __uint_as_float(v[j]);
+                    if (g.bias && c0 + j < ncols) x[j] += g.bias[n0 + c0 + j];
+                    if (g.relu) x[j] = fmaxf(x[j], 0.f);
+                    if (g.mask) x[j] = mk[j] > 0.f ? __bfloat162float(__float2bfloat16_rn(x[j])) : 0.f;
+                }
+                if (vec && c0 + 16 <= ncols) {
+                    float4 *o = reinterpret_cast<float4 *>(crow + n0 + c0);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) o[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; j++)
+                        if (c0 + j < ncols) crow[(long long)(n0 + c0 + j) * g.sCn] = x[j];
                 }
             }
+        }
+    } else if (threadIdx.x == 0) {
+        // a wait expired: let the MMAs already issued finish (bounded) before the memory goes;
+        // the last commit to buffer b was step s (s < issued, s = b mod 2), phase s >> 1
+        for (int b = 0; b < 2; b++) {
+            const int s = ((issued - 1) & 1) == b ? issued - 1 : issued - 2;
+            if (s < 0) continue;
+            const uint64_t t0 = global_ns();
+            while (!mbar_test(bar0 + 8 * b, (s >> 1) & 1) && global_ns() - t0 < UMMA_WAIT_NS) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(nt) : "memory");
+    }
 }
 
-cudaError_t gemm(const GemmArgs &a, cudaStream_t s)
+int gu_nsm()
 {
-    dim3 grid((a.N + GT - 1) / GT, (a.M + GT - 1) / GT);
-    k_gemm_bf16<<<grid, 128, 0, s>>>(a);
+    static int n = 0;
+    if (n <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            n <= 0)
+            n = 152;
+    }
+    return n;
+}
+
+// the widest tile whose grid (with nz slices of K) still gives every SM a block
+int gu_pick_nt(int M, int N, int nz)
+{
+    const long long mt = (M + 127) / 128;
+    for (int nt = 256; nt > 64; nt >>= 1)
+        if ((long long)((N + nt - 1) / nt) * mt * nz >= gu_nsm()) return nt;
+    return 64;
+}
+
+cudaError_t gu_launch(const GemmArgs &a, int nz, cudaStream_t s)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, gu_smem(256));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((a.N + a.nt - 1) / a.nt, (a.M + 127) / 128, nz);
+    k_gemm_umma<<<grid, GU_THREADS, gu_smem(a.nt), s>>>(a, GU_ERR);
     return cudaGetLastError();
 }
 
-// out[m][n] = sum_z part[z][m][n], z in increasing order (M x N dense partials)
-__global__ void k_sum_partials(const float *__restrict__ part, int nz, int M, int N, float *out, long long sOm)
+cudaError_t gemm(GemmArgs a, cudaStream_t s)
+{
+    if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+    a.nt = gu_pick_nt(a.M, a.N, 1);
+    return gu_launch(a, 1, s);
+}
+
+// out[m][n] = sum_z part[z][m][n], z in increasing order (M x N partials, rows
+// `ld` floats apart); with `ocol`, column N - 1 goes to ocol[m] instead
+__global__ void k_sum_partials(const float *__restrict__ part, int nz, int M, int N, int ld, float *out,
+                               long long sOm, float *ocol)
 {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)M * N) return;
+    const long long m = e / N, nn = e - m * N;
     float s = 0.f;
-    for (int z = 0; z < nz; z++) s += part[z * (long long)M * N + e];
-    out[(e / N) * sOm + e % N] = s;
+    for (int z = 0; z < nz; z++) s += part[(z * (long long)M + m) * ld + nn];
+    if (ocol && nn == N - 1) ocol[m] = s;
+    else out[m * sOm + nn] = s;
 }
 
 // A weight gradient C = A B with a long K (the batch): K split into slices whose
 // partial products land in `part` and are then summed in a fixed order, so the
-// result does not depend on scheduling.  C is M x N with row stride sCm.
-cudaError_t gemm_splitk(GemmArgs a, float *part, long long part_floats, cudaStream_t s)
+// result does not depend on scheduling.  C is M x N with row stride sCm; with
+// `ocol` (and a.bone = N - 1), C's last column -- the row sums of A -- goes to
+// ocol instead.
+cudaError_t gemm_splitk(GemmArgs a, float *part, long long part_floats, cudaStream_t s, float *ocol = nullptr)
 {
-    const int tiles = ((a.N + GT - 1) / GT) * ((a.M + GT - 1) / GT);
-    int nz = std::max(1, std::min(32, 256 / std::max(tiles, 1)));
-    nz = (int)std::min<long long>(nz, std::max(1LL, part_floats / ((long long)a.M * a.N)));
-    nz = std::min(nz, (a.K + GK - 1) / GK);
-    const int kchunk = ((a.K + nz - 1) / nz + GK - 1) / GK * GK;
-    nz = (a.K + kchunk - 1) / kchunk;
+    if (a.M <= 0 || a.N <= 0) return cudaSuccess;
+    const int ld = (a.N + 3) & ~3; // partial rows padded to 16 bytes (vector stores)
+    const long long mn = (long long)a.M * ld;
+    const long long nzmax = std::max(1LL, std::min({32LL, part_floats / mn, (long long)(a.K + GU_K - 1) / GU_K}));
+    a.nt = gu_pick_nt(a.M, a.N, (int)nzmax);
+    const long long tiles = (long long)((a.N + a.nt - 1) / a.nt) * ((a.M + 127) / 128);
+    int nz = (int)std::max(1LL, std::min(nzmax, (2LL * gu_nsm() + tiles - 1) / tiles)); // about two blocks per SM
+    int kchunk = 0;
+    if (a.K > 0) {
+        kchunk = ((a.K + nz - 1) / nz + GU_K - 1) / GU_K * GU_K;
+        nz = (a.K + kchunk - 1) / kchunk;
+    } else {
+        nz = 1;
+    }
     float *C = a.C;
     const long long sCm = a.sCm;
     a.C = part;
-    a.sCm = a.N;
+    a.sCm = ld;
     a.sCn = 1;
     a.kchunk = kchunk;
-    a.sCz = (long long)a.M * a.N;
-    dim3 grid((a.N + GT - 1) / GT, (a.M + GT - 1) / GT, nz);
-    k_gemm_bf16<<<grid, 128, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    a.sCz = mn;
+    cudaError_t e = gu_launch(a, nz, s);
     if (e != cudaSuccess) return e;
     const long long tot = (long long)a.M * a.N;
-    k_sum_partials<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nz, a.M, a.N, C, sCm);
+    k_sum_partials<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, nz, a.M, a.N, ld, C, sCm, ocol);
     return cudaGetLastError();
 }
 
@@ -207,61 +428,128 @@ __global__ void k_head(const float *__restrict__ h2, const float *__restrict__ w
     if (lane == 0) y[row] = s + b3[0];
 }
 
-// gy[b] = 2 (y[b] - t[b]) / n; dh2[b][j] = bf16(gy[b] bf16(w3[j])) if h2[b][j] > 0 else 0
-__global__ void k_head_back(const float *__restrict__ y, const float *__restrict__ t, const float *__restrict__ h2,
-                            const float *__restrict__ w3, int n, int H, float *gy, float *dh2)
-{
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (long long)n * H) return;
-    const int b = (int)(e / H), j = (int)(e - (long long)b * H);
-    const float g = 2.f * (y[b] - t[b]) / (float)n;
-    if (j == 0) gy[b] = g;
-    dh2[e] = h2[e] > 0.f ? rbf(g * rbf(w3[j])) : 0.f;
-}
+// The training head, for a batch of n rows:
+//   y[b]   = sum_j bf16(h2[b][j]) bf16(w3[j]) + b3            (the sum of k_head, same order)
+//   gy[b]  = 2 (y[b] - t[b]) / n                              (d loss / d y, mean squared error)
+//   dh2[b][j] = bf16(gy[b] bf16(w3[j])) where h2[b][j] > 0, else 0
+// and the sums over the batch dw3[j] = sum_b gy[b] bf16(h2[b][j]), db2[j] =
+// sum_b dh2[b][j], db3 = sum_b gy[b].  k_head_train: one warp per row (lane l
+// holds columns l + 32 i, the next row's loads issued before the current row's
+// arithmetic); block c sums its rows, warp by warp in order, into
+// part[c][0, 2H].  k_head_sums: one warp per entry adds the blocks' rows in a
+// fixed order (lane l the blocks l, l + 32, ..., then a fixed shuffle tree).
+constexpr int HT_THREADS = 256;
 
-// dh1 <- bf16(dh1) where h1 > 0, else 0 (in place)
-__global__ void k_relu_back(float *dh, const float *__restrict__ h, long long total)
+template <int NC>
+__global__ void __launch_bounds__(HT_THREADS) k_head_train(const float *__restrict__ h2, const float *__restrict__ w3,
+                                                           const float *__restrict__ b3, const float *__restrict__ t,
+                                                           int n, int H, int rows_per_block, float *y, float *gy,
+                                                           float *dh2, float *part)
 {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < total) dh[e] = h[e] > 0.f ? rbf(dh[e]) : 0.f;
-}
-
-// Column sums over the batch in two fixed-order stages: block c sums rows
-// [c CS, (c + 1) CS) of every column into part[c][j], then the chunks are
-// summed in order.  Terms: bf16(v[b][j]) (round_bf16), v[b][j], or, with w,
-// w[b] bf16(v[b][j]).
-constexpr int CS = 64;
-__global__ void k_colsum_part(const float *__restrict__ v, const float *__restrict__ w, int n, int H, int round_bf16,
-                              float *part)
-{
-    const int c = blockIdx.x, b0 = c * CS, b1 = min(n, b0 + CS);
-    for (int j = threadIdx.x; j < H; j += blockDim.x) {
-        float s = 0.f;
-        for (int b = b0; b < b1; b++) {
-            const float x = v[(long long)b * H + j];
-            if (w) s = fmaf(w[b], rbf(x), s);
-            else s += round_bf16 ? rbf(x) : x;
+    extern __shared__ float ht_s[]; // 2H + 1 block sums
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = HT_THREADS / 32;
+    const int r0 = blockIdx.x * rows_per_block, r1 = min(n, r0 + rows_per_block);
+    float w3r[NC], aw[NC], ab[NC], v[NC], a3 = 0.f;
+#pragma unroll
+    for (int i = 0; i < NC; i++) {
+        const int j = lane + 32 * i;
+        w3r[i] = j < H ? rbf(w3[j]) : 0.f;
+        aw[i] = ab[i] = 0.f;
+    }
+    int r = r0 + warp;
+    if (r < r1) {
+#pragma unroll
+        for (int i = 0; i < NC; i++) v[i] = lane + 32 * i < H ? h2[(long long)r * H + lane + 32 * i] : 0.f;
+    }
+    for (; r < r1; r += nw) {
+        float vn[NC];
+        const int rn = r + nw;
+#pragma unroll
+        for (int i = 0; i < NC; i++) vn[i] = (rn < r1 && lane + 32 * i < H) ? h2[(long long)rn * H + lane + 32 * i] : 0.f;
+        float sum = 0.f;
+#pragma unroll
+        for (int i = 0; i < NC; i++)
+            if (lane + 32 * i < H) sum = fmaf(rbf(v[i]), w3r[i], sum);
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        const float yr = sum + b3[0];
+        const float g = 2.f * (yr - t[r]) / (float)n;
+        if (lane == 0) {
+            y[r] = yr;
+            gy[r] = g;
         }
-        part[(long long)c * H + j] = s;
+        float *dr = dh2 + (long long)r * H;
+#pragma unroll
+        for (int i = 0; i < NC; i++) {
+            const int j = lane + 32 * i;
+            if (j < H) {
+                const float d = v[i] > 0.f ? rbf(g * w3r[i]) : 0.f;
+                dr[j] = d;
+                aw[i] = fmaf(g, rbf(v[i]), aw[i]);
+                ab[i] += d;
+            }
+            v[i] = vn[i];
+        }
+        a3 += g;
+    }
+    // block sums, warp 0 first
+    for (int w = 0; w < nw; w++) {
+        if (warp == w) {
+#pragma unroll
+            for (int i = 0; i < NC; i++) {
+                const int j = lane + 32 * i;
+                if (j < H) {
+                    ht_s[j] = w ? ht_s[j] + aw[i] : aw[i];
+                    ht_s[H + j] = w ? ht_s[H + j] + ab[i] : ab[i];
+                }
+            }
+            if (lane == 0) ht_s[2 * H] = w ? ht_s[2 * H] + a3 : a3;
+        }
+        __syncthreads();
+    }
+    const int W = 2 * H + 1;
+    for (int e = threadIdx.x; e < W; e += HT_THREADS) part[(long long)blockIdx.x * W + e] = ht_s[e];
+}
+
+__global__ void k_head_sums(const float *__restrict__ part, int nb, int H, float *dw3, float *db2, float *db3)
+{
+    const int W = 2 * H + 1;
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (e >= W) return;
+    float sum = 0.f;
+    for (int c = lane; c < nb; c += 32) sum += part[(long long)c * W + e];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) {
+        if (e < H) dw3[e] = sum;
+        else if (e < 2 * H) db2[e - H] = sum;
+        else db3[0] = sum;
     }
 }
 
-__global__ void k_colsum_fin(const float *__restrict__ part, int nc, int H, float *out)
-{
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= H) return;
-    float s = 0.f;
-    for (int c = 0; c < nc; c++) s += part[(long long)c * H + j];
-    out[j] = s;
-}
+constexpr int HT_MAX_BLOCKS = 1024;
 
-cudaError_t colsum(const float *v, const float *w, int n, int H, int round_bf16, float *part, float *out, cudaStream_t s)
+cudaError_t head_train(const float *h2, const float *w3, const float *b3, const float *t, int n, int H, float *y,
+                       float *gy, float *dh2, float *part, long long part_floats, float *dw3, float *db2, float *db3,
+                       cudaStream_t s)
 {
-    const int nc = (n + CS - 1) / CS;
-    k_colsum_part<<<nc, H >= 128 ? 128 : 32, 0, s>>>(v, w, n, H, round_bf16, part);
+    const long long W = 2LL * H + 1;
+    // about four rows per warp
+    int blocks = (int)std::min<long long>({(long long)(n + 31) / 32, (long long)HT_MAX_BLOCKS, part_floats / W});
+    blocks = std::max(blocks, 1);
+    const int rpb = (n + blocks - 1) / blocks;
+    blocks = (n + rpb - 1) / rpb;
+    const size_t smem = sizeof(float) * (size_t)W;
+    const int nc = (H + 31) / 32;
+#define HT_LAUNCH(NC) k_head_train<NC><<<blocks, HT_THREADS, smem, s>>>(h2, w3, b3, t, n, H, rpb, y, gy, dh2, part)
+    if (nc <= 1) HT_LAUNCH(1);
+    else if (nc <= 2) HT_LAUNCH(2);
+    else if (nc <= 4) HT_LAUNCH(4);
+    else if (nc <= 8) HT_LAUNCH(8);
+    else if (nc <= 16) HT_LAUNCH(16);
+    else HT_LAUNCH(32);
+#undef HT_LAUNCH
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_colsum_fin<<<(H + 127) / 128, 128, 0, s>>>(part, nc, H, out);
+    k_head_sums<<<(unsigned)((W + 7) / 8), 256, 0, s>>>(part, blocks, H, dw3, db2, db3);
     return cudaGetLastError();
 }
 
@@ -274,6 +562,19 @@ __global__ void k_gather_batch(const float *__restrict__ X, const float *__restr
     const int k = (int)(e / KPAD), col = (int)(e - (long long)k * KPAD);
     const long long src = (a * (long long)(b0 + k) + c) % n;
     Xb[e] = X[src * KPAD + col];
+    if (col == 0) tb[k] = t[src];
+}
+
+// the same with one float4 per thread (X 16-byte aligned; rows are KPAD = 36 float4)
+__global__ void k_gather_batch4(const float4 *__restrict__ X, const float *__restrict__ t, int n, long long a,
+                                long long c, int b0, int nb, float4 *Xb, float *tb)
+{
+    constexpr int R4 = KPAD / 4;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)nb * R4) return;
+    const int k = (int)(e / R4), col = (int)(e - (long long)k * R4);
+    const long long src = (a * (long long)(b0 + k) + c) % n;
+    Xb[e] = X[src * R4 + col];
     if (col == 0) tb[k] = t[src];
 }
 
@@ -453,17 +754,17 @@ bc_status ensure_batch(bc_mlp_t net, int n)
     MCK(cudaMalloc(&net->y, sizeof(float) * cap));
     MCK(cudaMalloc(&net->gy, sizeof(float) * cap));
     if (net->part) cudaFree(net->part);
-    // up to 32 split-K slices of the largest weight gradient (H x H or H x 132), and
-    // the column-sum partials (one row of H per CS batch rows)
-    net->part_floats = std::max(32LL * (long long)H * std::max<long long>((long long)H, KIN),
-                                (long long)((cap + CS - 1) / CS) * (long long)H);
+    // up to 32 split-K slices of the largest weight gradient (H x (H + 1) or H x 133,
+    // the last column the bias gradient), and the training head's block sums
+    net->part_floats = std::max(32LL * (long long)H * (std::max<long long>((long long)H, KIN) + 1),
+                                (long long)HT_MAX_BLOCKS * (2LL * (long long)H + 1));
     MCK(cudaMalloc(&net->part, sizeof(float) * net->part_floats));
     net->cap = cap;
     return BC_OK;
 }
 
-// forward pass into net->h1, net->h2, y
-bc_status forward(bc_mlp_t net, const float *X, int n, float *y, cudaStream_t s)
+// the hidden layers into net->h1, net->h2
+bc_status hidden_layers(bc_mlp_t net, const float *X, int n, cudaStream_t s)
 {
     const int H = net->H;
     const Offsets &o = net->off;
@@ -471,37 +772,47 @@ bc_status forward(bc_mlp_t net, const float *X, int n, float *y, cudaStream_t s)
     // W1 is stored [H][132]; rows of X are padded to 144 with zeros, so K runs to 144 and
     // B(k, n) = W1[n][k] must be zero for k >= 132: bound K by 132 instead.
     a1.K = KIN;
+    a1.err = ctx_err(net->ctx);
     MCK(gemm(a1, s));
     GemmArgs a2{net->h1, H, 1, net->p + o.W2, 1, H, net->h2, H, 1, n, H, H, net->p + o.b2, 1};
+    a2.err = ctx_err(net->ctx);
     MCK(gemm(a2, s));
-    k_head<<<(n + 7) / 8, 256, 0, s>>>(net->h2, net->p + o.w3, net->p + o.b3, n, H, y);
+    return BC_OK;
+}
+
+// forward pass into net->h1, net->h2, y
+bc_status forward(bc_mlp_t net, const float *X, int n, float *y, cudaStream_t s)
+{
+    if (bc_status st = hidden_layers(net, X, n, s)) return st;
+    const Offsets &o = net->off;
+    k_head<<<(n + 7) / 8, 256, 0, s>>>(net->h2, net->p + o.w3, net->p + o.b3, n, net->H, y);
     MCK(cudaGetLastError());
     return BC_OK;
 }
 
-// gradients of the mean squared error into net->g
-bc_status backward(bc_mlp_t net, const float *X, const float *t, int n, cudaStream_t s)
+// forward pass (net->y) and the gradients of the mean squared error into net->g
+bc_status forward_backward(bc_mlp_t net, const float *X, const float *t, int n, cudaStream_t s)
 {
+    if (bc_status st = hidden_layers(net, X, n, s)) return st;
     const int H = net->H;
     const Offsets &o = net->off;
-    const long long nh = (long long)n * H;
-    k_head_back<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(net->y, t, net->h2, net->p + o.w3, n, H, net->gy, net->dh2);
-    MCK(cudaGetLastError());
-    MCK(colsum(net->h2, net->gy, n, H, 1, net->part, net->g + o.w3, s)); // dw3[j] = sum_b gy[b] bf16(h2[b][j])
-    MCK(colsum(net->gy, nullptr, n, 1, 0, net->part, net->g + o.b3, s));
+    // y, gy, dh2 and the sums over the batch: dw3, db2, db3
+    MCK(head_train(net->h2, net->p + o.w3, net->p + o.b3, t, n, H, net->y, net->gy, net->dh2, net->part,
+                   net->part_floats, net->g + o.w3, net->g + o.b2, net->g + o.b3, s));
     // dW2 = dh2^T h1  (M = H out, N = H in, K = n)
     GemmArgs w2{net->dh2, 1, H, net->h1, H, 1, net->g + o.W2, H, 1, H, H, n, nullptr, 0};
+    w2.err = ctx_err(net->ctx);
     MCK(gemm_splitk(w2, net->part, net->part_floats, s));
-    MCK(colsum(net->dh2, nullptr, n, H, 1, net->part, net->g + o.b2, s));
-    // dh1 = (dh2 W2) masked by h1 > 0  (M = n, N = H in, K = H out)
+    // dh1 = bf16(dh2 W2) where h1 > 0, else 0  (M = n, N = H in, K = H out)
     GemmArgs d1{net->dh2, H, 1, net->p + o.W2, H, 1, net->dh1, H, 1, n, H, H, nullptr, 0};
+    d1.err = ctx_err(net->ctx);
+    d1.mask = net->h1;
     MCK(gemm(d1, s));
-    k_relu_back<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(net->dh1, net->h1, nh);
-    // dW1 = dh1^T X  (M = H, N = 132, K = n)
-    GemmArgs w1{net->dh1, 1, H, X, KPAD, 1, net->g + o.W1, KIN, 1, H, KIN, n, nullptr, 0};
-    MCK(gemm_splitk(w1, net->part, net->part_floats, s));
-    MCK(colsum(net->dh1, nullptr, n, H, 1, net->part, net->g + o.b1, s));
-    MCK(cudaGetLastError());
+    // [dW1 | db1] = dh1^T [X | 1]  (M = H, N = 132 + 1, K = n): the column of ones gives db1 = sum_b dh1[b]
+    GemmArgs w1{net->dh1, 1, H, X, KPAD, 1, net->g + o.W1, KIN, 1, H, KIN + 1, n, nullptr, 0};
+    w1.err = ctx_err(net->ctx);
+    w1.bone = KIN;
+    MCK(gemm_splitk(w1, net->part, net->part_floats, s, net->g + o.b1));
     return BC_OK;
 }
 
@@ -648,8 +959,7 @@ bc_status bc_mlp_grads(bc_mlp_t net, const float *X, const float *t, int n, floa
         if (!net->ctx) return mfail(BC_ERR_ARG, "bc_mlp_grads: the network's context was destroyed");
         if (bc_status st = ensure_batch(net, n)) return st;
         cudaStream_t s = ctx_stream(net->ctx);
-        if (bc_status st = forward(net, X, n, net->y, s)) return st;
-        if (bc_status st = backward(net, X, t, n, s)) return st;
+        if (bc_status st = forward_backward(net, X, t, n, s)) return st;
         if (loss) {
             k_loss<<<1, 256, 0, s>>>(net->y, t, n, loss);
             MCK(cudaGetLastError());
@@ -726,17 +1036,24 @@ bc_status bc_mlp_train(bc_mlp_t net, const float *X, const float *t, int n, int 
         const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
         const long long total = net->off.total;
         const int steps = n / batch;
+        const bool x16 = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
         for (int e = 0; e < epochs; e++) {
             long long a = 1, c = 0;
             epoch_order(seed, e, n, &a, &c);
             const float lr_e = (float)(lr * 0.5 * (1.0 + std::cos(M_PI * e / epochs)));
             for (int st = 0; st < steps; st++) {
-                const long long tot = (long long)batch * KPAD;
-                k_gather_batch<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, t, n, a, c, st * batch, batch, net->xb,
-                                                                             net->tb);
+                if (x16) {
+                    const long long tot = (long long)batch * (KPAD / 4);
+                    k_gather_batch4<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+                        reinterpret_cast<const float4 *>(X), t, n, a, c, st * batch, batch,
+                        reinterpret_cast<float4 *>(net->xb), net->tb);
+                } else {
+                    const long long tot = (long long)batch * KPAD;
+                    k_gather_batch<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, t, n, a, c, st * batch, batch,
+                                                                                 net->xb, net->tb);
+                }
                 MCK(cudaGetLastError());
-                if (bc_status r = forward(net, net->xb, batch, net->y, s)) return r;
-                if (bc_status r = backward(net, net->xb, net->tb, batch, s)) return r;
+                if (bc_status r = forward_backward(net, net->xb, net->tb, batch, s)) return r;
                 net->step++;
                 const float c1 = (float)(1.0 - std::pow(0.9, (double)net->step));
                 const float c2 = (float)(1.0 - std::pow(0.999, (double)net->step));

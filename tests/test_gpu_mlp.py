@@ -49,9 +49,11 @@ def problem(H=64, n=200, seed=0):
     return init, q.astype(np.float32), fa.astype(np.float32), fb.astype(np.float32), t
 
 
-@pytest.mark.parametrize("H", [64, 256])
-def test_forward_and_gradients_match_oracle(bc, H):
-    init, q, fa, fb, t = problem(H)
+# (hidden, batch): ragged row tiles (200, 203 = 4 k + 3), 20,000 rows (forward on
+# 256-column tiles), hidden 1024 (weight gradients on 128-column tiles)
+@pytest.mark.parametrize("H,n", [(64, 200), (256, 200), (64, 203), (256, 20000), (1024, 200)])
+def test_forward_and_gradients_match_oracle(bc, H, n):
+    init, q, fa, fb, t = problem(H, n)
     ctx = bc.Context(32, 6, synth.RADII_2)
     net = bc.MLP(ctx, H, init)
     dev = torch.device("cuda")
@@ -70,7 +72,7 @@ def test_forward_and_gradients_match_oracle(bc, H):
     assert abs(float(loss.item()) - lo) <= 1e-4 * abs(lo)
     for k in go:
         r = rel(g[k], go[k])
-        print(f"H={H} grad {k}: rel-L2 {r:.2e}")
+        print(f"H={H} n={n} grad {k}: rel-L2 {r:.2e}")
         assert r < GRAD_TOL, (k, r)
     net.close()
     ctx.close()
