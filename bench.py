@@ -639,7 +639,8 @@ def learned_study(args):
     N, W, H = 96, 8, 256
     stream = torch.cuda.current_stream(dev)
     ctx = bc.Context(N, W, synth.RADII_4, stream=stream)
-    net = bc.MLP(ctx, H, synth.mlp_init(H, 7))
+    rot = args.ligand_moments == "rotated"
+    net = bc.MLP(ctx, H, synth.mlp_init(H, 7), rotated_moments=rot)
     # labels and the recall judge come from the binned spreading, whose sums are
     # order-independent fixed point: bit-reproducible peaks, so every run trains the
     # same network and judges it against the same best rotation; timings use spread 0
@@ -660,8 +661,11 @@ def learned_study(args):
         hA, hB = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
         q = synth.shoemake_quaternions(synth.SplitMix64(seed + 200000), args.train_rot).astype(np.float32)
         peak, _ = ctx.sweep(hA, hB, q, batch=256)
-        fa, fb = bc.moments(ctx, hA), bc.moments(ctx, hB)
-        Xs.append(net.features(torch.tensor(q, device=dev), fa, fb))
+        qd = torch.tensor(q, device=dev)
+        fa = bc.moments(ctx, hA)
+        # the ligand's moments: once (as given), or per rotation (turned by it)
+        fb = bc.moments_rot(ctx, hB, qd) if rot else bc.moments(ctx, hB)
+        Xs.append(net.features(qd, fa, fb))
         z = (peak - peak.mean()) / peak.std()
         if args.target_alpha > 0:  # monotone stretch of the top: same ranking, MSE weighted toward it
             z = torch.exp(args.target_alpha * (z - 3.0))
@@ -670,8 +674,8 @@ def learned_study(args):
         rng_aug = synth.SplitMix64(seed + 500000)
         for s_q in synth.shoemake_quaternions(rng_aug, args.augment):
             hS = ctx.shape(synth.rotate_points(A.xyz, s_q), A.level)
-            Xs.append(net.features(torch.tensor(synth.compose_quaternions(s_q, q).astype(np.float32), device=dev),
-                                   bc.moments(ctx, hS), fb))
+            qs = torch.tensor(synth.compose_quaternions(s_q, q).astype(np.float32), device=dev)
+            Xs.append(net.features(qs, bc.moments(ctx, hS), bc.moments_rot(ctx, hB, qs) if rot else fb))
             ts.append(z)
             hS.close()
         hA.close()
@@ -718,7 +722,8 @@ def learned_study(args):
         ms_learn.append(e1.elapsed_time(e2))
         p = peak.cpu().numpy()
         # held-out fit of the network on this pair's standardised peaks
-        fa, fb = bc.moments(ctx, hA), bc.moments(ctx, hB)
+        fa = bc.moments(ctx, hA)
+        fb = bc.moments_rot(ctx, hB, qd) if rot else bc.moments(ctx, hB)
         pred = net.predict(net.features(qd, fa, fb)).cpu().numpy()
         z = (p - p.mean()) / p.std()
         if args.target_alpha > 0:
@@ -804,7 +809,7 @@ def learned_study(args):
                    "train_pairs": args.train_pairs, "train_rotations_per_pair": args.train_rot,
                    "eval_pairs": args.eval_pairs, "eval_rotations_per_pair": R, "topk": K, "hidden": H,
                    "epochs": args.epochs, "adam_steps": steps, "batch": bs, "lr": lr,
-                   "rotation_augmentation_per_pair": args.augment,
+                   "rotation_augmentation_per_pair": args.augment, "ligand_moments": args.ligand_moments,
                    "target": "exp(%g (z - 3))" % args.target_alpha if args.target_alpha > 0 else "z"},
         "plain_per_rotation_poses_s": plain,
         "batched_exhaustive_poses_s": batched,
@@ -888,6 +893,9 @@ def main():
                     help="learned workload: also rank by scores averaged over this many random receptor orientations")
     ap.add_argument("--target-alpha", type=float, default=0.0,
                     help="train on exp(alpha (z - 3)) of the standardised peak z instead of z (0: z)")
+    ap.add_argument("--ligand-moments", choices=("rotated", "fixed"), default="rotated",
+                    help="the network's ligand features: the moments of the ligand turned by each rotation, "
+                         "or of the ligand as given")
     ap.add_argument("--augment", type=int, default=64,
                     help="extra random orientations of each training receptor (rotation augmentation)")
     args = ap.parse_args()

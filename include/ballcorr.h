@@ -339,7 +339,9 @@ bc_status bc_autotune(bc_ctx_t ctx, bc_shape_t A, bc_shape_t B, int rotations, b
  * x = [q / |q| with w >= 0 (4); m_A (BC_MOMENTS); m_B (BC_MOMENTS)], where
  * m_S[i] = |f^_S(m_i)| / f^_S(0) over the BC_MOMENTS lowest modes of the half
  * spectrum (m_z >= 0, m != 0, components inside (-N/2, N/2)) ordered by
- * (|m|^2, m_x, m_y, m_z), for the unrotated shape.  Network: 132 -> H -> H -> 1,
+ * (|m|^2, m_x, m_y, m_z), for the unrotated shape -- or, for a network set to
+ * take them (bc_mlp_set_features), m_B of the ligand turned by the rotation,
+ * m_{R B}[i] = |f^_B(R^T m_i)| / f^_B(0).  Network: 132 -> H -> H -> 1,
  * ReLU, FP32 master weights, BF16 operands on the tensor cores with FP32
  * accumulation, mean squared error, Adam (beta1 0.9, beta2 0.999, eps 1e-8).
  * Parameter layout (FP32): W1 [H][132], b1 [H], W2 [H][H], b2 [H], w3 [H], b3 [1]. */
@@ -352,6 +354,16 @@ typedef struct bc_mlp_s *bc_mlp_t;
  * the correlation kernels (overwrites the context's cached spectrum).
  * Errors: BC_ERR_ARG (null pointer, empty shape, foreign shape), BC_ERR_CUDA. */
 bc_status bc_shape_moments(bc_ctx_t ctx, bc_shape_t shape, float *out);
+
+/* out (device, n x BC_MOMENTS floats): row r = the moments of the shape turned
+ * by rotation r of quats (device, n x 4, (w, x, y, z), normalised here), i.e.
+ * |f^_S(R_r^T m_i)| / f^_S(0) with f^_S(k) = sum_i h^(rho_{l_i}, |k|)
+ * exp(-2 pi i k . c_i / P) (Eq. (fballhat) summed directly over the knots, in
+ * FP32: the band-limited spectrum of Sec. 2.5 at the turned modes, no
+ * spreading).  A zero quaternion is reported by the next bc_sync as BC_ERR_ARG.
+ * Asynchronous.  Errors: BC_ERR_ARG (null pointer, empty or foreign shape,
+ * n < 1), BC_ERR_CUDA. */
+bc_status bc_shape_moments_rot(bc_ctx_t ctx, bc_shape_t shape, const float *quats, int n, float *out);
 
 /* Number of FP32 parameters of a network with H hidden units. */
 long long bc_mlp_param_count(int hidden);
@@ -368,6 +380,19 @@ bc_status bc_mlp_destroy(bc_mlp_t net);
  * is reported by the next bc_sync as BC_ERR_ARG. */
 bc_status bc_mlp_features(bc_mlp_t net, const float *quats, int n, const float *moments_a, const float *moments_b,
                           float *X);
+
+/* As bc_mlp_features with a ligand moment vector per row: moments_b_rows
+ * (device, n x BC_MOMENTS), row r for rotation r (bc_shape_moments_rot). */
+bc_status bc_mlp_features_rows(bc_mlp_t net, const float *quats, int n, const float *moments_a,
+                               const float *moments_b_rows, float *X);
+
+/* Which ligand moments the network takes: 0 (the default) the unrotated
+ * ligand's, the same for every rotation; 1 the rotated ligand's
+ * (bc_shape_moments_rot).  The learned sweeps build their features to match.
+ * Errors: BC_ERR_ARG (null network, value not 0 or 1). */
+bc_status bc_mlp_set_features(bc_mlp_t net, int rotated_moments);
+/* The current setting (0 for a null network). */
+int bc_mlp_rotated_moments(bc_mlp_t net);
 
 /* y (device, n) = network(X). */
 bc_status bc_mlp_predict(bc_mlp_t net, const float *X, int n, float *y);
@@ -398,7 +423,9 @@ bc_status bc_mlp_state(bc_mlp_t net, float *params, float *adam_m, float *adam_v
 
 /* Learned sweep: scores n rotations (device quats, n <= BC_TOPK_MAX) with the
  * network, keeps the topk best (ties to the lowest index), and computes the
- * peaks of their full correlations as bc_sweep does.  Outputs (device):
+ * peaks of their full correlations as bc_sweep does.  The features follow the
+ * network's setting (bc_mlp_set_features): the unrotated ligand's moments, or
+ * the rotated ligand's for every rotation.  Outputs (device):
  * idx[topk] (rotation indices, best score first), peak[topk], argmax[topk],
  * and scores[n] when not NULL.  Asynchronous.
  * Errors: BC_ERR_ARG (null pointer, n or topk out of range), BC_ERR_CUDA. */
@@ -409,7 +436,8 @@ bc_status bc_learned_sweep(bc_ctx_t ctx, bc_mlp_t net, bc_shape_t A, bc_shape_t 
  * mean of the network's scores for (A, R B) and, for each of the norient host
  * quaternions s_k (w, x, y, z), for (S_k A, S_k R B), which has the same peak
  * over translations (S_k A's moments come from its spectrum, computed on the
- * device; the rotations S_k R are composed on the device).  scores, when not
+ * device; the rotations S_k R are composed on the device, and with rotated
+ * ligand moments those of S_k R B are taken).  scores, when not
  * NULL, receives the averaged scores; the rest is bc_learned_sweep, which is
  * the norient = 0 case.  Asynchronous.  Errors as bc_learned_sweep, and
  * BC_ERR_ARG for norient < 0, norient > 0 with null orients, a zero

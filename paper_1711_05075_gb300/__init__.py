@@ -80,6 +80,11 @@ def lib():
         L.bc_pairs.argtypes = [vp, vp, vp, vp, i, vp, vp, vp, i]
         L.bc_pairs.restype = st
         L.bc_shape_moments.argtypes = [vp, vp, vp]
+        L.bc_shape_moments_rot.argtypes = [vp, vp, vp, i, vp]
+        L.bc_mlp_features_rows.argtypes = [vp, vp, i, vp, vp, vp]
+        L.bc_mlp_set_features.argtypes = [vp, i]
+        L.bc_mlp_rotated_moments.argtypes = [vp]
+        L.bc_mlp_rotated_moments.restype = i
         L.bc_mlp_param_count.argtypes = [i]
         L.bc_mlp_param_count.restype = ctypes.c_longlong
         L.bc_mlp_create.argtypes = [vp, i, vp, ctypes.POINTER(vp)]
@@ -99,7 +104,8 @@ def lib():
         for f in ("bc_sweep_plan", "bc_plan_run", "bc_plan_destroy"):
             getattr(L, f).restype = st
         L.bc_topk.restype = st
-        for f in ("bc_shape_moments", "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
+        for f in ("bc_shape_moments", "bc_shape_moments_rot", "bc_mlp_features_rows", "bc_mlp_set_features",
+                  "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
                   "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_train", "bc_mlp_state", "bc_learned_sweep",
                   "bc_learned_sweep_avg"):
             getattr(L, f).restype = st
@@ -213,6 +219,10 @@ def bc_shape_moments(ctx, shape, out):
     _check(lib().bc_shape_moments(ctx, shape, _ptr(out)))
 
 
+def bc_shape_moments_rot(ctx, shape, quats, n, out):
+    _check(lib().bc_shape_moments_rot(ctx, shape, _ptr(quats), int(n), _ptr(out)))
+
+
 def bc_mlp_param_count(hidden):
     return int(lib().bc_mlp_param_count(int(hidden)))
 
@@ -230,6 +240,18 @@ def bc_mlp_destroy(net):
 
 def bc_mlp_features(net, quats, n, fa, fb, X):
     _check(lib().bc_mlp_features(net, _ptr(quats), int(n), _ptr(fa), _ptr(fb), _ptr(X)))
+
+
+def bc_mlp_features_rows(net, quats, n, fa, fb_rows, X):
+    _check(lib().bc_mlp_features_rows(net, _ptr(quats), int(n), _ptr(fa), _ptr(fb_rows), _ptr(X)))
+
+
+def bc_mlp_set_features(net, rotated_moments):
+    _check(lib().bc_mlp_set_features(net, int(rotated_moments)))
+
+
+def bc_mlp_rotated_moments(net):
+    return int(lib().bc_mlp_rotated_moments(net))
 
 
 def bc_mlp_predict(net, X, n, y):
@@ -523,19 +545,31 @@ class Context:
 class MLP:
     """The learned rotation proposal (132 -> H -> H -> 1) on a context's device and stream."""
 
-    def __init__(self, ctx: Context, hidden: int, init):
+    def __init__(self, ctx: Context, hidden: int, init, rotated_moments=False):
         self.ctx, self.hidden = ctx, int(hidden)
         self.nparams = bc_mlp_param_count(hidden)
         init = np.ascontiguousarray(init, dtype=np.float32).reshape(-1)
         assert init.size == self.nparams
         self.handle = bc_mlp_create(ctx.handle, hidden, init)
         ctx._nets.add(self)
+        if rotated_moments:
+            bc_mlp_set_features(self.handle, 1)
+
+    @property
+    def rotated_moments(self):
+        return bc_mlp_rotated_moments(self.handle) == 1
 
     def features(self, quats_dev, fa, fb):
+        """Feature rows (n x 144): fb is one moment vector (64) for every row, or one per
+        row (n x 64, e.g. moments_rot of the ligand)."""
         import torch
         n = quats_dev.shape[0]
         X = torch.empty((n, 144), dtype=torch.float32, device="cuda")
-        bc_mlp_features(self.handle, quats_dev, n, fa, fb, X)
+        if fb.dim() == 2:
+            assert fb.shape == (n, 64) and fb.is_contiguous()
+            bc_mlp_features_rows(self.handle, quats_dev, n, fa, fb, X)
+        else:
+            bc_mlp_features(self.handle, quats_dev, n, fa, fb, X)
         return X
 
     def predict(self, X):
@@ -588,6 +622,15 @@ def moments(ctx: Context, shape) -> "torch.Tensor":
     import torch
     out = torch.empty(64, dtype=torch.float32, device="cuda")
     bc_shape_moments(ctx.handle, shape.handle, out)
+    return out
+
+
+def moments_rot(ctx: Context, shape, quats_dev) -> "torch.Tensor":
+    """(n, 64) CUDA tensor: the moments of `shape` turned by each of the n device quaternions."""
+    import torch
+    q = quats_dev.contiguous().float()
+    out = torch.empty((q.shape[0], 64), dtype=torch.float32, device="cuda")
+    bc_shape_moments_rot(ctx.handle, shape.handle, q, q.shape[0], out)
     return out
 
 

@@ -345,6 +345,10 @@ bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
             std::vector<int> tab(3 * BC_MOMENTS);
             for (int i = 0; i < BC_MOMENTS; i++)
                 for (int j = 0; j < 3; j++) tab[3 * i + j] = all[i][1 + j];
+            if (!moments_rot_table_matches(tab.data())) {
+                bc_destroy(c);
+                return fail(BC_ERR_INTERNAL, "bc_create: the compiled moment-mode table differs from the context's");
+            }
             if ((e = cudaMalloc(&c->modes, sizeof(int) * tab.size())) != cudaSuccess) return bail(e, "cudaMalloc modes");
             if ((e = cudaMemcpy(c->modes, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
                 return bail(e, "copy modes");
@@ -1433,6 +1437,22 @@ bc_status bc_shape_moments(bc_ctx_t c, bc_shape_t S, float *out)
     }
 }
 
+bc_status bc_shape_moments_rot(bc_ctx_t c, bc_shape_t S, const float *quats, int n, float *out)
+{
+    try {
+        if (!c || !S || !quats || !out) return fail(BC_ERR_ARG, "bc_shape_moments_rot: null argument");
+        if (S->ctx != c) return fail(BC_ERR_ARG, "bc_shape_moments_rot: shape belongs to another context");
+        if (S->n == 0) return fail(BC_ERR_ARG, "bc_shape_moments_rot: empty shape (f(0) = 0)");
+        if (n < 1) return fail(BC_ERR_ARG, "bc_shape_moments_rot: n < 1");
+        cudaError_t e = launch_moments_rot(S->knots, S->n, quats, n, c->ballft, c->qmax + 1, c->g.L,
+                                           (float)(2.0 / c->period), out, c->err_dev, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "moments of rotated shapes");
+        return BC_OK;
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_shape_moments_rot: unexpected exception");
+    }
+}
+
 bc_status bc_topk(bc_ctx_t c, const float *scores, int n, int k, int *idx)
 {
     if (!c || !scores || !idx) return fail(BC_ERR_ARG, "bc_topk: null argument");
@@ -1459,17 +1479,29 @@ bc_status bc_learned_sweep_avg(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_
             if (bc_status s = check_quats(orients, norient, "bc_learned_sweep")) return s;
         cudaStream_t st = c->stream;
         cudaError_t e;
+        const bool rot = bc_mlp_rotated_moments(net) != 0;
         // scratch: moments (2 x 64), features (n x 144), scores (n), score sum (n),
-        // composed rotations (n x 4), selected rotations (topk x 4)
+        // composed rotations (n x 4), selected rotations (topk x 4), and the rotated
+        // ligand's moments (n x 64) when the network takes those
         const size_t fbytes = sizeof(float) * (2 * BC_MOMENTS + (size_t)n * 144 + 2 * (size_t)n + 4 * (size_t)n +
-                                               4 * (size_t)topk);
+                                               4 * (size_t)topk + (rot ? (size_t)n * BC_MOMENTS : 0));
         if ((e = c->learn.ensure(fbytes, false, st)) != cudaSuccess) return cuda_fail(e, "learned scratch");
         float *fa = (float *)c->learn.p, *fb = fa + BC_MOMENTS, *X = fb + BC_MOMENTS;
         float *sc = X + (size_t)n * 144, *acc = sc + n, *qs = acc + n, *qsel = qs + 4 * (size_t)n;
+        float *fbr = qsel + 4 * (size_t)topk;
         float *total = scores ? scores : acc;
+        // features of rotations `q` against the receptor moments in fa
+        auto features = [&](const float *q) -> bc_status {
+            if (!rot) return bc_mlp_features(net, q, n, fa, fb, X);
+            cudaError_t e2 = launch_moments_rot(B->knots, B->n, q, n, c->ballft, c->qmax + 1, c->g.L,
+                                                (float)(2.0 / c->period), fbr, c->err_dev, st);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "moments of the rotated ligand");
+            return bc_mlp_features_rows(net, q, n, fa, fbr, X);
+        };
         if (bc_status s = shape_moments(c, A, nullptr, fa)) return s;
-        if (bc_status s = shape_moments(c, B, nullptr, fb)) return s;
-        if (bc_status s = bc_mlp_features(net, quats, n, fa, fb, X)) return s;
+        if (!rot)
+            if (bc_status s = shape_moments(c, B, nullptr, fb)) return s;
+        if (bc_status s = features(quats)) return s;
         if (bc_status s = bc_mlp_predict(net, X, n, total)) return s;
         // (S A, S R B) has the same peak over translations as (A, R B): score the
         // rotations S R of B against the receptor turned by S, and average
@@ -1477,7 +1509,7 @@ bc_status bc_learned_sweep_avg(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_
             const float *s4 = orients + 4 * (size_t)k;
             if (bc_status s = shape_moments(c, A, s4, fa)) return s;
             if ((e = launch_compose_quats(s4, quats, n, qs, st)) != cudaSuccess) return cuda_fail(e, "compose rotations");
-            if (bc_status s = bc_mlp_features(net, qs, n, fa, fb, X)) return s;
+            if (bc_status s = features(qs)) return s;
             if (bc_status s = bc_mlp_predict(net, X, n, sc)) return s;
             if ((e = launch_axpby(total, sc, n, 1.f, 1.f, st)) != cudaSuccess) return cuda_fail(e, "score sum");
         }

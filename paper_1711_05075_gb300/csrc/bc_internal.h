@@ -179,5 +179,13 @@ cudaError_t launch_compose_quats(const float *sq, const float *q, int n, float *
 cudaError_t launch_axpby(float *y, const float *x, int n, float alpha, float beta, cudaStream_t s);
 // out[i] = |F(m_i)| / F(0) for the modes[i] = (m_x, m_y, m_z), i < count, of a cached half spectrum.
 cudaError_t launch_moments(const float2 *F, const int *modes, int count, int N, int H, float *out, cudaStream_t s);
+// out[r][i] = |f^_S(R_r^T m_i)| / f^_S(0) for the BC_MOMENTS lowest modes m_i and
+// the n rotations R_r of `quats` (device, n x 4), by direct sums over the nk knots
+// (x, y, z, level bits) with the ball transforms ballft[l (qstride) + |m|^2]; a zero
+// quaternion raises bit 4 of *err.
+cudaError_t launch_moments_rot(const float4 *knots, int nk, const float *quats, int n, const float *ballft, int qstride,
+                               int L, float two_over_P, float *out, int *err, cudaStream_t s);
+// Whether the compiled mode table of launch_moments_rot equals `tab` (3 BC_MOMENTS ints).
+bool moments_rot_table_matches(const int *tab);
 
 } // namespace bc

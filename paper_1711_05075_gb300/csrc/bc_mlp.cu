@@ -611,8 +611,9 @@ __global__ void k_adam(float *p, float *m, float *v, const float *__restrict__ g
 }
 
 // x[r] = [q_r / |q_r| with w >= 0; fa; fb; zeros to KPAD]; err |= 4 on a zero quaternion
+// Row r: [q_r / |q_r| (w >= 0); fa; fb + r ldb] (ldb = 0: the same fb for every row).
 __global__ void k_features(const float *__restrict__ q, int n, const float *__restrict__ fa,
-                           const float *__restrict__ fb, float *X, int *err)
+                           const float *__restrict__ fb, long long ldb, float *X, int *err)
 {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)n * KPAD) return;
@@ -631,7 +632,7 @@ __global__ void k_features(const float *__restrict__ q, int n, const float *__re
     } else if (c < 68) {
         v = fa[c - 4];
     } else if (c < KIN) {
-        v = fb[c - 68];
+        v = fb[r * ldb + c - 68];
     }
     X[e] = v;
 }
@@ -717,6 +718,7 @@ struct bc_mlp_s {
     float *xb = nullptr, *tb = nullptr; // a gathered training batch (bc_mlp_train)
     int xb_cap = 0;
     float *loss = nullptr;
+    int rotated_moments = 0;      // the ligand features are the moments of the rotated ligand (bc_mlp_set_features)
 };
 
 namespace {
@@ -846,6 +848,141 @@ cudaError_t bc::launch_moments(const float2 *F, const int *modes, int count, int
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ moments of a rotated shape
+// m_{R S}[i] = |f^_S(R^T m_i)| / f^_S(0) (the moments of S turned by R) by direct
+// sums over the knots, f^_S(k) = sum_i h^(rho_{l_i}, |k|) exp(-2 pi i k . c_i / P)
+// (Eq. (fballhat) without spreading: the band-limited spectrum at off-grid
+// frequencies), for many rotations.  exp(-2 pi i m . R c / P) is the product of
+// u_a^{m_a}, u_a = exp(-i pi (2 / P) (R c)_a): three sincospif per knot, then two
+// complex products per mode.  The mode table is compiled in (the 64 lowest modes
+// are the same for every N >= 8: no component exceeds 3); the context checks it
+// against the one it builds.  One block per rotation: two groups of 128 threads
+// take 32 modes each over all knots (thread j of a group the knots j, j + 128,
+// ...), then warp shuffles and a fixed-order combine of the four warps.
+constexpr int MR_THREADS = 256, MR_GROUP = 32;
+
+// components of mode i offset by 'D' ('A' = -3 .. 'G' = +3), in the order of the table
+__host__ __device__ constexpr int mr_mode(int i, int a)
+{
+    return "CDDDCDDDEDEDEDDCCDCDECEDDCEDEEECDEDEEEDCCECEEECEEEEBDDDBDDDFDFDFDDBCDBDEBEDCBDCDFCFDDBEDCFDEFDFEEBDEDFEFDFCDFDEF"
+           "EDBCEBEECBECCFCEFCFEEBEECFEEFEFEFCEFEEBBDBDFBFDDBFDFFFBDFDFFFDADDBBEBCFBEFBFECBF"[3 * i + a] -
+           'D';
+}
+
+struct Cpx {
+    float x, y;
+};
+__device__ __forceinline__ Cpx cmul(Cpx a, Cpx b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+// u^m for |m| <= 3 from p[0..3] = u^0 .. u^3 (u on the unit circle: u^-m = conj(u^m))
+__device__ __forceinline__ Cpx cpow(const Cpx (&p)[4], int m)
+{
+    const Cpx v = p[m < 0 ? -m : m];
+    return m < 0 ? Cpx{v.x, -v.y} : v;
+}
+
+template <int G>
+__device__ __forceinline__ void mr_sums(const float4 *__restrict__ kn, int nk, int j0, const float (&R)[9],
+                                        float two_over_P, const float *wl, const float *w0, float (&acc)[2 * MR_GROUP],
+                                        float &a0)
+{
+    for (int i = j0; i < nk; i += MR_THREADS / 2) {
+        const float4 c = kn[i];
+        const int l = __float_as_int(c.w);
+        const float p[3] = {fmaf(R[0], c.x, fmaf(R[1], c.y, R[2] * c.z)), fmaf(R[3], c.x, fmaf(R[4], c.y, R[5] * c.z)),
+                            fmaf(R[6], c.x, fmaf(R[7], c.y, R[8] * c.z))};
+        Cpx u[3][4];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            float s, co;
+            sincospif(two_over_P * p[a], &s, &co);
+            u[a][0] = {1.f, 0.f};
+            u[a][1] = {co, -s};
+            u[a][2] = cmul(u[a][1], u[a][1]);
+            u[a][3] = cmul(u[a][2], u[a][1]);
+        }
+        const float *w = wl + l * BC_MOMENTS + G * MR_GROUP;
+#pragma unroll
+        for (int j = 0; j < MR_GROUP; j++) {
+            const int m = G * MR_GROUP + j;
+            const Cpx t = cmul(cmul(cpow(u[0], mr_mode(m, 0)), cpow(u[1], mr_mode(m, 1))), cpow(u[2], mr_mode(m, 2)));
+            acc[2 * j] = fmaf(w[j], t.x, acc[2 * j]);
+            acc[2 * j + 1] = fmaf(w[j], t.y, acc[2 * j + 1]);
+        }
+        if (G == 0) a0 += w0[l];
+    }
+}
+
+__global__ void __launch_bounds__(MR_THREADS) k_moments_rot(const float4 *__restrict__ knots, int nk,
+                                                            const float *__restrict__ quats,
+                                                            const float *__restrict__ ballft, int qstride, int L,
+                                                            float two_over_P, float *out, int *err)
+{
+    __shared__ float wl[BC_MAX_LEVELS * BC_MOMENTS], w0[BC_MAX_LEVELS];
+    __shared__ float red[MR_THREADS / 32][2 * MR_GROUP + 1];
+    const int r = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < L * BC_MOMENTS; e += MR_THREADS) {
+        const int l = e / BC_MOMENTS, i = e - l * BC_MOMENTS;
+        const int mx = mr_mode(i, 0), my = mr_mode(i, 1), mz = mr_mode(i, 2);
+        wl[e] = ballft[(long long)l * qstride + mx * mx + my * my + mz * mz];
+    }
+    if (threadIdx.x < L) w0[threadIdx.x] = ballft[(long long)threadIdx.x * qstride];
+    float qw = quats[4 * r], qx = quats[4 * r + 1], qy = quats[4 * r + 2], qz = quats[4 * r + 3];
+    const float nq = qw * qw + qx * qx + qy * qy + qz * qz;
+    if (!(nq > 0.f)) {
+        if (threadIdx.x == 0) atomicOr(err, 4);
+        qw = 1.f, qx = qy = qz = 0.f;
+    } else {
+        const float s = rsqrtf(nq);
+        qw *= s, qx *= s, qy *= s, qz *= s;
+    }
+    const float R[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                        2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                        2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+    __syncthreads();
+    float acc[2 * MR_GROUP], a0 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2 * MR_GROUP; j++) acc[j] = 0.f;
+    const int G = threadIdx.x / (MR_THREADS / 2), j0 = threadIdx.x % (MR_THREADS / 2);
+    if (G == 0) mr_sums<0>(knots, nk, j0, R, two_over_P, wl, w0, acc, a0);
+    else mr_sums<1>(knots, nk, j0, R, two_over_P, wl, w0, acc, a0);
+#pragma unroll
+    for (int j = 0; j < 2 * MR_GROUP; j++)
+        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+    for (int o = 16; o > 0; o >>= 1) a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < 2 * MR_GROUP; j++) red[warp][j] = acc[j];
+        red[warp][2 * MR_GROUP] = a0;
+    }
+    __syncthreads();
+    if (threadIdx.x < BC_MOMENTS) {
+        const int i = threadIdx.x, g = i / MR_GROUP, j = i - g * MR_GROUP, wpg = MR_THREADS / 64;
+        float re = 0.f, im = 0.f, f0 = 0.f;
+        for (int w = 0; w < wpg; w++) {
+            re += red[g * wpg + w][2 * j];
+            im += red[g * wpg + w][2 * j + 1];
+            f0 += red[w][2 * MR_GROUP];
+        }
+        out[(long long)r * BC_MOMENTS + i] = sqrtf(re * re + im * im) / f0;
+    }
+}
+
+cudaError_t bc::launch_moments_rot(const float4 *knots, int nk, const float *quats, int n, const float *ballft,
+                                   int qstride, int L, float two_over_P, float *out, int *err, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_moments_rot<<<n, MR_THREADS, 0, s>>>(knots, nk, quats, ballft, qstride, L, two_over_P, out, err);
+    return cudaGetLastError();
+}
+
+bool bc::moments_rot_table_matches(const int *tab)
+{
+    for (int i = 0; i < BC_MOMENTS; i++)
+        for (int a = 0; a < 3; a++)
+            if (tab[3 * i + a] != mr_mode(i, a)) return false;
+    return true;
+}
+
 cudaError_t bc::launch_gather_quats(const float *q, const int *idx, int k, float *out, cudaStream_t s)
 {
     if (k <= 0) return cudaSuccess;
@@ -930,15 +1067,37 @@ bc_status bc_mlp_destroy(bc_mlp_t net)
 
 long long bc_mlp_param_count(int hidden) { return offsets(hidden).total; }
 
-bc_status bc_mlp_features(bc_mlp_t net, const float *quats, int n, const float *fa, const float *fb, float *X)
+static bc_status features_impl(bc_mlp_t net, const float *quats, int n, const float *fa, const float *fb,
+                               long long ldb, float *X, const char *who)
 {
-    if (!net || !quats || !fa || !fb || !X || n < 1) return mfail(BC_ERR_ARG, "bc_mlp_features: bad arguments");
-    if (!net->ctx) return mfail(BC_ERR_ARG, "bc_mlp_features: the network's context was destroyed");
+    if (!net || !quats || !fa || !fb || !X || n < 1) return mfail(BC_ERR_ARG, std::string(who) + ": bad arguments");
+    if (!net->ctx) return mfail(BC_ERR_ARG, std::string(who) + ": the network's context was destroyed");
     const long long total = (long long)n * KPAD;
-    k_features<<<(unsigned)((total + 255) / 256), 256, 0, ctx_stream(net->ctx)>>>(quats, n, fa, fb, X, ctx_err(net->ctx));
+    k_features<<<(unsigned)((total + 255) / 256), 256, 0, ctx_stream(net->ctx)>>>(quats, n, fa, fb, ldb, X,
+                                                                                  ctx_err(net->ctx));
     MCK(cudaGetLastError());
     return BC_OK;
 }
+
+bc_status bc_mlp_features(bc_mlp_t net, const float *quats, int n, const float *fa, const float *fb, float *X)
+{
+    return features_impl(net, quats, n, fa, fb, 0, X, "bc_mlp_features");
+}
+
+bc_status bc_mlp_features_rows(bc_mlp_t net, const float *quats, int n, const float *fa, const float *fb_rows, float *X)
+{
+    return features_impl(net, quats, n, fa, fb_rows, BC_MOMENTS, X, "bc_mlp_features_rows");
+}
+
+bc_status bc_mlp_set_features(bc_mlp_t net, int rotated_moments)
+{
+    if (!net || (rotated_moments != 0 && rotated_moments != 1))
+        return mfail(BC_ERR_ARG, "bc_mlp_set_features: null network, or rotated_moments not 0 or 1");
+    net->rotated_moments = rotated_moments;
+    return BC_OK;
+}
+
+int bc_mlp_rotated_moments(bc_mlp_t net) { return net ? net->rotated_moments : 0; }
 
 bc_status bc_mlp_predict(bc_mlp_t net, const float *X, int n, float *y)
 {

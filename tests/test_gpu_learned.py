@@ -3,7 +3,8 @@ gains over ranking rotations without it, and the multi-step training call.
 
 Training labels come from the batched sweep with the binned spreading, whose
 sums are order-independent fixed point, so the labels -- and with the
-deterministic training the network -- are the same on every run.  The gain is
+deterministic training the network -- are the same on every run.  The network
+takes the moments of the ligand turned by each rotation.  The gain is
 measured on held-out receptor/ligand pairs against a random choice of the same
 number of rotations (the method without a network must correlate rotations it
 cannot rank: a random subset is the fair baseline for a fixed budget of full
@@ -54,14 +55,14 @@ def labelled(bc, ctx, net, seeds, nrot, augment, dev):
         q = synth.shoemake_quaternions(synth.SplitMix64(seed + 100), nrot).astype(np.float32)
         peak, _ = ctx.sweep(hA, hB, q, batch=128)
         z = (peak - peak.mean()) / peak.std()
-        fa, fb = bc.moments(ctx, hA), bc.moments(ctx, hB)
-        Xs.append(net.features(torch.tensor(q, device=dev), fa, fb))
+        qd = torch.tensor(q, device=dev)
+        Xs.append(net.features(qd, bc.moments(ctx, hA), bc.moments_rot(ctx, hB, qd)))
         ts.append(z)
         # (S A, S R B) has the peak of (A, R B): the same labels for turned receptors
         for s_q in synth.shoemake_quaternions(synth.SplitMix64(seed + 200), augment):
             hS = ctx.shape(synth.rotate_points(A.xyz, s_q), A.level)
-            qs = synth.compose_quaternions(s_q, q).astype(np.float32)
-            Xs.append(net.features(torch.tensor(qs, device=dev), bc.moments(ctx, hS), fb))
+            qs = torch.tensor(synth.compose_quaternions(s_q, q).astype(np.float32), device=dev)
+            Xs.append(net.features(qs, bc.moments(ctx, hS), bc.moments_rot(ctx, hB, qs)))
             ts.append(z)
             hS.close()
         hA.close()
@@ -74,7 +75,7 @@ def test_trained_network_beats_random_choice_on_held_out_pairs(bc):
     N, W, H, K = 32, 6, 64, 64
     ctx = bc.Context(N, W, synth.RADII_4)
     ctx.set_tuning(spread=1)  # fixed-point spreading sums: bit-reproducible labels
-    net = bc.MLP(ctx, H, synth.mlp_init(H, 3))
+    net = bc.MLP(ctx, H, synth.mlp_init(H, 3), rotated_moments=True)
     X, T = labelled(bc, ctx, net, range(1, 9), 1024, 8, dev)
     X2, T2 = labelled(bc, ctx, net, range(1, 9), 1024, 8, dev)
     assert torch.equal(X, X2) and torch.equal(T, T2)  # the labels are reproducible

@@ -1,6 +1,6 @@
 """GPU learned proposal: forward, gradients and Adam against the FP64 MLP oracle
-(BF16 rounding emulated where the GPU rounds), moment features against the
-spectrum oracle, top-k against a stable sort, checkpoint/resume, and the
+(BF16 rounding emulated where the GPU rounds), moment features (of the shapes
+as given and turned by rotations) against the spectrum oracle, top-k against a stable sort, checkpoint/resume, and the
 learned sweep against the plain sweep of the same rotations."""
 import ctypes
 
@@ -155,6 +155,74 @@ def test_moments_match_oracle(bc):
         np.testing.assert_allclose(got, ref, rtol=5e-5, atol=1e-7)
         h.close()
     ctx.close()
+
+
+def test_rotated_moments_match_oracle(bc):
+    # |f^_B(R^T m)| / f^_B(0) by direct sums on the device against the oracle's
+    # spectrum of the turned shape (layer (b)), for the identity, random rotations,
+    # an unnormalised quaternion and one with w < 0; a zero quaternion is reported.
+    wl = synth.small_pair(2)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    qs = np.concatenate([[[1.0, 0, 0, 0]], synth.shoemake_quaternions(synth.SplitMix64(21), 5),
+                         [[0.0, 3.0, -4.0, 0.0], [-0.5, 0.5, 0.5, 0.5]]]).astype(np.float32)
+    for S in (wl.A, wl.B):
+        h = ctx.shape(S.xyz, S.level)
+        got = bc.moments_rot(ctx, h, torch.tensor(qs, device="cuda")).cpu().numpy()
+        ctx.sync()
+        for r, q in enumerate(qs):
+            spec = O.shape_spectrum(S.xyz.astype(np.float32).astype(np.float64), S.level, S.radii, wl.N,
+                                    q=q.astype(np.float64))
+            ref = M.moments(spec, M.moment_modes(wl.N))
+            np.testing.assert_allclose(got[r], ref, rtol=2e-5, atol=2e-6)
+        # the identity row is the pipeline's moments of the shape as given
+        np.testing.assert_allclose(got[0], bc.moments(ctx, h).cpu().numpy(), rtol=5e-5, atol=1e-6)
+        h.close()
+    h = ctx.shape(wl.B.xyz, wl.B.level)
+    bc.moments_rot(ctx, h, torch.zeros((2, 4), device="cuda"))
+    with pytest.raises(bc.BallCorrError) as e:
+        ctx.sync()
+    assert e.value.status == 1
+    ctx.sync()  # the word is cleared; the context stays usable
+    h.close()
+    ctx.close()
+
+
+def test_learned_sweep_with_rotated_ligand_moments(bc):
+    # a network set to take the rotated ligand's moments: the sweep's scores are the
+    # network's predictions on [q, m_A, m_{R B}] built from moments_rot, with and
+    # without orientation averaging (S A against S R B)
+    wl = synth.small_pair(7)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    A, B = ctx.shape(wl.A.xyz, wl.A.level), ctx.shape(wl.B.xyz, wl.B.level)
+    net = bc.MLP(ctx, 64, synth.mlp_init(64, 9), rotated_moments=True)
+    assert net.rotated_moments
+    qn = synth.shoemake_quaternions(synth.SplitMix64(4), 2000).astype(np.float32)
+    q = torch.tensor(qn, device="cuda")
+    idx, peak, arg, scores = bc.learned_sweep(ctx, net, A, B, q, 32)
+    fa = bc.moments(ctx, A)
+    ref = net.predict(net.features(q, fa, bc.moments_rot(ctx, B, q))).cpu().numpy()
+    np.testing.assert_allclose(scores.cpu().numpy(), ref, rtol=1e-6, atol=1e-7)
+    S = synth.shoemake_quaternions(synth.SplitMix64(11), 2)
+    _, _, _, s_avg = bc.learned_sweep(ctx, net, A, B, q, 32, orientations=S.astype(np.float32))
+    per = [ref]
+    for s_q in S:
+        hS = ctx.shape(synth.rotate_points(wl.A.xyz, s_q), wl.A.level)
+        qs = torch.tensor(synth.compose_quaternions(s_q, qn).astype(np.float32), device="cuda")
+        per.append(net.predict(net.features(qs, bc.moments(ctx, hS), bc.moments_rot(ctx, B, qs))).cpu().numpy())
+        hS.close()
+    # The rotations S R are composed in FP32 on the device here and in FP64 on the
+    # host above, and the turned receptor's moments come from spectra whose
+    # spreading sums round in a run-dependent order: features that differ in the
+    # last bits, which the BF16 rounding of the network's inputs turns into steps
+    # of about 2^-8 of a feature for the few that straddle a rounding boundary.
+    ref_avg = np.mean(per, axis=0)
+    d = np.abs(s_avg.cpu().numpy() - ref_avg)
+    assert np.mean(d <= 1e-5 + 1e-4 * np.abs(ref_avg)) >= 0.99
+    assert d.max() <= 5e-3 * np.abs(ref_avg).max()
+    sel = qn[idx.cpu().numpy()]
+    p2, _ = ctx.sweep(A, B, sel)
+    np.testing.assert_allclose(peak.cpu().numpy(), p2.cpu().numpy(), rtol=1e-5)
+    net.close(); A.close(); B.close(); ctx.close()
 
 
 def test_topk_is_a_stable_descending_selection(bc):
