@@ -883,7 +883,7 @@ def main():
     ap.add_argument("--eval-pairs", type=int, default=20)
     ap.add_argument("--eval-rot", type=int, default=16384)
     ap.add_argument("--topk", type=int, default=256)
-    ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--epochs", type=int, default=120)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--refine", type=int, default=0,

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -880,10 +881,54 @@ __device__ __forceinline__ Cpx cpow(const Cpx (&p)[4], int m)
     return m < 0 ? Cpx{v.x, -v.y} : v;
 }
 
+// the earlier mode -m_i of the table, or -1 (|f^(-m)| = |f^(m)| for a real density,
+// so such a mode is not summed but copied)
+__host__ __device__ constexpr int mr_twin(int i)
+{
+    for (int j = 0; j < i; j++)
+        if (mr_mode(j, 0) == -mr_mode(i, 0) && mr_mode(j, 1) == -mr_mode(i, 1) && mr_mode(j, 2) == -mr_mode(i, 2))
+            return j;
+    return -1;
+}
+
+constexpr int MR_SHELLS = 10; // |m|^2 <= 9 over the table
+
+// exp(-2 pi i m . p / P) from the per-axis powers, skipping the zero components
+template <int MX, int MY, int MZ>
+__device__ __forceinline__ Cpx mr_phase(const Cpx (&u)[3][4])
+{
+    if constexpr (MX != 0 && MY != 0 && MZ != 0) return cmul(cmul(cpow(u[0], MX), cpow(u[1], MY)), cpow(u[2], MZ));
+    else if constexpr (MX != 0 && MY != 0) return cmul(cpow(u[0], MX), cpow(u[1], MY));
+    else if constexpr (MX != 0 && MZ != 0) return cmul(cpow(u[0], MX), cpow(u[2], MZ));
+    else if constexpr (MY != 0 && MZ != 0) return cmul(cpow(u[1], MY), cpow(u[2], MZ));
+    else if constexpr (MX != 0) return cpow(u[0], MX);
+    else if constexpr (MY != 0) return cpow(u[1], MY);
+    else return cpow(u[2], MZ);
+}
+
+// acc[2 j], acc[2 j + 1] += h^(rho_l, |m|) exp(-2 pi i m . p / P) for mode m = M (j = M mod 32)
+template <int M>
+__device__ __forceinline__ void mr_term(const Cpx (&u)[3][4], const float *wq, float (&acc)[2 * MR_GROUP])
+{
+    if constexpr (mr_twin(M) < 0) {
+        constexpr int mx = mr_mode(M, 0), my = mr_mode(M, 1), mz = mr_mode(M, 2), j = M % MR_GROUP;
+        const Cpx t = mr_phase<mx, my, mz>(u);
+        const float w = wq[mx * mx + my * my + mz * mz];
+        acc[2 * j] = fmaf(w, t.x, acc[2 * j]);
+        acc[2 * j + 1] = fmaf(w, t.y, acc[2 * j + 1]);
+    }
+}
+
+template <int G, int... J>
+__device__ __forceinline__ void mr_terms(std::integer_sequence<int, J...>, const Cpx (&u)[3][4], const float *wq,
+                                         float (&acc)[2 * MR_GROUP])
+{
+    (mr_term<G * MR_GROUP + J>(u, wq, acc), ...);
+}
+
 template <int G>
 __device__ __forceinline__ void mr_sums(const float4 *__restrict__ kn, int nk, int j0, const float (&R)[9],
-                                        float two_over_P, const float *wl, const float *w0, float (&acc)[2 * MR_GROUP],
-                                        float &a0)
+                                        float two_over_P, const float *wq_all, float (&acc)[2 * MR_GROUP], float &a0)
 {
     for (int i = j0; i < nk; i += MR_THREADS / 2) {
         const float4 c = kn[i];
@@ -900,15 +945,9 @@ __device__ __forceinline__ void mr_sums(const float4 *__restrict__ kn, int nk, i
             u[a][2] = cmul(u[a][1], u[a][1]);
             u[a][3] = cmul(u[a][2], u[a][1]);
         }
-        const float *w = wl + l * BC_MOMENTS + G * MR_GROUP;
-#pragma unroll
-        for (int j = 0; j < MR_GROUP; j++) {
-            const int m = G * MR_GROUP + j;
-            const Cpx t = cmul(cmul(cpow(u[0], mr_mode(m, 0)), cpow(u[1], mr_mode(m, 1))), cpow(u[2], mr_mode(m, 2)));
-            acc[2 * j] = fmaf(w[j], t.x, acc[2 * j]);
-            acc[2 * j + 1] = fmaf(w[j], t.y, acc[2 * j + 1]);
-        }
-        if (G == 0) a0 += w0[l];
+        const float *wq = wq_all + l * MR_SHELLS; // h^(rho_l, 2 pi sqrt(q) / P), q = |m|^2
+        mr_terms<G>(std::make_integer_sequence<int, MR_GROUP>{}, u, wq, acc);
+        if (G == 0) a0 += wq[0];
     }
 }
 
@@ -917,15 +956,13 @@ __global__ void __launch_bounds__(MR_THREADS) k_moments_rot(const float4 *__rest
                                                             const float *__restrict__ ballft, int qstride, int L,
                                                             float two_over_P, float *out, int *err)
 {
-    __shared__ float wl[BC_MAX_LEVELS * BC_MOMENTS], w0[BC_MAX_LEVELS];
+    __shared__ float wq[BC_MAX_LEVELS * MR_SHELLS];
     __shared__ float red[MR_THREADS / 32][2 * MR_GROUP + 1];
     const int r = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int e = threadIdx.x; e < L * BC_MOMENTS; e += MR_THREADS) {
-        const int l = e / BC_MOMENTS, i = e - l * BC_MOMENTS;
-        const int mx = mr_mode(i, 0), my = mr_mode(i, 1), mz = mr_mode(i, 2);
-        wl[e] = ballft[(long long)l * qstride + mx * mx + my * my + mz * mz];
+    for (int e = threadIdx.x; e < L * MR_SHELLS; e += MR_THREADS) {
+        const int l = e / MR_SHELLS, q = e - l * MR_SHELLS;
+        wq[e] = q < qstride ? ballft[(long long)l * qstride + q] : 0.f;
     }
-    if (threadIdx.x < L) w0[threadIdx.x] = ballft[(long long)threadIdx.x * qstride];
     float qw = quats[4 * r], qx = quats[4 * r + 1], qy = quats[4 * r + 2], qz = quats[4 * r + 3];
     const float nq = qw * qw + qx * qx + qy * qy + qz * qz;
     if (!(nq > 0.f)) {
@@ -943,8 +980,8 @@ __global__ void __launch_bounds__(MR_THREADS) k_moments_rot(const float4 *__rest
 #pragma unroll
     for (int j = 0; j < 2 * MR_GROUP; j++) acc[j] = 0.f;
     const int G = threadIdx.x / (MR_THREADS / 2), j0 = threadIdx.x % (MR_THREADS / 2);
-    if (G == 0) mr_sums<0>(knots, nk, j0, R, two_over_P, wl, w0, acc, a0);
-    else mr_sums<1>(knots, nk, j0, R, two_over_P, wl, w0, acc, a0);
+    if (G == 0) mr_sums<0>(knots, nk, j0, R, two_over_P, wq, acc, a0);
+    else mr_sums<1>(knots, nk, j0, R, two_over_P, wq, acc, a0);
 #pragma unroll
     for (int j = 0; j < 2 * MR_GROUP; j++)
         for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
@@ -956,14 +993,21 @@ __global__ void __launch_bounds__(MR_THREADS) k_moments_rot(const float4 *__rest
     }
     __syncthreads();
     if (threadIdx.x < BC_MOMENTS) {
-        const int i = threadIdx.x, g = i / MR_GROUP, j = i - g * MR_GROUP, wpg = MR_THREADS / 64;
+        int i = threadIdx.x;
+        // a mode whose negation comes earlier takes that one's sum (|f^(-m)| = |f^(m)|)
+        for (int t = 0; t < i; t++)
+            if (mr_mode(t, 0) == -mr_mode(i, 0) && mr_mode(t, 1) == -mr_mode(i, 1) && mr_mode(t, 2) == -mr_mode(i, 2)) {
+                i = t;
+                break;
+            }
+        const int g = i / MR_GROUP, j = i - g * MR_GROUP, wpg = MR_THREADS / 64;
         float re = 0.f, im = 0.f, f0 = 0.f;
         for (int w = 0; w < wpg; w++) {
             re += red[g * wpg + w][2 * j];
             im += red[g * wpg + w][2 * j + 1];
             f0 += red[w][2 * MR_GROUP];
         }
-        out[(long long)r * BC_MOMENTS + i] = sqrtf(re * re + im * im) / f0;
+        out[(long long)r * BC_MOMENTS + threadIdx.x] = sqrtf(re * re + im * im) / f0;
     }
 }
 
