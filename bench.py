@@ -618,6 +618,78 @@ def run_split(args):
     return 0
 
 
+# ------------------------------------------------------------------ network training
+def run_train(args):
+    """Training rate of the rotation-proposal network at the learned workload's size
+    (132 -> 256 -> 256 -> 1, batches of 8,192): `steps` passes over 16 batches in one
+    bc_mlp_train call (Adam steps gathered, products and updates all on the device), and
+    the forward pass alone over 131,072 rows.  Roofline: the products' flops per Adam step
+    against the measured dense BF16 tensor peak."""
+    import torch
+    import paper_1711_05075_gb300 as bc
+    from paper_1711_05075_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    H, B, nb, IN = 256, 8192, 16, 132
+    n = B * nb
+    ctx = bc.Context(32, 6, synth.RADII_2, stream=stream)
+    net = bc.MLP(ctx, H, synth.mlp_init(H, 3))
+    rng = synth.SplitMix64(1)
+    q = torch.tensor(synth.shoemake_quaternions(rng, n).astype(np.float32), device=dev)
+    fa = torch.tensor(rng.uniform(64).astype(np.float32), device=dev)
+    fb = torch.tensor(rng.uniform(n * 64).astype(np.float32).reshape(n, 64), device=dev)
+    X = net.features(q, fa, fb)
+    T = torch.tensor(rng.uniform(n).astype(np.float32), device=dev)
+    y = torch.empty(n, device=dev)
+    net.train(X, T, max(args.warmup, 1), B, 1e-4, seed=3)
+    for _ in range(3):
+        net.predict(X)
+    torch.cuda.synchronize(dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    sampler = ClockSampler(0)
+    sampler.start()
+    e[0].record(stream)
+    net.train(X, T, args.steps, B, 1e-4, seed=4)
+    e[1].record(stream)
+    for _ in range(args.steps):
+        bc.bc_mlp_predict(net.handle, X, n, y)
+    e[2].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ctx.sync()
+    steps = args.steps * nb
+    ms_step = e[0].elapsed_time(e[1]) / steps
+    ms_fwd = e[1].elapsed_time(e[2]) / args.steps
+    # products per Adam step: h1, h2 forward; dW2, dh1, [dW1 | db1] backward (2 flops per MAC)
+    flops_step = 2.0 * B * (IN * H + H * H) + 2.0 * B * (2 * H * H + (IN + 1) * H)
+    flops_fwd = 2.0 * n * (IN * H + H * H + H)
+    peak_tf, peak_kind = load_tensor_peak()
+    achieved = flops_step / (ms_step * 1e-3) / 1e12
+    line = {"metric": "MLP training (Adam steps of 8,192 samples per second)", "workload": "network training",
+            "value": 1e3 / ms_step, "unit": "steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "dtype": "bf16 x bf16 -> f32 (tcgen05), f32 master weights",
+            "data": "synthetic", "config": {"hidden": H, "batch": B, "samples": n, "in_features": 132},
+            "forward_rows_per_s": n / (ms_fwd * 1e-3), "forward_ms_per_131072_rows": ms_fwd,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": achieved / peak_tf, "traffic": None,
+                         "note": f"peak {peak_kind} (dense BF16); achieved = the products' flops per Adam step "
+                                 f"({flops_step / 1e9:.2f} GFLOP) / ms per step (all kernels of the step)"},
+            "forward_tflops": flops_fwd / (ms_fwd * 1e-3) / 1e12, "clocks": clocks}
+    net.close()
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def load_tensor_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured burst"
+    return 1900.0, "fallback"
+
+
 # ------------------------------------------------------------------ learned proposal
 def run_learned(args):
     """The learned-proposal study (learned_study) as its own JSON line."""
@@ -870,9 +942,10 @@ def main():
                     help="grid size of the --profile-correlations workload (the 20k+20k-ball pair)")
     ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1],
                     help="precision of the --profile-correlations context (1: split BF16 stages)")
-    ap.add_argument("--workload", choices=["scale", "learned", "score", "query", "lifted", "split"], default="scale",
+    ap.add_argument("--workload", choices=["scale", "learned", "score", "query", "lifted", "split", "train"],
+                    default="scale",
                     help="scale: the 20k+20k-ball N=128 correlation (default); learned: the rotation-proposal "
-                         "study; score: the complementarity score of the same pair; query: truncated "
+                         "study; train: the network's training rate; score: the complementarity score of the same pair; query: truncated "
                          "single-configuration queries of the same pair; lifted: the 4D nonequiradius "
                          "correlation; split: the split-precision path beside FP32 at N = 256")
     ap.add_argument("--lift-n", type=int, default=32)
@@ -920,6 +993,8 @@ def main():
         return run_query(args)
     if args.workload == "lifted":
         return run_lifted(args)
+    if args.workload == "train":
+        return run_train(args)
     if args.workload == "split":
         return run_split(args)
     if args.profile_correlations > 0:
