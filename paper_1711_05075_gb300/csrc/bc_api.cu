@@ -138,6 +138,10 @@ struct Workspace {
 struct bc_ctx_s {
     int device = 0;
     cudaStream_t stream = nullptr;
+    // stream-ordered pool for the shapes' knot arrays and upload staging, keeping
+    // its memory between uploads (the default pool hands it back at every
+    // synchronisation, and mapping it again costs more than the upload itself)
+    cudaMemPool_t pool = nullptr;
     int nsm = 1;
     Geometry g{};
     double beta = 0, period = 2.0;
@@ -353,6 +357,16 @@ bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
             if ((e = cudaMemcpy(c->modes, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
                 return bail(e, "copy modes");
         }
+        {
+            cudaMemPoolProps pp{};
+            pp.allocType = cudaMemAllocationTypePinned;
+            pp.location.type = cudaMemLocationTypeDevice;
+            pp.location.id = c->device;
+            if ((e = cudaMemPoolCreate(&c->pool, &pp)) != cudaSuccess) return bail(e, "cudaMemPoolCreate");
+            unsigned long long keep = ~0ull; // never trim at synchronisation (freed at bc_destroy)
+            if ((e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess)
+                return bail(e, "pool release threshold");
+        }
         if ((e = cudaMalloc(&c->err_dev, sizeof(int))) != cudaSuccess) return bail(e, "cudaMalloc err");
         if ((e = cudaMallocHost(&c->pin, sizeof(int))) != cudaSuccess) return bail(e, "cudaMallocHost");
         *c->pin = 0;
@@ -395,11 +409,13 @@ bc_status bc_destroy(bc_ctx_t c)
         cudaFree(c->zdft);
         prof_free(c);
         for (bc_shape_s *s : c->shapes) {
-            if (s->knots) cudaFree(s->knots);
+            if (s->knots) cudaFreeAsync(s->knots, c->stream);
             s->knots = nullptr;
             s->ctx = nullptr;
         }
         c->shapes.clear();
+        cudaStreamSynchronize(c->stream);
+        if (c->pool) cudaMemPoolDestroy(c->pool);
         for (bc_mlp_s *net : c->nets) mlp_orphan(net);
         c->nets.clear();
         for (bc_query_s *q : c->queries) {
@@ -488,7 +504,8 @@ bc_status bc_shapes_create(bc_ctx_t c, int count, const float *const *xyz, const
             made[i]->n = n[i];
         }
         cudaError_t e;
-        if (staged && (e = cudaMallocAsync(&staging, staged, st)) != cudaSuccess) return bail(e, "cudaMallocAsync staging");
+        if (staged && (e = cudaMallocFromPoolAsync(&staging, staged, c->pool, st)) != cudaSuccess)
+            return bail(e, "cudaMallocAsync staging");
         if ((e = c->stats.ensure(2 * sizeof(unsigned int) * (size_t)(count > 0 ? count : 1), false, st)) != cudaSuccess)
             return bail(e, "stats");
         if ((e = c->hstats.ensure(2 * sizeof(unsigned int) * (size_t)(count > 0 ? count : 1))) != cudaSuccess)
@@ -501,7 +518,7 @@ bc_status bc_shapes_create(bc_ctx_t c, int count, const float *const *xyz, const
             const int ni = n[i];
             if (ni == 0) continue;
             bc_shape_t s = made[i];
-            if ((e = cudaMallocAsync((void **)&s->knots, sizeof(float4) * ni, st)) != cudaSuccess)
+            if ((e = cudaMallocFromPoolAsync((void **)&s->knots, sizeof(float4) * ni, c->pool, st)) != cudaSuccess)
                 return bail(e, "cudaMallocAsync knots");
             const float *dx = xyz[i];
             const int *dl = level[i];
