@@ -4,7 +4,8 @@ gains over ranking rotations without it, and the multi-step training call.
 Training labels come from the batched sweep with the binned spreading, whose
 sums are order-independent fixed point, so the labels -- and with the
 deterministic training the network -- are the same on every run.  The network
-takes the moments of the ligand turned by each rotation.  The gain is
+takes the moments of the ligand as given or, in the second case, turned by
+each rotation.  The gain is
 measured on held-out receptor/ligand pairs against a random choice of the same
 number of rotations (the method without a network must correlate rotations it
 cannot rank: a random subset is the fair baseline for a fixed budget of full
@@ -47,7 +48,10 @@ def spearman(a, b):
     return float((ra * rb).sum() / np.sqrt((ra * ra).sum() * (rb * rb).sum()))
 
 
-def labelled(bc, ctx, net, seeds, nrot, augment, dev):
+def labelled(bc, ctx, net, seeds, nrot, augment, dev, rotated):
+    def ligand(hB, qd, fb):
+        return bc.moments_rot(ctx, hB, qd) if rotated else fb
+
     Xs, ts = [], []
     for seed in seeds:
         A, B = pair(seed)
@@ -56,13 +60,14 @@ def labelled(bc, ctx, net, seeds, nrot, augment, dev):
         peak, _ = ctx.sweep(hA, hB, q, batch=128)
         z = (peak - peak.mean()) / peak.std()
         qd = torch.tensor(q, device=dev)
-        Xs.append(net.features(qd, bc.moments(ctx, hA), bc.moments_rot(ctx, hB, qd)))
+        fb = bc.moments(ctx, hB)
+        Xs.append(net.features(qd, bc.moments(ctx, hA), ligand(hB, qd, fb)))
         ts.append(z)
         # (S A, S R B) has the peak of (A, R B): the same labels for turned receptors
         for s_q in synth.shoemake_quaternions(synth.SplitMix64(seed + 200), augment):
             hS = ctx.shape(synth.rotate_points(A.xyz, s_q), A.level)
             qs = torch.tensor(synth.compose_quaternions(s_q, q).astype(np.float32), device=dev)
-            Xs.append(net.features(qs, bc.moments(ctx, hS), bc.moments_rot(ctx, hB, qs)))
+            Xs.append(net.features(qs, bc.moments(ctx, hS), ligand(hB, qs, fb)))
             ts.append(z)
             hS.close()
         hA.close()
@@ -70,14 +75,16 @@ def labelled(bc, ctx, net, seeds, nrot, augment, dev):
     return torch.cat(Xs).contiguous(), torch.cat(ts).contiguous()
 
 
-def test_trained_network_beats_random_choice_on_held_out_pairs(bc):
+# the ligand's moments as given (the same for every rotation) or turned by each rotation
+@pytest.mark.parametrize("rotated", [False, True])
+def test_trained_network_beats_random_choice_on_held_out_pairs(bc, rotated):
     dev = torch.device("cuda", 0)
     N, W, H, K = 32, 6, 64, 64
     ctx = bc.Context(N, W, synth.RADII_4)
     ctx.set_tuning(spread=1)  # fixed-point spreading sums: bit-reproducible labels
-    net = bc.MLP(ctx, H, synth.mlp_init(H, 3), rotated_moments=True)
-    X, T = labelled(bc, ctx, net, range(1, 9), 1024, 8, dev)
-    X2, T2 = labelled(bc, ctx, net, range(1, 9), 1024, 8, dev)
+    net = bc.MLP(ctx, H, synth.mlp_init(H, 3), rotated_moments=rotated)
+    X, T = labelled(bc, ctx, net, range(1, 9), 1024, 8, dev, rotated)
+    X2, T2 = labelled(bc, ctx, net, range(1, 9), 1024, 8, dev, rotated)
     assert torch.equal(X, X2) and torch.equal(T, T2)  # the labels are reproducible
     loss = torch.empty(1, device=dev)
     net.train(X, T, epochs=40, batch=1024, lr=3e-3, seed=5, loss=loss)
