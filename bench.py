@@ -749,16 +749,17 @@ def learned_study(args):
         for v in variants:
             Xs[v].append(feats(v, qd, fa, hB, fb))
         ts.append(z)
-        # rotation augmentation: (S A, S R B) has the same peak over translations as (A, R B)
-        rng_aug = synth.SplitMix64(seed + 500000)
-        for s_q in synth.shoemake_quaternions(rng_aug, args.augment):
-            hS = ctx.shape(synth.rotate_points(A.xyz, s_q), A.level)
+        # rotation augmentation: (S A, S R B) has the same peak over translations as (A, R B);
+        # the turned receptors' moments by direct sums, all orientations of the pair in one launch
+        S_aug = synth.shoemake_quaternions(synth.SplitMix64(seed + 500000), args.augment)
+        if args.augment > 0:
+            fS_all = bc.moments_rot(ctx, hA, torch.tensor(S_aug.astype(np.float32), device=dev))
+        for k, s_q in enumerate(S_aug):
             qs = torch.tensor(synth.compose_quaternions(s_q, q).astype(np.float32), device=dev)
-            fS = bc.moments(ctx, hS)
+            fS = fS_all[k].contiguous()
             for v in variants:
                 Xs[v].append(feats(v, qs, fS, hB, fb))
             ts.append(z)
-            hS.close()
         hA.close()
         hB.close()
     T = torch.cat(ts).contiguous()
@@ -784,7 +785,8 @@ def learned_study(args):
     # ---- held-out evaluation
     K, R = args.topk, args.eval_rot
     Mv = {v: {"hits": 0, "hits_tol": 0, "regrets": [], "test_mse": [], "ms_learn": [], "hits_tta": 0,
-              "hits_tta_tol": 0, "ms_tta": [], "hits_ref": 0, "hits_ref_tol": 0, "ms_ref": []} for v in variants}
+              "hits_tta_tol": 0, "ms_tta": [], "hits_ref": 0, "hits_ref_tol": 0, "ms_ref": [],
+              "hits_cas": 0, "hits_cas_tol": 0, "ms_cas": []} for v in variants}
     rand_hits, ms_ex, near3, near4 = 0, [], [], []
     orients = synth.shoemake_quaternions(synth.SplitMix64(600000), args.tta).astype(np.float32) if args.tta > 0 else None
     for seed in range(1001, 1001 + args.eval_pairs):
@@ -839,6 +841,16 @@ def learned_study(args):
                 m["ms_tta"].append(e3.elapsed_time(e4))
                 m["hits_tta"] += best in set(it_.cpu().numpy().tolist())
                 m["hits_tta_tol"] += float(pt_.max()) >= p[best] * (1 - 1e-3)
+            if args.tta > 0 and 0 < args.cascade_keep < R:
+                # the same views for the one-view top cascade_keep only (bc_learned_sweep_cascade)
+                e3, e4 = ev(), ev()
+                e3.record(stream)
+                ic_, pc_, _, _ = bc.learned_sweep(ctx, net, hA, hB, qd, K, orientations=orients, keep=args.cascade_keep)
+                e4.record(stream)
+                torch.cuda.synchronize(dev)
+                m["ms_cas"].append(e3.elapsed_time(e4))
+                m["hits_cas"] += best in set(ic_.cpu().numpy().tolist())
+                m["hits_cas_tol"] += float(pc_.max()) >= p[best] * (1 - 1e-3)
             if args.refine > 0:
                 # two stages within the same K full correlations: the network's top K - refine, then
                 # the nearest rotations (largest |q . q'|) of the best peaks found, round robin
@@ -912,6 +924,11 @@ def learned_study(args):
                                       "effective_poses_s": poses / (np.mean(m["ms_tta"]) * 1e-3),
                                       "vs_plain": poses / (np.mean(m["ms_tta"]) * 1e-3) / plain}
             if args.tta > 0 else None,
+            "cascade": {"orientations": args.tta, "keep": args.cascade_keep, "recall_best": m["hits_cas"] / E,
+                        "recall_within_1e-3": m["hits_cas_tol"] / E, "ms_learned_sweep": float(np.mean(m["ms_cas"])),
+                        "effective_poses_s": poses / (np.mean(m["ms_cas"]) * 1e-3),
+                        "vs_plain": poses / (np.mean(m["ms_cas"]) * 1e-3) / plain}
+            if m["ms_cas"] else None,
             "mean_peak_ratio_topk_over_best": float(np.mean(m["regrets"])),
             "min_peak_ratio_topk_over_best": float(np.min(m["regrets"])),
             "ms_learned_sweep": float(np.mean(m["ms_learn"])),
@@ -999,6 +1016,9 @@ def main():
                     help="learned workload: also rank by scores averaged over this many random receptor orientations")
     ap.add_argument("--target-alpha", type=float, default=0.0,
                     help="train on exp(alpha (z - 3)) of the standardised peak z instead of z (0: z)")
+    ap.add_argument("--cascade-keep", type=int, default=2048,
+                    help="learned sweep in two stages: the one-view best this many get the orientation average "
+                         "(0: off)")
     ap.add_argument("--ligand-moments", choices=("both", "fixed", "rotated"), default="both",
                     help="the network's ligand features: the moments of the ligand as given (fixed, the main "
                          "figures), of the ligand turned by each rotation (rotated), or both networks on the "

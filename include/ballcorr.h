@@ -446,6 +446,24 @@ bc_status bc_learned_sweep_avg(bc_ctx_t ctx, bc_mlp_t net, bc_shape_t A, bc_shap
                                int topk, const float *orients, int norient, int *idx, float *peak, int *argmax,
                                float *scores);
 
+/* Learned sweep in two stages: the network scores all n rotations with one view
+ * (the receptor as given) and keeps the best `keep`; those are scored again
+ * against the receptor turned by each of the norient host orientations s_k
+ * (as in bc_learned_sweep_avg), the mean of the (norient + 1) views ranks them,
+ * and the topk best get full correlations as bc_sweep computes them.  The
+ * turned receptor's moments come from direct sums over its knots
+ * (bc_shape_moments_rot, all orientations in one launch), not from its
+ * spectrum.  Outputs (device): idx[topk] (indices into quats, best first;
+ * ties to the lower index), peak[topk], argmax[topk], and scores[n] (the
+ * one-view scores) when not NULL.  keep = n and the same orientations rank as
+ * bc_learned_sweep_avg would with those moments.  Asynchronous.  Errors:
+ * BC_ERR_ARG (null pointer, n outside [1, BC_TOPK_MAX], keep outside [1, n],
+ * topk outside [1, keep], norient < 0, orientations missing, a zero
+ * orientation quaternion, an empty or foreign shape), BC_ERR_CUDA. */
+bc_status bc_learned_sweep_cascade(bc_ctx_t ctx, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
+                                   int topk, const float *orients, int norient, int keep, int *idx, float *peak,
+                                   int *argmax, float *scores);
+
 /* Top-k selection: idx[0..k) (device) = indices of the k largest of scores[0..n)
  * (device), largest first, equal scores ordered by lower index.  n <= BC_TOPK_MAX.
  * Asynchronous on ctx's stream.  Errors: BC_ERR_ARG, BC_ERR_CUDA. */

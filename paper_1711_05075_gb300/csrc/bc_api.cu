@@ -1546,6 +1546,99 @@ bc_status bc_learned_sweep(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B,
     return bc_learned_sweep_avg(c, net, A, B, quats, n, topk, nullptr, 0, idx, peak, argmax, scores);
 }
 
+// ------------------------------------------------------------------ learned sweep, two stages
+namespace {
+__global__ void k_gather_scores(const float *__restrict__ x, const int *__restrict__ idx, int k, float *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) out[i] = x[idx[i]];
+}
+__global__ void k_compose_idx(const int *__restrict__ outer, const int *__restrict__ inner, int k, int *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) out[i] = outer[inner[i]];
+}
+} // namespace
+
+bc_status bc_learned_sweep_cascade(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
+                                   int topk, const float *orients, int norient, int keep, int *idx, float *peak,
+                                   int *argmax, float *scores)
+{
+    try {
+        if (!c || !net || !A || !B || !quats || !idx || !peak || !argmax)
+            return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: null argument");
+        if (A->ctx != c || B->ctx != c)
+            return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: shapes belong to another context");
+        if (n < 1 || n > BC_TOPK_MAX) return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: n must be in [1, 16384]");
+        if (keep < 1 || keep > n) return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: keep must be in [1, n]");
+        if (topk < 1 || topk > keep) return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: topk must be in [1, keep]");
+        if (norient < 0 || (norient > 0 && !orients))
+            return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: norient < 0, or orientations missing");
+        if (A->n == 0 || B->n == 0) return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: empty shape (f(0) = 0)");
+        if (norient > 0)
+            if (bc_status s = check_quats(orients, norient, "bc_learned_sweep_cascade")) return s;
+        cudaStream_t st = c->stream;
+        cudaError_t e;
+        const bool rot = bc_mlp_rotated_moments(net) != 0;
+        const size_t M = BC_MOMENTS, no = (size_t)norient, kp = (size_t)keep, N = (size_t)n;
+        // scratch (floats): receptor and ligand moments (2 M), features (n x 144), one-view
+        // scores (n), kept sums and scores (2 keep), kept and composed rotations (2 x 4 keep),
+        // selected rotations (4 topk), turned-receptor moments (norient M) and orientations
+        // (4 norient), rotated-ligand moments (n M, when the network takes them); ints: kept
+        // and selected indices (keep + topk)
+        const size_t nf = 2 * M + N * 144 + N + 2 * kp + 8 * kp + 4 * (size_t)topk + no * M + 4 * no + (rot ? N * M : 0);
+        const size_t bytes = sizeof(float) * nf + sizeof(int) * (kp + (size_t)topk);
+        if ((e = c->learn.ensure(bytes, false, st)) != cudaSuccess) return cuda_fail(e, "learned scratch");
+        float *fa = (float *)c->learn.p, *fb = fa + M, *X = fb + M, *s0 = X + N * 144, *acc = s0 + N, *sc = acc + kp;
+        float *q1 = sc + kp, *qs = q1 + 4 * kp, *qsel = qs + 4 * kp, *fo = qsel + 4 * (size_t)topk, *od = fo + no * M;
+        float *fbr = od + 4 * no;
+        int *i1 = (int *)(fbr + (rot ? N * M : 0)), *i2 = i1 + kp;
+        auto features = [&](const float *q, int rows, const float *fA) -> bc_status {
+            if (!rot) return bc_mlp_features(net, q, rows, fA, fb, X);
+            cudaError_t e2 = launch_moments_rot(B->knots, B->n, q, rows, c->ballft, c->qmax + 1, c->g.L,
+                                                (float)(2.0 / c->period), fbr, c->err_dev, st);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "moments of the rotated ligand");
+            return bc_mlp_features_rows(net, q, rows, fA, fbr, X);
+        };
+        float *s_all = scores ? scores : s0;
+        // stage 1: one view for every rotation, keep the best `keep`
+        if (bc_status s = shape_moments(c, A, nullptr, fa)) return s;
+        if (!rot)
+            if (bc_status s = shape_moments(c, B, nullptr, fb)) return s;
+        if (bc_status s = features(quats, n, fa)) return s;
+        if (bc_status s = bc_mlp_predict(net, X, n, s_all)) return s;
+        if ((e = launch_topk(s_all, n, keep, i1, st)) != cudaSuccess) return cuda_fail(e, "top-k (kept)");
+        if ((e = launch_gather_quats(quats, i1, keep, q1, st)) != cudaSuccess) return cuda_fail(e, "gather kept rotations");
+        k_gather_scores<<<(keep + 255) / 256, 256, 0, st>>>(s_all, i1, keep, acc);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gather kept scores");
+        // stage 2: the kept rotations against the receptor turned by each orientation S_k,
+        // whose moments come from one direct-sum launch over all orientations
+        if (norient > 0) {
+            if ((e = cudaMemcpyAsync(od, orients, sizeof(float) * 4 * no, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(e, "orientations");
+            if ((e = launch_moments_rot(A->knots, A->n, od, norient, c->ballft, c->qmax + 1, c->g.L,
+                                        (float)(2.0 / c->period), fo, c->err_dev, st)) != cudaSuccess)
+                return cuda_fail(e, "moments of the turned receptor");
+        }
+        for (int k = 0; k < norient; k++) {
+            if ((e = launch_compose_quats(orients + 4 * (size_t)k, q1, keep, qs, st)) != cudaSuccess)
+                return cuda_fail(e, "compose rotations");
+            if (bc_status s = features(qs, keep, fo + (size_t)k * M)) return s;
+            if (bc_status s = bc_mlp_predict(net, X, keep, sc)) return s;
+            if ((e = launch_axpby(acc, sc, keep, 1.f, 1.f, st)) != cudaSuccess) return cuda_fail(e, "score sum");
+        }
+        if (norient > 0 && (e = launch_axpby(acc, acc, keep, 1.f / (float)(norient + 1), 0.f, st)) != cudaSuccess)
+            return cuda_fail(e, "score mean");
+        if ((e = launch_topk(acc, keep, topk, i2, st)) != cudaSuccess) return cuda_fail(e, "top-k");
+        k_compose_idx<<<(topk + 255) / 256, 256, 0, st>>>(i1, i2, topk, idx);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "rotation indices");
+        if ((e = launch_gather_quats(q1, i2, topk, qsel, st)) != cudaSuccess) return cuda_fail(e, "gather rotations");
+        return sweep_impl(c, A, B, nullptr, qsel, topk, 0, peak, argmax, 1);
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_learned_sweep_cascade: unexpected exception");
+    }
+}
+
 // ------------------------------------------------------------------ tuning
 
 bc_status bc_get_tuning(bc_ctx_t c, bc_tuning *out)

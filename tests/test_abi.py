@@ -28,7 +28,8 @@ def test_header_declares_the_boundary():
               "bc_plan_destroy", "bc_score", "bc_score_sweep", "bc_query_create", "bc_query_eval", "bc_query_destroy",
               "bc_lift_create", "bc_lift_correlate", "bc_lift_destroy", "bc_get_tuning", "bc_set_tuning", "bc_autotune",
               "bc_correlate_noalloc", "bc_selftest_wait", "bc_learned_sweep_avg", "bc_shape_moments_rot",
-              "bc_mlp_features_rows", "bc_mlp_set_features", "bc_mlp_rotated_moments"):
+              "bc_mlp_features_rows", "bc_mlp_set_features", "bc_mlp_rotated_moments",
+              "bc_learned_sweep_cascade"):
         assert f in names
 
 

@@ -225,6 +225,51 @@ def test_learned_sweep_with_rotated_ligand_moments(bc):
     net.close(); A.close(); B.close(); ctx.close()
 
 
+@pytest.mark.parametrize("rotated", [False, True])
+def test_learned_sweep_cascade(bc, rotated):
+    # bc_learned_sweep_cascade: with keep = n and no orientations it is the plain learned
+    # sweep; with keep < n the picks come from the one-view top-keep, ranked by the mean
+    # over the views (the turned receptor's moments by direct sums), and their peaks are
+    # the plain sweep's peaks of the same rotations
+    wl = synth.small_pair(7)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    ctx.set_tuning(spread=1)  # fixed-point spreading sums: spectra and peaks repeat bit for bit
+    A, B = ctx.shape(wl.A.xyz, wl.A.level), ctx.shape(wl.B.xyz, wl.B.level)
+    net = bc.MLP(ctx, 64, synth.mlp_init(64, 9), rotated_moments=rotated)
+    qn = synth.shoemake_quaternions(synth.SplitMix64(4), 2000).astype(np.float32)
+    q = torch.tensor(qn, device="cuda")
+    i0, p0, a0, s0 = bc.learned_sweep(ctx, net, A, B, q, 32)
+    i1, p1, a1, s1 = bc.learned_sweep(ctx, net, A, B, q, 32, keep=2000)
+    np.testing.assert_array_equal(i1.cpu().numpy(), i0.cpu().numpy())
+    np.testing.assert_array_equal(p1.cpu().numpy(), p0.cpu().numpy())
+    np.testing.assert_array_equal(s1.cpu().numpy(), s0.cpu().numpy())
+    S = synth.shoemake_quaternions(synth.SplitMix64(11), 3).astype(np.float32)
+    keep = 300
+    idx, peak, arg, sv = bc.learned_sweep(ctx, net, A, B, q, 32, orientations=S, keep=keep)
+    sv = sv.cpu().numpy()
+    np.testing.assert_array_equal(sv, s0.cpu().numpy())  # the one-view scores
+    kept = np.lexsort((np.arange(sv.size), -sv))[:keep]
+    chosen = idx.cpu().numpy()
+    assert set(chosen.tolist()) <= set(kept.tolist())
+    # the mean over the views, formed on the host (rotations composed in FP64)
+    fo = bc.moments_rot(ctx, A, torch.tensor(S, device="cuda"))
+    fb = bc.moments(ctx, B)
+    q1 = qn[kept]
+    views = [sv[kept]]
+    for k, s_q in enumerate(S):
+        qs = torch.tensor(synth.compose_quaternions(s_q, q1).astype(np.float32), device="cuda")
+        lig = bc.moments_rot(ctx, B, qs) if rotated else fb
+        views.append(net.predict(net.features(qs, fo[k].contiguous(), lig)).cpu().numpy())
+    avg = np.mean(views, axis=0)
+    top_host = set(kept[np.lexsort((np.arange(keep), -avg))[:32]].tolist())
+    assert len(top_host & set(chosen.tolist())) >= 29  # near the cut the last bits may reorder a pick
+    p2, _ = ctx.sweep(A, B, qn[chosen])
+    np.testing.assert_allclose(peak.cpu().numpy(), p2.cpu().numpy(), rtol=1e-5)
+    with pytest.raises(bc.BallCorrError):
+        bc.learned_sweep(ctx, net, A, B, q, 32, orientations=S, keep=16)  # topk > keep
+    net.close(); A.close(); B.close(); ctx.close()
+
+
 def test_topk_is_a_stable_descending_selection(bc):
     rng = np.random.default_rng(0)
     ctx = bc.Context(32, 6, synth.RADII_2)
