@@ -1012,7 +1012,7 @@ def main():
     ap.add_argument("--refine", type=int, default=0,
                     help="of the top-k full correlations, spend this many on the nearest rotations of the best peaks")
     ap.add_argument("--refine-seeds", type=int, default=8)
-    ap.add_argument("--tta", type=int, default=64,
+    ap.add_argument("--tta", type=int, default=256,
                     help="learned workload: also rank by scores averaged over this many random receptor orientations")
     ap.add_argument("--target-alpha", type=float, default=0.0,
                     help="train on exp(alpha (z - 3)) of the standardised peak z instead of z (0: z)")
