@@ -619,6 +619,78 @@ def run_split(args):
     return 0
 
 
+# ------------------------------------------------------------------ batched sweep and ragged pairs
+def run_sweep(args):
+    """The batched rotation sweep of the 50,000-ball receptor and the 5,000-ball ligand
+    (2,048 Shoemake rotations, N = 96, W = 8: peak and argmax per rotation, bc_sweep)
+    and the ragged batch of 64 pairs with knot counts log-uniform in [10^3, 10^5]
+    (bc_pairs, peaks), each timed `steps` times after `warmup` untimed runs with CUDA
+    events (inputs are resident; the spreading boxes and planes exceed L2), beside
+    the plain per-rotation rate (one bc_correlate per rotation, A recomputed), plus
+    the per-stage device times of one profiled sweep pass."""
+    import torch
+    import paper_1711_05075_gb300 as bc
+    from paper_1711_05075_gb300 import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sw = synth.sweep_pair(0, k=2048)
+    ctx = bc.Context(sw.N, sw.W, sw.radii, stream=stream)
+    A, B = ctx.shape(sw.A.xyz, sw.A.level), ctx.shape(sw.B.xyz, sw.B.level)
+    q = sw.quats.astype(np.float32)
+    tuning = ctx.autotune(A, B, 256) if not args.no_autotune else ctx.tuning
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    ms_sweep = timed(lambda: ctx.sweep(A, B, q), args.steps)
+    out = torch.empty((1, sw.N, sw.N, sw.N), device=dev)
+    ms_plain = timed(lambda: [ctx.correlate(A, B, q[r:r + 1], out) for r in range(64)], max(1, args.steps // 4)) / 64
+    pairs, qr = synth.ragged_pairs(0)
+    hA = ctx.shapes([(a.xyz, a.level) for a, _ in pairs])
+    hB = ctx.shapes([(b.xyz, b.level) for _, b in pairs])
+    qr = qr.astype(np.float32)
+    ms_ragged = timed(lambda: ctx.pairs(hA, hB, qr, grids=False, peaks=True), args.steps)
+    clocks = sampler.stop()
+    bc.bc_profile_begin(ctx.handle, 64)
+    ctx.sweep(A, B, q)
+    prof = bc.bc_profile_end(ctx.handle)
+    knots = [a.n + b.n for a, b in pairs]
+    poses = len(q) * sw.N ** 3
+    line = {"metric": "batched rotation sweep and ragged pairs (peak per rotation / pair)", "workload": "batched sweep",
+            "unit": "poses/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"receptor_knots": sw.A.n, "ligand_knots": sw.B.n, "rotations": len(q), "N": sw.N, "W": sw.W,
+                       "levels": list(sw.radii), "ragged_pairs": len(pairs), "ragged_knots_min_max": [min(knots), max(knots)],
+                       "ragged_knots_total": int(sum(knots))},
+            "sweep_ms": ms_sweep, "sweep_rotations_s": len(q) / (ms_sweep * 1e-3), "sweep_poses_s": poses / (ms_sweep * 1e-3),
+            "plain_ms_per_rotation": ms_plain, "plain_poses_s": sw.N ** 3 / (ms_plain * 1e-3),
+            "sweep_vs_plain": (poses / (ms_sweep * 1e-3)) / (sw.N ** 3 / (ms_plain * 1e-3)),
+            "ragged_ms": ms_ragged, "ragged_pairs_s": len(pairs) / (ms_ragged * 1e-3),
+            "ragged_poses_s": len(pairs) * sw.N ** 3 / (ms_ragged * 1e-3),
+            "sweep_stage_ms": {st["name"]: round(st["ms"], 3) for st in prof["stages"]},
+            "sweep_stage_source": "one profiled sweep pass launched kernel by kernel with CUDA events between the stages",
+            "tuning": tuning, "clocks": clocks}
+    for h in hA + hB + [A, B]:
+        h.close()
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ network training
 def run_train(args):
     """Training rate of the rotation-proposal network at the learned workload's size
@@ -986,10 +1058,10 @@ def main():
                     help="grid size of the --profile-correlations workload (the 20k+20k-ball pair)")
     ap.add_argument("--profile-precision", type=int, default=0, choices=[0, 1],
                     help="precision of the --profile-correlations context (1: split BF16 stages)")
-    ap.add_argument("--workload", choices=["scale", "learned", "score", "query", "lifted", "split", "train"],
+    ap.add_argument("--workload", choices=["scale", "learned", "score", "query", "lifted", "split", "train", "sweep"],
                     default="scale",
                     help="scale: the 20k+20k-ball N=128 correlation (default); learned: the rotation-proposal "
-                         "study; train: the network's training rate; score: the complementarity score of the same pair; query: truncated "
+                         "study; train: the network's training rate; sweep: the batched rotation sweep and ragged pairs; score: the complementarity score of the same pair; query: truncated "
                          "single-configuration queries of the same pair; lifted: the 4D nonequiradius "
                          "correlation; split: the split-precision path beside FP32 at N = 256")
     ap.add_argument("--lift-n", type=int, default=32)
@@ -1043,6 +1115,8 @@ def main():
         return run_lifted(args)
     if args.workload == "train":
         return run_train(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.workload == "split":
         return run_split(args)
     if args.profile_correlations > 0:
