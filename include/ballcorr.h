@@ -307,8 +307,16 @@ bc_status bc_lift_destroy(bc_lift_t lift);
  *                device queue in order, each unit waiting (bounded, two
  *                seconds; bc_sync reports an expired wait as BC_ERR_TIMEOUT)
  *                for the units it reads to finish.  Same arithmetic.
- * A new context starts with {0, 64, 1, 0, 1, 0} (z_transform 0 where 1 is not
- * available).  Plans keep the choices in force when
+ *   overlap      1: every pass after the first of a correlation is launched
+ *                as a programmatic dependent of the pass before it, so its
+ *                blocks take the SMs the earlier pass leaves and run their
+ *                set-up (constant tables, tensor memory, barriers) while the
+ *                earlier pass finishes; each waits for the earlier pass to
+ *                complete before it reads what that pass wrote.  0: each pass
+ *                is launched after the previous one has ended.  Same
+ *                arithmetic.
+ * A new context starts with {0, 64, 1, 0, 1, 0, 1} (z_transform 0 where 1 is
+ * not available).  Plans keep the choices in force when
  * they were made.  bc_autotune times the candidates on the given shapes --
  * bc_correlate of A with B (identity) for `spread`, `z_transform` and `persistent` (when rotations > 0,
  * `z_transform` is decided again on the sweep with the chosen batch); in FP32 contexts the
@@ -328,6 +336,7 @@ typedef struct {
     int fft_schedule;
     int z_transform;
     int persistent;
+    int overlap;
 } bc_tuning;
 bc_status bc_get_tuning(bc_ctx_t ctx, bc_tuning *out);
 bc_status bc_set_tuning(bc_ctx_t ctx, const bc_tuning *t);

@@ -35,7 +35,8 @@ class bc_profile(ctypes.Structure):
 
 class bc_tuning(ctypes.Structure):
     _fields_ = [("spread", ctypes.c_int), ("sweep_batch", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("fft_schedule", ctypes.c_int), ("z_transform", ctypes.c_int), ("persistent", ctypes.c_int)]
+                ("fft_schedule", ctypes.c_int), ("z_transform", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("overlap", ctypes.c_int)]
 
 
 class bc_lift_params(ctypes.Structure):
@@ -369,7 +370,7 @@ def bc_query_destroy(q):
 
 def _tuning_dict(t):
     return {"spread": t.spread, "sweep_batch": t.sweep_batch, "graphs": t.graphs, "fft_schedule": t.fft_schedule,
-            "z_transform": t.z_transform, "persistent": t.persistent}
+            "z_transform": t.z_transform, "persistent": t.persistent, "overlap": t.overlap}
 
 
 def bc_get_tuning(ctx):
@@ -378,8 +379,9 @@ def bc_get_tuning(ctx):
     return _tuning_dict(t)
 
 
-def bc_set_tuning(ctx, spread, sweep_batch, graphs=1, fft_schedule=0, z_transform=0, persistent=1):
-    t = bc_tuning(int(spread), int(sweep_batch), int(graphs), int(fft_schedule), int(z_transform), int(persistent))
+def bc_set_tuning(ctx, spread, sweep_batch, graphs=1, fft_schedule=0, z_transform=0, persistent=1, overlap=1):
+    t = bc_tuning(int(spread), int(sweep_batch), int(graphs), int(fft_schedule), int(z_transform), int(persistent),
+                  int(overlap))
     _check(lib().bc_set_tuning(ctx, ctypes.byref(t)))
 
 
@@ -508,18 +510,19 @@ class Context:
     @property
     def tuning(self):
         """The context's implementation choices: {"spread", "sweep_batch", "graphs", "fft_schedule", "z_transform",
-        "persistent"}."""
+        "persistent", "overlap"}."""
         return bc_get_tuning(self.handle)
 
     def set_tuning(self, spread=None, sweep_batch=None, graphs=None, fft_schedule=None, z_transform=None,
-                   persistent=None):
+                   persistent=None, overlap=None):
         t = self.tuning
         bc_set_tuning(self.handle, t["spread"] if spread is None else spread,
                       t["sweep_batch"] if sweep_batch is None else sweep_batch,
                       t["graphs"] if graphs is None else graphs,
                       t["fft_schedule"] if fft_schedule is None else fft_schedule,
                       t["z_transform"] if z_transform is None else z_transform,
-                      t["persistent"] if persistent is None else persistent)
+                      t["persistent"] if persistent is None else persistent,
+                      t["overlap"] if overlap is None else overlap)
 
     def autotune(self, A, B, rotations=0):
         """Times the candidates on these shapes and keeps the fastest (see bc_autotune)."""

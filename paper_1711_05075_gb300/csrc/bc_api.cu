@@ -164,6 +164,7 @@ struct bc_ctx_s {
     int spread_mode = 0;  // 0: spreading boxes in HBM (k_spread + k_fft_z); 1: binned, fused into the z pass
     int sweep_batch = 64; // rotations per pass when a sweep's batch argument is 0
     int fft_sched = 0;    // alternative radix schedule per forward FP32 pass: bit 0 z, bit 1 y, bit 2 x
+    int overlap = 1;      // passes after k_prepare launched as programmatic dependents
     int z_tc = 0;         // z pass as a DFT product on the tensor cores (spread 0; needs zdft)
     int persistent = 0;   // x, inverse-y and inverse-z passes as one persistent launch (bc_back.cu)
     float *zdft = nullptr; // its 32-cell DFT block, split TF32 (hi, then lo), FP32 contexts with N <= 128
@@ -725,6 +726,7 @@ struct Job {
     int sched = 0; // radix schedule of the forward passes
     int ztc = 0;   // z pass on the tensor cores (mode 0 only)
     int back = 0;  // x, inverse-y and inverse-z passes as one persistent launch
+    int overlap = 0; // passes after k_prepare as programmatic dependents of the pass before
     bool yz = false; // inverse y and z of whole planes in one launch (batches of many pairs)
     Weights w;
     int nmain = 0, koff = 0, max_knots = 0, max_cap = 0;
@@ -743,6 +745,7 @@ static Job plan_job(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, const std
     j.sched = c->fft_sched;
     j.ztc = c->z_tc && c->spread_mode == 0 ? 1 : 0;
     j.back = c->persistent;
+    j.overlap = c->overlap;
     j.nmain = (int)pairs.size() - (cache_first ? 1 : 0);
     j.inst.resize(shapes.size());
     for (size_t i = 0; i < shapes.size(); i++) {
@@ -839,6 +842,7 @@ static bc_status launch_job(bc_ctx_t c, Workspace &ws, const Job &job, const Ins
     Geometry g = c->g;
     g.inv_P3 *= job.w.sign;
     g.sched = job.sched;
+    g.pdl = job.overlap;
     const int ninst = (int)job.inst.size();
     Tables t = tables_of(c);
     if (job.w.ballft) {
@@ -1003,7 +1007,7 @@ static bc_status enqueue(bc_ctx_t c, const std::vector<bc_shape_t> &shapes, cons
     const long long sig[] = {(long long)job.inst.size(), (long long)job.pairs.size(), (long long)job.nmain,
                              (long long)job.cache_first, (long long)job.koff, (long long)job.max_knots,
                              (long long)job.mode, (long long)job.sched, (long long)job.ztc, (long long)job.back,
-                             (long long)job.max_cap};
+                             (long long)job.max_cap, (long long)job.overlap};
     add(sig, sizeof(sig));
     const void *ptrs[] = {dout, keys, job.w.ballft, ws.ku.p, ws.plan.p, ws.inst.p, ws.pairs.p, ws.grid.p, ws.z1.p, ws.y1.p,
                           ws.h.p, ws.fa.p, ws.boxes.p, ws.cnt.p, ws.cur.p, ws.rec.p, ws.sync.p, c->stream};
@@ -1650,6 +1654,7 @@ bc_status bc_get_tuning(bc_ctx_t c, bc_tuning *out)
     out->fft_schedule = c->fft_sched;
     out->z_transform = c->z_tc;
     out->persistent = c->persistent;
+    out->overlap = c->overlap;
     return BC_OK;
 }
 
@@ -1662,10 +1667,12 @@ bc_status bc_set_tuning(bc_ctx_t c, const bc_tuning *t)
     if (t->fft_schedule < 0 || t->fft_schedule > 7) return fail(BC_ERR_ARG, "bc_set_tuning: fft_schedule must be in [0, 7]");
     if (t->z_transform != 0 && t->z_transform != 1) return fail(BC_ERR_ARG, "bc_set_tuning: z_transform must be 0 or 1");
     if (t->persistent != 0 && t->persistent != 1) return fail(BC_ERR_ARG, "bc_set_tuning: persistent must be 0 or 1");
+    if (t->overlap != 0 && t->overlap != 1) return fail(BC_ERR_ARG, "bc_set_tuning: overlap must be 0 or 1");
     if (t->z_transform == 1 && !c->zdft)
         return fail(BC_ERR_UNSUPPORTED, "bc_set_tuning: the tensor-core z transform needs an FP32 context with N <= 128");
     c->z_tc = t->z_transform;
     c->persistent = t->persistent;
+    c->overlap = t->overlap;
     c->fft_sched = t->fft_schedule;
     c->spread_mode = t->spread;
     c->sweep_batch = t->sweep_batch;

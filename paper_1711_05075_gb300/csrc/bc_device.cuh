@@ -2,6 +2,7 @@
 // bc_binned.cu).  Not part of the public interface.
 #pragma once
 #include <climits>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "bc_fft.cuh"
@@ -118,6 +119,37 @@ static cudaError_t set_smem(K kernel, size_t bytes)
 {
     if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     return cudaSuccess;
+}
+
+// Programmatic dependent launch.  A pass launched as a programmatic dependent
+// of the kernel before it on the stream may start once every block of that
+// kernel has signalled (pdl_signal) or exited: its blocks become resident as
+// the earlier kernel's blocks leave their SMs and run the prologue that reads
+// only the context's constant tables.  pdl_wait then holds every thread until
+// the earlier kernel has completed and its writes are visible; everything a
+// pass reads from earlier passes is read after it.  Both are no-ops for a
+// kernel launched the ordinary way.  The earlier kernel's signal cannot starve
+// it: the dependent launch needs all of its blocks to have started.
+__device__ __forceinline__ void pdl_signal() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// kernel<<<grid, threads, smem, s>>>(args...), as a programmatic dependent of
+// the previous kernel on s when `dependent` is set.
+template <typename... P, typename... A>
+static cudaError_t launch_k(void (*kernel)(P...), int grid, int threads, size_t smem, cudaStream_t s, bool dependent,
+                            A &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = dependent ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...);
 }
 
 } // namespace bc

@@ -60,6 +60,7 @@ struct Geometry {
     float beta, n_over_P, inv_P3;
     int prec;           // 0: FP32 transforms; 1: radix-8 stages as split BF16 tensor-core DFTs
     int sched;          // alternative radix schedule for the forward FP32 passes: bit 0 z, bit 1 y, bit 2 x
+    int pdl;            // 1: the passes after k_prepare launch as programmatic dependents of the one before
 };
 
 // Kernel launchers (bc_kernels.cu).  All return cudaGetLastError() after launch.

@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(PREP_THREADS)
 k_prepare(Geometry g, const InstDesc *__restrict__ inst, int ninst, float4 *ku, int *bb, int *cnt, InstPlan *plan,
           int *err)
 {
+    pdl_signal(); // the spreading pass may be launched (it waits for this grid)
     const int i = blockIdx.y;
     const InstDesc d = inst[i];
     const int j = blockIdx.x * PREP_THREADS + threadIdx.x;
@@ -386,6 +387,8 @@ k_spread(Geometry g, const float *__restrict__ consts, const InstDesc *__restric
     const int wa = lane / W, wt = lane - wa * W;
     float kc[KB_NC];
     kb_load(consts, lane < 3 * W ? wt : 0, kc);
+    pdl_signal();
+    pdl_wait(); // earlier passes' outputs are read from here on
     for (int k = blockIdx.x * SPREAD_WARPS + wib; k < total; k += gridDim.x * SPREAD_WARPS) {
         const float4 v = ku[k];
         const int tag = __float_as_int(v.w);
@@ -483,8 +486,8 @@ cudaError_t launch_spread(const Geometry &g, const Tables &t, const InstDesc *in
     (void)nsm; // one warp per knot: measured faster than resident-sized grid-stride loops
     int blocks = (total_knots + SPREAD_WARPS - 1) / SPREAD_WARPS;
     if (blocks > 65535) blocks = 65535;
-    k_spread<<<blocks, SPREAD_WARPS * 32, 0, s>>>(g, t.consts, inst, ku, plan, grid, total_knots);
-    return cudaGetLastError();
+    return launch_k(k_spread, blocks, SPREAD_WARPS * 32, 0, s, g.pdl != 0, g, t.consts, inst, ku, plan, grid,
+                    total_knots);
 }
 
 // ------------------------------------------------------------------ fft z
@@ -511,6 +514,8 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     float2 *OUT = three ? S0 : S1; // tile the last stage writes (not the one it reads)
     float2 *STG = three ? S1 : S0; // staging for the output rows
     load_twiddles<NF>(tw, tb.tw_n);
+    pdl_signal();
+    pdl_wait(); // earlier passes' outputs are read from here on
     constexpr int H = NF / 4; // kept z modes (N/2, n = 2N)
     const int L = g.L;
     FirstInputs<NF, Radix<NF, S>::r0, CL, TB> in;
@@ -596,6 +601,8 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
     float2 *tw = reinterpret_cast<float2 *>(sm4);
     float2 *S0 = tw + NF, *S1 = S0 + NF * CL;
     load_twiddles<NF>(tw, tb.tw_n);
+    pdl_signal();
+    pdl_wait(); // earlier passes' outputs are read from here on
     constexpr int H = NF / 4, N = NF / 2;
     const int L = g.L;
     constexpr int nch = H / CL;
@@ -734,6 +741,8 @@ k_fft_y_shift(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int nins
     float2 *S0 = tw + NF;
     float2 *T0 = S0 + NF * CL, *T1 = T0 + YS::MAXR * CL; // staging tiles
     load_twiddles<NF>(tw, tb.tw_n);
+    pdl_signal();
+    pdl_wait(); // earlier passes' outputs are read from here on
     constexpr int H = NF / 4, N = NF / 2;
     constexpr int nch = H / CL;
     const int L = g.L;
@@ -797,6 +806,8 @@ k_fft_x(Geometry g, Tables tb, const InstDesc *__restrict__ inst, const InstPlan
     const typename XL::Ptr sm = XL::carve(reinterpret_cast<float2 *>(sm4));
     load_twiddles<NF>(sm.twF, tb.tw_n);
     load_twiddles<NI>(sm.twI, tb.tw_N);
+    pdl_signal();
+    pdl_wait(); // earlier passes' outputs are read from here on
     constexpr int nch = NI / 2 / CL;
     const int items = NI * nch;
     RotStart rs;
@@ -822,6 +833,8 @@ k_ifft_y(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
     float2 *tw = reinterpret_cast<float2 *>(sm4);
     float2 *S0 = tw + NI, *S1 = S0 + NI * CL;
     load_twiddles<NI>(tw, tb.tw_N);
+    pdl_signal();
+    pdl_wait(); // earlier passes' outputs are read from here on
     constexpr int H = NI / 2, N = NI;
     constexpr int nch = H / CL;
     const int items = N * nch;
@@ -887,6 +900,8 @@ k_ifft_z(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs, 
     float2 *tw = reinterpret_cast<float2 *>(sm4);
     float2 *A = tw + NI, *B = A + NI * CL;
     load_twiddles<NI>(tw, tb.tw_N);
+    pdl_signal();
+    pdl_wait(); // earlier passes' outputs are read from here on
     constexpr int H = NI / 2, N = NI;
     const int nyb = N / 32;
     const int items = N * nyb;
@@ -976,6 +991,8 @@ k_ifft_yz(Geometry g, Tables tb, const PairDesc *__restrict__ pairs, int npairs,
     float2 *A = P + N * H;         // [N + 1][CL] scratch tiles
     float2 *B = A + NI * CL;
     load_twiddles<NI>(tw, tb.tw_N);
+    pdl_signal();
+    pdl_wait(); // earlier passes' outputs are read from here on
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = lane >> 1, odd = lane & 1;
     const int units = npairs * N;
@@ -1066,8 +1083,8 @@ static cudaError_t fft_z_t(const Geometry &g, const Tables &t, const InstDesc *i
     const size_t smem = sizeof(float2) * (NF + 2 * NF * CL);
     cudaError_t e = set_smem(k_fft_z<NF, SP, S>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_z<NF, SP, S><<<resident_blocks(k_fft_z<NF, SP, S>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, grid, z1);
-    return cudaGetLastError();
+    return launch_k(k_fft_z<NF, SP, S>, resident_blocks(k_fft_z<NF, SP, S>, smem, nsm), TB, smem, s, g.pdl != 0, g, t,
+                    inst, ninst, plan, grid, z1);
 }
 
 cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
@@ -1098,16 +1115,15 @@ static cudaError_t fft_y_t(const Geometry &g, const Tables &t, const InstDesc *i
             const size_t smem = YShift<NF, S>::smem;
             cudaError_t e = set_smem(k_fft_y_shift<NF, S>, smem);
             if (e != cudaSuccess) return e;
-            k_fft_y_shift<NF, S><<<resident_blocks(k_fft_y_shift<NF, S>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst,
-                                                                                                    plan, z1, y1);
-            return cudaGetLastError();
+            return launch_k(k_fft_y_shift<NF, S>, resident_blocks(k_fft_y_shift<NF, S>, smem, nsm), TB, smem, s,
+                            g.pdl != 0, g, t, inst, ninst, plan, z1, y1);
         }
     }
     const size_t smem = sizeof(float2) * (NF + (YStaged<NF, SP, S>::on ? 3 : 2) * NF * CL);
     cudaError_t e = set_smem(k_fft_y<NF, SP, S>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_y<NF, SP, S><<<resident_blocks(k_fft_y<NF, SP, S>, smem, nsm), TB, smem, s>>>(g, t, inst, ninst, plan, z1, y1);
-    return cudaGetLastError();
+    return launch_k(k_fft_y<NF, SP, S>, resident_blocks(k_fft_y<NF, SP, S>, smem, nsm), TB, smem, s, g.pdl != 0, g, t,
+                    inst, ninst, plan, z1, y1);
 }
 
 cudaError_t launch_fft_y(const Geometry &g, const Tables &t, const InstDesc *inst, int ninst, const InstPlan *plan,
@@ -1143,9 +1159,8 @@ static cudaError_t fft_x_t(const Geometry &g, const Tables &t, const InstDesc *i
     const size_t smem = XL::bytes(G);
     cudaError_t e = set_smem(k_fft_x<NF, NI, SP, S>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_x<NF, NI, SP, S><<<resident_blocks(k_fft_x<NF, NI, SP, S>, smem, nsm), TB, smem, s>>>(
-        g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, G);
-    return cudaGetLastError();
+    return launch_k(k_fft_x<NF, NI, SP, S>, resident_blocks(k_fft_x<NF, NI, SP, S>, smem, nsm), TB, smem, s,
+                    g.pdl != 0, g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, G);
 }
 
 cudaError_t launch_fft_x(const Geometry &g, const Tables &t, const InstDesc *inst, const InstPlan *plan,
@@ -1174,8 +1189,8 @@ static cudaError_t ifft_y_t(const Geometry &g, const Tables &t, const PairDesc *
     const size_t smem = sizeof(float2) * (NI + 2 * NI * CL);
     cudaError_t e = set_smem(k_ifft_y<NI>, smem);
     if (e != cudaSuccess) return e;
-    k_ifft_y<NI><<<resident_blocks(k_ifft_y<NI>, smem, nsm), TB, smem, s>>>(g, t, pairs, npairs, h);
-    return cudaGetLastError();
+    return launch_k(k_ifft_y<NI>, resident_blocks(k_ifft_y<NI>, smem, nsm), TB, smem, s, g.pdl != 0, g, t, pairs,
+                    npairs, h);
 }
 
 cudaError_t launch_ifft_y(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, float2 *h, int nsm,
@@ -1198,8 +1213,8 @@ static cudaError_t ifft_yz_t(const Geometry &g, const Tables &t, const PairDesc 
     const size_t smem = sizeof(float2) * (NI + (size_t)NI * (NI / 2) + 2 * (size_t)NI * CL);
     cudaError_t e = set_smem(k_ifft_yz<NI>, smem);
     if (e != cudaSuccess) return e;
-    k_ifft_yz<NI><<<resident_blocks(k_ifft_yz<NI>, smem, nsm), TB, smem, s>>>(g, t, pairs, npairs, h, out, keys);
-    return cudaGetLastError();
+    return launch_k(k_ifft_yz<NI>, resident_blocks(k_ifft_yz<NI>, smem, nsm), TB, smem, s, g.pdl != 0, g, t, pairs,
+                    npairs, h, out, keys);
 }
 
 cudaError_t launch_ifft_yz(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, const float2 *h,
@@ -1221,8 +1236,8 @@ static cudaError_t ifft_z_t(const Geometry &g, const Tables &t, const PairDesc *
     const size_t smem = sizeof(float2) * (NI + 2 * NI * CL);
     cudaError_t e = set_smem(k_ifft_z<NI>, smem);
     if (e != cudaSuccess) return e;
-    k_ifft_z<NI><<<resident_blocks(k_ifft_z<NI>, smem, nsm), TB, smem, s>>>(g, t, pairs, npairs, h, out, keys);
-    return cudaGetLastError();
+    return launch_k(k_ifft_z<NI>, resident_blocks(k_ifft_z<NI>, smem, nsm), TB, smem, s, g.pdl != 0, g, t, pairs,
+                    npairs, h, out, keys);
 }
 
 cudaError_t launch_ifft_z(const Geometry &g, const Tables &t, const PairDesc *pairs, int npairs, const float2 *h,

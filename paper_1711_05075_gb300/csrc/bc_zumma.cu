@@ -163,6 +163,8 @@ k_fft_z_umma(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *slot;
+    pdl_signal();
+    pdl_wait(); // the spreading boxes and plans are read from here on
     const int L = g.L;
     ZuWalk w;
 
@@ -408,8 +410,8 @@ static cudaError_t fft_z_umma_t(const Geometry &g, const Tables &t, const InstDe
 {
     cudaError_t e = cudaFuncSetAttribute(k_fft_z_umma<NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, ZU<NF>::SMEM);
     if (e != cudaSuccess) return e;
-    k_fft_z_umma<NF><<<nsm, ZU_THREADS, ZU<NF>::SMEM, s>>>(g, t, inst, ninst, plan, grid, z1, bhi, blo, err);
-    return cudaGetLastError();
+    return launch_k(k_fft_z_umma<NF>, nsm, ZU_THREADS, ZU<NF>::SMEM, s, g.pdl != 0, g, t, inst, ninst, plan, grid, z1,
+                    bhi, blo, err);
 }
 
 // Self-test of the bounded wait the tensor-core kernels use: one thread waits

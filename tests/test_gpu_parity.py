@@ -375,6 +375,37 @@ def test_autotune_keeps_a_valid_choice():
     sa.close(); sb.close(); ctx.close()
 
 
+@pytest.mark.parametrize("spread,zt", [(1, 0), (0, 1)])
+def test_launch_overlap_matches_ordinary_launches(spread, zt):
+    # overlap 1 (the default) launches every pass after the first as a programmatic
+    # dependent of the one before; overlap 0 launches each after the previous one has
+    # ended.  Same kernels and arithmetic: with the fixed-point binned spreading the
+    # grids agree bit for bit; with the atomic spreading both meet the oracle bar.
+    bc = bcmod()
+    wl = synth.small_pair(6)
+    q = synth.shoemake_quaternions(synth.SplitMix64(37), 1).astype(np.float32)
+    ref = oracle_grid(wl.A, wl.B, q[0], wl.N)
+    ctx = bc.Context(wl.N, wl.W, wl.radii)
+    assert ctx.tuning["overlap"] == 1
+    sa = ctx.shape(wl.A.xyz, wl.A.level)
+    sb = ctx.shape(wl.B.xyz, wl.B.level)
+    out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device="cuda")
+    grids = {}
+    for ov in (1, 0):
+        for graphs in (1, 0):
+            ctx.set_tuning(spread=spread, z_transform=zt, persistent=0, overlap=ov, graphs=graphs)
+            for _ in range(3):  # the second identical pass records a graph, the third replays it
+                ctx.correlate(sa, sb, q, out)
+            grids[(ov, graphs)] = out.double().cpu().numpy()[0].copy()
+            check(grids[(ov, graphs)], ref, what=f"overlap {ov}, graphs {graphs}, spread {spread}")
+    if spread == 1:
+        for key, g in grids.items():
+            assert np.array_equal(g, grids[(0, 0)]), key
+    with pytest.raises(bc.BallCorrError):
+        ctx.set_tuning(overlap=2)
+    sa.close(); sb.close(); ctx.close()
+
+
 @pytest.mark.parametrize("spread,zt,pe", MODES)
 def test_graph_replay_matches_oracle_and_kernel_by_kernel(spread, zt, pe):
     # Identical passes (same descriptors and buffers) replay the recorded graph;
