@@ -237,6 +237,9 @@ def run_ours(args, rank, world, local_rank):
         tuning = ctx.tuning
     else:
         tuning = ctx.autotune(A, B) if not args.no_autotune else ctx.tuning
+    if args.overlap is not None:
+        ctx.set_tuning(overlap=args.overlap)
+        tuning = ctx.tuning
     out = torch.empty((1, wl.N, wl.N, wl.N), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -331,7 +334,50 @@ def run_ours(args, rank, world, local_rank):
         e2e_step()
         e_sum += time.perf_counter() - s0
     barrier()
-    e2e_value = world * args.steps * wl.N ** 3 / max_over_ranks(e_sum)
+    e2e_seq = world * args.steps * wl.N ** 3 / max_over_ranks(e_sum)
+
+    # ---- e2e with two steps in flight: a second context (its own stream and
+    # workspaces, the same tuning) and one host thread per context, step i on
+    # context i mod 2; each step is the same upload, correlation and host read as
+    # above, so the copies and host work of one step overlap the other's kernels
+    e2e_value, e2e_two = e2e_seq, None
+    if args.e2e_streams == 2:
+        import threading
+        ctx2 = bc.Context(wl.N, wl.W, wl.radii, wl.period, stream=torch.cuda.Stream(dev))
+        ctx2.set_tuning(**tuning)
+        outs = [host_out, torch.empty_like(host_out).pin_memory()]
+        ctxs = [ctx, ctx2]
+
+        def worker(t, n, errs):
+            try:
+                for _ in range(n):
+                    ha, hb = bc.bc_shapes_create(ctxs[t].handle, [xa, xb], [la, lb], [wl.A.n, wl.B.n], 0)
+                    bc.bc_correlate(ctxs[t].handle, ha, hb, q, 1, outs[t], 0)
+                    bc.bc_shape_destroy(ha)
+                    bc.bc_shape_destroy(hb)
+            except Exception as exc:  # reported below
+                errs.append(exc)
+
+        def two_in_flight(n_steps):
+            errs = []
+            ths = [threading.Thread(target=worker, args=(t, (n_steps + 1 - t) // 2, errs)) for t in range(2)]
+            t0 = time.perf_counter()
+            for th in ths:
+                th.start()
+            for th in ths:
+                th.join()
+            if errs:
+                raise errs[0]
+            return time.perf_counter() - t0
+
+        two_in_flight(max(2 * args.warmup, 2))
+        torch.cuda.synchronize(dev)
+        barrier()
+        t_two = max_over_ranks(two_in_flight(args.steps))
+        barrier()
+        ctx2.close()
+        e2e_two = world * args.steps * wl.N ** 3 / t_two
+        e2e_value = e2e_two
 
     # ---- roofline of the dominant stage (times from the profiled pass)
     peak, peak_src = load_peaks()
@@ -390,7 +436,14 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(wl),
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "steps_in_flight": 2 if e2e_two is not None else 1,
+                    "sequential": {"value": e2e_seq, "unit": UNIT,
+                                   "note": "one step at a time, L2 flushed before each (host timer)"},
+                    "note": ("each step: bc_shapes_create from page-locked host knots, bc_correlate writing the "
+                             "128^3 grid to page-locked host memory (synchronous), shape release; with two in "
+                             "flight, two contexts on their own streams and host threads take alternate steps "
+                             "(no L2 flush: every step's inputs arrive from the host)")},
             "gpu_launches": int(args.steps * prof["launches"] // max(prof["calls"], 1)),
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -639,6 +692,9 @@ def run_sweep(args):
     A, B = ctx.shape(sw.A.xyz, sw.A.level), ctx.shape(sw.B.xyz, sw.B.level)
     q = sw.quats.astype(np.float32)
     tuning = ctx.autotune(A, B, 256) if not args.no_autotune else ctx.tuning
+    if args.overlap is not None:
+        ctx.set_tuning(overlap=args.overlap)
+        tuning = ctx.tuning
 
     def timed(fn, reps):
         for _ in range(max(args.warmup, 1)):
@@ -1050,6 +1106,10 @@ def main():
     ap.add_argument("--spread", type=int, choices=[0, 1], default=None,
                     help="force the spreading implementation (default: autotuned; 0 for --profile-correlations)")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT baseline timing")
+    ap.add_argument("--e2e-streams", type=int, choices=[1, 2], default=2,
+                    help="steps in flight in the e2e measurement (2: two contexts, one host thread each)")
+    ap.add_argument("--overlap", type=int, choices=[0, 1], default=None,
+                    help="launch overlap tuning field (default: the context's)")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-proposal study in the default line (about a minute)")
     ap.add_argument("--profile-correlations", type=int, default=0,
