@@ -77,7 +77,8 @@ typedef struct {
     const double *level_radii; /* host array of L radii (> 0); copied */
     int precision;             /* 0 = FP32; 1 = the radix-8 stages of the forward transforms run as
                                   BF16 hi+lo split DFT matmuls on the tensor cores with FP32
-                                  accumulation (built for N = 32 and 256) */
+                                  accumulation (radix schedules with radix-8 stages: 64 = 8.8,
+                                  128 = 8.16, 192 = 3.8.8, 256 = 4.8.8, 512 = 8.8.8; every N) */
 } bc_params;
 
 /* Creates a context on the current CUDA device bound to `cuda_stream`

@@ -281,7 +281,7 @@ bc_status bc_create(const bc_params *p, void *cuda_stream, bc_ctx_t *out)
         *out = nullptr;
         if (p->precision != 0 && p->precision != 1) return fail(BC_ERR_UNSUPPORTED, "bc_create: precision must be 0 or 1");
         if (p->precision == 1 && !supported_split(p->N))
-            return fail(BC_ERR_UNSUPPORTED, "bc_create: precision 1 (split BF16) is built for N = 32 and 256");
+            return fail(BC_ERR_UNSUPPORTED, "bc_create: precision 1 (split BF16) is built for N = 32, 64, 96, 128, 256");
         if (p->sigma != 2) return fail(BC_ERR_UNSUPPORTED, "bc_create: sigma must be 2");
         if (!supported_N(p->N)) return fail(BC_ERR_UNSUPPORTED, "bc_create: N must be one of 32, 64, 96, 128, 256");
         if (p->W < 2 || p->W > 10 || p->W > p->N) return fail(BC_ERR_ARG, "bc_create: W must be in [2, 10] and <= N");

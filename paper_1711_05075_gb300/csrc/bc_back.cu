@@ -243,9 +243,16 @@ cudaError_t launch_back(const Geometry &g, const Tables &t, const InstDesc *inst
 {
     if (npairs <= 0) return cudaSuccess;
     if (g.prec == 1) {
-        if (g.N == 32) return back_t<64, 32, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, h, out, keys, sync, err, nsm, s);
-        if (g.N == 256) return back_t<512, 256, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, h, out, keys, sync, err, nsm, s);
-        return cudaErrorInvalidValue;
+        switch (g.N) {
+        case 32: return back_t<64, 32, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, h, out, keys, sync, err, nsm, s);
+        case 64: return back_t<128, 64, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, h, out, keys, sync, err, nsm, s);
+        case 96: return back_t<192, 96, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, h, out, keys, sync, err, nsm, s);
+        case 128:
+            return back_t<256, 128, true, SplitSched<256>::S>(g, t, inst, plan, pairs, npairs, y1, fa_cache, h, out,
+                                                               keys, sync, err, nsm, s);
+        case 256: return back_t<512, 256, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, h, out, keys, sync, err, nsm, s);
+        default: return cudaErrorInvalidValue;
+        }
     }
     switch (g.N) {
     case 32: return back_t<64, 32>(g, t, inst, plan, pairs, npairs, y1, fa_cache, h, out, keys, sync, err, nsm, s);

@@ -273,7 +273,7 @@ k_fft_z_binned(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int nin
             else rr_first<NF, Radix<NF, S>::r0, false, CL, TB>(in, S0);
             __syncthreads();
             auto sink = [&](int, int, int c, int pos, float2 v) { OUT[pos * CL + c] = v; };
-            if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
+            if constexpr (SP) sp_all<NF, false, CL, TB, S>(S0, S1, tw, sink);
             else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
             __syncthreads();
             // Z = FFT(a + i b) -> A_k = (Z_k + conj Z_{n-k}) / 2, B_k = (Z_k - conj Z_{n-k}) / (2i),
@@ -320,9 +320,14 @@ cudaError_t launch_fft_z_binned(const Geometry &g, const Tables &t, const InstDe
 {
     if (g.W > MAX_W || 2 + 3 * g.W > BIN_REC) return cudaErrorInvalidValue;
     if (g.prec == 1) {
-        if (g.n == 64) return fft_z_binned_t<64, true>(g, t, inst, ninst, plan, cur, rec, z1, nsm, s);
-        if (g.n == 512) return fft_z_binned_t<512, true>(g, t, inst, ninst, plan, cur, rec, z1, nsm, s);
-        return cudaErrorInvalidValue;
+        switch (g.n) {
+        case 64: return fft_z_binned_t<64, true>(g, t, inst, ninst, plan, cur, rec, z1, nsm, s);
+        case 128: return fft_z_binned_t<128, true>(g, t, inst, ninst, plan, cur, rec, z1, nsm, s);
+        case 192: return fft_z_binned_t<192, true>(g, t, inst, ninst, plan, cur, rec, z1, nsm, s);
+        case 256: return fft_z_binned_t<256, true, SplitSched<256>::S>(g, t, inst, ninst, plan, cur, rec, z1, nsm, s);
+        case 512: return fft_z_binned_t<512, true>(g, t, inst, ninst, plan, cur, rec, z1, nsm, s);
+        default: return cudaErrorInvalidValue;
+        }
     }
     switch (g.n) {
     case 64: return fft_z_binned_t<64>(g, t, inst, ninst, plan, cur, rec, z1, nsm, s);

@@ -164,6 +164,13 @@ template <> struct Radix<192, 1> { static constexpr int r0 = 3, r1 = 4, r2 = 16;
 template <> struct Radix<256, 1> { static constexpr int r0 = 4, r1 = 8, r2 = 8; };
 template <> struct Radix<512, 1> { static constexpr int r0 = 8, r1 = 4, r2 = 16; };
 
+// Schedule of the split-precision passes: the default of each length, except
+// 256, whose default (16.16) has no radix-8 stage for the tensor cores.
+template <int NF>
+struct SplitSched {
+    static constexpr int S = NF == 256 ? 1 : 0;
+};
+
 // ---------------------------------------------------------------------------
 // Interleaved tiles: C lines stored as x[pos * C + c].  Consecutive threads take
 // consecutive lines c of the same butterfly, so every shared-memory access of
@@ -462,13 +469,14 @@ __device__ __forceinline__ void sp_stage(const float2 *in, float2 *out, const fl
 }
 
 // Split-precision transform of a tile whose inputs were scattered into s0 by
-// FirstInputs::scatter; then sink(it, r, c, pos, value) in the thread mapping
-// of rr_last.  All threads call it; the caller adds a barrier before s0/s1 are
+// FirstInputs::scatter (natural order, whatever the loading schedule); then
+// sink(it, r, c, pos, value) in the thread mapping of rr_last for radix
+// schedule S.  All threads call it; the caller adds a barrier before s0/s1 are
 // written again.
-template <int NF, bool INV, int C, int NT, class Sink>
+template <int NF, bool INV, int C, int NT, int S, class Sink>
 __device__ __forceinline__ void sp_all(float2 *s0, float2 *s1, const float2 *tw, Sink sink)
 {
-    using R = Radix<NF>;
+    using R = Radix<NF, S>;
     sp_stage<NF, R::r0, 1, INV, C, NT>(s0, s1, tw);
     __syncthreads();
     sp_stage<NF, R::r1, R::r0, INV, C, NT>(s1, s0, tw);
@@ -479,7 +487,7 @@ __device__ __forceinline__ void sp_all(float2 *s0, float2 *s1, const float2 *tw,
         __syncthreads();
         fin = s1;
     }
-    constexpr int RL = LastStage<NF>::R, NSL = LastStage<NF>::NS, TOT = NSL * C, IT = (TOT + NT - 1) / NT;
+    constexpr int RL = LastStage<NF, S>::R, NSL = LastStage<NF, S>::NS, TOT = NSL * C, IT = (TOT + NT - 1) / NT;
 #pragma unroll
     for (int it = 0; it < IT; it++) {
         const int idx = (int)threadIdx.x + it * NT;

@@ -37,7 +37,7 @@
 
 namespace bc {
 
-bool supported_split(int N) { return N == 32 || N == 256; }
+bool supported_split(int N) { return N == 32 || N == 64 || N == 96 || N == 128 || N == 256; }
 
 bool supported_N(int N)
 {
@@ -551,7 +551,7 @@ k_fft_z(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
             }
             if (it + (int)gridDim.x < items) in.load(src(it + gridDim.x));
             auto sink = [&](int, int, int c, int pos, float2 v) { OUT[pos * CL + c] = v; };
-            if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
+            if constexpr (SP) sp_all<NF, false, CL, TB, S>(S0, S1, tw, sink);
             else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
             __syncthreads();
             // unpack into a staging area [row][k] (row stride H + 1), then write
@@ -686,7 +686,7 @@ k_fft_y(Geometry g, Tables tb, const InstDesc *__restrict__ inst, int ninst, con
                     else return;
                     Y[(long long)jy * H + c] = jy == N / 2 ? make_float2(0.f, 0.f) : v;
                 };
-                if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
+                if constexpr (SP) sp_all<NF, false, CL, TB, S>(S0, S1, tw, sink);
                 else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
                 __syncthreads();
             }
@@ -1091,9 +1091,14 @@ cudaError_t launch_fft_z(const Geometry &g, const Tables &t, const InstDesc *ins
                          float *grid, float2 *z1, int nsm, cudaStream_t s)
 {
     if (g.prec == 1) {
-        if (g.n == 64) return fft_z_t<64, true>(g, t, inst, ninst, plan, grid, z1, nsm, s);
-        if (g.n == 512) return fft_z_t<512, true>(g, t, inst, ninst, plan, grid, z1, nsm, s);
-        return cudaErrorInvalidValue;
+        switch (g.n) {
+        case 64: return fft_z_t<64, true>(g, t, inst, ninst, plan, grid, z1, nsm, s);
+        case 128: return fft_z_t<128, true>(g, t, inst, ninst, plan, grid, z1, nsm, s);
+        case 192: return fft_z_t<192, true>(g, t, inst, ninst, plan, grid, z1, nsm, s);
+        case 256: return fft_z_t<256, true, SplitSched<256>::S>(g, t, inst, ninst, plan, grid, z1, nsm, s);
+        case 512: return fft_z_t<512, true>(g, t, inst, ninst, plan, grid, z1, nsm, s);
+        default: return cudaErrorInvalidValue;
+        }
     }
     switch (g.n) {
     case 64: return fft_z_t<64>(g, t, inst, ninst, plan, grid, z1, nsm, s);
@@ -1130,9 +1135,14 @@ cudaError_t launch_fft_y(const Geometry &g, const Tables &t, const InstDesc *ins
                          const float2 *z1, float2 *y1, int max_cap, int nsm, cudaStream_t s)
 {
     if (g.prec == 1) {
-        if (g.n == 64) return fft_y_t<64, true>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
-        if (g.n == 512) return fft_y_t<512, true>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
-        return cudaErrorInvalidValue;
+        switch (g.n) {
+        case 64: return fft_y_t<64, true>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+        case 128: return fft_y_t<128, true>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+        case 192: return fft_y_t<192, true>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+        case 256: return fft_y_t<256, true, SplitSched<256>::S>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+        case 512: return fft_y_t<512, true>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
+        default: return cudaErrorInvalidValue;
+        }
     }
     switch (g.n) {
     case 64: return fft_y_t<64>(g, t, inst, ninst, plan, z1, y1, max_cap, nsm, s);
@@ -1168,9 +1178,16 @@ cudaError_t launch_fft_x(const Geometry &g, const Tables &t, const InstDesc *ins
                          float2 *h, int nsm, cudaStream_t s)
 {
     if (g.prec == 1) {
-        if (g.N == 32) return fft_x_t<64, 32, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
-        if (g.N == 256) return fft_x_t<512, 256, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
-        return cudaErrorInvalidValue;
+        switch (g.N) {
+        case 32: return fft_x_t<64, 32, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
+        case 64: return fft_x_t<128, 64, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
+        case 96: return fft_x_t<192, 96, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
+        case 128:
+            return fft_x_t<256, 128, true, SplitSched<256>::S>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out,
+                                                                h, nsm, s);
+        case 256: return fft_x_t<512, 256, true>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);
+        default: return cudaErrorInvalidValue;
+        }
     }
     switch (g.N) {
     case 32: return fft_x_t<64, 32>(g, t, inst, plan, pairs, npairs, y1, fa_cache, fa_out, h, nsm, s);

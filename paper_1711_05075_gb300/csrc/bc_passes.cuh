@@ -102,7 +102,7 @@ __device__ __forceinline__ void spectrum_x(float2 (&F)[XModes<NF, S>::IT][XModes
             const float Mv = Tl[(mx < 0 ? -mx : mx) * CL + c];
             F[it][r] = make_float2(fmaf(Mv, v.x, F[it][r].x), fmaf(Mv, v.y, F[it][r].y));
         };
-        if constexpr (SP) sp_all<NF, false, CL, TB>(S0, S1, tw, sink);
+        if constexpr (SP) sp_all<NF, false, CL, TB, S>(S0, S1, tw, sink);
         else rr_rest<NF, false, CL, TB, S>(S0, S1, tw, sink);
         __syncthreads();
     }

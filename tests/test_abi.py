@@ -57,7 +57,6 @@ def _status(fn):
     (dict(N=32, W=6, radii=[-0.1]), 1),
     (dict(N=32, W=6, radii=[0.1], period=0.0), 1),
     (dict(N=32, W=6, radii=[0.1], sigma=3), 5),
-    (dict(N=128, W=6, radii=[0.1], precision=1), 5),
     (dict(N=32, W=6, radii=[0.1], precision=2), 5),
 ])
 def test_create_rejects_bad_parameters_before_device_work(kw, status):

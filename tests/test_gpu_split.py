@@ -66,3 +66,23 @@ def test_split_precision_scale_pair_N256_sampled(bc):
     print(f"N=256 20k+20k: FP32 rel-L2 {e32[0]:.2e} max-abs {e32[1]:.2e} | split BF16 rel-L2 {esp[0]:.2e} "
           f"max-abs {esp[1]:.2e} (|ref| max {np.abs(ref).max():.3e})")
     assert e32[0] <= FP32_TOL and esp[0] <= SPLIT_TOL
+
+
+@pytest.mark.parametrize("N", [64, 96, 128])
+def test_split_precision_each_N_sampled(bc, N):
+    # 2,000 + 2,000 balls (L = 4), W = 8, a random rotation; 4,096 sampled t.  The
+    # split passes use the radix schedules with radix-8 stages (128 = 8.16,
+    # 192 = 3.8.8, 256 = 4.8.8); both transforms of every pass are compared.
+    wl = synth.scale_pair(0, N=N, W=8, n=2000)
+    q = synth.shoemake_quaternions(synth.SplitMix64(40 + N), 1).astype(np.float32)
+    g32 = run(bc, wl.A, wl.B, q, N, wl.W, 0)[0].reshape(-1)
+    gsp = run(bc, wl.A, wl.B, q, N, wl.W, 1)[0].reshape(-1)
+    idx = synth.translation_sample(N, 4096, seed=1)
+    ghat = O.band_limited_spectrum(f32(wl.A), f32(wl.B), q[0].astype(np.float64), N)
+    ref = O.inverse_at(ghat, O.grid_points(N, idx=idx))
+    e32, esp = errs(g32[idx], ref), errs(gsp[idx], ref)
+    print(f"N={N} 2k+2k: FP32 rel-L2 {e32[0]:.2e} max-abs {e32[1]:.2e} | split BF16 rel-L2 {esp[0]:.2e} "
+          f"max-abs {esp[1]:.2e} (|ref| max {np.abs(ref).max():.3e})")
+    assert e32[0] <= FP32_TOL and esp[0] <= SPLIT_TOL
+    # the split passes differ from FP32 by their BF16 roundings, not by a different transform
+    assert errs(gsp[idx], g32[idx])[0] <= SPLIT_TOL
