@@ -49,9 +49,10 @@ L2_FLUSH_BYTES = 256 << 20
 # each).  An entry counts only while the device-code sources it was measured
 # on are unchanged (sha256 over KERNEL_SOURCES, first 16 hex digits).
 NCU_TRAFFIC = {
-    "k_spread": {"bytes": 1.838e+07, "kernel_hash": "04143992a3526772"},
-    "k_fft_z_umma": {"bytes": 7.917e+07, "kernel_hash": "04143992a3526772"},
-    "k_fft_x": {"bytes": 8.312e+07, "kernel_hash": "04143992a3526772"},
+    "k_spread": {"bytes": 1.840e+07, "kernel_hash": "837a4a425d7aa3ab"},
+    "k_fft_z_umma": {"bytes": 7.554e+07, "kernel_hash": "837a4a425d7aa3ab"},
+    "k_fft_y": {"bytes": 8.893e+07, "kernel_hash": "837a4a425d7aa3ab"},
+    "k_fft_x": {"bytes": 8.089e+07, "kernel_hash": "837a4a425d7aa3ab"},
 }
 
 
@@ -423,9 +424,9 @@ def run_ours(args, rank, world, local_rank):
             ls = learned_study(args)
             keep = ("plain_per_rotation_poses_s", "batched_exhaustive_poses_s", "learned_effective_poses_s",
                     "learned_vs_plain", "batched_vs_plain", "recall_best_in_topk", "recall_within_1e-3_of_best",
-                    "orientation_averaging", "random_topk_recall", "mean_peak_ratio_topk_over_best",
-                    "near_ties", "heldout_mse_standardised", "s_training", "config", "labels",
-                    "rotated_ligand_moments")
+                    "orientation_averaging", "cascade", "coarse", "coarse_exhaustive", "random_topk_recall",
+                    "mean_peak_ratio_topk_over_best", "near_ties", "heldout_mse_standardised", "s_training",
+                    "config", "labels", "rotated_ligand_moments")
             learned = {k: ls[k] for k in keep if k in ls}
             learned["s_total"] = time.perf_counter() - t0
         except Exception as exc:  # the main figures stand on their own
@@ -914,7 +915,23 @@ def learned_study(args):
     K, R = args.topk, args.eval_rot
     Mv = {v: {"hits": 0, "hits_tol": 0, "regrets": [], "test_mse": [], "ms_learn": [], "hits_tta": 0,
               "hits_tta_tol": 0, "ms_tta": [], "hits_ref": 0, "hits_ref_tol": 0, "ms_ref": [],
-              "hits_cas": 0, "hits_cas_tol": 0, "ms_cas": []} for v in variants}
+              "hits_cas": 0, "hits_cas_tol": 0, "ms_cas": [], "hits_co": 0, "hits_co_tol": 0, "ms_co": []}
+          for v in variants}
+    # coarse stage: correlations of the same shapes at a lower band limit (N = coarse_n)
+    ctxc = bc.Context(args.coarse_n, args.coarse_w, synth.RADII_4, stream=stream) if args.coarse_n > 0 else None
+    if ctxc is not None:
+        ctxc.set_tuning(sweep_batch=256)
+    coarse_ex = {"hits": 0, "hits_tol": 0, "ms": []}
+
+    def coarse_then_full(hA, hB, hAc, hBc, qn, cand, K):
+        """The best K of the rotations `cand` (device int32 indices into qn) by their coarse
+        peaks, then full-resolution peaks of those: (chosen indices, their full peaks)."""
+        pc, _ = ctxc.sweep(hAc, hBc, qn[cand.cpu().numpy()], batch=256)
+        iK = torch.empty(K, dtype=torch.int32, device=dev)
+        bc.bc_topk(ctx.handle, pc, cand.shape[0], K, iK)
+        sel = cand[iK.long()].cpu().numpy()
+        pK, _ = ctx.sweep(hA, hB, qn[sel], batch=256)
+        return sel, pK
     rand_hits, ms_ex, near3, near4 = 0, [], [], []
     orients = synth.shoemake_quaternions(synth.SplitMix64(600000), args.tta).astype(np.float32) if args.tta > 0 else None
     for seed in range(1001, 1001 + args.eval_pairs):
@@ -941,6 +958,17 @@ def learned_study(args):
         near3.append(int((p >= p[best] * (1 - 1e-3)).sum()) - 1)
         near4.append(int((p >= p[best] * (1 - 1e-4)).sum()) - 1)
         fa, fb = bc.moments(ctx, hA), bc.moments(ctx, hB)
+        if ctxc is not None:
+            hAc, hBc = ctxc.shape(A.xyz, A.level), ctxc.shape(B.xyz, B.level)
+            # coarse stage alone: every rotation at the coarse band limit, the best K at full resolution
+            e3, e4 = ev(), ev()
+            e3.record(stream)
+            sel, pK = coarse_then_full(hA, hB, hAc, hBc, qn, torch.arange(R, dtype=torch.int32, device=dev), K)
+            e4.record(stream)
+            torch.cuda.synchronize(dev)
+            coarse_ex["ms"].append(e3.elapsed_time(e4))
+            coarse_ex["hits"] += best in set(sel.tolist())
+            coarse_ex["hits_tol"] += float(pK.max()) >= p[best] * (1 - 1e-3)
         for v in variants:
             m, net = Mv[v], nets[v]
             e1, e2 = ev(), ev()
@@ -979,6 +1007,17 @@ def learned_study(args):
                 m["ms_cas"].append(e3.elapsed_time(e4))
                 m["hits_cas"] += best in set(ic_.cpu().numpy().tolist())
                 m["hits_cas_tol"] += float(pc_.max()) >= p[best] * (1 - 1e-3)
+            if ctxc is not None:
+                # three stages (bc_learned_sweep_coarse): the network's one-view best coarse_keep,
+                # their peaks at the coarse band limit, the best K of those at full resolution
+                e3, e4 = ev(), ev()
+                e3.record(stream)
+                ic_, pc_, _, _ = bc.learned_sweep(ctx, net, hA, hB, qd, K, coarse=(ctxc, hAc, hBc, args.coarse_keep))
+                e4.record(stream)
+                torch.cuda.synchronize(dev)
+                m["ms_co"].append(e3.elapsed_time(e4))
+                m["hits_co"] += best in set(ic_.cpu().numpy().tolist())
+                m["hits_co_tol"] += float(pc_.max()) >= p[best] * (1 - 1e-3)
             if args.refine > 0:
                 # two stages within the same K full correlations: the network's top K - refine, then
                 # the nearest rotations (largest |q . q'|) of the best peaks found, round robin
@@ -1010,6 +1049,9 @@ def learned_study(args):
         rand_hits += best in rnd
         hA.close()
         hB.close()
+        if ctxc is not None:
+            hAc.close()
+            hBc.close()
 
     # ---- plain per-rotation reference (one bc_correlate call per rotation, A recomputed)
     ctx.set_tuning(spread=0)
@@ -1057,6 +1099,12 @@ def learned_study(args):
                         "effective_poses_s": poses / (np.mean(m["ms_cas"]) * 1e-3),
                         "vs_plain": poses / (np.mean(m["ms_cas"]) * 1e-3) / plain}
             if m["ms_cas"] else None,
+            "coarse": {"coarse_N": args.coarse_n, "coarse_W": args.coarse_w, "network_keep": args.coarse_keep,
+                       "recall_best": m["hits_co"] / E, "recall_within_1e-3": m["hits_co_tol"] / E,
+                       "ms_learned_sweep": float(np.mean(m["ms_co"])),
+                       "effective_poses_s": poses / (np.mean(m["ms_co"]) * 1e-3),
+                       "vs_plain": poses / (np.mean(m["ms_co"]) * 1e-3) / plain}
+            if m["ms_co"] else None,
             "mean_peak_ratio_topk_over_best": float(np.mean(m["regrets"])),
             "min_peak_ratio_topk_over_best": float(np.min(m["regrets"])),
             "ms_learned_sweep": float(np.mean(m["ms_learn"])),
@@ -1087,6 +1135,12 @@ def learned_study(args):
     }
     if len(variants) > 1:
         line["rotated_ligand_moments"] = figures("rotated")
+    if ctxc is not None:
+        ms_c = float(np.mean(coarse_ex["ms"]))
+        line["coarse_exhaustive"] = {"coarse_N": args.coarse_n, "coarse_W": args.coarse_w,
+                                     "recall_best": coarse_ex["hits"] / E, "recall_within_1e-3": coarse_ex["hits_tol"] / E,
+                                     "ms": ms_c, "vs_plain": poses / (ms_c * 1e-3) / plain}
+        ctxc.close()
     for net in nets.values():
         net.close()
     ctx.close()
@@ -1155,6 +1209,12 @@ def main():
                     help="the network's ligand features: the moments of the ligand as given (fixed, the main "
                          "figures), of the ligand turned by each rotation (rotated), or both networks on the "
                          "same labels (both)")
+    ap.add_argument("--coarse-n", type=int, default=32, choices=[0, 32, 64],
+                    help="learned workload: also a coarse stage, correlations at this band limit between the "
+                         "network's ranking and the full correlations (0: off)")
+    ap.add_argument("--coarse-w", type=int, default=6, help="KB width of the coarse stage")
+    ap.add_argument("--coarse-keep", type=int, default=2048,
+                    help="rotations the network passes to the coarse stage")
     ap.add_argument("--augment", type=int, default=64,
                     help="extra random orientations of each training receptor (rotation augmentation)")
     args = ap.parse_args()

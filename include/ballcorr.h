@@ -474,6 +474,29 @@ bc_status bc_learned_sweep_cascade(bc_ctx_t ctx, bc_mlp_t net, bc_shape_t A, bc_
                                    int topk, const float *orients, int norient, int keep, int *idx, float *peak,
                                    int *argmax, float *scores);
 
+/* Learned sweep with a coarse stage: the network ranks the n rotations as
+ * bc_learned_sweep_cascade does (norient = 0 and keep = n: one view) and passes
+ * its best `coarse_keep` on; those are correlated on the coarse context `cctx`
+ * -- the same radius levels and period at a lower band limit (smaller N), with
+ * Ac and Bc the shapes A and B uploaded to it -- and ranked by their coarse
+ * peaks (max over cctx's translation grid, as bc_sweep computes them); the
+ * topk best get full correlations on ctx.  A coarse correlation is the same
+ * band-limited correlation (Eq. (ccghat)) with fewer modes: a smoother g whose
+ * peak ranks rotations by their overall overlap, which the network's moments
+ * rank less reliably.  Outputs (device) as bc_learned_sweep_cascade: idx[topk]
+ * (indices into quats, best coarse peak first, ties to the lower index),
+ * peak[topk], argmax[topk] (ctx's grid), scores[n] (one-view scores) when not
+ * NULL.  cctx's stream is ordered after ctx's for the coarse stage and ctx's
+ * after cctx's for the rest (events, when the streams differ).  Asynchronous.
+ * Errors as bc_learned_sweep_cascade (with coarse_keep in place of topk in
+ * the range checks), and BC_ERR_ARG for a null coarse context or shape, coarse
+ * shapes from another context or with other knot counts than A and B, a
+ * coarse context with other levels or period, or topk outside
+ * [1, coarse_keep]. */
+bc_status bc_learned_sweep_coarse(bc_ctx_t ctx, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
+                                  int topk, const float *orients, int norient, int keep, bc_ctx_t cctx, bc_shape_t Ac,
+                                  bc_shape_t Bc, int coarse_keep, int *idx, float *peak, int *argmax, float *scores);
+
 /* Top-k selection: idx[0..k) (device) = indices of the k largest of scores[0..n)
  * (device), largest first, equal scores ordered by lower index.  n <= BC_TOPK_MAX.
  * Asynchronous on ctx's stream.  Errors: BC_ERR_ARG, BC_ERR_CUDA. */

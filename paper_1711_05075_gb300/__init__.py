@@ -99,6 +99,7 @@ def lib():
         L.bc_learned_sweep.argtypes = [vp, vp, vp, vp, vp, i, i, vp, vp, vp, vp]
         L.bc_learned_sweep_avg.argtypes = [vp, vp, vp, vp, vp, i, i, vp, i, vp, vp, vp, vp]
         L.bc_learned_sweep_cascade.argtypes = [vp, vp, vp, vp, vp, i, i, vp, i, i, vp, vp, vp, vp]
+        L.bc_learned_sweep_coarse.argtypes = [vp, vp, vp, vp, vp, i, i, vp, i, i, vp, vp, vp, i, vp, vp, vp, vp]
         L.bc_topk.argtypes = [vp, vp, i, i, vp]
         L.bc_sweep_plan.argtypes = [vp, vp, vp, vp, i, i, vp, vp, ctypes.POINTER(vp)]
         L.bc_plan_run.argtypes = [vp]
@@ -109,7 +110,7 @@ def lib():
         for f in ("bc_shape_moments", "bc_shape_moments_rot", "bc_mlp_features_rows", "bc_mlp_set_features",
                   "bc_mlp_create", "bc_mlp_destroy", "bc_mlp_features", "bc_mlp_predict",
                   "bc_mlp_grads", "bc_mlp_train_step", "bc_mlp_train", "bc_mlp_state", "bc_learned_sweep",
-                  "bc_learned_sweep_avg", "bc_learned_sweep_cascade"):
+                  "bc_learned_sweep_avg", "bc_learned_sweep_cascade", "bc_learned_sweep_coarse"):
             getattr(L, f).restype = st
         L.bc_selftest_wait.argtypes = [vp]
         for f in ("bc_create", "bc_destroy", "bc_shape_create", "bc_shapes_create", "bc_shape_destroy", "bc_correlate",
@@ -638,20 +639,31 @@ def moments_rot(ctx: Context, shape, quats_dev) -> "torch.Tensor":
     return out
 
 
-def learned_sweep(ctx: Context, net: MLP, A, B, quats_dev, topk, orientations=None, keep=None):
+def learned_sweep(ctx: Context, net: MLP, A, B, quats_dev, topk, orientations=None, keep=None, coarse=None):
     """(idx, peak, argmax, scores) CUDA tensors: network scores of all rotations, the topk
     best, and the correlation peaks of those.  With `orientations` (k x 4 host quaternions)
     the scores are averaged over the receptor turned by each of them
     (bc_learned_sweep_avg); with `keep` as well, only the best `keep` rotations of the
     one-view scores are scored again (bc_learned_sweep_cascade; scores are then the
-    one-view scores)."""
+    one-view scores).  With coarse = (cctx, Ac, Bc, coarse_keep) the network's best
+    coarse_keep are correlated on the coarse context first and the topk best of those by
+    their coarse peaks get full correlations (bc_learned_sweep_coarse; keep defaults to
+    all rotations)."""
     import torch
     n = quats_dev.shape[0]
     idx = torch.empty(topk, dtype=torch.int32, device="cuda")
     peak = torch.empty(topk, dtype=torch.float32, device="cuda")
     arg = torch.empty(topk, dtype=torch.int32, device="cuda")
     scores = torch.empty(n, dtype=torch.float32, device="cuda")
-    if keep is not None:
+    if coarse is not None:
+        cctx, Ac, Bc, ckeep = coarse
+        o = np.ascontiguousarray(np.asarray(orientations if orientations is not None else np.zeros((0, 4)),
+                                            dtype=np.float32).reshape(-1, 4))
+        _check(lib().bc_learned_sweep_coarse(ctx.handle, net.handle, A.handle, B.handle, _ptr(quats_dev), int(n),
+                                             int(topk), _ptr(o), int(o.shape[0]), int(n if keep is None else keep),
+                                             cctx.handle, Ac.handle, Bc.handle, int(ckeep), _ptr(idx), _ptr(peak),
+                                             _ptr(arg), _ptr(scores)))
+    elif keep is not None:
         o = np.ascontiguousarray(np.asarray(orientations if orientations is not None else np.zeros((0, 4)),
                                             dtype=np.float32).reshape(-1, 4))
         _check(lib().bc_learned_sweep_cascade(ctx.handle, net.handle, A.handle, B.handle, _ptr(quats_dev), int(n),

@@ -184,6 +184,7 @@ struct bc_ctx_s {
     std::vector<cudaEvent_t> prof_ev; // prof_max x (BC_NUM_STAGES + 1)
     int last_ninst = 0, last_npairs = 0, last_mode = 0, last_back = 0, last_yz = 0;
     cudaStream_t capture_stream = nullptr; // private stream for recording graphs (the legacy stream cannot be captured)
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr; // orders a coarse context's stream with this one (bc_learned_sweep_coarse)
     bool replay = true;                    // repeated identical passes of direct calls replay a recorded graph
     std::vector<InstDesc> last_inst;
 };
@@ -426,6 +427,8 @@ bc_status bc_destroy(bc_ctx_t c)
         c->queries.clear();
         c->ws.release();
         if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+        if (c->ev_a) cudaEventDestroy(c->ev_a);
+        if (c->ev_b) cudaEventDestroy(c->ev_b);
         DevBuf *bufs[] = {&c->outbuf, &c->stats, &c->learn, &c->tune, &c->score_ft, &c->score_xw};
         for (DevBuf *b : bufs) b->release();
         c->hstats.release();
@@ -1564,82 +1567,172 @@ __global__ void k_compose_idx(const int *__restrict__ outer, const int *__restri
 }
 } // namespace
 
+// The network's ranking of the two-stage learned sweeps: stage 1 scores all n
+// rotations with one view and keeps the best `keep`; stage 2 scores those again
+// against the receptor turned by each orientation and ranks them by the mean of
+// the views; the best m are written to idx_out (indices into quats, device, m
+// ints) and their rotations to *q_out (device, 4 m floats, inside the learned
+// scratch); with idx_out null the indices go to the scratch as well, at
+// *picks.  `extra` bytes of the scratch, after the ranking's own, are handed to
+// the caller at *extra_out (256-byte aligned).  The caller validates.
+static bc_status learned_rank(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n, int m,
+                              const float *orients, int norient, int keep, float *scores, int *idx_out,
+                              const int **picks, const float **q_out, size_t extra, void **extra_out)
+{
+    cudaStream_t st = c->stream;
+    cudaError_t e;
+    const bool rot = bc_mlp_rotated_moments(net) != 0;
+    const size_t M = BC_MOMENTS, no = (size_t)norient, kp = (size_t)keep, N = (size_t)n;
+    // scratch (floats): receptor and ligand moments (2 M), features (n x 144), one-view
+    // scores (n), kept sums and scores (2 keep), kept and composed rotations (2 x 4 keep),
+    // selected rotations (4 m), turned-receptor moments (norient M) and orientations
+    // (4 norient), rotated-ligand moments (n M, when the network takes them); ints: kept
+    // and selected indices and the picks (keep + 2 m); then the caller's extra bytes
+    const size_t nf = 2 * M + N * 144 + N + 2 * kp + 8 * kp + 4 * (size_t)m + no * M + 4 * no + (rot ? N * M : 0);
+    const size_t own = ((sizeof(float) * nf + sizeof(int) * (kp + 2 * (size_t)m)) + 255) & ~(size_t)255;
+    if ((e = c->learn.ensure(own + extra, false, st)) != cudaSuccess) return cuda_fail(e, "learned scratch");
+    float *fa = (float *)c->learn.p, *fb = fa + M, *X = fb + M, *s0 = X + N * 144, *acc = s0 + N, *sc = acc + kp;
+    float *q1 = sc + kp, *qs = q1 + 4 * kp, *qsel = qs + 4 * kp, *fo = qsel + 4 * (size_t)m, *od = fo + no * M;
+    float *fbr = od + 4 * no;
+    int *i1 = (int *)(fbr + (rot ? N * M : 0)), *i2 = i1 + kp, *ip = i2 + m;
+    if (!idx_out) idx_out = ip;
+    if (picks) *picks = idx_out;
+    if (extra_out) *extra_out = (char *)c->learn.p + own;
+    auto features = [&](const float *q, int rows, const float *fA) -> bc_status {
+        if (!rot) return bc_mlp_features(net, q, rows, fA, fb, X);
+        cudaError_t e2 = launch_moments_rot(B->knots, B->n, q, rows, c->ballft, c->qmax + 1, c->g.L,
+                                            (float)(2.0 / c->period), fbr, c->err_dev, st);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "moments of the rotated ligand");
+        return bc_mlp_features_rows(net, q, rows, fA, fbr, X);
+    };
+    float *s_all = scores ? scores : s0;
+    // stage 1: one view for every rotation, keep the best `keep`
+    if (bc_status s = shape_moments(c, A, nullptr, fa)) return s;
+    if (!rot)
+        if (bc_status s = shape_moments(c, B, nullptr, fb)) return s;
+    if (bc_status s = features(quats, n, fa)) return s;
+    if (bc_status s = bc_mlp_predict(net, X, n, s_all)) return s;
+    if ((e = launch_topk(s_all, n, keep, i1, st)) != cudaSuccess) return cuda_fail(e, "top-k (kept)");
+    if ((e = launch_gather_quats(quats, i1, keep, q1, st)) != cudaSuccess) return cuda_fail(e, "gather kept rotations");
+    k_gather_scores<<<(keep + 255) / 256, 256, 0, st>>>(s_all, i1, keep, acc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gather kept scores");
+    // stage 2: the kept rotations against the receptor turned by each orientation S_k,
+    // whose moments come from one direct-sum launch over all orientations
+    if (norient > 0) {
+        if ((e = cudaMemcpyAsync(od, orients, sizeof(float) * 4 * no, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "orientations");
+        if ((e = launch_moments_rot(A->knots, A->n, od, norient, c->ballft, c->qmax + 1, c->g.L,
+                                    (float)(2.0 / c->period), fo, c->err_dev, st)) != cudaSuccess)
+            return cuda_fail(e, "moments of the turned receptor");
+    }
+    for (int k = 0; k < norient; k++) {
+        if ((e = launch_compose_quats(orients + 4 * (size_t)k, q1, keep, qs, st)) != cudaSuccess)
+            return cuda_fail(e, "compose rotations");
+        if (bc_status s = features(qs, keep, fo + (size_t)k * M)) return s;
+        if (bc_status s = bc_mlp_predict(net, X, keep, sc)) return s;
+        if ((e = launch_axpby(acc, sc, keep, 1.f, 1.f, st)) != cudaSuccess) return cuda_fail(e, "score sum");
+    }
+    if (norient > 0 && (e = launch_axpby(acc, acc, keep, 1.f / (float)(norient + 1), 0.f, st)) != cudaSuccess)
+        return cuda_fail(e, "score mean");
+    if ((e = launch_topk(acc, keep, m, i2, st)) != cudaSuccess) return cuda_fail(e, "top-k");
+    k_compose_idx<<<(m + 255) / 256, 256, 0, st>>>(i1, i2, m, idx_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "rotation indices");
+    if ((e = launch_gather_quats(q1, i2, m, qsel, st)) != cudaSuccess) return cuda_fail(e, "gather rotations");
+    *q_out = qsel;
+    return BC_OK;
+}
+
+// Arguments shared by the two-stage learned sweeps.
+static bc_status check_learned(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
+                               int topk, const float *orients, int norient, int keep, int *idx, float *peak,
+                               int *argmax, const char *who)
+{
+    if (!c || !net || !A || !B || !quats || !idx || !peak || !argmax) return fail(BC_ERR_ARG, std::string(who) + ": null argument");
+    if (A->ctx != c || B->ctx != c) return fail(BC_ERR_ARG, std::string(who) + ": shapes belong to another context");
+    if (n < 1 || n > BC_TOPK_MAX) return fail(BC_ERR_ARG, std::string(who) + ": n must be in [1, 16384]");
+    if (keep < 1 || keep > n) return fail(BC_ERR_ARG, std::string(who) + ": keep must be in [1, n]");
+    if (topk < 1 || topk > keep) return fail(BC_ERR_ARG, std::string(who) + ": topk must be in [1, keep]");
+    if (norient < 0 || (norient > 0 && !orients))
+        return fail(BC_ERR_ARG, std::string(who) + ": norient < 0, or orientations missing");
+    if (A->n == 0 || B->n == 0) return fail(BC_ERR_ARG, std::string(who) + ": empty shape (f(0) = 0)");
+    if (norient > 0)
+        if (bc_status s = check_quats(orients, norient, who)) return s;
+    return BC_OK;
+}
+
 bc_status bc_learned_sweep_cascade(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
                                    int topk, const float *orients, int norient, int keep, int *idx, float *peak,
                                    int *argmax, float *scores)
 {
     try {
-        if (!c || !net || !A || !B || !quats || !idx || !peak || !argmax)
-            return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: null argument");
-        if (A->ctx != c || B->ctx != c)
-            return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: shapes belong to another context");
-        if (n < 1 || n > BC_TOPK_MAX) return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: n must be in [1, 16384]");
-        if (keep < 1 || keep > n) return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: keep must be in [1, n]");
-        if (topk < 1 || topk > keep) return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: topk must be in [1, keep]");
-        if (norient < 0 || (norient > 0 && !orients))
-            return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: norient < 0, or orientations missing");
-        if (A->n == 0 || B->n == 0) return fail(BC_ERR_ARG, "bc_learned_sweep_cascade: empty shape (f(0) = 0)");
-        if (norient > 0)
-            if (bc_status s = check_quats(orients, norient, "bc_learned_sweep_cascade")) return s;
-        cudaStream_t st = c->stream;
-        cudaError_t e;
-        const bool rot = bc_mlp_rotated_moments(net) != 0;
-        const size_t M = BC_MOMENTS, no = (size_t)norient, kp = (size_t)keep, N = (size_t)n;
-        // scratch (floats): receptor and ligand moments (2 M), features (n x 144), one-view
-        // scores (n), kept sums and scores (2 keep), kept and composed rotations (2 x 4 keep),
-        // selected rotations (4 topk), turned-receptor moments (norient M) and orientations
-        // (4 norient), rotated-ligand moments (n M, when the network takes them); ints: kept
-        // and selected indices (keep + topk)
-        const size_t nf = 2 * M + N * 144 + N + 2 * kp + 8 * kp + 4 * (size_t)topk + no * M + 4 * no + (rot ? N * M : 0);
-        const size_t bytes = sizeof(float) * nf + sizeof(int) * (kp + (size_t)topk);
-        if ((e = c->learn.ensure(bytes, false, st)) != cudaSuccess) return cuda_fail(e, "learned scratch");
-        float *fa = (float *)c->learn.p, *fb = fa + M, *X = fb + M, *s0 = X + N * 144, *acc = s0 + N, *sc = acc + kp;
-        float *q1 = sc + kp, *qs = q1 + 4 * kp, *qsel = qs + 4 * kp, *fo = qsel + 4 * (size_t)topk, *od = fo + no * M;
-        float *fbr = od + 4 * no;
-        int *i1 = (int *)(fbr + (rot ? N * M : 0)), *i2 = i1 + kp;
-        auto features = [&](const float *q, int rows, const float *fA) -> bc_status {
-            if (!rot) return bc_mlp_features(net, q, rows, fA, fb, X);
-            cudaError_t e2 = launch_moments_rot(B->knots, B->n, q, rows, c->ballft, c->qmax + 1, c->g.L,
-                                                (float)(2.0 / c->period), fbr, c->err_dev, st);
-            if (e2 != cudaSuccess) return cuda_fail(e2, "moments of the rotated ligand");
-            return bc_mlp_features_rows(net, q, rows, fA, fbr, X);
-        };
-        float *s_all = scores ? scores : s0;
-        // stage 1: one view for every rotation, keep the best `keep`
-        if (bc_status s = shape_moments(c, A, nullptr, fa)) return s;
-        if (!rot)
-            if (bc_status s = shape_moments(c, B, nullptr, fb)) return s;
-        if (bc_status s = features(quats, n, fa)) return s;
-        if (bc_status s = bc_mlp_predict(net, X, n, s_all)) return s;
-        if ((e = launch_topk(s_all, n, keep, i1, st)) != cudaSuccess) return cuda_fail(e, "top-k (kept)");
-        if ((e = launch_gather_quats(quats, i1, keep, q1, st)) != cudaSuccess) return cuda_fail(e, "gather kept rotations");
-        k_gather_scores<<<(keep + 255) / 256, 256, 0, st>>>(s_all, i1, keep, acc);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gather kept scores");
-        // stage 2: the kept rotations against the receptor turned by each orientation S_k,
-        // whose moments come from one direct-sum launch over all orientations
-        if (norient > 0) {
-            if ((e = cudaMemcpyAsync(od, orients, sizeof(float) * 4 * no, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-                return cuda_fail(e, "orientations");
-            if ((e = launch_moments_rot(A->knots, A->n, od, norient, c->ballft, c->qmax + 1, c->g.L,
-                                        (float)(2.0 / c->period), fo, c->err_dev, st)) != cudaSuccess)
-                return cuda_fail(e, "moments of the turned receptor");
-        }
-        for (int k = 0; k < norient; k++) {
-            if ((e = launch_compose_quats(orients + 4 * (size_t)k, q1, keep, qs, st)) != cudaSuccess)
-                return cuda_fail(e, "compose rotations");
-            if (bc_status s = features(qs, keep, fo + (size_t)k * M)) return s;
-            if (bc_status s = bc_mlp_predict(net, X, keep, sc)) return s;
-            if ((e = launch_axpby(acc, sc, keep, 1.f, 1.f, st)) != cudaSuccess) return cuda_fail(e, "score sum");
-        }
-        if (norient > 0 && (e = launch_axpby(acc, acc, keep, 1.f / (float)(norient + 1), 0.f, st)) != cudaSuccess)
-            return cuda_fail(e, "score mean");
-        if ((e = launch_topk(acc, keep, topk, i2, st)) != cudaSuccess) return cuda_fail(e, "top-k");
-        k_compose_idx<<<(topk + 255) / 256, 256, 0, st>>>(i1, i2, topk, idx);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "rotation indices");
-        if ((e = launch_gather_quats(q1, i2, topk, qsel, st)) != cudaSuccess) return cuda_fail(e, "gather rotations");
+        if (bc_status s = check_learned(c, net, A, B, quats, n, topk, orients, norient, keep, idx, peak, argmax,
+                                        "bc_learned_sweep_cascade"))
+            return s;
+        const float *qsel = nullptr;
+        if (bc_status s = learned_rank(c, net, A, B, quats, n, topk, orients, norient, keep, scores, idx, nullptr,
+                                       &qsel, 0, nullptr))
+            return s;
         return sweep_impl(c, A, B, nullptr, qsel, topk, 0, peak, argmax, 1);
     } catch (...) {
         return fail(BC_ERR_INTERNAL, "bc_learned_sweep_cascade: unexpected exception");
+    }
+}
+
+bc_status bc_learned_sweep_coarse(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
+                                  int topk, const float *orients, int norient, int keep, bc_ctx_t cc, bc_shape_t Ac,
+                                  bc_shape_t Bc, int coarse_keep, int *idx, float *peak, int *argmax, float *scores)
+{
+    try {
+        const char *who = "bc_learned_sweep_coarse";
+        if (bc_status s = check_learned(c, net, A, B, quats, n, coarse_keep, orients, norient, keep, idx, peak,
+                                        argmax, who))
+            return s;
+        if (!cc || !Ac || !Bc) return fail(BC_ERR_ARG, "bc_learned_sweep_coarse: null coarse context or shape");
+        if (Ac->ctx != cc || Bc->ctx != cc)
+            return fail(BC_ERR_ARG, "bc_learned_sweep_coarse: coarse shapes belong to another context");
+        if (topk < 1 || topk > coarse_keep) return fail(BC_ERR_ARG, "bc_learned_sweep_coarse: topk must be in [1, coarse_keep]");
+        if (Ac->n != A->n || Bc->n != B->n)
+            return fail(BC_ERR_ARG, "bc_learned_sweep_coarse: coarse shapes have other knot counts than A and B");
+        if (cc->g.L != c->g.L || cc->period != c->period)
+            return fail(BC_ERR_ARG, "bc_learned_sweep_coarse: the coarse context has other levels or another period");
+        cudaStream_t st = c->stream;
+        cudaError_t e;
+        const size_t cm = (size_t)coarse_keep, tk = (size_t)topk;
+        // extra scratch: coarse peaks (cm floats), selected rotations (4 topk floats), coarse
+        // argmax (cm ints), the coarse ranking (topk ints)
+        const size_t extra = sizeof(float) * (cm + 4 * tk) + sizeof(int) * (cm + tk);
+        void *ex = nullptr;
+        const int *picks = nullptr;
+        const float *qm = nullptr;
+        // stages 1-2: the network's best coarse_keep
+        if (bc_status s = learned_rank(c, net, A, B, quats, n, coarse_keep, orients, norient, keep, scores, nullptr,
+                                       &picks, &qm, extra, &ex))
+            return s;
+        float *cpeak = (float *)ex, *qsel = cpeak + cm;
+        int *carg = (int *)(qsel + 4 * tk), *i3 = carg + cm;
+        // stage 3: their correlations at the coarse band limit, on the coarse context's stream
+        const bool two = cc->stream != st;
+        if (two) {
+            if (!c->ev_a && (e = cudaEventCreateWithFlags(&c->ev_a, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "event");
+            if (!c->ev_b && (e = cudaEventCreateWithFlags(&c->ev_b, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "event");
+            if ((e = cudaEventRecord(c->ev_a, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cc->stream, c->ev_a, 0)) != cudaSuccess)
+                return cuda_fail(e, "order the coarse stage after the ranking");
+        }
+        if (bc_status s = sweep_impl(cc, Ac, Bc, nullptr, qm, coarse_keep, 0, cpeak, carg, 1)) return s;
+        if (two) {
+            if ((e = cudaEventRecord(c->ev_b, cc->stream)) != cudaSuccess || (e = cudaStreamWaitEvent(st, c->ev_b, 0)) != cudaSuccess)
+                return cuda_fail(e, "order the full stage after the coarse one");
+        }
+        // stage 4: the best topk by their coarse peaks get full correlations
+        if ((e = launch_topk(cpeak, coarse_keep, topk, i3, st)) != cudaSuccess) return cuda_fail(e, "top-k (coarse)");
+        k_compose_idx<<<(topk + 255) / 256, 256, 0, st>>>(picks, i3, topk, idx);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "rotation indices");
+        if ((e = launch_gather_quats(qm, i3, topk, qsel, st)) != cudaSuccess) return cuda_fail(e, "gather rotations");
+        return sweep_impl(c, A, B, nullptr, qsel, topk, 0, peak, argmax, 1);
+    } catch (...) {
+        return fail(BC_ERR_INTERNAL, "bc_learned_sweep_coarse: unexpected exception");
     }
 }
 

@@ -29,7 +29,7 @@ def test_header_declares_the_boundary():
               "bc_lift_create", "bc_lift_correlate", "bc_lift_destroy", "bc_get_tuning", "bc_set_tuning", "bc_autotune",
               "bc_correlate_noalloc", "bc_selftest_wait", "bc_learned_sweep_avg", "bc_shape_moments_rot",
               "bc_mlp_features_rows", "bc_mlp_set_features", "bc_mlp_rotated_moments",
-              "bc_learned_sweep_cascade"):
+              "bc_learned_sweep_cascade", "bc_learned_sweep_coarse"):
         assert f in names
 
 

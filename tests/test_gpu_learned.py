@@ -167,3 +167,93 @@ def test_multi_step_training_matches_single_steps_and_is_deterministic(bc):
     for net in nets:
         net.close()
     ctx.close()
+
+
+def test_coarse_stage_matches_its_composed_calls(bc):
+    # bc_learned_sweep_coarse against the same stages composed from single calls:
+    # network scores -> top coarse_keep -> coarse sweep (N = 32) -> top K -> full
+    # sweep (N = 64).  The coarse context runs on a stream of its own (the entry
+    # point orders the two streams with events).  Fixed-point spreading on both
+    # contexts: the peaks do not depend on the batches, so both sides agree bit for bit.
+    dev = torch.device("cuda", 0)
+    ctx = bc.Context(64, 6, synth.RADII_4)
+    ctxc = bc.Context(32, 6, synth.RADII_4, stream=torch.cuda.Stream(dev))
+    ctx.set_tuning(spread=1)
+    ctxc.set_tuning(spread=1)
+    net = bc.MLP(ctx, 64, synth.mlp_init(64, 13))
+    A, B = pair(41)
+    hA, hB = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
+    hAc, hBc = ctxc.shape(A.xyz, A.level), ctxc.shape(B.xyz, B.level)
+    R, M, K = 2048, 256, 32
+    q = synth.shoemake_quaternions(synth.SplitMix64(17), R).astype(np.float32)
+    qd = torch.tensor(q, device=dev)
+    idx, peak, arg, scores = bc.learned_sweep(ctx, net, hA, hB, qd, K, coarse=(ctxc, hAc, hBc, M))
+    torch.cuda.synchronize(dev)
+    # the composed reference
+    s_ref = net.predict(net.features(qd, bc.moments(ctx, hA), bc.moments(ctx, hB)))
+    iM = torch.empty(M, dtype=torch.int32, device=dev)
+    bc.bc_topk(ctx.handle, s_ref, R, M, iM)
+    torch.cuda.synchronize(dev)
+    pc, _ = ctxc.sweep(hAc, hBc, q[iM.cpu().numpy()])
+    torch.cuda.synchronize(dev)
+    iK = torch.empty(K, dtype=torch.int32, device=dev)
+    bc.bc_topk(ctx.handle, pc, M, K, iK)
+    torch.cuda.synchronize(dev)
+    sel = iM.cpu().numpy()[iK.cpu().numpy()]
+    p_ref, a_ref = ctx.sweep(hA, hB, q[sel])
+    torch.cuda.synchronize(dev)
+    assert torch.equal(scores, s_ref)
+    np.testing.assert_array_equal(idx.cpu().numpy(), sel)
+    np.testing.assert_array_equal(peak.cpu().numpy(), p_ref.cpu().numpy())
+    np.testing.assert_array_equal(arg.cpu().numpy(), a_ref.cpu().numpy())
+    # the ranking is by coarse peak: the picks' coarse peaks are the largest M..K of them
+    pcs = np.sort(pc.cpu().numpy())[::-1]
+    got = pc.cpu().numpy()[iK.cpu().numpy()]
+    np.testing.assert_array_equal(np.sort(got)[::-1], pcs[:K])
+    with pytest.raises(bc.BallCorrError):  # topk above coarse_keep
+        bc.learned_sweep(ctx, net, hA, hB, qd, M + 1, coarse=(ctxc, hAc, hBc, M))
+    with pytest.raises(bc.BallCorrError):  # coarse shapes swapped (other knot counts)
+        bc.learned_sweep(ctx, net, hA, hB, qd, K, coarse=(ctxc, hBc, hAc, M))
+    for h in (hA, hB, hAc, hBc):
+        h.close()
+    net.close()
+    ctxc.close()
+    ctx.close()
+
+
+def test_coarse_stage_finds_the_exhaustive_best(bc):
+    # What the coarse stage gains at a small size: ranking every rotation by its peak
+    # at the coarse band limit (N = 32; coarse_keep = n, so the network does not
+    # matter) puts the exhaustive best at full resolution (N = 64) among the K picks,
+    # where a random choice of K holds it with probability K / R.
+    dev = torch.device("cuda", 0)
+    ctx = bc.Context(64, 6, synth.RADII_4)
+    ctxc = bc.Context(32, 6, synth.RADII_4)
+    ctx.set_tuning(spread=1)
+    ctxc.set_tuning(spread=1)
+    net = bc.MLP(ctx, 64, synth.mlp_init(64, 13))
+    R, K = 4096, 64
+    hits, ratios = 0, []
+    for seed in range(201, 207):
+        A, B = pair(seed)
+        hA, hB = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
+        hAc, hBc = ctxc.shape(A.xyz, A.level), ctxc.shape(B.xyz, B.level)
+        q = synth.shoemake_quaternions(synth.SplitMix64(seed + 300), R).astype(np.float32)
+        peak, _ = ctx.sweep(hA, hB, q, batch=256)
+        p = peak.cpu().numpy().astype(np.float64)
+        best = int(np.argmax(p))
+        idx, psel, _, _ = bc.learned_sweep(ctx, net, hA, hB, torch.tensor(q, device=dev), K,
+                                           coarse=(ctxc, hAc, hBc, R))
+        torch.cuda.synchronize(dev)
+        chosen = idx.cpu().numpy()
+        hits += best in set(chosen.tolist())
+        ratios.append(float(psel.max()) / p[best])
+        print(f"pair {seed}: exhaustive best in the coarse top-{K}: {best in set(chosen.tolist())}, "
+              f"best picked / best {ratios[-1]:.5f}")
+        for h in (hA, hB, hAc, hBc):
+            h.close()
+    print(f"coarse stage: {hits} of 6 (a random choice of {K} of {R}: {K / R:.3f} expected)")
+    assert hits >= 5 and min(ratios) > 0.99
+    net.close()
+    ctxc.close()
+    ctx.close()
