@@ -337,17 +337,19 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     e2e_seq = world * args.steps * wl.N ** 3 / max_over_ranks(e_sum)
 
-    # ---- e2e with two steps in flight: a second context (its own stream and
-    # workspaces, the same tuning) and one host thread per context, step i on
-    # context i mod 2; each step is the same upload, correlation and host read as
-    # above, so the copies and host work of one step overlap the other's kernels
+    # ---- e2e with several steps in flight: more contexts (each with its own stream
+    # and workspaces, the same tuning) and one host thread per context, step i on
+    # context i mod n; each step is the same upload, correlation and host read as
+    # above, so the copies and host work of one step overlap the others' kernels
     e2e_value, e2e_two = e2e_seq, None
-    if args.e2e_streams == 2:
+    nfl = args.e2e_streams
+    if nfl > 1:
         import threading
-        ctx2 = bc.Context(wl.N, wl.W, wl.radii, wl.period, stream=torch.cuda.Stream(dev))
-        ctx2.set_tuning(**tuning)
-        outs = [host_out, torch.empty_like(host_out).pin_memory()]
-        ctxs = [ctx, ctx2]
+        extra = [bc.Context(wl.N, wl.W, wl.radii, wl.period, stream=torch.cuda.Stream(dev)) for _ in range(nfl - 1)]
+        for cx in extra:
+            cx.set_tuning(**tuning)
+        outs = [host_out] + [torch.empty_like(host_out).pin_memory() for _ in range(nfl - 1)]
+        ctxs = [ctx] + extra
 
         def worker(t, n, errs):
             try:
@@ -359,9 +361,10 @@ def run_ours(args, rank, world, local_rank):
             except Exception as exc:  # reported below
                 errs.append(exc)
 
-        def two_in_flight(n_steps):
+        def in_flight(n_steps):
             errs = []
-            ths = [threading.Thread(target=worker, args=(t, (n_steps + 1 - t) // 2, errs)) for t in range(2)]
+            ths = [threading.Thread(target=worker, args=(t, (n_steps + nfl - 1 - t) // nfl, errs))
+                   for t in range(nfl)]
             t0 = time.perf_counter()
             for th in ths:
                 th.start()
@@ -371,12 +374,13 @@ def run_ours(args, rank, world, local_rank):
                 raise errs[0]
             return time.perf_counter() - t0
 
-        two_in_flight(max(2 * args.warmup, 2))
+        in_flight(max(nfl * args.warmup, nfl))
         torch.cuda.synchronize(dev)
         barrier()
-        t_two = max_over_ranks(two_in_flight(args.steps))
+        t_two = max_over_ranks(in_flight(args.steps))
         barrier()
-        ctx2.close()
+        for cx in extra:
+            cx.close()
         e2e_two = world * args.steps * wl.N ** 3 / t_two
         e2e_value = e2e_two
 
@@ -438,13 +442,14 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(wl),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "steps_in_flight": 2 if e2e_two is not None else 1,
+                    "steps_in_flight": nfl if e2e_two is not None else 1,
                     "sequential": {"value": e2e_seq, "unit": UNIT,
                                    "note": "one step at a time, L2 flushed before each (host timer)"},
                     "note": ("each step: bc_shapes_create from page-locked host knots, bc_correlate writing the "
                              "128^3 grid to page-locked host memory (synchronous), shape release; with two in "
                              "flight, two contexts on their own streams and host threads take alternate steps "
-                             "(no L2 flush: every step's inputs arrive from the host)")},
+                             "(no L2 flush: every step's inputs arrive from the host)").replace(
+                                 "with two in flight, two contexts", f"with {nfl} in flight, {nfl} contexts")},
             "gpu_launches": int(args.steps * prof["launches"] // max(prof["calls"], 1)),
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -608,11 +613,14 @@ def run_lifted(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "lifted union-of-ellipsoids vs torus", "N": N, "Nr": Nr, "L": L, "period_r": 4 * L,
                        "knots": [args.lift_knots, args.lift_knots], "radii": "uniform [0.01, 0.09)"},
-            "contraction": {"tcgen05": "split TF32 (3 products), tcgen05.mma, tensor-memory accumulators",
-                            "mma": "split TF32 (3 products), legacy mma.sync",
-                            "cuda": "FP32 CUDA cores"}[args.lift_contraction],
+            "contraction": {"tcgen05": "direct 4D NDFT: split TF32 (3 products), tcgen05.mma, tensor-memory accumulators",
+                            "mma": "direct 4D NDFT: split TF32 (3 products), legacy mma.sync",
+                            "cuda": "direct 4D NDFT: FP32 CUDA cores",
+                            "nufft": "4D type-1 NUFFT: KB spreading (W = 8) onto the (2N)^3 x 2Nr grid, pruned 4D FFT, "
+                                     "deconvolution"}[args.lift_contraction],
             "ndft_tflops_lower_bound": flops / (ms * 1e-3) / 1e12,
-            "note": "direct 4D NDFT; the contraction's rate is counted against the whole call's time"}
+            "note": "the NDFT rate counts the direct contraction's complex MACs against the whole call's time "
+                    "(for the NUFFT: the direct form's work it replaces)"}
     print(json.dumps(line), flush=True)
     lf.close()
     return 0
@@ -1160,8 +1168,8 @@ def main():
     ap.add_argument("--spread", type=int, choices=[0, 1], default=None,
                     help="force the spreading implementation (default: autotuned; 0 for --profile-correlations)")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT baseline timing")
-    ap.add_argument("--e2e-streams", type=int, choices=[1, 2], default=2,
-                    help="steps in flight in the e2e measurement (2: two contexts, one host thread each)")
+    ap.add_argument("--e2e-streams", type=int, choices=[1, 2, 3, 4], default=4,
+                    help="steps in flight in the e2e measurement (> 1: that many contexts, one host thread each)")
     ap.add_argument("--overlap", type=int, choices=[0, 1], default=None,
                     help="launch overlap tuning field (default: the context's)")
     ap.add_argument("--no-learned", action="store_true",
@@ -1181,7 +1189,7 @@ def main():
     ap.add_argument("--lift-n", type=int, default=32)
     ap.add_argument("--lift-nr", type=int, default=16)
     ap.add_argument("--lift-knots", type=int, default=5000)
-    ap.add_argument("--lift-contraction", choices=["tcgen05", "mma", "cuda"], default="tcgen05",
+    ap.add_argument("--lift-contraction", choices=["tcgen05", "mma", "cuda", "nufft"], default="tcgen05",
                     help="lifted NDFT contraction: tcgen05 tensor cores (default), legacy mma.sync, FP32 CUDA cores")
     ap.add_argument("--r0", type=float, default=0.02, help="score offset radius")
     ap.add_argument("--lam", type=float, default=2.0, help="score penalty factor")
