@@ -247,7 +247,8 @@ bc_status bc_query_destroy(bc_query_t q);
  * passes of 32,768 (their operands cost 16 N^2 + 16 N Nr bytes per knot), so
  * the workspace stays bounded for any knot count.  Errors: BC_ERR_ARG (null pointer, counts out of
  * range, zero quaternion, non-finite section), BC_ERR_UNSUPPORTED (N not 32,
- * 64, 96 or 128, Nr not 8, 16, 32 or 64), BC_ERR_OOM, BC_ERR_CUDA, BC_ERR_TIMEOUT (a
+ * 64, 96 or 128, Nr not 8, 16, 32 or 64, Nr = 8 with contraction 3),
+ * BC_ERR_OOM, BC_ERR_CUDA, BC_ERR_TIMEOUT (a
  * bounded wait inside the tcgen05 contraction expired; out is incomplete). */
 typedef struct bc_lift_s *bc_lift_t;
 typedef struct {
@@ -256,11 +257,14 @@ typedef struct {
     double L;        /* cone height */
     double period;   /* P, translation period */
     double period_r; /* P_r, period along the lifted axis */
-    int contraction; /* 4D NDFT contraction, all at FP32-level accuracy:
-                        2 tcgen05.mma tensor cores (accumulators in tensor memory, operands
-                          staged by bulk copies), 3-pass split TF32;
-                        1 mma.sync tensor cores, 3-pass split TF32;
-                        0 FP32 on the CUDA cores */
+    int contraction; /* how rho^ of Eq. (rhoAhat) is computed, all at FP32-level accuracy:
+                        2 direct 4D NDFT on the tcgen05.mma tensor cores (accumulators in
+                          tensor memory, operands staged by bulk copies), 3-pass split TF32;
+                        1 direct 4D NDFT on the mma.sync tensor cores, 3-pass split TF32;
+                        0 direct 4D NDFT in FP32 on the CUDA cores;
+                        3 4D type-1 NUFFT: Kaiser-Bessel spreading (width 8) of the lifted
+                          knots onto the (2N)^3 x 2Nr grid, a 4D FFT keeping the modes
+                          above, deconvolution (Nr >= 16; workspace 48 x 2Nr x N^3 bytes) */
 } bc_lift_params;
 bc_status bc_lift_create(const bc_lift_params *params, void *cuda_stream, bc_lift_t *out);
 bc_status bc_lift_correlate(bc_lift_t lift, const float *A, int nA, const float *B, int nB, const float *quat,

@@ -743,11 +743,12 @@ class Query:
             pass
 
 
-LIFT_CONTRACTIONS = {"tcgen05": 2, "mma": 1, "cuda": 0}
+LIFT_CONTRACTIONS = {"nufft": 3, "tcgen05": 2, "mma": 1, "cuda": 0}
 
 
 def bc_lift_create(N, Nr, L, period=2.0, period_r=None, stream=None, contraction="tcgen05"):
-    """contraction: "tcgen05" (default), "mma" (legacy mma.sync) or "cuda" (FP32 CUDA cores), or 2 / 1 / 0."""
+    """contraction: "tcgen05" (default), "mma" (legacy mma.sync), "cuda" (FP32 CUDA cores) -- the direct 4D
+    NDFT -- or "nufft" (the 4D type-1 NUFFT, Nr >= 16), or 2 / 1 / 0 / 3."""
     c = LIFT_CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
     p = bc_lift_params(int(N), int(Nr), float(L), float(period), float(4 * L if period_r is None else period_r), c)
     h = ctypes.c_void_p()

@@ -48,6 +48,7 @@
 
 #include "../../include/ballcorr.h"
 #include "bc_device.cuh"
+#include "bc_lift4.h"
 #include "bc_lift_umma.cuh"
 
 namespace bc {
@@ -495,6 +496,8 @@ struct bc_lift_s {
     int contraction = 2;
     double L = 0, period = 2, period_r = 0;
     float2 *cone = nullptr, *tw = nullptr;
+    Lift4Tables t4;            // contraction 3 (4D NUFFT): window and transform tables
+    void *t4_mem = nullptr;    // their storage
     void *ws = nullptr; // rho^_A, rho^_B, phase tables, h planes, slices, pair descriptors, staging
     size_t ws_bytes = 0;
     char *pin = nullptr; // pinned host staging: sections, pair descriptors, the error word
@@ -527,7 +530,10 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
     if (!(p->L > 0) || !std::isfinite(p->L)) return lift_fail(BC_ERR_ARG, "bc_lift_create: L must be > 0");
     if (!(p->period > 0) || !std::isfinite(p->period)) return lift_fail(BC_ERR_ARG, "bc_lift_create: period must be > 0");
     if (!(p->period_r > 0) || !std::isfinite(p->period_r)) return lift_fail(BC_ERR_ARG, "bc_lift_create: period_r must be > 0");
-    if (p->contraction < 0 || p->contraction > 2) return lift_fail(BC_ERR_ARG, "bc_lift_create: contraction must be 0, 1 or 2");
+    if (p->contraction < 0 || p->contraction > 3)
+        return lift_fail(BC_ERR_ARG, "bc_lift_create: contraction must be 0, 1, 2 or 3");
+    if (p->contraction == 3 && p->Nr < 16)
+        return lift_fail(BC_ERR_UNSUPPORTED, "bc_lift_create: the 4D NUFFT (contraction 3) needs Nr >= 16");
     bc_lift_s *lf = new (std::nothrow) bc_lift_s();
     if (!lf) return lift_fail(BC_ERR_OOM, "bc_lift_create: host allocation");
     lf->stream = (cudaStream_t)cuda_stream;
@@ -562,6 +568,32 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
                                                              g + LIFT_GAUSS, lf->cone);
     k_lift_twiddles<<<(lf->N + 63) / 64, 64, 0, lf->stream>>>(lf->N, lf->tw);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "bc_lift_create: tables");
+    if (lf->contraction == 3) {
+        // window (width 8, the default shape for oversampling 2, FP32-representable
+        // beta) and transform tables of the spatial and lifted axes
+        const int N = lf->N, Nr = lf->Nr, W = 8;
+        const double a = W / 2.0 * 1.5;
+        const double beta = (double)(float)(M_PI * std::sqrt(a * a - 0.8));
+        const size_t fl = (size_t)N + Nr + CONSTS_FLOATS + 2 * (size_t)N + 2 * (size_t)Nr;
+        const size_t bytes = sizeof(float) * fl + sizeof(float2) * (2 * (size_t)N + 2 * (size_t)Nr + N + Nr) + 256;
+        if ((e = cudaMalloc(&lf->t4_mem, bytes)) != cudaSuccess) return bail(e, "cudaMalloc NUFFT tables");
+        float2 *tw = (float2 *)lf->t4_mem; // n + n_r twiddles, then N + N_r scratch ones
+        lf->t4.tw_s = tw;
+        lf->t4.tw_r = tw + 2 * N;
+        float2 *twN = tw + 2 * N + 2 * Nr, *twNr = twN + N;
+        float *f = (float *)(twNr + Nr);
+        lf->t4.deconv_s = f;
+        lf->t4.deconv_r = f + N;
+        lf->t4.consts = f + N + Nr;
+        Geometry gs{}, gr{};
+        gs.N = N, gs.n = 2 * N, gs.W = W, gs.L = 0;
+        gr.N = Nr, gr.n = 2 * Nr, gr.W = W, gr.L = 0;
+        if ((e = launch_build_tables(gs, beta, lf->period, nullptr, lf->t4.deconv_s, nullptr, lf->t4.tw_s, twN,
+                                     lf->t4.consts, lf->stream)) != cudaSuccess ||
+            (e = launch_build_tables(gr, beta, lf->period_r, nullptr, lf->t4.deconv_r, nullptr, lf->t4.tw_r, twNr,
+                                     lf->t4.consts, lf->stream)) != cudaSuccess)
+            return bail(e, "bc_lift_create: NUFFT tables");
+    }
     if ((e = cudaStreamSynchronize(lf->stream)) != cudaSuccess) return bail(e, "bc_lift_create: sync");
     cudaFree(g);
     g = nullptr;
@@ -575,6 +607,7 @@ bc_status bc_lift_destroy(bc_lift_t lf)
     cudaStreamSynchronize(lf->stream);
     if (lf->cone) cudaFree(lf->cone);
     if (lf->tw) cudaFree(lf->tw);
+    if (lf->t4_mem) cudaFree(lf->t4_mem);
     if (lf->ws) cudaFree(lf->ws);
     if (lf->pin) cudaFreeHost(lf->pin);
     delete lf;
@@ -607,7 +640,8 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
     const size_t nchunk = nmax < (size_t)LIFT_CHUNK ? nmax : (size_t)LIFT_CHUNK;
     const int ld = nchunk > 0 ? (int)((nchunk + LIFT_KC - 1) / LIFT_KC) * LIFT_KC : LIFT_KC; // padded pass length
     // contraction 2: A blocks (hi, lo) 16 M ld bytes, B blocks 32 C ld bytes, fixed-point knots
-    const size_t e_bytes = lf->contraction == 2 ? (16 * M + 32 * C) * (size_t)ld + sizeof(LiftQ) * (nchunk + 1)
+    const size_t e_bytes = lf->contraction == 3 ? lift4_ws_bytes(N, Nr)
+                         : lf->contraction == 2 ? (16 * M + 32 * C) * (size_t)ld + sizeof(LiftQ) * (nchunk + 1)
                          : lf->contraction == 1 ? sizeof(float) * 2 * (M + C) * (size_t)ld + sizeof(LiftU) * (nchunk + 1)
                                                 : sizeof(float2) * (size_t)T * (nmax > 0 ? nmax : 1);
     const size_t plane = (size_t)N * N * H;
@@ -688,7 +722,14 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
             kper = ((kper + LIFT_KC - 1) / LIFT_KC) * LIFT_KC;
             return (len + kper - 1) / kper;
         };
-        if (lf->contraction == 2) {
+        if (lf->contraction == 3) {
+            const double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
+                                 2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
+                                 2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)};
+            if ((e = lift4_spectrum(lf->t4, N, Nr, kn, n, R, side, lf->period, lf->period_r, E, rho, lf->nsm, st)) !=
+                cudaSuccess)
+                return lift_cuda(e, "bc_lift_correlate: 4D NUFFT");
+        } else if (lf->contraction == 2) {
             const int mt = (int)(M / 128), ctn = (int)(C / 128);
             // A hi / lo: mt x nkb x 2 blocks of 128 x 32 floats = 2 M ld floats each;
             // B hi / lo: ctn x nkb x 2 blocks of 256 x 32 floats = 4 C ld floats each

@@ -68,6 +68,32 @@ def test_lifted_sections_match_oracle(bc, N, Nr, nA, nB, slices, contraction):
     lf.close()
 
 
+# the 4D type-1 NUFFT (contraction 3): spreading onto the (2N)^3 x 2Nr grid, 4D FFT,
+# deconvolution; the same sections as the direct NDFT within the same bar
+@pytest.mark.parametrize("N,Nr,nA,nB,slices", [(32, 32, 6, 6, (0.0, 0.03, -0.02)),
+                                                 (32, 16, 2000, 1500, (0.0, 0.04)),
+                                                 (64, 16, 800, 600, (0.0,)),
+                                                 (64, 32, 3000, 2000, (0.0, 0.02)),
+                                                 (96, 16, 300, 200, (0.0, 0.03)),
+                                                 (128, 16, 200, 150, (0.0,))])
+def test_lifted_nufft_matches_oracle_and_the_direct_form(bc, N, Nr, nA, nB, slices):
+    A = knots(synth.ellipsoid_shape(nA, 40 + nA), 1)
+    B = knots(synth.torus_shape(nB, 41 + nB), 2)
+    q = synth.shoemake_quaternions(synth.SplitMix64(42), 1)[0].astype(np.float32)
+    lf = bc.Lift(N, Nr, L, P, PR, contraction="nufft")
+    got = lf.correlate(A, B, q, slices).double().cpu().numpy()
+    lf.close()
+    ref = oracle(A, B, q, N, Nr, slices)
+    direct = bc.Lift(N, Nr, L, P, PR, contraction="tcgen05")
+    gd = direct.correlate(A, B, q, slices).double().cpu().numpy()
+    direct.close()
+    for s, rs in enumerate(slices):
+        e, ed = rel(got[s], ref[s]), rel(got[s], gd[s])
+        print(f"lifted NUFFT N={N} Nr={Nr} {nA}+{nB} knots, section {rs}: rel-L2 {e:.3e} (against the tcgen05 "
+              f"NDFT {ed:.3e})")
+        assert e <= REL_TOL and ed <= REL_TOL
+
+
 def test_lifted_arguments(bc):
     with pytest.raises(bc.BallCorrError) as e:
         bc.Lift(48, 16, L)
@@ -79,8 +105,11 @@ def test_lifted_arguments(bc):
     with pytest.raises(bc.BallCorrError):
         lf.correlate(A, A, synth.IDENTITY_QUAT[0], slices=np.zeros(17))
     with pytest.raises(bc.BallCorrError) as e:
-        bc.Lift(32, 8, L, contraction=3)
+        bc.Lift(32, 8, L, contraction=4)
     assert e.value.status == 1
+    with pytest.raises(bc.BallCorrError) as e:  # the 4D NUFFT needs Nr >= 16
+        bc.Lift(32, 8, L, contraction=3)
+    assert e.value.status == 5
     # empty shapes give zero
     z = lf.correlate(np.zeros((0, 4), np.float32), A, synth.IDENTITY_QUAT[0])
     assert float(z.abs().max()) == 0.0
