@@ -1189,8 +1189,8 @@ def main():
     ap.add_argument("--lift-n", type=int, default=32)
     ap.add_argument("--lift-nr", type=int, default=16)
     ap.add_argument("--lift-knots", type=int, default=5000)
-    ap.add_argument("--lift-contraction", choices=["tcgen05", "mma", "cuda", "nufft"], default="tcgen05",
-                    help="lifted NDFT contraction: tcgen05 tensor cores (default), legacy mma.sync, FP32 CUDA cores")
+    ap.add_argument("--lift-contraction", choices=["tcgen05", "mma", "cuda", "nufft"], default="nufft",
+                    help="lifted spectrum: 4D type-1 NUFFT (default), or the direct NDFT on the tcgen05 tensor cores, legacy mma.sync or FP32 CUDA cores")
     ap.add_argument("--r0", type=float, default=0.02, help="score offset radius")
     ap.add_argument("--lam", type=float, default=2.0, help="score penalty factor")
     ap.add_argument("--mprime", type=int, default=4096, help="modes kept by a query")

@@ -746,9 +746,11 @@ class Query:
 LIFT_CONTRACTIONS = {"nufft": 3, "tcgen05": 2, "mma": 1, "cuda": 0}
 
 
-def bc_lift_create(N, Nr, L, period=2.0, period_r=None, stream=None, contraction="tcgen05"):
-    """contraction: "tcgen05" (default), "mma" (legacy mma.sync), "cuda" (FP32 CUDA cores) -- the direct 4D
-    NDFT -- or "nufft" (the 4D type-1 NUFFT, Nr >= 16), or 2 / 1 / 0 / 3."""
+def bc_lift_create(N, Nr, L, period=2.0, period_r=None, stream=None, contraction=None):
+    """contraction: "nufft" (the 4D type-1 NUFFT, Nr >= 16), or the direct 4D NDFT as "tcgen05", "mma" (legacy
+    mma.sync) or "cuda" (FP32 CUDA cores), or 3 / 2 / 1 / 0; None: "nufft" where Nr >= 16, else "tcgen05"."""
+    if contraction is None:
+        contraction = "nufft" if int(Nr) >= 16 else "tcgen05"
     c = LIFT_CONTRACTIONS[contraction] if isinstance(contraction, str) else int(contraction)
     p = bc_lift_params(int(N), int(Nr), float(L), float(period), float(4 * L if period_r is None else period_r), c)
     h = ctypes.c_void_p()
@@ -768,7 +770,7 @@ def bc_lift_destroy(lf):
 class Lift:
     """Lifted (4D) nonequiradius correlation (Sec. 3.2) on the current CUDA device and stream."""
 
-    def __init__(self, N, Nr, L, period=2.0, period_r=None, stream=None, contraction="tcgen05"):
+    def __init__(self, N, Nr, L, period=2.0, period_r=None, stream=None, contraction=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required (no CPU fallback)")

@@ -574,7 +574,7 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
         const int N = lf->N, Nr = lf->Nr, W = 8;
         const double a = W / 2.0 * 1.5;
         const double beta = (double)(float)(M_PI * std::sqrt(a * a - 0.8));
-        const size_t fl = (size_t)N + Nr + CONSTS_FLOATS + 2 * (size_t)N + 2 * (size_t)Nr;
+        const size_t fl = (size_t)N + Nr + CONSTS_FLOATS + 2 * (size_t)N + 2 * (size_t)Nr + 8;
         const size_t bytes = sizeof(float) * fl + sizeof(float2) * (2 * (size_t)N + 2 * (size_t)Nr + N + Nr) + 256;
         if ((e = cudaMalloc(&lf->t4_mem, bytes)) != cudaSuccess) return bail(e, "cudaMalloc NUFFT tables");
         float2 *tw = (float2 *)lf->t4_mem; // n + n_r twiddles, then N + N_r scratch ones
@@ -585,6 +585,8 @@ bc_status bc_lift_create(const bc_lift_params *p, void *cuda_stream, bc_lift_t *
         lf->t4.deconv_s = f;
         lf->t4.deconv_r = f + N;
         lf->t4.consts = f + N + Nr;
+        lf->t4.dbox = (int *)(lf->t4.consts + CONSTS_FLOATS);
+        if ((e = cudaMallocHost(&lf->t4.hbox, 8 * sizeof(int))) != cudaSuccess) return bail(e, "cudaMallocHost box");
         Geometry gs{}, gr{};
         gs.N = N, gs.n = 2 * N, gs.W = W, gs.L = 0;
         gr.N = Nr, gr.n = 2 * Nr, gr.W = W, gr.L = 0;
@@ -608,6 +610,7 @@ bc_status bc_lift_destroy(bc_lift_t lf)
     if (lf->cone) cudaFree(lf->cone);
     if (lf->tw) cudaFree(lf->tw);
     if (lf->t4_mem) cudaFree(lf->t4_mem);
+    if (lf->t4.hbox) cudaFreeHost(lf->t4.hbox);
     if (lf->ws) cudaFree(lf->ws);
     if (lf->pin) cudaFreeHost(lf->pin);
     delete lf;
