@@ -982,7 +982,7 @@ def learned_study(args):
         qn = synth.shoemake_quaternions(synth.SplitMix64(seed + 300000), R).astype(np.float32)
         qd = torch.tensor(qn, device=dev)
         ctx.set_tuning(spread=1)
-        peak, _ = ctx.sweep(hA, hB, qn, batch=256)  # the judge (reproducible peaks)
+        peak, _ = ctx.sweep(hA, hB, qn, batch=256)  # the recall reference (reproducible peaks)
         ctx.set_tuning(spread=0)
         e0, e1 = ev(), ev()
         e0.record(stream)

@@ -418,18 +418,25 @@ k_lift_gemm_tc(const float *__restrict__ p1re, const float *__restrict__ p1im, c
 
 // h[s][jx][jy][mz] = sign scale sum_eta rho^_A conj(rho^_B) cone^2 exp(2 pi i eta r_s / P_r),
 // zero on the lower-edge modes; scale = P^-3 P_r^-1, sign = (-1)^(m_x + m_y + m_z).
+// NS >= nslices sections are accumulated in registers (the phases of the
+// sections beyond nslices are zero, and those sums are not written).
+template <int NS>
 __global__ void k_lift_collapse(const float2 *__restrict__ ra, const float2 *__restrict__ rb,
                                 const float2 *__restrict__ cone, int N, int Nr, const float *__restrict__ slices,
                                 int nslices, double period_r, float scale, float2 *h)
 {
-    __shared__ float2 ph[LIFT_MAX_SLICES][64];
-    for (int e = threadIdx.x; e < nslices * Nr; e += blockDim.x) {
+    __shared__ float2 ph[NS][64];
+    for (int e = threadIdx.x; e < NS * Nr; e += blockDim.x) {
         const int s = e / Nr, k = e - s * Nr;
-        double arg = lift_mode(k, Nr) * (double)slices[s] / period_r;
-        arg -= rint(arg);
-        double sn, cs;
-        sincospi(2.0 * arg, &sn, &cs);
-        ph[s][k] = make_float2((float)cs, (float)sn);
+        float2 v = make_float2(0.f, 0.f);
+        if (s < nslices) {
+            double arg = lift_mode(k, Nr) * (double)slices[s] / period_r;
+            arg -= rint(arg);
+            double sn, cs;
+            sincospi(2.0 * arg, &sn, &cs);
+            v = make_float2((float)cs, (float)sn);
+        }
+        ph[s][k] = v;
     }
     __syncthreads();
     const int H = N / 2;
@@ -438,23 +445,52 @@ __global__ void k_lift_collapse(const float2 *__restrict__ ra, const float2 *__r
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
         const int jx = u / (N * H), rem = u - jx * (N * H);
         const int jy = rem / H, mz = rem - jy * H;
-        float2 acc[LIFT_MAX_SLICES];
-        for (int s = 0; s < nslices; s++) acc[s] = make_float2(0.f, 0.f);
+        float2 acc[NS];
+#pragma unroll
+        for (int s = 0; s < NS; s++) acc[s] = make_float2(0.f, 0.f);
         if (jx != N / 2 && jy != N / 2) {
             const int mx = lift_mode(jx, N), my = lift_mode(jy, N);
             const int q = mx * mx + my * my + mz * mz;
             const long long base = (long long)(jx * N + jy) * (H * Nr) + (long long)mz * Nr;
-            for (int k = 0; k < Nr; k++) {
-                if (k == Nr / 2) continue;
-                const float2 f = cone[q * Nr + k];
-                const float2 p = cmul(cmulc(ra[base + k], rb[base + k]), cmul(f, f));
-                for (int s = 0; s < nslices; s++) acc[s] = cadd(acc[s], cmul(p, ph[s][k]));
+            // two modes eta per 16-byte load (each thread's N_r values are contiguous, so
+            // every sector a warp fetches is used whole)
+            const float4 *a4 = reinterpret_cast<const float4 *>(ra + base), *b4 = reinterpret_cast<const float4 *>(rb + base),
+                         *c4 = reinterpret_cast<const float4 *>(cone + (long long)q * Nr);
+            for (int k2 = 0; k2 < Nr / 2; k2++) {
+                const float4 av = a4[k2], bv = b4[k2], fv = c4[k2];
+#pragma unroll
+                for (int hh = 0; hh < 2; hh++) {
+                    const int k = 2 * k2 + hh;
+                    if (k == Nr / 2) continue;
+                    const float2 a = hh ? make_float2(av.z, av.w) : make_float2(av.x, av.y);
+                    const float2 b = hh ? make_float2(bv.z, bv.w) : make_float2(bv.x, bv.y);
+                    const float2 f = hh ? make_float2(fv.z, fv.w) : make_float2(fv.x, fv.y);
+                    const float2 p = cmul(cmulc(a, b), cmul(f, f));
+#pragma unroll
+                    for (int s = 0; s < NS; s++) acc[s] = cadd(acc[s], cmul(p, ph[s][k]));
+                }
             }
             const float sg = ((mx + my + mz) & 1) ? -scale : scale;
-            for (int s = 0; s < nslices; s++) acc[s] = cscale(acc[s], sg);
+#pragma unroll
+            for (int s = 0; s < NS; s++) acc[s] = cscale(acc[s], sg);
         }
-        for (int s = 0; s < nslices; s++) h[s * plane + u] = acc[s];
+#pragma unroll
+        for (int s = 0; s < NS; s++)
+            if (s < nslices) h[s * plane + u] = acc[s];
     }
+}
+
+static cudaError_t launch_lift_collapse(const float2 *ra, const float2 *rb, const float2 *cone, int N, int Nr,
+                                        const float *slices, int nslices, double period_r, float scale, float2 *h,
+                                        cudaStream_t st)
+{
+    const int blocks = (int)(((long long)N * N * (N / 2) + 255) / 256);
+    if (nslices <= 1) k_lift_collapse<1><<<blocks, 256, 0, st>>>(ra, rb, cone, N, Nr, slices, nslices, period_r, scale, h);
+    else if (nslices <= 2) k_lift_collapse<2><<<blocks, 256, 0, st>>>(ra, rb, cone, N, Nr, slices, nslices, period_r, scale, h);
+    else if (nslices <= 4) k_lift_collapse<4><<<blocks, 256, 0, st>>>(ra, rb, cone, N, Nr, slices, nslices, period_r, scale, h);
+    else if (nslices <= 8) k_lift_collapse<8><<<blocks, 256, 0, st>>>(ra, rb, cone, N, Nr, slices, nslices, period_r, scale, h);
+    else k_lift_collapse<16><<<blocks, 256, 0, st>>>(ra, rb, cone, N, Nr, slices, nslices, period_r, scale, h);
+    return cudaGetLastError();
 }
 
 // Inverse along x, in place: item (slice, jy, chunk of 16 z-modes); 16 lines
@@ -776,8 +812,8 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
         if ((e = cudaGetLastError()) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: spectrum");
     }
     const float scale = (float)(1.0 / (lf->period * lf->period * lf->period * lf->period_r));
-    k_lift_collapse<<<(int)((plane + 255) / 256), 256, 0, st>>>(rhoA, rhoB, lf->cone, N, Nr, dsl, nslices, lf->period_r,
-                                                                 scale, h);
+    if ((e = launch_lift_collapse(rhoA, rhoB, lf->cone, N, Nr, dsl, nslices, lf->period_r, scale, h, st)) != cudaSuccess)
+        return lift_cuda(e, "bc_lift_correlate: collapse");
     switch (N) {
     case 32: k_lift_ifft_x<32><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw); break;
     case 64: k_lift_ifft_x<64><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw); break;

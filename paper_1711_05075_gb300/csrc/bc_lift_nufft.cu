@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(TB) k_l4_mid(const float2 *__restrict__ in, fl
 
 // Transform along r (length NF = n_r), keep N_r = NF/2 modes, deconvolve in all
 // four axes, undo the half-period shift and write rho^ in the contraction
-// layout.  X1[i_r][j_x][j_y][m_z], box element i_r at position (lo + i_r) mod NF.
+// layout.  X1[j_x][j_y][i_r][m_z] (the b box planes of a mode row are 512-byte
+// neighbours), box element i_r at position (lo + i_r) mod NF.
 template <int NF>
 __global__ void __launch_bounds__(TB) k_l4_r(const float2 *__restrict__ X1, float2 *rho, int N, int lo, int b,
                                              const float *__restrict__ dxs, const float *__restrict__ drr,
@@ -219,18 +220,17 @@ __global__ void __launch_bounds__(TB) k_l4_r(const float2 *__restrict__ X1, floa
     constexpr int KEEP = NF / 2;
     for (int k = threadIdx.x; k < NF; k += TB) tw[k] = twg[k];
     const int H = N / 2, nch = H / CL;
-    const long long plane = (long long)N * N * H;
     const long long tiles = (long long)N * N * nch;
     for (long long tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
         const int o = (int)(tt / nch), ch = (int)(tt - (long long)o * nch);
         const int jx = o / N, jy = o - jx * N;
-        const float2 *src = X1 + (long long)o * H + CL * ch;
+        const float2 *src = X1 + (long long)o * b * H + CL * ch;
         __syncthreads();
         for (int e = threadIdx.x; e < CL * NF; e += TB) {
             const int pos = e / CL, c = e - pos * CL;
             int i = (pos - lo) % NF;
             i = i < 0 ? i + NF : i;
-            A[e] = i < b ? src[i * plane + c] : make_float2(0.f, 0.f);
+            A[e] = i < b ? src[(long long)i * H + c] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
@@ -361,11 +361,11 @@ cudaError_t lift4_spectrum(const Lift4Tables &t, int N, int Nr, const float4 *kn
     if ((e = mid(Z1, Y1, (long long)bR * bX, 1, (long long)bY * H, 0, H, (long long)N * H, 0, H, bx.lo[1], bY)) !=
         cudaSuccess)
         return e;
-    // x: outer (i_r, j_y), Y1[i_r][i_x][j_y][m_z] -> X1[i_r][j_x][j_y][m_z]
-    if ((e = mid(Y1, X1, (long long)bR * N, N, (long long)bX * N * H, H, (long long)N * H, (long long)N * N * H, H,
-                 (long long)N * H, bx.lo[0], bX)) != cudaSuccess)
+    // x: outer (i_r, j_y), Y1[i_r][i_x][j_y][m_z] -> X1[j_x][j_y][i_r][m_z]
+    if ((e = mid(Y1, X1, (long long)bR * N, N, (long long)bX * N * H, H, (long long)N * H, H, (long long)bR * H,
+                 (long long)N * bR * H, bx.lo[0], bX)) != cudaSuccess)
         return e;
-    // r: X1[i_r][j_x][j_y][m_z] -> rho[(j_x N + j_y)][m_z][k], deconvolved
+    // r: X1[j_x][j_y][i_r][m_z] -> rho[(j_x N + j_y)][m_z][k], deconvolved
     switch (nr) {
     case 32: return l4_r<32>(X1, rho, N, bx.lo[3], bR, t.deconv_s, t.deconv_r, t.tw_r, nsm, s);
     case 64: return l4_r<64>(X1, rho, N, bx.lo[3], bR, t.deconv_s, t.deconv_r, t.tw_r, nsm, s);

@@ -94,6 +94,30 @@ def test_lifted_nufft_matches_oracle_and_the_direct_form(bc, N, Nr, nA, nB, slic
         assert e <= REL_TOL and ed <= REL_TOL
 
 
+def test_lifted_nufft_box_falls_back_to_whole_axes(bc):
+    # knots on both sides of the period boundary in x (and spread over all of z): the
+    # support box of those axes is the whole axis, the others stay boxes; radii outside
+    # (0, L) as well (the r box then widens, still without wrapping errors)
+    N, Nr = 32, 16
+    rng = synth.SplitMix64(77)
+    n = 300
+    xyz = np.stack([0.97 * np.sign(rng.uniform(n) - 0.5), 0.3 * (rng.uniform(n) - 0.5), 1.9 * (rng.uniform(n) - 0.5)],
+                   axis=1)
+    r = 0.01 + 0.15 * rng.uniform(n)
+    A = np.concatenate([xyz, r[:, None]], axis=1).astype(np.float32)
+    B = knots(synth.torus_shape(250, 79), 80)
+    q = synth.shoemake_quaternions(synth.SplitMix64(81), 1)[0].astype(np.float32)
+    slices = (0.0, 0.05)
+    lf = bc.Lift(N, Nr, L, P, PR, contraction="nufft")
+    got = lf.correlate(A, B, q, slices).double().cpu().numpy()
+    lf.close()
+    ref = oracle(A, B, q, N, Nr, slices)
+    for s, rs in enumerate(slices):
+        e = rel(got[s], ref[s])
+        print(f"lifted NUFFT, knots across the period boundary, section {rs}: rel-L2 {e:.3e}")
+        assert e <= REL_TOL
+
+
 def test_lifted_arguments(bc):
     with pytest.raises(bc.BallCorrError) as e:
         bc.Lift(48, 16, L)
