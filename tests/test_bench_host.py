@@ -45,3 +45,27 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["sample"].startswith("full workload") and "20000+20000 knots" in cb["sample"]
     # the timed steps are whole oracle runs: the line's time is what was measured
     assert line["warmup"] >= 3 and line["steps"] == 1 and line["ms_per_step"] > 0
+
+
+def test_learned_target_picks_the_fastest_form_that_meets_it():
+    ls = {"recall_best_in_topk": 0.4, "recall_within_1e-3_of_best": 0.6, "learned_vs_plain": 200.0,
+          "ms_learned_sweep": 9.0,
+          "cascade": {"recall_best": 0.75, "recall_within_1e-3": 0.85, "vs_plain": 97.0, "ms_learned_sweep": 19.0},
+          "coarse": {"recall_best": 1.0, "recall_within_1e-3": 1.0, "vs_plain": 95.0, "ms_learned_sweep": 20.0},
+          "rotated_ligand_moments": {"recall_best_in_topk": 0.6, "recall_within_1e-3_of_best": 0.7,
+                                     "learned_vs_plain": 170.0, "ms_learned_sweep": 11.0,
+                                     "coarse": {"recall_best": 0.95, "recall_within_1e-3": 1.0, "vs_plain": 88.0,
+                                                "ms_learned_sweep": 21.0}},
+          "config": {"eval_pairs": 20, "topk": 256}}
+    t = bench.learned_target(ls)
+    assert t["met"] and t["recall_best"] == 1.0 and t["vs_plain"] == 95.0 and "coarse stage" in t["form"]
+    assert "configuration's ligand moments" in t["form"] and t["held_out_pairs"] == 20
+    # no form meets the target: the best recall is reported, met is false
+    ls["coarse"]["recall_best"] = 0.9
+    ls["rotated_ligand_moments"]["coarse"]["recall_best"] = 0.85
+    t = bench.learned_target(ls)
+    assert not t["met"] and t["recall_best"] == 0.9
+    # a form above the recall bar but below 10x plain does not count
+    ls["coarse"].update(recall_best=1.0, vs_plain=8.0)
+    t = bench.learned_target(ls)
+    assert not t["met"]

@@ -257,3 +257,41 @@ def test_coarse_stage_finds_the_exhaustive_best(bc):
     net.close()
     ctxc.close()
     ctx.close()
+
+
+def test_coarse_stage_after_orientation_average_ranks_the_cascade_picks(bc):
+    # With orientations, the network's ranking is bc_learned_sweep_cascade's (one view,
+    # then the orientation average for the best `keep`); the coarse stage must take
+    # exactly the cascade's best coarse_keep, and pick its K among them by coarse peak.
+    dev = torch.device("cuda", 0)
+    ctx = bc.Context(64, 6, synth.RADII_4)
+    ctxc = bc.Context(32, 6, synth.RADII_4)
+    ctx.set_tuning(spread=1)
+    ctxc.set_tuning(spread=1)
+    net = bc.MLP(ctx, 64, synth.mlp_init(64, 19), rotated_moments=True)
+    A, B = pair(43)
+    hA, hB = ctx.shape(A.xyz, A.level), ctx.shape(B.xyz, B.level)
+    hAc, hBc = ctxc.shape(A.xyz, A.level), ctxc.shape(B.xyz, B.level)
+    R, keep, M, K = 2048, 512, 128, 16
+    q = synth.shoemake_quaternions(synth.SplitMix64(23), R).astype(np.float32)
+    qd = torch.tensor(q, device=dev)
+    orients = synth.shoemake_quaternions(synth.SplitMix64(29), 3).astype(np.float32)
+    iM, _, _, s1 = bc.learned_sweep(ctx, net, hA, hB, qd, M, orientations=orients, keep=keep)
+    idx, peak, _, s2 = bc.learned_sweep(ctx, net, hA, hB, qd, K, orientations=orients, keep=keep,
+                                        coarse=(ctxc, hAc, hBc, M))
+    torch.cuda.synchronize(dev)
+    assert torch.equal(s1, s2)  # the same one-view scores
+    cand = iM.cpu().numpy()
+    got = idx.cpu().numpy()
+    assert set(got.tolist()) <= set(cand.tolist()) and len(set(got.tolist())) == K
+    pc, _ = ctxc.sweep(hAc, hBc, q[cand])
+    pc = pc.cpu().numpy()
+    order = cand[np.argsort(-pc, kind="stable")[:K]]  # coarse ranking, ties to the earlier candidate
+    np.testing.assert_array_equal(got, order)
+    pf, _ = ctx.sweep(hA, hB, q[got])
+    np.testing.assert_array_equal(peak.cpu().numpy(), pf.cpu().numpy())
+    for h in (hA, hB, hAc, hBc):
+        h.close()
+    net.close()
+    ctxc.close()
+    ctx.close()
