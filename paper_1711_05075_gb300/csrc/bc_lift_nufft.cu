@@ -19,7 +19,8 @@
 //   k_l4_spread   one warp per knot: the 4W window weights by the lanes, then
 //                 the W^4 stencil cells with atomic adds into the real grid
 //                 [g_r][g_x][g_y][g_z];
-//   k_l4_z        transform along z (real lines, 16 per tile), keep m_z < N/2;
+//   k_l4_z        transform along z (two real lines per complex line, 32 per
+//                 tile), keep m_z < N/2;
 //   k_l4_mid      transform along y, then along x (16 adjacent lines per tile,
 //                 one 128-byte row per position), keep N modes each;
 //   k_l4_r        transform along r, keep N_r modes, deconvolve, write rho^.
@@ -137,8 +138,10 @@ k_l4_spread(const float4 *__restrict__ knots, int n, L4Rot rot, int mirror, int 
     }
 }
 
-// Transform along z of the box grid's lines (b_r b_x b_y lines of b_z cells,
-// 16 consecutive lines per tile), Z1[line][m_z] for m_z < NF/4 (N/2).
+// Transform along z of the box grid's lines (b_r b_x b_y real lines of b_z
+// cells), two real lines per complex line (32 consecutive lines per tile): with
+// Z = FFT(a + i b), A_k = (Z_k + conj Z_{n-k}) / 2 and B_k = (Z_k - conj
+// Z_{n-k}) / (2i).  Z1[line][m_z] for m_z < NF/4 (N/2).
 template <int NF>
 __global__ void __launch_bounds__(TB) k_l4_z(const float *__restrict__ G, float2 *Z1, long long nlines, int bz, int loz,
                                              const float2 *__restrict__ twg)
@@ -147,22 +150,27 @@ __global__ void __launch_bounds__(TB) k_l4_z(const float *__restrict__ G, float2
     float2 *tw = l4sm, *A = tw + NF, *B = A + NF * CL;
     constexpr int H = NF / 4;
     for (int k = threadIdx.x; k < NF; k += TB) tw[k] = twg[k];
-    const long long tiles = (nlines + CL - 1) / CL;
+    const long long tiles = (nlines + 2 * CL - 1) / (2 * CL);
     for (long long tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
         __syncthreads();
         for (int e = threadIdx.x; e < CL * NF; e += TB) {
-            const int c = e / NF, pos = e - c * NF;
+            const int q = e / NF, pos = e - q * NF;
             int iz = (pos - loz) % NF;
             iz = iz < 0 ? iz + NF : iz;
-            const long long line = tt * CL + c;
-            A[pos * CL + c] = make_float2(line < nlines && iz < bz ? G[line * bz + iz] : 0.f, 0.f);
+            const long long l0 = tt * 2 * CL + 2 * q;
+            const bool in = iz < bz;
+            const float a = in && l0 < nlines ? G[l0 * bz + iz] : 0.f;
+            const float b = in && l0 + 1 < nlines ? G[(l0 + 1) * bz + iz] : 0.f;
+            A[pos * CL + q] = make_float2(a, b);
         }
         __syncthreads();
         const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
-        float2 *dst = Z1 + tt * CL * H;
-        for (int e = threadIdx.x; e < CL * H; e += TB) {
-            const int c = e / H, mz = e - c * H;
-            dst[e] = res[mz * CL + c];
+        float2 *dst = Z1 + tt * 2 * CL * H;
+        for (int e = threadIdx.x; e < 2 * CL * H; e += TB) {
+            const int r = e / H, mz = e - r * H, q = r >> 1;
+            const float2 zk = res[mz * CL + q], zn = res[(mz == 0 ? 0 : NF - mz) * CL + q];
+            dst[e] = (r & 1) ? make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x))
+                             : make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
         }
     }
 }
