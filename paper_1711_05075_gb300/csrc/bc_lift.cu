@@ -671,7 +671,7 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
     const int N = lf->N, Nr = lf->Nr, H = N / 2;
     const int T = 2 * N + H + Nr;
     const size_t M = (size_t)N * N, C = (size_t)H * Nr;
-    const size_t rho_bytes = sizeof(float2) * M * C;
+    const size_t rho_bytes = lf->contraction == 3 ? 0 : sizeof(float2) * M * C; // the NUFFT keeps no rho^
     const size_t nmax = (size_t)(nA > nB ? nA : nB);
     // the tensor-core contractions take the knots in passes of at most LIFT_CHUNK
     // (their operands cost 16 M + 32 C, resp. 8 (M + C), bytes per knot); each
@@ -742,6 +742,17 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
         (e = cudaMemcpyAsync(dpairs, ppairs, sizeof(PairDesc) * nslices, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return lift_cuda(e, "bc_lift_correlate: descriptors");
     if ((e = cudaMemsetAsync(derr, 0, sizeof(int), st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: error word");
+    const float scale = (float)(1.0 / (lf->period * lf->period * lf->period * lf->period_r));
+    if (lf->contraction == 3) {
+        // both spectra by the 4D NUFFT, their r transforms fused with the collapse
+        const double qw = quat[0] * inv, qx = quat[1] * inv, qy = quat[2] * inv, qz = quat[3] * inv;
+        const double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
+                             2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
+                             2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)};
+        if ((e = lift4_pair(lf->t4, N, Nr, kA, nA, kB, nB, R, lf->period, lf->period_r, lf->cone, dsl, nslices, scale, E,
+                            h, lf->nsm, st)) != cudaSuccess)
+            return lift_cuda(e, "bc_lift_correlate: 4D NUFFT");
+    } else {
     // both spectra are accumulated with atomics: one clear for the pair
     if ((e = cudaMemsetAsync(rhoA, 0, 2 * al(rho_bytes), st)) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: clear");
     // the two lifted spectra
@@ -761,14 +772,7 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
             kper = ((kper + LIFT_KC - 1) / LIFT_KC) * LIFT_KC;
             return (len + kper - 1) / kper;
         };
-        if (lf->contraction == 3) {
-            const double R[9] = {1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy),
-                                 2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx),
-                                 2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)};
-            if ((e = lift4_spectrum(lf->t4, N, Nr, kn, n, R, side, lf->period, lf->period_r, E, rho, lf->nsm, st)) !=
-                cudaSuccess)
-                return lift_cuda(e, "bc_lift_correlate: 4D NUFFT");
-        } else if (lf->contraction == 2) {
+        if (lf->contraction == 2) {
             const int mt = (int)(M / 128), ctn = (int)(C / 128);
             // A hi / lo: mt x nkb x 2 blocks of 128 x 32 floats = 2 M ld floats each;
             // B hi / lo: ctn x nkb x 2 blocks of 256 x 32 floats = 4 C ld floats each
@@ -811,9 +815,9 @@ bc_status bc_lift_correlate(bc_lift_t lf, const float *A, int nA, const float *B
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return lift_cuda(e, "bc_lift_correlate: spectrum");
     }
-    const float scale = (float)(1.0 / (lf->period * lf->period * lf->period * lf->period_r));
     if ((e = launch_lift_collapse(rhoA, rhoB, lf->cone, N, Nr, dsl, nslices, lf->period_r, scale, h, st)) != cudaSuccess)
         return lift_cuda(e, "bc_lift_correlate: collapse");
+    }
     switch (N) {
     case 32: k_lift_ifft_x<32><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw); break;
     case 64: k_lift_ifft_x<64><<<lf->nsm, TB, 0, st>>>(h, nslices, lf->tw); break;

@@ -17,10 +17,15 @@ struct Lift4Tables {
     int *hbox = nullptr;                            // and their page-locked host copy
 };
 size_t lift4_ws_bytes(int N, int Nr);
-// rho (N^2 x N/2 x N_r, overwritten) = the spectrum of Eq. (rhoAhat) of the n
-// knots (x, y, z, r) rotated by R (row major) and, with mirror, r -> -r; ws of
-// lift4_ws_bytes(N, Nr) bytes.  Synchronises s once (to size the support box).
-cudaError_t lift4_spectrum(const Lift4Tables &t, int N, int Nr, const float4 *knots, int n, const double (&R)[9],
-                           int mirror, double period, double period_r, void *ws, float2 *rho, int nsm, cudaStream_t s);
+// h[s][j_x][j_y][m_z] (N^2 x N/2 complex per section, the collapse of the
+// lifted correlation, as k_lift_collapse forms it from the two spectra) of the
+// knots kA (unrotated) and kB (rotated by RB, row major, and mirrored in r),
+// both spectra by the 4D NUFFT; cone = the cone transform table
+// ((3 (N/2)^2 + 1) x N_r), slices = device sections, scale = P^-3 P_r^-1; ws of
+// lift4_ws_bytes(N, Nr) bytes.  Synchronises s once per spectrum (to size its
+// support box).
+cudaError_t lift4_pair(const Lift4Tables &t, int N, int Nr, const float4 *kA, int nA, const float4 *kB, int nB,
+                       const double (&RB)[9], double period, double period_r, const float2 *cone, const float *slices,
+                       int nslices, float scale, void *ws, float2 *h, int nsm, cudaStream_t s);
 
 } // namespace bc

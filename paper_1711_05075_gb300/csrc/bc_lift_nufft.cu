@@ -1,10 +1,11 @@
-// The lifted spectrum rho^_X(xi, eta) of Eq. (rhoAhat) (Sec. 3.2) as a 4D
-// type-1 nonuniform FFT over (x, r), the alternative to the direct 4D NDFT
-// contractions of bc_lift.cu (contraction 3 of bc_lift_params).
+// The lifted spectra rho^_X(xi, eta) of Eq. (rhoAhat) (Sec. 3.2) as 4D type-1
+// nonuniform FFTs over (x, r), the alternative to the direct 4D NDFT
+// contractions of bc_lift.cu (contraction 3 of bc_lift_params), with the
+// collapse of the lifted correlation formed from them directly.
 //
 // Knot i of a shape, rotated (B) and mirrored in r (B), sits at the fine-grid
 // coordinates u_a = frac(x_a / P) n (a = x, y, z; n = 2N) and u_r = frac(r / P_r)
-// n_r (n_r = 2 N_r).  With the Kaiser-Bessel window phi of width W = 8 (the
+// n_r (n_r = 2 N_r) (half a period on, see the support box below).  With the Kaiser-Bessel window phi of width W = 8 (the
 // window of the correlation's spreading, its piecewise-polynomial evaluation
 // and its deconvolution table),
 //     G[g]     = sum_i prod_{a in x,y,z,r} phi(u_{i,a} - g_a)      (periodic in every axis)
@@ -13,8 +14,8 @@
 // which equals the direct sum of Eq. (rhoAhat) up to the window's aliasing
 // error, since exp(-2 pi i k u / n) = exp(-2 pi i k x / P).  Kept modes: xi_x,
 // xi_y in [-N/2, N/2) and eta in [-N_r/2, N_r/2) in FFT order, xi_z in [0, N/2)
-// (the density is real: the collapse uses the half space), in the layout of
-// the direct contractions, rho[(j_x N + j_y) (N/2 N_r) + m_z N_r + k].
+// (the density is real: the collapse uses the half space); they are formed
+// tile by tile inside k_l4_rc and never stored.
 //
 //   k_l4_spread   one warp per knot: the 4W window weights by the lanes, then
 //                 the W^4 stencil cells with atomic adds into the real grid
@@ -23,16 +24,19 @@
 //                 tile), keep m_z < N/2;
 //   k_l4_mid      transform along y, then along x (16 adjacent lines per tile,
 //                 one 128-byte row per position), keep N modes each;
-//   k_l4_r        transform along r, keep N_r modes, deconvolve, write rho^.
+//   k_l4_rc       transform along r of both shapes' x planes, keep N_r modes,
+//                 deconvolve, and form the collapse of the lifted correlation
+//                 (the sum over eta per section, as k_lift_collapse forms it
+//                 from rho^_A and rho^_B) without writing the spectra.
 // Support box: the coordinates are taken half a period on, u_a = frac(x_a / P +
 // 1/2) n and u_r = frac(r / P_r + 1/2) n_r, so that a shape around the origin
 // (and a lifted axis of radii in (0, L), mirrored for B) occupies one
 // contiguous range of cells per axis; k_l4_box finds the range the stencils
 // cover, and the grid, the spreading and every transform pass are restricted
 // to it (a range wider than the axis falls back to the whole axis).  The
-// half-period shift multiplies the spectrum by (-1)^(m_x + m_y + m_z + m_r),
-// undone with the deconvolution.  Box element i of an axis sits at line
-// position (lo + i) mod n; positions outside the box are zero.
+// half-period shift multiplies each spectrum by (-1)^(m_x + m_y + m_z + m_r),
+// which cancels in the product of the two spectra.  Box element i of an axis
+// sits at line position (lo + i) mod n; positions outside the box are zero.
 // Transforms: the library's shared-memory Stockham FFT (bc_fft.cuh) on tiles of
 // 16 interleaved lines.  The grid and the z planes share the workspace with
 // the y and x planes (each pass's output fits in the space its input left).
@@ -214,54 +218,103 @@ __global__ void __launch_bounds__(TB) k_l4_mid(const float2 *__restrict__ in, fl
     }
 }
 
-// Transform along r (length NF = n_r), keep N_r = NF/2 modes, deconvolve in all
-// four axes, undo the half-period shift and write rho^ in the contraction
-// layout.  X1[j_x][j_y][i_r][m_z] (the b box planes of a mode row are 512-byte
-// neighbours), box element i_r at position (lo + i_r) mod NF.
-template <int NF>
-__global__ void __launch_bounds__(TB) k_l4_r(const float2 *__restrict__ X1, float2 *rho, int N, int lo, int b,
-                                             const float *__restrict__ dxs, const float *__restrict__ drr,
-                                             const float2 *__restrict__ twg)
+// The r transforms of both spectra and the collapse of the lifted correlation
+// in one pass, without rho^ in memory: per tile (j_x, j_y, 16 z-modes) the box
+// planes of A and of B (X1[j_x][j_y][i_r][m_z], box element i_r at line position
+// (lo + i_r) mod n_r) are transformed along r, and for each section s
+//     h[s][j_x][j_y][m_z] = sign scale sum_{eta != -N_r/2} G^_A conj(G^_B)
+//                           (D_x D_y D_z D_r)^2 cone(|m|^2, eta)^2 exp(2 pi i eta r_s / P_r),
+// zero on the lower-edge modes (j_x or j_y = N/2); scale = P^-3 P_r^-1, sign =
+// (-1)^(m_x + m_y + m_z).  The half-period shifts of the two spectra cancel in
+// the product.  Thread (line c, eta group g) sums every 16th eta; the 16 groups
+// of a line are then added by shuffles within 16 lanes.
+template <int NF, int NS>
+__global__ void __launch_bounds__(TB) k_l4_rc(const float2 *__restrict__ XA, const float2 *__restrict__ XB, int N,
+                                              int loA, int bA, int loB, int bB, const float *__restrict__ dxs,
+                                              const float *__restrict__ drr, const float2 *__restrict__ cone,
+                                              const float *__restrict__ slices, int nslices, double period_r,
+                                              float scale, const float2 *__restrict__ twg, float2 *h)
 {
     extern __shared__ float2 l4sm[];
-    float2 *tw = l4sm, *A = tw + NF, *B = A + NF * CL;
-    constexpr int KEEP = NF / 2;
+    float2 *tw = l4sm, *TA = tw + NF, *SA = TA + NF * CL, *TBt = SA + NF * CL, *SB = TBt + NF * CL;
+    __shared__ float2 ph[NS][64];
+    constexpr int KEEP = NF / 2; // N_r
     for (int k = threadIdx.x; k < NF; k += TB) tw[k] = twg[k];
+    for (int e = threadIdx.x; e < NS * KEEP; e += TB) {
+        const int sec = e / KEEP, k = e - sec * KEEP;
+        float2 v = make_float2(0.f, 0.f);
+        if (sec < nslices) {
+            const int m = k < KEEP / 2 ? k : k - KEEP;
+            double arg = m * (double)slices[sec] / period_r;
+            arg -= rint(arg);
+            double sn, cs;
+            sincospi(2.0 * arg, &sn, &cs);
+            v = make_float2((float)cs, (float)sn);
+        }
+        ph[sec][k] = v;
+    }
     const int H = N / 2, nch = H / CL;
+    const long long plane = (long long)N * N * H;
     const long long tiles = (long long)N * N * nch;
+    const int c = threadIdx.x >> 4, g = threadIdx.x & 15;
     for (long long tt = blockIdx.x; tt < tiles; tt += gridDim.x) {
         const int o = (int)(tt / nch), ch = (int)(tt - (long long)o * nch);
         const int jx = o / N, jy = o - jx * N;
-        const float2 *src = X1 + (long long)o * b * H + CL * ch;
+        const float2 *srcA = XA + (long long)o * bA * H + CL * ch, *srcB = XB + (long long)o * bB * H + CL * ch;
         __syncthreads();
         for (int e = threadIdx.x; e < CL * NF; e += TB) {
-            const int pos = e / CL, c = e - pos * CL;
-            int i = (pos - lo) % NF;
-            i = i < 0 ? i + NF : i;
-            A[e] = i < b ? src[(long long)i * H + c] : make_float2(0.f, 0.f);
+            const int pos = e / CL, cc = e - pos * CL;
+            int ia = (pos - loA) % NF, ib = (pos - loB) % NF;
+            ia = ia < 0 ? ia + NF : ia;
+            ib = ib < 0 ? ib + NF : ib;
+            TA[e] = ia < bA ? srcA[(long long)ia * H + cc] : make_float2(0.f, 0.f);
+            TBt[e] = ib < bB ? srcB[(long long)ib * H + cc] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        const float2 *res = il_fft<NF, false, CL, TB>(A, B, tw);
-        const float dxy = dxs[jx] * dxs[jy];
-        float2 *dst = rho + (long long)o * H * KEEP + (long long)CL * ch * KEEP;
-        for (int e = threadIdx.x; e < CL * KEEP; e += TB) {
-            const int c = e / KEEP, k = e - c * KEEP;
+        const float2 *ra = il_fft<NF, false, CL, TB>(TA, SA, tw);
+        const float2 *rb = il_fft<NF, false, CL, TB>(TBt, SB, tw);
+        const int mz = CL * ch + c;
+        const int mx = jx < N / 2 ? jx : jx - N, my = jy < N / 2 ? jy : jy - N;
+        const int q = mx * mx + my * my + mz * mz;
+        const float dxyz = dxs[jx] * dxs[jy] * dxs[mz];
+        float2 acc[NS];
+#pragma unroll
+        for (int sec = 0; sec < NS; sec++) acc[sec] = make_float2(0.f, 0.f);
+        for (int k = g; k < KEEP; k += 16) {
+            if (k == KEEP / 2) continue;
             const int pos = k < KEEP / 2 ? k : NF - KEEP + k;
-            const int mz = CL * ch + c;
-            // (-1)^m of each axis: the parity of the FFT index (N and N_r are even)
-            const float sg = ((jx + jy + mz + k) & 1) ? -1.f : 1.f;
-            dst[e] = cscale(res[pos * CL + c], sg * dxy * dxs[mz] * drr[k]);
+            const float d = dxyz * drr[k];
+            const float2 f = cone[(long long)q * KEEP + k];
+            const float2 p = cscale(cmul(cmulc(ra[pos * CL + c], rb[pos * CL + c]), cmul(f, f)), d * d);
+#pragma unroll
+            for (int sec = 0; sec < NS; sec++) acc[sec] = cadd(acc[sec], cmul(p, ph[sec][k]));
+        }
+        const bool zero = jx == N / 2 || jy == N / 2;
+        const float sg = ((mx + my + mz) & 1) ? -scale : scale;
+#pragma unroll
+        for (int sec = 0; sec < NS; sec++) {
+            float2 v = acc[sec];
+#pragma unroll
+            for (int off = 8; off > 0; off >>= 1) {
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+            }
+            if (g == 0 && sec < nslices)
+                h[sec * plane + (long long)o * H + mz] = zero ? make_float2(0.f, 0.f) : cscale(v, sg);
         }
     }
 }
 
+// Workspace: the real grid (n_r (2N)^3 floats), the z planes (n_r (2N)^2 N/2
+// complex) and A's x planes (n_r N^2 N/2 complex); the y planes reuse the
+// grid's space, B's x planes the z planes'.
+static size_t l4_align(size_t b) { return (b + 255) & ~(size_t)255; }
 size_t lift4_ws_bytes(int N, int Nr)
 {
-    // the real grid (n_r (2N)^3 floats) and the z planes (n_r (2N)^2 N/2 complex);
-    // the y planes reuse the grid's space, the x planes the z planes'
     const size_t nr = 2 * (size_t)Nr, n = 2 * (size_t)N;
     const size_t g = sizeof(float) * nr * n * n * n, z = sizeof(float2) * nr * n * n * (N / 2);
-    return ((g + 255) & ~(size_t)255) + z;
+    const size_t x = sizeof(float2) * nr * (size_t)N * N * (N / 2);
+    return l4_align(g) + l4_align(z) + x;
 }
 
 template <int NF>
@@ -288,27 +341,14 @@ static cudaError_t l4_mid(const float2 *in, float2 *out, long long nouter, int n
     return cudaGetLastError();
 }
 
-template <int NF>
-static cudaError_t l4_r(const float2 *X1, float2 *rho, int N, int lo, int b, const float *dxs, const float *drr,
-                        const float2 *tw, int nsm, cudaStream_t s)
-{
-    const size_t smem = sizeof(float2) * (NF + 2 * (size_t)NF * CL);
-    cudaError_t e = set_smem(k_l4_r<NF>, smem);
-    if (e != cudaSuccess) return e;
-    k_l4_r<NF><<<resident_blocks(k_l4_r<NF>, smem, nsm), TB, smem, s>>>(X1, rho, N, lo, b, dxs, drr, tw);
-    return cudaGetLastError();
-}
-
-// rho (N^2 x N/2 x N_r complex, overwritten) = the lifted spectrum of n knots.
-// Synchronises s once (the support box comes back to the host through the
-// page-locked words hbox).
-cudaError_t lift4_spectrum(const Lift4Tables &t, int N, int Nr, const float4 *knots, int n, const double (&R)[9],
-                           int mirror, double period, double period_r, void *ws, float2 *rho, int nsm, cudaStream_t s)
+// The x planes X1[j_x][j_y][i_r][m_z] of n knots (box, spreading, z, y and x
+// passes); lo_r and b_r receive the box along r.  Synchronises s once (the
+// support box comes back to the host through the page-locked words hbox).
+static cudaError_t l4_xplanes(const Lift4Tables &t, int N, int Nr, const float4 *knots, int n, const L4Rot &rot,
+                              int mirror, double ip, double ipr, void *ws, float2 *X1, int &lo_r, int &b_r, int nsm,
+                              cudaStream_t s)
 {
     const int ns = 2 * N, nr = 2 * Nr, H = N / 2;
-    L4Rot rot;
-    for (int k = 0; k < 9; k++) rot.R[k] = R[k];
-    const double ip = 1.0 / period, ipr = 1.0 / period_r;
     // the support box
     cudaError_t e;
     if ((e = cudaMemsetAsync(t.dbox, 0x7f, 4 * sizeof(int), s)) != cudaSuccess ||
@@ -336,8 +376,10 @@ cudaError_t lift4_spectrum(const Lift4Tables &t, int N, int Nr, const float4 *kn
     const int bX = bx.b[0], bY = bx.b[1], bZ = bx.b[2], bR = bx.b[3];
     const size_t gfl = (size_t)bR * bX * bY * bZ;
     float *G = (float *)ws;
-    float2 *Z1 = (float2 *)((char *)ws + ((sizeof(float) * (size_t)nr * ns * ns * ns + 255) & ~(size_t)255));
-    float2 *Y1 = (float2 *)G, *X1 = Z1;
+    float2 *Z1 = (float2 *)((char *)ws + l4_align(sizeof(float) * (size_t)nr * ns * ns * ns));
+    float2 *Y1 = (float2 *)G;
+    lo_r = bx.lo[3];
+    b_r = bR;
     if ((e = cudaMemsetAsync(G, 0, sizeof(float) * gfl, s)) != cudaSuccess) return e;
     if (n > 0) {
         const int blocks = (n + 7) / 8 < 65535 ? (n + 7) / 8 : 65535;
@@ -370,14 +412,57 @@ cudaError_t lift4_spectrum(const Lift4Tables &t, int N, int Nr, const float4 *kn
         cudaSuccess)
         return e;
     // x: outer (i_r, j_y), Y1[i_r][i_x][j_y][m_z] -> X1[j_x][j_y][i_r][m_z]
-    if ((e = mid(Y1, X1, (long long)bR * N, N, (long long)bX * N * H, H, (long long)N * H, H, (long long)bR * H,
-                 (long long)N * bR * H, bx.lo[0], bX)) != cudaSuccess)
-        return e;
-    // r: X1[j_x][j_y][i_r][m_z] -> rho[(j_x N + j_y)][m_z][k], deconvolved
+    return mid(Y1, X1, (long long)bR * N, N, (long long)bX * N * H, H, (long long)N * H, H, (long long)bR * H,
+               (long long)N * bR * H, bx.lo[0], bX);
+}
+
+template <int NF, int NS>
+static cudaError_t l4_rc(const float2 *XA, const float2 *XB, int N, int loA, int bA, int loB, int bB,
+                         const Lift4Tables &t, const float2 *cone, const float *slices, int nslices, double period_r,
+                         float scale, float2 *h, int nsm, cudaStream_t s)
+{
+    const size_t smem = sizeof(float2) * (NF + 4 * (size_t)NF * CL);
+    cudaError_t e = set_smem(k_l4_rc<NF, NS>, smem);
+    if (e != cudaSuccess) return e;
+    k_l4_rc<NF, NS><<<resident_blocks(k_l4_rc<NF, NS>, smem, nsm), TB, smem, s>>>(
+        XA, XB, N, loA, bA, loB, bB, t.deconv_s, t.deconv_r, cone, slices, nslices, period_r, scale, t.tw_r, h);
+    return cudaGetLastError();
+}
+
+template <int NF>
+static cudaError_t l4_rc_ns(const float2 *XA, const float2 *XB, int N, int loA, int bA, int loB, int bB,
+                            const Lift4Tables &t, const float2 *cone, const float *slices, int nslices,
+                            double period_r, float scale, float2 *h, int nsm, cudaStream_t s)
+{
+    if (nslices <= 1) return l4_rc<NF, 1>(XA, XB, N, loA, bA, loB, bB, t, cone, slices, nslices, period_r, scale, h, nsm, s);
+    if (nslices <= 2) return l4_rc<NF, 2>(XA, XB, N, loA, bA, loB, bB, t, cone, slices, nslices, period_r, scale, h, nsm, s);
+    if (nslices <= 4) return l4_rc<NF, 4>(XA, XB, N, loA, bA, loB, bB, t, cone, slices, nslices, period_r, scale, h, nsm, s);
+    if (nslices <= 8) return l4_rc<NF, 8>(XA, XB, N, loA, bA, loB, bB, t, cone, slices, nslices, period_r, scale, h, nsm, s);
+    return l4_rc<NF, 16>(XA, XB, N, loA, bA, loB, bB, t, cone, slices, nslices, period_r, scale, h, nsm, s);
+}
+
+cudaError_t lift4_pair(const Lift4Tables &t, int N, int Nr, const float4 *kA, int nA, const float4 *kB, int nB,
+                       const double (&RB)[9], double period, double period_r, const float2 *cone, const float *slices,
+                       int nslices, float scale, void *ws, float2 *h, int nsm, cudaStream_t s)
+{
+    const int ns = 2 * N, nr = 2 * Nr;
+    if (nA == 0 || nB == 0) return cudaMemsetAsync(h, 0, sizeof(float2) * (size_t)N * N * (N / 2) * nslices, s);
+    const double ip = 1.0 / period, ipr = 1.0 / period_r;
+    float2 *Z1 = (float2 *)((char *)ws + l4_align(sizeof(float) * (size_t)nr * ns * ns * ns));
+    float2 *XA = (float2 *)((char *)Z1 + l4_align(sizeof(float2) * (size_t)nr * ns * ns * (N / 2)));
+    L4Rot ra, rb;
+    for (int k = 0; k < 9; k++) {
+        ra.R[k] = (k % 4 == 0) ? 1.0 : 0.0; // A unrotated
+        rb.R[k] = RB[k];
+    }
+    int loA = 0, bA = nr, loB = 0, bB = nr;
+    cudaError_t e;
+    if ((e = l4_xplanes(t, N, Nr, kA, nA, ra, 0, ip, ipr, ws, XA, loA, bA, nsm, s)) != cudaSuccess) return e;
+    if ((e = l4_xplanes(t, N, Nr, kB, nB, rb, 1, ip, ipr, ws, Z1, loB, bB, nsm, s)) != cudaSuccess) return e;
     switch (nr) {
-    case 32: return l4_r<32>(X1, rho, N, bx.lo[3], bR, t.deconv_s, t.deconv_r, t.tw_r, nsm, s);
-    case 64: return l4_r<64>(X1, rho, N, bx.lo[3], bR, t.deconv_s, t.deconv_r, t.tw_r, nsm, s);
-    case 128: return l4_r<128>(X1, rho, N, bx.lo[3], bR, t.deconv_s, t.deconv_r, t.tw_r, nsm, s);
+    case 32: return l4_rc_ns<32>(XA, Z1, N, loA, bA, loB, bB, t, cone, slices, nslices, period_r, scale, h, nsm, s);
+    case 64: return l4_rc_ns<64>(XA, Z1, N, loA, bA, loB, bB, t, cone, slices, nslices, period_r, scale, h, nsm, s);
+    case 128: return l4_rc_ns<128>(XA, Z1, N, loA, bA, loB, bB, t, cone, slices, nslices, period_r, scale, h, nsm, s);
     default: return cudaErrorInvalidValue;
     }
 }
