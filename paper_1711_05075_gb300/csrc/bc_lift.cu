@@ -40,6 +40,9 @@
 //   k_lift_ifft_x     inverse transform along x; the inverse along y and the
 //                     complex-to-real inverse along z are the correlation's own
 //                     passes (k_ifft_y, k_ifft_z).
+// Contraction 3 computes both spectra by the 4D type-1 NUFFT and forms the
+// collapse from them in bc_lift_nufft.cu (lift4_pair), in place of the direct
+// contractions and k_lift_collapse.
 #include <cmath>
 #include <cstring>
 #include <new>
