@@ -331,7 +331,7 @@ bc_status bc_lift_destroy(bc_lift_t lift);
  * the fastest in the context and returns them in out (may be NULL).  It
  * synchronises the stream, grows the context's workspaces to the largest
  * candidate and ends any profiling started with bc_profile_begin; it leaves
- * `graphs` as it is.  Errors: BC_ERR_ARG (null context
+ * `graphs` and `overlap` as they are.  Errors: BC_ERR_ARG (null context
  * or shape, shapes from another context, rotations outside [0, 65534], a
  * value out of range in bc_set_tuning), BC_ERR_OOM, BC_ERR_CUDA. */
 typedef struct {
@@ -495,7 +495,7 @@ bc_status bc_learned_sweep_cascade(bc_ctx_t ctx, bc_mlp_t net, bc_shape_t A, bc_
  * Errors as bc_learned_sweep_cascade (with coarse_keep in place of topk in
  * the range checks), and BC_ERR_ARG for a null coarse context or shape, coarse
  * shapes from another context or with other knot counts than A and B, a
- * coarse context with other levels or period, or topk outside
+ * coarse context with other radius levels or period, or topk outside
  * [1, coarse_keep]. */
 bc_status bc_learned_sweep_coarse(bc_ctx_t ctx, bc_mlp_t net, bc_shape_t A, bc_shape_t B, const float *quats, int n,
                                   int topk, const float *orients, int norient, int keep, bc_ctx_t cctx, bc_shape_t Ac,

@@ -1693,8 +1693,8 @@ bc_status bc_learned_sweep_coarse(bc_ctx_t c, bc_mlp_t net, bc_shape_t A, bc_sha
         if (topk < 1 || topk > coarse_keep) return fail(BC_ERR_ARG, "bc_learned_sweep_coarse: topk must be in [1, coarse_keep]");
         if (Ac->n != A->n || Bc->n != B->n)
             return fail(BC_ERR_ARG, "bc_learned_sweep_coarse: coarse shapes have other knot counts than A and B");
-        if (cc->g.L != c->g.L || cc->period != c->period)
-            return fail(BC_ERR_ARG, "bc_learned_sweep_coarse: the coarse context has other levels or another period");
+        if (cc->radii != c->radii || cc->period != c->period)
+            return fail(BC_ERR_ARG, "bc_learned_sweep_coarse: the coarse context has other radius levels or another period");
         cudaStream_t st = c->stream;
         cudaError_t e;
         const size_t cm = (size_t)coarse_keep, tk = (size_t)topk;
