@@ -264,7 +264,8 @@ typedef struct {
                         0 direct 4D NDFT in FP32 on the CUDA cores;
                         3 4D type-1 NUFFT: Kaiser-Bessel spreading (width 8) of the lifted
                           knots onto the (2N)^3 x 2Nr grid, a 4D FFT keeping the modes
-                          above, deconvolution (Nr >= 16; workspace 48 x 2Nr x N^3 bytes) */
+                          above, deconvolution, the collapse formed from the two
+                          spectra directly (Nr >= 16; workspace 52 x 2Nr x N^3 bytes) */
 } bc_lift_params;
 bc_status bc_lift_create(const bc_lift_params *params, void *cuda_stream, bc_lift_t *out);
 bc_status bc_lift_correlate(bc_lift_t lift, const float *A, int nA, const float *B, int nB, const float *quat,
