@@ -353,6 +353,7 @@ def run_ours(args, rank, world, local_rank):
 
         def worker(t, n, errs):
             try:
+                torch.cuda.set_device(dev)  # a new host thread starts on device 0
                 for _ in range(n):
                     ha, hb = bc.bc_shapes_create(ctxs[t].handle, [xa, xb], [la, lb], [wl.A.n, wl.B.n], 0)
                     bc.bc_correlate(ctxs[t].handle, ha, hb, q, 1, outs[t], 0)
