@@ -39,7 +39,9 @@
  *   - Caller-owned buffers stay caller-owned; the library copies what it keeps
  *     and owns all of its internal workspaces.
  *   - A context (and everything created on it) is used by one host thread at
- *     a time; different contexts may be used from different threads.
+ *     a time; different contexts may be used from different threads.  The
+ *     calling thread's current CUDA device must be the one that was current
+ *     when the context was created (a new host thread starts on device 0).
  */
 #ifndef BALLCORR_H
 #define BALLCORR_H
